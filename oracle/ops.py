@@ -1,0 +1,132 @@
+"""Oracle: reduce, inclusive scan, view copy and segmented reduce+scan
+(test infrastructure).
+
+Section 5 names four benchmarks -- block-wide parallel reduction, matrix
+transposition, scan and matrix multiplication -- without fixing their
+operators or types.  Readings used here: the reduction and the scan are sums
+(the scan inclusive), over int32 (two's-complement wrap-around, i.e. exact
+arithmetic mod 2^32) or FP32.
+
+All three ops here are defined over views (module ``views``).  The logical
+domain of a view is its select dimensions (in select order) followed by the
+dimensions left after its last op, in row-major order.
+
+  reduce  out[o] = sum of in[index(p)] over the logical points p whose
+          selected coordinates at levels <= out_level linearise to o
+  scan    within each segment -- the points sharing their selected coordinates
+          at levels <= seg_level -- out[index(p)] = sum of in[index(q)] over
+          q <= p in logical order
+  copy    out[index_out(p)] = in[index_in(p)] for every logical point p
+          (the transpose is the copy whose input view is a transpose)
+
+Integers are summed in int64 and wrapped to int32 at the end.  FP32 sums are
+exact (math.fsum, correctly rounded to FP64); FP32 prefix sums are FP64
+cumulative sums, whose error is below n * 2^-53 * sum|x| (< 3e-8 * sum|x| for
+n <= 2^28), far inside the 1e-5 * sum|x| tolerance they are compared with.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import views as V
+
+
+def wrap_i32(v):
+    """int64 -> int32 two's-complement wrap-around."""
+    v = np.asarray(v, dtype=np.int64)
+    return (((v + (1 << 31)) & ((1 << 32) - 1)) - (1 << 31)).astype(np.int32)
+
+
+def _rows(x, base_shape, ops, keep_level):
+    """Values of the logical domain as a 2-D array: one row per combination
+    of the selected coordinates at levels <= keep_level, the rest of the
+    domain (in logical order) along the row.  Returns (values, raw indices)."""
+    idx = V.domain_indices(base_shape, ops)
+    sels = V.selects(base_shape, ops)
+    nkeep = sum(1 for (lvl, _, _) in sels if lvl <= keep_level)
+    rows = int(np.prod([e for (_, _, e) in sels[:nkeep]])) if nkeep else 1
+    idx = idx.reshape(rows, -1)
+    return np.asarray(x).reshape(-1)[idx], idx
+
+
+def reduce(x, base_shape, ops, out_level, grid=None, block=None):
+    """Sum over the view, one output per resource at ``out_level``
+    (GRID: one scalar).  int32 input -> int32 output (wrapped); FP32 input
+    -> exact sums in FP64.  Also returns sum|x| per output (FP only)."""
+    if grid is not None:
+        V.check_selects(base_shape, ops, grid, block)
+    vals, _ = _rows(x, base_shape, ops, out_level)
+    if vals.dtype == np.int32:
+        return wrap_i32(vals.astype(np.int64).sum(axis=1)), None
+    s = np.array([math.fsum(r) for r in vals.astype(np.float64)])
+    a = np.array([math.fsum(np.abs(r)) for r in vals.astype(np.float64)])
+    return s, a
+
+
+def scan(x, out_init, base_shape, ops, seg_level, grid=None, block=None):
+    """Inclusive prefix sums over the view, segmented at ``seg_level``.
+
+    Returns (out, prefix_abs): ``out`` is ``out_init`` with every element the
+    view reaches replaced by its prefix sum (int32 wrapped, or FP64), and
+    ``prefix_abs`` the matching sum_{q<=p} |x_q| (FP only, else None)."""
+    if grid is not None:
+        V.check_selects(base_shape, ops, grid, block)
+    vals, idx = _rows(x, base_shape, ops, seg_level)
+    out = np.array(out_init, copy=True).reshape(-1)
+    if vals.dtype == np.int32:
+        out[idx.reshape(-1)] = wrap_i32(np.cumsum(vals.astype(np.int64), axis=1)).reshape(-1)
+        return out.reshape(np.shape(out_init)), None
+    out = out.astype(np.float64)
+    pa = np.zeros_like(out)
+    out[idx.reshape(-1)] = np.cumsum(vals.astype(np.float64), axis=1).reshape(-1)
+    pa[idx.reshape(-1)] = np.cumsum(np.abs(vals.astype(np.float64)), axis=1).reshape(-1)
+    return out.reshape(np.shape(out_init)), pa.reshape(np.shape(out_init))
+
+
+def view_copy(x, out_init, in_shape, in_ops, out_shape, out_ops):
+    """out[index_out(p)] = in[index_in(p)] over the common logical domain."""
+    if V.domain_shape(in_shape, in_ops) != V.domain_shape(out_shape, out_ops):
+        raise V.ViewError("input and output views have different domains")
+    ii = V.domain_indices(in_shape, in_ops).reshape(-1)
+    oi = V.domain_indices(out_shape, out_ops).reshape(-1)
+    out = np.array(out_init, copy=True).reshape(-1)
+    out[oi] = np.asarray(x).reshape(-1)[ii]
+    return out.reshape(np.shape(out_init))
+
+
+def transpose2d(x):
+    """out[j][i] = in[i][j] for a row-major R x C matrix, element by element."""
+    R, C = x.shape
+    out = np.empty((C, R), dtype=x.dtype)
+    for i in range(R):
+        out[:, i] = x[i, :]
+    return out
+
+
+def segmented_reduce_scan(x, offsets):
+    """Per segment s = [offsets[s], offsets[s+1]): its sum and its inclusive
+    prefix sums.  Returns (scan (FP64 / wrapped int32), sums, prefix |x|,
+    sum |x| per segment).  Empty segments have sum 0."""
+    x = np.asarray(x)
+    off = np.asarray(offsets, dtype=np.int64)
+    S = off.size - 1
+    is_int = x.dtype == np.int32
+    scan_out = np.zeros(x.size, dtype=np.int32 if is_int else np.float64)
+    pa = None if is_int else np.zeros(x.size, dtype=np.float64)
+    sums = np.zeros(S, dtype=np.int32 if is_int else np.float64)
+    sabs = None if is_int else np.zeros(S, dtype=np.float64)
+    for s in range(S):
+        a, b = int(off[s]), int(off[s + 1])
+        seg = x[a:b]
+        if is_int:
+            scan_out[a:b] = wrap_i32(np.cumsum(seg.astype(np.int64)))
+            sums[s] = wrap_i32(seg.astype(np.int64).sum())
+        else:
+            seg64 = seg.astype(np.float64)
+            scan_out[a:b] = np.cumsum(seg64)
+            pa[a:b] = np.cumsum(np.abs(seg64))
+            sums[s] = math.fsum(seg64)
+            sabs[s] = math.fsum(np.abs(seg64))
+    return scan_out, sums, pa, sabs

@@ -1,0 +1,136 @@
+"""Pins of the oracle's reduce, scan, view copy and segmented ops (CPU only):
+closed forms, brute force with per-point resolution, invariants between ops,
+and NumPy's transpose as a library special case."""
+import math
+import random
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import ops as O
+from oracle import views as V
+
+
+def brute_reduce(x, base, ops, out_level):
+    """Per-point loop: resolve each logical point on its own."""
+    dom = V.domain_shape(base, ops)
+    sels = V.selects(base, ops)
+    nsel = len(sels)
+    nkeep = sum(1 for s in sels if s[0] <= out_level)
+    nout = math.prod(dom[:nkeep]) if nkeep else 1
+    out = [0] * nout
+    flat = np.asarray(x).reshape(-1)
+    for p in np.ndindex(*dom):
+        e = V.resolve(base, ops, list(p[:nsel]), list(p[nsel:]))
+        o = 0
+        for c, n in zip(p[:nkeep], dom[:nkeep]):
+            o = o * n + c
+        out[o] += int(flat[e])
+    return O.wrap_i32(out)
+
+
+def test_closed_forms():
+    n = 1000
+    x = np.arange(1, n + 1, dtype=np.int32)
+    s, _ = O.reduce(x, [n], [], V.GRID)
+    assert s[0] == n * (n + 1) // 2
+    y, _ = O.scan(x, np.zeros(n, np.int32), [n], [], V.GRID)
+    i = np.arange(n, dtype=np.int64)
+    assert np.array_equal(y, (i + 1) * (i + 2) // 2)
+    ones = np.ones(n, dtype=np.int32)
+    y, _ = O.scan(ones, np.zeros(n, np.int32), [n], [], V.GRID)
+    assert np.array_equal(y, np.arange(1, n + 1))
+    assert O.reduce(ones, [n], [], V.GRID)[0][0] == n
+
+
+def test_int32_wraps_mod_2_32():
+    x = np.array([2**31 - 1, 1, 5], dtype=np.int32)
+    assert O.reduce(x, [3], [], V.GRID)[0][0] == -2**31 + 5
+    y, _ = O.scan(x, np.zeros(3, np.int32), [3], [], V.GRID)
+    assert y.tolist() == [2**31 - 1, -2**31, -2**31 + 5]
+
+
+def test_fp32_sum_is_exact_on_the_grid():
+    x = synth.uniform_grid(1 << 16, seed=3).numpy()
+    k = (x.astype(np.float64) * 2**23).astype(np.int64)
+    assert np.array_equal(k.astype(np.float64) * 2.0**-23, x.astype(np.float64))
+    s, a = O.reduce(x, [x.size], [], V.GRID)
+    assert s[0] == k.sum() * 2.0**-23
+    assert a[0] == np.abs(k).sum() * 2.0**-23
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_reduce_brute_force(seed):
+    rng = random.Random(seed)
+    n = rng.choice([128, 256])
+    g = rng.choice([2, 4])
+    x = synth.ints_pm1000(n, seed=seed).numpy()
+    ops = [("group", n // g, 0), ("select", V.BLOCK, V.X)]
+    if rng.random() < 0.5:
+        ops.append(("reverse", 0))
+    ops += [("group", 32, 0), ("select", V.WARP, V.X), ("select", V.THREAD, V.X)]
+    block = (n // g, 1, 1)
+    for lvl in (V.GRID, V.BLOCK, V.WARP, V.THREAD):
+        want = brute_reduce(x, [n], ops, lvl)
+        got, _ = O.reduce(x, [n], ops, lvl, (g, 1, 1), block)
+        assert np.array_equal(got, want)
+
+
+def test_last_scan_element_is_the_reduce():
+    for seed in range(5):
+        x = synth.ints_pm1000(4096, seed=seed).numpy()
+        ops = [("group", 1024, 0), ("select", V.BLOCK, V.X)]
+        y, _ = O.scan(x, np.zeros_like(x), [4096], ops, V.BLOCK)
+        r, _ = O.reduce(x, [4096], ops, V.BLOCK)
+        assert np.array_equal(y.reshape(4, 1024)[:, -1], r)
+        # consecutive differences give the input back (integers)
+        assert np.array_equal(np.diff(y.reshape(4, 1024).astype(np.int64), axis=1) % 2**32,
+                              x.reshape(4, 1024)[:, 1:].astype(np.int64) % 2**32)
+
+
+def test_scan_through_transpose_is_column_scan():
+    x = synth.ints_pm1000(12, seed=1).numpy().reshape(3, 4)
+    ops = [("transpose", 0), ("select", V.THREAD, V.X)]
+    y, _ = O.scan(x, np.zeros_like(x), [3, 4], ops, V.THREAD, (1, 1, 1), (4, 1, 1))
+    want = np.cumsum(x.astype(np.int64), axis=0)
+    assert np.array_equal(y, want)
+
+
+def test_segmented_with_one_segment_is_plain_scan():
+    x = synth.uniform_grid(777, seed=2).numpy()
+    y, _ = O.scan(x, np.zeros(777), [777], [], V.GRID)
+    ys, sums, _, _ = O.segmented_reduce_scan(x, [0, 777])
+    assert np.array_equal(ys, y)
+    assert sums[0] == O.reduce(x, [777], [], V.GRID)[0][0]
+
+
+def test_segmented_invariants():
+    L = synth.loguniform_lengths(60, seed=4, max_len=300).numpy()
+    L[5] = 0
+    L[6] = 1
+    off = np.concatenate([[0], np.cumsum(L)])
+    x = synth.ints_pm1000(int(off[-1]), seed=4).numpy()
+    ys, sums, _, _ = O.segmented_reduce_scan(x, off)
+    assert sums[5] == 0
+    assert ys[off[6]] == x[off[6]]
+    for s in range(len(L)):
+        if L[s]:
+            assert ys[off[s + 1] - 1] == sums[s]
+    assert O.wrap_i32(sums.astype(np.int64).sum()) == O.reduce(x, [x.size], [], V.GRID)[0][0]
+
+
+def test_transpose_matches_numpy_and_involution():
+    for R, C in ((33, 65), (1, 17), (17, 1), (64, 64)):
+        x = synth.normal_f32(R * C, seed=R).numpy().reshape(R, C)
+        t = O.transpose2d(x)
+        assert np.array_equal(t, x.T)
+        assert np.array_equal(O.transpose2d(t), x)
+        via_view = O.view_copy(x, np.zeros((C, R), np.float32), [R, C], [("transpose", 0)], [C, R], [])
+        assert np.array_equal(via_view, x.T)
+
+
+def test_view_copy_leaves_unreached_elements():
+    x = np.arange(10, dtype=np.float32)
+    out = O.view_copy(x, np.full(10, -7.0, np.float32), [10], [("split_fst", 4, 0)], [10], [("split_snd", 6, 0)])
+    assert out.tolist() == [-7.0] * 6 + [0.0, 1.0, 2.0, 3.0]
