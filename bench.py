@@ -1,0 +1,408 @@
+"""Benchmark of the memory-bound hot path on GB300.
+
+One step = one pass over the full-HBM memory-bound workload:
+  * int32 sum reduce of 2^30 values in [-1000, 1000] through the hierarchical
+    view group(1024)[[block]].group(32)[[warp]][[thread]] (one scalar out),
+  * FP32 inclusive scan of 2^28 values uniform in [-1, 1),
+  * FP32 out-of-place transpose of a 16384 x 16384 N(0,1) matrix,
+each through libdesc's C ABI, inputs resident in HBM.  value = algorithmic
+bytes of the step (reduce 4 B/elem, scan 8 B/elem, transpose 8 B/elem) per
+second.  Every input is larger than L2, so no flush is needed between steps.
+
+--impl reference times the CPU oracle instead, on bounded samples of the same
+workload, and prints the same line with "impl": "reference".
+Under torchrun every rank runs its own replica (the ops are single-GPU; no
+data-path collective); value sums the ranks' bytes over the slowest rank.
+"""
+from __future__ import annotations
+
+import argparse
+import datetime as dt
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "HBM GB/s & % roofline (reduce/scan/transpose); matmul TFLOP/s at stated error"
+WORKLOAD = "full-HBM memory-bound set: int32 reduce 2^30, FP32 inclusive scan 2^28, FP32 transpose 16384x16384"
+
+
+def sizes(small):
+    if small:   # for profiler captures: still larger than L2, a few hundred MB on the device
+        return {"reduce_n": 1 << 26, "scan_n": 1 << 26, "T": 4096}
+    return {"reduce_n": 1 << 30, "scan_n": 1 << 28, "T": 16384}
+
+
+def op_bytes(sz):
+    return {"reduce": 4 * sz["reduce_n"], "scan": 8 * sz["scan_n"], "transpose": 8 * sz["T"] * sz["T"]}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return {"hbm_gbs": float(d["hbm_gbs"]), "bf16_tflops": float(d["bf16_tflops"]),
+                "bf16_tflops_sustained": float(d.get("bf16_tflops_sustained", d["bf16_tflops"])),
+                "source": "measured"}
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "source": "fallback"}
+
+
+def traffic_for(op):
+    """DRAM bytes per launch from the committed ncu summary, or None when the
+    kernel source has changed since those counters were taken."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        f = line.split()
+        if len(f) >= 4 and not line.startswith("#") and f[0] == op:
+            src = os.path.join(ROOT, "paper_2305_03448_gb300", "csrc", f[3])
+            if os.path.exists(src) and hashlib.sha256(open(src, "rb").read()).hexdigest()[:12] == f[2]:
+                return float(f[1])
+    return None
+
+
+class Clocks:
+    """nvidia-smi samples of this GPU while the timed region runs."""
+    Q = ("timestamp,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = (uuid or "").lower()
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                                       "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+
+    def stop(self, t0, t1):
+        if self.p is None:
+            return None
+        time.sleep(0.1)
+        self.p.terminate()
+        out, _ = self.p.communicate(timeout=10)
+        rows = []
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            if self.uuid and self.uuid not in f[1].lower():
+                continue
+            try:
+                ts = dt.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append((ts, float(f[2]), float(f[3]), f[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        win = [r for r in rows if t0 - 0.05 <= r[0] <= t1 + 0.05] or rows
+        sm = sorted(r[1] for r in win)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in win for i in range(4) if r[3][i].lower().startswith("active")})
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(r[2] for r in win), "reasons": reasons,
+                "samples": len(win), "window": "timed" if len(win) < len(rows) or t1 - t0 > 0.05 else "run"}
+
+
+# --------------------------------------------------------------------- ours
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import paper_2305_03448_gb300 as D
+    import synth
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    sz = sizes(args.small)
+    nb = op_bytes(sz)
+    Rn, Sn, T = sz["reduce_n"], sz["scan_n"], sz["T"]
+    V = D
+    red_ops = [("group", 1024, 0), ("select", V.BLOCK, V.X), ("group", 32, 0), ("select", V.WARP, V.X),
+               ("select", V.THREAD, V.X)]
+    red_grid, red_block = (Rn // 1024, 1, 1), (1024, 1, 1)
+
+    xr = synth.ints_pm1000(Rn, seed=1 + rank, device=dev)
+    xs = synth.uniform_grid(Sn, seed=2 + rank, device=dev)
+    xt = synth.normal_f32(T * T, seed=3 + rank, device=dev).reshape(T, T)
+    out_r = torch.empty(1, dtype=torch.int32, device=dev)
+    out_s = torch.empty_like(xs)
+    out_t = torch.empty(T, T, dtype=torch.float32, device=dev)
+
+    def ws_for(kind):
+        import ctypes
+        n = ctypes.c_size_t(0)
+        L = D.lib()
+        if kind == "reduce":
+            L.desc_reduce_workspace_size(ctypes.byref(D.make_view([Rn], red_ops)),
+                                         ctypes.byref(D.make_exec(red_grid, red_block)), V.GRID, V.I32, ctypes.byref(n))
+        else:
+            L.desc_scan_workspace_size(ctypes.byref(D.make_view([Sn], [])), None, V.GRID, V.F32, ctypes.byref(n))
+        return torch.empty(max(n.value, 1), dtype=torch.uint8, device=dev)
+
+    ws_r, ws_s = ws_for("reduce"), ws_for("scan")
+    stream = torch.cuda.current_stream(dev)
+
+    def op_reduce(x=xr, out=out_r):
+        D.desc_reduce(x, [Rn], red_ops, V.GRID, red_grid, red_block, out=out, ws=ws_r, stream=stream)
+
+    def op_scan(x=xs, out=out_s):
+        D.desc_scan(x, [Sn], [], V.GRID, out=out, ws=ws_s, stream=stream)
+
+    def op_transpose(x=xt, out=out_t):
+        D.desc_transpose(x, [T, T], [("transpose", 0)], out, [T, T], [], stream=stream)
+
+    ops = [("reduce", op_reduce), ("scan", op_scan), ("transpose", op_transpose)]
+    only = set(args.ops.split(",")) if args.ops else None
+    if only:
+        ops = [o for o in ops if o[0] in only]
+    for _ in range(args.warmup):
+        for _, f in ops:
+            f()
+    torch.cuda.synchronize(dev)
+    status = D.desc_stream_status(stream)
+    if status != 0:
+        raise RuntimeError(f"device status {status} after warm-up")
+
+    K = args.steps
+    ev = {name: [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+          for name, _ in ops}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = Clocks(getattr(torch.cuda.get_device_properties(dev), "uuid", None) and
+                    str(torch.cuda.get_device_properties(dev).uuid)) if rank == 0 else None
+    if clocks:
+        clocks.start()
+        time.sleep(0.3)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    t0 = time.time()
+    e0.record(stream)
+    for k in range(K):
+        for name, f in ops:
+            a, b = ev[name][k]
+            a.record(stream)
+            f()
+            b.record(stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    t1 = time.time()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop(t0, t1) if clocks else None
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        tt = torch.tensor([ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        ms = float(tt.item())
+    status = D.desc_stream_status(stream)
+    if status != 0:
+        raise RuntimeError(f"device status {status} in the timed region")
+    step_bytes = sum(nb[name] for name, _ in ops)
+    value = world * step_bytes * K / (ms * 1e-3) / 1e9
+    per_op = {}
+    for name, _ in ops:
+        d = [a.elapsed_time(b) for a, b in ev[name]]
+        avg = sum(d) / len(d)
+        per_op[name] = {"ms": round(avg, 4), "GB/s": round(nb[name] / (avg * 1e-3) / 1e9, 1)}
+    pk = peaks()
+    for name in per_op:
+        per_op[name]["frac"] = round(per_op[name]["GB/s"] / pk["hbm_gbs"], 4)
+    dom = max(per_op, key=lambda n: per_op[n]["ms"])
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": per_op[dom]["GB/s"], "peak": pk["hbm_gbs"],
+                "unit": "GB/s", "frac": per_op[dom]["frac"],
+                "peak_source": f"{pk['source']} hbm_gbs (of {pk['source']})",
+                "traffic": traffic_for(dom)}
+
+    # end to end: pinned host buffers, copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, torch, dev, stream, ops, nb, Rn, Sn, T, op_reduce, op_scan, op_transpose, world)
+
+    line = {"metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world, "steps": K,
+            "warmup": args.warmup, "ms_per_step": round(ms / K, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "i32/f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD + (" (small)" if args.small else ""),
+                       "reduce_n": Rn, "scan_n": Sn, "transpose": [T, T],
+                       "reduce_view": "group(1024)[[block]].group(32)[[warp]][[thread]]",
+                       "l2": "inputs larger than L2 (129 MB); no flush", "parallelism": f"replicas x{world}"},
+            "ops": per_op, "roofline": roofline, "gpu_launches": K * len(ops), "e2e": e2e}
+    if clk:
+        line["clocks"] = {k: clk[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")}
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(sz, only)
+    return line
+
+
+def run_e2e(args, torch, dev, stream, ops, nb, Rn, Sn, T, op_reduce, op_scan, op_transpose, world):
+    names = [n for n, _ in ops]
+    h = {}
+    if "reduce" in names:
+        h["xr"] = torch.empty(Rn, dtype=torch.int32, pin_memory=True)
+        h["or"] = torch.empty(1, dtype=torch.int32, pin_memory=True)
+    if "scan" in names:
+        h["xs"] = torch.empty(Sn, dtype=torch.float32, pin_memory=True)
+        h["os"] = torch.empty(Sn, dtype=torch.float32, pin_memory=True)
+    if "transpose" in names:
+        h["xt"] = torch.empty(T, T, dtype=torch.float32, pin_memory=True)
+        h["ot"] = torch.empty(T, T, dtype=torch.float32, pin_memory=True)
+    import synth
+    if "reduce" in names:
+        h["xr"].copy_(synth.ints_pm1000(Rn, seed=1, device=dev))
+    if "scan" in names:
+        h["xs"].copy_(synth.uniform_grid(Sn, seed=2, device=dev))
+    if "transpose" in names:
+        h["xt"].copy_(synth.normal_f32(T * T, seed=3, device=dev).reshape(T, T))
+    dr = torch.empty(Rn, dtype=torch.int32, device=dev) if "reduce" in names else None
+    or_ = torch.empty(1, dtype=torch.int32, device=dev)
+    ds = torch.empty(Sn, dtype=torch.float32, device=dev) if "scan" in names else None
+    os_ = torch.empty_like(ds) if ds is not None else None
+    dt_ = torch.empty(T, T, dtype=torch.float32, device=dev) if "transpose" in names else None
+    ot = torch.empty_like(dt_) if dt_ is not None else None
+    h2d = d2h = 0
+
+    def step():
+        nonlocal h2d, d2h
+        h2d = d2h = 0
+        if dr is not None:
+            dr.copy_(h["xr"], non_blocking=True); h2d += Rn * 4
+            op_reduce(dr, or_)
+            h["or"].copy_(or_, non_blocking=True); d2h += 4
+        if ds is not None:
+            ds.copy_(h["xs"], non_blocking=True); h2d += Sn * 4
+            op_scan(ds, os_)
+            h["os"].copy_(os_, non_blocking=True); d2h += Sn * 4
+        if dt_ is not None:
+            dt_.copy_(h["xt"], non_blocking=True); h2d += T * T * 4
+            op_transpose(dt_, ot)
+            h["ot"].copy_(ot, non_blocking=True); d2h += T * T * 4
+
+    K = max(3, min(args.steps, args.e2e_steps))
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize(dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(K):
+        step()
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = a.elapsed_time(b)
+    if world > 1:
+        tt = torch.tensor([ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        ms = float(tt.item())
+    step_bytes = sum(nb[n] for n in names)
+    return {"value": round(world * step_bytes * K / (ms * 1e-3) / 1e9, 1), "unit": "GB/s",
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": K,
+            "ms_per_step": round(ms / K, 3)}
+
+
+# --------------------------------------------------------------------- oracle
+def oracle_rate(sz, only, scale):
+    """GB/s of the CPU oracle on samples of the workload, weighted by the
+    full step's bytes.  scale picks the sample size (1.0 ~ 10 s of work)."""
+    import numpy as np
+    import synth
+    from oracle import ops as O
+    full = op_bytes(sz)
+    nr = max(1 << 12, int((1 << 26) * scale))
+    ns = max(1 << 12, int((1 << 24) * scale))
+    tt = max(64, int(4096 * scale ** 0.5))
+    samples = {}
+    t_est = 0.0
+    if not only or "reduce" in only:
+        x = synth.ints_pm1000(nr, seed=11).numpy()
+        t = time.perf_counter(); O.reduce(x, [nr], [], 0); dt_ = time.perf_counter() - t
+        t_est += dt_ * full["reduce"] / (4 * nr)
+        samples["reduce"] = nr
+    if not only or "scan" in only:
+        x = synth.uniform_grid(ns, seed=12).numpy()
+        t = time.perf_counter(); O.scan(x, np.zeros(ns, np.float32), [ns], [], 0); dt_ = time.perf_counter() - t
+        t_est += dt_ * full["scan"] / (8 * ns)
+        samples["scan"] = ns
+    if not only or "transpose" in only:
+        x = synth.normal_f32(tt * tt, seed=13).numpy().reshape(tt, tt)
+        t = time.perf_counter(); O.transpose2d(x); dt_ = time.perf_counter() - t
+        t_est += dt_ * full["transpose"] / (8 * tt * tt)
+        samples["transpose"] = [tt, tt]
+    step_bytes = sum(full[k] for k in (only or full))
+    return step_bytes / t_est / 1e9, samples
+
+
+def cpu_baseline(sz, only):
+    v, s = oracle_rate(sz, only, 1.0)
+    return {"value": round(v, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"reduce {s.get('reduce')} int32, scan {s.get('scan')} FP32, transpose {s.get('transpose')} "
+                      "FP32 (NumPy, single-threaded); rates weighted by the full step's bytes"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    sz = sizes(args.small)
+    only = set(args.ops.split(",")) if args.ops else None
+    for _ in range(args.warmup):
+        oracle_rate(sz, only, 1 / 64)
+    t0 = time.perf_counter()
+    rates = []
+    for _ in range(args.steps):
+        r, samples = oracle_rate(sz, only, 1 / 64)
+        rates.append(r)
+    el = time.perf_counter() - t0
+    value = len(rates) / sum(1.0 / r for r in rates)     # bytes-weighted mean rate
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * el / args.steps, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i32/f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD + (" (small)" if args.small else ""), "reduce_n": sz["reduce_n"],
+                       "scan_n": sz["scan_n"], "transpose": [sz["T"], sz["T"]]},
+            "cpu_baseline": {"value": round(value, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                             "sample": f"per step: reduce {samples.get('reduce')}, scan {samples.get('scan')}, "
+                                       f"transpose {samples.get('transpose')}; rates weighted by the full step's bytes"},
+            "e2e": {"value": round(value, 3), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--small", action="store_true", help="small case for profiler captures")
+    ap.add_argument("--ops", default="", help="comma list: subset of reduce,scan,transpose")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    args = ap.parse_args()
+    if args.warmup < 3 and not args.small:
+        args.warmup = 3
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+        if line:
+            print(json.dumps(line), flush=True)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    line = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

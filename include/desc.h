@@ -1,0 +1,240 @@
+/*
+ * desc.h -- C ABI of libdesc: hierarchical, view-checked data-parallel
+ * primitives for one NVIDIA GB300 (sm_103a).
+ *
+ * The model follows Descend (Koepcke, Gorlatch, Steuwer, arXiv 2305.03448):
+ * a computation is scheduled over the execution resources grid -> block ->
+ * (warp ->) thread (Section 3.1), and memory is reached through *views* --
+ * group, split, transpose, reverse and their map compositions -- that select
+ * one part of an array per execution resource (Section 3.2).  Views never
+ * move data; a chain of views is turned into one raw index (Section 5).
+ *
+ * Conventions shared by every entry point
+ *  - Every call returns an int32 status (desc_status).  Nothing throws, aborts
+ *    or traps.  All checks run before any launch; on an error nothing is
+ *    launched and no output is touched.
+ *  - Device buffers belong to the caller.  The library never allocates device
+ *    memory in these calls: scratch space ("workspace") is passed in, sized by
+ *    the matching *_workspace_size query, and must stay untouched by others
+ *    until the work queued on the stream has finished.
+ *  - Pointers to device data must be device (or managed) memory; a host
+ *    pointer is rejected with DESC_ERR_HOST_POINTER (Section 2.3, GPU code
+ *    dereferencing CPU memory).  Byte sizes are checked against the element
+ *    counts the views imply (DESC_ERR_SIZE_MISMATCH; Section 2.3, a launch
+ *    sized in bytes instead of elements).
+ *  - Work is queued on the given stream (NULL = legacy default stream) and
+ *    runs asynchronously.  Device-side failures (a bounded wait that ran out)
+ *    are recorded in a per-device status word read by desc_stream_status().
+ *  - Descriptors are read during the call only and never kept.
+ *  - Calls are thread-safe; different streams may be used concurrently.
+ */
+#ifndef DESC_H
+#define DESC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t / CUstream. */
+typedef struct CUstream_st *desc_stream_t;
+
+typedef enum {
+  DESC_OK = 0,
+  DESC_ERR_INVALID_ARG = 1,     /* NULL pointer, unknown enum, negative size   */
+  DESC_ERR_SHAPE = 2,           /* view type error: divisibility, split bound,
+                                   select extent != resource count, selection
+                                   order, rank, domain mismatch                */
+  DESC_ERR_OVERLAP = 3,         /* access conflict: an element written by two
+                                   threads, or written by one and read by
+                                   another (Section 3.3 narrowing, Section 4) */
+  DESC_ERR_HOST_POINTER = 4,    /* host memory passed where device memory is
+                                   needed                                      */
+  DESC_ERR_SIZE_MISMATCH = 5,   /* buffer bytes != elements * element size    */
+  DESC_ERR_ALIGNMENT = 6,       /* pointer not aligned to its element size    */
+  DESC_ERR_UNSUPPORTED = 7,     /* valid request this build does not handle  */
+  DESC_ERR_CUDA = 8,            /* a CUDA runtime call failed                  */
+  DESC_ERR_DEVICE_TIMEOUT = 9,  /* a bounded device-side wait gave up          */
+  DESC_ERR_WORKSPACE = 10       /* workspace NULL or smaller than required     */
+} desc_status;
+
+/* Execution levels (Section 3.1; the warp level is an addition: 32
+ * consecutive linear thread ids, lin = x + X*(y + Y*z)). */
+typedef enum {
+  DESC_LEVEL_GRID = 0,
+  DESC_LEVEL_BLOCK = 1,
+  DESC_LEVEL_WARP = 2,
+  DESC_LEVEL_THREAD = 3
+} desc_level;
+
+/* Dimensions of an execution resource (Figure "Execution Resources and
+ * Dimensions").  DESC_DIM_LANE appears only in lowered maps: a THREAD select
+ * that follows a WARP select binds the lane within the warp. */
+typedef enum { DESC_DIM_X = 0, DESC_DIM_Y = 1, DESC_DIM_Z = 2, DESC_DIM_LANE = 3 } desc_dim;
+
+typedef enum { DESC_I32 = 0, DESC_F32 = 1 } desc_dtype;
+
+/* Basic views (Section 3.2 and its listing of basic view types) and select.
+ *   GROUP k      [[d; n]] -> [[ [[d; k]]; n/k ]]   requires k >= 1, n % k == 0
+ *   SPLIT_FST k  [[d; n]] -> [[d; k]]              requires 0 <= k <= n
+ *   SPLIT_SND k  [[d; n]] -> [[d; n-k]]            element i is input i + k
+ *   TRANSPOSE    [[ [[d; n]]; m ]] -> [[ [[d; m]]; n ]]
+ *   REVERSE      [[d; n]] -> [[d; n]]              element i is input n-1-i
+ *   SELECT       p[[e]]: the outermost dimension is distributed over the
+ *                sub-resources of e along one dimension, one element each;
+ *                its extent must equal their number.
+ * map(v) is written as v with depth > 0: the view acts on the arrays nested
+ * `depth` levels deep. */
+typedef enum {
+  DESC_V_GROUP = 0,
+  DESC_V_SPLIT_FST = 1,
+  DESC_V_SPLIT_SND = 2,
+  DESC_V_TRANSPOSE = 3,
+  DESC_V_REVERSE = 4,
+  DESC_V_SELECT = 5
+} desc_view_kind;
+
+#define DESC_MAX_RANK 4
+#define DESC_MAX_OPS 16
+#define DESC_MAX_DIMS 20
+
+typedef struct {
+  int32_t kind;   /* desc_view_kind                                      */
+  int32_t depth;  /* nesting depth the view acts on; must be 0 for SELECT */
+  int64_t k;      /* GROUP: group size; SPLIT_*: split position; else 0  */
+  int32_t level;  /* SELECT: DESC_LEVEL_BLOCK, _WARP or _THREAD           */
+  int32_t dim;    /* SELECT: DESC_DIM_X, _Y or _Z (WARP and lane: X)      */
+} desc_view_op;
+
+/* A place expression: a row-major contiguous base array of `rank` extents
+ * (outermost first) and the chain of views applied to it, ops[0] first. */
+typedef struct {
+  int32_t rank;
+  int32_t nops;
+  int64_t shape[DESC_MAX_RANK];
+  desc_view_op ops[DESC_MAX_OPS];
+} desc_view;
+
+/* The execution resource a view is selected by: gpu.grid<grid, block>
+ * (Section 3.1).  This is the *logical* resource of the view; kernels may
+ * run it on fewer physical threads, each doing the work of several. */
+typedef struct {
+  int64_t grid[3];   /* blocks along X, Y, Z   */
+  int64_t block[3];  /* threads along X, Y, Z  */
+} desc_exec;
+
+/* A lowered view: one affine map from the logical domain to the base array.
+ * The logical domain is the selected dimensions, in select order, followed
+ * by the dimensions left after the last view; logical point p reaches
+ *     element  offset + sum_i p_i * stride_i   (in elements, row-major base).
+ * level[i]/dim[i] tell which execution coordinate binds a selected
+ * dimension; local dimensions have level -1 and dim -1. */
+typedef struct {
+  int32_t ndims;
+  int32_t nsel;
+  int64_t extent[DESC_MAX_DIMS];
+  int64_t stride[DESC_MAX_DIMS];
+  int32_t level[DESC_MAX_DIMS];
+  int32_t dim[DESC_MAX_DIMS];
+  int64_t offset;
+  int64_t base_elems;
+} desc_lowered;
+
+/* One access of an op phase, for desc_check_disjoint.  Accesses with
+ * different `buffer` ids never conflict. */
+typedef struct {
+  desc_lowered map;
+  int32_t buffer;
+  int32_t is_write;
+} desc_access;
+
+/* Human-readable name of a status code (static storage). */
+const char *desc_status_string(int32_t status);
+
+/* ABI version, (major << 16) | minor. */
+int32_t desc_version(void);
+
+/* ---- View lowering (host only, no GPU needed) ------------------------
+ * Section 5: views are compiled into raw indices, transforming the index
+ * view by view starting with the view applied last.  Because every basic
+ * view is affine on its input index, the whole chain lowers to one affine
+ * map.  Validates the view types (DESC_ERR_SHAPE) and, when `ex` is not
+ * NULL, that each select's extent equals its resource count and that
+ * selections narrow block -> warp -> thread (Section 3.3).  `out` is written
+ * only on success. */
+int32_t desc_lower_view(const desc_view *v, const desc_exec *ex, desc_lowered *out);
+
+/* ---- Access-conflict check (host only, no GPU needed) ----------------
+ * Section 3.3 (narrowing, synchronization) and Section 4
+ * (access_safety_check): within one phase between barriers, no element may
+ * be written by two threads, or written by one thread and read by another.
+ * Each access is enumerated per thread of the grid `ex`: a thread reaches
+ * the logical points whose selected coordinates equal its own; execution
+ * dimensions an access does not select replicate it.  Returns DESC_OK or
+ * DESC_ERR_OVERLAP; on overlap, *first_conflict (if not NULL) receives the
+ * smallest conflicting element index over all buffers.
+ * Uses a structural proof for affine maps (sorted strides) and exact
+ * enumeration otherwise; DESC_ERR_UNSUPPORTED if enumeration would exceed
+ * 2^24 (element, thread) pairs. */
+int32_t desc_check_disjoint(const desc_access *acc, int32_t n, const desc_exec *ex,
+                            int64_t *first_conflict);
+
+/* ---- Reduce ----------------------------------------------------------
+ * Section 5 benchmark "block-wide parallel reduction"; the operator is a sum.
+ * out[o] = sum of in[index(p)] over the logical points p whose selected
+ * coordinates at levels <= out_level linearise (row-major, select order) to
+ * o.  out_level = GRID gives one scalar.  in: base array of `v` (dtype,
+ * in_bytes = elements * 4).  out: the number of outputs * 4 bytes.
+ * DESC_I32 sums wrap modulo 2^32 and are bit-exact; DESC_F32 sums use FP32
+ * arithmetic (error within 1e-5 * sum|x|), with compensated (Kahan)
+ * accumulation when flags has DESC_KAHAN. */
+#define DESC_KAHAN 1
+int32_t desc_reduce_workspace_size(const desc_view *v, const desc_exec *ex, int32_t out_level,
+                                   int32_t dtype, size_t *bytes);
+int32_t desc_reduce(const desc_view *v, const desc_exec *ex, int32_t out_level, int32_t dtype,
+                    const void *in, size_t in_bytes, void *out, size_t out_bytes, int32_t flags,
+                    void *ws, size_t ws_bytes, desc_stream_t stream);
+
+/* ---- Inclusive scan --------------------------------------------------
+ * Section 5 benchmark "scan" (inclusive sum).  Segments are the logical
+ * points that share their selected coordinates at levels <= seg_level
+ * (GRID: one segment).  Within a segment, in logical order,
+ * out[index(p)] = sum of in[index(q)] for q <= p.  `out` has the same base
+ * array as `in` and is written through the same view; elements the view
+ * does not reach are left untouched.  in == out (in place) is allowed.
+ * DESC_I32 wraps modulo 2^32 (bit-exact); DESC_F32 has per-element error
+ * within 1e-5 * sum_{q<=p} |x_q| (FP32 arithmetic, compensated carries). */
+/* Test hook for the bounded waits: tile 1 never publishes, and the waits
+ * give up after tens of milliseconds, so the call records
+ * DESC_ERR_DEVICE_TIMEOUT (read by desc_stream_status) instead of hanging.
+ * Not for production use: the output is left incomplete. */
+#define DESC_DEBUG_STALL_TILE (1 << 16)
+int32_t desc_scan_workspace_size(const desc_view *v, const desc_exec *ex, int32_t seg_level,
+                                 int32_t dtype, size_t *bytes);
+int32_t desc_scan(const desc_view *v, const desc_exec *ex, int32_t seg_level, int32_t dtype,
+                  const void *in, size_t in_bytes, void *out, size_t out_bytes, int32_t flags,
+                  void *ws, size_t ws_bytes, desc_stream_t stream);
+
+/* ---- Transpose (view-to-view copy) ----------------------------------
+ * Section 1 / Section 5 benchmark "matrix transposition", generalised to any
+ * pair of views with the same logical domain:
+ *     out[index_out(p)] = in[index_in(p)]  for every logical point p.
+ * A transpose is in_v = [R][C] with one TRANSPOSE view and out_v = [C][R].
+ * Bit copy (NaN payloads kept).  `ex` may be NULL when neither view selects.
+ * The output map must be injective, and when in and out are the same buffer
+ * the reads and writes must not conflict (DESC_ERR_OVERLAP); partially
+ * overlapping distinct buffers are rejected too. */
+int32_t desc_transpose(const desc_view *in_v, const desc_view *out_v, const desc_exec *ex,
+                       int32_t dtype, const void *in, size_t in_bytes, void *out, size_t out_bytes,
+                       desc_stream_t stream);
+
+/* Per-device status word: waits for the stream, returns the first device
+ * error recorded since the last call (DESC_OK if none) and clears it. */
+int32_t desc_stream_status(desc_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DESC_H */

@@ -1,0 +1,262 @@
+"""Python binding of libdesc (argument marshalling only).
+
+Every operation runs in libdesc.so's own CUDA kernels for sm_103a; this
+module only converts view descriptions and torch tensors into the C ABI of
+``include/desc.h`` and raises ``DescError`` on a non-OK status.  torch
+supplies device memory and streams.  There is no fallback: if libdesc.so has
+not been built, importing the library raises.
+
+Views are written as tuples, ops applied left to right:
+  ("group", k, depth) ("split_fst", k, depth) ("split_snd", k, depth)
+  ("transpose", depth) ("reverse", depth) ("select", level, dim)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_char_p, c_int32, c_int64, c_size_t, c_void_p
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdesc.so")
+
+GRID, BLOCK, WARP, THREAD = 0, 1, 2, 3
+X, Y, Z, LANE = 0, 1, 2, 3
+I32, F32 = 0, 1
+KAHAN = 1
+DEBUG_STALL_TILE = 1 << 16
+
+STATUS = {0: "DESC_OK", 1: "DESC_ERR_INVALID_ARG", 2: "DESC_ERR_SHAPE", 3: "DESC_ERR_OVERLAP",
+          4: "DESC_ERR_HOST_POINTER", 5: "DESC_ERR_SIZE_MISMATCH", 6: "DESC_ERR_ALIGNMENT",
+          7: "DESC_ERR_UNSUPPORTED", 8: "DESC_ERR_CUDA", 9: "DESC_ERR_DEVICE_TIMEOUT",
+          10: "DESC_ERR_WORKSPACE"}
+_KIND = {"group": 0, "split_fst": 1, "split_snd": 2, "transpose": 3, "reverse": 4, "select": 5}
+MAX_RANK, MAX_OPS, MAX_DIMS = 4, 16, 20
+
+
+class DescError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {STATUS.get(status, status)}")
+
+
+class ViewOp(ctypes.Structure):
+    _fields_ = [("kind", c_int32), ("depth", c_int32), ("k", c_int64), ("level", c_int32), ("dim", c_int32)]
+
+
+class View(ctypes.Structure):
+    _fields_ = [("rank", c_int32), ("nops", c_int32), ("shape", c_int64 * MAX_RANK), ("ops", ViewOp * MAX_OPS)]
+
+
+class Exec(ctypes.Structure):
+    _fields_ = [("grid", c_int64 * 3), ("block", c_int64 * 3)]
+
+
+class Lowered(ctypes.Structure):
+    _fields_ = [("ndims", c_int32), ("nsel", c_int32), ("extent", c_int64 * MAX_DIMS),
+                ("stride", c_int64 * MAX_DIMS), ("level", c_int32 * MAX_DIMS), ("dim", c_int32 * MAX_DIMS),
+                ("offset", c_int64), ("base_elems", c_int64)]
+
+    def as_dict(self):
+        n = self.ndims
+        return {"ndims": n, "nsel": self.nsel, "extent": list(self.extent[:n]), "stride": list(self.stride[:n]),
+                "level": list(self.level[:n]), "dim": list(self.dim[:n]), "offset": self.offset,
+                "base_elems": self.base_elems}
+
+
+class Access(ctypes.Structure):
+    _fields_ = [("map", Lowered), ("buffer", c_int32), ("is_write", c_int32)]
+
+
+_lib_handle = None
+
+
+def lib():
+    """The loaded libdesc.so (raises if it has not been built)."""
+    global _lib_handle
+    if _lib_handle is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        _declare(L)
+        _lib_handle = L
+    return _lib_handle
+
+
+def _declare(L):
+    P = c_void_p
+    sig = {
+        "desc_status_string": (c_char_p, [c_int32]),
+        "desc_version": (c_int32, []),
+        "desc_lower_view": (c_int32, [POINTER(View), POINTER(Exec), POINTER(Lowered)]),
+        "desc_check_disjoint": (c_int32, [POINTER(Access), c_int32, POINTER(Exec), POINTER(c_int64)]),
+        "desc_reduce_workspace_size": (c_int32, [POINTER(View), POINTER(Exec), c_int32, c_int32, POINTER(c_size_t)]),
+        "desc_reduce": (c_int32, [POINTER(View), POINTER(Exec), c_int32, c_int32, P, c_size_t, P, c_size_t,
+                                  c_int32, P, c_size_t, P]),
+        "desc_scan_workspace_size": (c_int32, [POINTER(View), POINTER(Exec), c_int32, c_int32, POINTER(c_size_t)]),
+        "desc_scan": (c_int32, [POINTER(View), POINTER(Exec), c_int32, c_int32, P, c_size_t, P, c_size_t,
+                                c_int32, P, c_size_t, P]),
+        "desc_transpose": (c_int32, [POINTER(View), POINTER(View), POINTER(Exec), c_int32, P, c_size_t, P,
+                                     c_size_t, P]),
+        "desc_stream_status": (c_int32, [P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+
+
+# ----------------------------------------------------------------- marshalling
+def make_view(base_shape, ops) -> View:
+    v = View()
+    if not 1 <= len(base_shape) <= MAX_RANK or len(ops) > MAX_OPS:
+        raise DescError(2, "view rank or op count")
+    v.rank = len(base_shape)
+    v.nops = len(ops)
+    for i, s in enumerate(base_shape):
+        v.shape[i] = int(s)
+    for i, op in enumerate(ops):
+        o = v.ops[i]
+        o.kind = _KIND[op[0]]
+        if op[0] == "select":
+            o.level, o.dim, o.depth, o.k = int(op[1]), int(op[2]), 0, 0
+        elif op[0] in ("transpose", "reverse"):
+            o.depth, o.k = int(op[1]), 0
+        else:
+            o.k, o.depth = int(op[1]), int(op[2])
+    return v
+
+
+def make_exec(grid=None, block=None):
+    if grid is None:
+        return None
+    e = Exec()
+    for i in range(3):
+        e.grid[i] = int(grid[i])
+        e.block[i] = int(block[i])
+    return e
+
+
+def _ref(x):
+    return ctypes.byref(x) if x is not None else None
+
+
+def _check(st, what):
+    if st != 0:
+        raise DescError(st, what)
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return c_void_p(s.cuda_stream)
+
+
+def _dtype_code(t):
+    import torch
+    if t.dtype == torch.int32:
+        return I32
+    if t.dtype == torch.float32:
+        return F32
+    raise DescError(1, f"dtype {t.dtype}")
+
+
+def _ptr(t):
+    return c_void_p(t.data_ptr()) if t.numel() else c_void_p(0)
+
+
+# ----------------------------------------------------------------- host-only ops
+def desc_lower_view(base_shape, ops, grid=None, block=None) -> dict:
+    out = Lowered()
+    _check(lib().desc_lower_view(ctypes.byref(make_view(base_shape, ops)), _ref(make_exec(grid, block)),
+                                 ctypes.byref(out)), "desc_lower_view")
+    return out.as_dict()
+
+
+def lowered_struct(d: dict) -> Lowered:
+    m = Lowered()
+    m.ndims, m.nsel = d["ndims"], d["nsel"]
+    for i in range(d["ndims"]):
+        m.extent[i], m.stride[i] = d["extent"][i], d["stride"][i]
+        m.level[i], m.dim[i] = d["level"][i], d["dim"][i]
+    m.offset = d["offset"]
+    m.base_elems = d.get("base_elems", 0)
+    return m
+
+
+def desc_check_disjoint(accesses, grid, block):
+    """accesses: list of (lowered dict, buffer id, is_write).  Returns None
+    when the accesses are disjoint, else the first conflicting element."""
+    n = len(accesses)
+    arr = (Access * max(n, 1))()
+    for i, (m, buf, w) in enumerate(accesses):
+        arr[i].map = lowered_struct(m)
+        arr[i].buffer = int(buf)
+        arr[i].is_write = 1 if w else 0
+    first = c_int64(-1)
+    st = lib().desc_check_disjoint(arr, n, ctypes.byref(make_exec(grid, block)), ctypes.byref(first))
+    if st == 3:
+        return first.value
+    _check(st, "desc_check_disjoint")
+    return None
+
+
+# ----------------------------------------------------------------- device ops
+def _workspace(nbytes, device):
+    import torch
+    return torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=device)
+
+
+def desc_reduce(x, base_shape, ops, out_level, grid=None, block=None, kahan=False, out=None,
+                ws=None, stream=None):
+    """Sum of tensor ``x`` (the base array) through a view; returns ``out``."""
+    import torch
+    L = lib()
+    v, e = make_view(base_shape, ops), make_exec(grid, block)
+    dt = _dtype_code(x)
+    if out is None:
+        low = desc_lower_view(base_shape, ops, grid, block)
+        nout = 1
+        for i in range(low["nsel"]):
+            if low["level"][i] <= out_level:
+                nout *= low["extent"][i]
+        out = torch.empty(nout, dtype=x.dtype, device=x.device)
+    if ws is None:
+        nb = c_size_t(0)
+        _check(L.desc_reduce_workspace_size(ctypes.byref(v), _ref(e), out_level, dt, ctypes.byref(nb)),
+               "desc_reduce_workspace_size")
+        ws = _workspace(nb.value, x.device)
+    _check(L.desc_reduce(ctypes.byref(v), _ref(e), out_level, dt, _ptr(x), x.numel() * 4, _ptr(out),
+                         out.numel() * 4, KAHAN if kahan else 0, _ptr(ws), ws.numel(), _stream(stream)),
+           "desc_reduce")
+    return out
+
+
+def desc_scan(x, base_shape, ops, seg_level, grid=None, block=None, out=None, ws=None, flags=0,
+              stream=None):
+    """Inclusive scan of ``x`` through a view into ``out`` (same base array)."""
+    import torch
+    L = lib()
+    v, e = make_view(base_shape, ops), make_exec(grid, block)
+    dt = _dtype_code(x)
+    if out is None:
+        out = torch.empty_like(x)
+    if ws is None:
+        nb = c_size_t(0)
+        _check(L.desc_scan_workspace_size(ctypes.byref(v), _ref(e), seg_level, dt, ctypes.byref(nb)),
+               "desc_scan_workspace_size")
+        ws = _workspace(nb.value, x.device)
+    _check(L.desc_scan(ctypes.byref(v), _ref(e), seg_level, dt, _ptr(x), x.numel() * 4, _ptr(out),
+                       out.numel() * 4, flags, _ptr(ws), ws.numel(), _stream(stream)), "desc_scan")
+    return out
+
+
+def desc_transpose(x, in_shape, in_ops, out, out_shape, out_ops, grid=None, block=None, stream=None):
+    """out[index_out(p)] = x[index_in(p)] over the common logical domain."""
+    _check(lib().desc_transpose(ctypes.byref(make_view(in_shape, in_ops)), ctypes.byref(make_view(out_shape, out_ops)),
+                                _ref(make_exec(grid, block)), _dtype_code(x), _ptr(x), x.numel() * 4, _ptr(out),
+                                out.numel() * 4, _stream(stream)), "desc_transpose")
+    return out
+
+
+def desc_stream_status(stream=None) -> int:
+    return lib().desc_stream_status(_stream(stream))

@@ -1,0 +1,247 @@
+// Entry points of libdesc: validate, lower the views, check accesses, pick
+// a schedule from the lowered maps, and launch.  Nothing is launched before
+// every check has passed.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstdlib>
+#include <vector>
+
+#include "desc_internal.h"
+
+namespace desc {
+
+int32_t check_device_ptr(const void *p, size_t align) {
+  if (!p) return DESC_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(p) % align) return DESC_ERR_ALIGNMENT;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return DESC_ERR_HOST_POINTER;
+  }
+  if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return DESC_OK;
+  return DESC_ERR_HOST_POINTER;
+}
+
+}  // namespace desc
+
+using namespace desc;
+
+namespace {
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+bool ranges_overlap(const void *a, size_t na, const void *b, size_t nb) {
+  const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+  return na && nb && x < y + nb && y < x + na;
+}
+
+// Write map of one op: with selects, no element may be written by two
+// logical threads (desc_check_disjoint).  The kernels write in parallel, so
+// an element reached twice by the same logical thread cannot keep its
+// write order either: such maps are not supported.
+int32_t check_writes(const desc_lowered &w, const desc_exec *ex) {
+  if (ex) {
+    desc_access a;
+    a.map = w;
+    a.buffer = 0;
+    a.is_write = 1;
+    int64_t first = 0;
+    const int32_t r = desc_check_disjoint(&a, 1, ex, &first);
+    if (r != DESC_OK) return r;
+  }
+  return injective_quick(w) ? DESC_OK : DESC_ERR_UNSUPPORTED;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- reduce
+extern "C" int32_t desc_reduce_workspace_size(const desc_view *v, const desc_exec *ex,
+                                              int32_t out_level, int32_t dtype, size_t *bytes) {
+  if (!bytes || !dtype_size(dtype)) return DESC_ERR_INVALID_ARG;
+  if (out_level < DESC_LEVEL_GRID || out_level > DESC_LEVEL_THREAD) return DESC_ERR_INVALID_ARG;
+  desc_lowered L;
+  int32_t r = desc_lower_view(v, ex, &L);
+  if (r != DESC_OK) return r;
+  const Plan p = split_plan(L, out_level);
+  int64_t start0, seg;
+  *bytes = rest_contiguous(p, true, &start0, &seg) ? reduce_segments_ws(dtype, p.n_rest, p.n_keep)
+                                                   : reduce_affine_ws(p.n_rest, p.n_keep);
+  return DESC_OK;
+}
+
+extern "C" int32_t desc_reduce(const desc_view *v, const desc_exec *ex, int32_t out_level,
+                               int32_t dtype, const void *in, size_t in_bytes, void *out,
+                               size_t out_bytes, int32_t flags, void *ws, size_t ws_bytes,
+                               desc_stream_t s) {
+  if (!dtype_size(dtype)) return DESC_ERR_INVALID_ARG;
+  if (out_level < DESC_LEVEL_GRID || out_level > DESC_LEVEL_THREAD) return DESC_ERR_INVALID_ARG;
+  if (flags & ~(DESC_KAHAN)) return DESC_ERR_INVALID_ARG;
+  desc_lowered L;
+  int32_t r = desc_lower_view(v, ex, &L);
+  if (r != DESC_OK) return r;
+  const Plan p = split_plan(L, out_level);
+  if (in_bytes != size_t(L.base_elems) * 4 || out_bytes != size_t(p.n_keep) * 4)
+    return DESC_ERR_SIZE_MISMATCH;
+  if (p.n_keep == 0) return DESC_OK;
+  if ((r = check_device_ptr(out, 4)) != DESC_OK) return r;
+  if (L.base_elems > 0 && (r = check_device_ptr(in, 4)) != DESC_OK) return r;
+  if (ranges_overlap(in, in_bytes, out, out_bytes)) return DESC_ERR_OVERLAP;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(s);
+  if (p.n_rest == 0) {
+    if (cudaMemsetAsync(out, 0, out_bytes, st) != cudaSuccess) return DESC_ERR_CUDA;
+    return DESC_OK;
+  }
+  int64_t start0, seg;
+  if (rest_contiguous(p, true, &start0, &seg))
+    return launch_reduce_segments(dtype, in, start0, seg, p.n_rest, p.n_keep, out, flags, ws,
+                                  ws_bytes, s);
+  return launch_reduce_affine(dtype, in, p, out, flags, ws, ws_bytes, s);
+}
+
+// ---------------------------------------------------------------- scan
+namespace {
+
+struct ScanPlan {
+  bool contig;       // fast path: one contiguous run [start, start + total)
+  int64_t start, total, period;
+};
+
+ScanPlan plan_scan(const desc_lowered &L, int32_t seg_level) {
+  const Plan p = split_plan(L, seg_level);
+  ScanPlan sp{false, 0, p.n_keep * p.n_rest, p.n_rest};
+  int64_t start0, seg;
+  if (rest_contiguous(p, false, &start0, &seg) && (p.n_keep <= 1 || seg == p.n_rest)) {
+    sp.contig = true;
+    sp.start = start0;
+  }
+  return sp;
+}
+
+}  // namespace
+
+extern "C" int32_t desc_scan_workspace_size(const desc_view *v, const desc_exec *ex,
+                                            int32_t seg_level, int32_t dtype, size_t *bytes) {
+  if (!bytes || !dtype_size(dtype)) return DESC_ERR_INVALID_ARG;
+  if (seg_level < DESC_LEVEL_GRID || seg_level > DESC_LEVEL_THREAD) return DESC_ERR_INVALID_ARG;
+  desc_lowered L;
+  int32_t r = desc_lower_view(v, ex, &L);
+  if (r != DESC_OK) return r;
+  const ScanPlan sp = plan_scan(L, seg_level);
+  *bytes = (sp.contig ? 0 : align256(size_t(sp.total) * 4)) + scan_contig_ws(dtype, sp.total);
+  return DESC_OK;
+}
+
+extern "C" int32_t desc_scan(const desc_view *v, const desc_exec *ex, int32_t seg_level,
+                             int32_t dtype, const void *in, size_t in_bytes, void *out,
+                             size_t out_bytes, int32_t flags, void *ws, size_t ws_bytes,
+                             desc_stream_t s) {
+  if (!dtype_size(dtype)) return DESC_ERR_INVALID_ARG;
+  if (seg_level < DESC_LEVEL_GRID || seg_level > DESC_LEVEL_THREAD) return DESC_ERR_INVALID_ARG;
+  if (flags & ~(DESC_DEBUG_STALL_TILE)) return DESC_ERR_INVALID_ARG;
+  desc_lowered L;
+  int32_t r = desc_lower_view(v, ex, &L);
+  if (r != DESC_OK) return r;
+  if (in_bytes != size_t(L.base_elems) * 4 || out_bytes != in_bytes) return DESC_ERR_SIZE_MISMATCH;
+  const ScanPlan sp = plan_scan(L, seg_level);
+  if (sp.total == 0) return DESC_OK;
+  if ((r = check_device_ptr(in, 4)) != DESC_OK) return r;
+  if ((r = check_device_ptr(out, 4)) != DESC_OK) return r;
+  if (in != out && ranges_overlap(in, in_bytes, out, out_bytes)) return DESC_ERR_OVERLAP;
+  if ((r = check_writes(L, ex)) != DESC_OK) return r;
+  const char *ib = static_cast<const char *>(in);
+  char *ob = static_cast<char *>(out);
+  if (sp.contig)
+    return launch_scan_contig(dtype, ib + sp.start * 4, ob + sp.start * 4, sp.total, sp.period,
+                              flags, ws, ws_bytes, s);
+  const size_t gather = align256(size_t(sp.total) * 4);
+  if (!ws || ws_bytes < gather + scan_contig_ws(dtype, sp.total)) return DESC_ERR_WORKSPACE;
+  // general path: gather in logical order, scan in place, scatter back
+  std::vector<int64_t> ext(L.extent, L.extent + L.ndims), st(L.stride, L.stride + L.ndims),
+      cst(L.ndims);
+  int64_t c = 1;
+  for (int i = L.ndims - 1; i >= 0; --i) {
+    cst[i] = c;
+    c *= ext[i];
+  }
+  void *buf = ws;
+  if ((r = launch_copy_affine(in, L.offset, st.data(), buf, 0, cst.data(), ext.data(), L.ndims, s)))
+    return r;
+  if ((r = launch_scan_contig(dtype, buf, buf, sp.total, sp.period, flags,
+                              static_cast<char *>(ws) + gather, ws_bytes - gather, s)))
+    return r;
+  return launch_copy_affine(buf, 0, cst.data(), out, L.offset, st.data(), ext.data(), L.ndims, s);
+}
+
+// ---------------------------------------------------------------- transpose
+extern "C" int32_t desc_transpose(const desc_view *in_v, const desc_view *out_v,
+                                  const desc_exec *ex, int32_t dtype, const void *in,
+                                  size_t in_bytes, void *out, size_t out_bytes, desc_stream_t s) {
+  if (!dtype_size(dtype)) return DESC_ERR_INVALID_ARG;
+  desc_lowered Li, Lo;
+  int32_t r;
+  if ((r = desc_lower_view(in_v, ex, &Li)) != DESC_OK) return r;
+  if ((r = desc_lower_view(out_v, ex, &Lo)) != DESC_OK) return r;
+  if (!ex && (Li.nsel || Lo.nsel)) return DESC_ERR_INVALID_ARG;
+  if (Li.ndims != Lo.ndims || Li.nsel != Lo.nsel) return DESC_ERR_SHAPE;
+  for (int i = 0; i < Li.ndims; ++i)
+    if (Li.extent[i] != Lo.extent[i] || Li.level[i] != Lo.level[i] || Li.dim[i] != Lo.dim[i])
+      return DESC_ERR_SHAPE;
+  if (in_bytes != size_t(Li.base_elems) * 4 || out_bytes != size_t(Lo.base_elems) * 4)
+    return DESC_ERR_SIZE_MISMATCH;
+  int64_t total = 1;
+  for (int i = 0; i < Li.ndims; ++i) total *= Li.extent[i];
+  if (total == 0) return DESC_OK;
+  if ((r = check_device_ptr(in, 4)) != DESC_OK) return r;
+  if ((r = check_device_ptr(out, 4)) != DESC_OK) return r;
+  // In place, the parallel copy would read elements other threads have
+  // already overwritten unless both views reach the same element per point.
+  if (in == out) {
+    if (!same_map_quick(Li, Lo)) return DESC_ERR_OVERLAP;
+  } else if (ranges_overlap(in, in_bytes, out, out_bytes)) {
+    return DESC_ERR_OVERLAP;
+  }
+  if ((r = check_writes(Lo, ex)) != DESC_OK) return r;
+
+  // canonical dims: (extent, in stride, out stride), output-major order
+  struct D { int64_t e, si, so; };
+  std::vector<D> d;
+  for (int i = 0; i < Li.ndims; ++i)
+    if (Li.extent[i] > 1) d.push_back({Li.extent[i], Li.stride[i], Lo.stride[i]});
+  bool pos = true;
+  for (auto &x : d) pos = pos && x.so > 0;
+  if (pos) {
+    std::sort(d.begin(), d.end(), [](const D &a, const D &b) { return a.so > b.so; });
+    std::vector<D> m;
+    for (auto &x : d) {
+      if (!m.empty() && m.back().si == x.si * x.e && m.back().so == x.so * x.e) {
+        m.back().e *= x.e;
+        m.back().si = x.si;
+        m.back().so = x.so;
+      } else {
+        m.push_back(x);
+      }
+    }
+    // [batch] x (C: out-major, in-stride 1) x (R: out-stride 1, in-stride ld_in)
+    const size_t k = m.size();
+    if ((k == 2 || k == 3) && m[k - 1].so == 1 && m[k - 2].si == 1) {
+      const int64_t R = m[k - 1].e, C = m[k - 2].e, ld_in = m[k - 1].si, ld_out = m[k - 2].so;
+      const int64_t batch = k == 3 ? m[0].e : 1, bs_in = k == 3 ? m[0].si : 0,
+                    bs_out = k == 3 ? m[0].so : 0;
+      if (ld_in >= C && ld_out >= R)
+        return launch_transpose(static_cast<const float *>(in) + Li.offset,
+                                static_cast<float *>(out) + Lo.offset, R, C, ld_in, ld_out, batch,
+                                bs_in, bs_out, s);
+    }
+  }
+  return launch_copy_affine(in, Li.offset, Li.stride, out, Lo.offset, Lo.stride, Li.extent,
+                            Li.ndims, s);
+}
+
+// ---------------------------------------------------------------- status
+extern "C" int32_t desc_stream_status(desc_stream_t s) {
+  if (cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(s)) != cudaSuccess) return DESC_ERR_CUDA;
+  const int32_t a = scan_status_take();
+  return a;
+}

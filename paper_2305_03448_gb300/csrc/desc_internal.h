@@ -1,0 +1,87 @@
+// Internal declarations shared by the translation units of libdesc.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/desc.h"
+
+namespace desc {
+
+// Element size of a dtype (0 when unknown).
+inline size_t dtype_size(int32_t t) { return (t == DESC_I32 || t == DESC_F32) ? 4 : 0; }
+
+// A view lowered and split into the dims an op keeps (selected dims at
+// levels <= a cut level, a prefix of the selected dims) and the dims it runs
+// over.  Each dim: extent and stride in elements.
+struct Dim {
+  int64_t extent;
+  int64_t stride;
+};
+
+struct Plan {
+  int32_t nkeep;           // number of kept dims (prefix of the lowered dims)
+  int32_t nrest;           // number of remaining dims
+  Dim keep[DESC_MAX_DIMS];  // in row-major output order
+  Dim rest[DESC_MAX_DIMS];  // in logical order (outermost first)
+  int64_t offset;
+  int64_t n_keep;          // product of kept extents (outputs or segments)
+  int64_t n_rest;          // product of remaining extents
+};
+
+// Split lowered view `L` at selection level `cut`: kept dims are the selected
+// dims whose level <= cut.
+Plan split_plan(const desc_lowered &L, int32_t cut);
+
+// True when the remaining dims of `p` cover one contiguous run of n_rest
+// elements (in logical order, or in any order when `any_order`), and the
+// runs of successive outputs start at *start0 + o * *seg_stride.
+bool rest_contiguous(const Plan &p, bool any_order, int64_t *start0, int64_t *seg_stride);
+
+// Structural injectivity of an affine map over its whole domain: sorted
+// |strides| with each stride larger than the span of the smaller ones.
+bool affine_injective(const int64_t *extent, const int64_t *stride, int n);
+
+bool injective_quick(const desc_lowered &w);
+bool same_map_quick(const desc_lowered &a, const desc_lowered &b);
+
+// Pointer checks: device (or managed) memory and element alignment.
+int32_t check_device_ptr(const void *p, size_t align);
+
+// Device status words of the translation units that hold bounded waits.
+int32_t scan_status_take();   // k_scan.cu
+
+// ----- launchers (k_*.cu) -------------------------------------------------
+// Reduce: contiguous segments [start + o*seg_stride, +len), o < nout.
+int32_t launch_reduce_segments(int32_t dtype, const void *in, int64_t start, int64_t seg_stride,
+                               int64_t len, int64_t nout, void *out, int32_t flags, void *ws,
+                               size_t ws_bytes, desc_stream_t s);
+size_t reduce_segments_ws(int32_t dtype, int64_t len, int64_t nout);
+// Reduce: general affine plan (chunk partials in ws when runs are long).
+size_t reduce_affine_ws(int64_t n_rest, int64_t nout);
+int32_t launch_reduce_affine(int32_t dtype, const void *in, const Plan &p, void *out,
+                             int32_t flags, void *ws, size_t ws_bytes, desc_stream_t s);
+
+// Scan of a contiguous array of n elements split into segments of length
+// `period` (period == n: one segment).  in may equal out.
+int32_t launch_scan_contig(int32_t dtype, const void *in, void *out, int64_t n, int64_t period,
+                           int32_t flags, void *ws, size_t ws_bytes, desc_stream_t s);
+size_t scan_contig_ws(int32_t dtype, int64_t n);
+// Scan segmented by CSR offsets (nseg + 1 entries, device); sums (nullable)
+// receives the total of every segment (0 for empty ones).
+int32_t launch_scan_csr(int32_t dtype, const void *in, void *out, int64_t n, const int64_t *offsets,
+                        int64_t nseg, void *sums, int32_t flags, void *ws, size_t ws_bytes,
+                        desc_stream_t s);
+size_t scan_csr_ws(int64_t n);
+
+// Copy over a common logical domain of `nd` dims: out[ostride . p] = in[istride . p].
+int32_t launch_copy_affine(const void *in, int64_t ioff, const int64_t *istride, void *out,
+                           int64_t ooff, const int64_t *ostride, const int64_t *extent, int nd,
+                           desc_stream_t s);
+// Tiled transpose of `batch` matrices R x C (row-major, leading dim ld_in)
+// into C x R (leading dim ld_out), batch strides bs_in / bs_out.
+int32_t launch_transpose(const float *in, float *out, int64_t R, int64_t C, int64_t ld_in,
+                         int64_t ld_out, int64_t batch, int64_t bs_in, int64_t bs_out,
+                         desc_stream_t s);
+
+}  // namespace desc

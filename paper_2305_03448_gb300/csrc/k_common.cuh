@@ -1,0 +1,98 @@
+// Device helpers shared by the kernels of libdesc.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "desc_internal.h"
+
+namespace desc {
+
+#define DESC_CUDA_TRY(expr)                        \
+  do {                                             \
+    cudaError_t _e = (expr);                       \
+    if (_e != cudaSuccess) return DESC_ERR_CUDA;   \
+  } while (0)
+
+// Streaming 128-bit loads: evict-first in L1/L2 (each byte is read once).
+__device__ __forceinline__ int4 ld_stream(const int4 *p) { return __ldcs(p); }
+__device__ __forceinline__ float4 ld_stream(const float4 *p) { return __ldcs(p); }
+
+// Error-free transformation of a sum (Knuth's TwoSum): s + e == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// Accumulators.  add1/add4 take elements, merge combines two partial
+// accumulators, value() gives the final sum.
+struct AccI32 {   // sum modulo 2^32
+  uint32_t s;
+  __device__ void init() { s = 0u; }
+  __device__ void add1(int32_t x) { s += (uint32_t)x; }
+  __device__ void add4(int4 v) { s += ((uint32_t)v.x + (uint32_t)v.y) + ((uint32_t)v.z + (uint32_t)v.w); }
+  __device__ void merge(const AccI32 &o) { s += o.s; }
+  __device__ void shfl_merge(int off) { AccI32 o; o.s = __shfl_down_sync(0xffffffffu, s, off); merge(o); }
+  __device__ uint2 pack() const { return make_uint2(s, 0u); }
+  __device__ void unpack(uint2 v) { s = v.x; }
+};
+
+struct AccF32 {   // plain FP32 sum, pairwise inside each vector
+  float s;
+  __device__ void init() { s = 0.f; }
+  __device__ void add1(float x) { s = __fadd_rn(s, x); }
+  __device__ void add4(float4 v) { s = __fadd_rn(s, __fadd_rn(__fadd_rn(v.x, v.y), __fadd_rn(v.z, v.w))); }
+  __device__ void merge(const AccF32 &o) { s = __fadd_rn(s, o.s); }
+  __device__ void shfl_merge(int off) { AccF32 o; o.s = __shfl_down_sync(0xffffffffu, s, off); merge(o); }
+  __device__ uint2 pack() const { return make_uint2(__float_as_uint(s), 0u); }
+  __device__ void unpack(uint2 v) { s = __uint_as_float(v.x); }
+};
+
+struct AccKahan {  // compensated FP32 sum (Neumaier's variant of Kahan summation)
+  float s, c;
+  __device__ void init() { s = 0.f; c = 0.f; }
+  __device__ void add1(float x) {
+    const float t = __fadd_rn(s, x);
+    if (fabsf(s) >= fabsf(x)) c = __fadd_rn(c, __fadd_rn(__fsub_rn(s, t), x));
+    else c = __fadd_rn(c, __fadd_rn(__fsub_rn(x, t), s));
+    s = t;
+  }
+  __device__ void add4(float4 v) { add1(v.x); add1(v.y); add1(v.z); add1(v.w); }
+  __device__ void merge(const AccKahan &o) {
+    float t, e;
+    two_sum(s, o.s, t, e);
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(o.c, e));
+  }
+  __device__ void shfl_merge(int off) {
+    AccKahan o;
+    o.s = __shfl_down_sync(0xffffffffu, s, off);
+    o.c = __shfl_down_sync(0xffffffffu, c, off);
+    merge(o);
+  }
+  __device__ uint2 pack() const { return make_uint2(__float_as_uint(s), __float_as_uint(c)); }
+  __device__ void unpack(uint2 v) { s = __uint_as_float(v.x); c = __uint_as_float(v.y); }
+};
+
+template <class A>
+__device__ __forceinline__ void warp_merge(A &a) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) a.shfl_merge(off);
+}
+
+// Block-wide merge; the result is valid in thread 0.  `sh` holds one A per warp.
+template <class A, int THREADS>
+__device__ __forceinline__ void block_merge(A &a, A *sh) {
+  warp_merge(a);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) sh[w] = a;
+  __syncthreads();
+  if (w == 0) {
+    if (lane < THREADS / 32) a = sh[lane];
+    else a.init();
+    warp_merge(a);
+  }
+}
+
+}  // namespace desc

@@ -1,0 +1,123 @@
+// Copy through views: the tiled transpose and the general affine copy.
+//
+// Transpose: each CTA moves one TD x TD tile (32 x 8 threads per 32-column
+// strip, as in the tiled transposes of Section 1) through a padded shared
+// tile, so that both the global reads (along input rows) and the global
+// writes (along output rows) are coalesced 128-byte lines.  The padding of
+// one word per row makes the column-wise shared-memory reads conflict-free.
+//
+// Affine copy: any pair of affine maps over a common domain; one element per
+// thread and iteration, indices decoded from the domain extents.
+#include <algorithm>
+
+#include "k_common.cuh"
+
+namespace desc {
+namespace {
+
+template <int TD, int BR>
+__global__ void __launch_bounds__(32 * BR) transpose_kernel(const float *__restrict__ in,
+                                                            float *__restrict__ out, int64_t R,
+                                                            int64_t C, int64_t ld_in, int64_t ld_out,
+                                                            int64_t bs_in, int64_t bs_out) {
+  __shared__ float tile[TD][TD + 1];
+  const int64_t b = blockIdx.z;
+  const float *src = in + b * bs_in;
+  float *dst = out + b * bs_out;
+  const int64_t r0 = int64_t(blockIdx.y) * TD, c0 = int64_t(blockIdx.x) * TD;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const bool interior = (r0 + TD <= R) && (c0 + TD <= C);
+  if (interior) {
+#pragma unroll
+    for (int j = 0; j < TD; j += BR)
+#pragma unroll
+      for (int i = 0; i < TD; i += 32)
+        tile[ty + j][tx + i] = __ldcs(src + (r0 + ty + j) * ld_in + c0 + tx + i);
+  } else {
+    for (int j = 0; j < TD; j += BR)
+      for (int i = 0; i < TD; i += 32) {
+        const int64_t r = r0 + ty + j, c = c0 + tx + i;
+        if (r < R && c < C) tile[ty + j][tx + i] = src[r * ld_in + c];
+      }
+  }
+  __syncthreads();
+  // out[c][r] = in[r][c]: output row c0 + ty + j, output column r0 + tx + i
+  if (interior) {
+#pragma unroll
+    for (int j = 0; j < TD; j += BR)
+#pragma unroll
+      for (int i = 0; i < TD; i += 32)
+        __stcs(dst + (c0 + ty + j) * ld_out + r0 + tx + i, tile[tx + i][ty + j]);
+  } else {
+    for (int j = 0; j < TD; j += BR)
+      for (int i = 0; i < TD; i += 32) {
+        const int64_t c = c0 + ty + j, r = r0 + tx + i;
+        if (r < R && c < C) dst[c * ld_out + r] = tile[tx + i][ty + j];
+      }
+  }
+}
+
+struct CopyArgs {
+  int32_t nd;
+  int64_t extent[DESC_MAX_DIMS];
+  int64_t istride[DESC_MAX_DIMS];
+  int64_t ostride[DESC_MAX_DIMS];
+  int64_t ioff, ooff, total;
+};
+
+__global__ void __launch_bounds__(256) copy_affine_kernel(const uint32_t *__restrict__ in,
+                                                          uint32_t *__restrict__ out,
+                                                          const CopyArgs a) {
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; q < a.total; q += stride) {
+    int64_t t = q, ie = a.ioff, oe = a.ooff;
+    for (int d = a.nd - 1; d >= 0; --d) {
+      const int64_t c = t % a.extent[d];
+      t /= a.extent[d];
+      ie += c * a.istride[d];
+      oe += c * a.ostride[d];
+    }
+    out[oe] = in[ie];
+  }
+}
+
+}  // namespace
+
+int32_t launch_transpose(const float *in, float *out, int64_t R, int64_t C, int64_t ld_in,
+                         int64_t ld_out, int64_t batch, int64_t bs_in, int64_t bs_out,
+                         desc_stream_t st) {
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(st);
+  if (R == 0 || C == 0 || batch == 0) return DESC_OK;
+  constexpr int TD = 32, BR = 8;
+  const int64_t gx = (C + TD - 1) / TD, gy = (R + TD - 1) / TD;
+  if (gx >= (int64_t(1) << 31) || gy > 65535 || batch > 65535) return DESC_ERR_UNSUPPORTED;
+  transpose_kernel<TD, BR><<<dim3((unsigned)gx, (unsigned)gy, (unsigned)batch), dim3(32, BR), 0, s>>>(
+      in, out, R, C, ld_in, ld_out, bs_in, bs_out);
+  DESC_CUDA_TRY(cudaGetLastError());
+  return DESC_OK;
+}
+
+int32_t launch_copy_affine(const void *in, int64_t ioff, const int64_t *istride, void *out,
+                           int64_t ooff, const int64_t *ostride, const int64_t *extent, int nd,
+                           desc_stream_t st) {
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(st);
+  CopyArgs a{};
+  a.nd = nd;
+  a.total = 1;
+  for (int i = 0; i < nd; ++i) {
+    a.extent[i] = extent[i];
+    a.istride[i] = istride[i];
+    a.ostride[i] = ostride[i];
+    a.total *= extent[i];
+  }
+  a.ioff = ioff;
+  a.ooff = ooff;
+  if (a.total == 0) return DESC_OK;
+  const int64_t ctas = std::min<int64_t>((a.total + 255) / 256, 152 * 16);
+  copy_affine_kernel<<<(unsigned)ctas, 256, 0, s>>>(static_cast<const uint32_t *>(in),
+                                                    static_cast<uint32_t *>(out), a);
+  DESC_CUDA_TRY(cudaGetLastError());
+  return DESC_OK;
+}
+
+}  // namespace desc

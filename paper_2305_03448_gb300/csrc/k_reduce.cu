@@ -1,0 +1,277 @@
+// Reduce kernels (sum over a lowered view).
+//
+// Three schedules, picked on the host from the lowered map:
+//  * runs:   every output sums one contiguous run of `len` elements, runs
+//            starting at start + o * seg_stride.  Long runs are cut into
+//            chunks, one CTA per (run, chunk); each CTA streams its chunk with
+//            128-bit evict-first loads, UNROLL vectors in flight per thread,
+//            merges warp-wide with shuffles and block-wide through shared
+//            memory; the last CTA of a run (atomic ticket) merges the chunk
+//            partials in chunk order.  Short runs go one warp or one thread
+//            per output.
+//  * affine: any other map; same chunk/partial structure, with every element
+//            index decoded from the remaining dims.
+// int32 sums wrap mod 2^32 (any order gives the same bits); FP32 sums are
+// plain or compensated (Neumaier) FP32.
+#include <algorithm>
+
+#include "k_common.cuh"
+
+namespace desc {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kUnroll = 4;
+constexpr int64_t kTargetCtas = 1216;      // 8 per SM on a 152-SM GB300
+constexpr int64_t kSmallRun = 16;          // <= this: one thread per output
+constexpr int64_t kWarpRun = 4096;         // <= this: one warp per output
+
+int64_t chunks_for(int64_t len, int64_t nout) {
+  const int64_t per_cta_min = int64_t(kThreads) * 4 * kUnroll;
+  int64_t by_fill = (kTargetCtas + nout - 1) / std::max<int64_t>(nout, 1);
+  int64_t by_len = (len + per_cta_min - 1) / per_cta_min;
+  return std::max<int64_t>(1, std::min(by_fill, by_len));
+}
+
+template <class A>
+__device__ __forceinline__ float final_value(const A &a);
+template <>
+__device__ __forceinline__ float final_value(const AccF32 &a) { return a.s; }
+template <>
+__device__ __forceinline__ float final_value(const AccKahan &a) { return __fadd_rn(a.s, a.c); }
+
+template <class A, class T>
+__device__ __forceinline__ void store_out(T *out, int64_t o, const A &a) {
+  out[o] = final_value(a);
+}
+template <>
+__device__ __forceinline__ void store_out<AccI32, int32_t>(int32_t *out, int64_t o, const AccI32 &a) {
+  out[o] = (int32_t)a.s;
+}
+
+// After a CTA has its block partial in thread 0: write it, or take part in
+// the last-CTA merge of the run's partials.
+template <class A, class T>
+__device__ __forceinline__ void finish_chunk(A &a, A *sh, int64_t o, int64_t c, int64_t chunks,
+                                             T *out, uint2 *partials, unsigned *counters) {
+  if (chunks == 1) {
+    if (threadIdx.x == 0) store_out<A, T>(out, o, a);
+    return;
+  }
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    partials[o * chunks + c] = a.pack();
+    __threadfence();
+    const unsigned t = atomicAdd(&counters[o], 1u);
+    last = (t == (unsigned)(chunks - 1));
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  A b;
+  b.init();
+  // chunk order within each thread, then a fixed tree: deterministic
+  for (int64_t i = threadIdx.x; i < chunks; i += kThreads) {
+    A p;
+    p.unpack(__ldcg(&partials[o * chunks + i]));
+    b.merge(p);
+  }
+  __syncthreads();
+  block_merge<A, kThreads>(b, sh);
+  if (threadIdx.x == 0) {
+    store_out<A, T>(out, o, b);
+    counters[o] = 0u;
+  }
+}
+
+template <class T> struct Vec;
+template <> struct Vec<int32_t> { using type = int4; };
+template <> struct Vec<float> { using type = float4; };
+
+// One CTA per (run, chunk).  grid.x = nout * chunks.
+template <class A, class T>
+__global__ void __launch_bounds__(kThreads) reduce_runs_kernel(
+    const T *__restrict__ in, int64_t start, int64_t seg_stride, int64_t len, int64_t chunks,
+    int64_t chunk_vec, T *__restrict__ out, uint2 *partials, unsigned *counters) {
+  using V = typename Vec<T>::type;
+  __shared__ A sh[kThreads / 32];
+  const int64_t o = blockIdx.x / chunks, c = blockIdx.x % chunks;
+  const T *p = in + start + o * seg_stride;
+  const int64_t mis = (reinterpret_cast<uintptr_t>(p) & 15) / sizeof(T);
+  const int64_t head = std::min<int64_t>(len, mis ? 4 - mis : 0);
+  const int64_t nvec = (len - head) / 4;
+  const int64_t tail = len - head - 4 * nvec;
+  A a;
+  a.init();
+  const V *pv = reinterpret_cast<const V *>(p + head);
+  const int64_t v0 = c * chunk_vec, v1 = std::min<int64_t>(nvec, v0 + chunk_vec);
+  int64_t i = v0 + threadIdx.x;
+  for (; i + (kUnroll - 1) * kThreads < v1; i += kUnroll * kThreads) {
+    V x[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) x[u] = ld_stream(pv + i + u * kThreads);
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) a.add4(x[u]);
+  }
+  for (; i < v1; i += kThreads) a.add4(ld_stream(pv + i));
+  if (c == 0 && threadIdx.x < head) a.add1(p[threadIdx.x]);
+  if (c == chunks - 1 && threadIdx.x < tail) a.add1(p[head + 4 * nvec + threadIdx.x]);
+  block_merge<A, kThreads>(a, sh);
+  finish_chunk<A, T>(a, sh, o, c, chunks, out, partials, counters);
+}
+
+// GROUP threads per output (GROUP = 1 or 32), grid-stride over outputs.
+template <class A, class T, int GROUP>
+__global__ void __launch_bounds__(kThreads) reduce_short_kernel(
+    const T *__restrict__ in, int64_t start, int64_t seg_stride, int64_t len, int64_t nout,
+    T *__restrict__ out) {
+  const int64_t gid = int64_t(blockIdx.x) * kThreads + threadIdx.x;
+  const int64_t ngroups = int64_t(gridDim.x) * (kThreads / GROUP);
+  const int lane = threadIdx.x % GROUP;
+  for (int64_t o = gid / GROUP; o < nout; o += ngroups) {
+    const T *p = in + start + o * seg_stride;
+    A a;
+    a.init();
+    for (int64_t j = lane; j < len; j += GROUP) a.add1(p[j]);
+    if (GROUP == 32) warp_merge(a);
+    if (lane == 0) store_out<A, T>(out, o, a);
+  }
+}
+
+struct AffineArgs {
+  int32_t nkeep, nrest;
+  int64_t keep_ext[DESC_MAX_DIMS], keep_st[DESC_MAX_DIMS];
+  int64_t rest_ext[DESC_MAX_DIMS], rest_st[DESC_MAX_DIMS];
+  int64_t offset, n_rest;
+};
+
+// One CTA per (output, chunk) over an arbitrary affine map.
+template <class A, class T>
+__global__ void __launch_bounds__(kThreads) reduce_affine_kernel(
+    const T *__restrict__ in, const AffineArgs args, int64_t chunks, int64_t chunk_len,
+    T *__restrict__ out, uint2 *partials, unsigned *counters) {
+  __shared__ A sh[kThreads / 32];
+  const int64_t o = blockIdx.x / chunks, c = blockIdx.x % chunks;
+  int64_t base = args.offset, r = o;
+  for (int d = args.nkeep - 1; d >= 0; --d) {
+    base += (r % args.keep_ext[d]) * args.keep_st[d];
+    r /= args.keep_ext[d];
+  }
+  A a;
+  a.init();
+  const int64_t q1 = std::min<int64_t>(args.n_rest, (c + 1) * chunk_len);
+  for (int64_t q = c * chunk_len + threadIdx.x; q < q1; q += kThreads) {
+    int64_t e = base, t = q;
+    for (int d = args.nrest - 1; d >= 0; --d) {
+      e += (t % args.rest_ext[d]) * args.rest_st[d];
+      t /= args.rest_ext[d];
+    }
+    a.add1(in[e]);
+  }
+  block_merge<A, kThreads>(a, sh);
+  finish_chunk<A, T>(a, sh, o, c, chunks, out, partials, counters);
+}
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+size_t ws_for(int64_t len, int64_t nout) {
+  if (len <= kWarpRun) return 0;
+  const int64_t ch = chunks_for(len, nout);
+  if (ch == 1) return 0;
+  return align256(size_t(nout) * ch * sizeof(uint2)) + align256(size_t(nout) * sizeof(unsigned));
+}
+
+template <class A, class T>
+int32_t run_runs(const T *in, int64_t start, int64_t seg_stride, int64_t len, int64_t nout, T *out,
+                 void *ws, size_t ws_bytes, cudaStream_t s) {
+  if (len <= kSmallRun) {
+    const int64_t ctas = std::min<int64_t>((nout + kThreads - 1) / kThreads, int64_t(1) << 20);
+    reduce_short_kernel<A, T, 1><<<(unsigned)ctas, kThreads, 0, s>>>(in, start, seg_stride, len, nout, out);
+  } else if (len <= kWarpRun) {
+    const int64_t ctas = std::min<int64_t>((nout * 32 + kThreads - 1) / kThreads, int64_t(1) << 20);
+    reduce_short_kernel<A, T, 32><<<(unsigned)ctas, kThreads, 0, s>>>(in, start, seg_stride, len, nout, out);
+  } else {
+    const int64_t chunks = chunks_for(len, nout);
+    uint2 *partials = nullptr;
+    unsigned *counters = nullptr;
+    if (chunks > 1) {
+      if (!ws || ws_bytes < ws_for(len, nout)) return DESC_ERR_WORKSPACE;
+      partials = static_cast<uint2 *>(ws);
+      counters = reinterpret_cast<unsigned *>(static_cast<char *>(ws) +
+                                              align256(size_t(nout) * chunks * sizeof(uint2)));
+      DESC_CUDA_TRY(cudaMemsetAsync(counters, 0, size_t(nout) * sizeof(unsigned), s));
+    }
+    const int64_t nvec = len / 4 + 1;
+    const int64_t chunk_vec = (nvec + chunks - 1) / chunks;
+    if (nout * chunks >= (int64_t(1) << 31)) return DESC_ERR_UNSUPPORTED;
+    reduce_runs_kernel<A, T><<<(unsigned)(nout * chunks), kThreads, 0, s>>>(
+        in, start, seg_stride, len, chunks, chunk_vec, out, partials, counters);
+  }
+  DESC_CUDA_TRY(cudaGetLastError());
+  return DESC_OK;
+}
+
+template <class A, class T>
+int32_t run_affine(const T *in, const Plan &p, T *out, void *ws, size_t ws_bytes, cudaStream_t s) {
+  AffineArgs a;
+  a.nkeep = p.nkeep;
+  a.nrest = p.nrest;
+  for (int i = 0; i < p.nkeep; ++i) { a.keep_ext[i] = p.keep[i].extent; a.keep_st[i] = p.keep[i].stride; }
+  for (int i = 0; i < p.nrest; ++i) { a.rest_ext[i] = p.rest[i].extent; a.rest_st[i] = p.rest[i].stride; }
+  a.offset = p.offset;
+  a.n_rest = p.n_rest;
+  const int64_t nout = p.n_keep;
+  const int64_t chunks = p.n_rest <= kWarpRun ? 1 : chunks_for(p.n_rest, nout);
+  const int64_t chunk_len = (p.n_rest + chunks - 1) / chunks;
+  uint2 *partials = nullptr;
+  unsigned *counters = nullptr;
+  if (chunks > 1) {
+    if (!ws || ws_bytes < ws_for(p.n_rest, nout)) return DESC_ERR_WORKSPACE;
+    partials = static_cast<uint2 *>(ws);
+    counters = reinterpret_cast<unsigned *>(static_cast<char *>(ws) +
+                                            align256(size_t(nout) * chunks * sizeof(uint2)));
+    DESC_CUDA_TRY(cudaMemsetAsync(counters, 0, size_t(nout) * sizeof(unsigned), s));
+  }
+  if (nout * chunks >= (int64_t(1) << 31)) return DESC_ERR_UNSUPPORTED;
+  reduce_affine_kernel<A, T><<<(unsigned)(nout * chunks), kThreads, 0, s>>>(in, a, chunks, chunk_len,
+                                                                           out, partials, counters);
+  DESC_CUDA_TRY(cudaGetLastError());
+  return DESC_OK;
+}
+
+}  // namespace
+
+size_t reduce_segments_ws(int32_t /*dtype*/, int64_t len, int64_t nout) { return ws_for(len, nout); }
+
+int32_t launch_reduce_segments(int32_t dtype, const void *in, int64_t start, int64_t seg_stride,
+                               int64_t len, int64_t nout, void *out, int32_t flags, void *ws,
+                               size_t ws_bytes, desc_stream_t st) {
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(st);
+  if (dtype == DESC_I32)
+    return run_runs<AccI32, int32_t>(static_cast<const int32_t *>(in), start, seg_stride, len, nout,
+                                     static_cast<int32_t *>(out), ws, ws_bytes, s);
+  if (flags & DESC_KAHAN)
+    return run_runs<AccKahan, float>(static_cast<const float *>(in), start, seg_stride, len, nout,
+                                     static_cast<float *>(out), ws, ws_bytes, s);
+  return run_runs<AccF32, float>(static_cast<const float *>(in), start, seg_stride, len, nout,
+                                 static_cast<float *>(out), ws, ws_bytes, s);
+}
+
+size_t reduce_affine_ws(int64_t n_rest, int64_t nout) {
+  return n_rest <= kWarpRun ? 0 : ws_for(n_rest, nout);
+}
+
+int32_t launch_reduce_affine(int32_t dtype, const void *in, const Plan &p, void *out, int32_t flags,
+                             void *ws, size_t ws_bytes, desc_stream_t st) {
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(st);
+  if (dtype == DESC_I32)
+    return run_affine<AccI32, int32_t>(static_cast<const int32_t *>(in), p,
+                                       static_cast<int32_t *>(out), ws, ws_bytes, s);
+  if (flags & DESC_KAHAN)
+    return run_affine<AccKahan, float>(static_cast<const float *>(in), p, static_cast<float *>(out),
+                                       ws, ws_bytes, s);
+  return run_affine<AccF32, float>(static_cast<const float *>(in), p, static_cast<float *>(out), ws,
+                                   ws_bytes, s);
+}
+
+}  // namespace desc
