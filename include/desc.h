@@ -217,6 +217,37 @@ int32_t desc_scan(const desc_view *v, const desc_exec *ex, int32_t seg_level, in
                   const void *in, size_t in_bytes, void *out, size_t out_bytes, int32_t flags,
                   void *ws, size_t ws_bytes, desc_stream_t stream);
 
+/* ---- Scan without any device allocation --------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that may not allocate device memory at the time they call: for example a
+ * plugin whose host framework owns and budgets every device allocation, an
+ * out-of-memory or allocator callback that must not re-enter the allocator,
+ * or a real-time loop that forbids allocation after start-up.  Such callers
+ * cannot obtain the workspace desc_scan needs.
+ *
+ * desc_scan_noalloc computes exactly what desc_scan computes, for views whose
+ * scan runs over one contiguous run of the base array (for example the plain
+ * array, a split of it, or groups selected at seg_level); other views return
+ * DESC_ERR_UNSUPPORTED.  It takes no workspace: its scratch is a fixed
+ * static device array inside the library, large enough for
+ * DESC_SCAN_NOALLOC_MAX_ELEMS elements (256 bytes plus 16 bytes per 4096
+ * elements, about 1 MiB).  Every GPU that loads the library holds that array
+ * until the process exits.  A larger scan returns DESC_ERR_WORKSPACE and
+ * launches nothing.  The call allocates nothing: no cudaMalloc, no cudaFree,
+ * no allocating library routine.
+ *
+ * All calls on a device share the one array and the call clears what it
+ * needs, so calls must not overlap on the GPU: two of them in flight at once
+ * (on different streams, or from different threads) race on the scratch and
+ * give wrong results.  Order them on one stream or synchronise between them.
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  The
+ * stream must belong to the current device. */
+#define DESC_SCAN_NOALLOC_MAX_ELEMS (1LL << 28)
+int32_t desc_scan_noalloc(const desc_view *v, const desc_exec *ex, int32_t seg_level, int32_t dtype,
+                          const void *in, size_t in_bytes, void *out, size_t out_bytes,
+                          desc_stream_t stream);
+
 /* ---- Transpose (view-to-view copy) ----------------------------------
  * Section 1 / Section 5 benchmark "matrix transposition", generalised to any
  * pair of views with the same logical domain:

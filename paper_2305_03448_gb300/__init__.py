@@ -98,6 +98,8 @@ def _declare(L):
         "desc_transpose": (c_int32, [POINTER(View), POINTER(View), POINTER(Exec), c_int32, P, c_size_t, P,
                                      c_size_t, P]),
         "desc_stream_status": (c_int32, [P]),
+        "desc_scan_noalloc": (c_int32, [POINTER(View), POINTER(Exec), c_int32, c_int32, P, c_size_t, P, c_size_t,
+                                        P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -255,6 +257,18 @@ def desc_transpose(x, in_shape, in_ops, out, out_shape, out_ops, grid=None, bloc
     _check(lib().desc_transpose(ctypes.byref(make_view(in_shape, in_ops)), ctypes.byref(make_view(out_shape, out_ops)),
                                 _ref(make_exec(grid, block)), _dtype_code(x), _ptr(x), x.numel() * 4, _ptr(out),
                                 out.numel() * 4, _stream(stream)), "desc_transpose")
+    return out
+
+
+def desc_scan_noalloc(x, base_shape, ops, seg_level, grid=None, block=None, out=None, stream=None):
+    """desc_scan without a workspace: the library's static scratch is used
+    (contiguous scans of at most 2^28 elements; calls must not overlap)."""
+    import torch
+    if out is None:
+        out = torch.empty_like(x)
+    _check(lib().desc_scan_noalloc(ctypes.byref(make_view(base_shape, ops)), _ref(make_exec(grid, block)), seg_level,
+                                   _dtype_code(x), _ptr(x), x.numel() * 4, _ptr(out), out.numel() * 4,
+                                   _stream(stream)), "desc_scan_noalloc")
     return out
 
 

@@ -174,6 +174,30 @@ extern "C" int32_t desc_scan(const desc_view *v, const desc_exec *ex, int32_t se
   return launch_copy_affine(buf, 0, cst.data(), out, L.offset, st.data(), ext.data(), L.ndims, s);
 }
 
+// ---------------------------------------------------------------- scan, no allocation
+extern "C" int32_t desc_scan_noalloc(const desc_view *v, const desc_exec *ex, int32_t seg_level,
+                                     int32_t dtype, const void *in, size_t in_bytes, void *out,
+                                     size_t out_bytes, desc_stream_t s) {
+  if (!dtype_size(dtype)) return DESC_ERR_INVALID_ARG;
+  if (seg_level < DESC_LEVEL_GRID || seg_level > DESC_LEVEL_THREAD) return DESC_ERR_INVALID_ARG;
+  desc_lowered L;
+  int32_t r = desc_lower_view(v, ex, &L);
+  if (r != DESC_OK) return r;
+  if (in_bytes != size_t(L.base_elems) * 4 || out_bytes != in_bytes) return DESC_ERR_SIZE_MISMATCH;
+  const ScanPlan sp = plan_scan(L, seg_level);
+  if (sp.total == 0) return DESC_OK;
+  if (!sp.contig) return DESC_ERR_UNSUPPORTED;
+  if (sp.total > DESC_SCAN_NOALLOC_MAX_ELEMS) return DESC_ERR_WORKSPACE;
+  if ((r = check_device_ptr(in, 4)) != DESC_OK) return r;
+  if ((r = check_device_ptr(out, 4)) != DESC_OK) return r;
+  if (in != out && ranges_overlap(in, in_bytes, out, out_bytes)) return DESC_ERR_OVERLAP;
+  if ((r = check_writes(L, ex)) != DESC_OK) return r;
+  const char *ib = static_cast<const char *>(in);
+  char *ob = static_cast<char *>(out);
+  return launch_scan_contig_noalloc(dtype, ib + sp.start * 4, ob + sp.start * 4, sp.total,
+                                    sp.period, s);
+}
+
 // ---------------------------------------------------------------- transpose
 extern "C" int32_t desc_transpose(const desc_view *in_v, const desc_view *out_v,
                                   const desc_exec *ex, int32_t dtype, const void *in,

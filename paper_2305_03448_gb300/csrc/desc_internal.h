@@ -67,6 +67,9 @@ int32_t launch_reduce_affine(int32_t dtype, const void *in, const Plan &p, void 
 int32_t launch_scan_contig(int32_t dtype, const void *in, void *out, int64_t n, int64_t period,
                            int32_t flags, void *ws, size_t ws_bytes, desc_stream_t s);
 size_t scan_contig_ws(int32_t dtype, int64_t n);
+// The same scan with the library's static scratch array (noalloc.cu).
+int32_t launch_scan_contig_noalloc(int32_t dtype, const void *in, void *out, int64_t n,
+                                   int64_t period, desc_stream_t s);
 // Scan segmented by CSR offsets (nseg + 1 entries, device); sums (nullable)
 // receives the total of every segment (0 for empty ones).
 int32_t launch_scan_csr(int32_t dtype, const void *in, void *out, int64_t n, const int64_t *offsets,
