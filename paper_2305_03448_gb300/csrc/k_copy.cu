@@ -1,10 +1,11 @@
 // Copy through views: the tiled transpose and the general affine copy.
 //
-// Transpose: each CTA moves one TD x TD tile (32 x 8 threads per 32-column
-// strip, as in the tiled transposes of Section 1) through a padded shared
-// tile, so that both the global reads (along input rows) and the global
-// writes (along output rows) are coalesced 128-byte lines.  The padding of
-// one word per row makes the column-wise shared-memory reads conflict-free.
+// Transpose: each CTA moves one TD x TD tile through a padded shared tile
+// with 32 x 8 threads (the thread shape of the tiled transposes of Section 1;
+// TD = 64 gives every thread 16 elements in flight), so that both the global
+// reads (along input rows) and the global writes (along output rows) are
+// coalesced 128-byte lines.  The padding of one word per row makes the
+// column-wise shared-memory reads conflict-free.
 //
 // Affine copy: any pair of affine maps over a common domain; one element per
 // thread and iteration, indices decoded from the domain extents.
@@ -88,11 +89,20 @@ int32_t launch_transpose(const float *in, float *out, int64_t R, int64_t C, int6
                          desc_stream_t st) {
   cudaStream_t s = reinterpret_cast<cudaStream_t>(st);
   if (R == 0 || C == 0 || batch == 0) return DESC_OK;
-  constexpr int TD = 32, BR = 8;
-  const int64_t gx = (C + TD - 1) / TD, gy = (R + TD - 1) / TD;
-  if (gx >= (int64_t(1) << 31) || gy > 65535 || batch > 65535) return DESC_ERR_UNSUPPORTED;
-  transpose_kernel<TD, BR><<<dim3((unsigned)gx, (unsigned)gy, (unsigned)batch), dim3(32, BR), 0, s>>>(
-      in, out, R, C, ld_in, ld_out, bs_in, bs_out);
+  constexpr int BR = 8;
+  if (R >= 64 && C >= 64) {       // 64 x 64 tiles: 16 loads in flight per thread
+    constexpr int TD = 64;
+    const int64_t gx = (C + TD - 1) / TD, gy = (R + TD - 1) / TD;
+    if (gx >= (int64_t(1) << 31) || gy > 65535 || batch > 65535) return DESC_ERR_UNSUPPORTED;
+    transpose_kernel<TD, BR><<<dim3((unsigned)gx, (unsigned)gy, (unsigned)batch), dim3(32, BR), 0, s>>>(
+        in, out, R, C, ld_in, ld_out, bs_in, bs_out);
+  } else {
+    constexpr int TD = 32;
+    const int64_t gx = (C + TD - 1) / TD, gy = (R + TD - 1) / TD;
+    if (gx >= (int64_t(1) << 31) || gy > 65535 || batch > 65535) return DESC_ERR_UNSUPPORTED;
+    transpose_kernel<TD, BR><<<dim3((unsigned)gx, (unsigned)gy, (unsigned)batch), dim3(32, BR), 0, s>>>(
+        in, out, R, C, ld_in, ld_out, bs_in, bs_out);
+  }
   DESC_CUDA_TRY(cudaGetLastError());
   return DESC_OK;
 }

@@ -21,7 +21,7 @@ namespace desc {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kUnroll = 4;
+constexpr int kUnroll = 8;
 constexpr int64_t kTargetCtas = 1216;      // 8 per SM on a 152-SM GB300
 constexpr int64_t kSmallRun = 16;          // <= this: one thread per output
 constexpr int64_t kWarpRun = 4096;         // <= this: one warp per output

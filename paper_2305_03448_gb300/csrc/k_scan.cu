@@ -13,17 +13,18 @@
 // `period` elements; or CSR offsets).  A tile that contains a head publishes
 // its inclusive value at once (nothing before the head can change it).
 //
-// Published words (64 bit, single-copy atomic): status in bits 63..62
-// (1 = tile total, 2 = inclusive prefix), value bits in 31..0.  FP32 values
-// travel as an unevaluated (hi, lo) pair, in two words that both carry the
-// status; a reader accepts them only when the two statuses agree.  The carry
-// is accumulated with error-free transformations, so the per-element error
+// Published words (64 bit, single-copy atomic, so one load reads a whole
+// state): status in bits 63..62 (1 = tile total, 2 = inclusive prefix) and
+// the value.  FP32 carries travel as an unevaluated (hi, lo) pair and are
+// accumulated with error-free transformations, so the per-element error
 // stays within (ITEMS + log2 THREADS + 2) ulp-sized terms of sum |x|.
 //
 // Every wait is bounded: a waiting warp gives up after a clock64 budget (or
 // as soon as another tile has given up), records DESC_ERR_DEVICE_TIMEOUT in
 // the device status word, and its CTA leaves without writing.
 #include <algorithm>
+#include <cstdlib>
+#include <cstring>
 
 #include "k_common.cuh"
 
@@ -33,9 +34,6 @@ __device__ int g_scan_status;
 
 namespace {
 
-constexpr int kThreads = 256;
-constexpr int kItems = 16;
-constexpr int kTile = kThreads * kItems;
 constexpr unsigned long long kStatAgg = 1ull, kStatIncl = 2ull;
 constexpr long long kBudgetCycles = 1ll << 31;      // about one second
 constexpr long long kDebugBudgetCycles = 1ll << 26; // tens of milliseconds
@@ -43,7 +41,7 @@ constexpr long long kDebugBudgetCycles = 1ll << 26; // tens of milliseconds
 enum Mode { PLAIN = 0, PERIODIC = 1, CSR = 2 };
 
 struct TileState {
-  unsigned long long w0, w1;
+  unsigned long long w;
 };
 
 struct ScanWs {
@@ -68,9 +66,6 @@ template <> struct Carry<int32_t> {
   __device__ static Carry of(int32_t x) { return {(uint32_t)x}; }
   __device__ Carry plus(const Carry &o) const { return {v + o.v}; }
   __device__ Carry shfl_down(int off) const { return {__shfl_down_sync(0xffffffffu, v, off)}; }
-  __device__ uint32_t hi_bits() const { return v; }
-  __device__ uint32_t lo_bits() const { return 0u; }
-  __device__ static Carry from_bits(uint32_t h, uint32_t) { return {h}; }
 };
 template <> struct Carry<float> {
   float hi, lo;
@@ -86,9 +81,6 @@ template <> struct Carry<float> {
   __device__ Carry shfl_down(int off) const {
     return {__shfl_down_sync(0xffffffffu, hi, off), __shfl_down_sync(0xffffffffu, lo, off)};
   }
-  __device__ uint32_t hi_bits() const { return __float_as_uint(hi); }
-  __device__ uint32_t lo_bits() const { return __float_as_uint(lo); }
-  __device__ static Carry from_bits(uint32_t h, uint32_t l) { return {__uint_as_float(h), __uint_as_float(l)}; }
 };
 
 template <class T>
@@ -106,16 +98,29 @@ __device__ __forceinline__ float apply_carry(float x, const Carry<float> &c) {
   return __fadd_rn(c.hi, __fadd_rn(c.lo, x));
 }
 
+// One 64-bit word per tile: status in bits 63..62, value below.  int32:
+// the value in bits 31..0.  FP32: hi in bits 31..0 and lo, with its two
+// lowest mantissa bits dropped (a relative change below 2^-21 of a term that
+// is itself below half an ulp of hi), in bits 61..32.
+__device__ __forceinline__ unsigned long long pack(unsigned long long status, const Carry<int32_t> &c) {
+  return (status << 62) | c.v;
+}
+__device__ __forceinline__ unsigned long long pack(unsigned long long status, const Carry<float> &c) {
+  return (status << 62) | ((unsigned long long)(__float_as_uint(c.lo) >> 2) << 32) | __float_as_uint(c.hi);
+}
 template <class T>
-__device__ __forceinline__ void publish(TileState *st, unsigned long long status, const Carry<T> &c) {
-  const unsigned long long tag = status << 62;
-  st_relaxed(&st->w0, tag | c.hi_bits());
-  if (sizeof(Carry<T>) > 4) st_relaxed(&st->w1, tag | c.lo_bits());
+__device__ __forceinline__ Carry<T> unpack(unsigned long long w);
+template <>
+__device__ __forceinline__ Carry<int32_t> unpack(unsigned long long w) { return {(uint32_t)w}; }
+template <>
+__device__ __forceinline__ Carry<float> unpack(unsigned long long w) {
+  return {__uint_as_float((uint32_t)w), __uint_as_float((uint32_t)((w >> 32) & 0x3FFFFFFFull) << 2)};
 }
 
-template <class T> struct VecOf;
-template <> struct VecOf<int32_t> { using type = int4; };
-template <> struct VecOf<float> { using type = float4; };
+template <class T>
+__device__ __forceinline__ void publish(TileState *st, unsigned long long status, const Carry<T> &c) {
+  st_relaxed(&st->w, pack(status, c));
+}
 
 struct ScanArgs {
   int64_t n;
@@ -127,7 +132,13 @@ struct ScanArgs {
   int32_t vec;             // in and out are 16-byte aligned: 128-bit accesses
 };
 
-// Looks back from tile `tile` (warp 0 only).  Returns false on timeout.
+// Looks back from tile `tile` (one warp).  Each poll reads a window of
+// 32 x kSlots tile states (lane l takes kSlots consecutive ones); everything
+// up to the nearest inclusive prefix in the window must have published
+// before the window is folded in.  Failed polls back off exponentially, which
+// keeps the hot tile states from being flooded.  Returns false on timeout.
+constexpr int kSlots = 1;
+
 template <class T>
 __device__ bool look_back(TileState *states, int64_t tile, ScanWs *ws, long long budget,
                           Carry<T> &prefix) {
@@ -135,24 +146,33 @@ __device__ bool look_back(TileState *states, int64_t tile, ScanWs *ws, long long
   Carry<T> acc = Carry<T>::zero();
   int64_t j = tile - 1;   // nearest predecessor not yet folded in
   const long long t0 = clock64();
+  unsigned polls = 0;
   while (true) {
-    const int64_t me = j - lane;
-    unsigned long long w0 = 0, w1 = 0, st = 0;
+    unsigned long long w[kSlots];
+    int stop;
+    unsigned incl_lanes;
     while (true) {
-      if (me >= 0) {
-        w0 = ld_relaxed(&states[me].w0);
-        st = w0 >> 62;
-        if (sizeof(Carry<T>) > 4 && st != 0) {
-          w1 = ld_relaxed(&states[me].w1);
-          if ((w1 >> 62) != st) st = 0;   // torn pair: read again
-        }
-      } else {
-        st = kStatIncl;                   // before tile 0: empty prefix
-        w0 = 0; w1 = 0;
+#pragma unroll
+      for (int k = 0; k < kSlots; ++k) {
+        const int64_t me = j - (lane * kSlots + k);
+        w[k] = me >= 0 ? ld_relaxed(&states[me].w) : (kStatIncl << 62);   // before tile 0: empty
       }
-      if (__all_sync(0xffffffffu, st != 0)) break;
+      int kin = kSlots;                                 // nearest inclusive slot of this lane
+#pragma unroll
+      for (int k = kSlots - 1; k >= 0; --k)
+        if ((w[k] >> 62) == kStatIncl) kin = k;
+      incl_lanes = __ballot_sync(0xffffffffu, kin < kSlots);
+      const int first = incl_lanes ? __ffs(incl_lanes) - 1 : 31;
+      const int kfirst = __shfl_sync(0xffffffffu, kin, first);
+      stop = incl_lanes ? first * kSlots + kfirst : 32 * kSlots - 1;
+      bool ready = true;
+#pragma unroll
+      for (int k = 0; k < kSlots; ++k)
+        if (lane * kSlots + k <= stop && (w[k] >> 62) == 0) ready = false;
+      if (__all_sync(0xffffffffu, ready)) break;
       int give_up = 0;
-      if (lane == 0)
+      ++polls;
+      if (lane == 0 && (polls & 31) == 0)      // the abort flag is one more L2 round trip
         give_up = (*(volatile unsigned *)&ws->abort != 0u) || (clock64() - t0 > budget);
       give_up = __shfl_sync(0xffffffffu, give_up, 0);
       if (give_up) {
@@ -162,73 +182,173 @@ __device__ bool look_back(TileState *states, int64_t tile, ScanWs *ws, long long
         }
         return false;
       }
-      __nanosleep(64);
+      __nanosleep(min(32u << min(polls, 5u), 1024u));   // exponential back-off
     }
-    const unsigned incl = __ballot_sync(0xffffffffu, st == kStatIncl);
-    const int stop = incl ? __ffs(incl) - 1 : 31;     // nearest inclusive prefix
-    Carry<T> mine = (lane <= stop) ? Carry<T>::from_bits((uint32_t)w0, (uint32_t)w1) : Carry<T>::zero();
+    Carry<T> mine = Carry<T>::zero();
+#pragma unroll
+    for (int k = 0; k < kSlots; ++k)
+      if (lane * kSlots + k <= stop) mine = mine.plus(unpack<T>(w[k]));
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) mine = mine.plus(mine.shfl_down(off));
-    acc = acc.plus(Carry<T>{mine});
-    if (incl) break;
-    j -= 32;
+    acc = acc.plus(mine);
+    if (incl_lanes) break;
+    j -= 32 * kSlots;
   }
   prefix = acc;
   return true;
 }
 
-template <class T, int MODE>
-__global__ void __launch_bounds__(kThreads) scan_kernel(const T *in, T *out,
-                                                        ScanArgs args, ScanWs *ws,
-                                                        TileState *states) {
-  using V = typename VecOf<T>::type;
+// ---- asynchronous tile copies (cp.async) into padded shared memory ------
+// A sub-tile is 1024 chunks of 16 bytes.  Chunk j sits at byte 16 * (j + j/8):
+// one 16-byte pad per 128 bytes makes both the striped accesses (lane l on
+// chunk base + l, used to move data to and from global memory with full
+// 128-byte lines) and the blocked accesses (thread t on chunks 4t..4t+3,
+// used by the scan) free of shared-memory bank conflicts.
+__device__ __forceinline__ int chunk_off(int j) { return 16 * (j + (j >> 3)); }
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, int src_bytes) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(s), "l"(gmem), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// A CTA scans one tile of kSub * SUB elements: SUB sub-tiles of kSub
+// elements (kThreads threads x kItems items), each staged in shared memory.
+// Large tiles matter: decoupled look-back serves at most about one window of
+// tiles per L2 round trip, so the bytes per tile set the attainable rate.
+constexpr int kThreads = 256;                       // scanning threads
+constexpr int kItems = 16;                          // elements per thread and sub-tile
+constexpr int kWarps = kThreads / 32;
+constexpr int kSub = kThreads * kItems;             // elements per sub-tile
+constexpr int kSubChunks = kSub / 4;                // 16-byte chunks per sub-tile
+constexpr int kStageBytes = 16 * (kSubChunks + kSubChunks / 8);
+
+__device__ __forceinline__ void compute_bar() { asm volatile("bar.sync 1, %0;" ::"n"(kThreads) : "memory"); }
+
+// Start copying kSub elements from g_start (elements past n read as zero).
+template <class T>
+__device__ __forceinline__ void load_sub(unsigned char *stage, const T *in, int64_t g_start,
+                                         int64_t n, bool vec) {
+#pragma unroll
+  for (int q = 0; q < kSubChunks / kThreads; ++q) {
+    const int j = q * kThreads + threadIdx.x;
+    const int64_t g = g_start + 4 * int64_t(j);
+    unsigned char *dst = stage + chunk_off(j);
+    if (vec) {
+      const int64_t rem = n - g;
+      const int bytes = rem >= 4 ? 16 : (rem > 0 ? int(rem) * 4 : 0);
+      cp_async16(dst, bytes ? static_cast<const void *>(in + g) : static_cast<const void *>(in), bytes);
+    } else {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        if (g + c < n) cp_async4(dst + 4 * c, in + g + c);
+        else *reinterpret_cast<T *>(dst + 4 * c) = T(0);
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void cp_async_wait_dyn(int pending) {
+  switch (pending) {
+    case 0: cp_async_wait<0>(); break;
+    case 1: cp_async_wait<1>(); break;
+    case 2: cp_async_wait<2>(); break;
+    default: cp_async_wait<3>(); break;
+  }
+}
+
+// The segment containing element t0: the largest s with offsets[s] <= t0
+// (one warp, 32-way search).
+__device__ __forceinline__ int64_t find_segment(const int64_t *offsets, int64_t nseg, int64_t t0) {
+  const int lane = threadIdx.x & 31;
+  int64_t lo = 0, hi = nseg;
+  while (hi - lo > 1) {
+    const int64_t step = (hi - lo + 31) / 32;
+    const int64_t probe = lo + int64_t(lane) * step;
+    const bool le = probe < hi && offsets[probe] <= t0;
+    const unsigned m = __ballot_sync(0xffffffffu, le);
+    const int last = 31 - __clz(m);   // lane 0 always qualifies
+    lo = lo + int64_t(last) * step;
+    hi = std::min<int64_t>(hi, lo + step);
+  }
+  return lo;
+}
+
+// One CTA per tile, tiles in ticket order.  Warps 0..7 load the tile (one
+// cp.async group per sub-tile into padded shared memory, full 128-byte
+// lines), scan the sub-tiles in order with an in-tile carry, and publish the
+// tile total as soon as it is known.  Warp 8 looks back meanwhile (the prefix
+// of a tile does not depend on its data) and publishes the inclusive prefix
+// once it has both.  The carry is added during the coalesced store pass, to
+// the elements that have no segment start before them in the tile.
+template <class T, int MODE, int SUB>
+__global__ void __launch_bounds__(kThreads + 32) scan_kernel(const T *in, T *out, ScanArgs args,
+                                                             ScanWs *ws, TileState *states) {
+  constexpr int kTile = kSub * SUB;
+  extern __shared__ __align__(128) unsigned char ring[];   // SUB stages
   __shared__ int64_t sh_tile;
-  __shared__ T sh_wval[kThreads / 32];
-  __shared__ int sh_wflag[kThreads / 32];
+  __shared__ T sh_wval[kWarps];
+  __shared__ int sh_wflag[kWarps];
+  __shared__ T sh_carry;                // in-tile carry after the sub-tiles done so far
+  __shared__ int sh_carry_flag;
   __shared__ Carry<T> sh_prefix;
   __shared__ int sh_ok;
-  __shared__ unsigned sh_heads[kTile / 32];
+  __shared__ unsigned sh_heads[MODE == CSR ? kTile / 32 : 1];
+  __shared__ unsigned short sh_need[MODE == PLAIN ? 1 : SUB * kThreads];  // carry-needed bits
   __shared__ int64_t sh_seg0;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (tid == 0) {
-    sh_tile = atomicAdd(&ws->ticket, 1u);
-    sh_ok = 1;
-  }
+  const int64_t n = args.n;
+  const bool vec = args.vec != 0;
+  if (tid == 0) sh_tile = atomicAdd(&ws->ticket, 1u);
   __syncthreads();
   const int64_t tile = sh_tile;
+  const int64_t ntiles = (n + kTile - 1) / kTile;
   const int64_t t0 = tile * kTile;
-  const int64_t n = args.n;
-  const bool full = t0 + kTile <= n;
-  const int64_t g0 = t0 + int64_t(tid) * kItems;
+  const bool stall = args.debug && tile == 1;
 
-  // ---- head flags of this thread's items (bit i = item i starts a segment)
-  unsigned hmask = 0u;
-  if (MODE == PERIODIC) {
-    int64_t r = g0 % args.period;
+  if (warp == kWarps) {
+    // ---- look-back warp: prefix of everything before t0
+    bool first_is_head = tile == 0;
+    if (MODE == PERIODIC) first_is_head = first_is_head || (t0 % args.period == 0);
+    if (MODE == CSR && !first_is_head)
+      first_is_head = args.offsets[find_segment(args.offsets, args.nseg, t0)] == t0;
+    Carry<T> prefix = Carry<T>::zero();
+    bool ok = true;
+    if (!first_is_head)
+      ok = look_back<T>(states, tile, ws, args.debug ? kDebugBudgetCycles : kBudgetCycles, prefix);
+    if (lane == 0) {
+      sh_prefix = prefix;
+      sh_ok = ok ? 1 : 0;
+    }
+    __syncthreads();                                    // (S) tile total known
+    if (ok && lane == 0 && !stall && tile != 0 && !sh_carry_flag)
+      publish<T>(&states[tile], kStatIncl, prefix.plus(Carry<T>::of(sh_carry)));
+    return;
+  }
+
+  // ---- compute warps
 #pragma unroll
-    for (int i = 0; i < kItems; ++i) {
-      if (r == 0) hmask |= 1u << i;
-      if (++r == args.period) r = 0;
-    }
-  } else if (MODE == CSR) {
+  for (int s = 0; s < SUB; ++s) {
+    load_sub<T>(ring + s * kStageBytes, in, t0 + int64_t(s) * kSub, n, vec);
+    cp_async_commit();
+  }
+  if (MODE == CSR) {
     for (int i = tid; i < kTile / 32; i += kThreads) sh_heads[i] = 0u;
-    // segment containing t0: largest s with offsets[s] <= t0 (warp 0 search)
     if (warp == 0) {
-      int64_t lo = 0, hi = args.nseg;   // answer in [lo, hi)
-      while (hi - lo > 1) {
-        const int64_t step = (hi - lo + 31) / 32;
-        const int64_t probe = lo + int64_t(lane) * step;
-        const bool le = probe < hi && args.offsets[probe] <= t0;
-        const unsigned m = __ballot_sync(0xffffffffu, le);
-        const int last = 31 - __clz(m);      // lane 0 always qualifies (offsets[lo] <= t0)
-        lo = lo + int64_t(last) * step;
-        hi = std::min<int64_t>(hi, lo + step);
-      }
-      if (lane == 0) sh_seg0 = lo;
+      const int64_t s0 = find_segment(args.offsets, args.nseg, t0);
+      if (lane == 0) sh_seg0 = s0;
     }
-    __syncthreads();
-    // heads: offsets[s] for s > seg0 with offsets[s] < t0 + kTile
+    compute_bar();
     const int64_t tend = std::min<int64_t>(t0 + kTile, n);
     for (int64_t s = sh_seg0 + 1 + tid; s < args.nseg; s += kThreads) {
       const int64_t b = args.offsets[s];
@@ -237,128 +357,157 @@ __global__ void __launch_bounds__(kThreads) scan_kernel(const T *in, T *out,
       atomicOr(&sh_heads[rel >> 5], 1u << (rel & 31));
     }
     if (tid == 0 && args.offsets[sh_seg0] == t0) atomicOr(&sh_heads[0], 1u);
-    __syncthreads();
-    const int64_t rel0 = int64_t(tid) * kItems;
-    hmask = (sh_heads[rel0 >> 5] >> (rel0 & 31)) & ((1u << kItems) - 1u);
+  }
+  if (tid == 0) {
+    sh_carry = T(0);
+    sh_carry_flag = 0;
   }
 
-  // ---- load and scan this thread's items
-  T v[kItems];
-  if (full && args.vec) {
-    const V *p = reinterpret_cast<const V *>(in + g0);
+#pragma unroll 1
+  for (int s = 0; s < SUB; ++s) {
+    unsigned char *st = ring + s * kStageBytes;
+    cp_async_wait_dyn(SUB - 1 - s);                     // sub-tile s has landed (this thread)
+    compute_bar();                                      // ... for every thread; carry visible
+    const T cv = sh_carry;
+    const int cf = sh_carry_flag;
+    const int64_t g0 = t0 + int64_t(s) * kSub + int64_t(tid) * kItems;
+    unsigned hmask = 0u;
+    if (MODE == PERIODIC) {
+      int64_t r = g0 % args.period;
+#pragma unroll
+      for (int i = 0; i < kItems; ++i) {
+        if (r == 0) hmask |= 1u << i;
+        if (++r == args.period) r = 0;
+      }
+    } else if (MODE == CSR) {
+      const int rel0 = s * kSub + tid * kItems;
+      hmask = (sh_heads[rel0 >> 5] >> (rel0 & 31)) & 0xffffu;
+    }
+    T v[kItems];
 #pragma unroll
     for (int q = 0; q < kItems / 4; ++q) {
-      const V x = ld_stream(p + q);
-      v[4 * q] = x.x; v[4 * q + 1] = x.y; v[4 * q + 2] = x.z; v[4 * q + 3] = x.w;
+      const int4 x = *reinterpret_cast<const int4 *>(st + chunk_off((kItems / 4) * tid + q));
+      v[4 * q] = __builtin_bit_cast(T, x.x);
+      v[4 * q + 1] = __builtin_bit_cast(T, x.y);
+      v[4 * q + 2] = __builtin_bit_cast(T, x.z);
+      v[4 * q + 3] = __builtin_bit_cast(T, x.w);
     }
-  } else {
 #pragma unroll
-    for (int i = 0; i < kItems; ++i) v[i] = (g0 + i < n) ? in[g0 + i] : T(0);
-  }
+    for (int i = 1; i < kItems; ++i)
+      if (!((hmask >> i) & 1u)) v[i] = add_t(v[i - 1], v[i]);
+    int f = hmask != 0u;
+    T a = v[kItems - 1];
 #pragma unroll
-  for (int i = 1; i < kItems; ++i)
-    if (!((hmask >> i) & 1u)) v[i] = add_t(v[i - 1], v[i]);
-  int f = hmask != 0u;
-  T a = v[kItems - 1];
-
-  // ---- warp inclusive scan of (flag, value) with the segmented operator
-#pragma unroll
-  for (int off = 1; off < 32; off <<= 1) {
-    const T au = __shfl_up_sync(0xffffffffu, a, off);
-    const int fu = __shfl_up_sync(0xffffffffu, f, off);
-    if (lane >= off) {
-      if (!f) a = add_t(au, a);
-      f |= fu;
-    }
-  }
-  if (lane == 31) {
-    sh_wval[warp] = a;
-    sh_wflag[warp] = f;
-  }
-  // thread-exclusive within the warp
-  T ex = __shfl_up_sync(0xffffffffu, a, 1);
-  int exf = __shfl_up_sync(0xffffffffu, f, 1);
-  if (lane == 0) { ex = T(0); exf = 0; }
-  __syncthreads();
-  // ---- scan of the warp totals (warp 0), exclusive per warp
-  if (warp == 0) {
-    T wa = lane < kThreads / 32 ? sh_wval[lane] : T(0);
-    int wf = lane < kThreads / 32 ? sh_wflag[lane] : 0;
-#pragma unroll
-    for (int off = 1; off < kThreads / 32; off <<= 1) {
-      const T au = __shfl_up_sync(0xffffffffu, wa, off);
-      const int fu = __shfl_up_sync(0xffffffffu, wf, off);
+    for (int off = 1; off < 32; off <<= 1) {           // warp scan, segmented operator
+      const T au = __shfl_up_sync(0xffffffffu, a, off);
+      const int fu = __shfl_up_sync(0xffffffffu, f, off);
       if (lane >= off) {
-        if (!wf) wa = add_t(au, wa);
-        wf |= fu;
+        if (!f) a = add_t(au, a);
+        f |= fu;
       }
     }
-    T we = __shfl_up_sync(0xffffffffu, wa, 1);
-    int wfe = __shfl_up_sync(0xffffffffu, wf, 1);
-    if (lane == 0) { we = T(0); wfe = 0; }
-    const T tile_val = __shfl_sync(0xffffffffu, wa, kThreads / 32 - 1);
-    const int tile_flag = __shfl_sync(0xffffffffu, wf, kThreads / 32 - 1);
-    __syncwarp();
-    if (lane < kThreads / 32) {
-      sh_wval[lane] = we;
-      sh_wflag[lane] = wfe;
+    if (lane == 31) {
+      sh_wval[warp] = a;
+      sh_wflag[warp] = f;
     }
-    // ---- publish, then look back when the tile's first item needs a carry
-    TileState *mine = &states[tile];
-    const bool stall = args.debug && tile == 1;
-    const bool head_first = (hmask & 1u) && tid == 0;   // lane 0 of warp 0 holds item 0
-    const bool first_is_head = __shfl_sync(0xffffffffu, head_first ? 1 : 0, 0) != 0;
-    Carry<T> prefix = Carry<T>::zero();
-    bool ok = true;
-    if (tile == 0 || tile_flag) {
-      if (lane == 0 && !stall) publish<T>(mine, kStatIncl, Carry<T>::of(tile_val));
-      if (tile != 0 && !first_is_head)
-        ok = look_back<T>(states, tile, ws, args.debug ? kDebugBudgetCycles : kBudgetCycles, prefix);
-    } else {
-      if (lane == 0 && !stall) publish<T>(mine, kStatAgg, Carry<T>::of(tile_val));
-      ok = look_back<T>(states, tile, ws, args.debug ? kDebugBudgetCycles : kBudgetCycles, prefix);
-      if (ok && lane == 0 && !stall) publish<T>(mine, kStatIncl, prefix.plus(Carry<T>::of(tile_val)));
-    }
-    if (lane == 0) {
-      sh_prefix = prefix;
-      sh_ok = ok ? 1 : 0;
-    }
-  }
-  __syncthreads();
-  if (!sh_ok) return;
-
-  // ---- combine: warp-exclusive, then thread-exclusive, then the tile carry
-  const T wex = sh_wval[warp];
-  const int wexf = sh_wflag[warp];
-  if (warp > 0 && !exf) ex = add_t(wex, ex);       // prefix of this thread within the tile
-  if (warp > 0) exf |= wexf;
-  const Carry<T> pre = sh_prefix;
-  const bool use_ex = (warp > 0) || (lane > 0);
+    T ex = __shfl_up_sync(0xffffffffu, a, 1);
+    int exf = __shfl_up_sync(0xffffffffu, f, 1);
+    if (lane == 0) { ex = T(0); exf = 0; }
+    compute_bar();
+    if (warp == 0) {                                    // scan of the warp totals
+      T wa = lane < kWarps ? sh_wval[lane] : T(0);
+      int wf = lane < kWarps ? sh_wflag[lane] : 0;
 #pragma unroll
-  for (int i = 0; i < kItems; ++i) {
-    // items after this thread's first head are already final
-    if ((hmask & ((2u << i) - 1u)) == 0u) {
-      T x = use_ex ? add_t(ex, v[i]) : v[i];
-      v[i] = exf ? x : apply_carry(x, pre);
+      for (int off = 1; off < kWarps; off <<= 1) {
+        const T au = __shfl_up_sync(0xffffffffu, wa, off);
+        const int fu = __shfl_up_sync(0xffffffffu, wf, off);
+        if (lane >= off) {
+          if (!wf) wa = add_t(au, wa);
+          wf |= fu;
+        }
+      }
+      T we = __shfl_up_sync(0xffffffffu, wa, 1);
+      int wfe = __shfl_up_sync(0xffffffffu, wf, 1);
+      if (lane == 0) { we = T(0); wfe = 0; }
+      const T sub_val = __shfl_sync(0xffffffffu, wa, kWarps - 1);
+      const int sub_flag = __shfl_sync(0xffffffffu, wf, kWarps - 1);
+      __syncwarp();
+      if (lane < kWarps) {
+        sh_wval[lane] = we;
+        sh_wflag[lane] = wfe;
+      }
+      if (lane == 0) {                                  // carry after this sub-tile
+        sh_carry = sub_flag ? sub_val : add_t(cv, sub_val);
+        sh_carry_flag = cf | sub_flag;
+      }
     }
-  }
-  if (full && args.vec) {
-    V *p = reinterpret_cast<V *>(out + g0);
+    compute_bar();
+    // prefix of this thread within the tile: carry, then warp, then thread
+    T pv = sh_wval[warp];
+    int pf = sh_wflag[warp];
+    if (!exf) ex = add_t(pv, ex);
+    exf |= pf;                                          // (pf, pv) (+) (exf, ex)
+    const T in_tile = exf ? ex : add_t(cv, ex);
+    const int in_flag = exf | cf;
+    unsigned need = 0u;                                 // elements with no head before them
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) {
+      if ((hmask & ((2u << i) - 1u)) == 0u) {           // before this thread's first head
+        v[i] = add_t(in_tile, v[i]);
+        if (!in_flag) need |= 1u << i;
+      }
+    }
+    if (MODE != PLAIN) sh_need[s * kThreads + tid] = (unsigned short)need;
 #pragma unroll
     for (int q = 0; q < kItems / 4; ++q) {
-      V x;
-      x.x = v[4 * q]; x.y = v[4 * q + 1]; x.z = v[4 * q + 2]; x.w = v[4 * q + 3];
-      __stcs(p + q, x);
+      int4 x;
+      x.x = __builtin_bit_cast(int, v[4 * q]);
+      x.y = __builtin_bit_cast(int, v[4 * q + 1]);
+      x.z = __builtin_bit_cast(int, v[4 * q + 2]);
+      x.w = __builtin_bit_cast(int, v[4 * q + 3]);
+      *reinterpret_cast<int4 *>(st + chunk_off((kItems / 4) * tid + q)) = x;
     }
-  } else {
-#pragma unroll
-    for (int i = 0; i < kItems; ++i)
-      if (g0 + i < n) out[g0 + i] = v[i];
   }
+  compute_bar();
+  if (tid == 0 && !stall) {
+    // publish at once: the inclusive value when nothing before can change it
+    // (tile 0, or a tile holding a segment start), else the tile total
+    publish<T>(&states[tile], (tile == 0 || sh_carry_flag) ? kStatIncl : kStatAgg, Carry<T>::of(sh_carry));
+  }
+  __syncthreads();                                      // (S) with the look-back warp
+  if (!sh_ok) return;                                   // a wait gave up: write nothing
 
-  // ---- CSR: totals of the segments ending in this tile, read back from out
-  if (MODE == CSR && args.sums) {
-    __syncthreads();
+  // ---- coalesced stores, adding the tile carry where needed
+  const Carry<T> pre = sh_prefix;
+#pragma unroll 1
+  for (int s = 0; s < SUB; ++s) {
+    const unsigned char *st = ring + s * kStageBytes;
+#pragma unroll
+    for (int q = 0; q < kSubChunks / kThreads; ++q) {
+      const int j = q * kThreads + tid;
+      const int64_t g = t0 + int64_t(s) * kSub + 4 * int64_t(j);
+      int4 x = *reinterpret_cast<const int4 *>(st + chunk_off(j));
+      const unsigned nb = MODE == PLAIN ? 0xfu : (unsigned(sh_need[s * kThreads + (j >> 2)]) >> ((j & 3) * 4)) & 0xfu;
+      T y[4] = {__builtin_bit_cast(T, x.x), __builtin_bit_cast(T, x.y), __builtin_bit_cast(T, x.z),
+                __builtin_bit_cast(T, x.w)};
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        if ((nb >> c) & 1u) y[c] = apply_carry(y[c], pre);
+      if (vec && g + 4 <= n) {
+        x.x = __builtin_bit_cast(int, y[0]);
+        x.y = __builtin_bit_cast(int, y[1]);
+        x.z = __builtin_bit_cast(int, y[2]);
+        x.w = __builtin_bit_cast(int, y[3]);
+        __stcs(reinterpret_cast<int4 *>(out + g), x);
+      } else {
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+          if (g + c < n) out[g + c] = y[c];
+      }
+    }
+  }
+  if (MODE == CSR && args.sums) {                       // totals of segments ending here
+    compute_bar();                                      // (sums read the stored outputs)
     T *sums = static_cast<T *>(args.sums);
     const int64_t tend = std::min<int64_t>(t0 + kTile, n);
     for (int64_t s = sh_seg0 + tid; s < args.nseg; s += kThreads) {
@@ -366,8 +515,6 @@ __global__ void __launch_bounds__(kThreads) scan_kernel(const T *in, T *out,
       if (b >= tend) break;
       if (e > b && e - 1 >= t0 && e - 1 < tend) sums[s] = __ldcg(out + (e - 1));
     }
-    // empty segments: this tile's share of the segment index space
-    const int64_t ntiles = (n + kTile - 1) / kTile;
     for (int64_t s = tile * kThreads + tid; s < args.nseg; s += ntiles * kThreads)
       if (args.offsets[s + 1] == args.offsets[s]) sums[s] = T(0);
   }
@@ -375,19 +522,48 @@ __global__ void __launch_bounds__(kThreads) scan_kernel(const T *in, T *out,
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-template <class T, int MODE>
-int32_t run_scan(const T *in, T *out, const ScanArgs &a, void *ws, size_t ws_bytes, cudaStream_t s) {
+constexpr int kWsTile = kSub;   // workspace is sized for the smallest tile
+
+// Sub-tiles per tile; DESC_SCAN_SUB picks another compiled size.
+int scan_sub() {
+  static int sub = 0;
+  if (!sub) {
+    const char *e = getenv("DESC_SCAN_SUB");
+    const int v = e ? atoi(e) : 4;
+    sub = (v == 1 || v == 2 || v == 4) ? v : 4;
+  }
+  return sub;
+}
+
+template <class T, int MODE, int SUB>
+int32_t run_scan_t(const T *in, T *out, const ScanArgs &a, void *ws, size_t ws_bytes, cudaStream_t s) {
+  constexpr int kTile = kSub * SUB;
   const int64_t ntiles = (a.n + kTile - 1) / kTile;
   if (ntiles == 0) return DESC_OK;
   const size_t need = align256(sizeof(ScanWs)) + size_t(ntiles) * sizeof(TileState);
   if (!ws || ws_bytes < need) return DESC_ERR_WORKSPACE;
   if (ntiles >= (int64_t(1) << 31)) return DESC_ERR_UNSUPPORTED;
+  const int smem = SUB * kStageBytes;
+  static bool attr = false;
+  if (!attr) {
+    DESC_CUDA_TRY(cudaFuncSetAttribute(scan_kernel<T, MODE, SUB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    attr = true;
+  }
   DESC_CUDA_TRY(cudaMemsetAsync(ws, 0, need, s));
   ScanWs *w = static_cast<ScanWs *>(ws);
   TileState *st = reinterpret_cast<TileState *>(static_cast<char *>(ws) + align256(sizeof(ScanWs)));
-  scan_kernel<T, MODE><<<(unsigned)ntiles, kThreads, 0, s>>>(in, out, a, w, st);
+  scan_kernel<T, MODE, SUB><<<(unsigned)ntiles, kThreads + 32, smem, s>>>(in, out, a, w, st);
   DESC_CUDA_TRY(cudaGetLastError());
   return DESC_OK;
+}
+
+template <class T, int MODE>
+int32_t run_scan(const T *in, T *out, const ScanArgs &a, void *ws, size_t ws_bytes, cudaStream_t s) {
+  switch (scan_sub()) {
+    case 1: return run_scan_t<T, MODE, 1>(in, out, a, ws, ws_bytes, s);
+    case 2: return run_scan_t<T, MODE, 2>(in, out, a, ws, ws_bytes, s);
+    default: return run_scan_t<T, MODE, 4>(in, out, a, ws, ws_bytes, s);
+  }
 }
 
 }  // namespace
@@ -400,7 +576,7 @@ int32_t scan_status_take() {
 }
 
 size_t scan_contig_ws(int32_t /*dtype*/, int64_t n) {
-  const int64_t ntiles = (n + kTile - 1) / kTile;
+  const int64_t ntiles = (n + kWsTile - 1) / kWsTile;
   return align256(sizeof(ScanWs)) + size_t(ntiles) * sizeof(TileState);
 }
 
