@@ -261,6 +261,30 @@ int32_t desc_transpose(const desc_view *in_v, const desc_view *out_v, const desc
                        int32_t dtype, const void *in, size_t in_bytes, void *out, size_t out_bytes,
                        desc_stream_t stream);
 
+/* ---- Matrix multiplication ------------------------------------------------
+ * Section 5 benchmark "matrix multiplication": C = A B with FP32 A (M x K),
+ * FP32 B (K x N) and FP32 C (M x N, row-major, contiguous).  a_v / b_v are
+ * views of the buffers A and B whose lowered maps are 2-D, extents (M, K) and
+ * (K, N), without selects (NULL: row-major contiguous); a transposed operand
+ * is a TRANSPOSE view.  precision:
+ *   DESC_MM_FP32_SIMT  FP32 fused multiply-adds on the CUDA cores; needs unit
+ *                      stride along K for A and along N for B
+ *   DESC_MM_BF16       A and B rounded to BF16 (nearest even), one tcgen05
+ *                      product, FP32 accumulation in tensor memory
+ *   DESC_MM_SPLIT3     x = x0 + x1 + x2 with BF16 terms (x0 = bf16(x),
+ *                      x1 = bf16(x - x0), x2 = bf16(x - x0 - x1)); the six
+ *                      products A_i B_j with i + j <= 2, one FP32 accumulator
+ *   DESC_MM_SPLIT2     two terms, the three products with i + j <= 1
+ * The tensor-core forms first write the BF16 terms of A and of B transposed
+ * into the workspace (zero padded to 128 / 256 / 64 multiples of M / N / K).
+ * Relative Frobenius error against the FP64 product (N(0,1) data, K = 8192):
+ * SPLIT3 <= 1e-5, BF16 <= 1e-2.  C must not overlap A or B. */
+typedef enum { DESC_MM_FP32_SIMT = 0, DESC_MM_BF16 = 1, DESC_MM_SPLIT3 = 2, DESC_MM_SPLIT2 = 3 } desc_mm_precision;
+int32_t desc_matmul_workspace_size(int64_t M, int64_t N, int64_t K, int32_t precision, size_t *bytes);
+int32_t desc_matmul(const desc_view *a_v, const desc_view *b_v, int64_t M, int64_t N, int64_t K, const float *A,
+                    size_t a_bytes, const float *B, size_t b_bytes, float *C, size_t c_bytes, int32_t precision,
+                    void *ws, size_t ws_bytes, desc_stream_t stream);
+
 /* Per-device status word: waits for the stream, returns the first device
  * error recorded since the last call (DESC_OK if none) and clears it. */
 int32_t desc_stream_status(desc_stream_t stream);

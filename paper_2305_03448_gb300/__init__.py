@@ -22,6 +22,7 @@ LIB_PATH = os.path.join(HERE, "libdesc.so")
 GRID, BLOCK, WARP, THREAD = 0, 1, 2, 3
 X, Y, Z, LANE = 0, 1, 2, 3
 I32, F32 = 0, 1
+MM_FP32_SIMT, MM_BF16, MM_SPLIT3, MM_SPLIT2 = 0, 1, 2, 3
 KAHAN = 1
 DEBUG_STALL_TILE = 1 << 16
 
@@ -98,6 +99,9 @@ def _declare(L):
         "desc_transpose": (c_int32, [POINTER(View), POINTER(View), POINTER(Exec), c_int32, P, c_size_t, P,
                                      c_size_t, P]),
         "desc_stream_status": (c_int32, [P]),
+        "desc_matmul_workspace_size": (c_int32, [c_int64, c_int64, c_int64, c_int32, POINTER(c_size_t)]),
+        "desc_matmul": (c_int32, [POINTER(View), POINTER(View), c_int64, c_int64, c_int64, P, c_size_t, P, c_size_t,
+                                  P, c_size_t, c_int32, P, c_size_t, P]),
         "desc_scan_noalloc": (c_int32, [POINTER(View), POINTER(Exec), c_int32, c_int32, P, c_size_t, P, c_size_t,
                                         P]),
     }
@@ -257,6 +261,34 @@ def desc_transpose(x, in_shape, in_ops, out, out_shape, out_ops, grid=None, bloc
     _check(lib().desc_transpose(ctypes.byref(make_view(in_shape, in_ops)), ctypes.byref(make_view(out_shape, out_ops)),
                                 _ref(make_exec(grid, block)), _dtype_code(x), _ptr(x), x.numel() * 4, _ptr(out),
                                 out.numel() * 4, _stream(stream)), "desc_transpose")
+    return out
+
+
+def desc_matmul(A, B, precision, a_view=None, b_view=None, M=None, N=None, K=None, out=None, ws=None,
+                stream=None):
+    """C = A B (FP32).  A and B are device tensors; by default row-major
+    (M x K) and (K x N).  a_view / b_view: (base_shape, ops) views of the
+    buffers (lowering to 2-D maps), e.g. a transposed operand."""
+    import torch
+    L = lib()
+    if M is None:
+        M = A.shape[0] if a_view is None else None
+    if a_view is not None or b_view is not None:
+        if M is None or N is None or K is None:
+            raise DescError(1, "desc_matmul: M, N, K are needed with views")
+    else:
+        M, K = A.shape
+        N = B.shape[1]
+    av = make_view(*a_view) if a_view is not None else None
+    bv = make_view(*b_view) if b_view is not None else None
+    if out is None:
+        out = torch.empty(M, N, dtype=torch.float32, device=A.device)
+    if ws is None:
+        nb = c_size_t(0)
+        _check(L.desc_matmul_workspace_size(M, N, K, precision, ctypes.byref(nb)), "desc_matmul_workspace_size")
+        ws = _workspace(nb.value, A.device)
+    _check(L.desc_matmul(_ref(av), _ref(bv), M, N, K, _ptr(A), A.numel() * 4, _ptr(B), B.numel() * 4, _ptr(out),
+                         out.numel() * 4, precision, _ptr(ws), ws.numel(), _stream(stream)), "desc_matmul")
     return out
 
 

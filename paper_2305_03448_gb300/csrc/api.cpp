@@ -263,9 +263,82 @@ extern "C" int32_t desc_transpose(const desc_view *in_v, const desc_view *out_v,
                             Li.ndims, s);
 }
 
+// ---------------------------------------------------------------- matmul
+namespace {
+
+// Lowered 2-D operand map: extents (r, c), strides, offset.
+int32_t operand_map(const desc_view *v, int64_t R, int64_t Cc, int64_t *off, int64_t *sr, int64_t *sc,
+                    int64_t *elems) {
+  if (!v) {
+    *off = 0; *sr = Cc; *sc = 1; *elems = R * Cc;
+    return DESC_OK;
+  }
+  desc_lowered L;
+  const int32_t r = desc_lower_view(v, nullptr, &L);
+  if (r != DESC_OK) return r;
+  if (L.nsel != 0 || L.ndims != 2 || L.extent[0] != R || L.extent[1] != Cc) return DESC_ERR_SHAPE;
+  *off = L.offset; *sr = L.stride[0]; *sc = L.stride[1]; *elems = L.base_elems;
+  return DESC_OK;
+}
+
+int mm_planes(int32_t precision) {
+  switch (precision) {
+    case DESC_MM_BF16: return 1;
+    case DESC_MM_SPLIT2: return 2;
+    case DESC_MM_SPLIT3: return 3;
+    default: return 0;
+  }
+}
+
+}  // namespace
+
+extern "C" int32_t desc_matmul_workspace_size(int64_t M, int64_t N, int64_t K, int32_t precision,
+                                              size_t *bytes) {
+  if (!bytes || M < 0 || N < 0 || K < 0) return DESC_ERR_INVALID_ARG;
+  if (precision == DESC_MM_FP32_SIMT) { *bytes = 0; return DESC_OK; }
+  const int planes = mm_planes(precision);
+  if (!planes) return DESC_ERR_INVALID_ARG;
+  *bytes = mm_tc_ws(M, N, K, planes);
+  return DESC_OK;
+}
+
+extern "C" int32_t desc_matmul(const desc_view *a_v, const desc_view *b_v, int64_t M, int64_t N, int64_t K,
+                               const float *A, size_t a_bytes, const float *B, size_t b_bytes, float *C,
+                               size_t c_bytes, int32_t precision, void *ws, size_t ws_bytes, desc_stream_t s) {
+  if (M < 0 || N < 0 || K < 0) return DESC_ERR_INVALID_ARG;
+  if (precision != DESC_MM_FP32_SIMT && !mm_planes(precision)) return DESC_ERR_INVALID_ARG;
+  int64_t ao, asr, asc, ae, bo, bsr, bsc, be;
+  int32_t r;
+  if ((r = operand_map(a_v, M, K, &ao, &asr, &asc, &ae)) != DESC_OK) return r;
+  if ((r = operand_map(b_v, K, N, &bo, &bsr, &bsc, &be)) != DESC_OK) return r;
+  if (a_bytes != size_t(ae) * 4 || b_bytes != size_t(be) * 4 || c_bytes != size_t(M) * N * 4)
+    return DESC_ERR_SIZE_MISMATCH;
+  if (M == 0 || N == 0) return DESC_OK;
+  if ((r = check_device_ptr(C, 4)) != DESC_OK) return r;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(s);
+  if (K == 0) return cudaMemsetAsync(C, 0, c_bytes, st) == cudaSuccess ? DESC_OK : DESC_ERR_CUDA;
+  if ((r = check_device_ptr(A, 4)) != DESC_OK) return r;
+  if ((r = check_device_ptr(B, 4)) != DESC_OK) return r;
+  if (ranges_overlap(A, a_bytes, C, c_bytes) || ranges_overlap(B, b_bytes, C, c_bytes)) return DESC_ERR_OVERLAP;
+  if (precision == DESC_MM_FP32_SIMT) {
+    if (asc != 1 || bsc != 1 || asr < 0 || bsr < 0) return DESC_ERR_UNSUPPORTED;
+    return launch_sgemm(A + ao, B + bo, C, M, N, K, asr, bsr, N, s);
+  }
+  // products in increasing order of magnitude (the largest, A_0 B_0, last)
+  static const int pa3[6] = {2, 1, 0, 1, 0, 0}, pb3[6] = {0, 1, 2, 0, 1, 0};
+  static const int pa2[3] = {1, 0, 0}, pb2[3] = {0, 1, 0};
+  static const int pa1[1] = {0}, pb1[1] = {0};
+  const int planes = mm_planes(precision);
+  const int nprod = planes == 3 ? 6 : (planes == 2 ? 3 : 1);
+  const int *pa = planes == 3 ? pa3 : (planes == 2 ? pa2 : pa1);
+  const int *pb = planes == 3 ? pb3 : (planes == 2 ? pb2 : pb1);
+  return launch_mm_tc(A, ao, asr, asc, B, bo, bsr, bsc, C, M, N, K, planes, nprod, pa, pb, ws, ws_bytes, s);
+}
+
 // ---------------------------------------------------------------- status
 extern "C" int32_t desc_stream_status(desc_stream_t s) {
   if (cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(s)) != cudaSuccess) return DESC_ERR_CUDA;
   const int32_t a = scan_status_take();
-  return a;
+  const int32_t b = mm_status_take();
+  return a != DESC_OK ? a : b;
 }

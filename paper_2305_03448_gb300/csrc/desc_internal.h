@@ -50,6 +50,7 @@ int32_t check_device_ptr(const void *p, size_t align);
 
 // Device status words of the translation units that hold bounded waits.
 int32_t scan_status_take();   // k_scan.cu
+int32_t mm_status_take();     // k_mm_tc.cu
 
 // ----- launchers (k_*.cu) -------------------------------------------------
 // Reduce: contiguous segments [start + o*seg_stride, +len), o < nout.
@@ -86,5 +87,13 @@ int32_t launch_copy_affine(const void *in, int64_t ioff, const int64_t *istride,
 int32_t launch_transpose(const float *in, float *out, int64_t R, int64_t C, int64_t ld_in,
                          int64_t ld_out, int64_t batch, int64_t bs_in, int64_t bs_out,
                          desc_stream_t s);
+
+// Matmul: FP32 SIMT (k_mm_simt.cu) and tensor-core forms (k_mm_tc.cu).
+int32_t launch_sgemm(const float *A, const float *B, float *C, int64_t M, int64_t N, int64_t K, int64_t lda,
+                     int64_t ldb, int64_t ldc, desc_stream_t s);
+size_t mm_tc_ws(int64_t M, int64_t N, int64_t K, int planes);
+int32_t launch_mm_tc(const float *A, int64_t a_off, int64_t a_sr, int64_t a_sc, const float *B, int64_t b_off,
+                     int64_t b_sr, int64_t b_sc, float *C, int64_t M, int64_t N, int64_t K, int planes,
+                     int nprod, const int *pa, const int *pb, void *ws, size_t ws_bytes, desc_stream_t s);
 
 }  // namespace desc

@@ -1,0 +1,388 @@
+// Tensor-core matrix multiplication on sm_103a: tcgen05.mma with the
+// accumulator in tensor memory (TMEM), operands staged by TMA.
+//
+// C (M x N, FP32) = sum over the products (i, j) of A_i B_j, where A_i and
+// B_j are BF16 planes written by the split pass: A_i is M x K (K-major) and
+// B_j is stored transposed, N x K (K-major).  Plain BF16 has one product;
+// the 3-term split has six (i + j <= 2).  All products accumulate into one
+// FP32 accumulator in TMEM.
+//
+// Accuracy: every product's K range is split in two halves accumulated in
+// two TMEM accumulators (all 512 columns), added in FP32 by the epilogue, so
+// no accumulator sums more than half of the K' = products x K terms.
+//
+// One CTA computes a 128 x 256 tile of C (192 threads, 1 CTA per SM):
+//   warp 0, one lane   TMA producer: A and B K-blocks of 64 into a 4-stage
+//                      ring (128-byte swizzle), one mbarrier per stage
+//   warp 1, one lane   MMA issuer: 4 x tcgen05.mma (M128 N256 K16) per stage,
+//                      tcgen05.commit frees the stage; warp 1 also owns the
+//                      TMEM allocation (512 columns)
+//   warps 2..5         epilogue: tcgen05.ld 32 rows x 32 columns per warp and
+//                      step (warp w reads TMEM lanes 32 (w mod 4) ...), FP32 stores
+// Every wait is bounded: a waiter that gives up sets an abort flag in shared
+// memory and records DESC_ERR_DEVICE_TIMEOUT; the producer then waits, again
+// with a limit, for the copies it has in flight, and TMEM is always freed.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "k_common.cuh"
+
+namespace desc {
+
+__device__ int g_mm_status;
+
+namespace {
+
+constexpr int BM = 128, BN = 256, BK = 64, UK = 16;
+constexpr int kStages = 4;
+constexpr int kABytes = BM * BK * 2;             // 16 KB
+constexpr int kBBytes = BN * BK * 2;             // 32 KB
+constexpr int kStageBytes = kABytes + kBBytes;
+constexpr int kTmemCols = 512;                  // two 256-column accumulators
+constexpr int kMmThreads = 192;
+constexpr int kSmemBytes = kStages * kStageBytes + 1024 + 256;
+constexpr long long kWaitBudget = 1ll << 32;     // clock cycles, about two seconds
+
+struct Products {
+  int n;
+  int pa[8];
+  int pb[8];
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for the phase with the given parity.  false: gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (*abort) return false;
+    if (clock64() - t0 > kWaitBudget) {
+      *abort = 1;
+      atomicCAS(&g_mm_status, 0, (int)DESC_ERR_DEVICE_TIMEOUT);
+      return false;
+    }
+  }
+  return true;
+}
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *tm, uint64_t *bar, int c0, int c1,
+                                            int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];"
+      ::"r"(smem_u32(dst)), "l"(tm), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows
+// of 64 BF16 (128 B), 8-row core groups 1024 B apart.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFF) >> 4);     // start address
+  d |= (uint64_t)1 << 16;                               // leading byte offset (unused here)
+  d |= (uint64_t)(1024 >> 4) << 32;                     // stride byte offset
+  d |= (uint64_t)1 << 46;                               // descriptor version
+  d |= (uint64_t)2 << 61;                               // 128-byte swizzle
+  return d;
+}
+// Instruction descriptor (kind::f16): FP32 accumulator, BF16 A and B, both
+// K-major, N = BN, M = BM.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                            ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t *slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+// 32 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(kMmThreads, 1)
+    mm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                 float *__restrict__ C, int64_t M, int64_t N, int64_t ldc, int kblocks, Products prods) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                                          ~uintptr_t(1023));
+  unsigned char *sA = smem;
+  unsigned char *sB = smem + kStages * kABytes;
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + kStages * kStageBytes);
+  uint64_t *empty = full + kStages;
+  uint64_t *done = empty + kStages;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+  volatile int *abort = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t m0 = int64_t(blockIdx.y) * BM, n0 = int64_t(blockIdx.x) * BN;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(done, 1);
+    *abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) tmem_alloc(tmem_slot, kTmemCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const int total = kblocks * prods.n;
+
+  if (warp == 0) {
+    if (lane == 0) {                                   // ---- TMA producer
+      int issued = 0;
+      for (int it = 0; it < total; ++it) {
+        const int s = it % kStages;
+        const uint32_t ph = (it / kStages) & 1;
+        if (!mbar_wait(&empty[s], ph ^ 1, abort)) break;
+        const int p = it / kblocks, kb = it % kblocks;
+        mbar_expect_tx(&full[s], kStageBytes);
+        tma_load_3d(sA + s * kABytes, &tmA, &full[s], kb * BK, (int)m0, prods.pa[p]);
+        tma_load_3d(sB + s * kBBytes, &tmB, &full[s], kb * BK, (int)n0, prods.pb[p]);
+        ++issued;
+      }
+      if (*abort) {                                    // copies still in flight: wait, bounded
+        for (int it = std::max(0, issued - kStages); it < issued; ++it) {
+          const long long t0 = clock64();
+          while (!mbar_try_wait(&full[it % kStages], (it / kStages) & 1) && clock64() - t0 < kWaitBudget) {
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {                                   // ---- MMA issuer
+      const int half = kblocks / 2;                    // k-blocks [half, kblocks) go to accumulator 1
+      for (int it = 0; it < total; ++it) {
+        const int s = it % kStages;
+        const uint32_t ph = (it / kStages) & 1;
+        if (!mbar_wait(&full[s], ph, abort)) break;
+        tc_fence_after();
+        const int p = it / kblocks, kb = it % kblocks;
+        const int acc = (half > 0 && kb >= half) ? 1 : 0;
+        const bool first = p == 0 && kb == (acc ? half : 0);
+        const uint32_t d = tmem + (uint32_t)(acc * BN);
+        const uint32_t a0 = smem_u32(sA + s * kABytes), b0 = smem_u32(sB + s * kBBytes);
+#pragma unroll
+        for (int k = 0; k < BK / UK; ++k)
+          umma_bf16(d, sdesc(a0 + k * UK * 2), sdesc(b0 + k * UK * 2), (first && k == 0) ? 0u : 1u);
+        umma_commit(&empty[s]);                        // stage reusable once these MMAs finish
+      }
+      umma_commit(done);                               // accumulators complete
+    }
+  } else {                                             // ---- epilogue, warps 2..5
+    const int q = warp & 3;                            // TMEM lanes 32 q .. 32 q + 31
+    if (mbar_wait(done, 0, abort)) {
+      tc_fence_after();
+      const int64_t row = m0 + q * 32 + lane;
+      const bool vec = ((ldc & 3) == 0) && ((reinterpret_cast<uintptr_t>(C) & 15) == 0);
+      const bool two = kblocks / 2 > 0;
+#pragma unroll 1
+      for (int c = 0; c < BN / 32; ++c) {
+        uint32_t r[32];
+        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(c * 32), r);
+        if (two) {
+          uint32_t r1[32];
+          tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(BN + c * 32), r1);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) r[j] = __float_as_uint(__fadd_rn(__uint_as_float(r[j]), __uint_as_float(r1[j])));
+        }
+        const int64_t col = n0 + c * 32;
+        if (row < M) {
+          float *dst = C + row * ldc + col;
+          if (vec && col + 32 <= N) {
+#pragma unroll
+            for (int j = 0; j < 32; j += 4)
+              __stcs(reinterpret_cast<float4 *>(dst + j),
+                     make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]), __uint_as_float(r[j + 2]),
+                                 __uint_as_float(r[j + 3])));
+          } else {
+            for (int j = 0; j < 32; ++j)
+              if (col + j < N) dst[j] = __uint_as_float(r[j]);
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) tmem_dealloc(tmem, kTmemCols);
+}
+
+// ---- split pass: FP32 source (any 2-D strides) -> P BF16 planes, zero padded
+// Output plane p is R x Kc row-major (R rows padded to Rp); element (r, c) of
+// the logical source is src[off + r * sr + c * sc].  Planes: p = 0 holds
+// bf16(x), p = 1 bf16(x - x0), p = 2 bf16(x - x0 - x1) (FP32 differences).
+constexpr int kTT = 64;
+
+__global__ void __launch_bounds__(256) split_planes_kernel(const float *__restrict__ src, int64_t off, int64_t sr,
+                                                           int64_t sc, int64_t R, int64_t Cc, int64_t Rp,
+                                                           int64_t Cp, int planes,
+                                                           __nv_bfloat16 *__restrict__ dst) {
+  __shared__ float tile[kTT][kTT + 1];
+  const int tid = threadIdx.x;
+  const int64_t r0 = int64_t(blockIdx.y) * kTT, c0 = int64_t(blockIdx.x) * kTT;
+  const bool rows_contig = (sr == 1 && sc != 1);        // read along r for coalescing
+#pragma unroll 4
+  for (int i = 0; i < kTT * kTT / 256; ++i) {
+    const int e = i * 256 + tid;
+    const int lr = rows_contig ? (e % kTT) : (e / kTT);
+    const int lc = rows_contig ? (e / kTT) : (e % kTT);
+    const int64_t r = r0 + lr, c = c0 + lc;
+    tile[lr][lc] = (r < R && c < Cc) ? src[off + r * sr + c * sc] : 0.f;
+  }
+  __syncthreads();
+  // each thread writes pairs of columns: (lr, 2 lc2 .. 2 lc2 + 1)
+#pragma unroll 4
+  for (int i = 0; i < kTT * kTT / 2 / 256; ++i) {
+    const int e = i * 256 + tid;
+    const int lr = e / (kTT / 2), lc = 2 * (e % (kTT / 2));
+    const int64_t r = r0 + lr, c = c0 + lc;
+    if (r >= Rp || c >= Cp) continue;
+    float x[2] = {tile[lr][lc], tile[lr][lc + 1]};
+    __nv_bfloat16 h[3][2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const __nv_bfloat16 a0 = __float2bfloat16_rn(x[k]);
+      const float r1 = __fsub_rn(x[k], __bfloat162float(a0));
+      const __nv_bfloat16 a1 = __float2bfloat16_rn(r1);
+      const float r2 = __fsub_rn(r1, __bfloat162float(a1));
+      h[0][k] = a0;
+      h[1][k] = a1;
+      h[2][k] = __float2bfloat16_rn(r2);
+    }
+    for (int p = 0; p < planes; ++p) {
+      __nv_bfloat162 v;
+      v.x = h[p][0];
+      v.y = h[p][1];
+      *reinterpret_cast<__nv_bfloat162 *>(dst + (int64_t(p) * Rp + r) * Cp + c) = v;
+    }
+  }
+}
+
+// ---- tensor maps -----------------------------------------------------------
+using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encoder() {
+  static EncodeTiled fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiled>(p);
+  });
+  return fn;
+}
+
+// [planes][rows][cols] BF16, box = box_rows x 64 columns x 1 plane.
+bool make_map(CUtensorMap *m, const void *base, int64_t planes, int64_t rows, int64_t cols, int box_rows) {
+  EncodeTiled enc = encoder();
+  if (!enc) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)cols, (cuuint64_t)rows, (cuuint64_t)planes};
+  cuuint64_t strides[2] = {(cuuint64_t)(cols * 2), (cuuint64_t)(rows * cols * 2)};
+  cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(base), dims, strides, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace
+
+int32_t mm_status_take() {
+  int v = 0, z = 0;
+  if (cudaMemcpyFromSymbol(&v, g_mm_status, sizeof(int)) != cudaSuccess) return DESC_ERR_CUDA;
+  if (v != 0 && cudaMemcpyToSymbol(g_mm_status, &z, sizeof(int)) != cudaSuccess) return DESC_ERR_CUDA;
+  return v;
+}
+
+// Planes needed by a precision: 1 (BF16), 2 (2-term split), 3 (3-term split).
+size_t mm_tc_ws(int64_t M, int64_t N, int64_t K, int planes) {
+  const int64_t Mp = round_up(M, BM), Np = round_up(N, BN), Kp = round_up(K, BK);
+  return align256(size_t(planes) * Mp * Kp * 2) + align256(size_t(planes) * Np * Kp * 2);
+}
+
+int32_t launch_mm_tc(const float *A, int64_t a_off, int64_t a_sr, int64_t a_sc, const float *B, int64_t b_off,
+                     int64_t b_sr, int64_t b_sc, float *C, int64_t M, int64_t N, int64_t K, int planes,
+                     int nprod, const int *pa, const int *pb, void *ws, size_t ws_bytes, desc_stream_t st) {
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(st);
+  const int64_t Mp = round_up(M, BM), Np = round_up(N, BN), Kp = round_up(K, BK);
+  if (!ws || ws_bytes < mm_tc_ws(M, N, K, planes)) return DESC_ERR_WORKSPACE;
+  if (Mp / BM > 65535 || Np / BN > (int64_t(1) << 30) || Kp > (int64_t(1) << 30)) return DESC_ERR_UNSUPPORTED;
+  __nv_bfloat16 *pA = static_cast<__nv_bfloat16 *>(ws);
+  __nv_bfloat16 *pB = reinterpret_cast<__nv_bfloat16 *>(static_cast<char *>(ws) +
+                                                         align256(size_t(planes) * Mp * Kp * 2));
+  // A (M x K) -> planes [P][Mp][Kp];  B (K x N) -> transposed planes [P][Np][Kp]
+  split_planes_kernel<<<dim3((unsigned)((Kp + kTT - 1) / kTT), (unsigned)((Mp + kTT - 1) / kTT)), 256, 0, s>>>(
+      A, a_off, a_sr, a_sc, M, K, Mp, Kp, planes, pA);
+  split_planes_kernel<<<dim3((unsigned)((Kp + kTT - 1) / kTT), (unsigned)((Np + kTT - 1) / kTT)), 256, 0, s>>>(
+      B, b_off, b_sc, b_sr, N, K, Np, Kp, planes, pB);
+  DESC_CUDA_TRY(cudaGetLastError());
+  CUtensorMap tmA, tmB;
+  if (!make_map(&tmA, pA, planes, Mp, Kp, BM) || !make_map(&tmB, pB, planes, Np, Kp, BN)) return DESC_ERR_CUDA;
+  Products pr{};
+  pr.n = nprod;
+  for (int i = 0; i < nprod; ++i) {
+    pr.pa[i] = pa[i];
+    pr.pb[i] = pb[i];
+  }
+  static bool attr = false;
+  if (!attr) {
+    DESC_CUDA_TRY(cudaFuncSetAttribute(mm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
+    attr = true;
+  }
+  mm_tc_kernel<<<dim3((unsigned)(Np / BN), (unsigned)(Mp / BM)), kMmThreads, kSmemBytes, s>>>(
+      tmA, tmB, C, M, N, N, (int)(Kp / BK), pr);
+  DESC_CUDA_TRY(cudaGetLastError());
+  return DESC_OK;
+}
+
+}  // namespace desc

@@ -1,0 +1,111 @@
+"""GPU parity of desc_matmul against the oracle (FP64 products).
+
+Two kinds of check per tensor-core form: against the exact FP64 product
+(the stated error bounds: SPLIT3 <= 1e-5, BF16 <= 1e-2 relative Frobenius),
+and against the FP64 product of the same BF16 terms (oracle's bit-level
+rounding and split), which isolates the tensor-core arithmetic: only FP32
+accumulation error may remain there."""
+import numpy as np
+import pytest
+import torch
+
+import paper_2305_03448_gb300 as D
+import synth
+from oracle import matmul as OM
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib(desc_lib):
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return desc_lib
+
+
+def mats(M, N, K, seed):
+    A = synth.normal_f32(M * K, seed=seed, stream=1).reshape(M, K)
+    B = synth.normal_f32(K * N, seed=seed, stream=2).reshape(K, N)
+    return A, B
+
+
+SHAPES = [(128, 256, 64), (256, 512, 128), (100, 300, 70), (1, 1, 1), (257, 513, 129), (384, 256, 1024)]
+
+
+@pytest.mark.parametrize("M,N,K", SHAPES)
+def test_simt_fp32(M, N, K):
+    A, B = mats(M, N, K, seed=M + N + K)
+    C = D.desc_matmul(A.cuda(), B.cuda(), D.MM_FP32_SIMT).cpu().numpy()
+    ref = OM.matmul_f64(A.numpy(), B.numpy())
+    assert OM.rel_frobenius(C, ref) <= 1e-6
+
+
+@pytest.mark.parametrize("M,N,K", SHAPES)
+def test_bf16_tensor_cores(M, N, K):
+    A, B = mats(M, N, K, seed=M * 3 + N + K)
+    C = D.desc_matmul(A.cuda(), B.cuda(), D.MM_BF16).cpu().numpy()
+    a, b = A.numpy(), B.numpy()
+    emul = OM.matmul_f64(OM.bf16_rne(a), OM.bf16_rne(b))     # same BF16 inputs, exact products
+    assert OM.rel_frobenius(C, emul) <= 2e-6
+    assert OM.rel_frobenius(C, OM.matmul_f64(a, b)) <= 1e-2
+
+
+@pytest.mark.parametrize("M,N,K", SHAPES)
+def test_split3_tensor_cores(M, N, K):
+    A, B = mats(M, N, K, seed=M + N * 5 + K)
+    C = D.desc_matmul(A.cuda(), B.cuda(), D.MM_SPLIT3).cpu().numpy()
+    a, b = A.numpy(), B.numpy()
+    assert OM.rel_frobenius(C, OM.split3_product_f64(a, b)) <= 2e-6
+    assert OM.rel_frobenius(C, OM.matmul_f64(a, b)) <= 1e-5
+
+
+def test_split2_between_bf16_and_split3():
+    M, N, K = 256, 256, 512
+    A, B = mats(M, N, K, seed=9)
+    ref = OM.matmul_f64(A.numpy(), B.numpy())
+    e = {p: OM.rel_frobenius(D.desc_matmul(A.cuda(), B.cuda(), p).cpu().numpy(), ref)
+         for p in (D.MM_BF16, D.MM_SPLIT2, D.MM_SPLIT3)}
+    assert e[D.MM_SPLIT3] < e[D.MM_SPLIT2] < e[D.MM_BF16]
+    assert e[D.MM_SPLIT2] <= 1e-4
+
+
+def test_closed_forms_on_tensor_cores():
+    # identity: A = I gives B exactly when B holds BF16 values (one term), and
+    # within the split's representation for general B
+    K, N = 256, 512
+    B = synth.normal_f32(K * N, seed=3).reshape(K, N)
+    Bb = torch.from_numpy(OM.bf16_rne(B.numpy()))
+    eye = torch.eye(K, dtype=torch.float32)
+    C = D.desc_matmul(eye.cuda(), Bb.cuda(), D.MM_BF16).cpu()
+    assert torch.equal(C, Bb)
+    C3 = D.desc_matmul(eye.cuda(), B.cuda(), D.MM_SPLIT3).cpu().numpy()
+    assert np.max(np.abs(C3 - B.numpy())) <= 2.0 ** -23 * np.max(np.abs(B.numpy()))
+    ones = torch.ones(128, 300)
+    C = D.desc_matmul(ones.cuda(), torch.ones(300, 256).cuda(), D.MM_BF16).cpu()
+    assert torch.all(C == 300.0)
+
+
+def test_transposed_operand_views():
+    M, N, K = 200, 300, 160
+    A, B = mats(M, N, K, seed=4)
+    At = A.t().contiguous()                     # buffer holds A^T (K x M)
+    ref = OM.matmul_f64(A.numpy(), B.numpy())
+    for p in (D.MM_BF16, D.MM_SPLIT3):
+        C = D.desc_matmul(At.cuda(), B.cuda(), p, a_view=([K, M], [("transpose", 0)]), b_view=([K, N], []),
+                          M=M, N=N, K=K).cpu().numpy()
+        assert OM.rel_frobenius(C, ref) <= (1e-5 if p == D.MM_SPLIT3 else 1e-2)
+    with pytest.raises(D.DescError) as e:     # the CUDA-core form needs unit stride along K
+        D.desc_matmul(At.cuda(), B.cuda(), D.MM_FP32_SIMT, a_view=([K, M], [("transpose", 0)]),
+                      b_view=([K, N], []), M=M, N=N, K=K)
+    assert e.value.status == 7
+
+
+def test_rejections():
+    A, B = mats(64, 64, 64, seed=5)
+    with pytest.raises(D.DescError) as e:       # host pointer
+        D.desc_matmul(A, B.cuda(), D.MM_BF16, out=torch.empty(64, 64, device="cuda"))
+    assert e.value.status == 4
+    Ad = A.cuda()
+    with pytest.raises(D.DescError) as e:       # C overlapping A
+        D.desc_matmul(Ad, B.cuda(), D.MM_FP32_SIMT, out=Ad)
+    assert e.value.status == 3
+    assert D.desc_stream_status() == 0
