@@ -235,9 +235,86 @@ def run_ours(args, rank, world, local_rank):
             "ops": per_op, "roofline": roofline, "gpu_launches": K * len(ops), "e2e": e2e}
     if clk:
         line["clocks"] = {k: clk[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")}
+    if not args.no_extras and not args.small:
+        line["matmul"] = run_matmul(torch, D, dev, stream, pk)
+        line["segmented"] = run_segmented(torch, D, synth, dev, stream)
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(sz, only)
     return line
+
+
+def _time(torch, stream, fn, reps):
+    fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def run_matmul(torch, D, dev, stream, pk, n=8192):
+    """C = A B at M = N = K = 8192, FP32 N(0,1) inputs: time of one call
+    (split pass included), effective TFLOP/s (2 n^3 / t), tensor TFLOP/s
+    (products x 2 n^3 / t) against the dense BF16 peak, and the relative
+    Frobenius error on 64 sampled rows against an FP64 product (torch, CPU)."""
+    import ctypes
+    import synth
+    A = synth.normal_f32(n * n, seed=1, stream=1, device=dev).reshape(n, n)
+    B = synth.normal_f32(n * n, seed=1, stream=2, device=dev).reshape(n, n)
+    rows = torch.arange(0, n, n // 64)
+    ref = (A[rows].double().cpu() @ B.double().cpu())
+    C = torch.empty(n, n, device=dev)
+    out = {"shape": [n, n, n], "peak_bf16_tflops": pk["bf16_tflops"],
+           "peak_source": f"bf16_tflops (burst, of {pk['source']})"}
+    for name, p, nprod, reps in (("split3", D.MM_SPLIT3, 6, 5), ("bf16", D.MM_BF16, 1, 10),
+                                 ("fp32_simt", D.MM_FP32_SIMT, 1, 2)):
+        nb = ctypes.c_size_t(0)
+        D.lib().desc_matmul_workspace_size(n, n, n, p, ctypes.byref(nb))
+        ws = torch.empty(max(nb.value, 1), dtype=torch.uint8, device=dev)
+        ms = _time(torch, stream, lambda: D.desc_matmul(A, B, p, out=C, ws=ws, stream=stream), reps)
+        got = C[rows].double().cpu()
+        err = float(torch.linalg.norm(got - ref) / torch.linalg.norm(ref))
+        eff = 2 * n ** 3 / (ms * 1e-3) / 1e12
+        r = {"ms": round(ms, 4), "effective_tflops": round(eff, 1), "rel_frobenius_err": float(f"{err:.3e}")}
+        if p != D.MM_FP32_SIMT:
+            r["tensor_tflops"] = round(nprod * eff, 1)
+            r["frac_of_bf16_peak"] = round(nprod * eff / pk["bf16_tflops"], 4)
+        out[name] = r
+        del ws
+    if D.desc_stream_status(stream) != 0:
+        raise RuntimeError("device status after matmul")
+    return out
+
+
+def run_segmented(torch, D, synth, dev, stream, nseg=20000):
+    """20,000 FP32 segments, lengths log-uniform in [1, 2^20]: every segment
+    reduced and inclusive-scanned.  One graph-captured persistent launch vs.
+    the same call launched directly vs. one scan + one reduce launch per
+    segment.  GB/s counts 8 B per element + 8 B of offsets + 4 B per sum."""
+    L = synth.loguniform_lengths(nseg, seed=7, device=dev)
+    off = synth.offsets_from_lengths(L)
+    total = int(off[-1])
+    x = synth.uniform_grid(total, seed=8, device=dev)
+    out = torch.empty_like(x)
+    sums = torch.empty(nseg, device=dev)
+    ws = D.desc_segmented_workspace(nseg, total, dev)
+    g = D.SegmentedGraph(x, off, out, sums, ws)
+    t_graph = _time(torch, stream, lambda: g.launch(stream), 10)
+    t_direct = _time(torch, stream, lambda: D.desc_segmented_reduce_scan(x, off, out=out, sums=sums, ws=ws,
+                                                                        stream=stream), 10)
+    h = off.cpu().tolist()
+    t_per = _time(torch, stream, lambda: D.desc_segmented_reduce_scan_per_segment(x, h, out=out, sums=sums, ws=ws,
+                                                                                 stream=stream), 1)
+    g.close()
+    nbytes = 8 * total + 8 * (nseg + 1) + 4 * nseg
+    if D.desc_stream_status(stream) != 0:
+        raise RuntimeError("device status after segmented")
+    return {"segments": nseg, "elements": total, "graph_ms": round(t_graph, 4), "direct_ms": round(t_direct, 4),
+            "per_segment_ms": round(t_per, 3), "graph_GB/s": round(nbytes / (t_graph * 1e-3) / 1e9, 1),
+            "speedup_vs_per_segment": round(t_per / t_graph, 1)}
 
 
 def run_e2e(args, torch, dev, stream, ops, nb, Rn, Sn, T, op_reduce, op_scan, op_transpose, world):
@@ -381,6 +458,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--no-extras", action="store_true", help="skip the matmul and segmented measurements")
     args = ap.parse_args()
     if args.warmup < 3 and not args.small:
         args.warmup = 3

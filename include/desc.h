@@ -285,6 +285,43 @@ int32_t desc_matmul(const desc_view *a_v, const desc_view *b_v, int64_t M, int64
                     size_t a_bytes, const float *B, size_t b_bytes, float *C, size_t c_bytes, int32_t precision,
                     void *ws, size_t ws_bytes, desc_stream_t stream);
 
+/* ---- Segmented reduce + scan (batched) -------------------------------------
+ * Many independent segments in one launch: segment s is in[offsets[s] ..
+ * offsets[s+1]) of a contiguous array of `total` elements.  For every segment
+ * scan_out gets its inclusive prefix sums (the Section 5 scan per segment) and
+ * sums_out[s] its total (the reduce; 0 for an empty segment), both from one
+ * read of the input by the look-back scan with segment heads taken from the
+ * offsets.  d_offsets: device int64 array of nseg + 1 entries, nondecreasing,
+ * offsets[0] = 0, offsets[nseg] = total (checked when flags has
+ * DESC_CHECK_OFFSETS, which copies them to the host; unchecked bad offsets
+ * give wrong values but no out-of-bounds access).  dtype DESC_I32 (wrap-around,
+ * bit-exact) or DESC_F32 (per-element error within 1e-5 * sum_{q<=p} |x_q|
+ * of the segment).  in == scan_out is allowed. */
+#define DESC_CHECK_OFFSETS (1 << 17)
+int32_t desc_segmented_workspace_size(int64_t nseg, int64_t total, size_t *bytes);
+int32_t desc_segmented_reduce_scan(const int64_t *d_offsets, int64_t nseg, int64_t total, int32_t dtype,
+                                   const void *in, void *scan_out, void *sums_out, int32_t flags, void *ws,
+                                   size_t ws_bytes, desc_stream_t stream);
+
+/* The same work as a CUDA graph, captured once and replayed: create captures
+ * the launch sequence of desc_segmented_reduce_scan for fixed pointers and
+ * sizes (the offsets are checked once, here); launch replays it on a stream;
+ * destroy frees the graph.  The handle owns host-side graph objects only. */
+typedef struct desc_graph_st *desc_graph_t;
+int32_t desc_segmented_graph_create(const int64_t *d_offsets, int64_t nseg, int64_t total, int32_t dtype,
+                                    const void *in, void *scan_out, void *sums_out, void *ws, size_t ws_bytes,
+                                    desc_graph_t *graph);
+int32_t desc_graph_launch(desc_graph_t graph, desc_stream_t stream);
+int32_t desc_graph_destroy(desc_graph_t graph);
+
+/* Baseline for the batched form: one scan launch and one reduce launch per
+ * segment (h_offsets on the host), through desc_scan and desc_reduce.  Same
+ * results; exists to measure what batching saves.  ws: at least
+ * desc_segmented_workspace_size bytes. */
+int32_t desc_segmented_reduce_scan_per_segment(const int64_t *h_offsets, int64_t nseg, int32_t dtype,
+                                               const void *in, void *scan_out, void *sums_out, void *ws,
+                                               size_t ws_bytes, desc_stream_t stream);
+
 /* Per-device status word: waits for the stream, returns the first device
  * error recorded since the last call (DESC_OK if none) and clears it. */
 int32_t desc_stream_status(desc_stream_t stream);

@@ -25,6 +25,7 @@ I32, F32 = 0, 1
 MM_FP32_SIMT, MM_BF16, MM_SPLIT3, MM_SPLIT2 = 0, 1, 2, 3
 KAHAN = 1
 DEBUG_STALL_TILE = 1 << 16
+CHECK_OFFSETS = 1 << 17
 
 STATUS = {0: "DESC_OK", 1: "DESC_ERR_INVALID_ARG", 2: "DESC_ERR_SHAPE", 3: "DESC_ERR_OVERLAP",
           4: "DESC_ERR_HOST_POINTER", 5: "DESC_ERR_SIZE_MISMATCH", 6: "DESC_ERR_ALIGNMENT",
@@ -102,6 +103,14 @@ def _declare(L):
         "desc_matmul_workspace_size": (c_int32, [c_int64, c_int64, c_int64, c_int32, POINTER(c_size_t)]),
         "desc_matmul": (c_int32, [POINTER(View), POINTER(View), c_int64, c_int64, c_int64, P, c_size_t, P, c_size_t,
                                   P, c_size_t, c_int32, P, c_size_t, P]),
+        "desc_segmented_workspace_size": (c_int32, [c_int64, c_int64, POINTER(c_size_t)]),
+        "desc_segmented_reduce_scan": (c_int32, [P, c_int64, c_int64, c_int32, P, P, P, c_int32, P, c_size_t, P]),
+        "desc_segmented_graph_create": (c_int32, [P, c_int64, c_int64, c_int32, P, P, P, P, c_size_t,
+                                                  POINTER(c_void_p)]),
+        "desc_graph_launch": (c_int32, [c_void_p, P]),
+        "desc_graph_destroy": (c_int32, [c_void_p]),
+        "desc_segmented_reduce_scan_per_segment": (c_int32, [POINTER(c_int64), c_int64, c_int32, P, P, P, P,
+                                                             c_size_t, P]),
         "desc_scan_noalloc": (c_int32, [POINTER(View), POINTER(Exec), c_int32, c_int32, P, c_size_t, P, c_size_t,
                                         P]),
     }
@@ -290,6 +299,73 @@ def desc_matmul(A, B, precision, a_view=None, b_view=None, M=None, N=None, K=Non
     _check(L.desc_matmul(_ref(av), _ref(bv), M, N, K, _ptr(A), A.numel() * 4, _ptr(B), B.numel() * 4, _ptr(out),
                          out.numel() * 4, precision, _ptr(ws), ws.numel(), _stream(stream)), "desc_matmul")
     return out
+
+
+def desc_segmented_workspace(nseg, total, device):
+    nb = c_size_t(0)
+    _check(lib().desc_segmented_workspace_size(nseg, total, ctypes.byref(nb)), "desc_segmented_workspace_size")
+    return _workspace(nb.value, device)
+
+
+def desc_segmented_reduce_scan(x, offsets, out=None, sums=None, ws=None, flags=0, stream=None):
+    """Per-segment inclusive scans and totals of x (segments from the device
+    int64 CSR offsets) in one launch.  Returns (out, sums)."""
+    import torch
+    nseg = offsets.numel() - 1
+    if out is None:
+        out = torch.empty_like(x)
+    if sums is None:
+        sums = torch.empty(nseg, dtype=x.dtype, device=x.device)
+    if ws is None:
+        ws = desc_segmented_workspace(nseg, x.numel(), x.device)
+    _check(lib().desc_segmented_reduce_scan(_ptr(offsets), nseg, x.numel(), _dtype_code(x), _ptr(x), _ptr(out),
+                                            _ptr(sums), flags, _ptr(ws), ws.numel(), _stream(stream)),
+           "desc_segmented_reduce_scan")
+    return out, sums
+
+
+class SegmentedGraph:
+    """desc_segmented_reduce_scan captured once as a CUDA graph and replayed."""
+
+    def __init__(self, x, offsets, out, sums, ws=None):
+        self.keep = (x, offsets, out, sums)
+        self.ws = ws if ws is not None else desc_segmented_workspace(offsets.numel() - 1, x.numel(), x.device)
+        h = c_void_p(0)
+        _check(lib().desc_segmented_graph_create(_ptr(offsets), offsets.numel() - 1, x.numel(), _dtype_code(x),
+                                                 _ptr(x), _ptr(out), _ptr(sums), _ptr(self.ws), self.ws.numel(),
+                                                 ctypes.byref(h)), "desc_segmented_graph_create")
+        self.handle = h
+
+    def launch(self, stream=None):
+        _check(lib().desc_graph_launch(self.handle, _stream(stream)), "desc_graph_launch")
+
+    def close(self):
+        if self.handle:
+            lib().desc_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def desc_segmented_reduce_scan_per_segment(x, h_offsets, out=None, sums=None, ws=None, stream=None):
+    """Baseline: one scan and one reduce launch per segment (host offsets)."""
+    import torch
+    nseg = len(h_offsets) - 1
+    if out is None:
+        out = torch.empty_like(x)
+    if sums is None:
+        sums = torch.empty(nseg, dtype=x.dtype, device=x.device)
+    if ws is None:
+        ws = desc_segmented_workspace(nseg, x.numel(), x.device)
+    arr = (c_int64 * len(h_offsets))(*[int(v) for v in h_offsets])
+    _check(lib().desc_segmented_reduce_scan_per_segment(arr, nseg, _dtype_code(x), _ptr(x), _ptr(out), _ptr(sums),
+                                                        _ptr(ws), ws.numel(), _stream(stream)),
+           "desc_segmented_reduce_scan_per_segment")
+    return out, sums
 
 
 def desc_scan_noalloc(x, base_shape, ops, seg_level, grid=None, block=None, out=None, stream=None):

@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cstdint>
 #include <cstdlib>
+#include <cstring>
 #include <vector>
 
 #include "desc_internal.h"
@@ -333,6 +334,149 @@ extern "C" int32_t desc_matmul(const desc_view *a_v, const desc_view *b_v, int64
   const int *pa = planes == 3 ? pa3 : (planes == 2 ? pa2 : pa1);
   const int *pb = planes == 3 ? pb3 : (planes == 2 ? pb2 : pb1);
   return launch_mm_tc(A, ao, asr, asc, B, bo, bsr, bsc, C, M, N, K, planes, nprod, pa, pb, ws, ws_bytes, s);
+}
+
+// ---------------------------------------------------------------- segmented
+namespace {
+
+int32_t check_offsets_host(const int64_t *h, int64_t nseg, int64_t total) {
+  if (h[0] != 0 || h[nseg] != total) return DESC_ERR_SHAPE;
+  for (int64_t i = 0; i < nseg; ++i)
+    if (h[i + 1] < h[i]) return DESC_ERR_SHAPE;
+  return DESC_OK;
+}
+
+int32_t check_offsets_device(const int64_t *d, int64_t nseg, int64_t total) {
+  std::vector<int64_t> h(size_t(nseg) + 1);
+  if (cudaMemcpy(h.data(), d, h.size() * sizeof(int64_t), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return DESC_ERR_CUDA;
+  return check_offsets_host(h.data(), nseg, total);
+}
+
+int32_t segmented_checks(const int64_t *d_offsets, int64_t nseg, int64_t total, int32_t dtype, const void *in,
+                         void *scan_out, void *sums_out) {
+  if (nseg < 0 || total < 0 || !dtype_size(dtype)) return DESC_ERR_INVALID_ARG;
+  int32_t r;
+  if ((r = check_device_ptr(d_offsets, 8)) != DESC_OK) return r;
+  if (nseg > 0 && (r = check_device_ptr(sums_out, 4)) != DESC_OK) return r;
+  if (total > 0) {
+    if ((r = check_device_ptr(in, 4)) != DESC_OK) return r;
+    if ((r = check_device_ptr(scan_out, 4)) != DESC_OK) return r;
+  }
+  const size_t tb = size_t(total) * 4, sb = size_t(nseg) * 4;
+  if (in != scan_out && ranges_overlap(in, tb, scan_out, tb)) return DESC_ERR_OVERLAP;
+  if (ranges_overlap(sums_out, sb, scan_out, tb) || ranges_overlap(sums_out, sb, in, tb) ||
+      ranges_overlap(d_offsets, size_t(nseg + 1) * 8, scan_out, tb) ||
+      ranges_overlap(d_offsets, size_t(nseg + 1) * 8, sums_out, sb))
+    return DESC_ERR_OVERLAP;
+  return DESC_OK;
+}
+
+}  // namespace
+
+struct desc_graph_st {
+  cudaGraph_t graph;
+  cudaGraphExec_t exec;
+};
+
+extern "C" int32_t desc_segmented_workspace_size(int64_t nseg, int64_t total, size_t *bytes) {
+  if (!bytes || nseg < 0 || total < 0) return DESC_ERR_INVALID_ARG;
+  *bytes = scan_csr_ws(total);
+  return DESC_OK;
+}
+
+extern "C" int32_t desc_segmented_reduce_scan(const int64_t *d_offsets, int64_t nseg, int64_t total,
+                                              int32_t dtype, const void *in, void *scan_out, void *sums_out,
+                                              int32_t flags, void *ws, size_t ws_bytes, desc_stream_t s) {
+  if (flags & ~(DESC_CHECK_OFFSETS | DESC_DEBUG_STALL_TILE)) return DESC_ERR_INVALID_ARG;
+  int32_t r = segmented_checks(d_offsets, nseg, total, dtype, in, scan_out, sums_out);
+  if (r != DESC_OK) return r;
+  if (nseg == 0) return total == 0 ? DESC_OK : DESC_ERR_SHAPE;
+  if ((flags & DESC_CHECK_OFFSETS) && (r = check_offsets_device(d_offsets, nseg, total)) != DESC_OK) return r;
+  if (total == 0)     // every segment is empty
+    return cudaMemsetAsync(sums_out, 0, size_t(nseg) * 4, reinterpret_cast<cudaStream_t>(s)) == cudaSuccess
+               ? DESC_OK : DESC_ERR_CUDA;
+  return launch_scan_csr(dtype, in, scan_out, total, d_offsets, nseg, sums_out, flags & DESC_DEBUG_STALL_TILE, ws,
+                         ws_bytes, s);
+}
+
+extern "C" int32_t desc_segmented_graph_create(const int64_t *d_offsets, int64_t nseg, int64_t total,
+                                               int32_t dtype, const void *in, void *scan_out, void *sums_out,
+                                               void *ws, size_t ws_bytes, desc_graph_t *graph) {
+  if (!graph) return DESC_ERR_INVALID_ARG;
+  int32_t r = segmented_checks(d_offsets, nseg, total, dtype, in, scan_out, sums_out);
+  if (r != DESC_OK) return r;
+  if (nseg == 0) return DESC_ERR_SHAPE;
+  if ((r = check_offsets_device(d_offsets, nseg, total)) != DESC_OK) return r;
+  if (total > 0 && (!ws || ws_bytes < scan_csr_ws(total))) return DESC_ERR_WORKSPACE;
+  cudaStream_t cs;
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return DESC_ERR_CUDA;
+  desc_graph_st *g = new desc_graph_st{nullptr, nullptr};
+  r = DESC_OK;
+  if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) r = DESC_ERR_CUDA;
+  if (r == DESC_OK) {
+    const int32_t lr = desc_segmented_reduce_scan(d_offsets, nseg, total, dtype, in, scan_out, sums_out, 0, ws,
+                                                  ws_bytes, reinterpret_cast<desc_stream_t>(cs));
+    const cudaError_t e = cudaStreamEndCapture(cs, &g->graph);
+    if (lr != DESC_OK) r = lr;
+    else if (e != cudaSuccess) r = DESC_ERR_CUDA;
+  }
+  if (r == DESC_OK && cudaGraphInstantiate(&g->exec, g->graph, 0) != cudaSuccess) r = DESC_ERR_CUDA;
+  cudaStreamDestroy(cs);
+  if (r != DESC_OK) {
+    (void)cudaGetLastError();
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    delete g;
+    return r;
+  }
+  *graph = g;
+  return DESC_OK;
+}
+
+extern "C" int32_t desc_graph_launch(desc_graph_t g, desc_stream_t s) {
+  if (!g || !g->exec) return DESC_ERR_INVALID_ARG;
+  return cudaGraphLaunch(g->exec, reinterpret_cast<cudaStream_t>(s)) == cudaSuccess ? DESC_OK : DESC_ERR_CUDA;
+}
+
+extern "C" int32_t desc_graph_destroy(desc_graph_t g) {
+  if (!g) return DESC_ERR_INVALID_ARG;
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  delete g;
+  return DESC_OK;
+}
+
+extern "C" int32_t desc_segmented_reduce_scan_per_segment(const int64_t *h_offsets, int64_t nseg, int32_t dtype,
+                                                          const void *in, void *scan_out, void *sums_out,
+                                                          void *ws, size_t ws_bytes, desc_stream_t s) {
+  if (!h_offsets || nseg < 0 || !dtype_size(dtype)) return DESC_ERR_INVALID_ARG;
+  if (nseg == 0) return DESC_OK;
+  const int64_t total = h_offsets[nseg];
+  int32_t r;
+  if ((r = check_offsets_host(h_offsets, nseg, total)) != DESC_OK) return r;
+  if ((r = check_device_ptr(sums_out, 4)) != DESC_OK) return r;
+  const char *ib = static_cast<const char *>(in);
+  char *ob = static_cast<char *>(scan_out);
+  char *sb = static_cast<char *>(sums_out);
+  for (int64_t i = 0; i < nseg; ++i) {
+    const int64_t a = h_offsets[i], len = h_offsets[i + 1] - a;
+    if (len == 0) {
+      if (cudaMemsetAsync(sb + i * 4, 0, 4, reinterpret_cast<cudaStream_t>(s)) != cudaSuccess) return DESC_ERR_CUDA;
+      continue;
+    }
+    desc_view v;
+    std::memset(&v, 0, sizeof(v));
+    v.rank = 1;
+    v.shape[0] = len;
+    if ((r = desc_scan(&v, nullptr, DESC_LEVEL_GRID, dtype, ib + a * 4, size_t(len) * 4, ob + a * 4,
+                       size_t(len) * 4, 0, ws, ws_bytes, s)) != DESC_OK)
+      return r;
+    if ((r = desc_reduce(&v, nullptr, DESC_LEVEL_GRID, dtype, ib + a * 4, size_t(len) * 4, sb + i * 4, 4, 0, ws,
+                         ws_bytes, s)) != DESC_OK)
+      return r;
+  }
+  return DESC_OK;
 }
 
 // ---------------------------------------------------------------- status

@@ -353,6 +353,7 @@ __global__ void __launch_bounds__(kThreads + 32) scan_kernel(const T *in, T *out
     for (int64_t s = sh_seg0 + 1 + tid; s < args.nseg; s += kThreads) {
       const int64_t b = args.offsets[s];
       if (b >= tend) break;
+      if (b < t0) continue;                             // only if the offsets were not sorted
       const int64_t rel = b - t0;
       atomicOr(&sh_heads[rel >> 5], 1u << (rel & 31));
     }
