@@ -322,6 +322,96 @@ int32_t desc_segmented_reduce_scan_per_segment(const int64_t *h_offsets, int64_t
                                                const void *in, void *scan_out, void *sums_out, void *ws,
                                                size_t ws_bytes, desc_stream_t stream);
 
+/* ---- Schedules: candidates, exhaustive tuner, learned picker ---------------
+ * Not in the paper.  Each tunable op has a few compiled schedule candidates
+ * (candidate 0 is the default):
+ *   DESC_OP_REDUCE     chunked reduce: (vectors in flight per thread, target
+ *                      CTA count) in {(8,1216), (4,1216), (8,608), (4,2432),
+ *                      (8,2432), (8,304)}
+ *   DESC_OP_SCAN       look-back scan: tile of 4096 x {4, 2, 1} elements
+ *   DESC_OP_TRANSPOSE  tiles of {64, 32} squared
+ *   DESC_OP_SEGMENTED  CSR look-back scan: tile of 4096 x {4, 2, 1} elements
+ * A problem describes one call's shape; ops look up the candidate recorded
+ * for their (op, dtype, floor(log2 n), floor(log2(aux + 1))) bucket in a
+ * process-wide table (thread-safe), else use candidate 0. */
+typedef enum { DESC_OP_REDUCE = 0, DESC_OP_SCAN = 1, DESC_OP_TRANSPOSE = 2, DESC_OP_SEGMENTED = 3 } desc_op;
+#define DESC_NUM_FEATURES 26
+typedef struct {
+  int32_t op;          /* desc_op                                                      */
+  int32_t dtype;       /* DESC_I32 / DESC_F32                                          */
+  int64_t n;           /* elements                                                     */
+  int64_t aux;         /* reduce: outputs (n/aux elements each); transpose: rows;
+                          segmented: segments; scan: 0                                 */
+  float seg_hist[8];   /* segmented: fraction of segments with floor(log2 len) in
+                          [0,3), [3,6), ..., [18,21), and empty ones in bucket 0         */
+} desc_problem;
+/* Device buffers a measurement runs on (the caller owns them): in (n elements
+ * of dtype), out (reduce: aux or 1 elements; others: n), sums (segmented: aux),
+ * offsets (segmented: aux + 1, device int64), ws (at least the op's workspace). */
+typedef struct {
+  const void *in;
+  void *out;
+  void *sums;
+  const int64_t *offsets;
+  void *ws;
+  size_t ws_bytes;
+} desc_tune_buffers;
+
+int32_t desc_candidate_count(int32_t op, int32_t *count);
+/* Features of (problem, candidate) for the cost model: op and dtype one-hot,
+ * log2 sizes, the segment-length histogram, the candidate's tile size,
+ * vectors in flight, CTA target and index one-hot (DESC_NUM_FEATURES floats). */
+int32_t desc_features(const desc_problem *p, int32_t cand, float *out, int32_t nout);
+/* Times every candidate on the given buffers (reps launches each, CUDA events
+ * on the stream, median), writing microseconds to us[count].  Synchronises. */
+int32_t desc_tune_measure(const desc_problem *p, const desc_tune_buffers *b, int32_t reps, desc_stream_t stream,
+                          float *us);
+/* Exhaustive autotuning: measure all candidates, record the fastest (ties:
+ * the lowest index) for the problem's bucket, return it. */
+int32_t desc_tune_exhaustive(const desc_problem *p, const desc_tune_buffers *b, int32_t reps,
+                             desc_stream_t stream, int32_t *best);
+int32_t desc_tune_record(const desc_problem *p, int32_t cand);
+int32_t desc_tune_lookup(const desc_problem *p, int32_t *cand);   /* -1 when nothing is recorded */
+int32_t desc_tune_clear(void);
+int32_t desc_tune_save(const char *path);                          /* text file, one bucket per line */
+int32_t desc_tune_load(const char *path);
+/* Per-thread override used while measuring: ops of `op` use candidate `cand`
+ * (-1: back to the table). */
+int32_t desc_force_candidate(int32_t op, int32_t cand);
+
+/* ---- Cost model: 3-layer MLP on the GPU ------------------------------------
+ * y = w3 . relu(W2 relu(W1 x + b1) + b2) + b3 predicts log(time in us) of a
+ * (problem, candidate) feature row; loss = mean squared error.  Parameters are
+ * one FP32 device vector [W1 (H x F, row-major), b1, W2 (H x H), b2, w3, b3]
+ * (desc_mlp_param_count), owned by the caller, as are the Adam moments m and v
+ * (same length) and the workspace.  F <= 64, H <= 64 (H a multiple of 32).
+ * Forward, backward and Adam run in this library's kernels. */
+int32_t desc_mlp_param_count(int32_t F, int32_t H, int64_t *count);
+int32_t desc_mlp_workspace_size(int32_t F, int32_t H, int64_t rows, size_t *bytes);
+int32_t desc_mlp_forward(const float *params, int32_t F, int32_t H, const float *X, int64_t rows, float *y,
+                         void *ws, size_t ws_bytes, desc_stream_t stream);
+/* grad = d loss / d params over the rows (mean squared error against t). */
+int32_t desc_mlp_backward(const float *params, int32_t F, int32_t H, const float *X, const float *t, int64_t rows,
+                          float *grad, void *ws, size_t ws_bytes, desc_stream_t stream);
+/* One Adam step (Kingma and Ba, Algorithm 1; step counts from 1). */
+int32_t desc_mlp_adam(float *params, const float *grad, float *m, float *v, int64_t count, int32_t step, float lr,
+                      float beta1, float beta2, float eps, desc_stream_t stream);
+/* Minibatch training: epochs over rows (taken in the given order, batches of
+ * `batch` consecutive rows); *loss receives the mean loss of the last epoch. */
+int32_t desc_mlp_train(float *params, float *grad, float *m, float *v, int32_t F, int32_t H, const float *X,
+                       const float *t, int64_t rows, int32_t epochs, int32_t batch, float lr, void *ws,
+                       size_t ws_bytes, desc_stream_t stream, float *loss);
+/* Scores ncand feature rows (device) and writes the index of the smallest
+ * prediction (ties: the lowest) to *best (device int32) and all predictions
+ * to pred (device, ncand). */
+int32_t desc_mlp_pick(const float *params, int32_t F, int32_t H, const float *Xcand, int32_t ncand, float *pred,
+                      int32_t *best, desc_stream_t stream);
+/* Learned schedules: the model (kept by reference: the caller keeps params
+ * alive and unchanged while it is set) picks the candidate of a problem
+ * without timing, and the pick is recorded like a tuned one. */
+int32_t desc_tune_set_model(const float *params, int32_t F, int32_t H);
+int32_t desc_tune_predict(const desc_problem *p, desc_stream_t stream, int32_t *best);
+
 /* Per-device status word: waits for the stream, returns the first device
  * error recorded since the last call (DESC_OK if none) and clears it. */
 int32_t desc_stream_status(desc_stream_t stream);

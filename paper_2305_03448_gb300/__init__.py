@@ -23,6 +23,8 @@ GRID, BLOCK, WARP, THREAD = 0, 1, 2, 3
 X, Y, Z, LANE = 0, 1, 2, 3
 I32, F32 = 0, 1
 MM_FP32_SIMT, MM_BF16, MM_SPLIT3, MM_SPLIT2 = 0, 1, 2, 3
+OP_REDUCE, OP_SCAN, OP_TRANSPOSE, OP_SEGMENTED = 0, 1, 2, 3
+NUM_FEATURES = 26
 KAHAN = 1
 DEBUG_STALL_TILE = 1 << 16
 CHECK_OFFSETS = 1 << 17
@@ -69,6 +71,15 @@ class Access(ctypes.Structure):
     _fields_ = [("map", Lowered), ("buffer", c_int32), ("is_write", c_int32)]
 
 
+class Problem(ctypes.Structure):
+    _fields_ = [("op", c_int32), ("dtype", c_int32), ("n", c_int64), ("aux", c_int64), ("seg_hist", ctypes.c_float * 8)]
+
+
+class TuneBuffers(ctypes.Structure):
+    _fields_ = [("inp", c_void_p), ("out", c_void_p), ("sums", c_void_p), ("offsets", c_void_p), ("ws", c_void_p),
+                ("ws_bytes", c_size_t)]
+
+
 _lib_handle = None
 
 
@@ -111,6 +122,27 @@ def _declare(L):
         "desc_graph_destroy": (c_int32, [c_void_p]),
         "desc_segmented_reduce_scan_per_segment": (c_int32, [POINTER(c_int64), c_int64, c_int32, P, P, P, P,
                                                              c_size_t, P]),
+        "desc_candidate_count": (c_int32, [c_int32, POINTER(c_int32)]),
+        "desc_features": (c_int32, [POINTER(Problem), c_int32, POINTER(ctypes.c_float), c_int32]),
+        "desc_tune_measure": (c_int32, [POINTER(Problem), POINTER(TuneBuffers), c_int32, P, POINTER(ctypes.c_float)]),
+        "desc_tune_exhaustive": (c_int32, [POINTER(Problem), POINTER(TuneBuffers), c_int32, P, POINTER(c_int32)]),
+        "desc_tune_record": (c_int32, [POINTER(Problem), c_int32]),
+        "desc_tune_lookup": (c_int32, [POINTER(Problem), POINTER(c_int32)]),
+        "desc_tune_clear": (c_int32, []),
+        "desc_tune_save": (c_int32, [c_char_p]),
+        "desc_tune_load": (c_int32, [c_char_p]),
+        "desc_force_candidate": (c_int32, [c_int32, c_int32]),
+        "desc_mlp_param_count": (c_int32, [c_int32, c_int32, POINTER(c_int64)]),
+        "desc_mlp_workspace_size": (c_int32, [c_int32, c_int32, c_int64, POINTER(c_size_t)]),
+        "desc_mlp_forward": (c_int32, [P, c_int32, c_int32, P, c_int64, P, P, c_size_t, P]),
+        "desc_mlp_backward": (c_int32, [P, c_int32, c_int32, P, P, c_int64, P, P, c_size_t, P]),
+        "desc_mlp_adam": (c_int32, [P, P, P, P, c_int64, c_int32, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                    ctypes.c_float, P]),
+        "desc_mlp_train": (c_int32, [P, P, P, P, c_int32, c_int32, P, P, c_int64, c_int32, c_int32, ctypes.c_float,
+                                     P, c_size_t, P, POINTER(ctypes.c_float)]),
+        "desc_mlp_pick": (c_int32, [P, c_int32, c_int32, P, c_int32, P, P, P]),
+        "desc_tune_set_model": (c_int32, [P, c_int32, c_int32]),
+        "desc_tune_predict": (c_int32, [POINTER(Problem), P, POINTER(c_int32)]),
         "desc_scan_noalloc": (c_int32, [POINTER(View), POINTER(Exec), c_int32, c_int32, P, c_size_t, P, c_size_t,
                                         P]),
     }
@@ -382,3 +414,221 @@ def desc_scan_noalloc(x, base_shape, ops, seg_level, grid=None, block=None, out=
 
 def desc_stream_status(stream=None) -> int:
     return lib().desc_stream_status(_stream(stream))
+
+
+# ----------------------------------------------------------------- schedules
+def seg_hist(lengths):
+    """Fraction of segments per floor(log2 len) bucket [0,3), [3,6) ... [21,24);
+    empty segments count in bucket 0."""
+    import math
+    h = [0.0] * 8
+    L = [int(v) for v in lengths]
+    for v in L:
+        b = 0 if v <= 0 else min(int(math.log2(v)) // 3, 7)
+        h[b] += 1.0
+    return [x / max(len(L), 1) for x in h]
+
+
+def make_problem(op, dtype, n, aux=0, lengths=None) -> Problem:
+    p = Problem()
+    p.op, p.dtype, p.n, p.aux = int(op), int(dtype), int(n), int(aux)
+    if lengths is not None:
+        for i, v in enumerate(seg_hist(lengths)):
+            p.seg_hist[i] = v
+    return p
+
+
+def candidate_count(op) -> int:
+    c = c_int32(0)
+    _check(lib().desc_candidate_count(int(op), ctypes.byref(c)), "desc_candidate_count")
+    return c.value
+
+
+def desc_features(problem: Problem, cand: int):
+    out = (ctypes.c_float * NUM_FEATURES)()
+    _check(lib().desc_features(ctypes.byref(problem), int(cand), out, NUM_FEATURES), "desc_features")
+    return list(out)
+
+
+def desc_force_candidate(op, cand):
+    _check(lib().desc_force_candidate(int(op), int(cand)), "desc_force_candidate")
+
+
+def desc_tune_record(problem, cand):
+    _check(lib().desc_tune_record(ctypes.byref(problem), int(cand)), "desc_tune_record")
+
+
+def desc_tune_lookup(problem):
+    c = c_int32(-1)
+    _check(lib().desc_tune_lookup(ctypes.byref(problem), ctypes.byref(c)), "desc_tune_lookup")
+    return c.value
+
+
+def desc_tune_clear():
+    _check(lib().desc_tune_clear(), "desc_tune_clear")
+
+
+def desc_tune_save(path):
+    _check(lib().desc_tune_save(str(path).encode()), "desc_tune_save")
+
+
+def desc_tune_load(path):
+    _check(lib().desc_tune_load(str(path).encode()), "desc_tune_load")
+
+
+class TuneArena:
+    """Device buffers the tuner measures on (the largest problem decides)."""
+
+    def __init__(self, max_n, max_seg, device="cuda"):
+        import torch
+        self.x = torch.zeros(max_n, dtype=torch.float32, device=device)
+        self.y = torch.zeros(max_n, dtype=torch.float32, device=device)
+        self.sums = torch.zeros(max(max_seg, 1), dtype=torch.float32, device=device)
+        self.offsets = torch.zeros(max_seg + 1, dtype=torch.int64, device=device)
+        nb = max(desc_segmented_workspace(max_seg, max_n, "cpu").numel(), 1 << 20)
+        nb2 = c_size_t(0)
+        _check(lib().desc_scan_workspace_size(ctypes.byref(make_view([max_n], [])), None, GRID, F32,
+                                              ctypes.byref(nb2)), "desc_scan_workspace_size")
+        self.ws = torch.empty(max(nb, nb2.value) + (64 << 20), dtype=torch.uint8, device=device)
+
+    def buffers(self, prob: dict):
+        import torch
+        b = TuneBuffers()
+        b.inp, b.out, b.sums = self.x.data_ptr(), self.y.data_ptr(), self.sums.data_ptr()
+        b.ws, b.ws_bytes = self.ws.data_ptr(), self.ws.numel()
+        if prob["op"] == OP_SEGMENTED:
+            L = prob["lengths"]
+            off = torch.zeros(L.numel() + 1, dtype=torch.int64)
+            off[1:] = torch.cumsum(L.to(torch.int64), 0)
+            self.offsets[: off.numel()].copy_(off)
+        b.offsets = self.offsets.data_ptr()
+        return b
+
+
+def desc_tune_measure(prob: dict, arena: TuneArena, reps=5, stream=None):
+    p = make_problem(prob["op"], prob["dtype"], prob["n"], prob["aux"], prob.get("lengths"))
+    nc = candidate_count(prob["op"])
+    us = (ctypes.c_float * nc)()
+    _check(lib().desc_tune_measure(ctypes.byref(p), ctypes.byref(arena.buffers(prob)), int(reps), _stream(stream),
+                                   us), "desc_tune_measure")
+    return list(us)
+
+
+def desc_tune_exhaustive(prob: dict, arena: TuneArena, reps=5, stream=None):
+    p = make_problem(prob["op"], prob["dtype"], prob["n"], prob["aux"], prob.get("lengths"))
+    best = c_int32(-1)
+    _check(lib().desc_tune_exhaustive(ctypes.byref(p), ctypes.byref(arena.buffers(prob)), int(reps),
+                                      _stream(stream), ctypes.byref(best)), "desc_tune_exhaustive")
+    return best.value
+
+
+class CostModel:
+    """The schedule cost model: FP32 parameters, Adam moments and workspace on
+    the device; forward, backward, Adam and the picker run in libdesc."""
+
+    def __init__(self, params, F=NUM_FEATURES, H=64):
+        import torch
+        self.F, self.H = F, H
+        self.p = params.to("cuda", torch.float32).contiguous().clone()
+        self.m = torch.zeros_like(self.p)
+        self.v = torch.zeros_like(self.p)
+        self.g = torch.zeros_like(self.p)
+
+    def _ws(self, rows):
+        import torch
+        nb = c_size_t(0)
+        _check(lib().desc_mlp_workspace_size(self.F, self.H, int(rows), ctypes.byref(nb)), "desc_mlp_workspace_size")
+        return torch.empty(max(nb.value, 4), dtype=torch.uint8, device="cuda")
+
+    def forward(self, X):
+        import torch
+        y = torch.empty(X.shape[0], dtype=torch.float32, device="cuda")
+        _check(lib().desc_mlp_forward(_ptr(self.p), self.F, self.H, _ptr(X), X.shape[0], _ptr(y), None, 0,
+                                      _stream(None)), "desc_mlp_forward")
+        return y
+
+    def backward(self, X, t):
+        ws = self._ws(X.shape[0])
+        _check(lib().desc_mlp_backward(_ptr(self.p), self.F, self.H, _ptr(X), _ptr(t), X.shape[0], _ptr(self.g),
+                                       _ptr(ws), ws.numel(), _stream(None)), "desc_mlp_backward")
+        return self.g
+
+    def adam(self, step, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+        _check(lib().desc_mlp_adam(_ptr(self.p), _ptr(self.g), _ptr(self.m), _ptr(self.v), self.p.numel(), int(step),
+                                   lr, beta1, beta2, eps, _stream(None)), "desc_mlp_adam")
+
+    def train(self, X, t, epochs, batch, lr):
+        ws = self._ws(X.shape[0])
+        loss = ctypes.c_float(0)
+        _check(lib().desc_mlp_train(_ptr(self.p), _ptr(self.g), _ptr(self.m), _ptr(self.v), self.F, self.H, _ptr(X),
+                                    _ptr(t), X.shape[0], int(epochs), int(batch), float(lr), _ptr(ws), ws.numel(),
+                                    _stream(None), ctypes.byref(loss)), "desc_mlp_train")
+        return loss.value
+
+    def pick(self, Xcand):
+        import torch
+        pred = torch.empty(Xcand.shape[0], dtype=torch.float32, device="cuda")
+        best = torch.empty(1, dtype=torch.int32, device="cuda")
+        _check(lib().desc_mlp_pick(_ptr(self.p), self.F, self.H, _ptr(Xcand), Xcand.shape[0], _ptr(pred), _ptr(best),
+                                   _stream(None)), "desc_mlp_pick")
+        return int(best.item()), pred
+
+    def install(self):
+        """Use this model for desc_tune_predict (kept by reference)."""
+        _check(lib().desc_tune_set_model(_ptr(self.p), self.F, self.H), "desc_tune_set_model")
+
+    def predict_problem(self, prob: dict, stream=None):
+        p = make_problem(prob["op"], prob["dtype"], prob["n"], prob["aux"], prob.get("lengths"))
+        best = c_int32(-1)
+        _check(lib().desc_tune_predict(ctypes.byref(p), _stream(stream), ctypes.byref(best)), "desc_tune_predict")
+        return best.value
+
+
+def feature_rows(prob: dict):
+    p = make_problem(prob["op"], prob["dtype"], prob["n"], prob["aux"], prob.get("lengths"))
+    return [desc_features(p, c) for c in range(candidate_count(prob["op"]))]
+
+
+def regret_study(train_probs, test_probs, arena, model: CostModel, epochs=300, batch=128, lr=2e-3, reps=5):
+    """Exhaustive timings of every candidate of every problem (training rows
+    and held-out ground truth), GPU training of the cost model on the training
+    rows (log time), and the regret of its picks on the held-out problems:
+    t(pick) / t(best) - 1.  Also the regret of the default candidate 0."""
+    import math
+    import time as _time
+    import torch
+    X, t = [], []
+    t0 = _time.time()
+    for prob in train_probs:
+        us = desc_tune_measure(prob, arena, reps)
+        for c, row in enumerate(feature_rows(prob)):
+            X.append(row)
+            t.append(math.log(max(us[c], 1e-3)))
+    measure_train_s = _time.time() - t0
+    Xt = torch.tensor(X, dtype=torch.float32, device="cuda")
+    tt = torch.tensor(t, dtype=torch.float32, device="cuda")
+    perm = torch.randperm(Xt.shape[0], generator=torch.Generator().manual_seed(0)).cuda()
+    t1 = _time.time()
+    loss = model.train(Xt[perm].contiguous(), tt[perm].contiguous(), epochs, batch, lr)
+    torch.cuda.synchronize()
+    train_s = _time.time() - t1
+    reg_model, reg_default, exact, exh_s, pick_s = [], [], 0, 0.0, 0.0
+    for prob in test_probs:
+        a = _time.time()
+        us = desc_tune_measure(prob, arena, reps)
+        exh_s += _time.time() - a
+        rows = torch.tensor(feature_rows(prob), dtype=torch.float32, device="cuda")
+        a = _time.time()
+        c, _ = model.pick(rows)
+        pick_s += _time.time() - a
+        best = min(us)
+        reg_model.append(us[c] / best - 1.0)
+        reg_default.append(us[0] / best - 1.0)
+        exact += int(us[c] == best)
+    n = len(test_probs)
+    srt = sorted(reg_model)
+    return {"train_rows": len(X), "train_problems": len(train_probs), "test_problems": n, "final_loss": loss,
+            "mean_regret": sum(reg_model) / n, "p90_regret": srt[int(0.9 * (n - 1))],
+            "default_mean_regret": sum(reg_default) / n, "exact_picks": exact / n,
+            "measure_train_s": measure_train_s, "train_s": train_s, "exhaustive_test_s": exh_s,
+            "model_pick_s": pick_s}

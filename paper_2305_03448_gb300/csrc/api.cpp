@@ -97,7 +97,9 @@ extern "C" int32_t desc_reduce(const desc_view *v, const desc_exec *ex, int32_t 
   int64_t start0, seg;
   if (rest_contiguous(p, true, &start0, &seg))
     return launch_reduce_segments(dtype, in, start0, seg, p.n_rest, p.n_keep, out, flags, ws,
-                                  ws_bytes, s);
+                                  ws_bytes, s,
+                                  schedule_for(DESC_OP_REDUCE, dtype, p.n_rest * p.n_keep,
+                                               p.n_keep > 1 ? p.n_keep : 0));
   return launch_reduce_affine(dtype, in, p, out, flags, ws, ws_bytes, s);
 }
 
@@ -155,7 +157,7 @@ extern "C" int32_t desc_scan(const desc_view *v, const desc_exec *ex, int32_t se
   char *ob = static_cast<char *>(out);
   if (sp.contig)
     return launch_scan_contig(dtype, ib + sp.start * 4, ob + sp.start * 4, sp.total, sp.period,
-                              flags, ws, ws_bytes, s);
+                              flags, ws, ws_bytes, s, schedule_for(DESC_OP_SCAN, dtype, sp.total, 0));
   const size_t gather = align256(size_t(sp.total) * 4);
   if (!ws || ws_bytes < gather + scan_contig_ws(dtype, sp.total)) return DESC_ERR_WORKSPACE;
   // general path: gather in logical order, scan in place, scatter back
@@ -170,7 +172,8 @@ extern "C" int32_t desc_scan(const desc_view *v, const desc_exec *ex, int32_t se
   if ((r = launch_copy_affine(in, L.offset, st.data(), buf, 0, cst.data(), ext.data(), L.ndims, s)))
     return r;
   if ((r = launch_scan_contig(dtype, buf, buf, sp.total, sp.period, flags,
-                              static_cast<char *>(ws) + gather, ws_bytes - gather, s)))
+                              static_cast<char *>(ws) + gather, ws_bytes - gather, s,
+                              schedule_for(DESC_OP_SCAN, dtype, sp.total, 0))))
     return r;
   return launch_copy_affine(buf, 0, cst.data(), out, L.offset, st.data(), ext.data(), L.ndims, s);
 }
@@ -257,7 +260,8 @@ extern "C" int32_t desc_transpose(const desc_view *in_v, const desc_view *out_v,
       if (ld_in >= C && ld_out >= R)
         return launch_transpose(static_cast<const float *>(in) + Li.offset,
                                 static_cast<float *>(out) + Lo.offset, R, C, ld_in, ld_out, batch,
-                                bs_in, bs_out, s);
+                                bs_in, bs_out, s,
+                                schedule_for(DESC_OP_TRANSPOSE, dtype, R * C, R));
     }
   }
   return launch_copy_affine(in, Li.offset, Li.stride, out, Lo.offset, Lo.stride, Li.extent,
@@ -397,7 +401,7 @@ extern "C" int32_t desc_segmented_reduce_scan(const int64_t *d_offsets, int64_t 
     return cudaMemsetAsync(sums_out, 0, size_t(nseg) * 4, reinterpret_cast<cudaStream_t>(s)) == cudaSuccess
                ? DESC_OK : DESC_ERR_CUDA;
   return launch_scan_csr(dtype, in, scan_out, total, d_offsets, nseg, sums_out, flags & DESC_DEBUG_STALL_TILE, ws,
-                         ws_bytes, s);
+                         ws_bytes, s, schedule_for(DESC_OP_SEGMENTED, dtype, total, nseg));
 }
 
 extern "C" int32_t desc_segmented_graph_create(const int64_t *d_offsets, int64_t nseg, int64_t total,

@@ -54,9 +54,11 @@ int32_t mm_status_take();     // k_mm_tc.cu
 
 // ----- launchers (k_*.cu) -------------------------------------------------
 // Reduce: contiguous segments [start + o*seg_stride, +len), o < nout.
+// `cand`: schedule candidate (-1: the default).
 int32_t launch_reduce_segments(int32_t dtype, const void *in, int64_t start, int64_t seg_stride,
                                int64_t len, int64_t nout, void *out, int32_t flags, void *ws,
-                               size_t ws_bytes, desc_stream_t s);
+                               size_t ws_bytes, desc_stream_t s, int cand);
+int reduce_candidates();
 size_t reduce_segments_ws(int32_t dtype, int64_t len, int64_t nout);
 // Reduce: general affine plan (chunk partials in ws when runs are long).
 size_t reduce_affine_ws(int64_t n_rest, int64_t nout);
@@ -66,7 +68,8 @@ int32_t launch_reduce_affine(int32_t dtype, const void *in, const Plan &p, void 
 // Scan of a contiguous array of n elements split into segments of length
 // `period` (period == n: one segment).  in may equal out.
 int32_t launch_scan_contig(int32_t dtype, const void *in, void *out, int64_t n, int64_t period,
-                           int32_t flags, void *ws, size_t ws_bytes, desc_stream_t s);
+                           int32_t flags, void *ws, size_t ws_bytes, desc_stream_t s, int cand);
+int scan_candidates();
 size_t scan_contig_ws(int32_t dtype, int64_t n);
 // The same scan with the library's static scratch array (noalloc.cu).
 int32_t launch_scan_contig_noalloc(int32_t dtype, const void *in, void *out, int64_t n,
@@ -75,7 +78,7 @@ int32_t launch_scan_contig_noalloc(int32_t dtype, const void *in, void *out, int
 // receives the total of every segment (0 for empty ones).
 int32_t launch_scan_csr(int32_t dtype, const void *in, void *out, int64_t n, const int64_t *offsets,
                         int64_t nseg, void *sums, int32_t flags, void *ws, size_t ws_bytes,
-                        desc_stream_t s);
+                        desc_stream_t s, int cand);
 size_t scan_csr_ws(int64_t n);
 
 // Copy over a common logical domain of `nd` dims: out[ostride . p] = in[istride . p].
@@ -86,7 +89,12 @@ int32_t launch_copy_affine(const void *in, int64_t ioff, const int64_t *istride,
 // into C x R (leading dim ld_out), batch strides bs_in / bs_out.
 int32_t launch_transpose(const float *in, float *out, int64_t R, int64_t C, int64_t ld_in,
                          int64_t ld_out, int64_t batch, int64_t bs_in, int64_t bs_out,
-                         desc_stream_t s);
+                         desc_stream_t s, int cand);
+int transpose_candidates();
+
+// Schedule selection (tune.cpp): the candidate an op call should use, from
+// the per-thread forced candidate, else the tuned table, else -1 (default).
+int32_t schedule_for(int32_t op, int32_t dtype, int64_t n, int64_t aux);
 
 // Matmul: FP32 SIMT (k_mm_simt.cu) and tensor-core forms (k_mm_tc.cu).
 int32_t launch_sgemm(const float *A, const float *B, float *C, int64_t M, int64_t N, int64_t K, int64_t lda,

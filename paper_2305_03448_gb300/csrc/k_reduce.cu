@@ -21,16 +21,30 @@ namespace desc {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kUnroll = 8;
-constexpr int64_t kTargetCtas = 1216;      // 8 per SM on a 152-SM GB300
 constexpr int64_t kSmallRun = 16;          // <= this: one thread per output
 constexpr int64_t kWarpRun = 4096;         // <= this: one warp per output
 
-int64_t chunks_for(int64_t len, int64_t nout) {
-  const int64_t per_cta_min = int64_t(kThreads) * 4 * kUnroll;
-  int64_t by_fill = (kTargetCtas + nout - 1) / std::max<int64_t>(nout, 1);
+// Schedule candidates of the chunked kernel: vectors in flight per thread and
+// the CTA count the chunking aims at (1216 = 8 CTAs on each of 152 SMs).
+struct ReduceCand {
+  int unroll;
+  int64_t target_ctas;
+};
+constexpr ReduceCand kCands[] = {{8, 1216}, {4, 1216}, {8, 608}, {4, 2432}, {8, 2432}, {8, 304}};
+constexpr int kNumCands = sizeof(kCands) / sizeof(kCands[0]);
+
+int64_t chunks_for(int64_t len, int64_t nout, const ReduceCand &c) {
+  const int64_t per_cta_min = int64_t(kThreads) * 4 * c.unroll;
+  int64_t by_fill = (c.target_ctas + nout - 1) / std::max<int64_t>(nout, 1);
   int64_t by_len = (len + per_cta_min - 1) / per_cta_min;
   return std::max<int64_t>(1, std::min(by_fill, by_len));
+}
+
+// The most chunks any candidate uses (sizes the partials).
+int64_t max_chunks(int64_t len, int64_t nout) {
+  int64_t m = 1;
+  for (const ReduceCand &c : kCands) m = std::max(m, chunks_for(len, nout, c));
+  return m;
 }
 
 template <class A>
@@ -89,7 +103,7 @@ template <> struct Vec<int32_t> { using type = int4; };
 template <> struct Vec<float> { using type = float4; };
 
 // One CTA per (run, chunk).  grid.x = nout * chunks.
-template <class A, class T>
+template <class A, class T, int kUnroll>
 __global__ void __launch_bounds__(kThreads) reduce_runs_kernel(
     const T *__restrict__ in, int64_t start, int64_t seg_stride, int64_t len, int64_t chunks,
     int64_t chunk_vec, T *__restrict__ out, uint2 *partials, unsigned *counters) {
@@ -176,14 +190,14 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 size_t ws_for(int64_t len, int64_t nout) {
   if (len <= kWarpRun) return 0;
-  const int64_t ch = chunks_for(len, nout);
+  const int64_t ch = max_chunks(len, nout);
   if (ch == 1) return 0;
   return align256(size_t(nout) * ch * sizeof(uint2)) + align256(size_t(nout) * sizeof(unsigned));
 }
 
 template <class A, class T>
 int32_t run_runs(const T *in, int64_t start, int64_t seg_stride, int64_t len, int64_t nout, T *out,
-                 void *ws, size_t ws_bytes, cudaStream_t s) {
+                 void *ws, size_t ws_bytes, cudaStream_t s, int cand) {
   if (len <= kSmallRun) {
     const int64_t ctas = std::min<int64_t>((nout + kThreads - 1) / kThreads, int64_t(1) << 20);
     reduce_short_kernel<A, T, 1><<<(unsigned)ctas, kThreads, 0, s>>>(in, start, seg_stride, len, nout, out);
@@ -191,21 +205,26 @@ int32_t run_runs(const T *in, int64_t start, int64_t seg_stride, int64_t len, in
     const int64_t ctas = std::min<int64_t>((nout * 32 + kThreads - 1) / kThreads, int64_t(1) << 20);
     reduce_short_kernel<A, T, 32><<<(unsigned)ctas, kThreads, 0, s>>>(in, start, seg_stride, len, nout, out);
   } else {
-    const int64_t chunks = chunks_for(len, nout);
+    const ReduceCand &cd = kCands[(cand >= 0 && cand < kNumCands) ? cand : 0];
+    const int64_t chunks = chunks_for(len, nout, cd);
     uint2 *partials = nullptr;
     unsigned *counters = nullptr;
     if (chunks > 1) {
       if (!ws || ws_bytes < ws_for(len, nout)) return DESC_ERR_WORKSPACE;
       partials = static_cast<uint2 *>(ws);
       counters = reinterpret_cast<unsigned *>(static_cast<char *>(ws) +
-                                              align256(size_t(nout) * chunks * sizeof(uint2)));
+                                              align256(size_t(nout) * max_chunks(len, nout) * sizeof(uint2)));
       DESC_CUDA_TRY(cudaMemsetAsync(counters, 0, size_t(nout) * sizeof(unsigned), s));
     }
     const int64_t nvec = len / 4 + 1;
     const int64_t chunk_vec = (nvec + chunks - 1) / chunks;
     if (nout * chunks >= (int64_t(1) << 31)) return DESC_ERR_UNSUPPORTED;
-    reduce_runs_kernel<A, T><<<(unsigned)(nout * chunks), kThreads, 0, s>>>(
-        in, start, seg_stride, len, chunks, chunk_vec, out, partials, counters);
+    if (cd.unroll == 4)
+      reduce_runs_kernel<A, T, 4><<<(unsigned)(nout * chunks), kThreads, 0, s>>>(
+          in, start, seg_stride, len, chunks, chunk_vec, out, partials, counters);
+    else
+      reduce_runs_kernel<A, T, 8><<<(unsigned)(nout * chunks), kThreads, 0, s>>>(
+          in, start, seg_stride, len, chunks, chunk_vec, out, partials, counters);
   }
   DESC_CUDA_TRY(cudaGetLastError());
   return DESC_OK;
@@ -221,7 +240,7 @@ int32_t run_affine(const T *in, const Plan &p, T *out, void *ws, size_t ws_bytes
   a.offset = p.offset;
   a.n_rest = p.n_rest;
   const int64_t nout = p.n_keep;
-  const int64_t chunks = p.n_rest <= kWarpRun ? 1 : chunks_for(p.n_rest, nout);
+  const int64_t chunks = p.n_rest <= kWarpRun ? 1 : chunks_for(p.n_rest, nout, kCands[0]);
   const int64_t chunk_len = (p.n_rest + chunks - 1) / chunks;
   uint2 *partials = nullptr;
   unsigned *counters = nullptr;
@@ -229,7 +248,7 @@ int32_t run_affine(const T *in, const Plan &p, T *out, void *ws, size_t ws_bytes
     if (!ws || ws_bytes < ws_for(p.n_rest, nout)) return DESC_ERR_WORKSPACE;
     partials = static_cast<uint2 *>(ws);
     counters = reinterpret_cast<unsigned *>(static_cast<char *>(ws) +
-                                            align256(size_t(nout) * chunks * sizeof(uint2)));
+                                            align256(size_t(nout) * max_chunks(p.n_rest, nout) * sizeof(uint2)));
     DESC_CUDA_TRY(cudaMemsetAsync(counters, 0, size_t(nout) * sizeof(unsigned), s));
   }
   if (nout * chunks >= (int64_t(1) << 31)) return DESC_ERR_UNSUPPORTED;
@@ -243,18 +262,20 @@ int32_t run_affine(const T *in, const Plan &p, T *out, void *ws, size_t ws_bytes
 
 size_t reduce_segments_ws(int32_t /*dtype*/, int64_t len, int64_t nout) { return ws_for(len, nout); }
 
+int reduce_candidates() { return kNumCands; }
+
 int32_t launch_reduce_segments(int32_t dtype, const void *in, int64_t start, int64_t seg_stride,
                                int64_t len, int64_t nout, void *out, int32_t flags, void *ws,
-                               size_t ws_bytes, desc_stream_t st) {
+                               size_t ws_bytes, desc_stream_t st, int cand) {
   cudaStream_t s = reinterpret_cast<cudaStream_t>(st);
   if (dtype == DESC_I32)
     return run_runs<AccI32, int32_t>(static_cast<const int32_t *>(in), start, seg_stride, len, nout,
-                                     static_cast<int32_t *>(out), ws, ws_bytes, s);
+                                     static_cast<int32_t *>(out), ws, ws_bytes, s, cand);
   if (flags & DESC_KAHAN)
     return run_runs<AccKahan, float>(static_cast<const float *>(in), start, seg_stride, len, nout,
-                                     static_cast<float *>(out), ws, ws_bytes, s);
+                                     static_cast<float *>(out), ws, ws_bytes, s, cand);
   return run_runs<AccF32, float>(static_cast<const float *>(in), start, seg_stride, len, nout,
-                                 static_cast<float *>(out), ws, ws_bytes, s);
+                                 static_cast<float *>(out), ws, ws_bytes, s, cand);
 }
 
 size_t reduce_affine_ws(int64_t n_rest, int64_t nout) {

@@ -23,8 +23,6 @@
 // as soon as another tile has given up), records DESC_ERR_DEVICE_TIMEOUT in
 // the device status word, and its CTA leaves without writing.
 #include <algorithm>
-#include <cstdlib>
-#include <cstring>
 
 #include "k_common.cuh"
 
@@ -525,16 +523,9 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 constexpr int kWsTile = kSub;   // workspace is sized for the smallest tile
 
-// Sub-tiles per tile; DESC_SCAN_SUB picks another compiled size.
-int scan_sub() {
-  static int sub = 0;
-  if (!sub) {
-    const char *e = getenv("DESC_SCAN_SUB");
-    const int v = e ? atoi(e) : 4;
-    sub = (v == 1 || v == 2 || v == 4) ? v : 4;
-  }
-  return sub;
-}
+// Schedule candidates: sub-tiles per tile (tile = 4096 x SUB elements).
+constexpr int kSubCands[] = {4, 2, 1};
+constexpr int kNumSubCands = 3;
 
 template <class T, int MODE, int SUB>
 int32_t run_scan_t(const T *in, T *out, const ScanArgs &a, void *ws, size_t ws_bytes, cudaStream_t s) {
@@ -559,8 +550,8 @@ int32_t run_scan_t(const T *in, T *out, const ScanArgs &a, void *ws, size_t ws_b
 }
 
 template <class T, int MODE>
-int32_t run_scan(const T *in, T *out, const ScanArgs &a, void *ws, size_t ws_bytes, cudaStream_t s) {
-  switch (scan_sub()) {
+int32_t run_scan(const T *in, T *out, const ScanArgs &a, void *ws, size_t ws_bytes, cudaStream_t s, int cand) {
+  switch (kSubCands[(cand >= 0 && cand < kNumSubCands) ? cand : 0]) {
     case 1: return run_scan_t<T, MODE, 1>(in, out, a, ws, ws_bytes, s);
     case 2: return run_scan_t<T, MODE, 2>(in, out, a, ws, ws_bytes, s);
     default: return run_scan_t<T, MODE, 4>(in, out, a, ws, ws_bytes, s);
@@ -581,8 +572,10 @@ size_t scan_contig_ws(int32_t /*dtype*/, int64_t n) {
   return align256(sizeof(ScanWs)) + size_t(ntiles) * sizeof(TileState);
 }
 
+int scan_candidates() { return kNumSubCands; }
+
 int32_t launch_scan_contig(int32_t dtype, const void *in, void *out, int64_t n, int64_t period,
-                           int32_t flags, void *ws, size_t ws_bytes, desc_stream_t st) {
+                           int32_t flags, void *ws, size_t ws_bytes, desc_stream_t st, int cand) {
   cudaStream_t s = reinterpret_cast<cudaStream_t>(st);
   ScanArgs a{};
   a.n = n;
@@ -593,20 +586,20 @@ int32_t launch_scan_contig(int32_t dtype, const void *in, void *out, int64_t n, 
   if (dtype == DESC_I32) {
     auto i = static_cast<const int32_t *>(in);
     auto o = static_cast<int32_t *>(out);
-    return periodic ? run_scan<int32_t, PERIODIC>(i, o, a, ws, ws_bytes, s)
-                    : run_scan<int32_t, PLAIN>(i, o, a, ws, ws_bytes, s);
+    return periodic ? run_scan<int32_t, PERIODIC>(i, o, a, ws, ws_bytes, s, cand)
+                    : run_scan<int32_t, PLAIN>(i, o, a, ws, ws_bytes, s, cand);
   }
   auto i = static_cast<const float *>(in);
   auto o = static_cast<float *>(out);
-  return periodic ? run_scan<float, PERIODIC>(i, o, a, ws, ws_bytes, s)
-                  : run_scan<float, PLAIN>(i, o, a, ws, ws_bytes, s);
+  return periodic ? run_scan<float, PERIODIC>(i, o, a, ws, ws_bytes, s, cand)
+                  : run_scan<float, PLAIN>(i, o, a, ws, ws_bytes, s, cand);
 }
 
 size_t scan_csr_ws(int64_t n) { return scan_contig_ws(DESC_F32, n); }
 
 int32_t launch_scan_csr(int32_t dtype, const void *in, void *out, int64_t n, const int64_t *offsets,
                         int64_t nseg, void *sums, int32_t flags, void *ws, size_t ws_bytes,
-                        desc_stream_t st) {
+                        desc_stream_t st, int cand) {
   cudaStream_t s = reinterpret_cast<cudaStream_t>(st);
   ScanArgs a{};
   a.n = n;
@@ -617,9 +610,9 @@ int32_t launch_scan_csr(int32_t dtype, const void *in, void *out, int64_t n, con
   a.vec = ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15) == 0;
   if (dtype == DESC_I32)
     return run_scan<int32_t, CSR>(static_cast<const int32_t *>(in), static_cast<int32_t *>(out), a,
-                                  ws, ws_bytes, s);
+                                  ws, ws_bytes, s, cand);
   return run_scan<float, CSR>(static_cast<const float *>(in), static_cast<float *>(out), a, ws,
-                              ws_bytes, s);
+                              ws_bytes, s, cand);
 }
 
 }  // namespace desc

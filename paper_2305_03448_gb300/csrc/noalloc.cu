@@ -53,7 +53,7 @@ int32_t launch_scan_contig_noalloc(int32_t dtype, const void *in, void *out, int
   void *ws = nullptr;
   const int32_t r = scratch_for_current_device(&ws);
   if (r != DESC_OK) return r;
-  return launch_scan_contig(dtype, in, out, n, period, 0, ws, kNoallocScratchBytes, s);
+  return launch_scan_contig(dtype, in, out, n, period, 0, ws, kNoallocScratchBytes, s, -1);
 }
 
 }  // namespace desc

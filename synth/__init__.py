@@ -135,3 +135,39 @@ def mlp_init(F: int, H: int, seed: int) -> torch.Tensor:
          for i in range(3)]
     z = torch.zeros(H, dtype=torch.float64)
     return torch.cat([u[0], z, u[1], z, u[2], torch.zeros(1, dtype=torch.float64)]).to(torch.float32)
+
+
+def tune_problems(count: int, seed: int) -> list:
+    """Seeded shapes for schedule tuning, drawn from the benchmark families:
+    reduce (full or per-group, log2 n in [10, 27]), scan (log2 n in [10, 27]),
+    transpose (rows, cols powers of two, 2^10 <= rows * cols <= 2^26),
+    segmented (10..5000 segments, log-uniform lengths up to 2^8..2^16).
+    Each item: dict(op, dtype, n, aux, lengths) with op 0..3 as in desc_op."""
+    u = _unit_f64(splitmix64(stream_key(seed, 1234), 0, 8 * count)).reshape(count, 8).tolist()
+    out = []
+    for i in range(count):
+        a = u[i]
+        op = min(int(a[0] * 4), 3)
+        dtype = 0 if a[1] < 0.5 else 1
+        if op == 0:
+            ln = 10 + int(a[2] * 18)
+            n = 1 << ln
+            aux = 0 if a[3] < 0.5 else 1 << int(a[4] * min(ln - 2, 14))
+            out.append(dict(op=0, dtype=dtype, n=n, aux=aux, lengths=None))
+        elif op == 1:
+            n = int(2 ** (10 + a[2] * 17.0))
+            out.append(dict(op=1, dtype=dtype, n=n, aux=0, lengths=None))
+        elif op == 2:
+            lr = 5 + int(a[2] * 10)
+            lc = 5 + int(a[3] * 10)
+            while lr + lc > 26:
+                lr, lc = lr - 1, lc - 1
+            while lr + lc < 10:
+                lr, lc = lr + 1, lc + 1
+            out.append(dict(op=2, dtype=1, n=(1 << lr) * (1 << lc), aux=1 << lr, lengths=None))
+        else:
+            nseg = 10 + int(a[2] * 4990)
+            mx = 1 << (8 + int(a[3] * 9))
+            L = loguniform_lengths(nseg, seed=seed * 100003 + i, max_len=mx)
+            out.append(dict(op=3, dtype=dtype, n=int(L.sum()), aux=nseg, lengths=L))
+    return out

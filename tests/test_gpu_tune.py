@@ -1,0 +1,150 @@
+"""GPU checks of the schedule machinery: the cost model's kernels against the
+oracle's FP64 twin (forward, gradient within 1e-4 relative, Adam), every
+schedule candidate against the oracle, the exhaustive tuner, and a small
+regret study of the learned picker against the exhaustive tuner."""
+import numpy as np
+import pytest
+import torch
+
+import paper_2305_03448_gb300 as D
+import synth
+from oracle import mlp as OMLP
+from oracle import ops as O
+from oracle import views as V
+
+pytestmark = pytest.mark.gpu
+F, H = D.NUM_FEATURES, 64
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib(desc_lib):
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    yield desc_lib
+    D.desc_tune_clear()
+
+
+def data(rows, seed):
+    X = synth.normal_f32(rows * F, seed=seed).reshape(rows, F)
+    t = synth.normal_f32(rows, seed=seed + 1)
+    return X, t
+
+
+def test_forward_matches_fp64_twin():
+    p = synth.mlp_init(F, H, seed=1)
+    X, _ = data(300, 2)
+    m = D.CostModel(p)
+    y = m.forward(X.cuda()).cpu().double().numpy()
+    want, _ = OMLP.forward(p.double().numpy(), X.double().numpy(), F, H)
+    assert np.max(np.abs(y - want)) <= 1e-5 * max(1.0, np.max(np.abs(want)))
+
+
+def test_gradient_matches_fp64_twin():
+    p = synth.mlp_init(F, H, seed=3)
+    p[H * F:H * F + H] = 0.05
+    X, t = data(257, 4)
+    m = D.CostModel(p)
+    g = m.backward(X.cuda(), t.cuda()).cpu().double().numpy()
+    _, want = OMLP.backward(p.double().numpy(), X.double().numpy(), t.double().numpy(), F, H)
+    assert np.linalg.norm(g - want) <= 1e-4 * np.linalg.norm(want)
+
+
+def test_adam_matches_fp64_twin_and_zero_lr_is_a_no_op():
+    p = synth.mlp_init(F, H, seed=5)
+    X, t = data(64, 6)
+    m = D.CostModel(p)
+    g = m.backward(X.cuda(), t.cuda()).clone()
+    m.adam(1, 1e-3)
+    want, _, _ = OMLP.adam(p.double().numpy(), g.cpu().double().numpy(), np.zeros(p.numel()), np.zeros(p.numel()),
+                           1, 1e-3)
+    assert np.max(np.abs(m.p.cpu().double().numpy() - want)) <= 1e-6
+    m2 = D.CostModel(p)
+    m2.backward(X.cuda(), t.cuda())
+    m2.adam(1, 0.0)
+    assert torch.equal(m2.p.cpu(), p)
+
+
+def test_training_fits_and_pick_is_argmin():
+    p = synth.mlp_init(F, H, seed=7)
+    X, t = data(8, 8)
+    m = D.CostModel(p)
+    l0 = float(np.mean((OMLP.forward(p.double().numpy(), X.double().numpy(), F, H)[0] - t.numpy()) ** 2))
+    loss = m.train(X.cuda(), t.cuda(), epochs=2000, batch=8, lr=3e-3)
+    assert loss < 1e-2 * l0
+    best, pred = m.pick(X[:5].cuda())
+    want, _ = OMLP.forward(m.p.cpu().double().numpy(), X[:5].double().numpy(), F, H)
+    assert best == int(np.argmin(want))
+    assert np.allclose(pred.cpu().numpy(), want, atol=1e-4)
+
+
+def test_every_candidate_is_correct():
+    """Each schedule candidate, forced, matches the oracle."""
+    n = (1 << 20) + 77
+    xi = synth.ints_pm1000(n, seed=9)
+    xf = synth.uniform_grid(n, seed=9)
+    for c in range(D.candidate_count(D.OP_REDUCE)):
+        D.desc_force_candidate(D.OP_REDUCE, c)
+        assert int(D.desc_reduce(xi.cuda(), [n], [], V.GRID).item()) == int(O.reduce(xi.numpy(), [n], [], V.GRID)[0][0])
+        g = 64
+        got = D.desc_reduce(xi[: g * 16384].cuda(), [g * 16384], [("group", 16384, 0), ("select", V.BLOCK, V.X)],
+                            V.BLOCK, (g, 1, 1), (1, 1, 1)).cpu().numpy()
+        want, _ = O.reduce(xi[: g * 16384].numpy(), [g * 16384], [("group", 16384, 0), ("select", V.BLOCK, V.X)],
+                           V.BLOCK)
+        assert np.array_equal(got, want)
+    D.desc_force_candidate(D.OP_REDUCE, -1)
+    for c in range(D.candidate_count(D.OP_SCAN)):
+        D.desc_force_candidate(D.OP_SCAN, c)
+        got = D.desc_scan(xi.cuda(), [n], [], V.GRID).cpu().numpy()
+        want, _ = O.scan(xi.numpy(), np.zeros(n, np.int32), [n], [], V.GRID)
+        assert np.array_equal(got, want)
+        gotf = D.desc_scan(xf.cuda(), [n], [], V.GRID).cpu().numpy()
+        wantf, pa = O.scan(xf.numpy(), np.zeros(n, np.float32), [n], [], V.GRID)
+        assert np.all(np.abs(gotf - wantf) <= 1e-5 * pa)
+    D.desc_force_candidate(D.OP_SCAN, -1)
+    L = synth.loguniform_lengths(500, seed=10, max_len=20000)
+    off = synth.offsets_from_lengths(L)
+    x = synth.ints_pm1000(int(off[-1]), seed=10)
+    want, wsum, _, _ = O.segmented_reduce_scan(x.numpy(), off.numpy())
+    for c in range(D.candidate_count(D.OP_SEGMENTED)):
+        D.desc_force_candidate(D.OP_SEGMENTED, c)
+        s, sums = D.desc_segmented_reduce_scan(x.cuda(), off.cuda())
+        assert np.array_equal(s.cpu().numpy(), want) and np.array_equal(sums.cpu().numpy(), wsum)
+    D.desc_force_candidate(D.OP_SEGMENTED, -1)
+    R, C = 300, 1000
+    xt = synth.normal_f32(R * C, seed=11).reshape(R, C)
+    for c in range(D.candidate_count(D.OP_TRANSPOSE)):
+        D.desc_force_candidate(D.OP_TRANSPOSE, c)
+        out = torch.empty(C, R, device="cuda")
+        D.desc_transpose(xt.cuda(), [R, C], [("transpose", 0)], out, [C, R], [])
+        assert torch.equal(out.cpu(), xt.t())
+    D.desc_force_candidate(D.OP_TRANSPOSE, -1)
+
+
+def test_exhaustive_tuner_records_the_fastest():
+    arena = D.TuneArena(1 << 22, 1000)
+    D.desc_tune_clear()
+    for prob in [dict(op=1, dtype=1, n=1 << 22, aux=0, lengths=None), dict(op=0, dtype=0, n=1 << 21, aux=0, lengths=None),
+                 dict(op=2, dtype=1, n=1 << 22, aux=1 << 11, lengths=None)]:
+        us = D.desc_tune_measure(prob, arena, reps=5)
+        assert len(us) == D.candidate_count(prob["op"]) and min(us) > 0
+        best = D.desc_tune_exhaustive(prob, arena, reps=5)
+        assert 0 <= best < len(us)
+        assert D.desc_tune_lookup(D.make_problem(prob["op"], prob["dtype"], prob["n"], prob["aux"])) == best
+    D.desc_tune_clear()
+
+
+def test_learned_picker_small_regret_study():
+    """A small version of the regret study the bench runs at full size."""
+    arena = D.TuneArena(1 << 27, 5000)
+    train = synth.tune_problems(160, seed=21)
+    test = synth.tune_problems(60, seed=22)
+    model = D.CostModel(synth.mlp_init(F, H, seed=23))
+    r = D.regret_study(train, test, arena, model, epochs=200, batch=64, lr=2e-3, reps=3)
+    print(r)
+    assert r["final_loss"] < 0.5
+    assert r["mean_regret"] <= 0.10
+    # the model predicts for a problem through the library's own picker too
+    model.install()
+    c = model.predict_problem(test[0])
+    assert D.desc_tune_lookup(D.make_problem(test[0]["op"], test[0]["dtype"], test[0]["n"], test[0]["aux"],
+                                             test[0]["lengths"])) == c
+    D.lib().desc_tune_set_model(None, 0, 0)
