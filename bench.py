@@ -162,6 +162,12 @@ def run_ours(args, rank, world, local_rank):
     only = set(args.ops.split(",")) if args.ops else None
     if only:
         ops = [o for o in ops if o[0] in only]
+    schedules = None
+    if not args.no_tune:
+        schedules = autotune_step(D, stream, {"reduce": (D.OP_REDUCE, D.I32, Rn, 0, xr, out_r, ws_r),
+                                              "scan": (D.OP_SCAN, D.F32, Sn, 0, xs, out_s, ws_s),
+                                              "transpose": (D.OP_TRANSPOSE, D.F32, T * T, T, xt, out_t, ws_s)},
+                                  [name for name, _ in ops])
     for _ in range(args.warmup):
         for _, f in ops:
             f()
@@ -231,16 +237,58 @@ def run_ours(args, rank, world, local_rank):
             "config": {"workload": WORKLOAD + (" (small)" if args.small else ""),
                        "reduce_n": Rn, "scan_n": Sn, "transpose": [T, T],
                        "reduce_view": "group(1024)[[block]].group(32)[[warp]][[thread]]",
-                       "l2": "inputs larger than L2 (129 MB); no flush", "parallelism": f"replicas x{world}"},
+                       "l2": "inputs larger than L2 (129 MB); no flush", "parallelism": f"replicas x{world}",
+                       "schedules": schedules},
             "ops": per_op, "roofline": roofline, "gpu_launches": K * len(ops), "e2e": e2e}
     if clk:
         line["clocks"] = {k: clk[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")}
     if not args.no_extras and not args.small:
         line["matmul"] = run_matmul(torch, D, dev, stream, pk)
         line["segmented"] = run_segmented(torch, D, synth, dev, stream)
+        if not args.no_model:
+            line["schedule_model"] = run_schedule_model(torch, D, synth)
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(sz, only)
     return line
+
+
+def autotune_step(D, stream, probs, names):
+    """Exhaustive autotuning of the step's own problems (every schedule
+    candidate timed with CUDA events on the step's buffers); the fastest is
+    recorded and used by the timed step.  Returns {op: {chosen, us: [...]}}."""
+    import ctypes
+    out = {}
+    for name in names:
+        op, dt, n, aux, x, y, ws = probs[name]
+        p = D.make_problem(op, dt, n, aux)
+        b = D.TuneBuffers()
+        b.inp, b.out, b.sums, b.offsets = x.data_ptr(), y.data_ptr(), None, None
+        b.ws, b.ws_bytes = ws.data_ptr(), ws.numel()
+        nc = D.candidate_count(op)
+        us = (ctypes.c_float * nc)()
+        D._check(D.lib().desc_tune_measure(ctypes.byref(p), ctypes.byref(b), 5, D._stream(stream), us),
+                 "desc_tune_measure")
+        us = list(us)
+        best = min(range(nc), key=lambda c: (us[c], c))
+        D.desc_tune_record(p, best)
+        out[name] = {"chosen": best, "us": [round(u, 1) for u in us]}
+    return out
+
+
+def run_schedule_model(torch, D, synth, n_train=860, n_test=500):
+    """Learned schedules: exhaustive timings of every candidate of seeded
+    problems from the reduce / scan / transpose / segmented families (about
+    3,000 training rows), the cost model trained on the GPU by the library's
+    kernels, and its picks on 500 held-out problems compared with the
+    exhaustive tuner (regret = t(pick) / t(best) - 1) and with the default."""
+    arena = D.TuneArena(1 << 27, 5000)
+    train = synth.tune_problems(n_train, seed=101)
+    test = synth.tune_problems(n_test, seed=202)
+    model = D.CostModel(synth.mlp_init(D.NUM_FEATURES, 64, seed=303))
+    r = D.regret_study(train, test, arena, model, epochs=300, batch=128, lr=2e-3, reps=5)
+    del arena
+    torch.cuda.empty_cache()
+    return {k: (round(v, 4) if isinstance(v, float) else v) for k, v in r.items()}
 
 
 def _time(torch, stream, fn, reps):
@@ -459,6 +507,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-extras", action="store_true", help="skip the matmul and segmented measurements")
+    ap.add_argument("--no-model", action="store_true", help="skip the learned-schedule regret study")
+    ap.add_argument("--no-tune", action="store_true", help="time the default schedules, without autotuning")
     args = ap.parse_args()
     if args.warmup < 3 and not args.small:
         args.warmup = 3
