@@ -509,6 +509,10 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the matmul and segmented measurements")
     ap.add_argument("--no-model", action="store_true", help="skip the learned-schedule regret study")
     ap.add_argument("--no-tune", action="store_true", help="time the default schedules, without autotuning")
+    ap.add_argument("--case", choices=["step", "matmul", "segmented"], default="step",
+                    help="matmul / segmented: run only that measurement (for profiler captures)")
+    ap.add_argument("--mm-n", type=int, default=8192, help="matmul size for --case matmul")
+    ap.add_argument("--seg-count", type=int, default=20000, help="segments for --case segmented")
     args = ap.parse_args()
     if args.warmup < 3 and not args.small:
         args.warmup = 3
@@ -524,7 +528,19 @@ def main():
         import torch
         torch.cuda.set_device(local_rank)
         torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
-    line = run_ours(args, rank, world, local_rank)
+    if args.case != "step":
+        import torch
+        import paper_2305_03448_gb300 as D
+        import synth
+        dev = torch.device("cuda", local_rank)
+        torch.cuda.set_device(dev)
+        stream = torch.cuda.current_stream(dev)
+        if args.case == "matmul":
+            line = {"case": "matmul", "matmul": run_matmul(torch, D, dev, stream, peaks(), n=args.mm_n)}
+        else:
+            line = {"case": "segmented", "segmented": run_segmented(torch, D, synth, dev, stream, nseg=args.seg_count)}
+    else:
+        line = run_ours(args, rank, world, local_rank)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
