@@ -196,13 +196,14 @@ __device__ bool look_back(TileState *states, int64_t tile, ScanWs *ws, long long
   return true;
 }
 
-// ---- asynchronous tile copies (cp.async) into padded shared memory ------
-// A sub-tile is 1024 chunks of 16 bytes.  Chunk j sits at byte 16 * (j + j/8):
-// one 16-byte pad per 128 bytes makes both the striped accesses (lane l on
-// chunk base + l, used to move data to and from global memory with full
-// 128-byte lines) and the blocked accesses (thread t on chunks 4t..4t+3,
-// used by the scan) free of shared-memory bank conflicts.
-__device__ __forceinline__ int chunk_off(int j) { return 16 * (j + (j >> 3)); }
+// ---- asynchronous tile copies (cp.async) into swizzled shared memory ----
+// A sub-tile is 1024 chunks of 16 bytes.  Chunk j sits in slot
+// j ^ ((j >> 3) & 3): within each 128-byte row the slots are permuted so
+// that both the striped accesses (lane l on chunk base + l, used to move
+// data to and from global memory with full 128-byte lines) and the blocked
+// accesses (thread t on chunks 4t..4t+3, used by the scan) hit 8 distinct
+// 16-byte bank groups in every phase of 8 lanes, without padding.
+__device__ __forceinline__ int chunk_off(int j) { return 16 * (j ^ ((j >> 3) & 3)); }
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem, int src_bytes) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -228,7 +229,7 @@ constexpr int kItems = 16;                          // elements per thread and s
 constexpr int kWarps = kThreads / 32;
 constexpr int kSub = kThreads * kItems;             // elements per sub-tile
 constexpr int kSubChunks = kSub / 4;                // 16-byte chunks per sub-tile
-constexpr int kStageBytes = 16 * (kSubChunks + kSubChunks / 8);
+constexpr int kStageBytes = 16 * kSubChunks;
 
 __device__ __forceinline__ void compute_bar() { asm volatile("bar.sync 1, %0;" ::"n"(kThreads) : "memory"); }
 
