@@ -163,11 +163,16 @@ def run_ours(args, rank, world, local_rank):
     if only:
         ops = [o for o in ops if o[0] in only]
     schedules = None
-    if not args.no_tune:
+    if args.load_tune:
+        D.desc_tune_load(args.load_tune)
+        schedules = {"loaded": args.load_tune}
+    elif not args.no_tune:
         schedules = autotune_step(D, stream, {"reduce": (D.OP_REDUCE, D.I32, Rn, 0, xr, out_r, ws_r),
                                               "scan": (D.OP_SCAN, D.F32, Sn, 0, xs, out_s, ws_s),
                                               "transpose": (D.OP_TRANSPOSE, D.F32, T * T, T, xt, out_t, ws_s)},
                                   [name for name, _ in ops])
+        if args.save_tune:
+            D.desc_tune_save(args.save_tune)
     for _ in range(args.warmup):
         for _, f in ops:
             f()
@@ -526,6 +531,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the matmul and segmented measurements")
     ap.add_argument("--no-model", action="store_true", help="skip the learned-schedule regret study")
     ap.add_argument("--no-tune", action="store_true", help="time the default schedules, without autotuning")
+    ap.add_argument("--save-tune", default="", help="save the tuned schedule table to this file")
+    ap.add_argument("--load-tune", default="", help="use a saved schedule table instead of tuning")
     ap.add_argument("--case", choices=["step", "matmul", "segmented"], default="step",
                     help="matmul / segmented: run only that measurement (for profiler captures)")
     ap.add_argument("--mm-n", type=int, default=8192, help="matmul size for --case matmul")

@@ -326,8 +326,10 @@ int32_t desc_segmented_reduce_scan_per_segment(const int64_t *h_offsets, int64_t
  * Not in the paper.  Each tunable op has a few compiled schedule candidates
  * (candidate 0 is the default):
  *   DESC_OP_REDUCE     chunked reduce: (vectors in flight per thread, target
- *                      CTA count) in {(8,1216), (4,1216), (8,608), (4,2432),
- *                      (8,2432), (8,304)}
+ *                      CTA count, load path) in {(8,1216,s), (4,1216,s),
+ *                      (8,608,s), (4,2432,s), (8,2432,s), (8,304,s),
+ *                      (4,2432,r), (8,1216,r)}; s = evict-first streaming
+ *                      loads, r = read-only path without L1 allocation
  *   DESC_OP_SCAN       look-back scan: tile of 4096 x {4, 2, 1} elements
  *   DESC_OP_TRANSPOSE  tiles of {64, 32} squared
  *   DESC_OP_SEGMENTED  CSR look-back scan: tile of 4096 x {4, 2, 1} elements
@@ -335,7 +337,7 @@ int32_t desc_segmented_reduce_scan_per_segment(const int64_t *h_offsets, int64_t
  * for their (op, dtype, floor(log2 n), floor(log2(aux + 1))) bucket in a
  * process-wide table (thread-safe), else use candidate 0. */
 typedef enum { DESC_OP_REDUCE = 0, DESC_OP_SCAN = 1, DESC_OP_TRANSPOSE = 2, DESC_OP_SEGMENTED = 3 } desc_op;
-#define DESC_NUM_FEATURES 26
+#define DESC_NUM_FEATURES 29
 typedef struct {
   int32_t op;          /* desc_op                                                      */
   int32_t dtype;       /* DESC_I32 / DESC_F32                                          */
@@ -360,7 +362,8 @@ typedef struct {
 int32_t desc_candidate_count(int32_t op, int32_t *count);
 /* Features of (problem, candidate) for the cost model: op and dtype one-hot,
  * log2 sizes, the segment-length histogram, the candidate's tile size,
- * vectors in flight, CTA target and index one-hot (DESC_NUM_FEATURES floats). */
+ * vectors in flight, CTA target, index one-hot (8 slots) and load path
+ * (DESC_NUM_FEATURES floats). */
 int32_t desc_features(const desc_problem *p, int32_t cand, float *out, int32_t nout);
 /* Times every candidate on the given buffers (reps launches each, CUDA events
  * on the stream, median), writing microseconds to us[count].  Synchronises. */

@@ -24,7 +24,7 @@ X, Y, Z, LANE = 0, 1, 2, 3
 I32, F32 = 0, 1
 MM_FP32_SIMT, MM_BF16, MM_SPLIT3, MM_SPLIT2 = 0, 1, 2, 3
 OP_REDUCE, OP_SCAN, OP_TRANSPOSE, OP_SEGMENTED = 0, 1, 2, 3
-NUM_FEATURES = 26
+NUM_FEATURES = 29
 KAHAN = 1
 DEBUG_STALL_TILE = 1 << 16
 CHECK_OFFSETS = 1 << 17

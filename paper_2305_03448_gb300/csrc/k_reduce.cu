@@ -24,13 +24,17 @@ constexpr int kThreads = 256;
 constexpr int64_t kSmallRun = 16;          // <= this: one thread per output
 constexpr int64_t kWarpRun = 4096;         // <= this: one warp per output
 
-// Schedule candidates of the chunked kernel: vectors in flight per thread and
-// the CTA count the chunking aims at (1216 = 8 CTAs on each of 152 SMs).
+// Schedule candidates of the chunked kernel: vectors in flight per thread,
+// the CTA count the chunking aims at (1216 = 8 CTAs on each of 152 SMs) and
+// the load path (0: evict-first streaming loads, 1: read-only path without
+// L1 allocation).
 struct ReduceCand {
   int unroll;
   int64_t target_ctas;
+  int nc;
 };
-constexpr ReduceCand kCands[] = {{8, 1216}, {4, 1216}, {8, 608}, {4, 2432}, {8, 2432}, {8, 304}};
+constexpr ReduceCand kCands[] = {{8, 1216, 0}, {4, 1216, 0}, {8, 608, 0}, {4, 2432, 0},
+                                 {8, 2432, 0}, {8, 304, 0},  {4, 2432, 1}, {8, 1216, 1}};
 constexpr int kNumCands = sizeof(kCands) / sizeof(kCands[0]);
 
 int64_t chunks_for(int64_t len, int64_t nout, const ReduceCand &c) {
@@ -102,8 +106,28 @@ template <class T> struct Vec;
 template <> struct Vec<int32_t> { using type = int4; };
 template <> struct Vec<float> { using type = float4; };
 
+__device__ __forceinline__ int4 ld_nc(const int4 *p) {
+  int4 v;
+  asm volatile("ld.global.nc.L1::no_allocate.v4.s32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p));
+  return v;
+}
+__device__ __forceinline__ float4 ld_nc(const float4 *p) {
+  float4 v;
+  asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "l"(p));
+  return v;
+}
+template <int NC, class V>
+__device__ __forceinline__ V ld_vec(const V *p) {
+  if (NC) return ld_nc(p);
+  return ld_stream(p);
+}
+
 // One CTA per (run, chunk).  grid.x = nout * chunks.
-template <class A, class T, int kUnroll>
+template <class A, class T, int kUnroll, int NC>
 __global__ void __launch_bounds__(kThreads) reduce_runs_kernel(
     const T *__restrict__ in, int64_t start, int64_t seg_stride, int64_t len, int64_t chunks,
     int64_t chunk_vec, T *__restrict__ out, uint2 *partials, unsigned *counters) {
@@ -123,11 +147,11 @@ __global__ void __launch_bounds__(kThreads) reduce_runs_kernel(
   for (; i + (kUnroll - 1) * kThreads < v1; i += kUnroll * kThreads) {
     V x[kUnroll];
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) x[u] = ld_stream(pv + i + u * kThreads);
+    for (int u = 0; u < kUnroll; ++u) x[u] = ld_vec<NC>(pv + i + u * kThreads);
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) a.add4(x[u]);
   }
-  for (; i < v1; i += kThreads) a.add4(ld_stream(pv + i));
+  for (; i < v1; i += kThreads) a.add4(ld_vec<NC>(pv + i));
   if (c == 0 && threadIdx.x < head) a.add1(p[threadIdx.x]);
   if (c == chunks - 1 && threadIdx.x < tail) a.add1(p[head + 4 * nvec + threadIdx.x]);
   block_merge<A, kThreads>(a, sh);
@@ -219,12 +243,19 @@ int32_t run_runs(const T *in, int64_t start, int64_t seg_stride, int64_t len, in
     const int64_t nvec = len / 4 + 1;
     const int64_t chunk_vec = (nvec + chunks - 1) / chunks;
     if (nout * chunks >= (int64_t(1) << 31)) return DESC_ERR_UNSUPPORTED;
-    if (cd.unroll == 4)
-      reduce_runs_kernel<A, T, 4><<<(unsigned)(nout * chunks), kThreads, 0, s>>>(
-          in, start, seg_stride, len, chunks, chunk_vec, out, partials, counters);
+    const unsigned grid = (unsigned)(nout * chunks);
+    if (cd.unroll == 4 && !cd.nc)
+      reduce_runs_kernel<A, T, 4, 0><<<grid, kThreads, 0, s>>>(in, start, seg_stride, len, chunks, chunk_vec, out,
+                                                               partials, counters);
+    else if (cd.unroll == 4)
+      reduce_runs_kernel<A, T, 4, 1><<<grid, kThreads, 0, s>>>(in, start, seg_stride, len, chunks, chunk_vec, out,
+                                                               partials, counters);
+    else if (!cd.nc)
+      reduce_runs_kernel<A, T, 8, 0><<<grid, kThreads, 0, s>>>(in, start, seg_stride, len, chunks, chunk_vec, out,
+                                                               partials, counters);
     else
-      reduce_runs_kernel<A, T, 8><<<(unsigned)(nout * chunks), kThreads, 0, s>>>(
-          in, start, seg_stride, len, chunks, chunk_vec, out, partials, counters);
+      reduce_runs_kernel<A, T, 8, 1><<<grid, kThreads, 0, s>>>(in, start, seg_stride, len, chunks, chunk_vec, out,
+                                                               partials, counters);
   }
   DESC_CUDA_TRY(cudaGetLastError());
   return DESC_OK;

@@ -95,13 +95,15 @@ extern "C" int32_t desc_features(const desc_problem *p, int32_t cand, float *out
   out[8] = lg((double)p->n / ((double)p->aux + 1.0) + 1.0) / 32.f;
   if (p->op == DESC_OP_SEGMENTED)
     for (int i = 0; i < 8; ++i) out[9 + i] = p->seg_hist[i];
-  static const int unroll[6] = {8, 4, 8, 4, 8, 8};
-  static const int ctas[6] = {1216, 1216, 608, 2432, 2432, 304};
+  static const int unroll[8] = {8, 4, 8, 4, 8, 8, 4, 8};
+  static const int ctas[8] = {1216, 1216, 608, 2432, 2432, 304, 2432, 1216};
+  static const int nc[8] = {0, 0, 0, 0, 0, 0, 1, 1};
   static const int subs[3] = {4, 2, 1};
   if (p->op == DESC_OP_REDUCE) {
     out[17] = lg(256.0 * 4 * unroll[cand]) / 32.f;
     out[18] = unroll[cand] / 16.f;
     out[19] = lg((double)ctas[cand]) / 16.f;
+    out[28] = (float)nc[cand];
   } else if (p->op == DESC_OP_TRANSPOSE) {
     const double td = cand == 0 ? 64 : 32;
     out[17] = lg(td * td) / 32.f;

@@ -9,7 +9,7 @@ import synth
 
 
 def test_candidate_counts(desc_lib):
-    assert [D.candidate_count(o) for o in range(4)] == [6, 3, 2, 3]
+    assert [D.candidate_count(o) for o in range(4)] == [8, 3, 2, 3]
     with pytest.raises(D.DescError):
         D.candidate_count(7)
 
@@ -21,7 +21,7 @@ def test_features_encode_problem_and_candidate(desc_lib):
         assert len(f) == D.NUM_FEATURES
         assert f[0:4] == [0.0, 1.0, 0.0, 0.0] and f[4:6] == [0.0, 1.0]
         assert abs(f[6] - 20 / 32) < 1e-6
-        assert f[20 + c] == 1.0 and sum(f[20:26]) == 1.0
+        assert f[20 + c] == 1.0 and sum(f[20:28]) == 1.0
     assert rows[0][17] > rows[1][17] > rows[2][17]          # tile sizes 16384 > 8192 > 4096
     L = synth.loguniform_lengths(100, seed=1, max_len=1 << 12)
     ps = D.make_problem(D.OP_SEGMENTED, D.I32, int(L.sum()), 100, L)
@@ -48,7 +48,7 @@ def test_table_record_lookup_save_load(desc_lib, tmp_path):
     D.desc_tune_load(path)
     assert D.desc_tune_lookup(p) == 3
     with pytest.raises(D.DescError):
-        D.desc_tune_record(p, 6)                            # out of range
+        D.desc_tune_record(p, 8)                            # out of range
     open(path, "w").write("0 0 22 0 9\n")
     with pytest.raises(D.DescError):
         D.desc_tune_load(path)
