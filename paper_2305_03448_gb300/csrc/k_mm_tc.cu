@@ -45,6 +45,7 @@ constexpr int kTmemCols = 512;                  // two 256-column accumulators
 constexpr int kMmThreads = 192;
 constexpr int kSmemBytes = kStages * kStageBytes + 1024 + 256;
 constexpr long long kWaitBudget = 1ll << 32;     // clock cycles, about two seconds
+constexpr int kGroupM = 16;                      // tile rows per rasterisation group
 
 struct Products {
   int n;
@@ -136,9 +137,34 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Tile order: groups of kGroupM tile rows, column by column inside a group,
+// so that the operand panels a wave of CTAs touches stay in L2.
+struct TileMap {
+  int Mt, Nt, group_m;
+};
+__device__ __forceinline__ void tile_coords(int t, const TileMap &g, int &mt, int &nt) {
+  const int per_group = g.group_m * g.Nt;
+  const int first = (t / per_group) * g.group_m;
+  const int gm = min(g.Mt - first, g.group_m);
+  const int r = t % per_group;
+  mt = first + r % gm;
+  nt = r / gm;
+}
+
+// Persistent: CTA b takes tiles b, b + gridDim.x, ...  The producer streams
+// the operand stages of consecutive tiles without a break, so the next tile's
+// loads overlap the current tile's epilogue.  Accumulator sets in TMEM:
+// with one product (BF16) two sets of 256 columns alternate between tiles,
+// so the epilogue of tile i overlaps the MMAs of tile i + 1; with the split
+// forms one set spans both 256-column accumulators (the two K halves).
 __global__ void __launch_bounds__(kMmThreads, 1)
     mm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                 float *__restrict__ C, int64_t M, int64_t N, int64_t ldc, int kblocks, Products prods) {
+                 float *__restrict__ C, int64_t M, int64_t N, int64_t ldc, int kblocks, Products prods, TileMap tm,
+                 int ntiles, int split_acc) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                           ~uintptr_t(1023));
@@ -146,18 +172,21 @@ __global__ void __launch_bounds__(kMmThreads, 1)
   unsigned char *sB = smem + kStages * kABytes;
   uint64_t *full = reinterpret_cast<uint64_t *>(smem + kStages * kStageBytes);
   uint64_t *empty = full + kStages;
-  uint64_t *done = empty + kStages;
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+  uint64_t *tfull = empty + kStages;
+  uint64_t *tempty = tfull + 2;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tempty + 2);
   volatile int *abort = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t m0 = int64_t(blockIdx.y) * BM, n0 = int64_t(blockIdx.x) * BN;
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(done, 1);
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&tfull[a], 1);
+      mbar_init(&tempty[a], 4);                        // one arrival per epilogue warp
+    }
     *abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -167,63 +196,92 @@ __global__ void __launch_bounds__(kMmThreads, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  const int total = kblocks * prods.n;
+  const int per_tile = kblocks * prods.n;              // stages per tile
+  const int nsets = split_acc ? 1 : 2;
 
   if (warp == 0) {
     if (lane == 0) {                                   // ---- TMA producer
-      int issued = 0;
-      for (int it = 0; it < total; ++it) {
-        const int s = it % kStages;
-        const uint32_t ph = (it / kStages) & 1;
-        if (!mbar_wait(&empty[s], ph ^ 1, abort)) break;
-        const int p = it / kblocks, kb = it % kblocks;
-        mbar_expect_tx(&full[s], kStageBytes);
-        tma_load_3d(sA + s * kABytes, &tmA, &full[s], kb * BK, (int)m0, prods.pa[p]);
-        tma_load_3d(sB + s * kBBytes, &tmB, &full[s], kb * BK, (int)n0, prods.pb[p]);
-        ++issued;
+      int it = 0, issued = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        int mt, nt;
+        tile_coords(t, tm, mt, nt);
+        for (int j = 0; j < per_tile; ++j, ++it) {
+          const int s = it % kStages;
+          const uint32_t ph = (it / kStages) & 1;
+          if (!mbar_wait(&empty[s], ph ^ 1, abort)) { ok = false; break; }
+          const int p = j / kblocks, kb = j % kblocks;
+          mbar_expect_tx(&full[s], kStageBytes);
+          tma_load_3d(sA + s * kABytes, &tmA, &full[s], kb * BK, mt * BM, prods.pa[p]);
+          tma_load_3d(sB + s * kBBytes, &tmB, &full[s], kb * BK, nt * BN, prods.pb[p]);
+          issued = it + 1;
+        }
       }
       if (*abort) {                                    // copies still in flight: wait, bounded
-        for (int it = std::max(0, issued - kStages); it < issued; ++it) {
+        for (int i = std::max(0, issued - kStages); i < issued; ++i) {
           const long long t0 = clock64();
-          while (!mbar_try_wait(&full[it % kStages], (it / kStages) & 1) && clock64() - t0 < kWaitBudget) {
+          while (!mbar_try_wait(&full[i % kStages], (i / kStages) & 1) && clock64() - t0 < kWaitBudget) {
           }
         }
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {                                   // ---- MMA issuer
-      const int half = kblocks / 2;                    // k-blocks [half, kblocks) go to accumulator 1
-      for (int it = 0; it < total; ++it) {
-        const int s = it % kStages;
-        const uint32_t ph = (it / kStages) & 1;
-        if (!mbar_wait(&full[s], ph, abort)) break;
+      const int half = kblocks / 2;
+      int it = 0, li = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++li) {
+        const int si = li % nsets;
+        const uint32_t use = (uint32_t)(li / nsets);
+        if (!mbar_wait(&tempty[si], (use & 1) ^ 1, abort)) break;   // epilogue has drained this set
         tc_fence_after();
-        const int p = it / kblocks, kb = it % kblocks;
-        const int acc = (half > 0 && kb >= half) ? 1 : 0;
-        const bool first = p == 0 && kb == (acc ? half : 0);
-        const uint32_t d = tmem + (uint32_t)(acc * BN);
-        const uint32_t a0 = smem_u32(sA + s * kABytes), b0 = smem_u32(sB + s * kBBytes);
+        for (int j = 0; j < per_tile; ++j, ++it) {
+          const int s = it % kStages;
+          const uint32_t ph = (it / kStages) & 1;
+          if (!mbar_wait(&full[s], ph, abort)) { ok = false; break; }
+          tc_fence_after();
+          const int p = j / kblocks, kb = j % kblocks;
+          int acc;
+          bool first;
+          if (split_acc) {                             // K halves in two accumulators
+            acc = (half > 0 && kb >= half) ? 1 : 0;
+            first = p == 0 && kb == (acc ? half : 0);
+          } else {
+            acc = si;
+            first = j == 0;
+          }
+          const uint32_t d = tmem + (uint32_t)(acc * BN);
+          const uint32_t a0 = smem_u32(sA + s * kABytes), b0 = smem_u32(sB + s * kBBytes);
 #pragma unroll
-        for (int k = 0; k < BK / UK; ++k)
-          umma_bf16(d, sdesc(a0 + k * UK * 2), sdesc(b0 + k * UK * 2), (first && k == 0) ? 0u : 1u);
-        umma_commit(&empty[s]);                        // stage reusable once these MMAs finish
+          for (int k = 0; k < BK / UK; ++k)
+            umma_bf16(d, sdesc(a0 + k * UK * 2), sdesc(b0 + k * UK * 2), (first && k == 0) ? 0u : 1u);
+          umma_commit(&empty[s]);                      // stage reusable once these MMAs finish
+        }
+        if (ok) umma_commit(&tfull[si]);               // this tile's accumulators complete
       }
-      umma_commit(done);                               // accumulators complete
     }
   } else {                                             // ---- epilogue, warps 2..5
     const int q = warp & 3;                            // TMEM lanes 32 q .. 32 q + 31
-    if (mbar_wait(done, 0, abort)) {
+    const bool vec = ((ldc & 3) == 0) && ((reinterpret_cast<uintptr_t>(C) & 15) == 0);
+    const bool two = split_acc && kblocks / 2 > 0;
+    int li = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++li) {
+      const int si = li % nsets;
+      const uint32_t use = (uint32_t)(li / nsets);
+      if (!mbar_wait(&tfull[si], use & 1, abort)) break;
       tc_fence_after();
-      const int64_t row = m0 + q * 32 + lane;
-      const bool vec = ((ldc & 3) == 0) && ((reinterpret_cast<uintptr_t>(C) & 15) == 0);
-      const bool two = kblocks / 2 > 0;
+      int mt, nt;
+      tile_coords(t, tm, mt, nt);
+      const int64_t row = int64_t(mt) * BM + q * 32 + lane;
+      const int64_t n0 = int64_t(nt) * BN;
+      const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(split_acc ? 0 : si * BN);
 #pragma unroll 1
       for (int c = 0; c < BN / 32; ++c) {
         uint32_t r[32];
-        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(c * 32), r);
+        tmem_ld32(base + (uint32_t)(c * 32), r);
         if (two) {
           uint32_t r1[32];
-          tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(BN + c * 32), r1);
+          tmem_ld32(base + (uint32_t)(BN + c * 32), r1);
 #pragma unroll
           for (int j = 0; j < 32; ++j) r[j] = __float_as_uint(__fadd_rn(__uint_as_float(r[j]), __uint_as_float(r1[j])));
         }
@@ -242,6 +300,9 @@ __global__ void __launch_bounds__(kMmThreads, 1)
           }
         }
       }
+      tc_fence_before();                               // TMEM reads done before the set is reused
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[si]);
     }
   }
   tc_fence_before();
@@ -375,12 +436,23 @@ int32_t launch_mm_tc(const float *A, int64_t a_off, int64_t a_sr, int64_t a_sc, 
     pr.pb[i] = pb[i];
   }
   static bool attr = false;
+  static int nsm = 0;
   if (!attr) {
     DESC_CUDA_TRY(cudaFuncSetAttribute(mm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
+    int dev = 0;
+    DESC_CUDA_TRY(cudaGetDevice(&dev));
+    DESC_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     attr = true;
   }
-  mm_tc_kernel<<<dim3((unsigned)(Np / BN), (unsigned)(Mp / BM)), kMmThreads, kSmemBytes, s>>>(
-      tmA, tmB, C, M, N, N, (int)(Kp / BK), pr);
+  TileMap tmap;
+  tmap.Mt = (int)(Mp / BM);
+  tmap.Nt = (int)(Np / BN);
+  tmap.group_m = std::min(tmap.Mt, kGroupM);
+  const int64_t ntiles = int64_t(tmap.Mt) * tmap.Nt;
+  if (ntiles >= (int64_t(1) << 31)) return DESC_ERR_UNSUPPORTED;
+  const int grid = (int)std::min<int64_t>(ntiles, std::max(nsm, 1));
+  mm_tc_kernel<<<grid, kMmThreads, kSmemBytes, s>>>(tmA, tmB, C, M, N, N, (int)(Kp / BK), pr, tmap, (int)ntiles,
+                                                     planes > 1 ? 1 : 0);
   DESC_CUDA_TRY(cudaGetLastError());
   return DESC_OK;
 }
