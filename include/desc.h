@@ -230,8 +230,8 @@ int32_t desc_scan(const desc_view *v, const desc_exec *ex, int32_t seg_level, in
  * array, a split of it, or groups selected at seg_level); other views return
  * DESC_ERR_UNSUPPORTED.  It takes no workspace: its scratch is a fixed
  * static device array inside the library, large enough for
- * DESC_SCAN_NOALLOC_MAX_ELEMS elements (256 bytes plus 16 bytes per 4096
- * elements, about 1 MiB).  Every GPU that loads the library holds that array
+ * DESC_SCAN_NOALLOC_MAX_ELEMS elements (256 bytes plus 128 bytes per 16384
+ * elements, about 2 MiB).  Every GPU that loads the library holds that array
  * until the process exits.  A larger scan returns DESC_ERR_WORKSPACE and
  * launches nothing.  The call allocates nothing: no cudaMalloc, no cudaFree,
  * no allocating library routine.

@@ -71,6 +71,12 @@ int32_t launch_scan_contig(int32_t dtype, const void *in, void *out, int64_t n, 
                            int32_t flags, void *ws, size_t ws_bytes, desc_stream_t s, int cand);
 int scan_candidates();
 size_t scan_contig_ws(int32_t dtype, int64_t n);
+// Bytes per look-back tile state: one state per 128-byte L2 line, so that the
+// polls of hundreds of look-back warps spread over many L2 slices instead of
+// queueing on the few lines next to the newest published prefix.
+constexpr size_t kScanTileStateBytes = 128;
+// The no-alloc scan always runs the 16384-element tile.
+constexpr int64_t kScanNoallocTile = 16384;
 // The same scan with the library's static scratch array (noalloc.cu).
 int32_t launch_scan_contig_noalloc(int32_t dtype, const void *in, void *out, int64_t n,
                                    int64_t period, desc_stream_t s);

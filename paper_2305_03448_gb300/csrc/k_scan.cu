@@ -35,10 +35,11 @@ namespace {
 constexpr unsigned long long kStatAgg = 1ull, kStatIncl = 2ull;
 constexpr long long kBudgetCycles = 1ll << 31;      // about one second
 constexpr long long kDebugBudgetCycles = 1ll << 26; // tens of milliseconds
+constexpr unsigned kGoSpins = 1u << 16;                // x 64 ns: the look-back start wait
 
 enum Mode { PLAIN = 0, PERIODIC = 1, CSR = 2 };
 
-struct TileState {
+struct alignas(kScanTileStateBytes) TileState {
   unsigned long long w;
 };
 
@@ -304,11 +305,15 @@ __global__ void __launch_bounds__(kThreads + 32) scan_kernel(const T *in, T *out
   __shared__ unsigned sh_heads[MODE == CSR ? kTile / 32 : 1];
   __shared__ unsigned short sh_need[MODE == PLAIN ? 1 : SUB * kThreads];  // carry-needed bits
   __shared__ int64_t sh_seg0;
+  __shared__ volatile int sh_go;        // look-back may start polling
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t n = args.n;
   const bool vec = args.vec != 0;
-  if (tid == 0) sh_tile = atomicAdd(&ws->ticket, 1u);
+  if (tid == 0) {
+    sh_tile = atomicAdd(&ws->ticket, 1u);
+    sh_go = 0;
+  }
   __syncthreads();
   const int64_t tile = sh_tile;
   const int64_t ntiles = (n + kTile - 1) / kTile;
@@ -323,8 +328,13 @@ __global__ void __launch_bounds__(kThreads + 32) scan_kernel(const T *in, T *out
       first_is_head = args.offsets[find_segment(args.offsets, args.nseg, t0)] == t0;
     Carry<T> prefix = Carry<T>::zero();
     bool ok = true;
-    if (!first_is_head)
+    if (!first_is_head) {
+      // Polls made before the predecessors, which started just before this
+      // tile, can have published only fail and load the tile states; start
+      // once part of this tile's own input has landed (bounded wait).
+      for (unsigned i = 0; i < kGoSpins && !sh_go; ++i) __nanosleep(64);
       ok = look_back<T>(states, tile, ws, args.debug ? kDebugBudgetCycles : kBudgetCycles, prefix);
+    }
     if (lane == 0) {
       sh_prefix = prefix;
       sh_ok = ok ? 1 : 0;
@@ -368,6 +378,7 @@ __global__ void __launch_bounds__(kThreads + 32) scan_kernel(const T *in, T *out
     unsigned char *st = ring + s * kStageBytes;
     cp_async_wait_dyn(SUB - 1 - s);                     // sub-tile s has landed (this thread)
     compute_bar();                                      // ... for every thread; carry visible
+    if (s == SUB / 2 && tid == 0) sh_go = 1;
     const T cv = sh_carry;
     const int cf = sh_carry_flag;
     const int64_t g0 = t0 + int64_t(s) * kSub + int64_t(tid) * kItems;
@@ -526,6 +537,7 @@ constexpr int kWsTile = kSub;   // workspace is sized for the smallest tile
 
 // Schedule candidates: sub-tiles per tile (tile = 4096 x SUB elements).
 constexpr int kSubCands[] = {4, 2, 1};
+static_assert(kSub * kSubCands[0] == kScanNoallocTile, "the no-alloc scan runs candidate 0");
 constexpr int kNumSubCands = 3;
 
 template <class T, int MODE, int SUB>

@@ -18,8 +18,10 @@
 namespace desc {
 namespace {
 
-// 256 bytes of header (ticket, abort flag) + 16 bytes per 4096-element tile.
-constexpr size_t kNoallocScratchBytes = 256 + size_t(DESC_SCAN_NOALLOC_MAX_ELEMS / 4096) * 16;
+// 256 bytes of header (ticket, abort flag) + one tile state per tile of
+// kScanNoallocTile elements.
+constexpr size_t kNoallocScratchBytes =
+    256 + size_t(DESC_SCAN_NOALLOC_MAX_ELEMS / kScanNoallocTile) * kScanTileStateBytes;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
 
