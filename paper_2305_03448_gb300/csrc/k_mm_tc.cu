@@ -19,6 +19,15 @@
 //                      TMEM allocation (512 columns)
 //   warps 2..5         epilogue: tcgen05.ld 32 rows x 32 columns per warp and
 //                      step (warp w reads TMEM lanes 32 (w mod 4) ...), FP32 stores
+// Pairs (mm_tc_pair_kernel, used when the 128-row tiles pair up): the two
+// CTAs of a thread-block cluster compute one 256 x 256 tile with
+// tcgen05.mma.cta_group::2 (M256 N256 K16).  Each CTA stages its own 128 rows
+// of A and its own 128 of the 256 B rows, so a stage is 32 KB instead of
+// 48 KB for the same work per SM: six stages fit, and each SM takes in a
+// third less from L2.  The even CTA issues the MMAs for both; its full
+// barriers count the bytes of both CTAs' copies, its MMA commits free the
+// stages and publish the accumulators in both CTAs, and the epilogue warps
+// of both CTAs (each reads its own 128 accumulator rows) report to it.
 // Every wait is bounded: a waiter that gives up sets an abort flag in shared
 // memory and records DESC_ERR_DEVICE_TIMEOUT; the producer then waits, again
 // with a limit, for the copies it has in flight, and TMEM is always freed.
@@ -310,6 +319,238 @@ __global__ void __launch_bounds__(kMmThreads, 1)
   if (warp == 1) tmem_dealloc(tmem, kTmemCols);
 }
 
+// ---- pairs of CTAs: cta_group::2 ---------------------------------------------
+constexpr int kPairStages = 6;
+constexpr int kPairABytes = BM * BK * 2;               // this CTA's 128 rows of A: 16 KB
+constexpr int kPairBBytes = (BN / 2) * BK * 2;         // this CTA's 128 of the 256 B rows: 16 KB
+constexpr int kPairStageBytes = kPairABytes + kPairBBytes;
+constexpr int kPairSmemBytes = kPairStages * kPairStageBytes + 1024 + 256;
+// kind::f16, FP32 accumulator, BF16 A and B, both K-major, N = 256, M = 256.
+constexpr uint32_t kIdescPair = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                                ((uint32_t)((2 * BM) >> 4) << 24);
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release;\n barrier.cluster.wait.acquire;" ::: "memory");
+}
+// Address of this CTA's shared variable `p` in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t map_rank(const void *p, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+}
+// Tile into this CTA's shared memory; the bytes are counted on the mbarrier
+// at cluster address `bar` (here: the even CTA's).
+__device__ __forceinline__ void tma_load_3d_pair(void *dst, const CUtensorMap *tm, uint32_t bar, int c0, int c1,
+                                                 int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cta.global.tile.mbarrier::complete_tx::bytes.cta_group::2"
+      " [%0], [%1, {%3, %4, %5}], [%2];"
+      ::"r"(smem_u32(dst)), "l"(tm), "r"(bar), "r"(c0), "r"(c1), "r"(c2)
+      : "memory");
+}
+__device__ __forceinline__ void umma_bf16_pair(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(kIdescPair), "r"(accumulate)
+      : "memory");
+}
+// Arrive, once the MMAs issued so far complete, on the mbarrier at the
+// offset of `bar` in both CTAs of the pair.
+__device__ __forceinline__ void umma_commit_pair_both(uint64_t *bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          smem_u32(bar)),
+      "h"((uint16_t)3)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit_pair_local(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+// One warp of each CTA of the pair takes part (same columns in both).
+__device__ __forceinline__ void tmem_alloc_pair(uint32_t *slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc_pair(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// Launched as clusters of two CTAs; `tm` and `ntiles` count 256 x 256 tiles.
+__global__ void __launch_bounds__(kMmThreads, 1)
+    mm_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                      float *__restrict__ C, int64_t M, int64_t N, int64_t ldc, int kblocks, Products prods,
+                      TileMap tm, int ntiles, int split_acc) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                                          ~uintptr_t(1023));
+  unsigned char *sA = smem;
+  unsigned char *sB = smem + kPairStages * kPairABytes;
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + kPairStages * kPairStageBytes);
+  uint64_t *empty = full + kPairStages;
+  uint64_t *tfull = empty + kPairStages;
+  uint64_t *tempty = tfull + 2;
+  uint64_t *mdone = tempty + 2;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mdone + 1);
+  volatile int *abort = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t crank = cluster_rank();
+  const bool leader = crank == 0;
+  const int cid = blockIdx.x / 2, ncl = gridDim.x / 2;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kPairStages; ++s) {
+      mbar_init(&full[s], 1);                          // even CTA: its producer + both CTAs' bytes
+      mbar_init(&empty[s], 1);                         // the even CTA's MMA commit
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&tfull[a], 1);
+      mbar_init(&tempty[a], 8);                        // even CTA: 4 epilogue warps x 2 CTAs
+    }
+    mbar_init(mdone, 1);
+    *abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) tmem_alloc_pair(tmem_slot, kTmemCols);
+  tc_fence_before();
+  cluster_sync();                                      // both CTAs' barriers exist before any remote use
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const int per_tile = kblocks * prods.n;
+  const int nsets = split_acc ? 1 : 2;
+
+  if (warp == 0) {
+    if (lane == 0) {                                   // ---- TMA producer (both CTAs)
+      int it = 0, issued = 0;
+      bool ok = true;
+      for (int t = cid; t < ntiles && ok; t += ncl) {
+        int mp, nt;
+        tile_coords(t, tm, mp, nt);
+        const int arow = mp * 2 * BM + (int)crank * BM, brow = nt * BN + (int)crank * (BN / 2);
+        for (int j = 0; j < per_tile; ++j, ++it) {
+          const int s = it % kPairStages;
+          const uint32_t ph = (it / kPairStages) & 1;
+          if (!mbar_wait(&empty[s], ph ^ 1, abort)) { ok = false; break; }
+          const int p = j / kblocks, kb = j % kblocks;
+          if (leader) mbar_expect_tx(&full[s], 2 * kPairStageBytes);
+          const uint32_t fb = map_rank(&full[s], 0);
+          tma_load_3d_pair(sA + s * kPairABytes, &tmA, fb, kb * BK, arow, prods.pa[p]);
+          tma_load_3d_pair(sB + s * kPairBBytes, &tmB, fb, kb * BK, brow, prods.pb[p]);
+          issued = it + 1;
+        }
+      }
+      // Before leaving: every issued stage consumed (its MMAs, which read this
+      // CTA's shared memory, are done) -- bounded.
+      const long long t0 = clock64();
+      for (int i = std::max(0, issued - kPairStages); i < issued; ++i)
+        while (!mbar_try_wait(&empty[i % kPairStages], (i / kPairStages) & 1) && clock64() - t0 < kWaitBudget) {
+        }
+    }
+  } else if (warp == 1) {
+    if (lane == 0 && leader) {                         // ---- MMA issuer (even CTA only)
+      const int half = kblocks / 2;
+      int it = 0, li = 0;
+      bool ok = true, issued_any = false;
+      for (int t = cid; t < ntiles && ok; t += ncl, ++li) {
+        const int si = li % nsets;
+        const uint32_t use = (uint32_t)(li / nsets);
+        if (!mbar_wait(&tempty[si], (use & 1) ^ 1, abort)) break;   // both epilogues drained this set
+        tc_fence_after();
+        for (int j = 0; j < per_tile; ++j, ++it) {
+          const int s = it % kPairStages;
+          const uint32_t ph = (it / kPairStages) & 1;
+          if (!mbar_wait(&full[s], ph, abort)) { ok = false; break; }
+          tc_fence_after();
+          const int p = j / kblocks, kb = j % kblocks;
+          int acc;
+          bool first;
+          if (split_acc) {                             // K halves in two accumulators
+            acc = (half > 0 && kb >= half) ? 1 : 0;
+            first = p == 0 && kb == (acc ? half : 0);
+          } else {
+            acc = si;
+            first = j == 0;
+          }
+          const uint32_t d = tmem + (uint32_t)(acc * BN);
+          const uint32_t a0 = smem_u32(sA + s * kPairABytes), b0 = smem_u32(sB + s * kPairBBytes);
+#pragma unroll
+          for (int k = 0; k < BK / UK; ++k)
+            umma_bf16_pair(d, sdesc(a0 + k * UK * 2), sdesc(b0 + k * UK * 2), (first && k == 0) ? 0u : 1u);
+          umma_commit_pair_both(&empty[s]);            // both CTAs' stage s reusable after these MMAs
+          issued_any = true;
+        }
+        if (ok) umma_commit_pair_both(&tfull[si]);     // accumulators complete in both CTAs
+      }
+      if (issued_any) {                                // every MMA finished before TMEM is freed (bounded)
+        umma_commit_pair_local(mdone);
+        const long long t0 = clock64();
+        while (!mbar_try_wait(mdone, 0) && clock64() - t0 < kWaitBudget) {
+        }
+      }
+    }
+  } else {                                             // ---- epilogue, warps 2..5 (both CTAs)
+    const int q = warp & 3;                            // TMEM lanes 32 q .. 32 q + 31
+    const bool vec = ((ldc & 3) == 0) && ((reinterpret_cast<uintptr_t>(C) & 15) == 0);
+    const bool two = split_acc && kblocks / 2 > 0;
+    int li = 0;
+    for (int t = cid; t < ntiles; t += ncl, ++li) {
+      const int si = li % nsets;
+      const uint32_t use = (uint32_t)(li / nsets);
+      if (!mbar_wait(&tfull[si], use & 1, abort)) break;
+      tc_fence_after();
+      int mp, nt;
+      tile_coords(t, tm, mp, nt);
+      const int64_t row = int64_t(mp) * 2 * BM + int64_t(crank) * BM + q * 32 + lane;
+      const int64_t n0 = int64_t(nt) * BN;
+      const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(split_acc ? 0 : si * BN);
+#pragma unroll 1
+      for (int c = 0; c < BN / 32; ++c) {
+        uint32_t r[32];
+        tmem_ld32(base + (uint32_t)(c * 32), r);
+        if (two) {
+          uint32_t r1[32];
+          tmem_ld32(base + (uint32_t)(BN + c * 32), r1);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) r[j] = __float_as_uint(__fadd_rn(__uint_as_float(r[j]), __uint_as_float(r1[j])));
+        }
+        const int64_t col = n0 + c * 32;
+        if (row < M) {
+          float *dst = C + row * ldc + col;
+          if (vec && col + 32 <= N) {
+#pragma unroll
+            for (int j = 0; j < 32; j += 4)
+              __stcs(reinterpret_cast<float4 *>(dst + j),
+                     make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]), __uint_as_float(r[j + 2]),
+                                 __uint_as_float(r[j + 3])));
+          } else {
+            for (int j = 0; j < 32; ++j)
+              if (col + j < N) dst[j] = __uint_as_float(r[j]);
+          }
+        }
+      }
+      tc_fence_before();                               // TMEM reads done before the set is reused
+      __syncwarp();
+      if (lane == 0) mbar_arrive_cluster(map_rank(&tempty[si], 0));
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync();                                      // both CTAs done with TMEM and each other's barriers
+  if (warp == 1) tmem_dealloc_pair(tmem, kTmemCols);
+  cluster_sync();                                      // neither CTA of the pair leaves first
+}
+
 // ---- split pass: FP32 source (any 2-D strides) -> P BF16 planes, zero padded
 // Output plane p is R x Kc row-major (R rows padded to Rp); element (r, c) of
 // the logical source is src[off + r * sr + c * sc].  Planes: p = 0 holds
@@ -427,8 +668,11 @@ int32_t launch_mm_tc(const float *A, int64_t a_off, int64_t a_sr, int64_t a_sc, 
   split_planes_kernel<<<dim3((unsigned)((Kp + kTT - 1) / kTT), (unsigned)((Np + kTT - 1) / kTT)), 256, 0, s>>>(
       B, b_off, b_sc, b_sr, N, K, Np, Kp, planes, pB);
   DESC_CUDA_TRY(cudaGetLastError());
+  const int Mt = (int)(Mp / BM);
+  const bool pairs = Mt % 2 == 0;                      // 128-row tiles pair up: cta_group::2
   CUtensorMap tmA, tmB;
-  if (!make_map(&tmA, pA, planes, Mp, Kp, BM) || !make_map(&tmB, pB, planes, Np, Kp, BN)) return DESC_ERR_CUDA;
+  if (!make_map(&tmA, pA, planes, Mp, Kp, BM) || !make_map(&tmB, pB, planes, Np, Kp, pairs ? BN / 2 : BN))
+    return DESC_ERR_CUDA;
   Products pr{};
   pr.n = nprod;
   for (int i = 0; i < nprod; ++i) {
@@ -436,23 +680,62 @@ int32_t launch_mm_tc(const float *A, int64_t a_off, int64_t a_sr, int64_t a_sc, 
     pr.pb[i] = pb[i];
   }
   static bool attr = false;
-  static int nsm = 0;
+  static int nsm = 0, max_pairs = 0;
   if (!attr) {
     DESC_CUDA_TRY(cudaFuncSetAttribute(mm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
+    DESC_CUDA_TRY(
+        cudaFuncSetAttribute(mm_tc_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kPairSmemBytes));
     int dev = 0;
     DESC_CUDA_TRY(cudaGetDevice(&dev));
     DESC_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    // Pairs resident at once (an SM without a partner in its GPC stays idle).
+    cudaLaunchConfig_t q{};
+    cudaLaunchAttribute qa[1];
+    qa[0].id = cudaLaunchAttributeClusterDimension;
+    qa[0].val.clusterDim.x = 2;
+    qa[0].val.clusterDim.y = 1;
+    qa[0].val.clusterDim.z = 1;
+    q.gridDim = dim3(2 * (unsigned)std::max(nsm / 2, 1));
+    q.blockDim = dim3(kMmThreads);
+    q.dynamicSmemBytes = kPairSmemBytes;
+    q.attrs = qa;
+    q.numAttrs = 1;
+    DESC_CUDA_TRY(cudaOccupancyMaxActiveClusters(&max_pairs, mm_tc_pair_kernel, &q));
     attr = true;
   }
-  TileMap tmap;
-  tmap.Mt = (int)(Mp / BM);
+  TileMap tmap;                                        // over 128 x 256 tiles, or 256 x 256 pair tiles
+  tmap.Mt = pairs ? Mt / 2 : Mt;
   tmap.Nt = (int)(Np / BN);
-  tmap.group_m = std::min(tmap.Mt, kGroupM);
+  tmap.group_m = std::min(tmap.Mt, pairs ? kGroupM / 2 : kGroupM);
   const int64_t ntiles = int64_t(tmap.Mt) * tmap.Nt;
   if (ntiles >= (int64_t(1) << 31)) return DESC_ERR_UNSUPPORTED;
-  const int grid = (int)std::min<int64_t>(ntiles, std::max(nsm, 1));
-  mm_tc_kernel<<<grid, kMmThreads, kSmemBytes, s>>>(tmA, tmB, C, M, N, N, (int)(Kp / BK), pr, tmap, (int)ntiles,
-                                                     planes > 1 ? 1 : 0);
+  const int kblocks = (int)(Kp / BK), split = planes > 1 ? 1 : 0;
+  if (!pairs || max_pairs < 1) {
+    if (pairs) {                                       // no pair fits: the single-CTA map of B
+      tmap.Mt = Mt;
+      tmap.group_m = std::min(Mt, kGroupM);
+      if (!make_map(&tmB, pB, planes, Np, Kp, BN)) return DESC_ERR_CUDA;
+    }
+    const int64_t nt1 = int64_t(tmap.Mt) * tmap.Nt;
+    const int grid = (int)std::min<int64_t>(nt1, std::max(nsm, 1));
+    mm_tc_kernel<<<grid, kMmThreads, kSmemBytes, s>>>(tmA, tmB, C, M, N, N, kblocks, pr, tmap, (int)nt1, split);
+  } else {
+    const int npairs = (int)std::min<int64_t>(ntiles, max_pairs);
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute la[1];
+    la[0].id = cudaLaunchAttributeClusterDimension;
+    la[0].val.clusterDim.x = 2;
+    la[0].val.clusterDim.y = 1;
+    la[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(2 * (unsigned)npairs);
+    cfg.blockDim = dim3(kMmThreads);
+    cfg.dynamicSmemBytes = kPairSmemBytes;
+    cfg.stream = s;
+    cfg.attrs = la;
+    cfg.numAttrs = 1;
+    DESC_CUDA_TRY(cudaLaunchKernelEx(&cfg, mm_tc_pair_kernel, tmA, tmB, C, M, N, N, kblocks, pr, tmap, (int)ntiles,
+                                     split));
+  }
   DESC_CUDA_TRY(cudaGetLastError());
   return DESC_OK;
 }

@@ -28,7 +28,10 @@ def mats(M, N, K, seed):
     return A, B
 
 
-SHAPES = [(128, 256, 64), (256, 512, 128), (100, 300, 70), (1, 1, 1), (257, 513, 129), (384, 256, 1024)]
+# Tile rows (128) odd or even: even counts run as pairs of CTAs sharing B;
+# (4096, 2048, 256) gives each pair of an SM pair several tiles in turn.
+SHAPES = [(128, 256, 64), (256, 512, 128), (100, 300, 70), (1, 1, 1), (257, 513, 129), (384, 256, 1024),
+          (1000, 700, 300), (4096, 2048, 256)]
 
 
 @pytest.mark.parametrize("M,N,K", SHAPES)
