@@ -112,6 +112,11 @@ class Clocks:
                 "samples": len(win), "window": "timed" if len(win) < len(rows) or t1 - t0 > 0.05 else "run"}
 
 
+def _gpu_uuid(torch, dev):
+    u = getattr(torch.cuda.get_device_properties(dev), "uuid", None)
+    return str(u) if u else None
+
+
 # --------------------------------------------------------------------- ours
 def run_ours(args, rank, world, local_rank):
     import torch
@@ -185,8 +190,7 @@ def run_ours(args, rank, world, local_rank):
     ev = {name: [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
           for name, _ in ops}
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    clocks = Clocks(getattr(torch.cuda.get_device_properties(dev), "uuid", None) and
-                    str(torch.cuda.get_device_properties(dev).uuid)) if rank == 0 else None
+    clocks = Clocks(_gpu_uuid(torch, dev)) if rank == 0 else None
     if clocks:
         clocks.start()
         time.sleep(0.3)
@@ -308,7 +312,7 @@ def _time(torch, stream, fn, reps):
     return a.elapsed_time(b) / reps
 
 
-def run_matmul(torch, D, dev, stream, pk, n=8192):
+def run_matmul(torch, D, dev, stream, pk, n=8192, forms=("split3", "bf16", "fp32_simt"), quick=False):
     """C = A B at M = N = K = 8192, FP32 N(0,1) inputs: time of one call
     (split pass included), effective TFLOP/s (2 n^3 / t), tensor TFLOP/s
     (products x 2 n^3 / t) against the dense BF16 peak, and the relative
@@ -324,14 +328,35 @@ def run_matmul(torch, D, dev, stream, pk, n=8192):
            "peak_source": f"bf16_tflops (burst, of {pk['source']})"}
     for name, p, nprod, reps in (("split3", D.MM_SPLIT3, 6, 5), ("bf16", D.MM_BF16, 1, 10),
                                  ("fp32_simt", D.MM_FP32_SIMT, 1, 2)):
+        if name not in forms:
+            continue
+        if quick:
+            reps = 1
         nb = ctypes.c_size_t(0)
         D.lib().desc_matmul_workspace_size(n, n, n, p, ctypes.byref(nb))
         ws = torch.empty(max(nb.value, 1), dtype=torch.uint8, device=dev)
         ms = _time(torch, stream, lambda: D.desc_matmul(A, B, p, out=C, ws=ws, stream=stream), reps)
+        # the same call back to back for about 0.4 s, with the SM clock sampled
+        ms_long, clk = ms, None
+        if not quick and p != D.MM_FP32_SIMT:
+            ck = Clocks(_gpu_uuid(torch, dev))
+            ck.start()
+            time.sleep(0.2)
+            t0 = time.time()
+            ms_long = _time(torch, stream, lambda: D.desc_matmul(A, B, p, out=C, ws=ws, stream=stream),
+                            max(reps, int(400 / max(ms, 1e-3))))
+            t1 = time.time()
+            clk = ck.stop(t0, t1)
         got = C[rows].double().cpu()
         err = float(torch.linalg.norm(got - ref) / torch.linalg.norm(ref))
         eff = 2 * n ** 3 / (ms * 1e-3) / 1e12
         r = {"ms": round(ms, 4), "effective_tflops": round(eff, 1), "rel_frobenius_err": float(f"{err:.3e}")}
+        if p != D.MM_FP32_SIMT:
+            eff_long = 2 * n ** 3 / (ms_long * 1e-3) / 1e12
+            r["sustained"] = {"ms": round(ms_long, 4), "tensor_tflops": round(nprod * eff_long, 1),
+                              "frac_of_bf16_sustained_peak": round(nprod * eff_long / pk["bf16_tflops_sustained"], 4)}
+            if clk:
+                r["sustained"]["clocks"] = {k: clk[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")}
         if p != D.MM_FP32_SIMT:
             r["tensor_tflops"] = round(nprod * eff, 1)
             r["frac_of_bf16_peak"] = round(nprod * eff / pk["bf16_tflops"], 4)
@@ -536,6 +561,10 @@ def main():
     ap.add_argument("--case", choices=["step", "matmul", "segmented"], default="step",
                     help="matmul / segmented: run only that measurement (for profiler captures)")
     ap.add_argument("--mm-n", type=int, default=8192, help="matmul size for --case matmul")
+    ap.add_argument("--mm-prec", default="split3,bf16,fp32_simt",
+                    help="matmul forms for --case matmul (comma list of split3, bf16, fp32_simt)")
+    ap.add_argument("--mm-quick", action="store_true",
+                    help="--case matmul: one warm-up and one timed call per form, no sustained loop")
     ap.add_argument("--seg-count", type=int, default=20000, help="segments for --case segmented")
     args = ap.parse_args()
     if args.warmup < 3 and not args.small:
@@ -560,7 +589,8 @@ def main():
         torch.cuda.set_device(dev)
         stream = torch.cuda.current_stream(dev)
         if args.case == "matmul":
-            line = {"case": "matmul", "matmul": run_matmul(torch, D, dev, stream, peaks(), n=args.mm_n)}
+            line = {"case": "matmul", "matmul": run_matmul(torch, D, dev, stream, peaks(), n=args.mm_n,
+                                                           forms=args.mm_prec.split(","), quick=args.mm_quick)}
         else:
             line = {"case": "segmented", "segmented": run_segmented(torch, D, synth, dev, stream, nseg=args.seg_count)}
     else:
