@@ -254,6 +254,7 @@ def run_ours(args, rank, world, local_rank):
     if not args.no_extras and not args.small:
         line["matmul"] = run_matmul(torch, D, dev, stream, pk)
         line["segmented"] = run_segmented(torch, D, synth, dev, stream)
+        line["view_overhead"] = run_view_overhead(torch, D, synth, dev, stream)
         if not args.no_model:
             line["schedule_model"] = run_schedule_model(torch, D, synth)
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -364,6 +365,86 @@ def run_matmul(torch, D, dev, stream, pk, n=8192, forms=("split3", "bf16", "fp32
         del ws
     if D.desc_stream_status(stream) != 0:
         raise RuntimeError("device status after matmul")
+    return out
+
+
+def run_view_overhead(torch, D, synth, dev, stream, reps=100, mbs=(256, 512, 1024)):
+    """Section 5's overhead experiment on this GPU: each op through its view,
+    once with the hand-indexed kernel the lowering selects and once through
+    the general kernels that evaluate the lowered affine map element by
+    element (desc_force_generic).  Sizes are input bytes (256 MB, 512 MB,
+    1 GB); each time is the median of `reps` launches (CUDA events)."""
+    import ctypes
+    V = D
+
+    def med(fn):
+        fn()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for a, b in ev:
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize()
+        d = sorted(a.elapsed_time(b) for a, b in ev)
+        return d[len(d) // 2]
+
+    def ws_of(query):
+        n = ctypes.c_size_t(0)
+        query(ctypes.byref(n))
+        return torch.empty(max(n.value, 1), dtype=torch.uint8, device=dev)
+
+    red_ops = [("group", 1024, 0), ("select", V.BLOCK, V.X), ("group", 32, 0), ("select", V.WARP, V.X),
+               ("select", V.THREAD, V.X)]
+    out = {"reps": reps, "sizes": "input bytes", "views": {
+        "reduce": "int32, group(1024)[[block]].group(32)[[warp]][[thread]] -> one scalar",
+        "scan": "FP32 inclusive scan of the whole array",
+        "transpose": "FP32 R x C -> C x R, transpose view on the input"}}
+    L = D.lib()
+    for mb in mbs:
+        n = mb * (1 << 20) // 4
+        row = {}
+        x = synth.ints_pm1000(n, seed=11, device=dev)
+        r = torch.empty(1, dtype=torch.int32, device=dev)
+        grid, block = (n // 1024, 1, 1), (1024, 1, 1)
+        t = {}
+        for gen in (False, True):
+            D.desc_force_generic(gen)
+            ws = ws_of(lambda b: L.desc_reduce_workspace_size(ctypes.byref(D.make_view([n], red_ops)),
+                                                              ctypes.byref(D.make_exec(grid, block)), V.GRID,
+                                                              V.I32, b))
+            t[gen] = med(lambda: D.desc_reduce(x, [n], red_ops, V.GRID, grid, block, out=r, ws=ws, stream=stream))
+            del ws
+        D.desc_force_generic(False)
+        row["reduce"] = t
+        del x
+        xs = synth.uniform_grid(n, seed=12, device=dev)
+        ys = torch.empty_like(xs)
+        t = {}
+        for gen in (False, True):
+            D.desc_force_generic(gen)
+            ws = ws_of(lambda b: L.desc_scan_workspace_size(ctypes.byref(D.make_view([n], [])), None, V.GRID,
+                                                            V.F32, b))
+            t[gen] = med(lambda: D.desc_scan(xs, [n], [], V.GRID, out=ys, ws=ws, stream=stream))
+            del ws
+        D.desc_force_generic(False)
+        row["scan"] = t
+        del xs, ys
+        R = 1 << ((n.bit_length() - 1) // 2)
+        C = n // R
+        xt = synth.normal_f32(n, seed=13, device=dev).reshape(R, C)
+        yt = torch.empty(C, R, device=dev)
+        t = {}
+        for gen in (False, True):
+            D.desc_force_generic(gen)
+            t[gen] = med(lambda: D.desc_transpose(xt, [R, C], [("transpose", 0)], yt, [C, R], [], stream=stream))
+        D.desc_force_generic(False)
+        row["transpose"] = t
+        del xt, yt
+        out[f"{mb}MB"] = {k: {"hand_indexed_ms": round(v[False], 4), "generic_ms": round(v[True], 4),
+                              "overhead_pct": round(100 * (v[True] / v[False] - 1), 1)} for k, v in row.items()}
+    if D.desc_stream_status(stream) != 0:
+        raise RuntimeError("device status after the view-overhead runs")
     return out
 
 
@@ -558,7 +639,7 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="time the default schedules, without autotuning")
     ap.add_argument("--save-tune", default="", help="save the tuned schedule table to this file")
     ap.add_argument("--load-tune", default="", help="use a saved schedule table instead of tuning")
-    ap.add_argument("--case", choices=["step", "matmul", "segmented"], default="step",
+    ap.add_argument("--case", choices=["step", "matmul", "segmented", "overhead"], default="step",
                     help="matmul / segmented: run only that measurement (for profiler captures)")
     ap.add_argument("--mm-n", type=int, default=8192, help="matmul size for --case matmul")
     ap.add_argument("--mm-prec", default="split3,bf16,fp32_simt",
@@ -591,6 +672,8 @@ def main():
         if args.case == "matmul":
             line = {"case": "matmul", "matmul": run_matmul(torch, D, dev, stream, peaks(), n=args.mm_n,
                                                            forms=args.mm_prec.split(","), quick=args.mm_quick)}
+        elif args.case == "overhead":
+            line = {"case": "overhead", "view_overhead": run_view_overhead(torch, D, synth, dev, stream)}
         else:
             line = {"case": "segmented", "segmented": run_segmented(torch, D, synth, dev, stream, nseg=args.seg_count)}
     else:

@@ -382,6 +382,20 @@ int32_t desc_tune_load(const char *path);
  * (-1: back to the table). */
 int32_t desc_force_candidate(int32_t op, int32_t cand);
 
+/* ---- View-overhead switch --------------------------------------------
+ * Section 5 compares kernels whose indexing comes from views with
+ * hand-indexed CUDA of the same operations.  Here every view is lowered to
+ * an affine map; where that map has a simple form (contiguous runs, a 2-D
+ * transposition) a hand-indexed kernel runs, and otherwise a general kernel
+ * evaluates the map element by element.  With `on` != 0 the calling thread's
+ * desc_reduce, desc_scan and desc_transpose calls (and their workspace
+ * queries) take the general path even where a hand-indexed kernel applies:
+ * reduce through the affine reduction kernel, scan through an affine gather
+ * into the workspace, the scan and an affine scatter, transpose through the
+ * affine copy kernel.  Results are the same; only the time differs.  Query
+ * the workspace with the same setting as the call.  Returns DESC_OK. */
+int32_t desc_force_generic(int32_t on);
+
 /* ---- Cost model: 3-layer MLP on the GPU ------------------------------------
  * y = w3 . relu(W2 relu(W1 x + b1) + b2) + b3 predicts log(time in us) of a
  * (problem, candidate) feature row; loss = mean squared error.  Parameters are

@@ -132,6 +132,7 @@ def _declare(L):
         "desc_tune_save": (c_int32, [c_char_p]),
         "desc_tune_load": (c_int32, [c_char_p]),
         "desc_force_candidate": (c_int32, [c_int32, c_int32]),
+        "desc_force_generic": (c_int32, [c_int32]),
         "desc_mlp_param_count": (c_int32, [c_int32, c_int32, POINTER(c_int64)]),
         "desc_mlp_workspace_size": (c_int32, [c_int32, c_int32, c_int64, POINTER(c_size_t)]),
         "desc_mlp_forward": (c_int32, [P, c_int32, c_int32, P, c_int64, P, P, c_size_t, P]),
@@ -452,6 +453,12 @@ def desc_features(problem: Problem, cand: int):
 
 def desc_force_candidate(op, cand):
     _check(lib().desc_force_candidate(int(op), int(cand)), "desc_force_candidate")
+
+
+def desc_force_generic(on):
+    """Evaluate this thread's reduce / scan / transpose views through the
+    general affine-map kernels (the view-overhead experiment's other arm)."""
+    _check(lib().desc_force_generic(1 if on else 0), "desc_force_generic")
 
 
 def desc_tune_record(problem, cand):

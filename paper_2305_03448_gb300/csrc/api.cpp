@@ -57,6 +57,15 @@ int32_t check_writes(const desc_lowered &w, const desc_exec *ex) {
 
 }  // namespace
 
+// Per-thread switch: evaluate every view through the general affine kernels.
+namespace {
+thread_local bool t_generic = false;
+}
+extern "C" int32_t desc_force_generic(int32_t on) {
+  t_generic = on != 0;
+  return DESC_OK;
+}
+
 // ---------------------------------------------------------------- reduce
 extern "C" int32_t desc_reduce_workspace_size(const desc_view *v, const desc_exec *ex,
                                               int32_t out_level, int32_t dtype, size_t *bytes) {
@@ -67,8 +76,8 @@ extern "C" int32_t desc_reduce_workspace_size(const desc_view *v, const desc_exe
   if (r != DESC_OK) return r;
   const Plan p = split_plan(L, out_level);
   int64_t start0, seg;
-  *bytes = rest_contiguous(p, true, &start0, &seg) ? reduce_segments_ws(dtype, p.n_rest, p.n_keep)
-                                                   : reduce_affine_ws(p.n_rest, p.n_keep);
+  *bytes = (!t_generic && rest_contiguous(p, true, &start0, &seg)) ? reduce_segments_ws(dtype, p.n_rest, p.n_keep)
+                                                                   : reduce_affine_ws(p.n_rest, p.n_keep);
   return DESC_OK;
 }
 
@@ -95,7 +104,7 @@ extern "C" int32_t desc_reduce(const desc_view *v, const desc_exec *ex, int32_t 
     return DESC_OK;
   }
   int64_t start0, seg;
-  if (rest_contiguous(p, true, &start0, &seg))
+  if (!t_generic && rest_contiguous(p, true, &start0, &seg))
     return launch_reduce_segments(dtype, in, start0, seg, p.n_rest, p.n_keep, out, flags, ws,
                                   ws_bytes, s,
                                   schedule_for(DESC_OP_REDUCE, dtype, p.n_rest * p.n_keep,
@@ -115,7 +124,7 @@ ScanPlan plan_scan(const desc_lowered &L, int32_t seg_level) {
   const Plan p = split_plan(L, seg_level);
   ScanPlan sp{false, 0, p.n_keep * p.n_rest, p.n_rest};
   int64_t start0, seg;
-  if (rest_contiguous(p, false, &start0, &seg) && (p.n_keep <= 1 || seg == p.n_rest)) {
+  if (!t_generic && rest_contiguous(p, false, &start0, &seg) && (p.n_keep <= 1 || seg == p.n_rest)) {
     sp.contig = true;
     sp.start = start0;
   }
@@ -237,7 +246,7 @@ extern "C" int32_t desc_transpose(const desc_view *in_v, const desc_view *out_v,
   std::vector<D> d;
   for (int i = 0; i < Li.ndims; ++i)
     if (Li.extent[i] > 1) d.push_back({Li.extent[i], Li.stride[i], Lo.stride[i]});
-  bool pos = true;
+  bool pos = !t_generic;
   for (auto &x : d) pos = pos && x.so > 0;
   if (pos) {
     std::sort(d.begin(), d.end(), [](const D &a, const D &b) { return a.so > b.so; });

@@ -95,4 +95,51 @@ __device__ __forceinline__ void block_merge(A &a, A *sh) {
   }
 }
 
+// ---- affine maps evaluated element by element --------------------------
+// Unsigned 32-bit division by a divisor fixed for the whole launch, by one
+// multiply-high and shifts (Granlund and Montgomery, "Division by Invariant
+// Integers using Multiplication", PLDI 1994, Figure 4.1): with
+// l = ceil(log2 d) and m = floor(2^32 (2^l - d) / d) + 1,
+// n / d = (t + ((n - t) >> min(l, 1))) >> max(l - 1, 0), t = mulhi(m, n),
+// for every 32-bit n and 1 <= d <= 2^31.
+struct FastDiv {
+  uint32_t d, m, s1, s2;
+};
+inline FastDiv make_fastdiv(uint32_t d) {
+  uint32_t l = 0;
+  while (l < 32 && (uint64_t(1) << l) < d) ++l;
+  FastDiv f;
+  f.d = d;
+  f.m = (uint32_t)((((uint64_t(1) << l) - d) << 32) / d + 1);
+  f.s1 = l < 1 ? l : 1;
+  f.s2 = l > 1 ? l - 1 : 0;
+  return f;
+}
+__device__ __forceinline__ uint32_t fast_div(uint32_t n, const FastDiv &f) {
+  const uint32_t t = __umulhi(f.m, n);
+  return (t + ((n - t) >> f.s1)) >> f.s2;
+}
+
+// Drops extent-1 dims and merges neighbours that every stride set walks as
+// one (outer stride = inner stride x inner extent), keeping the row-major
+// logical order of the points.  ext/st[k] are arrays of nd entries; returns
+// the new nd.
+inline int canon_dims(int nd, int64_t *ext, int64_t *const *st, int nsets) {
+  int m = 0;
+  for (int i = 0; i < nd; ++i) {
+    if (ext[i] == 1) continue;
+    bool merge = m > 0;
+    for (int k = 0; k < nsets && merge; ++k) merge = st[k][m - 1] == st[k][i] * ext[i];
+    if (merge) {
+      ext[m - 1] *= ext[i];
+      for (int k = 0; k < nsets; ++k) st[k][m - 1] = st[k][i];
+    } else {
+      ext[m] = ext[i];
+      for (int k = 0; k < nsets; ++k) st[k][m] = st[k][i];
+      ++m;
+    }
+  }
+  return m;
+}
+
 }  // namespace desc

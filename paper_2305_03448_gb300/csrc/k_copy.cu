@@ -63,20 +63,39 @@ struct CopyArgs {
   int64_t extent[DESC_MAX_DIMS];
   int64_t istride[DESC_MAX_DIMS];
   int64_t ostride[DESC_MAX_DIMS];
+  FastDiv div[DESC_MAX_DIMS];   // FAST: the extents as 32-bit invariant divisors
   int64_t ioff, ooff, total;
 };
 
+// One point per thread and step, decoded from its row-major logical index.
+// FAST (fewer than 2^32 points, every extent <= 2^31): 32-bit decoding by
+// multiply-high; otherwise 64-bit division.
+template <bool FAST>
 __global__ void __launch_bounds__(256) copy_affine_kernel(const uint32_t *__restrict__ in,
                                                           uint32_t *__restrict__ out,
                                                           const CopyArgs a) {
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
   for (int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; q < a.total; q += stride) {
-    int64_t t = q, ie = a.ioff, oe = a.ooff;
-    for (int d = a.nd - 1; d >= 0; --d) {
-      const int64_t c = t % a.extent[d];
-      t /= a.extent[d];
-      ie += c * a.istride[d];
-      oe += c * a.ostride[d];
+    int64_t ie = a.ioff, oe = a.ooff;
+    if (FAST) {
+      uint32_t t = (uint32_t)q;
+      for (int d = a.nd - 1; d > 0; --d) {
+        const uint32_t qd = fast_div(t, a.div[d]);
+        const int64_t c = int64_t(t - qd * a.div[d].d);
+        ie += c * a.istride[d];
+        oe += c * a.ostride[d];
+        t = qd;
+      }
+      ie += int64_t(t) * a.istride[0];
+      oe += int64_t(t) * a.ostride[0];
+    } else {
+      int64_t t = q;
+      for (int d = a.nd - 1; d >= 0; --d) {
+        const int64_t c = t % a.extent[d];
+        t /= a.extent[d];
+        ie += c * a.istride[d];
+        oe += c * a.ostride[d];
+      }
     }
     out[oe] = in[ie];
   }
@@ -114,7 +133,6 @@ int32_t launch_copy_affine(const void *in, int64_t ioff, const int64_t *istride,
                            desc_stream_t st) {
   cudaStream_t s = reinterpret_cast<cudaStream_t>(st);
   CopyArgs a{};
-  a.nd = nd;
   a.total = 1;
   for (int i = 0; i < nd; ++i) {
     a.extent[i] = extent[i];
@@ -125,9 +143,25 @@ int32_t launch_copy_affine(const void *in, int64_t ioff, const int64_t *istride,
   a.ioff = ioff;
   a.ooff = ooff;
   if (a.total == 0) return DESC_OK;
+  int64_t *sets[2] = {a.istride, a.ostride};
+  a.nd = canon_dims(nd, a.extent, sets, 2);
+  if (a.nd == 0) {                                     // a single point
+    a.nd = 1;
+    a.extent[0] = 1;
+    a.istride[0] = a.ostride[0] = 0;
+  }
+  bool fast = a.total < (int64_t(1) << 32);
+  for (int i = 0; i < a.nd; ++i) {
+    fast = fast && a.extent[i] <= (int64_t(1) << 31);
+    if (fast) a.div[i] = make_fastdiv((uint32_t)a.extent[i]);
+  }
   const int64_t ctas = std::min<int64_t>((a.total + 255) / 256, 152 * 16);
-  copy_affine_kernel<<<(unsigned)ctas, 256, 0, s>>>(static_cast<const uint32_t *>(in),
-                                                    static_cast<uint32_t *>(out), a);
+  if (fast)
+    copy_affine_kernel<true><<<(unsigned)ctas, 256, 0, s>>>(static_cast<const uint32_t *>(in),
+                                                            static_cast<uint32_t *>(out), a);
+  else
+    copy_affine_kernel<false><<<(unsigned)ctas, 256, 0, s>>>(static_cast<const uint32_t *>(in),
+                                                             static_cast<uint32_t *>(out), a);
   DESC_CUDA_TRY(cudaGetLastError());
   return DESC_OK;
 }

@@ -15,6 +15,8 @@
 // plain or compensated (Neumaier) FP32.
 #include <algorithm>
 
+#include <type_traits>
+
 #include "k_common.cuh"
 
 namespace desc {
@@ -180,11 +182,18 @@ struct AffineArgs {
   int32_t nkeep, nrest;
   int64_t keep_ext[DESC_MAX_DIMS], keep_st[DESC_MAX_DIMS];
   int64_t rest_ext[DESC_MAX_DIMS], rest_st[DESC_MAX_DIMS];
+  FastDiv rest_div[DESC_MAX_DIMS];   // FAST: the summed extents as 32-bit invariant divisors
   int64_t offset, n_rest;
 };
 
-// One CTA per (output, chunk) over an arbitrary affine map.
-template <class A, class T>
+// One CTA per (output, chunk) over an arbitrary affine map; each point's
+// element is decoded from its row-major index over the summed dims.  FAST
+// (fewer than 2^32 summed points, extents <= 2^31): 32-bit decoding by
+// multiply-high; otherwise 64-bit division.
+// VEC (with FAST): the innermost summed dim is contiguous, its extent, the
+// other strides and the offset are multiples of 4 and `in` is 16-byte
+// aligned, so points go in groups of 4 with one 128-bit load each.
+template <class A, class T, bool FAST, bool VEC>
 __global__ void __launch_bounds__(kThreads) reduce_affine_kernel(
     const T *__restrict__ in, const AffineArgs args, int64_t chunks, int64_t chunk_len,
     T *__restrict__ out, uint2 *partials, unsigned *counters) {
@@ -198,11 +207,47 @@ __global__ void __launch_bounds__(kThreads) reduce_affine_kernel(
   A a;
   a.init();
   const int64_t q1 = std::min<int64_t>(args.n_rest, (c + 1) * chunk_len);
+  if (VEC) {
+    using V4 = typename std::conditional<std::is_same<T, float>::value, float4, int4>::type;
+    constexpr int U = 4;                               // groups in flight per thread
+    for (int64_t q0 = c * chunk_len + 4 * threadIdx.x; q0 < q1; q0 += 4 * U * kThreads) {
+      V4 v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t q = q0 + int64_t(u) * 4 * kThreads;
+        if (q < q1) {
+          int64_t e = base;
+          uint32_t t = (uint32_t)q;
+          for (int d = args.nrest - 1; d > 0; --d) {
+            const uint32_t qd = fast_div(t, args.rest_div[d]);
+            e += int64_t(t - qd * args.rest_div[d].d) * args.rest_st[d];
+            t = qd;
+          }
+          e += int64_t(t) * args.rest_st[0];
+          v[u] = __ldcs(reinterpret_cast<const V4 *>(in + e));
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (q0 + int64_t(u) * 4 * kThreads < q1) a.add4(v[u]);
+    }
+  } else
   for (int64_t q = c * chunk_len + threadIdx.x; q < q1; q += kThreads) {
-    int64_t e = base, t = q;
-    for (int d = args.nrest - 1; d >= 0; --d) {
-      e += (t % args.rest_ext[d]) * args.rest_st[d];
-      t /= args.rest_ext[d];
+    int64_t e = base;
+    if (FAST) {
+      uint32_t t = (uint32_t)q;
+      for (int d = args.nrest - 1; d > 0; --d) {
+        const uint32_t qd = fast_div(t, args.rest_div[d]);
+        e += int64_t(t - qd * args.rest_div[d].d) * args.rest_st[d];
+        t = qd;
+      }
+      e += int64_t(t) * args.rest_st[0];
+    } else {
+      int64_t t = q;
+      for (int d = args.nrest - 1; d >= 0; --d) {
+        e += (t % args.rest_ext[d]) * args.rest_st[d];
+        t /= args.rest_ext[d];
+      }
     }
     a.add1(in[e]);
   }
@@ -265,14 +310,30 @@ template <class A, class T>
 int32_t run_affine(const T *in, const Plan &p, T *out, void *ws, size_t ws_bytes, cudaStream_t s) {
   AffineArgs a;
   a.nkeep = p.nkeep;
-  a.nrest = p.nrest;
   for (int i = 0; i < p.nkeep; ++i) { a.keep_ext[i] = p.keep[i].extent; a.keep_st[i] = p.keep[i].stride; }
   for (int i = 0; i < p.nrest; ++i) { a.rest_ext[i] = p.rest[i].extent; a.rest_st[i] = p.rest[i].stride; }
+  int64_t *sets[1] = {a.rest_st};
+  a.nrest = canon_dims(p.nrest, a.rest_ext, sets, 1);
+  if (a.nrest == 0) {                                  // one point per output
+    a.nrest = 1;
+    a.rest_ext[0] = 1;
+    a.rest_st[0] = 0;
+  }
+  bool fast = p.n_rest < (int64_t(1) << 32);
+  for (int i = 0; i < a.nrest; ++i) {
+    fast = fast && a.rest_ext[i] <= (int64_t(1) << 31);
+    if (fast) a.rest_div[i] = make_fastdiv((uint32_t)a.rest_ext[i]);
+  }
   a.offset = p.offset;
   a.n_rest = p.n_rest;
   const int64_t nout = p.n_keep;
   const int64_t chunks = p.n_rest <= kWarpRun ? 1 : chunks_for(p.n_rest, nout, kCands[0]);
-  const int64_t chunk_len = (p.n_rest + chunks - 1) / chunks;
+  bool vec = fast && a.rest_st[a.nrest - 1] == 1 && a.rest_ext[a.nrest - 1] % 4 == 0 && a.offset % 4 == 0 &&
+             (reinterpret_cast<uintptr_t>(in) & 15) == 0;
+  for (int i = 0; i + 1 < a.nrest; ++i) vec = vec && a.rest_st[i] % 4 == 0;
+  for (int i = 0; i < a.nkeep; ++i) vec = vec && a.keep_st[i] % 4 == 0;
+  int64_t chunk_len = (p.n_rest + chunks - 1) / chunks;
+  if (vec) chunk_len = (chunk_len + 3) / 4 * 4;        // chunks start on a group of 4
   uint2 *partials = nullptr;
   unsigned *counters = nullptr;
   if (chunks > 1) {
@@ -283,8 +344,16 @@ int32_t run_affine(const T *in, const Plan &p, T *out, void *ws, size_t ws_bytes
     DESC_CUDA_TRY(cudaMemsetAsync(counters, 0, size_t(nout) * sizeof(unsigned), s));
   }
   if (nout * chunks >= (int64_t(1) << 31)) return DESC_ERR_UNSUPPORTED;
-  reduce_affine_kernel<A, T><<<(unsigned)(nout * chunks), kThreads, 0, s>>>(in, a, chunks, chunk_len,
-                                                                           out, partials, counters);
+  const unsigned grid = (unsigned)(nout * chunks);
+  if (vec)
+    reduce_affine_kernel<A, T, true, true><<<grid, kThreads, 0, s>>>(in, a, chunks, chunk_len, out, partials,
+                                                                     counters);
+  else if (fast)
+    reduce_affine_kernel<A, T, true, false><<<grid, kThreads, 0, s>>>(in, a, chunks, chunk_len, out, partials,
+                                                                      counters);
+  else
+    reduce_affine_kernel<A, T, false, false><<<grid, kThreads, 0, s>>>(in, a, chunks, chunk_len, out, partials,
+                                                                       counters);
   DESC_CUDA_TRY(cudaGetLastError());
   return DESC_OK;
 }
