@@ -305,6 +305,7 @@ __global__ void __launch_bounds__(kThreads + 32) scan_kernel(const T *in, T *out
   __shared__ unsigned sh_heads[MODE == CSR ? kTile / 32 : 1];
   __shared__ unsigned short sh_need[MODE == PLAIN ? 1 : SUB * kThreads];  // carry-needed bits
   __shared__ int64_t sh_seg0;
+  __shared__ int sh_any_end;            // CSR: a non-empty segment ends in this tile
   __shared__ volatile int sh_go;        // look-back may start polling
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -316,7 +317,6 @@ __global__ void __launch_bounds__(kThreads + 32) scan_kernel(const T *in, T *out
   }
   __syncthreads();
   const int64_t tile = sh_tile;
-  const int64_t ntiles = (n + kTile - 1) / kTile;
   const int64_t t0 = tile * kTile;
   const bool stall = args.debug && tile == 1;
 
@@ -357,15 +357,26 @@ __global__ void __launch_bounds__(kThreads + 32) scan_kernel(const T *in, T *out
       const int64_t s0 = find_segment(args.offsets, args.nseg, t0);
       if (lane == 0) sh_seg0 = s0;
     }
+    if (tid == 0) sh_any_end = 0;
     compute_bar();
+    // Boundaries b = offsets[s] in (t0, tend]: a segment starts at b (b <
+    // tend) and segment s - 1 ends at b - 1 in this tile.  Empty segments get
+    // their zero total here; the others are summed after the store pass.
     const int64_t tend = std::min<int64_t>(t0 + kTile, n);
-    for (int64_t s = sh_seg0 + 1 + tid; s < args.nseg; s += kThreads) {
+    T *sums = static_cast<T *>(args.sums);
+    for (int64_t s = sh_seg0 + 1 + tid; s <= args.nseg; s += kThreads) {
       const int64_t b = args.offsets[s];
-      if (b >= tend) break;
-      if (b < t0) continue;                             // only if the offsets were not sorted
+      if (b > tend) break;
+      if (b <= t0) continue;                            // only if the offsets were not sorted
       const int64_t rel = b - t0;
-      atomicOr(&sh_heads[rel >> 5], 1u << (rel & 31));
+      if (b < tend) atomicOr(&sh_heads[rel >> 5], 1u << (rel & 31));
+      if (sums) {
+        if (args.offsets[s - 1] == b) sums[s - 1] = T(0);
+        else sh_any_end = 1;
+      }
     }
+    if (sums && tile == 0)                              // empty segments before the first element
+      for (int64_t s = tid; s < sh_seg0; s += kThreads) sums[s] = T(0);
     if (tid == 0 && args.offsets[sh_seg0] == t0) atomicOr(&sh_heads[0], 1u);
   }
   if (tid == 0) {
@@ -517,17 +528,21 @@ __global__ void __launch_bounds__(kThreads + 32) scan_kernel(const T *in, T *out
       }
     }
   }
-  if (MODE == CSR && args.sums) {                       // totals of segments ending here
-    compute_bar();                                      // (sums read the stored outputs)
+  if (MODE == CSR && args.sums && sh_any_end) {         // totals of non-empty segments ending here
+    // the value at the segment's last element, from the staged tile
     T *sums = static_cast<T *>(args.sums);
     const int64_t tend = std::min<int64_t>(t0 + kTile, n);
-    for (int64_t s = sh_seg0 + tid; s < args.nseg; s += kThreads) {
-      const int64_t b = args.offsets[s], e = args.offsets[s + 1];
-      if (b >= tend) break;
-      if (e > b && e - 1 >= t0 && e - 1 < tend) sums[s] = __ldcg(out + (e - 1));
+    for (int64_t s = sh_seg0 + 1 + tid; s <= args.nseg; s += kThreads) {
+      const int64_t b = args.offsets[s];
+      if (b > tend) break;
+      if (b <= t0 || args.offsets[s - 1] == b) continue;
+      const int rel = (int)(b - 1 - t0);
+      const int sub = rel / kSub, r2 = rel % kSub;
+      const T *v = reinterpret_cast<const T *>(ring + sub * kStageBytes + chunk_off(r2 / 4));
+      T y = v[r2 % 4];
+      if ((sh_need[sub * kThreads + r2 / kItems] >> (r2 % kItems)) & 1u) y = apply_carry(y, pre);
+      sums[s - 1] = y;
     }
-    for (int64_t s = tile * kThreads + tid; s < args.nseg; s += ntiles * kThreads)
-      if (args.offsets[s + 1] == args.offsets[s]) sums[s] = T(0);
   }
 }
 
