@@ -57,7 +57,10 @@ typedef enum {
   DESC_ERR_UNSUPPORTED = 7,     /* valid request this build does not handle  */
   DESC_ERR_CUDA = 8,            /* a CUDA runtime call failed                  */
   DESC_ERR_DEVICE_TIMEOUT = 9,  /* a bounded device-side wait gave up          */
-  DESC_ERR_WORKSPACE = 10       /* workspace NULL or smaller than required     */
+  DESC_ERR_WORKSPACE = 10,      /* workspace NULL or smaller than required     */
+  DESC_ERR_BARRIER = 11         /* a barrier that some thread of its scope
+                                   does not reach (Section 2.2: a sync inside a
+                                   split of the threads it synchronises)      */
 } desc_status;
 
 /* Execution levels (Section 3.1; the warp level is an addition: 32
@@ -180,6 +183,51 @@ int32_t desc_lower_view(const desc_view *v, const desc_exec *ex, desc_lowered *o
  * 2^24 (element, thread) pairs. */
 int32_t desc_check_disjoint(const desc_access *acc, int32_t n, const desc_exec *ex,
                             int64_t *first_conflict);
+
+/* ---- Programs: accesses, barriers and splits across a kernel body ----
+ * Section 3.3 and Section 4 track, per execution resource, which places
+ * were accessed; a barrier releases the accesses of the threads it
+ * synchronises (Section 3.3, "Synchronization"), and a barrier inside a
+ * split of the threads it synchronises is rejected (Section 2.2, the
+ * "barrier not allowed here" example).  desc_check_program runs these checks
+ * over a whole kernel body given as a flattened statement tree:
+ *   ACCESS  one view access (lowered map, buffer id, read or write) by every
+ *           thread of the current (sub-)resource; its selected coordinates
+ *           are relative to that sub-resource and each select's extent must
+ *           equal the sub-resource's count (DESC_ERR_SHAPE otherwise);
+ *   SYNC    level BLOCK (__syncthreads: releases earlier accesses between
+ *           threads of the same block), WARP (__syncwarp: between threads of
+ *           the same warp) or GRID (a kernel boundary: releases everything;
+ *           only outside every split);
+ *   SPLIT   level BLOCK (the grid's blocks along dim), THREAD (each block's
+ *           threads along dim) or WARP (each block's warps, dim X): the first
+ *           `n_first` statements after it run on coordinates < at, the next
+ *           `n_second` on the rest (coordinates relative to `at`); the two
+ *           parts run concurrently, and the statements after the split run
+ *           on the whole resource again.
+ * Two accesses conflict when they reach the same element of the same buffer
+ * from two threads, at least one writes, and no barrier since the earlier
+ * one synchronises both threads.  Returns DESC_OK; DESC_ERR_OVERLAP with
+ * *bad_stmt the first conflicting access and *first_conflict its smallest
+ * conflicting element; DESC_ERR_BARRIER with *bad_stmt the offending SYNC
+ * (a BLOCK sync inside a THREAD or WARP split, a WARP sync inside a THREAD
+ * split or in blocks whose thread count is not a multiple of 32, a GRID sync
+ * inside any split); DESC_ERR_SHAPE (a split position outside (0, extent),
+ * a select extent that does not match its sub-resource, warp selects where
+ * the threads are split); DESC_ERR_INVALID_ARG (malformed tree);
+ * DESC_ERR_UNSUPPORTED beyond 2^22 recorded (element, thread) pairs.
+ * Host only; exact enumeration. */
+typedef enum { DESC_STMT_ACCESS = 0, DESC_STMT_SYNC = 1, DESC_STMT_SPLIT = 2 } desc_stmt_kind;
+typedef struct {
+  int32_t kind;
+  int32_t level;               /* SYNC / SPLIT: a desc_level                  */
+  int32_t dim;                 /* SPLIT: DESC_DIM_X / Y / Z                    */
+  int32_t n_first, n_second;   /* SPLIT: flattened statements of each part   */
+  int64_t at;                  /* SPLIT: first part = coordinates < at        */
+  desc_access access;          /* ACCESS                                      */
+} desc_stmt;
+int32_t desc_check_program(const desc_stmt *prog, int32_t n, const desc_exec *ex, int32_t *bad_stmt,
+                           int64_t *first_conflict);
 
 /* ---- Reduce ----------------------------------------------------------
  * Section 5 benchmark "block-wide parallel reduction"; the operator is a sum.

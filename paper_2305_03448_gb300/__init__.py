@@ -71,6 +71,11 @@ class Access(ctypes.Structure):
     _fields_ = [("map", Lowered), ("buffer", c_int32), ("is_write", c_int32)]
 
 
+class Stmt(ctypes.Structure):
+    _fields_ = [("kind", c_int32), ("level", c_int32), ("dim", c_int32), ("n_first", c_int32),
+                ("n_second", c_int32), ("at", c_int64), ("access", Access)]
+
+
 class Problem(ctypes.Structure):
     _fields_ = [("op", c_int32), ("dtype", c_int32), ("n", c_int64), ("aux", c_int64), ("seg_hist", ctypes.c_float * 8)]
 
@@ -102,6 +107,7 @@ def _declare(L):
         "desc_version": (c_int32, []),
         "desc_lower_view": (c_int32, [POINTER(View), POINTER(Exec), POINTER(Lowered)]),
         "desc_check_disjoint": (c_int32, [POINTER(Access), c_int32, POINTER(Exec), POINTER(c_int64)]),
+        "desc_check_program": (c_int32, [POINTER(Stmt), c_int32, POINTER(Exec), POINTER(c_int32), POINTER(c_int64)]),
         "desc_reduce_workspace_size": (c_int32, [POINTER(View), POINTER(Exec), c_int32, c_int32, POINTER(c_size_t)]),
         "desc_reduce": (c_int32, [POINTER(View), POINTER(Exec), c_int32, c_int32, P, c_size_t, P, c_size_t,
                                   c_int32, P, c_size_t, P]),
@@ -246,6 +252,58 @@ def desc_check_disjoint(accesses, grid, block):
         return first.value
     _check(st, "desc_check_disjoint")
     return None
+
+
+STMT_ACCESS, STMT_SYNC, STMT_SPLIT = 0, 1, 2
+
+
+def _flatten_program(prog, out):
+    """Nested statements -> flat Stmt list (preorder); returns the count."""
+    start = len(out)
+    for st in prog:
+        kind = st[0]
+        if kind == "access":
+            _, buf, base_shape, ops, w = st
+            x = Stmt()
+            x.kind = STMT_ACCESS
+            x.access.map = lowered_struct(desc_lower_view(base_shape, ops))
+            x.access.buffer = int(buf)
+            x.access.is_write = 1 if w else 0
+            out.append(x)
+        elif kind == "sync":
+            x = Stmt()
+            x.kind, x.level = STMT_SYNC, int(st[1])
+            out.append(x)
+        elif kind == "split":
+            _, level, dim, at, first, second = st
+            x = Stmt()
+            x.kind, x.level, x.dim, x.at = STMT_SPLIT, int(level), int(dim), int(at)
+            out.append(x)
+            x.n_first = _flatten_program(first, out)
+            x.n_second = _flatten_program(second, out)
+        else:
+            raise DescError(1, f"statement {kind!r}")
+    return len(out) - start
+
+
+def desc_check_program(prog, grid, block):
+    """Access safety of a kernel body.  ``prog`` is a list of statements:
+    ("access", buffer, base_shape, ops, is_write), ("sync", level) and
+    ("split", level, dim, at, [first part], [second part]).  Views are
+    lowered without a resource (their select extents are checked against
+    the sub-resource by the checker).  Returns (status, statement index,
+    first conflicting element): status 0 (safe), 3 (DESC_ERR_OVERLAP),
+    11 (DESC_ERR_BARRIER) or 2 (DESC_ERR_SHAPE); statement indices count the
+    flattened preorder.  Other statuses raise DescError."""
+    flat = []
+    _flatten_program(prog, flat)
+    arr = (Stmt * max(len(flat), 1))(*flat)
+    bad, first = c_int32(-1), c_int64(-1)
+    st = lib().desc_check_program(arr, len(flat), ctypes.byref(make_exec(grid, block)), ctypes.byref(bad),
+                                  ctypes.byref(first))
+    if st not in (0, 2, 3, 11):
+        _check(st, "desc_check_program")
+    return st, bad.value, (first.value if st == 3 else None)
 
 
 # ----------------------------------------------------------------- device ops

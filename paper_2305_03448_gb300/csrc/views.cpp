@@ -76,6 +76,7 @@ extern "C" const char *desc_status_string(int32_t s) {
     case DESC_ERR_CUDA: return "DESC_ERR_CUDA";
     case DESC_ERR_DEVICE_TIMEOUT: return "DESC_ERR_DEVICE_TIMEOUT";
     case DESC_ERR_WORKSPACE: return "DESC_ERR_WORKSPACE";
+    case DESC_ERR_BARRIER: return "DESC_ERR_BARRIER";
     default: return "DESC_ERR_UNKNOWN";
   }
 }
