@@ -287,11 +287,11 @@ def autotune_step(D, stream, probs, names):
 
 def run_schedule_model(torch, D, synth, n_train=860, n_test=500):
     """Learned schedules: exhaustive timings of every candidate of seeded
-    problems from the reduce / scan / transpose / segmented families (about
-    3,000 training rows), the cost model trained on the GPU by the library's
-    kernels, and its picks on 500 held-out problems compared with the
-    exhaustive tuner (regret = t(pick) / t(best) - 1) and with the default."""
-    arena = D.TuneArena(1 << 27, 5000)
+    problems from the reduce / scan / transpose / segmented / matmul families
+    (about 3,000 training rows), the cost model trained on the GPU by the
+    library's kernels, and its picks on 500 held-out problems compared with
+    the exhaustive tuner (regret = t(pick) / t(best) - 1) and with the default."""
+    arena = D.TuneArena(1 << 27, 5000, max_mm=4096)
     train = synth.tune_problems(n_train, seed=101)
     test = synth.tune_problems(n_test, seed=202)
     model = D.CostModel(synth.mlp_init(D.NUM_FEATURES, 64, seed=303))

@@ -381,23 +381,36 @@ int32_t desc_segmented_reduce_scan_per_segment(const int64_t *h_offsets, int64_t
  *   DESC_OP_SCAN       look-back scan: tile of 4096 x {4, 2, 1} elements
  *   DESC_OP_TRANSPOSE  tiles of {64, 32} squared
  *   DESC_OP_SEGMENTED  CSR look-back scan: tile of 4096 x {4, 2, 1} elements
+ *   DESC_OP_MATMUL     tensor-core forms: {CTA pairs on 256 x 256 tiles where
+ *                      the 128-row tiles pair up, one CTA per 128 x 256 tile}
+ *                      x {wide, narrow} rasterisation groups: 16 / 4 tile
+ *                      rows (single) and 8 / 2 tile-row pairs (pairs)
  * A problem describes one call's shape; ops look up the candidate recorded
  * for their (op, dtype, floor(log2 n), floor(log2(aux + 1))) bucket in a
  * process-wide table (thread-safe), else use candidate 0. */
-typedef enum { DESC_OP_REDUCE = 0, DESC_OP_SCAN = 1, DESC_OP_TRANSPOSE = 2, DESC_OP_SEGMENTED = 3 } desc_op;
-#define DESC_NUM_FEATURES 29
+typedef enum {
+  DESC_OP_REDUCE = 0,
+  DESC_OP_SCAN = 1,
+  DESC_OP_TRANSPOSE = 2,
+  DESC_OP_SEGMENTED = 3,
+  DESC_OP_MATMUL = 4
+} desc_op;
+#define DESC_NUM_FEATURES 32
 typedef struct {
   int32_t op;          /* desc_op                                                      */
-  int32_t dtype;       /* DESC_I32 / DESC_F32                                          */
-  int64_t n;           /* elements                                                     */
+  int32_t dtype;       /* DESC_I32 / DESC_F32 (matmul: DESC_F32)                        */
+  int64_t n;           /* elements; matmul: M                                          */
   int64_t aux;         /* reduce: outputs (n/aux elements each); transpose: rows;
-                          segmented: segments; scan: 0                                 */
+                          segmented: segments; scan: 0; matmul: N                      */
   float seg_hist[8];   /* segmented: fraction of segments with floor(log2 len) in
                           [0,3), [3,6), ..., [18,21), and empty ones in bucket 0         */
+  int64_t k;           /* matmul: K (the bucket is (M, N)); other ops: 0               */
 } desc_problem;
 /* Device buffers a measurement runs on (the caller owns them): in (n elements
- * of dtype), out (reduce: aux or 1 elements; others: n), sums (segmented: aux),
- * offsets (segmented: aux + 1, device int64), ws (at least the op's workspace). */
+ * of dtype; matmul: A, M x K FP32), out (reduce: aux or 1 elements; matmul:
+ * M x N; others: n), sums (segmented: aux), offsets (segmented: aux + 1,
+ * device int64), ws (at least the op's workspace), in2 (matmul: B, K x N FP32;
+ * else unused).  Matmul problems are timed in DESC_MM_BF16. */
 typedef struct {
   const void *in;
   void *out;
@@ -405,13 +418,14 @@ typedef struct {
   const int64_t *offsets;
   void *ws;
   size_t ws_bytes;
+  const void *in2;
 } desc_tune_buffers;
 
 int32_t desc_candidate_count(int32_t op, int32_t *count);
 /* Features of (problem, candidate) for the cost model: op and dtype one-hot,
  * log2 sizes, the segment-length histogram, the candidate's tile size,
- * vectors in flight, CTA target, index one-hot (8 slots) and load path
- * (DESC_NUM_FEATURES floats). */
+ * vectors in flight, CTA target (matmul: rasterisation group), index one-hot
+ * (8 slots), load path, log2 K and CTA pairing (DESC_NUM_FEATURES floats). */
 int32_t desc_features(const desc_problem *p, int32_t cand, float *out, int32_t nout);
 /* Times every candidate on the given buffers (reps launches each, CUDA events
  * on the stream, median), writing microseconds to us[count].  Synchronises. */

@@ -23,8 +23,8 @@ GRID, BLOCK, WARP, THREAD = 0, 1, 2, 3
 X, Y, Z, LANE = 0, 1, 2, 3
 I32, F32 = 0, 1
 MM_FP32_SIMT, MM_BF16, MM_SPLIT3, MM_SPLIT2 = 0, 1, 2, 3
-OP_REDUCE, OP_SCAN, OP_TRANSPOSE, OP_SEGMENTED = 0, 1, 2, 3
-NUM_FEATURES = 29
+OP_REDUCE, OP_SCAN, OP_TRANSPOSE, OP_SEGMENTED, OP_MATMUL = 0, 1, 2, 3, 4
+NUM_FEATURES = 32
 KAHAN = 1
 DEBUG_STALL_TILE = 1 << 16
 CHECK_OFFSETS = 1 << 17
@@ -77,12 +77,13 @@ class Stmt(ctypes.Structure):
 
 
 class Problem(ctypes.Structure):
-    _fields_ = [("op", c_int32), ("dtype", c_int32), ("n", c_int64), ("aux", c_int64), ("seg_hist", ctypes.c_float * 8)]
+    _fields_ = [("op", c_int32), ("dtype", c_int32), ("n", c_int64), ("aux", c_int64), ("seg_hist", ctypes.c_float * 8),
+                ("k", c_int64)]
 
 
 class TuneBuffers(ctypes.Structure):
     _fields_ = [("inp", c_void_p), ("out", c_void_p), ("sums", c_void_p), ("offsets", c_void_p), ("ws", c_void_p),
-                ("ws_bytes", c_size_t)]
+                ("ws_bytes", c_size_t), ("in2", c_void_p)]
 
 
 _lib_handle = None
@@ -488,9 +489,10 @@ def seg_hist(lengths):
     return [x / max(len(L), 1) for x in h]
 
 
-def make_problem(op, dtype, n, aux=0, lengths=None) -> Problem:
+def make_problem(op, dtype, n, aux=0, lengths=None, k=0) -> Problem:
+    """Matmul: n = M, aux = N, k = K."""
     p = Problem()
-    p.op, p.dtype, p.n, p.aux = int(op), int(dtype), int(n), int(aux)
+    p.op, p.dtype, p.n, p.aux, p.k = int(op), int(dtype), int(n), int(aux), int(k)
     if lengths is not None:
         for i, v in enumerate(seg_hist(lengths)):
             p.seg_hist[i] = v
@@ -542,25 +544,33 @@ def desc_tune_load(path):
 
 
 class TuneArena:
-    """Device buffers the tuner measures on (the largest problem decides)."""
+    """Device buffers the tuner measures on (the largest problem decides);
+    max_mm > 0 adds room for matmul problems up to M = N = K = max_mm."""
 
-    def __init__(self, max_n, max_seg, device="cuda"):
+    def __init__(self, max_n, max_seg, device="cuda", max_mm=0):
         import torch
+        max_n = max(max_n, max_mm * max_mm)
         self.x = torch.zeros(max_n, dtype=torch.float32, device=device)
         self.y = torch.zeros(max_n, dtype=torch.float32, device=device)
+        self.b = torch.zeros(max(max_mm * max_mm, 1), dtype=torch.float32, device=device)
         self.sums = torch.zeros(max(max_seg, 1), dtype=torch.float32, device=device)
         self.offsets = torch.zeros(max_seg + 1, dtype=torch.int64, device=device)
         nb = max(desc_segmented_workspace(max_seg, max_n, "cpu").numel(), 1 << 20)
         nb2 = c_size_t(0)
         _check(lib().desc_scan_workspace_size(ctypes.byref(make_view([max_n], [])), None, GRID, F32,
                                               ctypes.byref(nb2)), "desc_scan_workspace_size")
-        self.ws = torch.empty(max(nb, nb2.value) + (64 << 20), dtype=torch.uint8, device=device)
+        nb3 = c_size_t(0)
+        if max_mm:
+            _check(lib().desc_matmul_workspace_size(max_mm, max_mm, max_mm, MM_BF16, ctypes.byref(nb3)),
+                   "desc_matmul_workspace_size")
+        self.ws = torch.empty(max(nb, nb2.value, nb3.value) + (64 << 20), dtype=torch.uint8, device=device)
 
     def buffers(self, prob: dict):
         import torch
         b = TuneBuffers()
         b.inp, b.out, b.sums = self.x.data_ptr(), self.y.data_ptr(), self.sums.data_ptr()
         b.ws, b.ws_bytes = self.ws.data_ptr(), self.ws.numel()
+        b.in2 = self.b.data_ptr()
         if prob["op"] == OP_SEGMENTED:
             L = prob["lengths"]
             off = torch.zeros(L.numel() + 1, dtype=torch.int64)
@@ -571,7 +581,7 @@ class TuneArena:
 
 
 def desc_tune_measure(prob: dict, arena: TuneArena, reps=5, stream=None):
-    p = make_problem(prob["op"], prob["dtype"], prob["n"], prob["aux"], prob.get("lengths"))
+    p = make_problem(prob["op"], prob["dtype"], prob["n"], prob["aux"], prob.get("lengths"), prob.get("k", 0))
     nc = candidate_count(prob["op"])
     us = (ctypes.c_float * nc)()
     _check(lib().desc_tune_measure(ctypes.byref(p), ctypes.byref(arena.buffers(prob)), int(reps), _stream(stream),
@@ -580,7 +590,7 @@ def desc_tune_measure(prob: dict, arena: TuneArena, reps=5, stream=None):
 
 
 def desc_tune_exhaustive(prob: dict, arena: TuneArena, reps=5, stream=None):
-    p = make_problem(prob["op"], prob["dtype"], prob["n"], prob["aux"], prob.get("lengths"))
+    p = make_problem(prob["op"], prob["dtype"], prob["n"], prob["aux"], prob.get("lengths"), prob.get("k", 0))
     best = c_int32(-1)
     _check(lib().desc_tune_exhaustive(ctypes.byref(p), ctypes.byref(arena.buffers(prob)), int(reps),
                                       _stream(stream), ctypes.byref(best)), "desc_tune_exhaustive")
@@ -643,14 +653,14 @@ class CostModel:
         _check(lib().desc_tune_set_model(_ptr(self.p), self.F, self.H), "desc_tune_set_model")
 
     def predict_problem(self, prob: dict, stream=None):
-        p = make_problem(prob["op"], prob["dtype"], prob["n"], prob["aux"], prob.get("lengths"))
+        p = make_problem(prob["op"], prob["dtype"], prob["n"], prob["aux"], prob.get("lengths"), prob.get("k", 0))
         best = c_int32(-1)
         _check(lib().desc_tune_predict(ctypes.byref(p), _stream(stream), ctypes.byref(best)), "desc_tune_predict")
         return best.value
 
 
 def feature_rows(prob: dict):
-    p = make_problem(prob["op"], prob["dtype"], prob["n"], prob["aux"], prob.get("lengths"))
+    p = make_problem(prob["op"], prob["dtype"], prob["n"], prob["aux"], prob.get("lengths"), prob.get("k", 0))
     return [desc_features(p, c) for c in range(candidate_count(prob["op"]))]
 
 

@@ -754,6 +754,19 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 }  // namespace
 
+// Schedule candidates: 0 pairs (where the tile rows pair up), wide groups;
+// 1 single CTAs, wide groups; 2 pairs, narrow groups; 3 single, narrow.
+constexpr int kMmCands = 4;
+constexpr int kMmPairs[kMmCands] = {1, 0, 1, 0};
+constexpr int kMmGroupRows[kMmCands] = {kGroupM, kGroupM, 4, 4};
+
+int mm_candidates() { return kMmCands; }
+void mm_candidate(int cand, int *pairs, int *group_rows) {
+  const int c = (cand >= 0 && cand < kMmCands) ? cand : 0;
+  *pairs = kMmPairs[c];
+  *group_rows = kMmGroupRows[c];
+}
+
 int32_t mm_status_take() {
   int v = 0, z = 0;
   if (cudaMemcpyFromSymbol(&v, g_mm_status, sizeof(int)) != cudaSuccess) return DESC_ERR_CUDA;
@@ -789,7 +802,9 @@ int32_t launch_mm_tc(const float *A, int64_t a_off, int64_t a_sr, int64_t a_sc, 
   r = launch_split(B, b_off, b_sc, b_sr, N, K, Np, Kp, planes, pB, s, nsm_split);
   if (r != DESC_OK) return r;
   const int Mt = (int)(Mp / BM);
-  const bool pairs = Mt % 2 == 0;                      // 128-row tiles pair up: cta_group::2
+  int want_pairs = 1, group_rows = kGroupM;
+  mm_candidate(schedule_for(DESC_OP_MATMUL, DESC_F32, M, N), &want_pairs, &group_rows);
+  const bool pairs = want_pairs && Mt % 2 == 0;        // 128-row tiles pair up: cta_group::2
   CUtensorMap tmA, tmB;
   if (!make_map(&tmA, pA, planes, Mp, Kp, BM) || !make_map(&tmB, pB, planes, Np, Kp, pairs ? BN / 2 : BN))
     return DESC_ERR_CUDA;
@@ -826,14 +841,14 @@ int32_t launch_mm_tc(const float *A, int64_t a_off, int64_t a_sr, int64_t a_sc, 
   TileMap tmap;                                        // over 128 x 256 tiles, or 256 x 256 pair tiles
   tmap.Mt = pairs ? Mt / 2 : Mt;
   tmap.Nt = (int)(Np / BN);
-  tmap.group_m = std::min(tmap.Mt, pairs ? kGroupM / 2 : kGroupM);
+  tmap.group_m = std::min(tmap.Mt, pairs ? group_rows / 2 : group_rows);
   const int64_t ntiles = int64_t(tmap.Mt) * tmap.Nt;
   if (ntiles >= (int64_t(1) << 31)) return DESC_ERR_UNSUPPORTED;
   const int kblocks = (int)(Kp / BK), split = planes > 1 ? 1 : 0;
   if (!pairs || max_pairs < 1) {
     if (pairs) {                                       // no pair fits: the single-CTA map of B
       tmap.Mt = Mt;
-      tmap.group_m = std::min(Mt, kGroupM);
+      tmap.group_m = std::min(Mt, group_rows);
       if (!make_map(&tmB, pB, planes, Np, Kp, BN)) return DESC_ERR_CUDA;
     }
     const int64_t nt1 = int64_t(tmap.Mt) * tmap.Nt;

@@ -22,12 +22,12 @@ using namespace desc;
 
 namespace {
 
-constexpr int kOps = 4;
+constexpr int kOps = 5;
 using Key = std::tuple<int32_t, int32_t, int32_t, int32_t>;
 
 std::mutex g_mu;
 std::map<Key, int32_t> g_table;
-thread_local int32_t g_force[kOps] = {-1, -1, -1, -1};
+thread_local int32_t g_force[kOps] = {-1, -1, -1, -1, -1};
 const float *g_model = nullptr;
 int32_t g_model_F = 0, g_model_H = 0;
 
@@ -50,12 +50,13 @@ int ncand(int32_t op) {
     case DESC_OP_SCAN: return scan_candidates();
     case DESC_OP_TRANSPOSE: return transpose_candidates();
     case DESC_OP_SEGMENTED: return scan_candidates();
+    case DESC_OP_MATMUL: return mm_candidates();
     default: return 0;
   }
 }
 
 bool problem_ok(const desc_problem *p) {
-  return p && p->op >= 0 && p->op < kOps && dtype_size(p->dtype) && p->n >= 0 && p->aux >= 0;
+  return p && p->op >= 0 && p->op < kOps && dtype_size(p->dtype) && p->n >= 0 && p->aux >= 0 && p->k >= 0;
 }
 
 }  // namespace
@@ -86,32 +87,42 @@ extern "C" int32_t desc_force_candidate(int32_t op, int32_t cand) {
 extern "C" int32_t desc_features(const desc_problem *p, int32_t cand, float *out, int32_t nout) {
   if (!problem_ok(p) || !out || nout < DESC_NUM_FEATURES || cand < 0 || cand >= ncand(p->op))
     return DESC_ERR_INVALID_ARG;
+  // [0, 5) op, [5, 7) dtype, [7] log2 n, [8] log2 (aux + 1), [9] log2 (n / (aux + 1) + 1),
+  // [10, 18) segment histogram, [18] log2 tile, [19] vectors, [20] log2 CTAs or group,
+  // [21, 29) candidate, [29] load path, [30] log2 (K + 1), [31] CTA pairs
   for (int i = 0; i < DESC_NUM_FEATURES; ++i) out[i] = 0.f;
   auto lg = [](double x) { return (float)std::log2(std::max(x, 1.0)); };
   out[p->op] = 1.f;
-  out[4 + (p->dtype == DESC_F32 ? 1 : 0)] = 1.f;
-  out[6] = lg((double)p->n) / 32.f;
-  out[7] = lg((double)p->aux + 1.0) / 32.f;
-  out[8] = lg((double)p->n / ((double)p->aux + 1.0) + 1.0) / 32.f;
+  out[5 + (p->dtype == DESC_F32 ? 1 : 0)] = 1.f;
+  out[7] = lg((double)p->n) / 32.f;
+  out[8] = lg((double)p->aux + 1.0) / 32.f;
+  out[9] = lg((double)p->n / ((double)p->aux + 1.0) + 1.0) / 32.f;
   if (p->op == DESC_OP_SEGMENTED)
-    for (int i = 0; i < 8; ++i) out[9 + i] = p->seg_hist[i];
+    for (int i = 0; i < 8; ++i) out[10 + i] = p->seg_hist[i];
   static const int unroll[8] = {8, 4, 8, 4, 8, 8, 4, 8};
   static const int ctas[8] = {1216, 1216, 608, 2432, 2432, 304, 2432, 1216};
   static const int nc[8] = {0, 0, 0, 0, 0, 0, 1, 1};
   static const int subs[3] = {4, 2, 1};
   if (p->op == DESC_OP_REDUCE) {
-    out[17] = lg(256.0 * 4 * unroll[cand]) / 32.f;
-    out[18] = unroll[cand] / 16.f;
-    out[19] = lg((double)ctas[cand]) / 16.f;
-    out[28] = (float)nc[cand];
+    out[18] = lg(256.0 * 4 * unroll[cand]) / 32.f;
+    out[19] = unroll[cand] / 16.f;
+    out[20] = lg((double)ctas[cand]) / 16.f;
+    out[29] = (float)nc[cand];
   } else if (p->op == DESC_OP_TRANSPOSE) {
     const double td = cand == 0 ? 64 : 32;
-    out[17] = lg(td * td) / 32.f;
+    out[18] = lg(td * td) / 32.f;
+  } else if (p->op == DESC_OP_MATMUL) {
+    int pairs = 0, group = 0;
+    mm_candidate(cand, &pairs, &group);
+    out[18] = lg(pairs ? 256.0 * 256.0 : 128.0 * 256.0) / 32.f;
+    out[20] = lg((double)group) / 16.f;
+    out[30] = lg((double)p->k + 1.0) / 32.f;
+    out[31] = (float)pairs;
   } else {
-    out[17] = lg(4096.0 * subs[cand]) / 32.f;
-    out[18] = 16.f / 16.f;
+    out[18] = lg(4096.0 * subs[cand]) / 32.f;
+    out[19] = 16.f / 16.f;
   }
-  out[20 + cand] = 1.f;
+  out[21 + cand] = 1.f;
   return DESC_OK;
 }
 
@@ -158,6 +169,12 @@ int32_t run_problem(const desc_problem *p, const desc_tune_buffers *b, desc_stre
     case DESC_OP_SEGMENTED:
       return desc_segmented_reduce_scan(b->offsets, p->aux, p->n, p->dtype, b->in, b->out, b->sums, 0, b->ws,
                                         b->ws_bytes, s);
+    case DESC_OP_MATMUL: {
+      const int64_t M = p->n, N = p->aux, K = p->k;
+      return desc_matmul(nullptr, nullptr, M, N, K, static_cast<const float *>(b->in), size_t(M * K) * 4,
+                         static_cast<const float *>(b->in2), size_t(K * N) * 4, static_cast<float *>(b->out),
+                         size_t(M * N) * 4, DESC_MM_BF16, b->ws, b->ws_bytes, s);
+    }
     default:
       return DESC_ERR_INVALID_ARG;
   }

@@ -141,13 +141,18 @@ def tune_problems(count: int, seed: int) -> list:
     """Seeded shapes for schedule tuning, drawn from the benchmark families:
     reduce (full or per-group, log2 n in [10, 27]), scan (log2 n in [10, 27]),
     transpose (rows, cols powers of two, 2^10 <= rows * cols <= 2^26),
-    segmented (10..5000 segments, log-uniform lengths up to 2^8..2^16).
-    Each item: dict(op, dtype, n, aux, lengths) with op 0..3 as in desc_op."""
+    segmented (10..5000 segments, log-uniform lengths up to 2^8..2^16),
+    matmul (M, N, K each 2^8..2^12, FP32 operands; n = M, aux = N, k = K).
+    Each item: dict(op, dtype, n, aux, lengths, k) with op 0..4 as in desc_op."""
     u = _unit_f64(splitmix64(stream_key(seed, 1234), 0, 8 * count)).reshape(count, 8).tolist()
     out = []
     for i in range(count):
         a = u[i]
-        op = min(int(a[0] * 4), 3)
+        op = min(int(a[0] * 5), 4)
+        if op == 4:
+            M, N, K = (1 << (8 + int(a[j] * 5)) for j in (2, 3, 4))
+            out.append(dict(op=4, dtype=1, n=M, aux=N, lengths=None, k=K))
+            continue
         dtype = 0 if a[1] < 0.5 else 1
         if op == 0:
             ln = 10 + int(a[2] * 18)

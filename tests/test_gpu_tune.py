@@ -120,21 +120,42 @@ def test_every_candidate_is_correct():
 
 
 def test_exhaustive_tuner_records_the_fastest():
-    arena = D.TuneArena(1 << 22, 1000)
+    arena = D.TuneArena(1 << 22, 1000, max_mm=2048)
     D.desc_tune_clear()
     for prob in [dict(op=1, dtype=1, n=1 << 22, aux=0, lengths=None), dict(op=0, dtype=0, n=1 << 21, aux=0, lengths=None),
-                 dict(op=2, dtype=1, n=1 << 22, aux=1 << 11, lengths=None)]:
+                 dict(op=2, dtype=1, n=1 << 22, aux=1 << 11, lengths=None),
+                 dict(op=4, dtype=1, n=2048, aux=1024, lengths=None, k=512)]:
         us = D.desc_tune_measure(prob, arena, reps=5)
         assert len(us) == D.candidate_count(prob["op"]) and min(us) > 0
         best = D.desc_tune_exhaustive(prob, arena, reps=5)
         assert 0 <= best < len(us)
-        assert D.desc_tune_lookup(D.make_problem(prob["op"], prob["dtype"], prob["n"], prob["aux"])) == best
+        assert D.desc_tune_lookup(D.make_problem(prob["op"], prob["dtype"], prob["n"], prob["aux"],
+                                                 k=prob.get("k", 0))) == best
     D.desc_tune_clear()
+
+
+@pytest.mark.parametrize("M,N,K", [(512, 768, 320), (384, 256, 200), (1000, 700, 129)])
+def test_every_matmul_candidate_is_correct(M, N, K):
+    """Each matmul schedule (CTA pairs or single CTAs, wide or narrow
+    rasterisation groups), forced, gives the same BF16 products."""
+    from oracle import matmul as OM
+    A = synth.normal_f32(M * K, seed=M, stream=1).reshape(M, K)
+    B = synth.normal_f32(K * N, seed=M, stream=2).reshape(K, N)
+    emul = OM.matmul_f64(OM.bf16_rne(A.numpy()), OM.bf16_rne(B.numpy()))
+    for c in range(D.candidate_count(D.OP_MATMUL)):
+        D.desc_force_candidate(D.OP_MATMUL, c)
+        for prec in (D.MM_BF16, D.MM_SPLIT3):
+            C = D.desc_matmul(A.cuda(), B.cuda(), prec).cpu().numpy()
+            if prec == D.MM_BF16:
+                assert OM.rel_frobenius(C, emul) <= 2e-6, c
+            else:
+                assert OM.rel_frobenius(C, OM.split3_product_f64(A.numpy(), B.numpy())) <= 2e-6, c
+    D.desc_force_candidate(D.OP_MATMUL, -1)
 
 
 def test_learned_picker_small_regret_study():
     """A small version of the regret study the bench runs at full size."""
-    arena = D.TuneArena(1 << 27, 5000)
+    arena = D.TuneArena(1 << 27, 5000, max_mm=4096)
     train = synth.tune_problems(160, seed=21)
     test = synth.tune_problems(60, seed=22)
     model = D.CostModel(synth.mlp_init(F, H, seed=23))
@@ -146,5 +167,5 @@ def test_learned_picker_small_regret_study():
     model.install()
     c = model.predict_problem(test[0])
     assert D.desc_tune_lookup(D.make_problem(test[0]["op"], test[0]["dtype"], test[0]["n"], test[0]["aux"],
-                                             test[0]["lengths"])) == c
+                                             test[0]["lengths"], test[0].get("k", 0))) == c
     D.lib().desc_tune_set_model(None, 0, 0)
