@@ -246,20 +246,23 @@ bool rest_contiguous(const Plan &p, bool any_order, int64_t *start0, int64_t *se
     }
   }
   if (have && st != 1) return false;
-  // Kept dims must be regular: output o starts at start0 + o * seg_stride.
-  int64_t expect = -1, cum = 1;
+  // Kept dims must be regular: output o starts at start0 + o * seg_stride
+  // (seg_stride may be negative: kept dims walked backwards).
+  int64_t expect = 0, cum = 1;
+  bool have_keep = false;
   for (int i = p.nkeep - 1; i >= 0; --i) {
     const Dim &d = p.keep[i];
     if (d.extent == 1) continue;
-    if (expect < 0) {
+    if (!have_keep) {
       expect = d.stride;
       cum = d.extent;
+      have_keep = true;
     } else {
       if (d.stride != expect * cum) return false;
       cum *= d.extent;
     }
   }
-  *seg_stride = expect < 0 ? p.n_rest : expect;
+  *seg_stride = have_keep ? expect : p.n_rest;
   *start0 = p.offset + lo_adj;
   return true;
 }

@@ -250,3 +250,17 @@ def test_rejections_launch_nothing():
     assert e.value.status == 10
     torch.cuda.synchronize()
     assert torch.all(out.cpu() == 123)
+
+
+@pytest.mark.parametrize("m,g", [(16, 4096), (4096, 64), (8192, 37)])
+def test_reversed_outer_groups(m, g):
+    """Groups taken in reverse order (the kept dimension walks backwards):
+    per-group reduce and segmented scan stay on the right elements."""
+    n = m * g
+    x = synth.ints_pm1000(n, seed=m + g)
+    for ops in ([("group", m, 0), ("reverse", 0), ("select", V.BLOCK, V.X)],
+                [("reverse", 0), ("group", m, 0), ("select", V.BLOCK, V.X)]):
+        got = D.desc_reduce(x.cuda(), [n], ops, V.BLOCK, (g, 1, 1), (1, 1, 1)).cpu().numpy()
+        want, _ = O.reduce(x.numpy(), [n], ops, V.BLOCK, (g, 1, 1), (1, 1, 1))
+        assert np.array_equal(got, want)
+        check_scan(x, [n], ops, V.BLOCK, (g, 1, 1), (1, 1, 1))
