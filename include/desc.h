@@ -239,6 +239,18 @@ int32_t desc_check_program(const desc_stmt *prog, int32_t n, const desc_exec *ex
  * arithmetic (error within 1e-5 * sum|x|), with compensated (Kahan)
  * accumulation when flags has DESC_KAHAN. */
 #define DESC_KAHAN 1
+/* Operators other than the sum (Section 5 fixes no operator; the generic
+ * reduce and scan take any associative one): DESC_MAX / DESC_MIN give the
+ * maximum / minimum instead, exact in both dtypes (FP32 follows IEEE maxNum /
+ * minNum: a NaN operand is ignored unless every operand is NaN).  The value
+ * of an empty reduction or segment is the operator's identity: 0 for the sum,
+ * INT32_MIN or -inf for the maximum, INT32_MAX or +inf for the minimum.  At
+ * most one of DESC_KAHAN, DESC_MAX, DESC_MIN. */
+#define DESC_MAX (1 << 1)
+#define DESC_MIN (1 << 2)
+/* Scans: out[p] combines the inputs strictly before p in its segment (the
+ * identity for a segment's first point) instead of up to and including p. */
+#define DESC_EXCLUSIVE (1 << 3)
 int32_t desc_reduce_workspace_size(const desc_view *v, const desc_exec *ex, int32_t out_level,
                                    int32_t dtype, size_t *bytes);
 int32_t desc_reduce(const desc_view *v, const desc_exec *ex, int32_t out_level, int32_t dtype,
@@ -253,7 +265,9 @@ int32_t desc_reduce(const desc_view *v, const desc_exec *ex, int32_t out_level, 
  * array as `in` and is written through the same view; elements the view
  * does not reach are left untouched.  in == out (in place) is allowed.
  * DESC_I32 wraps modulo 2^32 (bit-exact); DESC_F32 has per-element error
- * within 1e-5 * sum_{q<=p} |x_q| (FP32 arithmetic, compensated carries). */
+ * within 1e-5 * sum_{q<=p} |x_q| (FP32 arithmetic, compensated carries).
+ * flags: DESC_MAX or DESC_MIN (the operator; exact, always the default
+ * 16384-element tile), DESC_EXCLUSIVE (q < p instead of q <= p). */
 /* Test hook for the bounded waits: tile 1 never publishes, and the waits
  * give up after tens of milliseconds, so the call records
  * DESC_ERR_DEVICE_TIMEOUT (read by desc_stream_status) instead of hanging.
@@ -344,7 +358,10 @@ int32_t desc_matmul(const desc_view *a_v, const desc_view *b_v, int64_t M, int64
  * DESC_CHECK_OFFSETS, which copies them to the host; unchecked bad offsets
  * give wrong values but no out-of-bounds access).  dtype DESC_I32 (wrap-around,
  * bit-exact) or DESC_F32 (per-element error within 1e-5 * sum_{q<=p} |x_q|
- * of the segment).  in == scan_out is allowed. */
+ * of the segment).  in == scan_out is allowed.  flags may add DESC_MAX or
+ * DESC_MIN (scans and totals under that operator; an empty segment's total is
+ * the operator's identity) and DESC_EXCLUSIVE (exclusive scans; the totals are
+ * unchanged). */
 #define DESC_CHECK_OFFSETS (1 << 17)
 int32_t desc_segmented_workspace_size(int64_t nseg, int64_t total, size_t *bytes);
 int32_t desc_segmented_reduce_scan(const int64_t *d_offsets, int64_t nseg, int64_t total, int32_t dtype,

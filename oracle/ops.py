@@ -130,3 +130,110 @@ def segmented_reduce_scan(x, offsets):
             sums[s] = math.fsum(seg64)
             sabs[s] = math.fsum(np.abs(seg64))
     return scan_out, sums, pa, sabs
+
+
+# ---- other operators ---------------------------------------------------------
+# Section 5 fixes no operator for its reduction and scan; a generic reduce or
+# scan takes any associative operator.  Besides the sum: the maximum and the
+# minimum (exact; on FP32 they follow IEEE maxNum / minNum, so a NaN operand
+# is ignored unless every operand is NaN), and exclusive scans, where a point
+# gets the combination of the points strictly before it in its segment (the
+# operator's identity for the first one).
+
+def identity(op, is_int):
+    """0 for the sum, the smallest / largest value for the maximum / minimum."""
+    if op == "sum":
+        return 0
+    if op == "max":
+        return np.iinfo(np.int32).min if is_int else -np.inf
+    return np.iinfo(np.int32).max if is_int else np.inf
+
+
+def _combine_rows(vals, op, exclusive):
+    """Prefix combination along each row (inclusive or exclusive), with the
+    sum in int64 (wrapped later) or FP64, max / min exactly."""
+    is_int = vals.dtype == np.int32
+    if op == "sum":
+        v = vals.astype(np.int64 if is_int else np.float64)
+        inc = np.cumsum(v, axis=1)
+    else:
+        f = np.fmax if op == "max" else np.fmin
+        v = vals.astype(np.int64 if is_int else np.float64)
+        inc = f.accumulate(v, axis=1) if v.shape[1] else v
+    if not exclusive:
+        return inc
+    out = np.empty_like(inc)
+    if inc.shape[1]:
+        out[:, 0] = identity(op, is_int)
+        out[:, 1:] = inc[:, :-1]
+    return out
+
+
+def reduce_op(x, base_shape, ops, out_level, op, grid=None, block=None):
+    """Maximum or minimum (op "max" / "min") over the view, one output per
+    resource at ``out_level``; the identity for an empty row."""
+    if grid is not None:
+        V.check_selects(base_shape, ops, grid, block)
+    vals, _ = _rows(x, base_shape, ops, out_level)
+    is_int = vals.dtype == np.int32
+    f = np.fmax if op == "max" else np.fmin
+    ident = identity(op, is_int)
+    out = np.array([f.reduce(r) if r.size else ident for r in vals], dtype=np.int64 if is_int else np.float64)
+    return out.astype(np.int32) if is_int else out
+
+
+def scan_op(x, out_init, base_shape, ops, seg_level, op="sum", exclusive=False, grid=None, block=None):
+    """Prefix combination over the view, segmented at ``seg_level``, with op
+    "sum" / "max" / "min", inclusive or exclusive.  Returns (out, prefix_abs):
+    prefix_abs is sum |x| over the combined points (FP sums only, else
+    None), the scale of the sum's tolerance."""
+    if grid is not None:
+        V.check_selects(base_shape, ops, grid, block)
+    vals, idx = _rows(x, base_shape, ops, seg_level)
+    is_int = vals.dtype == np.int32
+    res = _combine_rows(vals, op, exclusive)
+    out = np.array(out_init, copy=True).reshape(-1)
+    if is_int:
+        out[idx.reshape(-1)] = wrap_i32(res).reshape(-1) if op == "sum" else res.astype(np.int32).reshape(-1)
+        return out.reshape(np.shape(out_init)), None
+    out = out.astype(np.float64)
+    out[idx.reshape(-1)] = res.reshape(-1)
+    pa = None
+    if op == "sum":
+        pa = np.zeros_like(out)
+        pa[idx.reshape(-1)] = _combine_rows(np.abs(vals.astype(np.float64)).astype(np.float32), "sum",
+                                            exclusive).reshape(-1)
+    return out.reshape(np.shape(out_init)), pa if pa is None else pa.reshape(np.shape(out_init))
+
+
+def segmented_op(x, offsets, op="sum", exclusive=False):
+    """Per segment [offsets[s], offsets[s+1]): the prefix combination
+    (inclusive or exclusive) and the total, under op.  Returns (scan, totals,
+    prefix |x| (FP sums), total |x| (FP sums)); empty segments total the
+    identity."""
+    x = np.asarray(x)
+    off = np.asarray(offsets, dtype=np.int64)
+    S = off.size - 1
+    is_int = x.dtype == np.int32
+    scan_out = np.zeros(x.size, dtype=np.int32 if is_int else np.float64)
+    tot = np.zeros(S, dtype=np.int32 if is_int else np.float64)
+    fp_sum = (not is_int) and op == "sum"
+    pa = np.zeros(x.size) if fp_sum else None
+    sabs = np.zeros(S) if fp_sum else None
+    for s in range(S):
+        a, b = int(off[s]), int(off[s + 1])
+        seg = x[a:b].reshape(1, -1)
+        r = _combine_rows(seg, op, exclusive).reshape(-1)
+        full = _combine_rows(seg, op, False).reshape(-1)
+        if is_int:
+            scan_out[a:b] = wrap_i32(r) if op == "sum" else r.astype(np.int32)
+            t = full[-1] if b > a else identity(op, True)
+            tot[s] = wrap_i32(t) if op == "sum" else np.int32(t)
+        else:
+            scan_out[a:b] = r
+            tot[s] = (math.fsum(seg.reshape(-1).astype(np.float64)) if op == "sum" else full[-1]) if b > a \
+                else identity(op, False)
+            if fp_sum:
+                pa[a:b] = _combine_rows(np.abs(seg).astype(np.float32), "sum", exclusive).reshape(-1)
+                sabs[s] = math.fsum(np.abs(seg.reshape(-1).astype(np.float64)))
+    return scan_out, tot, pa, sabs

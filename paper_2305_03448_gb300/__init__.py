@@ -26,6 +26,7 @@ MM_FP32_SIMT, MM_BF16, MM_SPLIT3, MM_SPLIT2 = 0, 1, 2, 3
 OP_REDUCE, OP_SCAN, OP_TRANSPOSE, OP_SEGMENTED, OP_MATMUL = 0, 1, 2, 3, 4
 NUM_FEATURES = 32
 KAHAN = 1
+MAX, MIN, EXCLUSIVE = 1 << 1, 1 << 2, 1 << 3
 DEBUG_STALL_TILE = 1 << 16
 CHECK_OFFSETS = 1 << 17
 
@@ -314,8 +315,9 @@ def _workspace(nbytes, device):
 
 
 def desc_reduce(x, base_shape, ops, out_level, grid=None, block=None, kahan=False, out=None,
-                ws=None, stream=None):
-    """Sum of tensor ``x`` (the base array) through a view; returns ``out``."""
+                ws=None, stream=None, flags=0):
+    """Sum of tensor ``x`` (the base array) through a view; returns ``out``.
+    flags: MAX or MIN for the maximum / minimum instead."""
     import torch
     L = lib()
     v, e = make_view(base_shape, ops), make_exec(grid, block)
@@ -333,7 +335,7 @@ def desc_reduce(x, base_shape, ops, out_level, grid=None, block=None, kahan=Fals
                "desc_reduce_workspace_size")
         ws = _workspace(nb.value, x.device)
     _check(L.desc_reduce(ctypes.byref(v), _ref(e), out_level, dt, _ptr(x), x.numel() * 4, _ptr(out),
-                         out.numel() * 4, KAHAN if kahan else 0, _ptr(ws), ws.numel(), _stream(stream)),
+                         out.numel() * 4, (KAHAN if kahan else 0) | flags, _ptr(ws), ws.numel(), _stream(stream)),
            "desc_reduce")
     return out
 

@@ -87,7 +87,9 @@ extern "C" int32_t desc_reduce(const desc_view *v, const desc_exec *ex, int32_t 
                                desc_stream_t s) {
   if (!dtype_size(dtype)) return DESC_ERR_INVALID_ARG;
   if (out_level < DESC_LEVEL_GRID || out_level > DESC_LEVEL_THREAD) return DESC_ERR_INVALID_ARG;
-  if (flags & ~(DESC_KAHAN)) return DESC_ERR_INVALID_ARG;
+  if (flags & ~(DESC_KAHAN | DESC_MAX | DESC_MIN)) return DESC_ERR_INVALID_ARG;
+  if (((flags & DESC_KAHAN) != 0) + ((flags & DESC_MAX) != 0) + ((flags & DESC_MIN) != 0) > 1)
+    return DESC_ERR_INVALID_ARG;
   desc_lowered L;
   int32_t r = desc_lower_view(v, ex, &L);
   if (r != DESC_OK) return r;
@@ -99,10 +101,7 @@ extern "C" int32_t desc_reduce(const desc_view *v, const desc_exec *ex, int32_t 
   if (L.base_elems > 0 && (r = check_device_ptr(in, 4)) != DESC_OK) return r;
   if (ranges_overlap(in, in_bytes, out, out_bytes)) return DESC_ERR_OVERLAP;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(s);
-  if (p.n_rest == 0) {
-    if (cudaMemsetAsync(out, 0, out_bytes, st) != cudaSuccess) return DESC_ERR_CUDA;
-    return DESC_OK;
-  }
+  if (p.n_rest == 0) return fill_identity(out, p.n_keep, dtype, flags, s);
   int64_t start0, seg;
   if (!t_generic && rest_contiguous(p, true, &start0, &seg))
     return launch_reduce_segments(dtype, in, start0, seg, p.n_rest, p.n_keep, out, flags, ws,
@@ -151,7 +150,8 @@ extern "C" int32_t desc_scan(const desc_view *v, const desc_exec *ex, int32_t se
                              desc_stream_t s) {
   if (!dtype_size(dtype)) return DESC_ERR_INVALID_ARG;
   if (seg_level < DESC_LEVEL_GRID || seg_level > DESC_LEVEL_THREAD) return DESC_ERR_INVALID_ARG;
-  if (flags & ~(DESC_DEBUG_STALL_TILE)) return DESC_ERR_INVALID_ARG;
+  if (flags & ~(DESC_DEBUG_STALL_TILE | DESC_MAX | DESC_MIN | DESC_EXCLUSIVE)) return DESC_ERR_INVALID_ARG;
+  if ((flags & DESC_MAX) && (flags & DESC_MIN)) return DESC_ERR_INVALID_ARG;
   desc_lowered L;
   int32_t r = desc_lower_view(v, ex, &L);
   if (r != DESC_OK) return r;
@@ -401,16 +401,17 @@ extern "C" int32_t desc_segmented_workspace_size(int64_t nseg, int64_t total, si
 extern "C" int32_t desc_segmented_reduce_scan(const int64_t *d_offsets, int64_t nseg, int64_t total,
                                               int32_t dtype, const void *in, void *scan_out, void *sums_out,
                                               int32_t flags, void *ws, size_t ws_bytes, desc_stream_t s) {
-  if (flags & ~(DESC_CHECK_OFFSETS | DESC_DEBUG_STALL_TILE)) return DESC_ERR_INVALID_ARG;
+  if (flags & ~(DESC_CHECK_OFFSETS | DESC_DEBUG_STALL_TILE | DESC_MAX | DESC_MIN | DESC_EXCLUSIVE))
+    return DESC_ERR_INVALID_ARG;
+  if ((flags & DESC_MAX) && (flags & DESC_MIN)) return DESC_ERR_INVALID_ARG;
   int32_t r = segmented_checks(d_offsets, nseg, total, dtype, in, scan_out, sums_out);
   if (r != DESC_OK) return r;
   if (nseg == 0) return total == 0 ? DESC_OK : DESC_ERR_SHAPE;
   if ((flags & DESC_CHECK_OFFSETS) && (r = check_offsets_device(d_offsets, nseg, total)) != DESC_OK) return r;
-  if (total == 0)     // every segment is empty
-    return cudaMemsetAsync(sums_out, 0, size_t(nseg) * 4, reinterpret_cast<cudaStream_t>(s)) == cudaSuccess
-               ? DESC_OK : DESC_ERR_CUDA;
-  return launch_scan_csr(dtype, in, scan_out, total, d_offsets, nseg, sums_out, flags & DESC_DEBUG_STALL_TILE, ws,
-                         ws_bytes, s, schedule_for(DESC_OP_SEGMENTED, dtype, total, nseg));
+  if (total == 0) return fill_identity(sums_out, nseg, dtype, flags, s);   // every segment is empty
+  return launch_scan_csr(dtype, in, scan_out, total, d_offsets, nseg, sums_out,
+                         flags & (DESC_DEBUG_STALL_TILE | DESC_MAX | DESC_MIN | DESC_EXCLUSIVE), ws, ws_bytes, s,
+                         schedule_for(DESC_OP_SEGMENTED, dtype, total, nseg));
 }
 
 extern "C" int32_t desc_segmented_graph_create(const int64_t *d_offsets, int64_t nseg, int64_t total,

@@ -62,6 +62,9 @@ int reduce_candidates();
 size_t reduce_segments_ws(int32_t dtype, int64_t len, int64_t nout);
 // Reduce: general affine plan (chunk partials in ws when runs are long).
 size_t reduce_affine_ws(int64_t n_rest, int64_t nout);
+// out[0 .. count) = the identity of the operator flags select (DESC_MAX,
+// DESC_MIN, else the sum) in dtype.
+int32_t fill_identity(void *out, int64_t count, int32_t dtype, int32_t flags, desc_stream_t s);
 int32_t launch_reduce_affine(int32_t dtype, const void *in, const Plan &p, void *out,
                              int32_t flags, void *ws, size_t ws_bytes, desc_stream_t s);
 

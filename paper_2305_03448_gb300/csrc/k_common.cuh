@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <type_traits>
 
 #include "desc_internal.h"
 
@@ -73,6 +74,29 @@ struct AccKahan {  // compensated FP32 sum (Neumaier's variant of Kahan summatio
   }
   __device__ uint2 pack() const { return make_uint2(__float_as_uint(s), __float_as_uint(c)); }
   __device__ void unpack(uint2 v) { s = __uint_as_float(v.x); c = __uint_as_float(v.y); }
+};
+
+// Maximum / minimum (MAX true / false) of int32 or FP32; FP32 uses
+// fmaxf / fminf, which ignore a NaN operand.
+template <class T, bool MAX>
+struct AccExt {
+  T v;
+  __device__ static T ident() {
+    if constexpr (std::is_same<T, float>::value) return MAX ? -__int_as_float(0x7f800000) : __int_as_float(0x7f800000);
+    else return MAX ? INT32_MIN : INT32_MAX;
+  }
+  __device__ static T op(T a, T b) {
+    if constexpr (std::is_same<T, float>::value) return MAX ? fmaxf(a, b) : fminf(a, b);
+    else return MAX ? max(a, b) : min(a, b);
+  }
+  __device__ void init() { v = ident(); }
+  __device__ void add1(T x) { v = op(v, x); }
+  template <class V4>
+  __device__ void add4(V4 q) { v = op(v, op(op(q.x, q.y), op(q.z, q.w))); }
+  __device__ void merge(const AccExt &o) { v = op(v, o.v); }
+  __device__ void shfl_merge(int off) { AccExt o; o.v = __shfl_down_sync(0xffffffffu, v, off); merge(o); }
+  __device__ uint2 pack() const { return make_uint2(__builtin_bit_cast(uint32_t, v), 0u); }
+  __device__ void unpack(uint2 q) { v = __builtin_bit_cast(T, q.x); }
 };
 
 template <class A>

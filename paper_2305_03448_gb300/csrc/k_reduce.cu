@@ -62,7 +62,10 @@ __device__ __forceinline__ float final_value(const AccKahan &a) { return __fadd_
 
 template <class A, class T>
 __device__ __forceinline__ void store_out(T *out, int64_t o, const A &a) {
-  out[o] = final_value(a);
+  if constexpr (std::is_same<A, AccExt<T, true>>::value || std::is_same<A, AccExt<T, false>>::value)
+    out[o] = a.v;
+  else
+    out[o] = final_value(a);
 }
 template <>
 __device__ __forceinline__ void store_out<AccI32, int32_t>(int32_t *out, int64_t o, const AccI32 &a) {
@@ -368,6 +371,19 @@ int32_t launch_reduce_segments(int32_t dtype, const void *in, int64_t start, int
                                int64_t len, int64_t nout, void *out, int32_t flags, void *ws,
                                size_t ws_bytes, desc_stream_t st, int cand) {
   cudaStream_t s = reinterpret_cast<cudaStream_t>(st);
+  if (flags & (DESC_MAX | DESC_MIN)) {
+    const bool mx = (flags & DESC_MAX) != 0;
+    if (dtype == DESC_I32) {
+      auto i = static_cast<const int32_t *>(in);
+      auto o = static_cast<int32_t *>(out);
+      return mx ? run_runs<AccExt<int32_t, true>, int32_t>(i, start, seg_stride, len, nout, o, ws, ws_bytes, s, cand)
+                : run_runs<AccExt<int32_t, false>, int32_t>(i, start, seg_stride, len, nout, o, ws, ws_bytes, s, cand);
+    }
+    auto i = static_cast<const float *>(in);
+    auto o = static_cast<float *>(out);
+    return mx ? run_runs<AccExt<float, true>, float>(i, start, seg_stride, len, nout, o, ws, ws_bytes, s, cand)
+              : run_runs<AccExt<float, false>, float>(i, start, seg_stride, len, nout, o, ws, ws_bytes, s, cand);
+  }
   if (dtype == DESC_I32)
     return run_runs<AccI32, int32_t>(static_cast<const int32_t *>(in), start, seg_stride, len, nout,
                                      static_cast<int32_t *>(out), ws, ws_bytes, s, cand);
@@ -385,6 +401,19 @@ size_t reduce_affine_ws(int64_t n_rest, int64_t nout) {
 int32_t launch_reduce_affine(int32_t dtype, const void *in, const Plan &p, void *out, int32_t flags,
                              void *ws, size_t ws_bytes, desc_stream_t st) {
   cudaStream_t s = reinterpret_cast<cudaStream_t>(st);
+  if (flags & (DESC_MAX | DESC_MIN)) {
+    const bool mx = (flags & DESC_MAX) != 0;
+    if (dtype == DESC_I32) {
+      auto i = static_cast<const int32_t *>(in);
+      auto o = static_cast<int32_t *>(out);
+      return mx ? run_affine<AccExt<int32_t, true>, int32_t>(i, p, o, ws, ws_bytes, s)
+                : run_affine<AccExt<int32_t, false>, int32_t>(i, p, o, ws, ws_bytes, s);
+    }
+    auto i = static_cast<const float *>(in);
+    auto o = static_cast<float *>(out);
+    return mx ? run_affine<AccExt<float, true>, float>(i, p, o, ws, ws_bytes, s)
+              : run_affine<AccExt<float, false>, float>(i, p, o, ws, ws_bytes, s);
+  }
   if (dtype == DESC_I32)
     return run_affine<AccI32, int32_t>(static_cast<const int32_t *>(in), p,
                                        static_cast<int32_t *>(out), ws, ws_bytes, s);
@@ -393,6 +422,26 @@ int32_t launch_reduce_affine(int32_t dtype, const void *in, const Plan &p, void 
                                        ws, ws_bytes, s);
   return run_affine<AccF32, float>(static_cast<const float *>(in), p, static_cast<float *>(out), ws,
                                    ws_bytes, s);
+}
+
+namespace {
+__global__ void fill_u32_kernel(uint32_t *out, int64_t n, uint32_t v) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    out[i] = v;
+}
+}  // namespace
+
+int32_t fill_identity(void *out, int64_t count, int32_t dtype, int32_t flags, desc_stream_t st) {
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(st);
+  if (count <= 0) return DESC_OK;
+  uint32_t v = 0u;
+  if (flags & DESC_MAX) v = dtype == DESC_I32 ? 0x80000000u : 0xff800000u;   // INT32_MIN, -inf
+  if (flags & DESC_MIN) v = dtype == DESC_I32 ? 0x7fffffffu : 0x7f800000u;   // INT32_MAX, +inf
+  if (v == 0u) return cudaMemsetAsync(out, 0, size_t(count) * 4, s) == cudaSuccess ? DESC_OK : DESC_ERR_CUDA;
+  const int64_t blocks = std::min<int64_t>((count + 255) / 256, 4096);
+  fill_u32_kernel<<<(unsigned)blocks, 256, 0, s>>>(static_cast<uint32_t *>(out), count, v);
+  DESC_CUDA_TRY(cudaGetLastError());
+  return DESC_OK;
 }
 
 }  // namespace desc

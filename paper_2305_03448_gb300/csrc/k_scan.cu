@@ -116,9 +116,56 @@ __device__ __forceinline__ Carry<float> unpack(unsigned long long w) {
   return {__uint_as_float((uint32_t)w), __uint_as_float((uint32_t)((w >> 32) & 0x3FFFFFFFull) << 2)};
 }
 
+// Scan operators.  O::C is the carry type a look-back folds; apply(x, c)
+// combines a carry with an element's in-tile prefix; pack/unpack place a
+// carry in the 62 value bits of a tile state.
 template <class T>
-__device__ __forceinline__ void publish(TileState *st, unsigned long long status, const Carry<T> &c) {
-  st_relaxed(&st->w, pack(status, c));
+struct SumOp {                          // sum: int32 modulo 2^32, FP32 with compensated carries
+  using C = Carry<T>;
+  __device__ static T id() { return T(0); }
+  __device__ static T comb(T a, T b) { return add_t(a, b); }
+  __device__ static T apply(T x, const C &c) { return apply_carry(x, c); }
+  __device__ static unsigned long long pack(unsigned long long st, const C &c) { return desc::pack(st, c); }
+  __device__ static C unpack(unsigned long long w) { return desc::unpack<T>(w); }
+};
+
+template <class T, bool MAX>
+struct ExtOp {                          // maximum / minimum; FP32 ignores NaN operands (IEEE maxNum / minNum)
+  __device__ static T id();
+  __device__ static T comb(T a, T b);
+  struct C {
+    T v;
+    __device__ static C zero() { return {ExtOp::id()}; }
+    __device__ static C of(T x) { return {x}; }
+    __device__ C plus(const C &o) const { return {ExtOp::comb(v, o.v)}; }
+    __device__ C shfl_down(int off) const { return {__shfl_down_sync(0xffffffffu, v, off)}; }
+  };
+  __device__ static T apply(T x, const C &c) { return comb(c.v, x); }
+  __device__ static unsigned long long pack(unsigned long long st, const C &c) {
+    return (st << 62) | (unsigned long long)__builtin_bit_cast(uint32_t, c.v);
+  }
+  __device__ static C unpack(unsigned long long w) { return {__builtin_bit_cast(T, (uint32_t)w)}; }
+};
+template <>
+__device__ __forceinline__ int32_t ExtOp<int32_t, true>::id() { return INT32_MIN; }
+template <>
+__device__ __forceinline__ int32_t ExtOp<int32_t, false>::id() { return INT32_MAX; }
+template <>
+__device__ __forceinline__ float ExtOp<float, true>::id() { return -__int_as_float(0x7f800000); }
+template <>
+__device__ __forceinline__ float ExtOp<float, false>::id() { return __int_as_float(0x7f800000); }
+template <>
+__device__ __forceinline__ int32_t ExtOp<int32_t, true>::comb(int32_t a, int32_t b) { return max(a, b); }
+template <>
+__device__ __forceinline__ int32_t ExtOp<int32_t, false>::comb(int32_t a, int32_t b) { return min(a, b); }
+template <>
+__device__ __forceinline__ float ExtOp<float, true>::comb(float a, float b) { return fmaxf(a, b); }
+template <>
+__device__ __forceinline__ float ExtOp<float, false>::comb(float a, float b) { return fminf(a, b); }
+
+template <class O>
+__device__ __forceinline__ void publish(TileState *st, unsigned long long status, const typename O::C &c) {
+  st_relaxed(&st->w, O::pack(status, c));
 }
 
 struct ScanArgs {
@@ -138,11 +185,12 @@ struct ScanArgs {
 // keeps the hot tile states from being flooded.  Returns false on timeout.
 constexpr int kSlots = 1;
 
-template <class T>
+template <class O>
 __device__ bool look_back(TileState *states, int64_t tile, ScanWs *ws, long long budget,
-                          Carry<T> &prefix) {
+                          typename O::C &prefix) {
+  using CT = typename O::C;
   const int lane = threadIdx.x & 31;
-  Carry<T> acc = Carry<T>::zero();
+  CT acc = CT::zero();
   int64_t j = tile - 1;   // nearest predecessor not yet folded in
   const long long t0 = clock64();
   unsigned polls = 0;
@@ -183,10 +231,10 @@ __device__ bool look_back(TileState *states, int64_t tile, ScanWs *ws, long long
       }
       __nanosleep(min(32u << min(polls, 5u), 1024u));   // exponential back-off
     }
-    Carry<T> mine = Carry<T>::zero();
+    CT mine = CT::zero();
 #pragma unroll
     for (int k = 0; k < kSlots; ++k)
-      if (lane * kSlots + k <= stop) mine = mine.plus(unpack<T>(w[k]));
+      if (lane * kSlots + k <= stop) mine = mine.plus(O::unpack(w[k]));
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) mine = mine.plus(mine.shfl_down(off));
     acc = acc.plus(mine);
@@ -290,9 +338,10 @@ __device__ __forceinline__ int64_t find_segment(const int64_t *offsets, int64_t 
 // of a tile does not depend on its data) and publishes the inclusive prefix
 // once it has both.  The carry is added during the coalesced store pass, to
 // the elements that have no segment start before them in the tile.
-template <class T, int MODE, int SUB>
+template <class T, class O, int MODE, int SUB, bool EXCL>
 __global__ void __launch_bounds__(kThreads + 32) scan_kernel(const T *in, T *out, ScanArgs args,
                                                              ScanWs *ws, TileState *states) {
+  using CT = typename O::C;
   constexpr int kTile = kSub * SUB;
   extern __shared__ __align__(128) unsigned char ring[];   // SUB stages
   __shared__ int64_t sh_tile;
@@ -300,7 +349,7 @@ __global__ void __launch_bounds__(kThreads + 32) scan_kernel(const T *in, T *out
   __shared__ int sh_wflag[kWarps];
   __shared__ T sh_carry;                // in-tile carry after the sub-tiles done so far
   __shared__ int sh_carry_flag;
-  __shared__ Carry<T> sh_prefix;
+  __shared__ CT sh_prefix;
   __shared__ int sh_ok;
   __shared__ unsigned sh_heads[MODE == CSR ? kTile / 32 : 1];
   __shared__ unsigned short sh_need[MODE == PLAIN ? 1 : SUB * kThreads];  // carry-needed bits
@@ -326,14 +375,14 @@ __global__ void __launch_bounds__(kThreads + 32) scan_kernel(const T *in, T *out
     if (MODE == PERIODIC) first_is_head = first_is_head || (t0 % args.period == 0);
     if (MODE == CSR && !first_is_head)
       first_is_head = args.offsets[find_segment(args.offsets, args.nseg, t0)] == t0;
-    Carry<T> prefix = Carry<T>::zero();
+    CT prefix = CT::zero();
     bool ok = true;
     if (!first_is_head) {
       // Polls made before the predecessors, which started just before this
       // tile, can have published only fail and load the tile states; start
       // once part of this tile's own input has landed (bounded wait).
       for (unsigned i = 0; i < kGoSpins && !sh_go; ++i) __nanosleep(64);
-      ok = look_back<T>(states, tile, ws, args.debug ? kDebugBudgetCycles : kBudgetCycles, prefix);
+      ok = look_back<O>(states, tile, ws, args.debug ? kDebugBudgetCycles : kBudgetCycles, prefix);
     }
     if (lane == 0) {
       sh_prefix = prefix;
@@ -341,7 +390,7 @@ __global__ void __launch_bounds__(kThreads + 32) scan_kernel(const T *in, T *out
     }
     __syncthreads();                                    // (S) tile total known
     if (ok && lane == 0 && !stall && tile != 0 && !sh_carry_flag)
-      publish<T>(&states[tile], kStatIncl, prefix.plus(Carry<T>::of(sh_carry)));
+      publish<O>(&states[tile], kStatIncl, prefix.plus(CT::of(sh_carry)));
     return;
   }
 
@@ -371,16 +420,16 @@ __global__ void __launch_bounds__(kThreads + 32) scan_kernel(const T *in, T *out
       const int64_t rel = b - t0;
       if (b < tend) atomicOr(&sh_heads[rel >> 5], 1u << (rel & 31));
       if (sums) {
-        if (args.offsets[s - 1] == b) sums[s - 1] = T(0);
+        if (args.offsets[s - 1] == b) sums[s - 1] = O::id();
         else sh_any_end = 1;
       }
     }
     if (sums && tile == 0)                              // empty segments before the first element
-      for (int64_t s = tid; s < sh_seg0; s += kThreads) sums[s] = T(0);
+      for (int64_t s = tid; s < sh_seg0; s += kThreads) sums[s] = O::id();
     if (tid == 0 && args.offsets[sh_seg0] == t0) atomicOr(&sh_heads[0], 1u);
   }
   if (tid == 0) {
-    sh_carry = T(0);
+    sh_carry = O::id();
     sh_carry_flag = 0;
   }
 
@@ -416,7 +465,7 @@ __global__ void __launch_bounds__(kThreads + 32) scan_kernel(const T *in, T *out
     }
 #pragma unroll
     for (int i = 1; i < kItems; ++i)
-      if (!((hmask >> i) & 1u)) v[i] = add_t(v[i - 1], v[i]);
+      if (!((hmask >> i) & 1u)) v[i] = O::comb(v[i - 1], v[i]);
     int f = hmask != 0u;
     T a = v[kItems - 1];
 #pragma unroll
@@ -424,7 +473,7 @@ __global__ void __launch_bounds__(kThreads + 32) scan_kernel(const T *in, T *out
       const T au = __shfl_up_sync(0xffffffffu, a, off);
       const int fu = __shfl_up_sync(0xffffffffu, f, off);
       if (lane >= off) {
-        if (!f) a = add_t(au, a);
+        if (!f) a = O::comb(au, a);
         f |= fu;
       }
     }
@@ -434,23 +483,23 @@ __global__ void __launch_bounds__(kThreads + 32) scan_kernel(const T *in, T *out
     }
     T ex = __shfl_up_sync(0xffffffffu, a, 1);
     int exf = __shfl_up_sync(0xffffffffu, f, 1);
-    if (lane == 0) { ex = T(0); exf = 0; }
+    if (lane == 0) { ex = O::id(); exf = 0; }
     compute_bar();
     if (warp == 0) {                                    // scan of the warp totals
-      T wa = lane < kWarps ? sh_wval[lane] : T(0);
+      T wa = lane < kWarps ? sh_wval[lane] : O::id();
       int wf = lane < kWarps ? sh_wflag[lane] : 0;
 #pragma unroll
       for (int off = 1; off < kWarps; off <<= 1) {
         const T au = __shfl_up_sync(0xffffffffu, wa, off);
         const int fu = __shfl_up_sync(0xffffffffu, wf, off);
         if (lane >= off) {
-          if (!wf) wa = add_t(au, wa);
+          if (!wf) wa = O::comb(au, wa);
           wf |= fu;
         }
       }
       T we = __shfl_up_sync(0xffffffffu, wa, 1);
       int wfe = __shfl_up_sync(0xffffffffu, wf, 1);
-      if (lane == 0) { we = T(0); wfe = 0; }
+      if (lane == 0) { we = O::id(); wfe = 0; }
       const T sub_val = __shfl_sync(0xffffffffu, wa, kWarps - 1);
       const int sub_flag = __shfl_sync(0xffffffffu, wf, kWarps - 1);
       __syncwarp();
@@ -459,7 +508,7 @@ __global__ void __launch_bounds__(kThreads + 32) scan_kernel(const T *in, T *out
         sh_wflag[lane] = wfe;
       }
       if (lane == 0) {                                  // carry after this sub-tile
-        sh_carry = sub_flag ? sub_val : add_t(cv, sub_val);
+        sh_carry = sub_flag ? sub_val : O::comb(cv, sub_val);
         sh_carry_flag = cf | sub_flag;
       }
     }
@@ -467,15 +516,15 @@ __global__ void __launch_bounds__(kThreads + 32) scan_kernel(const T *in, T *out
     // prefix of this thread within the tile: carry, then warp, then thread
     T pv = sh_wval[warp];
     int pf = sh_wflag[warp];
-    if (!exf) ex = add_t(pv, ex);
+    if (!exf) ex = O::comb(pv, ex);
     exf |= pf;                                          // (pf, pv) (+) (exf, ex)
-    const T in_tile = exf ? ex : add_t(cv, ex);
+    const T in_tile = exf ? ex : O::comb(cv, ex);
     const int in_flag = exf | cf;
     unsigned need = 0u;                                 // elements with no head before them
 #pragma unroll
     for (int i = 0; i < kItems; ++i) {
       if ((hmask & ((2u << i) - 1u)) == 0u) {           // before this thread's first head
-        v[i] = add_t(in_tile, v[i]);
+        v[i] = O::comb(in_tile, v[i]);
         if (!in_flag) need |= 1u << i;
       }
     }
@@ -494,13 +543,14 @@ __global__ void __launch_bounds__(kThreads + 32) scan_kernel(const T *in, T *out
   if (tid == 0 && !stall) {
     // publish at once: the inclusive value when nothing before can change it
     // (tile 0, or a tile holding a segment start), else the tile total
-    publish<T>(&states[tile], (tile == 0 || sh_carry_flag) ? kStatIncl : kStatAgg, Carry<T>::of(sh_carry));
+    publish<O>(&states[tile], (tile == 0 || sh_carry_flag) ? kStatIncl : kStatAgg, CT::of(sh_carry));
   }
   __syncthreads();                                      // (S) with the look-back warp
   if (!sh_ok) return;                                   // a wait gave up: write nothing
 
-  // ---- coalesced stores, adding the tile carry where needed
-  const Carry<T> pre = sh_prefix;
+  // ---- coalesced stores, adding the tile carry where needed (the exclusive
+  // form, chosen once per launch, shifts each segment by one)
+  const CT pre = sh_prefix;
 #pragma unroll 1
   for (int s = 0; s < SUB; ++s) {
     const unsigned char *st = ring + s * kStageBytes;
@@ -514,7 +564,32 @@ __global__ void __launch_bounds__(kThreads + 32) scan_kernel(const T *in, T *out
                 __builtin_bit_cast(T, x.w)};
 #pragma unroll
       for (int c = 0; c < 4; ++c)
-        if ((nb >> c) & 1u) y[c] = apply_carry(y[c], pre);
+        if ((nb >> c) & 1u) y[c] = O::apply(y[c], pre);
+      if (EXCL) {                                       // shift by one within each segment
+        const int rel0 = s * kSub + 4 * j;
+        T prev = __shfl_up_sync(0xffffffffu, y[3], 1);  // lane - 1 holds chunk j - 1
+        if (lane == 0) {
+          if (rel0 == 0) {
+            prev = O::apply(O::id(), pre);              // everything before the tile
+          } else {                                      // from the staged tile
+            const int r = rel0 - 1, sb = r / kSub, r2 = r % kSub;
+            const T v = reinterpret_cast<const T *>(ring + sb * kStageBytes + chunk_off(r2 / 4))[r2 % 4];
+            const bool nd = MODE == PLAIN || ((sh_need[sb * kThreads + r2 / kItems] >> (r2 % kItems)) & 1u);
+            prev = nd ? O::apply(v, pre) : v;
+          }
+        }
+        T e[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          bool head;
+          if (MODE == PLAIN) head = g + c == 0;
+          else if (MODE == PERIODIC) head = (g + c) % args.period == 0;
+          else head = (sh_heads[(rel0 + c) >> 5] >> ((rel0 + c) & 31)) & 1u;
+          e[c] = head ? O::id() : (c == 0 ? prev : y[c - 1]);
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) y[c] = e[c];
+      }
       if (vec && g + 4 <= n) {
         x.x = __builtin_bit_cast(int, y[0]);
         x.y = __builtin_bit_cast(int, y[1]);
@@ -540,7 +615,7 @@ __global__ void __launch_bounds__(kThreads + 32) scan_kernel(const T *in, T *out
       const int sub = rel / kSub, r2 = rel % kSub;
       const T *v = reinterpret_cast<const T *>(ring + sub * kStageBytes + chunk_off(r2 / 4));
       T y = v[r2 % 4];
-      if ((sh_need[sub * kThreads + r2 / kItems] >> (r2 % kItems)) & 1u) y = apply_carry(y, pre);
+      if ((sh_need[sub * kThreads + r2 / kItems] >> (r2 % kItems)) & 1u) y = O::apply(y, pre);
       sums[s - 1] = y;
     }
   }
@@ -555,7 +630,7 @@ constexpr int kSubCands[] = {4, 2, 1};
 static_assert(kSub * kSubCands[0] == kScanNoallocTile, "the no-alloc scan runs candidate 0");
 constexpr int kNumSubCands = 3;
 
-template <class T, int MODE, int SUB>
+template <class T, class O, int MODE, int SUB, bool EXCL = false>
 int32_t run_scan_t(const T *in, T *out, const ScanArgs &a, void *ws, size_t ws_bytes, cudaStream_t s) {
   constexpr int kTile = kSub * SUB;
   const int64_t ntiles = (a.n + kTile - 1) / kTile;
@@ -566,23 +641,34 @@ int32_t run_scan_t(const T *in, T *out, const ScanArgs &a, void *ws, size_t ws_b
   const int smem = SUB * kStageBytes;
   static bool attr = false;
   if (!attr) {
-    DESC_CUDA_TRY(cudaFuncSetAttribute(scan_kernel<T, MODE, SUB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    DESC_CUDA_TRY(
+        cudaFuncSetAttribute(scan_kernel<T, O, MODE, SUB, EXCL>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     attr = true;
   }
   DESC_CUDA_TRY(cudaMemsetAsync(ws, 0, need, s));
   ScanWs *w = static_cast<ScanWs *>(ws);
   TileState *st = reinterpret_cast<TileState *>(static_cast<char *>(ws) + align256(sizeof(ScanWs)));
-  scan_kernel<T, MODE, SUB><<<(unsigned)ntiles, kThreads + 32, smem, s>>>(in, out, a, w, st);
+  scan_kernel<T, O, MODE, SUB, EXCL><<<(unsigned)ntiles, kThreads + 32, smem, s>>>(in, out, a, w, st);
   DESC_CUDA_TRY(cudaGetLastError());
   return DESC_OK;
 }
 
+// Inclusive sums take every schedule candidate; maximum, minimum and the
+// exclusive forms the default tile.
 template <class T, int MODE>
-int32_t run_scan(const T *in, T *out, const ScanArgs &a, void *ws, size_t ws_bytes, cudaStream_t s, int cand) {
+int32_t run_scan(const T *in, T *out, const ScanArgs &a, void *ws, size_t ws_bytes, cudaStream_t s, int cand,
+                 int32_t flags) {
+  if (flags & DESC_EXCLUSIVE) {
+    if (flags & DESC_MAX) return run_scan_t<T, ExtOp<T, true>, MODE, 4, true>(in, out, a, ws, ws_bytes, s);
+    if (flags & DESC_MIN) return run_scan_t<T, ExtOp<T, false>, MODE, 4, true>(in, out, a, ws, ws_bytes, s);
+    return run_scan_t<T, SumOp<T>, MODE, 4, true>(in, out, a, ws, ws_bytes, s);
+  }
+  if (flags & DESC_MAX) return run_scan_t<T, ExtOp<T, true>, MODE, 4>(in, out, a, ws, ws_bytes, s);
+  if (flags & DESC_MIN) return run_scan_t<T, ExtOp<T, false>, MODE, 4>(in, out, a, ws, ws_bytes, s);
   switch (kSubCands[(cand >= 0 && cand < kNumSubCands) ? cand : 0]) {
-    case 1: return run_scan_t<T, MODE, 1>(in, out, a, ws, ws_bytes, s);
-    case 2: return run_scan_t<T, MODE, 2>(in, out, a, ws, ws_bytes, s);
-    default: return run_scan_t<T, MODE, 4>(in, out, a, ws, ws_bytes, s);
+    case 1: return run_scan_t<T, SumOp<T>, MODE, 1>(in, out, a, ws, ws_bytes, s);
+    case 2: return run_scan_t<T, SumOp<T>, MODE, 2>(in, out, a, ws, ws_bytes, s);
+    default: return run_scan_t<T, SumOp<T>, MODE, 4>(in, out, a, ws, ws_bytes, s);
   }
 }
 
@@ -614,13 +700,13 @@ int32_t launch_scan_contig(int32_t dtype, const void *in, void *out, int64_t n, 
   if (dtype == DESC_I32) {
     auto i = static_cast<const int32_t *>(in);
     auto o = static_cast<int32_t *>(out);
-    return periodic ? run_scan<int32_t, PERIODIC>(i, o, a, ws, ws_bytes, s, cand)
-                    : run_scan<int32_t, PLAIN>(i, o, a, ws, ws_bytes, s, cand);
+    return periodic ? run_scan<int32_t, PERIODIC>(i, o, a, ws, ws_bytes, s, cand, flags)
+                    : run_scan<int32_t, PLAIN>(i, o, a, ws, ws_bytes, s, cand, flags);
   }
   auto i = static_cast<const float *>(in);
   auto o = static_cast<float *>(out);
-  return periodic ? run_scan<float, PERIODIC>(i, o, a, ws, ws_bytes, s, cand)
-                  : run_scan<float, PLAIN>(i, o, a, ws, ws_bytes, s, cand);
+  return periodic ? run_scan<float, PERIODIC>(i, o, a, ws, ws_bytes, s, cand, flags)
+                  : run_scan<float, PLAIN>(i, o, a, ws, ws_bytes, s, cand, flags);
 }
 
 size_t scan_csr_ws(int64_t n) { return scan_contig_ws(DESC_F32, n); }
@@ -638,9 +724,9 @@ int32_t launch_scan_csr(int32_t dtype, const void *in, void *out, int64_t n, con
   a.vec = ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15) == 0;
   if (dtype == DESC_I32)
     return run_scan<int32_t, CSR>(static_cast<const int32_t *>(in), static_cast<int32_t *>(out), a,
-                                  ws, ws_bytes, s, cand);
+                                  ws, ws_bytes, s, cand, flags);
   return run_scan<float, CSR>(static_cast<const float *>(in), static_cast<float *>(out), a, ws,
-                              ws_bytes, s, cand);
+                              ws_bytes, s, cand, flags);
 }
 
 }  // namespace desc

@@ -134,3 +134,85 @@ def test_view_copy_leaves_unreached_elements():
     x = np.arange(10, dtype=np.float32)
     out = O.view_copy(x, np.full(10, -7.0, np.float32), [10], [("split_fst", 4, 0)], [10], [("split_snd", 6, 0)])
     assert out.tolist() == [-7.0] * 6 + [0.0, 1.0, 2.0, 3.0]
+
+
+# ---- other operators: maximum, minimum, exclusive scans ----------------------
+def test_max_min_closed_forms():
+    n = 1000
+    x = np.arange(1, n + 1, dtype=np.int32)[::-1].copy()            # n .. 1
+    assert O.reduce_op(x, [n], [], V.GRID, "max")[0] == n
+    assert O.reduce_op(x, [n], [], V.GRID, "min")[0] == 1
+    # per block of 10: the block's first element is its maximum (decreasing data)
+    got = O.reduce_op(x, [n], [("group", 10, 0), ("select", V.BLOCK, V.X)], V.BLOCK, "max")
+    assert np.array_equal(got, x[::10])
+    xf = np.array([-3.5, -1.25, -7.0], np.float32)
+    assert O.reduce_op(xf, [3], [], V.GRID, "max")[0] == -1.25   # all negative: not 0
+    assert O.reduce_op(xf, [3], [], V.GRID, "min")[0] == -7.0
+
+
+def test_max_ignores_nan_and_identity_of_empty():
+    xf = np.array([np.nan, 2.0, np.nan, -1.0], np.float32)
+    assert O.reduce_op(xf, [4], [], V.GRID, "max")[0] == 2.0
+    assert O.reduce_op(xf, [4], [], V.GRID, "min")[0] == -1.0
+    assert np.isnan(O.reduce_op(np.array([np.nan], np.float32), [1], [], V.GRID, "max")[0])
+    _, tot, _, _ = O.segmented_op(np.zeros(3, np.int32), [0, 0, 3], "max")
+    assert tot[0] == np.iinfo(np.int32).min and tot[1] == 0
+    _, tot, _, _ = O.segmented_op(np.zeros(3, np.float32), [0, 3, 3], "min")
+    assert tot[1] == np.inf
+
+
+def test_exclusive_scan_closed_forms():
+    n = 500
+    ones = np.ones(n, np.int32)
+    out, _ = O.scan_op(ones, np.zeros(n, np.int32), [n], [], V.GRID, "sum", True)
+    assert np.array_equal(out, np.arange(n))                          # i ones before point i
+    x = np.arange(1, n + 1, dtype=np.int32)
+    out, _ = O.scan_op(x, np.zeros(n, np.int32), [n], [], V.GRID, "sum", True)
+    i = np.arange(n)
+    assert np.array_equal(out, i * (i + 1) // 2)
+    out, _ = O.scan_op(x, np.zeros(n, np.int32), [n], [], V.GRID, "max", True)
+    assert out[0] == np.iinfo(np.int32).min and np.array_equal(out[1:], x[:-1])   # increasing data
+    out, _ = O.scan_op(x, np.zeros(n, np.int32), [n], [], V.GRID, "min", False)
+    assert np.all(out == 1)
+
+
+def test_operators_brute_force_small():
+    rng = np.random.default_rng(7)
+    for trial in range(20):
+        m = int(rng.integers(1, 9))
+        g = int(rng.integers(1, 9))
+        n = m * g
+        x = rng.integers(-50, 50, size=n).astype(np.int32)
+        ops = [("group", m, 0), ("select", V.BLOCK, V.X)]
+        for op, f in (("max", max), ("min", min)):
+            want = [f(x[k * m:(k + 1) * m].tolist()) for k in range(g)]
+            assert O.reduce_op(x, [n], ops, V.BLOCK, op).tolist() == want
+            for excl in (False, True):
+                got, _ = O.scan_op(x, np.zeros(n, np.int32), [n], ops, V.BLOCK, op, excl)
+                for k in range(g):
+                    seg = x[k * m:(k + 1) * m].tolist()
+                    for i in range(m):
+                        part = seg[:i] if excl else seg[:i + 1]
+                        exp = f(part) if part else (-2 ** 31 if op == "max" else 2 ** 31 - 1)
+                        assert got[k * m + i] == exp
+        # exclusive sums are the inclusive ones shifted within each segment
+        inc, _ = O.scan_op(x, np.zeros(n, np.int32), [n], ops, V.BLOCK, "sum", False)
+        exc, _ = O.scan_op(x, np.zeros(n, np.int32), [n], ops, V.BLOCK, "sum", True)
+        assert np.array_equal(inc - x, exc)
+
+
+def test_segmented_operators_match_per_segment_definition():
+    rng = np.random.default_rng(11)
+    L = rng.integers(0, 7, size=30)
+    off = np.concatenate([[0], np.cumsum(L)])
+    x = rng.integers(-9, 9, size=int(off[-1])).astype(np.int32)
+    for op in ("sum", "max", "min"):
+        for excl in (False, True):
+            sc, tot, _, _ = O.segmented_op(x, off, op, excl)
+            for s in range(30):
+                a, b = off[s], off[s + 1]
+                want, _ = O.scan_op(x[a:b], np.zeros(b - a, np.int32), [int(b - a)], [], V.GRID, op, excl) \
+                    if b > a else (np.zeros(0, np.int32), None)
+                assert np.array_equal(sc[a:b], want)
+                if b > a and not excl:
+                    assert tot[s] == sc[b - 1]          # total = last inclusive value
