@@ -3,8 +3,10 @@
 // Three schedules, picked on the host from the lowered map:
 //  * runs:   every output sums one contiguous run of `len` elements, runs
 //            starting at start + o * seg_stride.  Long runs are cut into
-//            chunks, one CTA per (run, chunk); each CTA streams its chunk with
-//            128-bit evict-first loads, UNROLL vectors in flight per thread,
+//            chunks, one CTA per (run, chunk); the chunks interleave in
+//            stripes of UNROLL x 256 vectors (all CTAs of a run sweep the run
+//            together), read with 128-bit loads, UNROLL vectors in flight per
+//            thread,
 //            merges warp-wide with shuffles and block-wide through shared
 //            memory; the last CTA of a run (atomic ticket) merges the chunk
 //            partials in chunk order.  Short runs go one warp or one thread
@@ -135,7 +137,7 @@ __device__ __forceinline__ V ld_vec(const V *p) {
 template <class A, class T, int kUnroll, int NC>
 __global__ void __launch_bounds__(kThreads) reduce_runs_kernel(
     const T *__restrict__ in, int64_t start, int64_t seg_stride, int64_t len, int64_t chunks,
-    int64_t chunk_vec, T *__restrict__ out, uint2 *partials, unsigned *counters) {
+    int64_t /*chunk_vec*/, T *__restrict__ out, uint2 *partials, unsigned *counters) {
   using V = typename Vec<T>::type;
   __shared__ A sh[kThreads / 32];
   const int64_t o = blockIdx.x / chunks, c = blockIdx.x % chunks;
@@ -147,16 +149,22 @@ __global__ void __launch_bounds__(kThreads) reduce_runs_kernel(
   A a;
   a.init();
   const V *pv = reinterpret_cast<const V *>(p + head);
-  const int64_t v0 = c * chunk_vec, v1 = std::min<int64_t>(nvec, v0 + chunk_vec);
-  int64_t i = v0 + threadIdx.x;
-  for (; i + (kUnroll - 1) * kThreads < v1; i += kUnroll * kThreads) {
+  // The run's vectors in stripes of kUnroll x kThreads; CTA c takes stripes
+  // c, c + chunks, ... so that the CTAs of a run read neighbouring stripes
+  // at the same time (DRAM rows stay open across the GPU) rather than each
+  // walking a distant chunk of its own.
+  constexpr int64_t kStripe = int64_t(kUnroll) * kThreads;
+  const int64_t step = chunks * kStripe;
+  int64_t b = c * kStripe;
+  for (; b + kStripe <= nvec; b += step) {
     V x[kUnroll];
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) x[u] = ld_vec<NC>(pv + i + u * kThreads);
+    for (int u = 0; u < kUnroll; ++u) x[u] = ld_vec<NC>(pv + b + u * kThreads + threadIdx.x);
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) a.add4(x[u]);
   }
-  for (; i < v1; i += kThreads) a.add4(ld_vec<NC>(pv + i));
+  if (b < nvec)                                        // the last, partial stripe
+    for (int64_t i = b + threadIdx.x; i < nvec; i += kThreads) a.add4(ld_vec<NC>(pv + i));
   if (c == 0 && threadIdx.x < head) a.add1(p[threadIdx.x]);
   if (c == chunks - 1 && threadIdx.x < tail) a.add1(p[head + 4 * nvec + threadIdx.x]);
   block_merge<A, kThreads>(a, sh);
@@ -211,14 +219,19 @@ __global__ void __launch_bounds__(kThreads) reduce_affine_kernel(
   a.init();
   const int64_t q1 = std::min<int64_t>(args.n_rest, (c + 1) * chunk_len);
   if (VEC) {
+    // stripes of 4 x U x kThreads points; CTA c takes stripes c, c + chunks,
+    // ... (the CTAs of an output sweep its points together)
     using V4 = typename std::conditional<std::is_same<T, float>::value, float4, int4>::type;
     constexpr int U = 4;                               // groups in flight per thread
-    for (int64_t q0 = c * chunk_len + 4 * threadIdx.x; q0 < q1; q0 += 4 * U * kThreads) {
+    constexpr int64_t kStripe = int64_t(4) * U * kThreads;
+    const int64_t qend = args.n_rest;
+    for (int64_t s0 = c * kStripe; s0 < qend; s0 += chunks * kStripe) {
+      const int64_t q0 = s0 + 4 * threadIdx.x;
       V4 v[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int64_t q = q0 + int64_t(u) * 4 * kThreads;
-        if (q < q1) {
+        if (q < qend) {
           int64_t e = base;
           uint32_t t = (uint32_t)q;
           for (int d = args.nrest - 1; d > 0; --d) {
@@ -232,7 +245,7 @@ __global__ void __launch_bounds__(kThreads) reduce_affine_kernel(
       }
 #pragma unroll
       for (int u = 0; u < U; ++u)
-        if (q0 + int64_t(u) * 4 * kThreads < q1) a.add4(v[u]);
+        if (q0 + int64_t(u) * 4 * kThreads < qend) a.add4(v[u]);
     }
   } else
   for (int64_t q = c * chunk_len + threadIdx.x; q < q1; q += kThreads) {
