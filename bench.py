@@ -255,6 +255,7 @@ def run_ours(args, rank, world, local_rank):
         line["matmul"] = run_matmul(torch, D, dev, stream, pk)
         line["segmented"] = run_segmented(torch, D, synth, dev, stream)
         line["view_overhead"] = run_view_overhead(torch, D, synth, dev, stream)
+        line["split_launch"] = run_split_launch(torch, D, synth, dev)
         if not args.no_model:
             line["schedule_model"] = run_schedule_model(torch, D, synth)
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -448,6 +449,63 @@ def run_view_overhead(torch, D, synth, dev, stream, reps=100, mbs=(256, 512, 102
     return out
 
 
+def run_split_launch(torch, D, synth, dev, iters=20, replays=10):
+    """One launch whose first blocks reduce and whose other blocks transpose
+    (desc_split_reduce_transpose) against the two separate launches, both
+    captured in CUDA graphs (so host time does not enter), per iteration:
+    small (int32 reduce of 2^20, 1024^2 transpose) and large (2^28, 8192^2)."""
+    import ctypes
+    res = {}
+    D.desc_force_candidate(D.OP_REDUCE, 0)              # the schedule the split launch runs
+    try:
+        for name, n, T in (("small", 1 << 20, 1024), ("large", 1 << 28, 8192)):
+            x = synth.ints_pm1000(n, seed=21, device=dev)
+            t = synth.normal_f32(T * T, seed=22, device=dev).reshape(T, T)
+            to = torch.empty(T, T, device=dev)
+            r = torch.empty(1, dtype=torch.int32, device=dev)
+            nb = ctypes.c_size_t(0)
+            D.lib().desc_reduce_workspace_size(ctypes.byref(D.make_view([n], [])), None, D.GRID, D.I32,
+                                               ctypes.byref(nb))
+            ws = torch.empty(max(nb.value, 1), dtype=torch.uint8, device=dev)
+            side = torch.cuda.Stream(dev)
+
+            def sep(st):
+                D.desc_reduce(x, [n], [], D.GRID, out=r, ws=ws, stream=st)
+                D.desc_transpose(t, [T, T], [("transpose", 0)], to, [T, T], [], stream=st)
+
+            def fused(st):
+                D.desc_split_reduce_transpose(x, [n], [], D.GRID, None, None, t, to, out=r, ws=ws, stream=st)
+
+            times = {}
+            for key, fn in (("separate", sep), ("split", fused)):
+                with torch.cuda.stream(side):
+                    fn(side)                              # warm-up outside the capture
+                torch.cuda.synchronize()
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g, stream=side):
+                    for _ in range(iters):
+                        fn(side)
+                g.replay()
+                torch.cuda.synchronize()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                for _ in range(replays):
+                    g.replay()
+                b.record()
+                torch.cuda.synchronize()
+                times[key] = a.elapsed_time(b) / (replays * iters)
+            total = int(x.to(torch.int64).sum().item())
+            if int(r.item()) != ((total + (1 << 31)) % (1 << 32)) - (1 << 31):   # int32 wrap-around
+                raise RuntimeError("split launch reduce result")
+            res[name] = {"reduce_n": n, "transpose": [T, T], "separate_us": round(1000 * times["separate"], 2),
+                         "split_us": round(1000 * times["split"], 2),
+                         "speedup": round(times["separate"] / times["split"], 3)}
+            del x, t, to, ws
+    finally:
+        D.desc_force_candidate(D.OP_REDUCE, -1)
+    return res
+
+
 def run_segmented(torch, D, synth, dev, stream, nseg=20000):
     """20,000 FP32 segments, lengths log-uniform in [1, 2^20]: every segment
     reduced and inclusive-scanned.  One graph-captured persistent launch vs.
@@ -639,7 +697,7 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="time the default schedules, without autotuning")
     ap.add_argument("--save-tune", default="", help="save the tuned schedule table to this file")
     ap.add_argument("--load-tune", default="", help="use a saved schedule table instead of tuning")
-    ap.add_argument("--case", choices=["step", "matmul", "segmented", "overhead"], default="step",
+    ap.add_argument("--case", choices=["step", "matmul", "segmented", "overhead", "split"], default="step",
                     help="matmul / segmented: run only that measurement (for profiler captures)")
     ap.add_argument("--mm-n", type=int, default=8192, help="matmul size for --case matmul")
     ap.add_argument("--mm-prec", default="split3,bf16,fp32_simt",
@@ -672,6 +730,8 @@ def main():
         if args.case == "matmul":
             line = {"case": "matmul", "matmul": run_matmul(torch, D, dev, stream, peaks(), n=args.mm_n,
                                                            forms=args.mm_prec.split(","), quick=args.mm_quick)}
+        elif args.case == "split":
+            line = {"case": "split", "split_launch": run_split_launch(torch, D, synth, dev)}
         elif args.case == "overhead":
             line = {"case": "overhead", "view_overhead": run_view_overhead(torch, D, synth, dev, stream)}
         else:

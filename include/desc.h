@@ -347,6 +347,23 @@ int32_t desc_matmul(const desc_view *a_v, const desc_view *b_v, int64_t M, int64
                     size_t a_bytes, const float *B, size_t b_bytes, float *C, size_t c_bytes, int32_t precision,
                     void *ws, size_t ws_bytes, desc_stream_t stream);
 
+/* ---- Split launch: two ops on the two parts of one grid -------------------
+ * Section 3.3 splits an execution resource so that its parts run different
+ * code.  desc_split_reduce_transpose runs ONE kernel launch whose first
+ * blocks compute what desc_reduce computes for the view `rv` (sum; the view
+ * must reduce contiguous runs longer than 4096 elements, e.g. the whole
+ * array or group<k>[[block]] with k > 4096, else DESC_ERR_UNSUPPORTED) and
+ * whose other blocks transpose the row-major R x C FP32 matrix tin into the
+ * C x R matrix tout (what desc_transpose computes for a transpose view).
+ * The four buffers must not overlap (DESC_ERR_OVERLAP): the two parts are
+ * disjoint, which is what makes them safe to run concurrently.  ws: at least
+ * desc_reduce_workspace_size for rv.  Results are bit-identical to the two
+ * separate calls with the default schedules. */
+int32_t desc_split_reduce_transpose(const desc_view *rv, const desc_exec *rex, int32_t out_level, int32_t dtype,
+                                    const void *rin, size_t rin_bytes, void *rout, size_t rout_bytes, void *ws,
+                                    size_t ws_bytes, const float *tin, float *tout, int64_t R, int64_t C,
+                                    desc_stream_t stream);
+
 /* ---- Segmented reduce + scan (batched) -------------------------------------
  * Many independent segments in one launch: segment s is in[offsets[s] ..
  * offsets[s+1]) of a contiguous array of `total` elements.  For every segment

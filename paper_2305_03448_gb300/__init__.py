@@ -110,6 +110,9 @@ def _declare(L):
         "desc_lower_view": (c_int32, [POINTER(View), POINTER(Exec), POINTER(Lowered)]),
         "desc_check_disjoint": (c_int32, [POINTER(Access), c_int32, POINTER(Exec), POINTER(c_int64)]),
         "desc_check_program": (c_int32, [POINTER(Stmt), c_int32, POINTER(Exec), POINTER(c_int32), POINTER(c_int64)]),
+        "desc_split_reduce_transpose": (c_int32, [POINTER(View), POINTER(Exec), c_int32, c_int32, c_void_p, c_size_t,
+                                                  c_void_p, c_size_t, c_void_p, c_size_t, c_void_p, c_void_p, c_int64,
+                                                  c_int64, c_void_p]),
         "desc_reduce_workspace_size": (c_int32, [POINTER(View), POINTER(Exec), c_int32, c_int32, POINTER(c_size_t)]),
         "desc_reduce": (c_int32, [POINTER(View), POINTER(Exec), c_int32, c_int32, P, c_size_t, P, c_size_t,
                                   c_int32, P, c_size_t, P]),
@@ -356,6 +359,32 @@ def desc_scan(x, base_shape, ops, seg_level, grid=None, block=None, out=None, ws
         ws = _workspace(nb.value, x.device)
     _check(L.desc_scan(ctypes.byref(v), _ref(e), seg_level, dt, _ptr(x), x.numel() * 4, _ptr(out),
                        out.numel() * 4, flags, _ptr(ws), ws.numel(), _stream(stream)), "desc_scan")
+    return out
+
+
+def desc_split_reduce_transpose(x, base_shape, ops, out_level, grid, block, t_in, t_out, out=None, ws=None,
+                                stream=None):
+    """One launch: the sum of x through a view (as desc_reduce) on the first
+    blocks, t_out = t_in^T (2-D FP32) on the others.  Returns ``out``."""
+    import torch
+    L = lib()
+    v, e = make_view(base_shape, ops), make_exec(grid, block)
+    if out is None:
+        low = desc_lower_view(base_shape, ops, grid, block)
+        nout = 1
+        for i in range(low["nsel"]):
+            if low["level"][i] <= out_level:
+                nout *= low["extent"][i]
+        out = torch.empty(nout, dtype=x.dtype, device=x.device)
+    if ws is None:
+        nb = c_size_t(0)
+        _check(L.desc_reduce_workspace_size(ctypes.byref(v), _ref(e), out_level, _dtype_code(x), ctypes.byref(nb)),
+               "desc_reduce_workspace_size")
+        ws = _workspace(nb.value, x.device)
+    R, C = t_in.shape
+    _check(L.desc_split_reduce_transpose(ctypes.byref(v), _ref(e), out_level, _dtype_code(x), _ptr(x), x.numel() * 4,
+                                         _ptr(out), out.numel() * 4, _ptr(ws), ws.numel(), _ptr(t_in), _ptr(t_out),
+                                         int(R), int(C), _stream(stream)), "desc_split_reduce_transpose")
     return out
 
 

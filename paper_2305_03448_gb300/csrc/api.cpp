@@ -111,6 +111,32 @@ extern "C" int32_t desc_reduce(const desc_view *v, const desc_exec *ex, int32_t 
   return launch_reduce_affine(dtype, in, p, out, flags, ws, ws_bytes, s);
 }
 
+// ---------------------------------------------------------------- split launch
+extern "C" int32_t desc_split_reduce_transpose(const desc_view *rv, const desc_exec *rex, int32_t out_level,
+                                               int32_t dtype, const void *rin, size_t rin_bytes, void *rout,
+                                               size_t rout_bytes, void *ws, size_t ws_bytes, const float *tin,
+                                               float *tout, int64_t R, int64_t C, desc_stream_t s) {
+  if (!dtype_size(dtype) || R < 0 || C < 0) return DESC_ERR_INVALID_ARG;
+  if (out_level < DESC_LEVEL_GRID || out_level > DESC_LEVEL_THREAD) return DESC_ERR_INVALID_ARG;
+  desc_lowered L;
+  int32_t r = desc_lower_view(rv, rex, &L);
+  if (r != DESC_OK) return r;
+  const Plan p = split_plan(L, out_level);
+  if (rin_bytes != size_t(L.base_elems) * 4 || rout_bytes != size_t(p.n_keep) * 4) return DESC_ERR_SIZE_MISMATCH;
+  int64_t start0, seg;
+  if (p.n_keep == 0 || p.n_rest == 0 || !rest_contiguous(p, true, &start0, &seg)) return DESC_ERR_UNSUPPORTED;
+  const size_t tb = size_t(R) * size_t(C) * 4;
+  if ((r = check_device_ptr(rout, 4)) != DESC_OK || (r = check_device_ptr(rin, 4)) != DESC_OK) return r;
+  if (tb && ((r = check_device_ptr(tin, 4)) != DESC_OK || (r = check_device_ptr(tout, 4)) != DESC_OK)) return r;
+  const void *bufs[4] = {rin, rout, tin, tout};
+  const size_t sizes[4] = {rin_bytes, rout_bytes, tb, tb};
+  for (int i = 0; i < 4; ++i)
+    for (int j = i + 1; j < 4; ++j)
+      if (ranges_overlap(bufs[i], sizes[i], bufs[j], sizes[j])) return DESC_ERR_OVERLAP;
+  return launch_split_reduce_transpose(dtype, rin, start0, seg, p.n_rest, p.n_keep, rout, ws, ws_bytes, tin, tout,
+                                       R, C, s);
+}
+
 // ---------------------------------------------------------------- scan
 namespace {
 

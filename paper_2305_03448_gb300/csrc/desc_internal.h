@@ -62,6 +62,11 @@ int reduce_candidates();
 size_t reduce_segments_ws(int32_t dtype, int64_t len, int64_t nout);
 // Reduce: general affine plan (chunk partials in ws when runs are long).
 size_t reduce_affine_ws(int64_t n_rest, int64_t nout);
+// One grid: the chunked reduce of runs (sum, default schedule) on its first
+// blocks, the 64 x 64 tiled transpose of an R x C FP32 matrix on the rest.
+int32_t launch_split_reduce_transpose(int32_t dtype, const void *in, int64_t start, int64_t seg_stride,
+                                      int64_t len, int64_t nout, void *out, void *ws, size_t ws_bytes,
+                                      const float *tin, float *tout, int64_t R, int64_t C, desc_stream_t s);
 // out[0 .. count) = the identity of the operator flags select (DESC_MAX,
 // DESC_MIN, else the sum) in dtype.
 int32_t fill_identity(void *out, int64_t count, int32_t dtype, int32_t flags, desc_stream_t s);

@@ -11,6 +11,7 @@
 // thread and iteration, indices decoded from the domain extents.
 #include <algorithm>
 
+#include "k_bodies.cuh"
 #include "k_common.cuh"
 
 namespace desc {
@@ -22,40 +23,8 @@ __global__ void __launch_bounds__(32 * BR) transpose_kernel(const float *__restr
                                                             int64_t C, int64_t ld_in, int64_t ld_out,
                                                             int64_t bs_in, int64_t bs_out) {
   __shared__ float tile[TD][TD + 1];
-  const int64_t b = blockIdx.z;
-  const float *src = in + b * bs_in;
-  float *dst = out + b * bs_out;
-  const int64_t r0 = int64_t(blockIdx.y) * TD, c0 = int64_t(blockIdx.x) * TD;
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  const bool interior = (r0 + TD <= R) && (c0 + TD <= C);
-  if (interior) {
-#pragma unroll
-    for (int j = 0; j < TD; j += BR)
-#pragma unroll
-      for (int i = 0; i < TD; i += 32)
-        tile[ty + j][tx + i] = __ldcs(src + (r0 + ty + j) * ld_in + c0 + tx + i);
-  } else {
-    for (int j = 0; j < TD; j += BR)
-      for (int i = 0; i < TD; i += 32) {
-        const int64_t r = r0 + ty + j, c = c0 + tx + i;
-        if (r < R && c < C) tile[ty + j][tx + i] = src[r * ld_in + c];
-      }
-  }
-  __syncthreads();
-  // out[c][r] = in[r][c]: output row c0 + ty + j, output column r0 + tx + i
-  if (interior) {
-#pragma unroll
-    for (int j = 0; j < TD; j += BR)
-#pragma unroll
-      for (int i = 0; i < TD; i += 32)
-        __stcs(dst + (c0 + ty + j) * ld_out + r0 + tx + i, tile[tx + i][ty + j]);
-  } else {
-    for (int j = 0; j < TD; j += BR)
-      for (int i = 0; i < TD; i += 32) {
-        const int64_t c = c0 + ty + j, r = r0 + tx + i;
-        if (r < R && c < C) dst[c * ld_out + r] = tile[tx + i][ty + j];
-      }
-  }
+  transpose_tile<TD, BR>(in, out, R, C, ld_in, ld_out, bs_in, bs_out, blockIdx.x, blockIdx.y, blockIdx.z,
+                         threadIdx.x, threadIdx.y, tile);
 }
 
 struct CopyArgs {

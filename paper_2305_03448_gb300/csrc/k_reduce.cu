@@ -19,6 +19,7 @@
 
 #include <type_traits>
 
+#include "k_bodies.cuh"
 #include "k_common.cuh"
 
 namespace desc {
@@ -133,14 +134,15 @@ __device__ __forceinline__ V ld_vec(const V *p) {
   return ld_stream(p);
 }
 
-// One CTA per (run, chunk).  grid.x = nout * chunks.
+// The work of CTA `blk` of the chunked reduce: run blk / chunks, chunk
+// blk % chunks.
 template <class A, class T, int kUnroll, int NC>
-__global__ void __launch_bounds__(kThreads) reduce_runs_kernel(
-    const T *__restrict__ in, int64_t start, int64_t seg_stride, int64_t len, int64_t chunks,
-    int64_t /*chunk_vec*/, T *__restrict__ out, uint2 *partials, unsigned *counters) {
+__device__ __forceinline__ void reduce_runs_block(const T *__restrict__ in, int64_t start, int64_t seg_stride,
+                                                  int64_t len, int64_t chunks, T *__restrict__ out,
+                                                  uint2 *partials, unsigned *counters, int64_t blk) {
   using V = typename Vec<T>::type;
   __shared__ A sh[kThreads / 32];
-  const int64_t o = blockIdx.x / chunks, c = blockIdx.x % chunks;
+  const int64_t o = blk / chunks, c = blk % chunks;
   const T *p = in + start + o * seg_stride;
   const int64_t mis = (reinterpret_cast<uintptr_t>(p) & 15) / sizeof(T);
   const int64_t head = std::min<int64_t>(len, mis ? 4 - mis : 0);
@@ -169,6 +171,38 @@ __global__ void __launch_bounds__(kThreads) reduce_runs_kernel(
   if (c == chunks - 1 && threadIdx.x < tail) a.add1(p[head + 4 * nvec + threadIdx.x]);
   block_merge<A, kThreads>(a, sh);
   finish_chunk<A, T>(a, sh, o, c, chunks, out, partials, counters);
+}
+
+// One CTA per (run, chunk).  grid.x = nout * chunks.
+template <class A, class T, int kUnroll, int NC>
+__global__ void __launch_bounds__(kThreads) reduce_runs_kernel(
+    const T *__restrict__ in, int64_t start, int64_t seg_stride, int64_t len, int64_t chunks,
+    int64_t /*chunk_vec*/, T *__restrict__ out, uint2 *partials, unsigned *counters) {
+  reduce_runs_block<A, T, kUnroll, NC>(in, start, seg_stride, len, chunks, out, partials, counters, blockIdx.x);
+}
+
+// A split launch (Section 3.3: the parts of a split resource run different
+// code): blocks [0, nred) reduce runs as reduce_runs_kernel, the others
+// transpose a matrix in 64 x 64 tiles as transpose_kernel (256 threads seen
+// as 32 x 8).  Each block runs one part entirely, so the barriers inside each
+// part are reached by all of its threads.
+struct SplitTranspose {
+  const float *in;
+  float *out;
+  int64_t R, C, gx;
+};
+template <class A, class T>
+__global__ void __launch_bounds__(kThreads) split_reduce_transpose_kernel(
+    const T *__restrict__ in, int64_t start, int64_t seg_stride, int64_t len, int64_t chunks, T *__restrict__ out,
+    uint2 *partials, unsigned *counters, int64_t nred, SplitTranspose tr) {
+  __shared__ float tile[64][65];
+  if (int64_t(blockIdx.x) < nred) {
+    reduce_runs_block<A, T, 8, 0>(in, start, seg_stride, len, chunks, out, partials, counters, blockIdx.x);
+  } else {
+    const int64_t t = int64_t(blockIdx.x) - nred;
+    transpose_tile<64, 8>(tr.in, tr.out, tr.R, tr.C, tr.C, tr.R, 0, 0, t % tr.gx, t / tr.gx, 0,
+                          threadIdx.x & 31, threadIdx.x >> 5, tile);
+  }
 }
 
 // GROUP threads per output (GROUP = 1 or 32), grid-stride over outputs.
@@ -435,6 +469,40 @@ int32_t launch_reduce_affine(int32_t dtype, const void *in, const Plan &p, void 
                                        ws, ws_bytes, s);
   return run_affine<AccF32, float>(static_cast<const float *>(in), p, static_cast<float *>(out), ws,
                                    ws_bytes, s);
+}
+
+int32_t launch_split_reduce_transpose(int32_t dtype, const void *in, int64_t start, int64_t seg_stride,
+                                      int64_t len, int64_t nout, void *out, void *ws, size_t ws_bytes,
+                                      const float *tin, float *tout, int64_t R, int64_t C, desc_stream_t st) {
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(st);
+  if (len <= kWarpRun) return DESC_ERR_UNSUPPORTED;   // the chunked schedule only
+  const ReduceCand &cd = kCands[0];
+  const int64_t chunks = chunks_for(len, nout, cd);
+  uint2 *partials = nullptr;
+  unsigned *counters = nullptr;
+  if (chunks > 1) {
+    if (!ws || ws_bytes < ws_for(len, nout)) return DESC_ERR_WORKSPACE;
+    partials = static_cast<uint2 *>(ws);
+    counters = reinterpret_cast<unsigned *>(static_cast<char *>(ws) +
+                                            align256(size_t(nout) * max_chunks(len, nout) * sizeof(uint2)));
+    DESC_CUDA_TRY(cudaMemsetAsync(counters, 0, size_t(nout) * sizeof(unsigned), s));
+  }
+  const int64_t nred = nout * chunks;
+  SplitTranspose tr{tin, tout, R, C, (C + 63) / 64};
+  const int64_t ntr = tr.gx * ((R + 63) / 64);
+  if (nred + ntr >= (int64_t(1) << 31)) return DESC_ERR_UNSUPPORTED;
+  const unsigned grid = (unsigned)(nred + ntr);
+  if (grid == 0) return DESC_OK;
+  if (dtype == DESC_I32)
+    split_reduce_transpose_kernel<AccI32, int32_t><<<grid, kThreads, 0, s>>>(
+        static_cast<const int32_t *>(in), start, seg_stride, len, chunks, static_cast<int32_t *>(out), partials,
+        counters, nred, tr);
+  else
+    split_reduce_transpose_kernel<AccF32, float><<<grid, kThreads, 0, s>>>(
+        static_cast<const float *>(in), start, seg_stride, len, chunks, static_cast<float *>(out), partials,
+        counters, nred, tr);
+  DESC_CUDA_TRY(cudaGetLastError());
+  return DESC_OK;
 }
 
 namespace {
