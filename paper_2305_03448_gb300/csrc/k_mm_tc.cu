@@ -390,11 +390,60 @@ __device__ __forceinline__ void tmem_dealloc_pair(uint32_t taddr, uint32_t ncols
   asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
 }
 
+// Work units of the pair kernel.  Units below `nwhole` are whole tiles; the
+// tiles after them (the last, partial wave) are cut along K into `pieces`
+// consecutive K-block ranges, one unit each, so that the last wave keeps
+// more SMs busy.  Unit u >= nwhole: tile nwhole + (u - nwhole) / pieces, piece
+// (u - nwhole) % pieces, K blocks [piece kblocks / pieces, (piece + 1) kblocks / pieces).
+struct Unit {
+  int t, kb0, nk, slot, piece;                         // slot, piece = -1 for a whole tile
+};
+__device__ __forceinline__ Unit unit_of(int u, int nwhole, int pieces, int kblocks) {
+  Unit w;
+  if (u < nwhole) {
+    w.t = u;
+    w.kb0 = 0;
+    w.nk = kblocks;
+    w.slot = w.piece = -1;
+  } else {
+    const int v = u - nwhole;
+    w.slot = v / pieces;
+    w.piece = v % pieces;
+    w.t = nwhole + w.slot;
+    w.kb0 = w.piece * kblocks / pieces;
+    w.nk = (w.piece + 1) * kblocks / pieces - w.kb0;
+  }
+  return w;
+}
+// 32 consecutive outputs of one row of C (columns col .. col + 31).
+__device__ __forceinline__ void store_row32(float *__restrict__ C, int64_t row, int64_t col, int64_t M, int64_t N,
+                                            int64_t ldc, bool vec, const uint32_t (&r)[32]) {
+  if (row >= M) return;
+  float *dst = C + row * ldc + col;
+  if (vec && col + 32 <= N) {
+#pragma unroll
+    for (int j = 0; j < 32; j += 4)
+      __stcs(reinterpret_cast<float4 *>(dst + j), make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
+                                                             __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3])));
+  } else {
+    for (int j = 0; j < 32; ++j)
+      if (col + j < N) dst[j] = __uint_as_float(r[j]);
+  }
+}
+
 // Launched as clusters of two CTAs; `tm` and `ntiles` count 256 x 256 tiles.
+// Pieces of a split tile write FP32 partial tiles to `part` ([slot][piece]
+// [8 warps][64][32 lanes] float4: a warp's 32 rows x 256 columns with the
+// lanes interleaved, so that every warp access is 512 contiguous bytes); each
+// epilogue warp then counts its rows in `cnt` (zeroed before the launch), and
+// the warp that arrives last adds the partials in piece order and writes C,
+// so the result does not depend on which piece finishes first.  No CTA waits
+// for another.
 __global__ void __launch_bounds__(kMmThreads, 1)
     mm_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                       float *__restrict__ C, int64_t M, int64_t N, int64_t ldc, int kblocks, Products prods,
-                      TileMap tm, int ntiles, int split_acc) {
+                      TileMap tm, int ntiles, int split_acc, int nwhole, int pieces, float *__restrict__ part,
+                      int *__restrict__ cnt) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                           ~uintptr_t(1023));
@@ -431,22 +480,24 @@ __global__ void __launch_bounds__(kMmThreads, 1)
   cluster_sync();                                      // both CTAs' barriers exist before any remote use
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  const int per_tile = kblocks * prods.n;
   const int nsets = split_acc ? 1 : 2;
+  const int nunits = nwhole + (ntiles - nwhole) * pieces;
 
   if (warp == 0) {
     if (lane == 0) {                                   // ---- TMA producer (both CTAs)
       int it = 0, issued = 0;
       bool ok = true;
-      for (int t = cid; t < ntiles && ok; t += ncl) {
+      for (int u = cid; u < nunits && ok; u += ncl) {
+        const Unit w = unit_of(u, nwhole, pieces, kblocks);
         int mp, nt;
-        tile_coords(t, tm, mp, nt);
+        tile_coords(w.t, tm, mp, nt);
         const int arow = mp * 2 * BM + (int)crank * BM, brow = nt * BN + (int)crank * (BN / 2);
-        for (int j = 0; j < per_tile; ++j, ++it) {
+        const int stages = w.nk * prods.n;
+        for (int j = 0; j < stages; ++j, ++it) {
           const int s = it % kPairStages;
           const uint32_t ph = (it / kPairStages) & 1;
           if (!mbar_wait(&empty[s], ph ^ 1, abort)) { ok = false; break; }
-          const int p = j / kblocks, kb = j % kblocks;
+          const int p = j / w.nk, kb = w.kb0 + j % w.nk;
           if (leader) mbar_expect_tx(&full[s], 2 * kPairStageBytes);
           const uint32_t fb = map_rank(&full[s], 0);
           tma_load_3d_pair(sA + s * kPairABytes, &tmA, fb, kb * BK, arow, prods.pa[p]);
@@ -463,25 +514,26 @@ __global__ void __launch_bounds__(kMmThreads, 1)
     }
   } else if (warp == 1) {
     if (lane == 0 && leader) {                         // ---- MMA issuer (even CTA only)
-      const int half = kblocks / 2;
       int it = 0, li = 0;
       bool ok = true, issued_any = false;
-      for (int t = cid; t < ntiles && ok; t += ncl, ++li) {
+      for (int u = cid; u < nunits && ok; u += ncl, ++li) {
+        const Unit w = unit_of(u, nwhole, pieces, kblocks);
+        const int half = w.nk / 2, stages = w.nk * prods.n;
         const int si = li % nsets;
         const uint32_t use = (uint32_t)(li / nsets);
         if (!mbar_wait(&tempty[si], (use & 1) ^ 1, abort)) break;   // both epilogues drained this set
         tc_fence_after();
-        for (int j = 0; j < per_tile; ++j, ++it) {
+        for (int j = 0; j < stages; ++j, ++it) {
           const int s = it % kPairStages;
           const uint32_t ph = (it / kPairStages) & 1;
           if (!mbar_wait(&full[s], ph, abort)) { ok = false; break; }
           tc_fence_after();
-          const int p = j / kblocks, kb = j % kblocks;
+          const int p = j / w.nk, kr = j % w.nk;       // K block kb0 + kr of product p
           int acc;
           bool first;
-          if (split_acc) {                             // K halves in two accumulators
-            acc = (half > 0 && kb >= half) ? 1 : 0;
-            first = p == 0 && kb == (acc ? half : 0);
+          if (split_acc) {                             // the unit's K range in two halves, one per accumulator
+            acc = (half > 0 && kr >= half) ? 1 : 0;
+            first = p == 0 && kr == (acc ? half : 0);
           } else {
             acc = si;
             first = j == 0;
@@ -506,18 +558,24 @@ __global__ void __launch_bounds__(kMmThreads, 1)
   } else {                                             // ---- epilogue, warps 2..5 (both CTAs)
     const int q = warp & 3;                            // TMEM lanes 32 q .. 32 q + 31
     const bool vec = ((ldc & 3) == 0) && ((reinterpret_cast<uintptr_t>(C) & 15) == 0);
-    const bool two = split_acc && kblocks / 2 > 0;
+    const int64_t prow_off = int64_t(crank) * BM + q * 32 + lane;   // this thread's row of a 256-row tile
+    const int64_t pstride = int64_t(2 * BM) * BN / 4;  // one partial tile, in float4
+    const int64_t pwarp = (int64_t(crank) * 4 + q) * (32 * BN / 4) + lane;   // this lane's first float4
     int li = 0;
-    for (int t = cid; t < ntiles; t += ncl, ++li) {
+    for (int u = cid; u < nunits; u += ncl, ++li) {
+      const Unit w = unit_of(u, nwhole, pieces, kblocks);
+      const bool two = split_acc && w.nk / 2 > 0;
       const int si = li % nsets;
       const uint32_t use = (uint32_t)(li / nsets);
       if (!mbar_wait(&tfull[si], use & 1, abort)) break;
       tc_fence_after();
       int mp, nt;
-      tile_coords(t, tm, mp, nt);
-      const int64_t row = int64_t(mp) * 2 * BM + int64_t(crank) * BM + q * 32 + lane;
+      tile_coords(w.t, tm, mp, nt);
+      const int64_t row = int64_t(mp) * 2 * BM + prow_off;
       const int64_t n0 = int64_t(nt) * BN;
       const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(split_acc ? 0 : si * BN);
+      float4 *prow = w.piece >= 0 ? reinterpret_cast<float4 *>(part) + (int64_t(w.slot) * pieces + w.piece) * pstride + pwarp
+                                  : nullptr;
 #pragma unroll 1
       for (int c = 0; c < BN / 32; ++c) {
         uint32_t r[32];
@@ -528,24 +586,57 @@ __global__ void __launch_bounds__(kMmThreads, 1)
 #pragma unroll
           for (int j = 0; j < 32; ++j) r[j] = __float_as_uint(__fadd_rn(__uint_as_float(r[j]), __uint_as_float(r1[j])));
         }
-        const int64_t col = n0 + c * 32;
-        if (row < M) {
-          float *dst = C + row * ldc + col;
-          if (vec && col + 32 <= N) {
+        if (prow) {                                    // a piece: the partial tile, kept in L2
 #pragma unroll
-            for (int j = 0; j < 32; j += 4)
-              __stcs(reinterpret_cast<float4 *>(dst + j),
-                     make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]), __uint_as_float(r[j + 2]),
-                                 __uint_as_float(r[j + 3])));
-          } else {
-            for (int j = 0; j < 32; ++j)
-              if (col + j < N) dst[j] = __uint_as_float(r[j]);
-          }
+          for (int j = 0; j < 8; ++j)
+            __stcg(prow + (c * 8 + j) * 32, make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
+                                                        __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3])));
+        } else {
+          store_row32(C, row, n0 + c * 32, M, N, ldc, vec, r);
         }
       }
       tc_fence_before();                               // TMEM reads done before the set is reused
       __syncwarp();
       if (lane == 0) mbar_arrive_cluster(map_rank(&tempty[si], 0));
+      if (prow) {                                      // the last piece to arrive writes C
+        __threadfence();
+        __syncwarp();
+        int seen = 0;
+        if (lane == 0) seen = atomicAdd(&cnt[w.slot * 8 + (int)crank * 4 + q], 1);
+        seen = __shfl_sync(0xffffffffu, seen, 0);
+        if (seen == pieces - 1) {
+          __threadfence();
+          const float4 *p0 = reinterpret_cast<const float4 *>(part) + int64_t(w.slot) * pieces * pstride + pwarp;
+#pragma unroll 1
+          for (int c = 0; c < BN / 32; c += 2) {       // 64 columns: 16 loads in flight per piece
+            float4 a[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) a[j] = __ldcg(p0 + (c * 8 + j) * 32);
+#pragma unroll 1
+            for (int pc = 1; pc < pieces; ++pc) {
+              float4 b[16];
+#pragma unroll
+              for (int j = 0; j < 16; ++j) b[j] = __ldcg(p0 + pc * pstride + (c * 8 + j) * 32);
+#pragma unroll
+              for (int j = 0; j < 16; ++j)
+                a[j] = make_float4(__fadd_rn(a[j].x, b[j].x), __fadd_rn(a[j].y, b[j].y), __fadd_rn(a[j].z, b[j].z),
+                                   __fadd_rn(a[j].w, b[j].w));
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              uint32_t r[32];
+#pragma unroll
+              for (int j = 0; j < 8; ++j) {
+                r[4 * j] = __float_as_uint(a[8 * h + j].x);
+                r[4 * j + 1] = __float_as_uint(a[8 * h + j].y);
+                r[4 * j + 2] = __float_as_uint(a[8 * h + j].z);
+                r[4 * j + 3] = __float_as_uint(a[8 * h + j].w);
+              }
+              store_row32(C, row, n0 + (c + h) * 32, M, N, ldc, vec, r);
+            }
+          }
+        }
+      }
     }
   }
   tc_fence_before();
@@ -611,9 +702,16 @@ __device__ __forceinline__ void store8(__nv_bfloat16 *__restrict__ dst, int64_t 
   for (int p = 0; p < 3; ++p)
     if (p < planes) *reinterpret_cast<uint4 *>(dst + (int64_t(p) * Rp + r) * Cp + c) = o[p];
 }
+// Block 0 of each split kernel also zeroes `clear[0, nclear)` (the matmul's
+// piece counters), which saves a launch.
+__device__ __forceinline__ void clear_words(int *clear, int nclear) {
+  if (blockIdx.x == 0)
+    for (int i = threadIdx.x; i < nclear; i += blockDim.x) clear[i] = 0;
+}
 __global__ void __launch_bounds__(256) split_rows_kernel(const float *__restrict__ src, int64_t off, int64_t sr,
                                                          int64_t R, int64_t Cc, int64_t Rp, int64_t Cp, int planes,
-                                                         __nv_bfloat16 *__restrict__ dst) {
+                                                         __nv_bfloat16 *__restrict__ dst, int *clear, int nclear) {
+  clear_words(clear, nclear);
   const int64_t per_row = Cp / 8, total = Rp * per_row;
   const int64_t stride = int64_t(gridDim.x) * 256;
   for (int64_t i = int64_t(blockIdx.x) * 256 + threadIdx.x; i < total; i += 2 * stride) {
@@ -633,7 +731,8 @@ __global__ void __launch_bounds__(256) split_rows_kernel(const float *__restrict
 // read as float4 along r, written as 8 BF16 along c.
 __global__ void __launch_bounds__(256) split_cols_kernel(const float *__restrict__ src, int64_t off, int64_t sc,
                                                          int64_t R, int64_t Cc, int64_t Rp, int64_t Cp, int planes,
-                                                         __nv_bfloat16 *__restrict__ dst) {
+                                                         __nv_bfloat16 *__restrict__ dst, int *clear, int nclear) {
+  clear_words(clear, nclear);
   __shared__ float tile[kTT][kTT + 1];                 // [c][r]
   const int tid = threadIdx.x;
   const int64_t tiles_c = Cp / kTT;
@@ -671,7 +770,8 @@ __global__ void __launch_bounds__(256) split_cols_kernel(const float *__restrict
 __global__ void __launch_bounds__(256) split_planes_kernel(const float *__restrict__ src, int64_t off, int64_t sr,
                                                            int64_t sc, int64_t R, int64_t Cc, int64_t Rp,
                                                            int64_t Cp, int planes,
-                                                           __nv_bfloat16 *__restrict__ dst) {
+                                                           __nv_bfloat16 *__restrict__ dst, int *clear, int nclear) {
+  clear_words(clear, nclear);
   __shared__ float tile[kTT][kTT + 1];
   const int tid = threadIdx.x;
   const int64_t tiles_c = Cp / kTT;
@@ -699,19 +799,21 @@ __global__ void __launch_bounds__(256) split_planes_kernel(const float *__restri
 
 // Planes of one operand; Rp and Cp are multiples of 64.
 int32_t launch_split(const float *src, int64_t off, int64_t sr, int64_t sc, int64_t R, int64_t Cc, int64_t Rp,
-                     int64_t Cp, int planes, __nv_bfloat16 *dst, cudaStream_t s, int nsm) {
+                     int64_t Cp, int planes, __nv_bfloat16 *dst, cudaStream_t s, int nsm, int *clear = nullptr,
+                     int nclear = 0) {
   const bool base16 = ((reinterpret_cast<uintptr_t>(src + off)) & 15) == 0;
   const int64_t tiles = (Rp / kTT) * (Cp / kTT);
   if (sc == 1 && base16 && (sr & 3) == 0) {
     const int64_t blocks = std::min<int64_t>((Rp * (Cp / 8) + 255) / 256, int64_t(nsm) * 64);
     split_rows_kernel<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, s>>>(src, off, sr, R, Cc, Rp, Cp, planes,
-                                                                            dst);
+                                                                            dst, clear, nclear);
   } else {
     if (tiles >= (int64_t(1) << 31)) return DESC_ERR_UNSUPPORTED;
     if (sr == 1 && base16 && (sc & 3) == 0)
-      split_cols_kernel<<<(unsigned)tiles, 256, 0, s>>>(src, off, sc, R, Cc, Rp, Cp, planes, dst);
+      split_cols_kernel<<<(unsigned)tiles, 256, 0, s>>>(src, off, sc, R, Cc, Rp, Cp, planes, dst, clear, nclear);
     else
-      split_planes_kernel<<<(unsigned)tiles, 256, 0, s>>>(src, off, sr, sc, R, Cc, Rp, Cp, planes, dst);
+      split_planes_kernel<<<(unsigned)tiles, 256, 0, s>>>(src, off, sr, sc, R, Cc, Rp, Cp, planes, dst, clear,
+                                                          nclear);
   }
   DESC_CUDA_TRY(cudaGetLastError());
   return DESC_OK;
@@ -774,10 +876,84 @@ int32_t mm_status_take() {
   return v;
 }
 
-// Planes needed by a precision: 1 (BF16), 2 (2-term split), 3 (3-term split).
+namespace {
+
+constexpr int kMaxPieces = 4;         // K pieces per tile of the last wave
+// Stages (K blocks of 64 x products) per piece, at least: a piece costs a
+// partial-tile round trip through L2 and the final sum, which pays off only
+// when it saves more MMA time than that (measured on GB300: BF16 products
+// lost with 12 stages per piece and gained with 32).
+constexpr int kMinPieceStages = 24;
+constexpr size_t kPartTileBytes = size_t(2 * BM) * BN * 4;
+
+struct MmDevice {
+  int32_t status = DESC_ERR_CUDA;
+  int nsm = 0, max_pairs = 0;
+};
+
+// Kernel attributes, SM count and the number of CTA pairs resident at once
+// (an SM without a partner in its GPC stays idle), once per process.
+const MmDevice &mm_device() {
+  static MmDevice d;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&d.nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaFuncSetAttribute(mm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) != cudaSuccess ||
+        cudaFuncSetAttribute(mm_tc_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kPairSmemBytes) !=
+            cudaSuccess)
+      return;
+    cudaLaunchConfig_t q{};
+    cudaLaunchAttribute qa[1];
+    qa[0].id = cudaLaunchAttributeClusterDimension;
+    qa[0].val.clusterDim.x = 2;
+    qa[0].val.clusterDim.y = 1;
+    qa[0].val.clusterDim.z = 1;
+    q.gridDim = dim3(2 * (unsigned)std::max(d.nsm / 2, 1));
+    q.blockDim = dim3(kMmThreads);
+    q.dynamicSmemBytes = kPairSmemBytes;
+    q.attrs = qa;
+    q.numAttrs = 1;
+    if (cudaOccupancyMaxActiveClusters(&d.max_pairs, mm_tc_pair_kernel, &q) != cudaSuccess) return;
+    d.status = DESC_OK;
+  });
+  return d;
+}
+
+// How the pair kernel cuts the last wave: tiles [0, *full) whole, the rest
+// in *pieces K ranges.  ntiles counts 256 x 256 tiles.
+void pair_units(int64_t ntiles, int kblocks, int nprod, int max_pairs, int64_t *full, int *pieces) {
+  *full = ntiles;
+  *pieces = 1;
+  if (max_pairs < 1) return;
+  const int64_t tail = ntiles % max_pairs;
+  if (tail == 0) return;
+  const int pc =
+      (int)std::min<int64_t>({kMaxPieces, max_pairs / tail, int64_t(kblocks) * nprod / kMinPieceStages});
+  if (pc < 2) return;
+  *full = ntiles - tail;
+  *pieces = pc;
+}
+
+// Room for the partial tiles and counters of the pieces: at most one
+// partial tile per resident pair.
+size_t part_bytes(int64_t M, int64_t N) {
+  const int64_t Mp = round_up(M, BM), Np = round_up(N, BN);
+  if ((Mp / BM) % 2 != 0) return 0;                    // tile rows do not pair up
+  const int mp = mm_device().max_pairs;
+  const int64_t ntiles = (Mp / (2 * BM)) * (Np / BN);
+  const int64_t slots = std::min<int64_t>(mp, ntiles * kMaxPieces);
+  return slots > 0 ? align256(size_t(slots) * kPartTileBytes) + align256(size_t(mp) * 8 * sizeof(int)) : 0;
+}
+
+}  // namespace
+
+// Planes needed by a precision: 1 (BF16), 2 (2-term split), 3 (3-term split),
+// then the pieces' partial tiles.
 size_t mm_tc_ws(int64_t M, int64_t N, int64_t K, int planes) {
   const int64_t Mp = round_up(M, BM), Np = round_up(N, BN), Kp = round_up(K, BK);
-  return align256(size_t(planes) * Mp * Kp * 2) + align256(size_t(planes) * Np * Kp * 2);
+  return align256(size_t(planes) * Mp * Kp * 2) + align256(size_t(planes) * Np * Kp * 2) + part_bytes(M, N);
 }
 
 int32_t launch_mm_tc(const float *A, int64_t a_off, int64_t a_sr, int64_t a_sc, const float *B, int64_t b_off,
@@ -787,24 +963,50 @@ int32_t launch_mm_tc(const float *A, int64_t a_off, int64_t a_sr, int64_t a_sc, 
   const int64_t Mp = round_up(M, BM), Np = round_up(N, BN), Kp = round_up(K, BK);
   if (!ws || ws_bytes < mm_tc_ws(M, N, K, planes)) return DESC_ERR_WORKSPACE;
   if (Mp / BM > 65535 || Np / BN > (int64_t(1) << 30) || Kp > (int64_t(1) << 30)) return DESC_ERR_UNSUPPORTED;
+  const MmDevice &dv = mm_device();
+  if (dv.status != DESC_OK) return dv.status;
+  const int nsm = dv.nsm, max_pairs = dv.max_pairs;
   __nv_bfloat16 *pA = static_cast<__nv_bfloat16 *>(ws);
   __nv_bfloat16 *pB = reinterpret_cast<__nv_bfloat16 *>(static_cast<char *>(ws) +
                                                          align256(size_t(planes) * Mp * Kp * 2));
-  static int nsm_split = 0;
-  if (!nsm_split) {
-    int dev = 0;
-    DESC_CUDA_TRY(cudaGetDevice(&dev));
-    DESC_CUDA_TRY(cudaDeviceGetAttribute(&nsm_split, cudaDevAttrMultiProcessorCount, dev));
-  }
-  // A (M x K) -> planes [P][Mp][Kp];  B (K x N) -> transposed planes [P][Np][Kp]
-  int32_t r = launch_split(A, a_off, a_sr, a_sc, M, K, Mp, Kp, planes, pA, s, nsm_split);
-  if (r != DESC_OK) return r;
-  r = launch_split(B, b_off, b_sc, b_sr, N, K, Np, Kp, planes, pB, s, nsm_split);
-  if (r != DESC_OK) return r;
+  char *pbase = static_cast<char *>(ws) + align256(size_t(planes) * Mp * Kp * 2) +
+                align256(size_t(planes) * Np * Kp * 2);
+
+  // Schedule: CTA pairs over 256 x 256 tiles where the 128-row tiles pair up
+  // (cta_group::2), else single CTAs over 128 x 256 tiles.
   const int Mt = (int)(Mp / BM);
   int want_pairs = 1, group_rows = kGroupM;
   mm_candidate(schedule_for(DESC_OP_MATMUL, DESC_F32, M, N), &want_pairs, &group_rows);
-  const bool pairs = want_pairs && Mt % 2 == 0;        // 128-row tiles pair up: cta_group::2
+  const bool pairs = want_pairs && Mt % 2 == 0 && max_pairs >= 1;
+  TileMap tmap;
+  tmap.Mt = pairs ? Mt / 2 : Mt;
+  tmap.Nt = (int)(Np / BN);
+  tmap.group_m = std::min(tmap.Mt, pairs ? group_rows / 2 : group_rows);
+  const int64_t ntiles = int64_t(tmap.Mt) * tmap.Nt;
+  if (ntiles >= (int64_t(1) << 31)) return DESC_ERR_UNSUPPORTED;
+  const int kblocks = (int)(Kp / BK), split = planes > 1 ? 1 : 0;
+  int64_t nwhole = ntiles;
+  int pieces = 1;
+  float *part = nullptr;
+  int *cnt = nullptr;
+  int ncnt = 0;
+  if (pairs) {
+    pair_units(ntiles, kblocks, nprod, max_pairs, &nwhole, &pieces);
+    if (nwhole + (ntiles - nwhole) * pieces >= (int64_t(1) << 31)) return DESC_ERR_UNSUPPORTED;
+    if (pieces > 1) {
+      const int64_t slots = ntiles - nwhole;
+      part = reinterpret_cast<float *>(pbase);
+      cnt = reinterpret_cast<int *>(pbase + align256(size_t(slots * pieces) * kPartTileBytes));
+      ncnt = (int)(slots * 8);
+    }
+  }
+
+  // A (M x K) -> planes [P][Mp][Kp];  B (K x N) -> transposed planes [P][Np][Kp];
+  // the A pass also zeroes the pieces' counters.
+  int32_t r = launch_split(A, a_off, a_sr, a_sc, M, K, Mp, Kp, planes, pA, s, nsm, cnt, ncnt);
+  if (r != DESC_OK) return r;
+  r = launch_split(B, b_off, b_sc, b_sr, N, K, Np, Kp, planes, pB, s, nsm);
+  if (r != DESC_OK) return r;
   CUtensorMap tmA, tmB;
   if (!make_map(&tmA, pA, planes, Mp, Kp, BM) || !make_map(&tmB, pB, planes, Np, Kp, pairs ? BN / 2 : BN))
     return DESC_ERR_CUDA;
@@ -814,48 +1016,12 @@ int32_t launch_mm_tc(const float *A, int64_t a_off, int64_t a_sr, int64_t a_sc, 
     pr.pa[i] = pa[i];
     pr.pb[i] = pb[i];
   }
-  static bool attr = false;
-  static int nsm = 0, max_pairs = 0;
-  if (!attr) {
-    DESC_CUDA_TRY(cudaFuncSetAttribute(mm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
-    DESC_CUDA_TRY(
-        cudaFuncSetAttribute(mm_tc_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kPairSmemBytes));
-    int dev = 0;
-    DESC_CUDA_TRY(cudaGetDevice(&dev));
-    DESC_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    // Pairs resident at once (an SM without a partner in its GPC stays idle).
-    cudaLaunchConfig_t q{};
-    cudaLaunchAttribute qa[1];
-    qa[0].id = cudaLaunchAttributeClusterDimension;
-    qa[0].val.clusterDim.x = 2;
-    qa[0].val.clusterDim.y = 1;
-    qa[0].val.clusterDim.z = 1;
-    q.gridDim = dim3(2 * (unsigned)std::max(nsm / 2, 1));
-    q.blockDim = dim3(kMmThreads);
-    q.dynamicSmemBytes = kPairSmemBytes;
-    q.attrs = qa;
-    q.numAttrs = 1;
-    DESC_CUDA_TRY(cudaOccupancyMaxActiveClusters(&max_pairs, mm_tc_pair_kernel, &q));
-    attr = true;
-  }
-  TileMap tmap;                                        // over 128 x 256 tiles, or 256 x 256 pair tiles
-  tmap.Mt = pairs ? Mt / 2 : Mt;
-  tmap.Nt = (int)(Np / BN);
-  tmap.group_m = std::min(tmap.Mt, pairs ? group_rows / 2 : group_rows);
-  const int64_t ntiles = int64_t(tmap.Mt) * tmap.Nt;
-  if (ntiles >= (int64_t(1) << 31)) return DESC_ERR_UNSUPPORTED;
-  const int kblocks = (int)(Kp / BK), split = planes > 1 ? 1 : 0;
-  if (!pairs || max_pairs < 1) {
-    if (pairs) {                                       // no pair fits: the single-CTA map of B
-      tmap.Mt = Mt;
-      tmap.group_m = std::min(Mt, group_rows);
-      if (!make_map(&tmB, pB, planes, Np, Kp, BN)) return DESC_ERR_CUDA;
-    }
-    const int64_t nt1 = int64_t(tmap.Mt) * tmap.Nt;
-    const int grid = (int)std::min<int64_t>(nt1, std::max(nsm, 1));
-    mm_tc_kernel<<<grid, kMmThreads, kSmemBytes, s>>>(tmA, tmB, C, M, N, N, kblocks, pr, tmap, (int)nt1, split);
+  if (!pairs) {
+    const int grid = (int)std::min<int64_t>(ntiles, std::max(nsm, 1));
+    mm_tc_kernel<<<grid, kMmThreads, kSmemBytes, s>>>(tmA, tmB, C, M, N, N, kblocks, pr, tmap, (int)ntiles, split);
   } else {
-    const int npairs = (int)std::min<int64_t>(ntiles, max_pairs);
+    const int64_t nunits = nwhole + (ntiles - nwhole) * pieces;
+    const int npairs = (int)std::min<int64_t>(nunits, max_pairs);
     cudaLaunchConfig_t cfg{};
     cudaLaunchAttribute la[1];
     la[0].id = cudaLaunchAttributeClusterDimension;
@@ -869,7 +1035,7 @@ int32_t launch_mm_tc(const float *A, int64_t a_off, int64_t a_sr, int64_t a_sc, 
     cfg.attrs = la;
     cfg.numAttrs = 1;
     DESC_CUDA_TRY(cudaLaunchKernelEx(&cfg, mm_tc_pair_kernel, tmA, tmB, C, M, N, N, kblocks, pr, tmap, (int)ntiles,
-                                     split));
+                                     split, (int)nwhole, pieces, part, cnt));
   }
   DESC_CUDA_TRY(cudaGetLastError());
   return DESC_OK;

@@ -5,6 +5,8 @@ Two kinds of check per tensor-core form: against the exact FP64 product
 and against the FP64 product of the same BF16 terms (oracle's bit-level
 rounding and split), which isolates the tensor-core arithmetic: only FP32
 accumulation error may remain there."""
+import ctypes
+
 import numpy as np
 import pytest
 import torch
@@ -111,4 +113,36 @@ def test_rejections():
     with pytest.raises(D.DescError) as e:       # C overlapping A
         D.desc_matmul(Ad, B.cuda(), D.MM_FP32_SIMT, out=Ad)
     assert e.value.status == 3
+    assert D.desc_stream_status() == 0
+
+
+# The last, partial wave of 256 x 256 pair tiles is cut along K into pieces
+# (at least 24 K blocks x products each) whose partial tiles the
+# last-arriving piece adds in order.  With 76 resident pairs: 16 tiles ->
+# SPLIT3 in 4 pieces of 4 K blocks, SPLIT2 in 2; K = 1090 -> 18 K blocks,
+# SPLIT3 pieces of 4, 5, 4, 5; 100 tiles -> 76 whole tiles and 24 tiles in 3
+# pieces (SPLIT3); K = 3100 -> 49 K blocks, BF16 pieces of 24 and 25.
+PIECE_SHAPES = [(1024, 1024, 1024), (1000, 1000, 1090), (2560, 2560, 1024), (1000, 1000, 3100)]
+
+
+@pytest.mark.parametrize("M,N,K", PIECE_SHAPES)
+def test_last_wave_pieces(M, N, K):
+    A, B = mats(M, N, K, seed=M + 2 * N + K)
+    a, b = A.numpy(), B.numpy()
+    Ad, Bd = A.cuda(), B.cuda()
+    exact = OM.matmul_f64(a, b)
+    emul = OM.matmul_f64(OM.bf16_rne(a), OM.bf16_rne(b))
+    split3 = OM.split3_product_f64(a, b)
+    for p, ref, tol, tol_exact in ((D.MM_BF16, emul, 2e-6, 1e-2), (D.MM_SPLIT3, split3, 2e-6, 1e-5),
+                                   (D.MM_SPLIT2, None, None, 1e-4)):
+        nb = ctypes.c_size_t(0)
+        assert D.lib().desc_matmul_workspace_size(M, N, K, p, ctypes.byref(nb)) == 0
+        ws = torch.full((nb.value,), 0xFF, dtype=torch.uint8, device="cuda")   # stale counters
+        C1 = D.desc_matmul(Ad, Bd, p, ws=ws)
+        C2 = D.desc_matmul(Ad, Bd, p, ws=ws)
+        assert torch.equal(C1, C2)                  # independent of which piece finishes last
+        c = C1.cpu().numpy()
+        if ref is not None:
+            assert OM.rel_frobenius(c, ref) <= tol
+        assert OM.rel_frobenius(c, exact) <= tol_exact
     assert D.desc_stream_status() == 0
