@@ -56,7 +56,11 @@ constexpr int kBBytes = BN * BK * 2;             // 32 KB
 constexpr int kStageBytes = kABytes + kBBytes;
 constexpr int kTmemCols = 512;                  // two 256-column accumulators
 constexpr int kMmThreads = 192;
-constexpr int kSmemBytes = kStages * kStageBytes + 1024 + 256;
+// Epilogue staging for the TMA stores of C: per epilogue warp two buffers of
+// 32 rows x 32 FP32 (128-byte swizzle), after the operand stages.
+constexpr int kEpiBufBytes = 32 * 32 * 4;
+constexpr int kEpiBytes = 4 * 2 * kEpiBufBytes;
+constexpr int kSmemBytes = kStages * kStageBytes + kEpiBytes + 1024 + 256;
 constexpr long long kWaitBudget = 1ll << 32;     // clock cycles, about two seconds
 constexpr int kGroupM = 16;                      // tile rows per rasterisation group
 
@@ -154,6 +158,64 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
+// 32 consecutive outputs of one row of C (columns col .. col + 31).
+__device__ __forceinline__ void store_row32(float *__restrict__ C, int64_t row, int64_t col, int64_t M, int64_t N,
+                                            int64_t ldc, bool vec, const uint32_t (&r)[32]) {
+  if (row >= M) return;
+  float *dst = C + row * ldc + col;
+  if (vec && col + 32 <= N) {
+#pragma unroll
+    for (int j = 0; j < 32; j += 4)
+      __stcs(reinterpret_cast<float4 *>(dst + j), make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
+                                                             __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3])));
+  } else {
+    for (int j = 0; j < 32; ++j)
+      if (col + j < N) dst[j] = __uint_as_float(r[j]);
+  }
+}
+
+// ---- epilogue stores of C through TMA ------------------------------------
+// A warp holds 32 rows of C (one per lane) x 32 columns per step.  Writing
+// them row by row from registers makes every warp store touch 32 lines; here
+// each lane puts its row into a 128-byte-swizzled staging buffer (16-byte
+// chunk k of row r at chunk k ^ (r mod 8): conflict-free) and one lane
+// stores the 32 x 32 box with cp.async.bulk.tensor, which clips at the edges
+// of C.  Two buffers per warp: a buffer is rewritten only after the store
+// issued from it two steps earlier has read it.
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap *tm, const void *src, int x, int y) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(tm),
+               "r"(smem_u32(src)), "r"(x), "r"(y)
+               : "memory");
+}
+struct EpiStage {
+  unsigned char *buf;   // this warp's two buffers (1024-byte aligned)
+  int n;                // boxes issued so far
+};
+__device__ __forceinline__ void epi_store_box(EpiStage &e, const CUtensorMap *tm, int x, int y, bool inside,
+                                              int lane, const uint32_t (&r)[32]) {
+  unsigned char *b = e.buf + (e.n & 1) * kEpiBufBytes;
+  if (e.n >= 2) {
+    if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+    __syncwarp();
+  }
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+    *reinterpret_cast<uint4 *>(b + lane * 128 + ((k ^ (lane & 7)) << 4)) =
+        make_uint4(r[4 * k], r[4 * k + 1], r[4 * k + 2], r[4 * k + 3]);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  __syncwarp();
+  if (lane == 0) {                                   // one group per box, empty where it lies outside C
+    if (inside) tma_store_2d(tm, b, x, y);
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+  }
+  ++e.n;
+}
+// Every store of this lane complete (before the CTA leaves).
+__device__ __forceinline__ void epi_drain(int lane) {
+  if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+  __syncwarp();
+}
+
 // Tile order: groups of kGroupM tile rows, column by column inside a group,
 // so that the operand panels a wave of CTAs touches stay in L2.
 struct TileMap {
@@ -176,14 +238,15 @@ __device__ __forceinline__ void tile_coords(int t, const TileMap &g, int &mt, in
 // forms one set spans both 256-column accumulators (the two K halves).
 __global__ void __launch_bounds__(kMmThreads, 1)
     mm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                 float *__restrict__ C, int64_t M, int64_t N, int64_t ldc, int kblocks, Products prods, TileMap tm,
-                 int ntiles, int split_acc) {
+                 const __grid_constant__ CUtensorMap tmC, float *__restrict__ C, int64_t M, int64_t N, int64_t ldc,
+                 int kblocks, Products prods, TileMap tm, int ntiles, int split_acc, int tma_c) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                           ~uintptr_t(1023));
   unsigned char *sA = smem;
   unsigned char *sB = smem + kStages * kABytes;
-  uint64_t *full = reinterpret_cast<uint64_t *>(smem + kStages * kStageBytes);
+  unsigned char *sEpi = smem + kStages * kStageBytes;
+  uint64_t *full = reinterpret_cast<uint64_t *>(sEpi + kEpiBytes);
   uint64_t *empty = full + kStages;
   uint64_t *tfull = empty + kStages;
   uint64_t *tempty = tfull + 2;
@@ -277,6 +340,7 @@ __global__ void __launch_bounds__(kMmThreads, 1)
     const int q = warp & 3;                            // TMEM lanes 32 q .. 32 q + 31
     const bool vec = ((ldc & 3) == 0) && ((reinterpret_cast<uintptr_t>(C) & 15) == 0);
     const bool two = split_acc && kblocks / 2 > 0;
+    EpiStage es{sEpi + q * 2 * kEpiBufBytes, 0};
     int li = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++li) {
       const int si = li % nsets;
@@ -298,25 +362,17 @@ __global__ void __launch_bounds__(kMmThreads, 1)
 #pragma unroll
           for (int j = 0; j < 32; ++j) r[j] = __float_as_uint(__fadd_rn(__uint_as_float(r[j]), __uint_as_float(r1[j])));
         }
-        const int64_t col = n0 + c * 32;
-        if (row < M) {
-          float *dst = C + row * ldc + col;
-          if (vec && col + 32 <= N) {
-#pragma unroll
-            for (int j = 0; j < 32; j += 4)
-              __stcs(reinterpret_cast<float4 *>(dst + j),
-                     make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]), __uint_as_float(r[j + 2]),
-                                 __uint_as_float(r[j + 3])));
-          } else {
-            for (int j = 0; j < 32; ++j)
-              if (col + j < N) dst[j] = __uint_as_float(r[j]);
-          }
-        }
+        const int64_t col = n0 + c * 32, row0 = row - lane;
+        if (tma_c)
+          epi_store_box(es, &tmC, (int)col, (int)row0, row0 < M && col < N, lane, r);
+        else
+          store_row32(C, row, col, M, N, ldc, vec, r);
       }
       tc_fence_before();                               // TMEM reads done before the set is reused
       __syncwarp();
       if (lane == 0) mbar_arrive(&tempty[si]);
     }
+    epi_drain(lane);
   }
   tc_fence_before();
   __syncthreads();
@@ -328,7 +384,7 @@ constexpr int kPairStages = 6;
 constexpr int kPairABytes = BM * BK * 2;               // this CTA's 128 rows of A: 16 KB
 constexpr int kPairBBytes = (BN / 2) * BK * 2;         // this CTA's 128 of the 256 B rows: 16 KB
 constexpr int kPairStageBytes = kPairABytes + kPairBBytes;
-constexpr int kPairSmemBytes = kPairStages * kPairStageBytes + 1024 + 256;
+constexpr int kPairSmemBytes = kPairStages * kPairStageBytes + kEpiBytes + 1024 + 256;
 // kind::f16, FP32 accumulator, BF16 A and B, both K-major, N = 256, M = 256.
 constexpr uint32_t kIdescPair = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
                                 ((uint32_t)((2 * BM) >> 4) << 24);
@@ -415,22 +471,6 @@ __device__ __forceinline__ Unit unit_of(int u, int nwhole, int pieces, int kbloc
   }
   return w;
 }
-// 32 consecutive outputs of one row of C (columns col .. col + 31).
-__device__ __forceinline__ void store_row32(float *__restrict__ C, int64_t row, int64_t col, int64_t M, int64_t N,
-                                            int64_t ldc, bool vec, const uint32_t (&r)[32]) {
-  if (row >= M) return;
-  float *dst = C + row * ldc + col;
-  if (vec && col + 32 <= N) {
-#pragma unroll
-    for (int j = 0; j < 32; j += 4)
-      __stcs(reinterpret_cast<float4 *>(dst + j), make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
-                                                             __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3])));
-  } else {
-    for (int j = 0; j < 32; ++j)
-      if (col + j < N) dst[j] = __uint_as_float(r[j]);
-  }
-}
-
 // Launched as clusters of two CTAs; `tm` and `ntiles` count 256 x 256 tiles.
 // Pieces of a split tile write FP32 partial tiles to `part` ([slot][piece]
 // [8 warps][64][32 lanes] float4: a warp's 32 rows x 256 columns with the
@@ -441,15 +481,16 @@ __device__ __forceinline__ void store_row32(float *__restrict__ C, int64_t row, 
 // for another.
 __global__ void __launch_bounds__(kMmThreads, 1)
     mm_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                      float *__restrict__ C, int64_t M, int64_t N, int64_t ldc, int kblocks, Products prods,
-                      TileMap tm, int ntiles, int split_acc, int nwhole, int pieces, float *__restrict__ part,
-                      int *__restrict__ cnt) {
+                      const __grid_constant__ CUtensorMap tmC, float *__restrict__ C, int64_t M, int64_t N,
+                      int64_t ldc, int kblocks, Products prods, TileMap tm, int ntiles, int split_acc, int tma_c,
+                      int nwhole, int pieces, float *__restrict__ part, int *__restrict__ cnt) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                           ~uintptr_t(1023));
   unsigned char *sA = smem;
   unsigned char *sB = smem + kPairStages * kPairABytes;
-  uint64_t *full = reinterpret_cast<uint64_t *>(smem + kPairStages * kPairStageBytes);
+  unsigned char *sEpi = smem + kPairStages * kPairStageBytes;
+  uint64_t *full = reinterpret_cast<uint64_t *>(sEpi + kEpiBytes);
   uint64_t *empty = full + kPairStages;
   uint64_t *tfull = empty + kPairStages;
   uint64_t *tempty = tfull + 2;
@@ -561,6 +602,7 @@ __global__ void __launch_bounds__(kMmThreads, 1)
     const int64_t prow_off = int64_t(crank) * BM + q * 32 + lane;   // this thread's row of a 256-row tile
     const int64_t pstride = int64_t(2 * BM) * BN / 4;  // one partial tile, in float4
     const int64_t pwarp = (int64_t(crank) * 4 + q) * (32 * BN / 4) + lane;   // this lane's first float4
+    EpiStage es{sEpi + q * 2 * kEpiBufBytes, 0};
     int li = 0;
     for (int u = cid; u < nunits; u += ncl, ++li) {
       const Unit w = unit_of(u, nwhole, pieces, kblocks);
@@ -591,6 +633,8 @@ __global__ void __launch_bounds__(kMmThreads, 1)
           for (int j = 0; j < 8; ++j)
             __stcg(prow + (c * 8 + j) * 32, make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
                                                         __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3])));
+        } else if (tma_c) {
+          epi_store_box(es, &tmC, (int)(n0 + c * 32), (int)(row - lane), row - lane < M && n0 + c * 32 < N, lane, r);
         } else {
           store_row32(C, row, n0 + c * 32, M, N, ldc, vec, r);
         }
@@ -632,12 +676,17 @@ __global__ void __launch_bounds__(kMmThreads, 1)
                 r[4 * j + 2] = __float_as_uint(a[8 * h + j].z);
                 r[4 * j + 3] = __float_as_uint(a[8 * h + j].w);
               }
-              store_row32(C, row, n0 + (c + h) * 32, M, N, ldc, vec, r);
+              const int64_t col = n0 + (c + h) * 32;
+              if (tma_c)
+                epi_store_box(es, &tmC, (int)col, (int)(row - lane), row - lane < M && col < N, lane, r);
+              else
+                store_row32(C, row, col, M, N, ldc, vec, r);
             }
           }
         }
       }
     }
+    epi_drain(lane);
   }
   tc_fence_before();
   __syncthreads();
@@ -851,6 +900,24 @@ bool make_map(CUtensorMap *m, const void *base, int64_t planes, int64_t rows, in
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// C (M x N FP32, rows ldc apart) for the epilogue's TMA stores: 32 x 32
+// boxes, 128-byte swizzle.  false where TMA cannot address C (base not 16-byte
+// aligned, row pitch not a multiple of 16 bytes, extents of 2^31 or more);
+// the epilogue then stores from registers.
+bool make_map_c(CUtensorMap *m, float *C, int64_t M, int64_t N, int64_t ldc) {
+  EncodeTiled enc = encoder();
+  if (!enc || (reinterpret_cast<uintptr_t>(C) & 15) != 0 || (ldc & 3) != 0 || M >= (int64_t(1) << 31) ||
+      N >= (int64_t(1) << 31))
+    return false;
+  cuuint64_t dims[2] = {(cuuint64_t)N, (cuuint64_t)M};
+  cuuint64_t strides[1] = {(cuuint64_t)(ldc * 4)};
+  cuuint32_t box[2] = {32, 32};
+  cuuint32_t es[2] = {1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, C, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -1007,9 +1074,10 @@ int32_t launch_mm_tc(const float *A, int64_t a_off, int64_t a_sr, int64_t a_sc, 
   if (r != DESC_OK) return r;
   r = launch_split(B, b_off, b_sc, b_sr, N, K, Np, Kp, planes, pB, s, nsm);
   if (r != DESC_OK) return r;
-  CUtensorMap tmA, tmB;
+  CUtensorMap tmA, tmB, tmC{};
   if (!make_map(&tmA, pA, planes, Mp, Kp, BM) || !make_map(&tmB, pB, planes, Np, Kp, pairs ? BN / 2 : BN))
     return DESC_ERR_CUDA;
+  const int tma_c = make_map_c(&tmC, C, M, N, N) ? 1 : 0;
   Products pr{};
   pr.n = nprod;
   for (int i = 0; i < nprod; ++i) {
@@ -1018,7 +1086,8 @@ int32_t launch_mm_tc(const float *A, int64_t a_off, int64_t a_sr, int64_t a_sc, 
   }
   if (!pairs) {
     const int grid = (int)std::min<int64_t>(ntiles, std::max(nsm, 1));
-    mm_tc_kernel<<<grid, kMmThreads, kSmemBytes, s>>>(tmA, tmB, C, M, N, N, kblocks, pr, tmap, (int)ntiles, split);
+    mm_tc_kernel<<<grid, kMmThreads, kSmemBytes, s>>>(tmA, tmB, tmC, C, M, N, N, kblocks, pr, tmap, (int)ntiles, split,
+                                                      tma_c);
   } else {
     const int64_t nunits = nwhole + (ntiles - nwhole) * pieces;
     const int npairs = (int)std::min<int64_t>(nunits, max_pairs);
@@ -1034,8 +1103,8 @@ int32_t launch_mm_tc(const float *A, int64_t a_off, int64_t a_sr, int64_t a_sc, 
     cfg.stream = s;
     cfg.attrs = la;
     cfg.numAttrs = 1;
-    DESC_CUDA_TRY(cudaLaunchKernelEx(&cfg, mm_tc_pair_kernel, tmA, tmB, C, M, N, N, kblocks, pr, tmap, (int)ntiles,
-                                     split, (int)nwhole, pieces, part, cnt));
+    DESC_CUDA_TRY(cudaLaunchKernelEx(&cfg, mm_tc_pair_kernel, tmA, tmB, tmC, C, M, N, N, kblocks, pr, tmap,
+                                     (int)ntiles, split, tma_c, (int)nwhole, pieces, part, cnt));
   }
   DESC_CUDA_TRY(cudaGetLastError());
   return DESC_OK;
