@@ -777,40 +777,60 @@ __global__ void __launch_bounds__(256) split_rows_kernel(const float *__restrict
 
 // sr == 1 (rows contiguous: the source is the transpose of the planes'
 // layout), 16-byte aligned columns: 64 x 64 tiles through shared memory,
-// read as float4 along r, written as 8 BF16 along c.
-__global__ void __launch_bounds__(256) split_cols_kernel(const float *__restrict__ src, int64_t off, int64_t sc,
-                                                         int64_t R, int64_t Cc, int64_t Rp, int64_t Cp, int planes,
-                                                         __nv_bfloat16 *__restrict__ dst, int *clear, int nclear) {
-  clear_words(clear, nclear);
-  __shared__ float tile[kTT][kTT + 1];                 // [c][r]
-  const int tid = threadIdx.x;
-  const int64_t tiles_c = Cp / kTT;
-  const int64_t r0 = (int64_t(blockIdx.x) / tiles_c) * kTT, c0 = (int64_t(blockIdx.x) % tiles_c) * kTT;
+// read as float4 along r, written as 8 BF16 along c.  Persistent: a CTA walks
+// tiles blockIdx.x, blockIdx.x + gridDim.x, ..., and the loads of its next
+// tile are in flight while the current one is split and stored.
+__device__ __forceinline__ void split_cols_load(const float *__restrict__ src, int64_t off, int64_t sc, int64_t R,
+                                                int64_t Cc, int64_t r0, int64_t c0, int tid, float4 (&v)[4]) {
 #pragma unroll
   for (int i = 0; i < kTT * kTT / 4 / 256; ++i) {
     const int f = i * 256 + tid;
     const int lc = f / (kTT / 4), lr = (f % (kTT / 4)) * 4;
     const int64_t r = r0 + lr, c = c0 + lc;
-    float v[4];
     if (c < Cc && r + 4 <= R) {
-      const float4 a = __ldcs(reinterpret_cast<const float4 *>(src + off + r + c * sc));
-      v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+      v[i] = __ldcs(reinterpret_cast<const float4 *>(src + off + r + c * sc));
     } else {
+      float e[4];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) v[j] = (c < Cc && r + j < R) ? src[off + r + j + c * sc] : 0.f;
+      for (int j = 0; j < 4; ++j) e[j] = (c < Cc && r + j < R) ? src[off + r + j + c * sc] : 0.f;
+      v[i] = make_float4(e[0], e[1], e[2], e[3]);
     }
-#pragma unroll
-    for (int j = 0; j < 4; ++j) tile[lc][lr + j] = v[j];
   }
-  __syncthreads();
+}
+__global__ void __launch_bounds__(256, 6) split_cols_kernel(const float *__restrict__ src, int64_t off, int64_t sc,
+                                                         int64_t R, int64_t Cc, int64_t Rp, int64_t Cp, int planes,
+                                                         __nv_bfloat16 *__restrict__ dst, int *clear, int nclear) {
+  clear_words(clear, nclear);
+  __shared__ float tile[kTT][kTT + 1];                 // [c][r]
+  const int tid = threadIdx.x;
+  const int64_t tiles_c = Cp / kTT, ntiles = (Rp / kTT) * tiles_c;
+  int64_t t = blockIdx.x;
+  float4 v[4];
+  if (t < ntiles) split_cols_load(src, off, sc, R, Cc, (t / tiles_c) * kTT, (t % tiles_c) * kTT, tid, v);
+  for (; t < ntiles; t += gridDim.x) {
+    const int64_t r0 = (t / tiles_c) * kTT, c0 = (t % tiles_c) * kTT;
+    __syncthreads();                                   // the previous tile's shared reads are done
 #pragma unroll
-  for (int i = 0; i < kTT * kTT / 8 / 256; ++i) {
-    const int e = i * 256 + tid;
-    const int lr = e / (kTT / 8), lc = (e % (kTT / 8)) * 8;
-    float x[8];
+    for (int i = 0; i < kTT * kTT / 4 / 256; ++i) {
+      const int f = i * 256 + tid;
+      const int lc = f / (kTT / 4), lr = (f % (kTT / 4)) * 4;
+      tile[lc][lr] = v[i].x;
+      tile[lc][lr + 1] = v[i].y;
+      tile[lc][lr + 2] = v[i].z;
+      tile[lc][lr + 3] = v[i].w;
+    }
+    __syncthreads();
+    const int64_t tn = t + gridDim.x;
+    if (tn < ntiles) split_cols_load(src, off, sc, R, Cc, (tn / tiles_c) * kTT, (tn % tiles_c) * kTT, tid, v);
 #pragma unroll
-    for (int j = 0; j < 8; ++j) x[j] = tile[lc + j][lr];
-    store8(dst, Rp, Cp, planes, r0 + lr, c0 + lc, x);
+    for (int i = 0; i < kTT * kTT / 8 / 256; ++i) {
+      const int e = i * 256 + tid;
+      const int lr = e / (kTT / 8), lc = (e % (kTT / 8)) * 8;
+      float x[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) x[j] = tile[lc + j][lr];
+      store8(dst, Rp, Cp, planes, r0 + lr, c0 + lc, x);
+    }
   }
 }
 
@@ -859,7 +879,8 @@ int32_t launch_split(const float *src, int64_t off, int64_t sr, int64_t sc, int6
   } else {
     if (tiles >= (int64_t(1) << 31)) return DESC_ERR_UNSUPPORTED;
     if (sr == 1 && base16 && (sc & 3) == 0)
-      split_cols_kernel<<<(unsigned)tiles, 256, 0, s>>>(src, off, sc, R, Cc, Rp, Cp, planes, dst, clear, nclear);
+      split_cols_kernel<<<(unsigned)std::min<int64_t>(tiles, int64_t(nsm) * 6), 256, 0, s>>>(   // 6 resident per SM
+          src, off, sc, R, Cc, Rp, Cp, planes, dst, clear, nclear);
     else
       split_planes_kernel<<<(unsigned)tiles, 256, 0, s>>>(src, off, sr, sc, R, Cc, Rp, Cp, planes, dst, clear,
                                                           nclear);
