@@ -281,6 +281,8 @@ constexpr int kSubChunks = kSub / 4;                // 16-byte chunks per sub-ti
 constexpr int kStageBytes = 16 * kSubChunks;
 
 __device__ __forceinline__ void compute_bar() { asm volatile("bar.sync 1, %0;" ::"n"(kThreads) : "memory"); }
+// CSR: the compute warps and the look-back warp, once the tile's segment heads are marked.
+__device__ __forceinline__ void heads_bar() { asm volatile("bar.sync 2, %0;" ::"n"(kThreads + 32) : "memory"); }
 
 // Start copying kSub elements from g_start (elements past n read as zero).
 template <class T>
@@ -355,6 +357,7 @@ __global__ void __launch_bounds__(kThreads + 32) scan_kernel(const T *in, T *out
   __shared__ unsigned short sh_need[MODE == PLAIN ? 1 : SUB * kThreads];  // carry-needed bits
   __shared__ int64_t sh_seg0;
   __shared__ int sh_any_end;            // CSR: a non-empty segment ends in this tile
+  __shared__ int sh_dense;              // CSR: more boundaries than one warp-wide read covers
   __shared__ volatile int sh_go;        // look-back may start polling
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -373,8 +376,44 @@ __global__ void __launch_bounds__(kThreads + 32) scan_kernel(const T *in, T *out
     // ---- look-back warp: prefix of everything before t0
     bool first_is_head = tile == 0;
     if (MODE == PERIODIC) first_is_head = first_is_head || (t0 % args.period == 0);
-    if (MODE == CSR && !first_is_head)
-      first_is_head = args.offsets[find_segment(args.offsets, args.nseg, t0)] == t0;
+    if (MODE == CSR) {
+      // The tile's segment heads, found while the compute warps' loads are in
+      // flight: zero the bitmap, find the segment holding t0, and mark the
+      // boundaries b = offsets[s] in (t0, tend] -- a segment starts at b
+      // (b < tend) and segment s - 1 ends at b - 1 -- from one warp-wide read
+      // of the next 32 offsets.  Where all 32 lie in the tile there may be
+      // more: the compute warps then mark them together (sh_dense).
+      for (int i = lane; i < kTile / 32; i += 32) sh_heads[i] = 0u;
+      const int64_t tend = std::min<int64_t>(t0 + kTile, n);
+      T *sums = static_cast<T *>(args.sums);
+      const int64_t s0 = find_segment(args.offsets, args.nseg, t0);
+      const int64_t sl = s0 + 1 + lane;
+      const int64_t b = sl <= args.nseg ? args.offsets[sl] : INT64_MAX;
+      const int64_t bprev = sl <= args.nseg ? args.offsets[sl - 1] : 0;   // lane 0: offsets[s0]
+      const bool h0 = __shfl_sync(0xffffffffu, bprev, 0) == t0;           // a segment starts at t0
+      const bool dense = __all_sync(0xffffffffu, b <= tend);
+      __syncwarp();                                     // bitmap zeroed before marking
+      int ends = 0;
+      if (!dense && b > t0 && b <= tend) {
+        const int64_t rel = b - t0;
+        if (b < tend) atomicOr(&sh_heads[rel >> 5], 1u << (rel & 31));
+        if (sums) {                                     // empty segments get their total here
+          if (bprev == b) sums[sl - 1] = O::id();
+          else ends = 1;
+        }
+      }
+      ends = __any_sync(0xffffffffu, ends);
+      if (sums && tile == 0)                            // empty segments before the first element
+        for (int64_t q = lane; q < s0; q += 32) sums[q] = O::id();
+      if (lane == 0) {
+        if (h0) atomicOr(&sh_heads[0], 1u);
+        sh_seg0 = s0;
+        sh_dense = dense ? 1 : 0;
+        sh_any_end = ends;
+      }
+      first_is_head = first_is_head || h0;
+      heads_bar();
+    }
     CT prefix = CT::zero();
     bool ok = true;
     if (!first_is_head) {
@@ -400,34 +439,6 @@ __global__ void __launch_bounds__(kThreads + 32) scan_kernel(const T *in, T *out
     load_sub<T>(ring + s * kStageBytes, in, t0 + int64_t(s) * kSub, n, vec);
     cp_async_commit();
   }
-  if (MODE == CSR) {
-    for (int i = tid; i < kTile / 32; i += kThreads) sh_heads[i] = 0u;
-    if (warp == 0) {
-      const int64_t s0 = find_segment(args.offsets, args.nseg, t0);
-      if (lane == 0) sh_seg0 = s0;
-    }
-    if (tid == 0) sh_any_end = 0;
-    compute_bar();
-    // Boundaries b = offsets[s] in (t0, tend]: a segment starts at b (b <
-    // tend) and segment s - 1 ends at b - 1 in this tile.  Empty segments get
-    // their zero total here; the others are summed after the store pass.
-    const int64_t tend = std::min<int64_t>(t0 + kTile, n);
-    T *sums = static_cast<T *>(args.sums);
-    for (int64_t s = sh_seg0 + 1 + tid; s <= args.nseg; s += kThreads) {
-      const int64_t b = args.offsets[s];
-      if (b > tend) break;
-      if (b <= t0) continue;                            // only if the offsets were not sorted
-      const int64_t rel = b - t0;
-      if (b < tend) atomicOr(&sh_heads[rel >> 5], 1u << (rel & 31));
-      if (sums) {
-        if (args.offsets[s - 1] == b) sums[s - 1] = O::id();
-        else sh_any_end = 1;
-      }
-    }
-    if (sums && tile == 0)                              // empty segments before the first element
-      for (int64_t s = tid; s < sh_seg0; s += kThreads) sums[s] = O::id();
-    if (tid == 0 && args.offsets[sh_seg0] == t0) atomicOr(&sh_heads[0], 1u);
-  }
   if (tid == 0) {
     sh_carry = O::id();
     sh_carry_flag = 0;
@@ -437,7 +448,27 @@ __global__ void __launch_bounds__(kThreads + 32) scan_kernel(const T *in, T *out
   for (int s = 0; s < SUB; ++s) {
     unsigned char *st = ring + s * kStageBytes;
     cp_async_wait_dyn(SUB - 1 - s);                     // sub-tile s has landed (this thread)
-    compute_bar();                                      // ... for every thread; carry visible
+    if (MODE == CSR && s == 0) {                        // ... for every thread, and the heads are marked
+      heads_bar();
+      if (sh_dense) {                                   // many boundaries: all compute threads mark them
+        const int64_t tend = std::min<int64_t>(t0 + kTile, n);
+        T *sums = static_cast<T *>(args.sums);
+        for (int64_t q = sh_seg0 + 1 + tid; q <= args.nseg; q += kThreads) {
+          const int64_t b = args.offsets[q];
+          if (b > tend) break;
+          if (b <= t0) continue;                        // only if the offsets were not sorted
+          const int64_t rel = b - t0;
+          if (b < tend) atomicOr(&sh_heads[rel >> 5], 1u << (rel & 31));
+          if (sums) {
+            if (args.offsets[q - 1] == b) sums[q - 1] = O::id();
+            else sh_any_end = 1;
+          }
+        }
+        compute_bar();
+      }
+    } else {
+      compute_bar();                                    // ... for every thread; carry visible
+    }
     if (s == SUB / 2 && tid == 0) sh_go = 1;
     const T cv = sh_carry;
     const int cf = sh_carry_flag;
