@@ -335,12 +335,20 @@ int32_t desc_transpose(const desc_view *in_v, const desc_view *out_v, const desc
  *                      product, FP32 accumulation in tensor memory
  *   DESC_MM_SPLIT3     x = x0 + x1 + x2 with BF16 terms (x0 = bf16(x),
  *                      x1 = bf16(x - x0), x2 = bf16(x - x0 - x1)); the six
- *                      products A_i B_j with i + j <= 2, one FP32 accumulator
+ *                      products A_i B_j with i + j <= 2, FP32 accumulation
  *   DESC_MM_SPLIT2     two terms, the three products with i + j <= 1
  * The tensor-core forms first write the BF16 terms of A and of B transposed
  * into the workspace (zero padded to 128 / 256 / 64 multiples of M / N / K).
- * Relative Frobenius error against the FP64 product (N(0,1) data, K = 8192):
- * SPLIT3 <= 1e-5, BF16 <= 1e-2.  C must not overlap A or B. */
+ * The split forms accumulate each half of the K range in its own FP32
+ * accumulator and add the two; output tiles of the last, partial wave may be
+ * cut along K into up to four pieces whose FP32 partial tiles (also in the
+ * workspace, at most 256 KB per CTA pair the GPU holds at once) are added in
+ * a fixed order, so results do not vary between runs.  Relative Frobenius
+ * error against the FP64 product (N(0,1) data, K = 8192): SPLIT3 <= 1e-5,
+ * BF16 <= 1e-2.  C must not overlap A or B.  The call allocates nothing and
+ * issues only kernel launches, so it can be captured in a CUDA graph; the
+ * first tensor-core call or desc_matmul_workspace_size on a device sets the
+ * kernels' attributes, so make one of them before capturing. */
 typedef enum { DESC_MM_FP32_SIMT = 0, DESC_MM_BF16 = 1, DESC_MM_SPLIT3 = 2, DESC_MM_SPLIT2 = 3 } desc_mm_precision;
 int32_t desc_matmul_workspace_size(int64_t M, int64_t N, int64_t K, int32_t precision, size_t *bytes);
 int32_t desc_matmul(const desc_view *a_v, const desc_view *b_v, int64_t M, int64_t N, int64_t K, const float *A,

@@ -146,3 +146,31 @@ def test_last_wave_pieces(M, N, K):
             assert OM.rel_frobenius(c, ref) <= tol
         assert OM.rel_frobenius(c, exact) <= tol_exact
     assert D.desc_stream_status() == 0
+
+
+@pytest.mark.parametrize("M,N,K,p", [(1024, 1024, 1024, D.MM_SPLIT3), (1000, 1000, 3100, D.MM_BF16),
+                                     (384, 520, 300, D.MM_SPLIT3)])
+def test_matmul_captured_in_cuda_graph(M, N, K, p):
+    """The tensor-core call issues kernel launches only (split passes, the
+    counters cleared by the A pass, the GEMM with its last-wave pieces), so it
+    replays from a CUDA graph with the same bits as the direct call."""
+    A, B = mats(M, N, K, seed=M + N + K + 11)
+    Ad, Bd = A.cuda(), B.cuda()
+    nb = ctypes.c_size_t(0)
+    assert D.lib().desc_matmul_workspace_size(M, N, K, p, ctypes.byref(nb)) == 0
+    ws = torch.empty(nb.value, dtype=torch.uint8, device="cuda")
+    ref = D.desc_matmul(Ad, Bd, p, ws=ws)              # direct call (also the first call on the device)
+    C = torch.full_like(ref, float("nan"))
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        D.desc_matmul(Ad, Bd, p, out=C, ws=ws, stream=s)
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(C, ref)
+    C.fill_(float("nan"))
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(C, ref)
+    assert D.desc_stream_status() == 0
