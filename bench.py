@@ -52,6 +52,20 @@ def peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "source": "fallback"}
 
 
+def max_over_ranks(torch, ms, dev):
+    """The slowest rank's time: every rank gets the maximum of the ranks' ms
+    (the process group's backend decides the device of the reduction)."""
+    tt = torch.tensor([float(ms)], dtype=torch.float64, device=dev)
+    torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_rate(world, step_bytes, steps, ms):
+    """Whole-job GB/s: the bytes every rank moved in `steps` steps over the
+    slowest rank's time (replicas: each rank runs the full step)."""
+    return world * step_bytes * steps / (ms * 1e-3) / 1e9
+
+
 def traffic_for(op):
     """DRAM bytes per launch from the committed ncu summary, or None when the
     kernel source has changed since those counters were taken."""
@@ -213,14 +227,12 @@ def run_ours(args, rank, world, local_rank):
     clk = clocks.stop(t0, t1) if clocks else None
     ms = e0.elapsed_time(e1)
     if world > 1:
-        tt = torch.tensor([ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms = float(tt.item())
+        ms = max_over_ranks(torch, ms, dev)
     status = D.desc_stream_status(stream)
     if status != 0:
         raise RuntimeError(f"device status {status} in the timed region")
     step_bytes = sum(nb[name] for name, _ in ops)
-    value = world * step_bytes * K / (ms * 1e-3) / 1e9
+    value = job_rate(world, step_bytes, K, ms)
     per_op = {}
     for name, _ in ops:
         d = [a.elapsed_time(b) for a, b in ev[name]]
