@@ -174,3 +174,26 @@ def test_matmul_captured_in_cuda_graph(M, N, K, p):
     torch.cuda.synchronize()
     assert torch.equal(C, ref)
     assert D.desc_stream_status() == 0
+
+
+@pytest.mark.parametrize("M", [640, 768])              # odd / even 128-row tile counts: single CTAs / pairs
+@pytest.mark.parametrize("p", [D.MM_BF16, D.MM_SPLIT3])
+def test_operands_and_output_off_16_byte_alignment(p, M):
+    """A, B and C each start one float past a 16-byte boundary: the split
+    passes take the general kernel and C cannot be stored by TMA, so the
+    epilogue stores from registers."""
+    N, K = 768, 320
+    A, B = mats(M, N, K, seed=31)
+    bufA = torch.zeros(M * K + 1, device="cuda")
+    bufB = torch.zeros(K * N + 1, device="cuda")
+    bufC = torch.full((M * N + 1,), float("nan"), device="cuda")
+    Ad, Bd, Cd = bufA[1:].view(M, K), bufB[1:].view(K, N), bufC[1:].view(M, N)
+    Ad.copy_(A.cuda())
+    Bd.copy_(B.cuda())
+    assert Ad.data_ptr() % 16 == 4 and Cd.data_ptr() % 16 == 4
+    D.desc_matmul(Ad, Bd, p, out=Cd)
+    ref = D.desc_matmul(A.cuda(), B.cuda(), p).cpu()
+    assert torch.equal(Cd.cpu(), ref)                   # same terms, same products, same order
+    assert torch.isnan(bufC[0].cpu())                   # nothing written before C
+    a, b = A.numpy(), B.numpy()
+    assert OM.rel_frobenius(Cd.cpu().numpy(), OM.matmul_f64(a, b)) <= (1e-5 if p == D.MM_SPLIT3 else 1e-2)
