@@ -594,10 +594,11 @@ def run_segmented(torch, D, synth, dev, stream, nseg=20000):
 
 def run_e2e(args, torch, dev, stream, ops, nb, Rn, Sn, T, op_reduce, op_scan, op_transpose, world):
     """The step end to end through the public API: every step copies its
-    inputs from pinned host memory and its results back.  Two streams: one
-    for host-to-device copies and the ops, one for device-to-host copies, with
-    double-buffered device outputs, so a step's results travel back while the
-    next step's inputs travel in (the link carries both directions at once)."""
+    inputs from pinned host memory and its results back.  Three streams -- one
+    for host-to-device copies, one for the ops, one for device-to-host copies
+    -- with double-buffered device inputs and outputs, so an op runs while the
+    next op's input travels in and the previous results travel back (the link
+    carries both directions at once).  Events order each buffer's reuse."""
     import synth
     names = [n for n, _ in ops]
     h = {}
@@ -613,64 +614,77 @@ def run_e2e(args, torch, dev, stream, ops, nb, Rn, Sn, T, op_reduce, op_scan, op
         h["xt"] = torch.empty(T, T, dtype=torch.float32, pin_memory=True)
         h["ot"] = torch.empty(T, T, dtype=torch.float32, pin_memory=True)
         h["xt"].copy_(synth.normal_f32(T * T, seed=3, device=dev).reshape(T, T))
-    dr = torch.empty(Rn, dtype=torch.int32, device=dev) if "reduce" in names else None
-    ds = torch.empty(Sn, dtype=torch.float32, device=dev) if "scan" in names else None
-    dt_ = torch.empty(T, T, dtype=torch.float32, device=dev) if "transpose" in names else None
-    or_ = [torch.empty(1, dtype=torch.int32, device=dev) for _ in range(2)]
-    os_ = [torch.empty_like(ds) for _ in range(2)] if ds is not None else None
-    ot = [torch.empty_like(dt_) for _ in range(2)] if dt_ is not None else None
-    sa, sb = stream, torch.cuda.Stream(dev)
-    done = [torch.cuda.Event() for _ in range(2)]
-    ready = {k: [torch.cuda.Event() for _ in range(2)] for k in ("r", "s", "t")}
+    two = lambda f: [f() for _ in range(2)]
+    dr = two(lambda: torch.empty(Rn, dtype=torch.int32, device=dev)) if "reduce" in names else None
+    ds = two(lambda: torch.empty(Sn, dtype=torch.float32, device=dev)) if "scan" in names else None
+    dt_ = two(lambda: torch.empty(T, T, dtype=torch.float32, device=dev)) if "transpose" in names else None
+    or_ = two(lambda: torch.empty(1, dtype=torch.int32, device=dev))
+    os_ = two(lambda: torch.empty(Sn, dtype=torch.float32, device=dev)) if ds is not None else None
+    ot = two(lambda: torch.empty(T, T, dtype=torch.float32, device=dev)) if dt_ is not None else None
+    sin, sk, sout = torch.cuda.Stream(dev), stream, torch.cuda.Stream(dev)
+    ev = lambda: [torch.cuda.Event() for _ in range(2)]
+    loaded = {k: ev() for k in ("r", "s", "t")}        # input of buffer b is on the device
+    ready = {k: ev() for k in ("r", "s", "t")}         # output of buffer b is computed
+    consumed, shipped = ev(), ev()                     # buffer b's inputs read / outputs copied back
+    used = [False, False]
     h2d = d2h = 0
-    first = [True, True]
 
     def step(k):
         nonlocal h2d, d2h
         b = k % 2
         h2d = d2h = 0
-        with torch.cuda.stream(sa):
-            if not first[b]:
-                sa.wait_event(done[b])          # outputs of buffer b have left the device
-            first[b] = False
-            if dr is not None:
-                dr.copy_(h["xr"], non_blocking=True); h2d += Rn * 4
-                op_reduce(dr, or_[b]); ready["r"][b].record(sa)
-            if ds is not None:
-                ds.copy_(h["xs"], non_blocking=True); h2d += Sn * 4
-                op_scan(ds, os_[b]); ready["s"][b].record(sa)
-            if dt_ is not None:
-                dt_.copy_(h["xt"], non_blocking=True); h2d += T * T * 4
-                op_transpose(dt_, ot[b]); ready["t"][b].record(sa)
-        with torch.cuda.stream(sb):
-            if dr is not None:
-                sb.wait_event(ready["r"][b]); h["or"].copy_(or_[b], non_blocking=True); d2h += 4
-            if ds is not None:
-                sb.wait_event(ready["s"][b]); h["os"].copy_(os_[b], non_blocking=True); d2h += Sn * 4
-            if dt_ is not None:
-                sb.wait_event(ready["t"][b]); h["ot"].copy_(ot[b], non_blocking=True); d2h += T * T * 4
-            done[b].record(sb)
+        plan = []
+        if dr is not None:
+            plan.append(("r", h["xr"], dr[b], Rn * 4, lambda: op_reduce(dr[b], or_[b]), h["or"], or_[b], 4))
+        if ds is not None:
+            plan.append(("s", h["xs"], ds[b], Sn * 4, lambda: op_scan(ds[b], os_[b], stream=sk), h["os"], os_[b],
+                         Sn * 4))
+        if dt_ is not None:
+            plan.append(("t", h["xt"], dt_[b], T * T * 4, lambda: op_transpose(dt_[b], ot[b]), h["ot"], ot[b],
+                         T * T * 4))
+        with torch.cuda.stream(sin):
+            if used[b]:
+                sin.wait_event(consumed[b])             # the ops of step k - 2 have read buffer b
+            for key, hx, dx, nbytes, _, _, _, _ in plan:
+                dx.copy_(hx, non_blocking=True)
+                h2d += nbytes
+                loaded[key][b].record(sin)
+        with torch.cuda.stream(sk):
+            if used[b]:
+                sk.wait_event(shipped[b])               # step k - 2's results have left buffer b
+            for key, _, _, _, op, _, _, _ in plan:
+                sk.wait_event(loaded[key][b])
+                op()
+                ready[key][b].record(sk)
+            consumed[b].record(sk)
+        with torch.cuda.stream(sout):
+            for key, _, _, _, _, ho, do, nbytes in plan:
+                sout.wait_event(ready[key][b])
+                ho.copy_(do, non_blocking=True)
+                d2h += nbytes
+            shipped[b].record(sout)
+        used[b] = True
 
     K = max(3, min(args.steps, args.e2e_steps))
     for k in range(2):
         step(k)
     torch.cuda.synchronize(dev)
     a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(sa)
+    a.record(sk)
     for k in range(K):
         step(k)
-    sa.wait_stream(sb)
-    e.record(sa)
+    sk.wait_stream(sin)
+    sk.wait_stream(sout)
+    e.record(sk)
     torch.cuda.synchronize(dev)
     ms = a.elapsed_time(e)
     if world > 1:
-        tt = torch.tensor([ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms = float(tt.item())
+        ms = max_over_ranks(torch, ms, dev)
     step_bytes = sum(nb[n] for n in names)
-    return {"value": round(world * step_bytes * K / (ms * 1e-3) / 1e9, 1), "unit": "GB/s",
+    return {"value": round(job_rate(world, step_bytes, K, ms), 1), "unit": "GB/s",
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": K,
-            "ms_per_step": round(ms / K, 3), "overlap": "D2H of a step with H2D of the next (two streams)"}
+            "ms_per_step": round(ms / K, 3),
+            "overlap": "three streams: inputs in, ops, results out; double-buffered device inputs and outputs"}
 
 
 # --------------------------------------------------------------------- oracle
