@@ -980,14 +980,18 @@ struct MmDevice {
 };
 
 // Kernel attributes, SM count and the number of CTA pairs resident at once
-// (an SM without a partner in its GPC stays idle), once per process.
+// (an SM without a partner in its GPC stays idle), once per device (kernel
+// attributes belong to the device that is current when they are set).
+constexpr int kMaxDevices = 64;
 const MmDevice &mm_device() {
-  static MmDevice d;
-  static std::once_flag once;
-  std::call_once(once, [] {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&d.nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+  static MmDevice per_dev[kMaxDevices];
+  static std::once_flag once[kMaxDevices];
+  static const MmDevice none;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return none;
+  MmDevice &d = per_dev[dev];
+  std::call_once(once[dev], [&d, dev] {
+    if (cudaDeviceGetAttribute(&d.nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
         cudaFuncSetAttribute(mm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) != cudaSuccess ||
         cudaFuncSetAttribute(mm_tc_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kPairSmemBytes) !=
             cudaSuccess)

@@ -23,6 +23,7 @@
 // as soon as another tile has given up), records DESC_ERR_DEVICE_TIMEOUT in
 // the device status word, and its CTA leaves without writing.
 #include <algorithm>
+#include <atomic>
 
 #include "k_common.cuh"
 
@@ -670,11 +671,14 @@ int32_t run_scan_t(const T *in, T *out, const ScanArgs &a, void *ws, size_t ws_b
   if (!ws || ws_bytes < need) return DESC_ERR_WORKSPACE;
   if (ntiles >= (int64_t(1) << 31)) return DESC_ERR_UNSUPPORTED;
   const int smem = SUB * kStageBytes;
-  static bool attr = false;
-  if (!attr) {
+  static std::atomic<unsigned long long> attr_devs{0};   // devices this kernel's attribute is set on
+  int dev = 0;
+  DESC_CUDA_TRY(cudaGetDevice(&dev));
+  const unsigned long long bit = dev >= 0 && dev < 64 ? 1ull << dev : 0ull;
+  if (!(attr_devs.load(std::memory_order_acquire) & bit) || !bit) {
     DESC_CUDA_TRY(
         cudaFuncSetAttribute(scan_kernel<T, O, MODE, SUB, EXCL>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    attr = true;
+    attr_devs.fetch_or(bit, std::memory_order_release);
   }
   DESC_CUDA_TRY(cudaMemsetAsync(ws, 0, need, s));
   ScanWs *w = static_cast<ScanWs *>(ws);
