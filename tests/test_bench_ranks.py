@@ -56,12 +56,13 @@ def test_job_rate_counts_every_rank():
     assert bench.job_rate(1, 1e9, 10, 20.0) == pytest.approx(500.0)
 
 
-def test_reference_arm_under_torchrun_world2():
+def test_reference_arm_under_torchrun_world2(tmp_path):
     port = _free_port()
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
            "--master-addr", "127.0.0.1", "--master-port", str(port), "bench.py", "--impl", "reference",
            "--gpus", "2", "--steps", "1", "--warmup", "3", "--ops", "reduce"]
-    r = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=300)
+    env = dict(os.environ, TMPDIR=str(tmp_path))        # torchrun's log directory goes under pytest's
+    r = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=300, env=env)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
     assert len(lines) == 1                          # rank 0 alone prints
