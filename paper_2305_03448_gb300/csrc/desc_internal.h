@@ -117,7 +117,7 @@ size_t mm_tc_ws(int64_t M, int64_t N, int64_t K, int planes);
 // Tensor-core matmul schedule candidates: CTA pairs or not, and the
 // rasterisation group in tile rows.
 int mm_candidates();
-void mm_candidate(int cand, int *pairs, int *group_rows);
+void mm_candidate(int cand, int *pairs, int *group_rows, int *width);
 int32_t launch_mm_tc(const float *A, int64_t a_off, int64_t a_sr, int64_t a_sc, const float *B, int64_t b_off,
                      int64_t b_sr, int64_t b_sc, float *C, int64_t M, int64_t N, int64_t K, int planes,
                      int nprod, const int *pa, const int *pb, void *ws, size_t ws_bytes, desc_stream_t s);

@@ -380,11 +380,23 @@ __global__ void __launch_bounds__(kMmThreads, 1)
 }
 
 // ---- pairs of CTAs: cta_group::2 ---------------------------------------------
-constexpr int kPairStages = 6;
-constexpr int kPairABytes = BM * BK * 2;               // this CTA's 128 rows of A: 16 KB
-constexpr int kPairBBytes = (BN / 2) * BK * 2;         // this CTA's 128 of the 256 B rows: 16 KB
-constexpr int kPairStageBytes = kPairABytes + kPairBBytes;
-constexpr int kPairSmemBytes = kPairStages * kPairStageBytes + kEpiBytes + 1024 + 256;
+// Pair tiles of 256 x 256 NW: NW tcgen05 M256 N256 MMAs per K step.  NW = 1
+// keeps two 256-column accumulator sets (consecutive tiles, or the two K
+// halves of the split forms); NW = 2 fills TMEM with one tile's 512 columns
+// and takes in a quarter fewer operand bytes per flop.
+template <int NW>
+struct PairCfg {
+  static constexpr int kStages = NW == 1 ? 6 : 4;
+  static constexpr int kABytes = BM * BK * 2;          // this CTA's 128 rows of A: 16 KB
+  static constexpr int kBBox = (BN / 2) * BK * 2;      // this CTA's 128 B rows of one N256 MMA: 16 KB
+  static constexpr int kBBytes = NW * kBBox;
+  static constexpr int kStageBytes = kABytes + kBBytes;
+  static constexpr int kTileN = NW * BN;
+  static constexpr int kSmemBytes = kStages * kStageBytes + kEpiBytes + 1024 + 256;
+};
+constexpr int kPairSmemBytes = PairCfg<1>::kSmemBytes;
+static_assert(PairCfg<2>::kSmemBytes == kPairSmemBytes, "both pair widths use the same shared memory");
+static_assert(kPairSmemBytes <= 232448, "more shared memory than a CTA may have");
 // kind::f16, FP32 accumulator, BF16 A and B, both K-major, N = 256, M = 256.
 constexpr uint32_t kIdescPair = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
                                 ((uint32_t)((2 * BM) >> 4) << 24);
@@ -471,6 +483,26 @@ __device__ __forceinline__ Unit unit_of(int u, int nwhole, int pieces, int kbloc
   }
   return w;
 }
+
+// Product p and K block kb0 + kr of stage j of a unit.  `phased` units run
+// in two phases -- the first K half of every product, then the second halves
+// -- so that the split forms keep two half sums with one accumulator set.
+__device__ __forceinline__ void stage_pk(int j, const Unit &w, int nprod, bool phased, int &p, int &kr) {
+  if (!phased) {
+    p = j / w.nk;
+    kr = j % w.nk;
+    return;
+  }
+  const int h = w.nk / 2, first = nprod * h;
+  if (j < first) {
+    p = j / h;
+    kr = j % h;
+  } else {
+    const int jj = j - first, h2 = w.nk - h;
+    p = jj / h2;
+    kr = h + jj % h2;
+  }
+}
 // Launched as clusters of two CTAs; `tm` and `ntiles` count 256 x 256 tiles.
 // Pieces of a split tile write FP32 partial tiles to `part` ([slot][piece]
 // [8 warps][64][32 lanes] float4: a warp's 32 rows x 256 columns with the
@@ -479,20 +511,23 @@ __device__ __forceinline__ Unit unit_of(int u, int nwhole, int pieces, int kbloc
 // the warp that arrives last adds the partials in piece order and writes C,
 // so the result does not depend on which piece finishes first.  No CTA waits
 // for another.
+template <int NW>
 __global__ void __launch_bounds__(kMmThreads, 1)
     mm_tc_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                       const __grid_constant__ CUtensorMap tmC, float *__restrict__ C, int64_t M, int64_t N,
                       int64_t ldc, int kblocks, Products prods, TileMap tm, int ntiles, int split_acc, int tma_c,
-                      int nwhole, int pieces, float *__restrict__ part, int *__restrict__ cnt) {
+                      int nwhole, int pieces, float *__restrict__ part, int *__restrict__ cnt,
+                      float *__restrict__ halfws) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                           ~uintptr_t(1023));
+  using P = PairCfg<NW>;
   unsigned char *sA = smem;
-  unsigned char *sB = smem + kPairStages * kPairABytes;
-  unsigned char *sEpi = smem + kPairStages * kPairStageBytes;
+  unsigned char *sB = smem + P::kStages * P::kABytes;
+  unsigned char *sEpi = smem + P::kStages * P::kStageBytes;
   uint64_t *full = reinterpret_cast<uint64_t *>(sEpi + kEpiBytes);
-  uint64_t *empty = full + kPairStages;
-  uint64_t *tfull = empty + kPairStages;
+  uint64_t *empty = full + P::kStages;
+  uint64_t *tfull = empty + P::kStages;
   uint64_t *tempty = tfull + 2;
   uint64_t *mdone = tempty + 2;
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mdone + 1);
@@ -503,7 +538,7 @@ __global__ void __launch_bounds__(kMmThreads, 1)
   const bool leader = crank == 0;
   const int cid = blockIdx.x / 2, ncl = gridDim.x / 2;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kPairStages; ++s) {
+    for (int s = 0; s < P::kStages; ++s) {
       mbar_init(&full[s], 1);                          // even CTA: its producer + both CTAs' bytes
       mbar_init(&empty[s], 1);                         // the even CTA's MMA commit
     }
@@ -521,7 +556,8 @@ __global__ void __launch_bounds__(kMmThreads, 1)
   cluster_sync();                                      // both CTAs' barriers exist before any remote use
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  const int nsets = split_acc ? 1 : 2;
+  const bool halves = NW == 1 && split_acc;            // the split forms' two K-half accumulators
+  const int nsets = (NW == 1 && !split_acc) ? 2 : 1;
   const int nunits = nwhole + (ntiles - nwhole) * pieces;
 
   if (warp == 0) {
@@ -532,62 +568,77 @@ __global__ void __launch_bounds__(kMmThreads, 1)
         const Unit w = unit_of(u, nwhole, pieces, kblocks);
         int mp, nt;
         tile_coords(w.t, tm, mp, nt);
-        const int arow = mp * 2 * BM + (int)crank * BM, brow = nt * BN + (int)crank * (BN / 2);
+        // B rows of MMA h: nt * 256 NW + 256 h + (this CTA's half of 256)
+        const int arow = mp * 2 * BM + (int)crank * BM, brow = nt * P::kTileN + (int)crank * (BN / 2);
         const int stages = w.nk * prods.n;
+        const bool phased = NW == 2 && split_acc && w.nk / 2 > 0;
         for (int j = 0; j < stages; ++j, ++it) {
-          const int s = it % kPairStages;
-          const uint32_t ph = (it / kPairStages) & 1;
+          const int s = it % P::kStages;
+          const uint32_t ph = (it / P::kStages) & 1;
           if (!mbar_wait(&empty[s], ph ^ 1, abort)) { ok = false; break; }
-          const int p = j / w.nk, kb = w.kb0 + j % w.nk;
-          if (leader) mbar_expect_tx(&full[s], 2 * kPairStageBytes);
+          int p, kr;
+          stage_pk(j, w, prods.n, phased, p, kr);
+          const int kb = w.kb0 + kr;
+          if (leader) mbar_expect_tx(&full[s], 2 * P::kStageBytes);
           const uint32_t fb = map_rank(&full[s], 0);
-          tma_load_3d_pair(sA + s * kPairABytes, &tmA, fb, kb * BK, arow, prods.pa[p]);
-          tma_load_3d_pair(sB + s * kPairBBytes, &tmB, fb, kb * BK, brow, prods.pb[p]);
+          tma_load_3d_pair(sA + s * P::kABytes, &tmA, fb, kb * BK, arow, prods.pa[p]);
+#pragma unroll
+          for (int h = 0; h < NW; ++h)
+            tma_load_3d_pair(sB + s * P::kBBytes + h * P::kBBox, &tmB, fb, kb * BK, brow + h * BN, prods.pb[p]);
           issued = it + 1;
         }
       }
       // Before leaving: every issued stage consumed (its MMAs, which read this
       // CTA's shared memory, are done) -- bounded.
       const long long t0 = clock64();
-      for (int i = std::max(0, issued - kPairStages); i < issued; ++i)
-        while (!mbar_try_wait(&empty[i % kPairStages], (i / kPairStages) & 1) && clock64() - t0 < kWaitBudget) {
+      for (int i = std::max(0, issued - P::kStages); i < issued; ++i)
+        while (!mbar_try_wait(&empty[i % P::kStages], (i / P::kStages) & 1) && clock64() - t0 < kWaitBudget) {
         }
     }
   } else if (warp == 1) {
     if (lane == 0 && leader) {                         // ---- MMA issuer (even CTA only)
       int it = 0, li = 0;
       bool ok = true, issued_any = false;
-      for (int u = cid; u < nunits && ok; u += ncl, ++li) {
+      for (int u = cid; u < nunits && ok; u += ncl) {
         const Unit w = unit_of(u, nwhole, pieces, kblocks);
         const int half = w.nk / 2, stages = w.nk * prods.n;
+        const bool phased = NW == 2 && split_acc && half > 0;
+        int j = 0;
+        for (int phz = 0; phz < (phased ? 2 : 1) && ok; ++phz, ++li) {   // one accumulation per phase
         const int si = li % nsets;
         const uint32_t use = (uint32_t)(li / nsets);
-        if (!mbar_wait(&tempty[si], (use & 1) ^ 1, abort)) break;   // both epilogues drained this set
+        if (!mbar_wait(&tempty[si], (use & 1) ^ 1, abort)) { ok = false; break; }   // both epilogues drained it
         tc_fence_after();
-        for (int j = 0; j < stages; ++j, ++it) {
-          const int s = it % kPairStages;
-          const uint32_t ph = (it / kPairStages) & 1;
+        const int jbeg = j, jend = (phased && phz == 0) ? prods.n * half : stages;
+        for (; j < jend; ++j, ++it) {
+          const int s = it % P::kStages;
+          const uint32_t ph = (it / P::kStages) & 1;
           if (!mbar_wait(&full[s], ph, abort)) { ok = false; break; }
           tc_fence_after();
-          const int p = j / w.nk, kr = j % w.nk;       // K block kb0 + kr of product p
+          int p, kr;                                   // K block kb0 + kr of product p
+          stage_pk(j, w, prods.n, phased, p, kr);
           int acc;
           bool first;
-          if (split_acc) {                             // the unit's K range in two halves, one per accumulator
+          if (halves) {                                // the unit's K range in two halves, one per accumulator
             acc = (half > 0 && kr >= half) ? 1 : 0;
             first = p == 0 && kr == (acc ? half : 0);
           } else {
             acc = si;
-            first = j == 0;
+            first = j == jbeg;
           }
-          const uint32_t d = tmem + (uint32_t)(acc * BN);
-          const uint32_t a0 = smem_u32(sA + s * kPairABytes), b0 = smem_u32(sB + s * kPairBBytes);
+          const uint32_t d = tmem + (uint32_t)(acc * BN);      // NW = 2: acc = 0, MMA h writes columns 256 h ..
+          const uint32_t a0 = smem_u32(sA + s * P::kABytes), b0 = smem_u32(sB + s * P::kBBytes);
 #pragma unroll
           for (int k = 0; k < BK / UK; ++k)
-            umma_bf16_pair(d, sdesc(a0 + k * UK * 2), sdesc(b0 + k * UK * 2), (first && k == 0) ? 0u : 1u);
+#pragma unroll
+            for (int h = 0; h < NW; ++h)
+              umma_bf16_pair(d + (uint32_t)(h * BN), sdesc(a0 + k * UK * 2), sdesc(b0 + h * P::kBBox + k * UK * 2),
+                             (first && k == 0) ? 0u : 1u);
           umma_commit_pair_both(&empty[s]);            // both CTAs' stage s reusable after these MMAs
           issued_any = true;
         }
         if (ok) umma_commit_pair_both(&tfull[si]);     // accumulators complete in both CTAs
+        }
       }
       if (issued_any) {                                // every MMA finished before TMEM is freed (bounded)
         umma_commit_pair_local(mdone);
@@ -600,29 +651,51 @@ __global__ void __launch_bounds__(kMmThreads, 1)
     const int q = warp & 3;                            // TMEM lanes 32 q .. 32 q + 31
     const bool vec = ((ldc & 3) == 0) && ((reinterpret_cast<uintptr_t>(C) & 15) == 0);
     const int64_t prow_off = int64_t(crank) * BM + q * 32 + lane;   // this thread's row of a 256-row tile
-    const int64_t pstride = int64_t(2 * BM) * BN / 4;  // one partial tile, in float4
-    const int64_t pwarp = (int64_t(crank) * 4 + q) * (32 * BN / 4) + lane;   // this lane's first float4
+    constexpr int kChunks = P::kTileN / 32;            // 32-column steps of a row
+    const int64_t pstride = int64_t(2 * BM) * P::kTileN / 4;   // one partial tile, in float4
+    const int64_t pwarp = (int64_t(crank) * 4 + q) * (32 * P::kTileN / 4) + lane;   // this lane's first float4
     EpiStage es{sEpi + q * 2 * kEpiBufBytes, 0};
+    float4 *hrow = halfws ? reinterpret_cast<float4 *>(halfws) + int64_t(cid) * pstride + pwarp : nullptr;
     int li = 0;
-    for (int u = cid; u < nunits; u += ncl, ++li) {
+    bool stop = false;
+    for (int u = cid; u < nunits && !stop; u += ncl) {
       const Unit w = unit_of(u, nwhole, pieces, kblocks);
-      const bool two = split_acc && w.nk / 2 > 0;
-      const int si = li % nsets;
-      const uint32_t use = (uint32_t)(li / nsets);
-      if (!mbar_wait(&tfull[si], use & 1, abort)) break;
-      tc_fence_after();
+      const bool two = halves && w.nk / 2 > 0;
+      const bool phased = NW == 2 && split_acc && w.nk / 2 > 0;
       int mp, nt;
       tile_coords(w.t, tm, mp, nt);
       const int64_t row = int64_t(mp) * 2 * BM + prow_off;
-      const int64_t n0 = int64_t(nt) * BN;
-      const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(split_acc ? 0 : si * BN);
+      const int64_t n0 = int64_t(nt) * P::kTileN;
       float4 *prow = w.piece >= 0 ? reinterpret_cast<float4 *>(part) + (int64_t(w.slot) * pieces + w.piece) * pstride + pwarp
                                   : nullptr;
+      for (int phz = 0; phz < (phased ? 2 : 1); ++phz, ++li) {
+      const int si = li % nsets;
+      const uint32_t use = (uint32_t)(li / nsets);
+      if (!mbar_wait(&tfull[si], use & 1, abort)) { stop = true; break; }
+      tc_fence_after();
+      const bool keep = phased && phz == 0;           // the first K half: kept for the second phase
+      const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(nsets == 2 ? si * BN : 0);
 #pragma unroll 1
-      for (int c = 0; c < BN / 32; ++c) {
+      for (int c = 0; c < kChunks; ++c) {
         uint32_t r[32];
         tmem_ld32(base + (uint32_t)(c * 32), r);
-        if (two) {
+        if (keep) {                                    // this lane's own slots: read back by it alone
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            __stcg(hrow + (c * 8 + j) * 32, make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
+                                                        __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3])));
+          continue;
+        }
+        if (phased) {                                  // first half + second half, as the two accumulators add
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const float4 v = __ldcg(hrow + (c * 8 + j) * 32);
+            r[4 * j] = __float_as_uint(__fadd_rn(v.x, __uint_as_float(r[4 * j])));
+            r[4 * j + 1] = __float_as_uint(__fadd_rn(v.y, __uint_as_float(r[4 * j + 1])));
+            r[4 * j + 2] = __float_as_uint(__fadd_rn(v.z, __uint_as_float(r[4 * j + 2])));
+            r[4 * j + 3] = __float_as_uint(__fadd_rn(v.w, __uint_as_float(r[4 * j + 3])));
+          }
+        } else if (two) {
           uint32_t r1[32];
           tmem_ld32(base + (uint32_t)(BN + c * 32), r1);
 #pragma unroll
@@ -642,6 +715,8 @@ __global__ void __launch_bounds__(kMmThreads, 1)
       tc_fence_before();                               // TMEM reads done before the set is reused
       __syncwarp();
       if (lane == 0) mbar_arrive_cluster(map_rank(&tempty[si], 0));
+      }
+      if (stop) break;
       if (prow) {                                      // the last piece to arrive writes C
         __threadfence();
         __syncwarp();
@@ -652,7 +727,7 @@ __global__ void __launch_bounds__(kMmThreads, 1)
           __threadfence();
           const float4 *p0 = reinterpret_cast<const float4 *>(part) + int64_t(w.slot) * pieces * pstride + pwarp;
 #pragma unroll 1
-          for (int c = 0; c < BN / 32; c += 2) {       // 64 columns: 16 loads in flight per piece
+          for (int c = 0; c < kChunks; c += 2) {       // 64 columns: 16 loads in flight per piece
             float4 a[16];
 #pragma unroll
             for (int j = 0; j < 16; ++j) a[j] = __ldcg(p0 + (c * 8 + j) * 32);
@@ -945,16 +1020,19 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 }  // namespace
 
 // Schedule candidates: 0 pairs (where the tile rows pair up), wide groups;
-// 1 single CTAs, wide groups; 2 pairs, narrow groups; 3 single, narrow.
-constexpr int kMmCands = 4;
-constexpr int kMmPairs[kMmCands] = {1, 0, 1, 0};
-constexpr int kMmGroupRows[kMmCands] = {kGroupM, kGroupM, 4, 4};
+// 1 single CTAs, wide groups; 2 pairs, narrow groups; 3 single, narrow;
+// 4 / 5 pairs with 256 x 512 tiles, wide / narrow groups.
+constexpr int kMmCands = 6;
+constexpr int kMmPairs[kMmCands] = {1, 0, 1, 0, 1, 1};
+constexpr int kMmGroupRows[kMmCands] = {kGroupM, kGroupM, 4, 4, kGroupM, 4};
+constexpr int kMmWidth[kMmCands] = {1, 1, 1, 1, 2, 2};
 
 int mm_candidates() { return kMmCands; }
-void mm_candidate(int cand, int *pairs, int *group_rows) {
+void mm_candidate(int cand, int *pairs, int *group_rows, int *width) {
   const int c = (cand >= 0 && cand < kMmCands) ? cand : 0;
   *pairs = kMmPairs[c];
   *group_rows = kMmGroupRows[c];
+  if (width) *width = kMmWidth[c];
 }
 
 int32_t mm_status_take() {
@@ -972,7 +1050,7 @@ constexpr int kMaxPieces = 4;         // K pieces per tile of the last wave
 // when it saves more MMA time than that (measured on GB300: BF16 products
 // lost with 12 stages per piece and gained with 32).
 constexpr int kMinPieceStages = 24;
-constexpr size_t kPartTileBytes = size_t(2 * BM) * BN * 4;
+constexpr size_t kPartTileBytes = size_t(2 * BM) * PairCfg<2>::kTileN * 4;   // the wider pair tile
 
 struct MmDevice {
   int32_t status = DESC_ERR_CUDA;
@@ -993,7 +1071,9 @@ const MmDevice &mm_device() {
   std::call_once(once[dev], [&d, dev] {
     if (cudaDeviceGetAttribute(&d.nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
         cudaFuncSetAttribute(mm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) != cudaSuccess ||
-        cudaFuncSetAttribute(mm_tc_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kPairSmemBytes) !=
+        cudaFuncSetAttribute(mm_tc_pair_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPairSmemBytes) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(mm_tc_pair_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPairSmemBytes) !=
             cudaSuccess)
       return;
     cudaLaunchConfig_t q{};
@@ -1007,7 +1087,11 @@ const MmDevice &mm_device() {
     q.dynamicSmemBytes = kPairSmemBytes;
     q.attrs = qa;
     q.numAttrs = 1;
-    if (cudaOccupancyMaxActiveClusters(&d.max_pairs, mm_tc_pair_kernel, &q) != cudaSuccess) return;
+    int wide_pairs = 0;
+    if (cudaOccupancyMaxActiveClusters(&d.max_pairs, mm_tc_pair_kernel<1>, &q) != cudaSuccess ||
+        cudaOccupancyMaxActiveClusters(&wide_pairs, mm_tc_pair_kernel<2>, &q) != cudaSuccess)
+      return;
+    d.max_pairs = std::min(d.max_pairs, wide_pairs);
     d.status = DESC_OK;
   });
   return d;
@@ -1028,15 +1112,21 @@ void pair_units(int64_t ntiles, int kblocks, int nprod, int max_pairs, int64_t *
   *pieces = pc;
 }
 
-// Room for the partial tiles and counters of the pieces: at most one
-// partial tile per resident pair.
-size_t part_bytes(int64_t M, int64_t N) {
+// Room for the split forms' first K halves of 512-wide tiles (one tile per
+// resident pair), then the partial tiles and counters of the pieces (at most
+// one partial tile per resident pair).
+size_t half_bytes(int planes) {
+  const int mp = mm_device().max_pairs;
+  return planes > 1 && mp > 0 ? align256(size_t(mp) * kPartTileBytes) : 0;
+}
+size_t part_bytes(int64_t M, int64_t N, int planes) {
   const int64_t Mp = round_up(M, BM), Np = round_up(N, BN);
   if ((Mp / BM) % 2 != 0) return 0;                    // tile rows do not pair up
   const int mp = mm_device().max_pairs;
   const int64_t ntiles = (Mp / (2 * BM)) * (Np / BN);
   const int64_t slots = std::min<int64_t>(mp, ntiles * kMaxPieces);
-  return slots > 0 ? align256(size_t(slots) * kPartTileBytes) + align256(size_t(mp) * 8 * sizeof(int)) : 0;
+  return half_bytes(planes) +
+         (slots > 0 ? align256(size_t(slots) * kPartTileBytes) + align256(size_t(mp) * 8 * sizeof(int)) : 0);
 }
 
 }  // namespace
@@ -1045,7 +1135,7 @@ size_t part_bytes(int64_t M, int64_t N) {
 // then the pieces' partial tiles.
 size_t mm_tc_ws(int64_t M, int64_t N, int64_t K, int planes) {
   const int64_t Mp = round_up(M, BM), Np = round_up(N, BN), Kp = round_up(K, BK);
-  return align256(size_t(planes) * Mp * Kp * 2) + align256(size_t(planes) * Np * Kp * 2) + part_bytes(M, N);
+  return align256(size_t(planes) * Mp * Kp * 2) + align256(size_t(planes) * Np * Kp * 2) + part_bytes(M, N, planes);
 }
 
 int32_t launch_mm_tc(const float *A, int64_t a_off, int64_t a_sr, int64_t a_sc, const float *B, int64_t b_off,
@@ -1067,12 +1157,22 @@ int32_t launch_mm_tc(const float *A, int64_t a_off, int64_t a_sr, int64_t a_sc, 
   // Schedule: CTA pairs over 256 x 256 tiles where the 128-row tiles pair up
   // (cta_group::2), else single CTAs over 128 x 256 tiles.
   const int Mt = (int)(Mp / BM);
-  int want_pairs = 1, group_rows = kGroupM;
-  mm_candidate(schedule_for(DESC_OP_MATMUL, DESC_F32, M, N), &want_pairs, &group_rows);
+  // Untuned: 256 x 512 pair tiles where they fill at least half of the
+  // resident pairs (measured on GB300: SPLIT3 8192^3 4.32 -> 3.63 ms, 4096^3
+  // 0.615 -> 0.542 ms, BF16 8192^3 756 -> 728 us; at 2048^3, 16 wide tiles,
+  // BF16 42 -> 50 us and SPLIT3 111 -> 113 us), else 256 x 256.
+  int cand = schedule_for(DESC_OP_MATMUL, DESC_F32, M, N);
+  if (cand < 0) {
+    const int64_t wide_tiles = (Mp / (2 * BM)) * ((Np + 2 * BN - 1) / (2 * BN));
+    cand = 2 * wide_tiles >= max_pairs ? 4 : 0;
+  }
+  int want_pairs = 1, group_rows = kGroupM, width = 1;
+  mm_candidate(cand, &want_pairs, &group_rows, &width);
   const bool pairs = want_pairs && Mt % 2 == 0 && max_pairs >= 1;
+  if (!pairs) width = 1;
   TileMap tmap;
   tmap.Mt = pairs ? Mt / 2 : Mt;
-  tmap.Nt = (int)(Np / BN);
+  tmap.Nt = (int)((Np + BN * width - 1) / (BN * width));
   tmap.group_m = std::min(tmap.Mt, pairs ? group_rows / 2 : group_rows);
   const int64_t ntiles = int64_t(tmap.Mt) * tmap.Nt;
   if (ntiles >= (int64_t(1) << 31)) return DESC_ERR_UNSUPPORTED;
@@ -1087,8 +1187,8 @@ int32_t launch_mm_tc(const float *A, int64_t a_off, int64_t a_sr, int64_t a_sc, 
     if (nwhole + (ntiles - nwhole) * pieces >= (int64_t(1) << 31)) return DESC_ERR_UNSUPPORTED;
     if (pieces > 1) {
       const int64_t slots = ntiles - nwhole;
-      part = reinterpret_cast<float *>(pbase);
-      cnt = reinterpret_cast<int *>(pbase + align256(size_t(slots * pieces) * kPartTileBytes));
+      part = reinterpret_cast<float *>(pbase + half_bytes(planes));
+      cnt = reinterpret_cast<int *>(pbase + half_bytes(planes) + align256(size_t(slots * pieces) * kPartTileBytes));
       ncnt = (int)(slots * 8);
     }
   }
@@ -1128,8 +1228,13 @@ int32_t launch_mm_tc(const float *A, int64_t a_off, int64_t a_sr, int64_t a_sc, 
     cfg.stream = s;
     cfg.attrs = la;
     cfg.numAttrs = 1;
-    DESC_CUDA_TRY(cudaLaunchKernelEx(&cfg, mm_tc_pair_kernel, tmA, tmB, tmC, C, M, N, N, kblocks, pr, tmap,
-                                     (int)ntiles, split, tma_c, (int)nwhole, pieces, part, cnt));
+    float *halfws = (width == 2 && split) ? reinterpret_cast<float *>(pbase) : nullptr;
+    if (width == 2)
+      DESC_CUDA_TRY(cudaLaunchKernelEx(&cfg, mm_tc_pair_kernel<2>, tmA, tmB, tmC, C, M, N, N, kblocks, pr, tmap,
+                                       (int)ntiles, split, tma_c, (int)nwhole, pieces, part, cnt, halfws));
+    else
+      DESC_CUDA_TRY(cudaLaunchKernelEx(&cfg, mm_tc_pair_kernel<1>, tmA, tmB, tmC, C, M, N, N, kblocks, pr, tmap,
+                                       (int)ntiles, split, tma_c, (int)nwhole, pieces, part, cnt, halfws));
   }
   DESC_CUDA_TRY(cudaGetLastError());
   return DESC_OK;

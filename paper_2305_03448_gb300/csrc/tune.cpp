@@ -112,9 +112,9 @@ extern "C" int32_t desc_features(const desc_problem *p, int32_t cand, float *out
     const double td = cand == 0 ? 64 : 32;
     out[18] = lg(td * td) / 32.f;
   } else if (p->op == DESC_OP_MATMUL) {
-    int pairs = 0, group = 0;
-    mm_candidate(cand, &pairs, &group);
-    out[18] = lg(pairs ? 256.0 * 256.0 : 128.0 * 256.0) / 32.f;
+    int pairs = 0, group = 0, width = 1;
+    mm_candidate(cand, &pairs, &group, &width);
+    out[18] = lg(pairs ? 256.0 * 256.0 * width : 128.0 * 256.0) / 32.f;
     out[20] = lg((double)group) / 16.f;
     out[30] = lg((double)p->k + 1.0) / 32.f;
     out[31] = (float)pairs;

@@ -125,8 +125,17 @@ def test_rejections():
 PIECE_SHAPES = [(1024, 1024, 1024), (1000, 1000, 1090), (2560, 2560, 1024), (1000, 1000, 3100)]
 
 
+@pytest.mark.parametrize("cand", [-1, 4])              # the default schedule; 256 x 512 pair tiles
 @pytest.mark.parametrize("M,N,K", PIECE_SHAPES)
-def test_last_wave_pieces(M, N, K):
+def test_last_wave_pieces(M, N, K, cand):
+    D.desc_force_candidate(D.OP_MATMUL, cand)
+    try:
+        _check_pieces(M, N, K)
+    finally:
+        D.desc_force_candidate(D.OP_MATMUL, -1)
+
+
+def _check_pieces(M, N, K):
     A, B = mats(M, N, K, seed=M + 2 * N + K)
     a, b = A.numpy(), B.numpy()
     Ad, Bd = A.cuda(), B.cuda()
@@ -197,3 +206,24 @@ def test_operands_and_output_off_16_byte_alignment(p, M):
     assert torch.isnan(bufC[0].cpu())                   # nothing written before C
     a, b = A.numpy(), B.numpy()
     assert OM.rel_frobenius(Cd.cpu().numpy(), OM.matmul_f64(a, b)) <= (1e-5 if p == D.MM_SPLIT3 else 1e-2)
+
+
+@pytest.mark.parametrize("M,N,K", [(512, 1024, 320), (768, 1280, 256), (1000, 700, 200)])
+def test_wide_pair_tiles_give_the_same_bits(M, N, K):
+    """256 x 512 pair tiles (two N256 MMAs per K step, one accumulator set)
+    against 256 x 256 tiles: the split forms run each tile's K range in two
+    phases (first halves of every product, then second halves), so every sum
+    adds the same products in the same order -- bit-identical results.  K is
+    too short here for the last wave's pieces, which depend on the tile count."""
+    A, B = mats(M, N, K, seed=M + N + 3 * K)
+    Ad, Bd = A.cuda(), B.cuda()
+    for p in (D.MM_BF16, D.MM_SPLIT2, D.MM_SPLIT3):
+        out = {}
+        for cand in (0, 4, 2, 5):
+            D.desc_force_candidate(D.OP_MATMUL, cand)
+            try:
+                out[cand] = D.desc_matmul(Ad, Bd, p).cpu()
+            finally:
+                D.desc_force_candidate(D.OP_MATMUL, -1)
+        assert torch.equal(out[0], out[4]) and torch.equal(out[2], out[5]) and torch.equal(out[0], out[2]), p
+    assert D.desc_stream_status() == 0

@@ -9,7 +9,7 @@ import synth
 
 
 def test_candidate_counts(desc_lib):
-    assert [D.candidate_count(o) for o in range(5)] == [8, 3, 2, 3, 4]
+    assert [D.candidate_count(o) for o in range(5)] == [8, 3, 2, 3, 6]
     with pytest.raises(D.DescError):
         D.candidate_count(7)
 
@@ -33,12 +33,13 @@ def test_features_encode_problem_and_candidate(desc_lib):
     with pytest.raises(D.DescError):
         D.desc_features(p, 3)                               # scan has 3 candidates
     pm = D.make_problem(D.OP_MATMUL, D.F32, 2048, 1024, k=4096)
-    mm = [D.desc_features(pm, c) for c in range(4)]
+    mm = [D.desc_features(pm, c) for c in range(6)]
     for c, f in enumerate(mm):
         assert f[4] == 1.0 and abs(f[7] - 11 / 32) < 1e-6 and abs(f[30] - 12 / 32) < 1e-3
         assert f[21 + c] == 1.0
-    assert [f[31] for f in mm] == [1.0, 0.0, 1.0, 0.0]      # CTA pairs
+    assert [f[31] for f in mm] == [1.0, 0.0, 1.0, 0.0, 1.0, 1.0]   # CTA pairs
     assert mm[0][18] > mm[1][18] and mm[0][20] > mm[2][20]   # pair tiles larger; narrow groups
+    assert mm[4][18] > mm[0][18] and mm[4][20] > mm[5][20]   # 256 x 512 pair tiles; narrow groups
 
 
 def test_table_record_lookup_save_load(desc_lib, tmp_path):
