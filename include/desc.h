@@ -339,11 +339,13 @@ int32_t desc_transpose(const desc_view *in_v, const desc_view *out_v, const desc
  *   DESC_MM_SPLIT2     two terms, the three products with i + j <= 1
  * The tensor-core forms first write the BF16 terms of A and of B transposed
  * into the workspace (zero padded to 128 / 256 / 64 multiples of M / N / K).
- * The split forms accumulate each half of the K range in its own FP32
- * accumulator and add the two; output tiles of the last, partial wave may be
- * cut along K into up to four pieces whose FP32 partial tiles (also in the
- * workspace, at most 256 KB per CTA pair the GPU holds at once) are added in
- * a fixed order, so results do not vary between runs.  Relative Frobenius
+ * The split forms sum each half of the K range separately in FP32 and add
+ * the two (on 256 x 512 output tiles the first half's sums wait in the
+ * workspace, 512 KB per CTA pair the GPU holds at once); output tiles of the
+ * last, partial wave may be cut along K into up to four pieces whose FP32
+ * partial tiles (also in the workspace, at most 512 KB per CTA pair) are
+ * added in a fixed order, so results do not vary between runs or between
+ * tile shapes.  Relative Frobenius
  * error against the FP64 product (N(0,1) data, K = 8192): SPLIT3 <= 1e-5,
  * BF16 <= 1e-2.  C must not overlap A or B.  The call allocates nothing and
  * issues only kernel launches, so it can be captured in a CUDA graph; the
