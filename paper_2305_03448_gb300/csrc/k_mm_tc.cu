@@ -7,9 +7,12 @@
 // the 3-term split has six (i + j <= 2).  All products accumulate into one
 // FP32 accumulator in TMEM.
 //
-// Accuracy: every product's K range is split in two halves accumulated in
-// two TMEM accumulators (all 512 columns), added in FP32 by the epilogue, so
-// no accumulator sums more than half of the K' = products x K terms.
+// Accuracy: every product's K range is split in two halves whose sums are
+// added in FP32 by the epilogue, so no sum takes more than half of the
+// K' = products x K terms: two TMEM accumulators (all 512 columns) for
+// 256-column tiles, or two phases of one 512-column accumulator set for
+// 512-column tiles (the first half's sums parked in workspace) -- the same
+// sums in the same order, bit-identical results.
 // Stage order: product by product, each over all of K.  (Taking all products
 // of a K block in turn would re-read planes while still in L2, but it mixes
 // the small correction products into the running sum earlier and measured
@@ -23,12 +26,14 @@
 //                      TMEM allocation (512 columns)
 //   warps 2..5         epilogue: tcgen05.ld 32 rows x 32 columns per warp and
 //                      step (warp w reads TMEM lanes 32 (w mod 4) ...), FP32 stores
-// Pairs (mm_tc_pair_kernel, used when the 128-row tiles pair up): the two
-// CTAs of a thread-block cluster compute one 256 x 256 tile with
-// tcgen05.mma.cta_group::2 (M256 N256 K16).  Each CTA stages its own 128 rows
-// of A and its own 128 of the 256 B rows, so a stage is 32 KB instead of
-// 48 KB for the same work per SM: six stages fit, and each SM takes in a
-// third less from L2.  The even CTA issues the MMAs for both; its full
+//                      through TMA from a staging buffer
+// Pairs (mm_tc_pair_kernel<NW>, used when the 128-row tiles pair up): the two
+// CTAs of a thread-block cluster compute one 256 x 256 NW tile with NW
+// tcgen05.mma.cta_group::2 (M256 N256 K16) per K step.  Each CTA stages its
+// own 128 rows of A and its own 128 of each 256 B rows, so for NW = 1 a
+// stage is 32 KB instead of 48 KB for the same work per SM (six stages), and
+// for NW = 2 48 KB for twice the work (four stages): the operand stream into
+// each SM, not the tensor pipe, had set the pace of the 256 x 256 tiles.  The even CTA issues the MMAs for both; its full
 // barriers count the bytes of both CTAs' copies, its MMA commits free the
 // stages and publish the accumulators in both CTAs, and the epilogue warps
 // of both CTAs (each reads its own 128 accumulator rows) report to it.
