@@ -130,8 +130,8 @@ def _c_verdict_views(accesses, grid, block):
 def test_paper_verdicts_through_the_abi(desc_lib):
     g, b = (32, 1, 1), (32, 1, 1)
     full = [("group", 32, 0), ("select", V.BLOCK, V.X), ("select", V.THREAD, V.X)]
-    assert _c_verdict_views([(0, [1024], full, True)], g, b) is None                     # line 8
-    assert _c_verdict_views([(0, [1024], [], True)], g, b) == 0                          # line 4
+    assert _c_verdict_views([(0, [1024], full, True)], g, b) is None   # narrowed to one element per thread: accept
+    assert _c_verdict_views([(0, [1024], [], True)], g, b) == 0        # the whole array written by every thread
     assert _c_verdict_views([(0, [1024], [("group", 32, 0), ("select", V.THREAD, V.X)], True)], g, b) == 0
     n, B = 256, 64
     w = (0, [n], [("group", B, 0), ("select", V.BLOCK, V.X), ("select", V.THREAD, V.X)], True)
