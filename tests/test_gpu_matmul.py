@@ -208,7 +208,10 @@ def test_operands_and_output_off_16_byte_alignment(p, M):
     assert OM.rel_frobenius(Cd.cpu().numpy(), OM.matmul_f64(a, b)) <= (1e-5 if p == D.MM_SPLIT3 else 1e-2)
 
 
-@pytest.mark.parametrize("M,N,K", [(512, 1024, 320), (768, 1280, 256), (1000, 700, 200)])
+# K of one and two K blocks (no second phase / halves of one block); N = 256:
+# the second MMA of each 512-wide tile reads only zero padding.
+@pytest.mark.parametrize("M,N,K", [(512, 1024, 320), (768, 1280, 256), (1000, 700, 200), (512, 512, 64),
+                                   (512, 768, 100), (512, 256, 128)])
 def test_wide_pair_tiles_give_the_same_bits(M, N, K):
     """256 x 512 pair tiles (two N256 MMAs per K step, one accumulator set)
     against 256 x 256 tiles: the split forms run each tile's K range in two
