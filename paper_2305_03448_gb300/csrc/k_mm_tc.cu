@@ -1049,6 +1049,11 @@ int32_t mm_status_take() {
 
 namespace {
 
+// One product: odd 128-row tile counts from this one up are padded to pair
+// up (measured on GB300, N = K = 4096: 3 to 7 tile rows ran 1-6 % slower
+// padded, 15 rows 2-7 % faster, M = 8064 at 8192^2 14 % faster; the split
+// forms ran faster padded at every count, M = 8064 by 22 %).
+constexpr int kMinPadRowsBF16 = 9;
 constexpr int kMaxPieces = 4;         // K pieces per tile of the last wave
 // Stages (K blocks of 64 x products) per piece, at least: a piece costs a
 // partial-tile round trip through L2 and the final sum, which pays off only
@@ -1125,8 +1130,7 @@ size_t half_bytes(int planes) {
   return planes > 1 && mp > 0 ? align256(size_t(mp) * kPartTileBytes) : 0;
 }
 size_t part_bytes(int64_t M, int64_t N, int planes) {
-  const int64_t Mp = round_up(M, BM), Np = round_up(N, BN);
-  if ((Mp / BM) % 2 != 0) return 0;                    // tile rows do not pair up
+  const int64_t Mp = round_up(M, 2 * BM), Np = round_up(N, BN);   // tile rows padded to pair up
   const int mp = mm_device().max_pairs;
   const int64_t ntiles = (Mp / (2 * BM)) * (Np / BN);
   const int64_t slots = std::min<int64_t>(mp, ntiles * kMaxPieces);
@@ -1138,8 +1142,10 @@ size_t part_bytes(int64_t M, int64_t N, int planes) {
 
 // Planes needed by a precision: 1 (BF16), 2 (2-term split), 3 (3-term split),
 // then the pieces' partial tiles.
+// The A planes have room for an even number of 128-row tiles (an odd count
+// may be padded with a zero tile row so that the rows pair up).
 size_t mm_tc_ws(int64_t M, int64_t N, int64_t K, int planes) {
-  const int64_t Mp = round_up(M, BM), Np = round_up(N, BN), Kp = round_up(K, BK);
+  const int64_t Mp = round_up(M, 2 * BM), Np = round_up(N, BN), Kp = round_up(K, BK);
   return align256(size_t(planes) * Mp * Kp * 2) + align256(size_t(planes) * Np * Kp * 2) + part_bytes(M, N, planes);
 }
 
@@ -1147,32 +1153,38 @@ int32_t launch_mm_tc(const float *A, int64_t a_off, int64_t a_sr, int64_t a_sc, 
                      int64_t b_sr, int64_t b_sc, float *C, int64_t M, int64_t N, int64_t K, int planes,
                      int nprod, const int *pa, const int *pb, void *ws, size_t ws_bytes, desc_stream_t st) {
   cudaStream_t s = reinterpret_cast<cudaStream_t>(st);
-  const int64_t Mp = round_up(M, BM), Np = round_up(N, BN), Kp = round_up(K, BK);
+  const int64_t Mp2 = round_up(M, 2 * BM), Np = round_up(N, BN), Kp = round_up(K, BK);
   if (!ws || ws_bytes < mm_tc_ws(M, N, K, planes)) return DESC_ERR_WORKSPACE;
-  if (Mp / BM > 65535 || Np / BN > (int64_t(1) << 30) || Kp > (int64_t(1) << 30)) return DESC_ERR_UNSUPPORTED;
+  if (Mp2 / BM > 65535 || Np / BN > (int64_t(1) << 30) || Kp > (int64_t(1) << 30)) return DESC_ERR_UNSUPPORTED;
   const MmDevice &dv = mm_device();
   if (dv.status != DESC_OK) return dv.status;
   const int nsm = dv.nsm, max_pairs = dv.max_pairs;
   __nv_bfloat16 *pA = static_cast<__nv_bfloat16 *>(ws);
   __nv_bfloat16 *pB = reinterpret_cast<__nv_bfloat16 *>(static_cast<char *>(ws) +
-                                                         align256(size_t(planes) * Mp * Kp * 2));
-  char *pbase = static_cast<char *>(ws) + align256(size_t(planes) * Mp * Kp * 2) +
+                                                         align256(size_t(planes) * Mp2 * Kp * 2));
+  char *pbase = static_cast<char *>(ws) + align256(size_t(planes) * Mp2 * Kp * 2) +
                 align256(size_t(planes) * Np * Kp * 2);
-
-  // Schedule: CTA pairs over 256 x 256 tiles where the 128-row tiles pair up
-  // (cta_group::2), else single CTAs over 128 x 256 tiles.
-  const int Mt = (int)(Mp / BM);
   // Untuned: 256 x 512 pair tiles where they fill at least half of the
-  // resident pairs (measured on GB300: SPLIT3 8192^3 4.32 -> 3.63 ms, 4096^3
-  // 0.615 -> 0.542 ms, BF16 8192^3 756 -> 728 us; at 2048^3, 16 wide tiles,
-  // BF16 42 -> 50 us and SPLIT3 111 -> 113 us), else 256 x 256.
+  // resident pairs for one product, a quarter for the split forms (measured on
+  // GB300: SPLIT3 8192^3 4.32 -> 3.63 ms, 4096^3 0.615 -> 0.542 ms, 640 x 4096^2
+  // 198 -> 162 us with 24 wide tiles; BF16 8192^3 756 -> 728 us, but at 2048^3,
+  // 16 wide tiles, BF16 42 -> 50 us and SPLIT3 111 -> 113 us), else 256 x 256.
   int cand = schedule_for(DESC_OP_MATMUL, DESC_F32, M, N);
   if (cand < 0) {
-    const int64_t wide_tiles = (Mp / (2 * BM)) * ((Np + 2 * BN - 1) / (2 * BN));
-    cand = 2 * wide_tiles >= max_pairs ? 4 : 0;
+    const int64_t wide_tiles = (Mp2 / (2 * BM)) * ((Np + 2 * BN - 1) / (2 * BN));
+    cand = (nprod > 1 ? 4 * wide_tiles : 2 * wide_tiles) >= max_pairs ? 4 : 0;
   }
   int want_pairs = 1, group_rows = kGroupM, width = 1;
   mm_candidate(cand, &want_pairs, &group_rows, &width);
+  // Schedule: CTA pairs over 256 x 256 (or 256 x 512) tiles (cta_group::2),
+  // else single CTAs over 128 x 256 tiles.  An odd count of 128-row tiles is
+  // padded with one zero tile row (the split pass writes zeros there, the
+  // epilogue stores no row past M) where the pairs' leaner operand stream
+  // pays for the extra row.
+  const int64_t Mp1 = round_up(M, BM);
+  const bool pad = want_pairs && max_pairs >= 1 && (Mp1 / BM) % 2 == 1 && (nprod > 1 || Mp1 / BM >= kMinPadRowsBF16);
+  const int64_t Mp = pad ? Mp2 : Mp1;
+  const int Mt = (int)(Mp / BM);
   const bool pairs = want_pairs && Mt % 2 == 0 && max_pairs >= 1;
   if (!pairs) width = 1;
   TileMap tmap;

@@ -230,3 +230,25 @@ def test_wide_pair_tiles_give_the_same_bits(M, N, K):
                 D.desc_force_candidate(D.OP_MATMUL, -1)
         assert torch.equal(out[0], out[4]) and torch.equal(out[2], out[5]) and torch.equal(out[0], out[2]), p
     assert D.desc_stream_status() == 0
+
+
+@pytest.mark.parametrize("M,N,K", [(896, 768, 320), (1152, 640, 200), (128, 512, 256), (1000, 520, 64)])
+def test_odd_tile_rows_padded_to_pairs(M, N, K):
+    """An odd count of 128-row tiles is padded with a zero tile row so that CTA
+    pairs take it (split forms always, BF16 from nine tile rows): same bits as
+    the single-CTA kernel, no row of C past M written.  K is too short here
+    for the last wave's pieces."""
+    A, B = mats(M, N, K, seed=M + 5 * N + K)
+    Ad, Bd = A.cuda(), B.cuda()
+    for p in (D.MM_BF16, D.MM_SPLIT2, D.MM_SPLIT3):
+        buf = torch.full(((M + 1) * N,), float("nan"), device="cuda")
+        C = buf[:M * N].view(M, N)
+        D.desc_matmul(Ad, Bd, p, out=C)
+        assert torch.isnan(buf[M * N:]).all()              # the row after C untouched
+        D.desc_force_candidate(D.OP_MATMUL, 1)             # single CTAs, no padding
+        try:
+            ref = D.desc_matmul(Ad, Bd, p)
+        finally:
+            D.desc_force_candidate(D.OP_MATMUL, -1)
+        assert torch.equal(C, ref), p
+    assert D.desc_stream_status() == 0
