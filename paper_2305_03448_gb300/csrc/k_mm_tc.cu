@@ -33,10 +33,11 @@
 // own 128 rows of A and its own 128 of each 256 B rows, so for NW = 1 a
 // stage is 32 KB instead of 48 KB for the same work per SM (six stages), and
 // for NW = 2 48 KB for twice the work (four stages): the operand stream into
-// each SM, not the tensor pipe, had set the pace of the 256 x 256 tiles.  The even CTA issues the MMAs for both; its full
-// barriers count the bytes of both CTAs' copies, its MMA commits free the
-// stages and publish the accumulators in both CTAs, and the epilogue warps
-// of both CTAs (each reads its own 128 accumulator rows) report to it.
+// each SM, not the tensor pipe, had set the pace of the 256 x 256 tiles.
+// The even CTA issues the MMAs for both; its full barriers count the bytes
+// of both CTAs' copies, its MMA commits free the stages and publish the
+// accumulators in both CTAs, and the epilogue warps of both CTAs (each reads
+// its own 128 accumulator rows) report to it.
 // Every wait is bounded: a waiter that gives up sets an abort flag in shared
 // memory and records DESC_ERR_DEVICE_TIMEOUT; the producer then waits, again
 // with a limit, for the copies it has in flight, and TMEM is always freed.
@@ -610,39 +611,39 @@ __global__ void __launch_bounds__(kMmThreads, 1)
         const bool phased = NW == 2 && split_acc && half > 0;
         int j = 0;
         for (int phz = 0; phz < (phased ? 2 : 1) && ok; ++phz, ++li) {   // one accumulation per phase
-        const int si = li % nsets;
-        const uint32_t use = (uint32_t)(li / nsets);
-        if (!mbar_wait(&tempty[si], (use & 1) ^ 1, abort)) { ok = false; break; }   // both epilogues drained it
-        tc_fence_after();
-        const int jbeg = j, jend = (phased && phz == 0) ? prods.n * half : stages;
-        for (; j < jend; ++j, ++it) {
-          const int s = it % P::kStages;
-          const uint32_t ph = (it / P::kStages) & 1;
-          if (!mbar_wait(&full[s], ph, abort)) { ok = false; break; }
+          const int si = li % nsets;
+          const uint32_t use = (uint32_t)(li / nsets);
+          if (!mbar_wait(&tempty[si], (use & 1) ^ 1, abort)) { ok = false; break; }   // both epilogues drained it
           tc_fence_after();
-          int p, kr;                                   // K block kb0 + kr of product p
-          stage_pk(j, w, prods.n, phased, p, kr);
-          int acc;
-          bool first;
-          if (halves) {                                // the unit's K range in two halves, one per accumulator
-            acc = (half > 0 && kr >= half) ? 1 : 0;
-            first = p == 0 && kr == (acc ? half : 0);
-          } else {
-            acc = si;
-            first = j == jbeg;
+          const int jbeg = j, jend = (phased && phz == 0) ? prods.n * half : stages;
+          for (; j < jend; ++j, ++it) {
+            const int s = it % P::kStages;
+            const uint32_t ph = (it / P::kStages) & 1;
+            if (!mbar_wait(&full[s], ph, abort)) { ok = false; break; }
+            tc_fence_after();
+            int p, kr;                                   // K block kb0 + kr of product p
+            stage_pk(j, w, prods.n, phased, p, kr);
+            int acc;
+            bool first;
+            if (halves) {                                // the unit's K range in two halves, one per accumulator
+              acc = (half > 0 && kr >= half) ? 1 : 0;
+              first = p == 0 && kr == (acc ? half : 0);
+            } else {
+              acc = si;
+              first = j == jbeg;
+            }
+            const uint32_t d = tmem + (uint32_t)(acc * BN);      // NW = 2: acc = 0, MMA h writes columns 256 h ..
+            const uint32_t a0 = smem_u32(sA + s * P::kABytes), b0 = smem_u32(sB + s * P::kBBytes);
+#pragma unroll
+            for (int k = 0; k < BK / UK; ++k)
+#pragma unroll
+              for (int h = 0; h < NW; ++h)
+                umma_bf16_pair(d + (uint32_t)(h * BN), sdesc(a0 + k * UK * 2), sdesc(b0 + h * P::kBBox + k * UK * 2),
+                               (first && k == 0) ? 0u : 1u);
+            umma_commit_pair_both(&empty[s]);            // both CTAs' stage s reusable after these MMAs
+            issued_any = true;
           }
-          const uint32_t d = tmem + (uint32_t)(acc * BN);      // NW = 2: acc = 0, MMA h writes columns 256 h ..
-          const uint32_t a0 = smem_u32(sA + s * P::kABytes), b0 = smem_u32(sB + s * P::kBBytes);
-#pragma unroll
-          for (int k = 0; k < BK / UK; ++k)
-#pragma unroll
-            for (int h = 0; h < NW; ++h)
-              umma_bf16_pair(d + (uint32_t)(h * BN), sdesc(a0 + k * UK * 2), sdesc(b0 + h * P::kBBox + k * UK * 2),
-                             (first && k == 0) ? 0u : 1u);
-          umma_commit_pair_both(&empty[s]);            // both CTAs' stage s reusable after these MMAs
-          issued_any = true;
-        }
-        if (ok) umma_commit_pair_both(&tfull[si]);     // accumulators complete in both CTAs
+          if (ok) umma_commit_pair_both(&tfull[si]);     // accumulators complete in both CTAs
         }
       }
       if (issued_any) {                                // every MMA finished before TMEM is freed (bounded)
@@ -671,55 +672,59 @@ __global__ void __launch_bounds__(kMmThreads, 1)
       tile_coords(w.t, tm, mp, nt);
       const int64_t row = int64_t(mp) * 2 * BM + prow_off;
       const int64_t n0 = int64_t(nt) * P::kTileN;
-      float4 *prow = w.piece >= 0 ? reinterpret_cast<float4 *>(part) + (int64_t(w.slot) * pieces + w.piece) * pstride + pwarp
-                                  : nullptr;
+      float4 *prow = w.piece >= 0
+                         ? reinterpret_cast<float4 *>(part) + (int64_t(w.slot) * pieces + w.piece) * pstride + pwarp
+                         : nullptr;
       for (int phz = 0; phz < (phased ? 2 : 1); ++phz, ++li) {
-      const int si = li % nsets;
-      const uint32_t use = (uint32_t)(li / nsets);
-      if (!mbar_wait(&tfull[si], use & 1, abort)) { stop = true; break; }
-      tc_fence_after();
-      const bool keep = phased && phz == 0;           // the first K half: kept for the second phase
-      const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(nsets == 2 ? si * BN : 0);
+        const int si = li % nsets;
+        const uint32_t use = (uint32_t)(li / nsets);
+        if (!mbar_wait(&tfull[si], use & 1, abort)) { stop = true; break; }
+        tc_fence_after();
+        const bool keep = phased && phz == 0;           // the first K half: kept for the second phase
+        const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(nsets == 2 ? si * BN : 0);
 #pragma unroll 1
-      for (int c = 0; c < kChunks; ++c) {
-        uint32_t r[32];
-        tmem_ld32(base + (uint32_t)(c * 32), r);
-        if (keep) {                                    // this lane's own slots: read back by it alone
+        for (int c = 0; c < kChunks; ++c) {
+          uint32_t r[32];
+          tmem_ld32(base + (uint32_t)(c * 32), r);
+          if (keep) {                                    // this lane's own slots: read back by it alone
 #pragma unroll
-          for (int j = 0; j < 8; ++j)
-            __stcg(hrow + (c * 8 + j) * 32, make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
-                                                        __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3])));
-          continue;
-        }
-        if (phased) {                                  // first half + second half, as the two accumulators add
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const float4 v = __ldcg(hrow + (c * 8 + j) * 32);
-            r[4 * j] = __float_as_uint(__fadd_rn(v.x, __uint_as_float(r[4 * j])));
-            r[4 * j + 1] = __float_as_uint(__fadd_rn(v.y, __uint_as_float(r[4 * j + 1])));
-            r[4 * j + 2] = __float_as_uint(__fadd_rn(v.z, __uint_as_float(r[4 * j + 2])));
-            r[4 * j + 3] = __float_as_uint(__fadd_rn(v.w, __uint_as_float(r[4 * j + 3])));
+            for (int j = 0; j < 8; ++j)
+              __stcg(hrow + (c * 8 + j) * 32,
+                   make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]), __uint_as_float(r[4 * j + 2]),
+                               __uint_as_float(r[4 * j + 3])));
+            continue;
           }
-        } else if (two) {
-          uint32_t r1[32];
-          tmem_ld32(base + (uint32_t)(BN + c * 32), r1);
+          if (phased) {                                  // first half + second half, as the two accumulators add
 #pragma unroll
-          for (int j = 0; j < 32; ++j) r[j] = __float_as_uint(__fadd_rn(__uint_as_float(r[j]), __uint_as_float(r1[j])));
-        }
-        if (prow) {                                    // a piece: the partial tile, kept in L2
+            for (int j = 0; j < 8; ++j) {
+              const float4 v = __ldcg(hrow + (c * 8 + j) * 32);
+              r[4 * j] = __float_as_uint(__fadd_rn(v.x, __uint_as_float(r[4 * j])));
+              r[4 * j + 1] = __float_as_uint(__fadd_rn(v.y, __uint_as_float(r[4 * j + 1])));
+              r[4 * j + 2] = __float_as_uint(__fadd_rn(v.z, __uint_as_float(r[4 * j + 2])));
+              r[4 * j + 3] = __float_as_uint(__fadd_rn(v.w, __uint_as_float(r[4 * j + 3])));
+            }
+          } else if (two) {
+            uint32_t r1[32];
+            tmem_ld32(base + (uint32_t)(BN + c * 32), r1);
 #pragma unroll
-          for (int j = 0; j < 8; ++j)
-            __stcg(prow + (c * 8 + j) * 32, make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
-                                                        __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3])));
-        } else if (tma_c) {
-          epi_store_box(es, &tmC, (int)(n0 + c * 32), (int)(row - lane), row - lane < M && n0 + c * 32 < N, lane, r);
-        } else {
-          store_row32(C, row, n0 + c * 32, M, N, ldc, vec, r);
+            for (int j = 0; j < 32; ++j)
+              r[j] = __float_as_uint(__fadd_rn(__uint_as_float(r[j]), __uint_as_float(r1[j])));
+          }
+          if (prow) {                                    // a piece: the partial tile, kept in L2
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+              __stcg(prow + (c * 8 + j) * 32,
+                     make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
+                                 __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3])));
+          } else if (tma_c) {
+            epi_store_box(es, &tmC, (int)(n0 + c * 32), (int)(row - lane), row - lane < M && n0 + c * 32 < N, lane, r);
+          } else {
+            store_row32(C, row, n0 + c * 32, M, N, ldc, vec, r);
+          }
         }
-      }
-      tc_fence_before();                               // TMEM reads done before the set is reused
-      __syncwarp();
-      if (lane == 0) mbar_arrive_cluster(map_rank(&tempty[si], 0));
+        tc_fence_before();                               // TMEM reads done before the set is reused
+        __syncwarp();
+        if (lane == 0) mbar_arrive_cluster(map_rank(&tempty[si], 0));
       }
       if (stop) break;
       if (prow) {                                      // the last piece to arrive writes C
