@@ -357,6 +357,27 @@ int32_t desc_matmul(const desc_view *a_v, const desc_view *b_v, int64_t M, int64
                     size_t a_bytes, const float *B, size_t b_bytes, float *C, size_t c_bytes, int32_t precision,
                     void *ws, size_t ws_bytes, desc_stream_t stream);
 
+/* The schedule a tensor-core form of desc_matmul takes for a shape (host
+ * only, no launch).  candidate: -1 for what desc_matmul would take (the
+ * forced or tuned candidate, else the size rule), or 0 .. 5 (see
+ * desc_candidate_count for DESC_OP_MATMUL).  max_pairs: the number of CTA
+ * pairs the GPU holds at once; 0 asks the current device (DESC_ERR_CUDA
+ * without one).  precision must be DESC_MM_BF16, DESC_MM_SPLIT2 or
+ * DESC_MM_SPLIT3; M, N, K must be positive. */
+typedef struct {
+  int32_t candidate;    /* the schedule candidate taken */
+  int32_t pairs;        /* 1: CTA pairs over 256-row tiles, 0: single CTAs over 128-row tiles */
+  int32_t tile_n;       /* output tile columns: 256, or 512 for the wide pair tiles */
+  int32_t padded;       /* 1: an odd count of 128-row tiles padded with a zero tile row */
+  int64_t rows;         /* rows of the A terms the GEMM reads (M rounded up, padding included) */
+  int64_t tiles;        /* output tiles */
+  int64_t whole_tiles;  /* tiles computed whole; each of the others is cut along K into `pieces` */
+  int32_t pieces;
+  int32_t max_pairs;    /* the resident pair count the plan used */
+} desc_mm_plan;
+int32_t desc_matmul_plan(int64_t M, int64_t N, int64_t K, int32_t precision, int32_t candidate,
+                         int32_t max_pairs, desc_mm_plan *plan);
+
 /* ---- Split launch: two ops on the two parts of one grid -------------------
  * Section 3.3 splits an execution resource so that its parts run different
  * code.  desc_split_reduce_transpose runs ONE kernel launch whose first

@@ -82,6 +82,12 @@ class Problem(ctypes.Structure):
                 ("k", c_int64)]
 
 
+class MmPlan(ctypes.Structure):
+    _fields_ = [("candidate", c_int32), ("pairs", c_int32), ("tile_n", c_int32), ("padded", c_int32),
+                ("rows", c_int64), ("tiles", c_int64), ("whole_tiles", c_int64), ("pieces", c_int32),
+                ("max_pairs", c_int32)]
+
+
 class TuneBuffers(ctypes.Structure):
     _fields_ = [("inp", c_void_p), ("out", c_void_p), ("sums", c_void_p), ("offsets", c_void_p), ("ws", c_void_p),
                 ("ws_bytes", c_size_t), ("in2", c_void_p)]
@@ -123,6 +129,7 @@ def _declare(L):
                                      c_size_t, P]),
         "desc_stream_status": (c_int32, [P]),
         "desc_matmul_workspace_size": (c_int32, [c_int64, c_int64, c_int64, c_int32, POINTER(c_size_t)]),
+        "desc_matmul_plan": (c_int32, [c_int64, c_int64, c_int64, c_int32, c_int32, c_int32, POINTER(MmPlan)]),
         "desc_matmul": (c_int32, [POINTER(View), POINTER(View), c_int64, c_int64, c_int64, P, c_size_t, P, c_size_t,
                                   P, c_size_t, c_int32, P, c_size_t, P]),
         "desc_segmented_workspace_size": (c_int32, [c_int64, c_int64, POINTER(c_size_t)]),
@@ -422,6 +429,15 @@ def desc_matmul(A, B, precision, a_view=None, b_view=None, M=None, N=None, K=Non
     _check(L.desc_matmul(_ref(av), _ref(bv), M, N, K, _ptr(A), A.numel() * 4, _ptr(B), B.numel() * 4, _ptr(out),
                          out.numel() * 4, precision, _ptr(ws), ws.numel(), _stream(stream)), "desc_matmul")
     return out
+
+
+def desc_matmul_plan(M, N, K, precision, candidate=-1, max_pairs=0) -> dict:
+    """The schedule a tensor-core desc_matmul takes for this shape (no
+    launch): candidate -1 is what desc_matmul would take; max_pairs 0 asks
+    the current device."""
+    pl = MmPlan()
+    _check(lib().desc_matmul_plan(M, N, K, precision, candidate, max_pairs, ctypes.byref(pl)), "desc_matmul_plan")
+    return {name: getattr(pl, name) for name, _ in MmPlan._fields_}
 
 
 def desc_segmented_workspace(nseg, total, device):

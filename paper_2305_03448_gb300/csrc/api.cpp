@@ -342,6 +342,30 @@ extern "C" int32_t desc_matmul_workspace_size(int64_t M, int64_t N, int64_t K, i
   return DESC_OK;
 }
 
+extern "C" int32_t desc_matmul_plan(int64_t M, int64_t N, int64_t K, int32_t precision, int32_t candidate,
+                                    int32_t max_pairs, desc_mm_plan *plan) {
+  const int planes = mm_planes(precision);
+  if (!plan || !planes || M <= 0 || N <= 0 || K <= 0 || candidate < -1 || candidate >= mm_candidates() ||
+      max_pairs < 0)
+    return DESC_ERR_INVALID_ARG;
+  if (max_pairs == 0 && (max_pairs = mm_max_pairs()) <= 0) return DESC_ERR_CUDA;
+  const int nprod = planes == 3 ? 6 : (planes == 2 ? 3 : 1);
+  MmPlan pl;
+  const int32_t r = mm_plan(M, N, K, nprod, candidate >= 0 ? candidate : schedule_for(DESC_OP_MATMUL, DESC_F32, M, N),
+                            max_pairs, &pl);
+  if (r != DESC_OK) return r;
+  plan->candidate = pl.cand;
+  plan->pairs = pl.pairs;
+  plan->tile_n = 256 * pl.width;
+  plan->padded = pl.padded;
+  plan->rows = pl.Mp;
+  plan->tiles = pl.tiles;
+  plan->whole_tiles = pl.whole;
+  plan->pieces = pl.pieces;
+  plan->max_pairs = max_pairs;
+  return DESC_OK;
+}
+
 extern "C" int32_t desc_matmul(const desc_view *a_v, const desc_view *b_v, int64_t M, int64_t N, int64_t K,
                                const float *A, size_t a_bytes, const float *B, size_t b_bytes, float *C,
                                size_t c_bytes, int32_t precision, void *ws, size_t ws_bytes, desc_stream_t s) {

@@ -118,6 +118,22 @@ size_t mm_tc_ws(int64_t M, int64_t N, int64_t K, int planes);
 // rasterisation group in tile rows.
 int mm_candidates();
 void mm_candidate(int cand, int *pairs, int *group_rows, int *width);
+// The schedule of a tensor-core product, decided on the host from the shape,
+// the number of products, the candidate (-1: the size rule) and the number
+// of CTA pairs the GPU holds at once.
+struct MmPlan {
+  int cand;                    // candidate taken
+  int pairs;                   // 1: CTA pairs (cta_group::2), 0: single CTAs
+  int width;                   // pair tiles are 256 x 256 width
+  int padded;                  // an odd count of 128-row tiles padded with a zero row
+  int group_rows;              // rasterisation group, in 128-row tiles
+  int64_t Mp;                  // rows of the A planes the GEMM reads
+  int64_t tiles_m, tiles_n;    // output tiles (tile-row pairs when pairs)
+  int64_t tiles, whole;        // output tiles, and those computed whole
+  int pieces;                  // K pieces of each of the other tiles
+};
+int32_t mm_plan(int64_t M, int64_t N, int64_t K, int nprod, int cand, int max_pairs, MmPlan *pl);
+int mm_max_pairs();            // CTA pairs resident at once on the current device, 0 without one
 int32_t launch_mm_tc(const float *A, int64_t a_off, int64_t a_sr, int64_t a_sc, const float *B, int64_t b_off,
                      int64_t b_sr, int64_t b_sc, float *C, int64_t M, int64_t N, int64_t K, int planes,
                      int nprod, const int *pa, const int *pb, void *ws, size_t ws_bytes, desc_stream_t s);

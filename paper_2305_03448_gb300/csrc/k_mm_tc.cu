@@ -1147,6 +1147,53 @@ size_t part_bytes(int64_t M, int64_t N, int planes) {
 
 // Planes needed by a precision: 1 (BF16), 2 (2-term split), 3 (3-term split),
 // then the pieces' partial tiles.
+int mm_max_pairs() {
+  const MmDevice &d = mm_device();
+  return d.status == DESC_OK ? d.max_pairs : 0;
+}
+
+int32_t mm_plan(int64_t M, int64_t N, int64_t K, int nprod, int cand, int max_pairs, MmPlan *pl) {
+  if (!pl || M <= 0 || N <= 0 || K <= 0 || nprod < 1 || cand >= kMmCands) return DESC_ERR_INVALID_ARG;
+  const int64_t Mp1 = round_up(M, BM), Mp2 = round_up(M, 2 * BM), Np = round_up(N, BN), Kp = round_up(K, BK);
+  if (Mp2 / BM > 65535 || Np / BN > (int64_t(1) << 30) || Kp > (int64_t(1) << 30)) return DESC_ERR_UNSUPPORTED;
+  // Untuned: 256 x 512 pair tiles where they fill at least half of the
+  // resident pairs for one product, a quarter for the split forms (measured on
+  // GB300: SPLIT3 8192^3 4.32 -> 3.63 ms, 4096^3 0.615 -> 0.542 ms, 640 x 4096^2
+  // 198 -> 162 us with 24 wide tiles; BF16 8192^3 756 -> 728 us, but at 2048^3,
+  // 32 wide tiles, BF16 42 -> 50 us, and SPLIT3 111 -> 113 us), else 256 x 256.
+  if (cand < 0) {
+    const int64_t wide_tiles = (Mp2 / (2 * BM)) * ((Np + 2 * BN - 1) / (2 * BN));
+    cand = (nprod > 1 ? 4 * wide_tiles : 2 * wide_tiles) >= max_pairs ? 4 : 0;
+  }
+  int want_pairs = 1, group_rows = kGroupM, width = 1;
+  mm_candidate(cand, &want_pairs, &group_rows, &width);
+  // CTA pairs over 256 x 256 (or 256 x 512) tiles (cta_group::2), else single
+  // CTAs over 128 x 256 tiles.  An odd count of 128-row tiles is padded with
+  // one zero tile row (the split pass writes zeros there, the epilogue stores
+  // no row past M) where the pairs' leaner operand stream pays for the extra row.
+  const bool pad = want_pairs && max_pairs >= 1 && (Mp1 / BM) % 2 == 1 && (nprod > 1 || Mp1 / BM >= kMinPadRowsBF16);
+  const int64_t Mp = pad ? Mp2 : Mp1;
+  const bool pairs = want_pairs && (Mp / BM) % 2 == 0 && max_pairs >= 1;
+  if (!pairs) width = 1;
+  pl->cand = cand;
+  pl->pairs = pairs ? 1 : 0;
+  pl->width = width;
+  pl->padded = pad ? 1 : 0;
+  pl->group_rows = group_rows;
+  pl->Mp = Mp;
+  pl->tiles_m = pairs ? Mp / (2 * BM) : Mp / BM;
+  pl->tiles_n = (Np + BN * width - 1) / (BN * width);
+  pl->tiles = pl->tiles_m * pl->tiles_n;
+  if (pl->tiles >= (int64_t(1) << 31)) return DESC_ERR_UNSUPPORTED;
+  pl->whole = pl->tiles;
+  pl->pieces = 1;
+  if (pairs) {
+    pair_units(pl->tiles, (int)(Kp / BK), nprod, max_pairs, &pl->whole, &pl->pieces);
+    if (pl->whole + (pl->tiles - pl->whole) * pl->pieces >= (int64_t(1) << 31)) return DESC_ERR_UNSUPPORTED;
+  }
+  return DESC_OK;
+}
+
 // The A planes have room for an even number of 128-row tiles (an odd count
 // may be padded with a zero tile row so that the rows pair up).
 size_t mm_tc_ws(int64_t M, int64_t N, int64_t K, int planes) {
@@ -1169,55 +1216,31 @@ int32_t launch_mm_tc(const float *A, int64_t a_off, int64_t a_sr, int64_t a_sc, 
                                                          align256(size_t(planes) * Mp2 * Kp * 2));
   char *pbase = static_cast<char *>(ws) + align256(size_t(planes) * Mp2 * Kp * 2) +
                 align256(size_t(planes) * Np * Kp * 2);
-  // Untuned: 256 x 512 pair tiles where they fill at least half of the
-  // resident pairs for one product, a quarter for the split forms (measured on
-  // GB300: SPLIT3 8192^3 4.32 -> 3.63 ms, 4096^3 0.615 -> 0.542 ms, 640 x 4096^2
-  // 198 -> 162 us with 24 wide tiles; BF16 8192^3 756 -> 728 us, but at 2048^3,
-  // 16 wide tiles, BF16 42 -> 50 us and SPLIT3 111 -> 113 us), else 256 x 256.
-  int cand = schedule_for(DESC_OP_MATMUL, DESC_F32, M, N);
-  if (cand < 0) {
-    const int64_t wide_tiles = (Mp2 / (2 * BM)) * ((Np + 2 * BN - 1) / (2 * BN));
-    cand = (nprod > 1 ? 4 * wide_tiles : 2 * wide_tiles) >= max_pairs ? 4 : 0;
-  }
-  int want_pairs = 1, group_rows = kGroupM, width = 1;
-  mm_candidate(cand, &want_pairs, &group_rows, &width);
-  // Schedule: CTA pairs over 256 x 256 (or 256 x 512) tiles (cta_group::2),
-  // else single CTAs over 128 x 256 tiles.  An odd count of 128-row tiles is
-  // padded with one zero tile row (the split pass writes zeros there, the
-  // epilogue stores no row past M) where the pairs' leaner operand stream
-  // pays for the extra row.
-  const int64_t Mp1 = round_up(M, BM);
-  const bool pad = want_pairs && max_pairs >= 1 && (Mp1 / BM) % 2 == 1 && (nprod > 1 || Mp1 / BM >= kMinPadRowsBF16);
-  const int64_t Mp = pad ? Mp2 : Mp1;
-  const int Mt = (int)(Mp / BM);
-  const bool pairs = want_pairs && Mt % 2 == 0 && max_pairs >= 1;
-  if (!pairs) width = 1;
+  MmPlan pl;
+  int32_t r = mm_plan(M, N, K, nprod, schedule_for(DESC_OP_MATMUL, DESC_F32, M, N), max_pairs, &pl);
+  if (r != DESC_OK) return r;
+  const bool pairs = pl.pairs != 0;
+  const int width = pl.width;
+  const int64_t Mp = pl.Mp, ntiles = pl.tiles, nwhole = pl.whole;
+  const int pieces = pl.pieces;
   TileMap tmap;
-  tmap.Mt = pairs ? Mt / 2 : Mt;
-  tmap.Nt = (int)((Np + BN * width - 1) / (BN * width));
-  tmap.group_m = std::min(tmap.Mt, pairs ? group_rows / 2 : group_rows);
-  const int64_t ntiles = int64_t(tmap.Mt) * tmap.Nt;
-  if (ntiles >= (int64_t(1) << 31)) return DESC_ERR_UNSUPPORTED;
+  tmap.Mt = (int)pl.tiles_m;
+  tmap.Nt = (int)pl.tiles_n;
+  tmap.group_m = std::min(tmap.Mt, pairs ? pl.group_rows / 2 : pl.group_rows);
   const int kblocks = (int)(Kp / BK), split = planes > 1 ? 1 : 0;
-  int64_t nwhole = ntiles;
-  int pieces = 1;
   float *part = nullptr;
   int *cnt = nullptr;
   int ncnt = 0;
-  if (pairs) {
-    pair_units(ntiles, kblocks, nprod, max_pairs, &nwhole, &pieces);
-    if (nwhole + (ntiles - nwhole) * pieces >= (int64_t(1) << 31)) return DESC_ERR_UNSUPPORTED;
-    if (pieces > 1) {
-      const int64_t slots = ntiles - nwhole;
-      part = reinterpret_cast<float *>(pbase + half_bytes(planes));
-      cnt = reinterpret_cast<int *>(pbase + half_bytes(planes) + align256(size_t(slots * pieces) * kPartTileBytes));
-      ncnt = (int)(slots * 8);
-    }
+  if (pieces > 1) {
+    const int64_t slots = ntiles - nwhole;
+    part = reinterpret_cast<float *>(pbase + half_bytes(planes));
+    cnt = reinterpret_cast<int *>(pbase + half_bytes(planes) + align256(size_t(slots * pieces) * kPartTileBytes));
+    ncnt = (int)(slots * 8);
   }
 
   // A (M x K) -> planes [P][Mp][Kp];  B (K x N) -> transposed planes [P][Np][Kp];
   // the A pass also zeroes the pieces' counters.
-  int32_t r = launch_split(A, a_off, a_sr, a_sc, M, K, Mp, Kp, planes, pA, s, nsm, cnt, ncnt);
+  r = launch_split(A, a_off, a_sr, a_sc, M, K, Mp, Kp, planes, pA, s, nsm, cnt, ncnt);
   if (r != DESC_OK) return r;
   r = launch_split(B, b_off, b_sc, b_sr, N, K, Np, Kp, planes, pB, s, nsm);
   if (r != DESC_OK) return r;

@@ -116,16 +116,18 @@ def test_rejections():
     assert D.desc_stream_status() == 0
 
 
-# The last, partial wave of 256 x 256 pair tiles is cut along K into pieces
-# (at least 24 K blocks x products each) whose partial tiles the
-# last-arriving piece adds in order.  With 76 resident pairs: 16 tiles ->
-# SPLIT3 in 4 pieces of 4 K blocks, SPLIT2 in 2; K = 1090 -> 18 K blocks,
-# SPLIT3 pieces of 4, 5, 4, 5; 100 tiles -> 76 whole tiles and 24 tiles in 3
-# pieces (SPLIT3); K = 3100 -> 49 K blocks, BF16 pieces of 24 and 25.
+# The last, partial wave of pair tiles is cut along K into pieces (at least
+# 24 K blocks x products each) whose partial tiles the last-arriving piece
+# adds in order.  With 76 resident pairs (the cases of test_mm_plan.py):
+# 16 tiles of 256 x 256 -> SPLIT3 in 4 pieces of 4 K blocks, SPLIT2 in 2;
+# K = 1090 -> 18 K blocks, SPLIT3 pieces of 4, 5, 4, 5; 2560^2 on 256 x 256
+# tiles (candidate 0) -> 76 whole tiles and 24 in 3 pieces (SPLIT3), on
+# 256 x 512 tiles 50 whole tiles; K = 3100 -> 49 K blocks, BF16 pieces of 24
+# and 25.
 PIECE_SHAPES = [(1024, 1024, 1024), (1000, 1000, 1090), (2560, 2560, 1024), (1000, 1000, 3100)]
 
 
-@pytest.mark.parametrize("cand", [-1, 4])              # the default schedule; 256 x 512 pair tiles
+@pytest.mark.parametrize("cand", [-1, 0, 4])           # the default schedule; 256 x 256; 256 x 512
 @pytest.mark.parametrize("M,N,K", PIECE_SHAPES)
 def test_last_wave_pieces(M, N, K, cand):
     D.desc_force_candidate(D.OP_MATMUL, cand)
