@@ -254,3 +254,15 @@ def test_odd_tile_rows_padded_to_pairs(M, N, K):
             D.desc_force_candidate(D.OP_MATMUL, -1)
         assert torch.equal(C, ref), p
     assert D.desc_stream_status() == 0
+
+
+def test_simt_fp32_wide_tiles_sampled_rows():
+    """Enough 128 x 256 tiles for eight waves (152 SMs): the CUDA-core form
+    takes its 8 x 16-outputs-per-thread kernel; sampled rows against FP64."""
+    M, N, K = 4864, 8192, 96
+    A, B = mats(M, N, K, seed=77)
+    C = D.desc_matmul(A.cuda(), B.cuda(), D.MM_FP32_SIMT).cpu().numpy()
+    rows = np.array([0, 1, 127, 128, 2437, 4800, 4863])
+    ref = OM.matmul_f64(A.numpy()[rows], B.numpy())
+    assert OM.rel_frobenius(C[rows], ref) <= 1e-6
+    assert np.isfinite(C).all()
