@@ -100,7 +100,6 @@ extern "C" int32_t desc_reduce(const desc_view *v, const desc_exec *ex, int32_t 
   if ((r = check_device_ptr(out, 4)) != DESC_OK) return r;
   if (L.base_elems > 0 && (r = check_device_ptr(in, 4)) != DESC_OK) return r;
   if (ranges_overlap(in, in_bytes, out, out_bytes)) return DESC_ERR_OVERLAP;
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(s);
   if (p.n_rest == 0) return fill_identity(out, p.n_keep, dtype, flags, s);
   int64_t start0, seg;
   if (!t_generic && rest_contiguous(p, true, &start0, &seg))

@@ -41,7 +41,8 @@ __host__ __device__ inline int64_t row_stride(int H) { return 4 * int64_t(H) + 2
 // Forward of one row by one warp.  Lane l owns hidden units l and l + 32.
 // Returns y (in every lane); z1/z2/h1/h2 of the owned units in the arrays.
 __device__ __forceinline__ float forward_row(const float *__restrict__ P, int F, int H, const float *__restrict__ x,
-                                             float (&z1)[2], float (&z2)[2], float (&h1)[2], float (&h2)[2]) {
+                                             float (&z1)[kMaxH / 32], float (&z2)[kMaxH / 32], float (&h1)[kMaxH / 32],
+                                             float (&h2)[kMaxH / 32]) {
   const Layout L = layout(F, H);
   const int lane = threadIdx.x & 31, per = H / 32;
   for (int u = 0; u < per; ++u) {
@@ -77,7 +78,7 @@ __global__ void __launch_bounds__(256) mlp_rows_kernel(const float *__restrict__
   if (r >= rows) return;
   const int lane = threadIdx.x & 31, per = H / 32;
   const float *x = X + r * F;
-  float z1[2], z2[2], h1[2], h2[2];
+  float z1[kMaxH / 32], z2[kMaxH / 32], h1[kMaxH / 32], h2[kMaxH / 32];
   const float y = forward_row(P, F, H, x, z1, z2, h1, h2);
   if (y_out && lane == 0) y_out[r] = y;
   if (!TRAIN) return;
@@ -85,7 +86,7 @@ __global__ void __launch_bounds__(256) mlp_rows_kernel(const float *__restrict__
   float *S = scratch + r * row_stride(H);
   const float err = y - t[r];
   const float dy = 2.f * err / float(rows);
-  float dz2[2], dz1[2];
+  float dz2[kMaxH / 32], dz1[kMaxH / 32];
   for (int u = 0; u < per; ++u) dz2[u] = z2[u] > 0.f ? dy * P[L.w3 + lane + 32 * u] : 0.f;
   for (int u = 0; u < per; ++u) {
     const int i = lane + 32 * u;
@@ -156,7 +157,7 @@ __global__ void __launch_bounds__(kMaxCand * 32) mlp_pick_kernel(const float *__
   __shared__ float sp[kMaxCand];
   const int w = threadIdx.x >> 5;
   if (w < ncand) {
-    float z1[2], z2[2], h1[2], h2[2];
+    float z1[kMaxH / 32], z2[kMaxH / 32], h1[kMaxH / 32], h2[kMaxH / 32];
     const float y = forward_row(P, F, H, Xc + int64_t(w) * F, z1, z2, h1, h2);
     if ((threadIdx.x & 31) == 0) sp[w] = y;
   }
