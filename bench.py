@@ -186,9 +186,10 @@ def run_ours(args, rank, world, local_rank):
         D.desc_tune_load(args.load_tune)
         schedules = {"loaded": args.load_tune}
     elif not args.no_tune:
-        schedules = autotune_step(D, stream, {"reduce": (D.OP_REDUCE, D.I32, Rn, 0, xr, out_r, ws_r),
-                                              "scan": (D.OP_SCAN, D.F32, Sn, 0, xs, out_s, ws_s),
-                                              "transpose": (D.OP_TRANSPOSE, D.F32, T * T, T, xt, out_t, ws_s)},
+        red_view = dict(view=([Rn], red_ops), grid=red_grid, block=red_block, level=V.GRID)
+        schedules = autotune_step(D, stream, {"reduce": (D.OP_REDUCE, D.I32, Rn, 0, xr, out_r, ws_r, red_view),
+                                              "scan": (D.OP_SCAN, D.F32, Sn, 0, xs, out_s, ws_s, None),
+                                              "transpose": (D.OP_TRANSPOSE, D.F32, T * T, T, xt, out_t, ws_s, None)},
                                   [name for name, _ in ops])
         if args.save_tune:
             D.desc_tune_save(args.save_tune)
@@ -293,14 +294,14 @@ def autotune_step(D, stream, probs, names):
     import ctypes
     out = {}
     for name in names:
-        op, dt, n, aux, x, y, ws = probs[name]
-        p = D.make_problem(op, dt, n, aux)
+        op, dt, n, aux, x, y, ws, view = probs[name]
+        p = D.make_problem(op, dt, n, aux, **(view or {}))
         b = D.TuneBuffers()
         b.inp, b.out, b.sums, b.offsets = x.data_ptr(), y.data_ptr(), None, None
         b.ws, b.ws_bytes = ws.data_ptr(), ws.numel()
         nc = D.candidate_count(op)
         us = (ctypes.c_float * nc)()
-        D._check(D.lib().desc_tune_measure(ctypes.byref(p), ctypes.byref(b), 5, D._stream(stream), us),
+        D._check(D.lib().desc_tune_measure(p.ref(), ctypes.byref(b), 5, D._stream(stream), us),
                  "desc_tune_measure")
         us = list(us)
         best = min(range(nc), key=lambda c: (us[c], c))
@@ -344,17 +345,105 @@ def run_step_concurrent(torch, D, dev, stream, op_reduce, op_scan, op_transpose,
                                     "every step"}
 
 
+def bucket_of(prob):
+    """The tuned-table bucket a problem falls in (op, dtype, floor(log2 n),
+    floor(log2(aux + 1))), with n and aux as the op call sees them."""
+    n, aux = prob["n"], prob["aux"]
+    if prob.get("view") is not None:
+        if prob["op"] == 1:
+            ops = prob["view"][1]
+            n = n - sum(o[1] for o in ops if o[0] == "split_snd")
+            aux = 0
+        elif prob["level"] == 0:
+            aux = 0
+        else:
+            aux = prob["grid"][0]
+    elif prob["op"] == 1:
+        aux = 0
+    elif prob["op"] == 0 and aux <= 1:
+        aux = 0
+    return (prob["op"], prob["dtype"], max(int(n), 1).bit_length() - 1, (int(aux) + 1).bit_length() - 1)
+
+
+def regret_study(D, train_probs, test_probs, arena, model, epochs=300, batch=128, lr=2e-3, reps=5, retime_reps=20):
+    """Learned schedules against exhaustive autotuning.  Every candidate of
+    every problem is timed (training rows, and the held-out ground truth); the
+    cost model is trained on the GPU by the library's kernels (log time); on
+    each held-out problem the exhaustive winner, the model's pick and the
+    default (candidate 0) are then timed again together, in interleaved rounds
+    of `retime_reps`, and regret = t(pick) / min(t(winner), t(pick)) - 1 comes
+    from those times (so a pick measured as fast as the winner has no regret).
+    Also reports how many held-out problems share a tuned-table bucket or an
+    exact shape with a training problem."""
+    import math
+    import time as _time
+    import torch
+    X, t = [], []
+    t0 = _time.time()
+    for prob in train_probs:
+        us = D.desc_tune_measure(prob, arena, reps)
+        for c, row in enumerate(D.feature_rows(prob)):
+            X.append(row)
+            t.append(math.log(max(us[c], 1e-3)))
+    measure_train_s = _time.time() - t0
+    Xt = torch.tensor(X, dtype=torch.float32, device="cuda")
+    tt = torch.tensor(t, dtype=torch.float32, device="cuda")
+    perm = torch.randperm(Xt.shape[0], generator=torch.Generator().manual_seed(0)).cuda()
+    t1 = _time.time()
+    loss = model.train(Xt[perm].contiguous(), tt[perm].contiguous(), epochs, batch, lr)
+    torch.cuda.synchronize()
+    train_s = _time.time() - t1
+    train_buckets = {bucket_of(p) for p in train_probs}
+
+    def shape_key(p):
+        L = p.get("lengths")
+        return (p["op"], p["dtype"], p["n"], p["aux"], p.get("k", 0), repr(p.get("view")), p.get("level", 0),
+                None if L is None else tuple(L.tolist()))
+    train_shapes = {shape_key(p) for p in train_probs}
+    reg_model, reg_default, exact, exh_s, pick_s, retime_s = [], [], 0, 0.0, 0.0, 0.0
+    bucket_overlap = sum(1 for p in test_probs if bucket_of(p) in train_buckets)
+    shape_overlap = sum(1 for p in test_probs if shape_key(p) in train_shapes)
+    for prob in test_probs:
+        a = _time.time()
+        us = D.desc_tune_measure(prob, arena, reps)
+        exh_s += _time.time() - a
+        win = min(range(len(us)), key=lambda c: (us[c], c))
+        rows = torch.tensor(D.feature_rows(prob), dtype=torch.float32, device="cuda")
+        a = _time.time()
+        c, _ = model.pick(rows)
+        pick_s += _time.time() - a
+        cands = sorted({win, c, 0})
+        a = _time.time()
+        ut = dict(zip(cands, D.desc_tune_measure_cands(prob, arena, cands, retime_reps)))
+        retime_s += _time.time() - a
+        best = min(ut[win], ut[c])
+        reg_model.append(ut[c] / best - 1.0)
+        reg_default.append(ut[0] / min(ut[win], ut[0]) - 1.0)
+        exact += int(c == win)
+    n = len(test_probs)
+    srt = sorted(reg_model)
+    return {"train_rows": len(X), "train_problems": len(train_probs), "test_problems": n, "final_loss": loss,
+            "mean_regret": sum(reg_model) / n, "p90_regret": srt[int(0.9 * (n - 1))],
+            "default_mean_regret": sum(reg_default) / n, "exact_picks": exact / n,
+            "overlap": {"bucket": bucket_overlap, "shape": shape_overlap},
+            "split": "train: floor(log2 n) even; held out: odd (no shared tuned-table bucket)",
+            "retime_reps": retime_reps, "measure_train_s": measure_train_s, "train_s": train_s,
+            "exhaustive_test_s": exh_s, "retime_test_s": retime_s, "model_pick_s": pick_s}
+
+
 def run_schedule_model(torch, D, synth, n_train=860, n_test=500):
     """Learned schedules: exhaustive timings of every candidate of seeded
     problems from the reduce / scan / transpose / segmented / matmul families
-    (about 3,000 training rows), the cost model trained on the GPU by the
-    library's kernels, and its picks on 500 held-out problems compared with
-    the exhaustive tuner (regret = t(pick) / t(best) - 1) and with the default."""
+    (about 3,000 training rows, sizes with even floor(log2 n)), the cost model
+    trained on the GPU by the library's kernels, and its picks on 500 held-out
+    problems (odd floor(log2 n): no tuned-table bucket in common) compared with
+    the exhaustive tuner and with the default (regret = t(pick) / t(best) - 1,
+    from re-timed winners and picks)."""
     arena = D.TuneArena(1 << 27, 5000, max_mm=4096)
-    train = synth.tune_problems(n_train, seed=101)
-    test = synth.tune_problems(n_test, seed=202)
+    train = synth.tune_problems(n_train, seed=101, part="even")
+    test = synth.tune_problems(n_test, seed=202, part="odd")
     model = D.CostModel(synth.mlp_init(D.NUM_FEATURES, 64, seed=303))
-    r = D.regret_study(train, test, arena, model, epochs=300, batch=128, lr=2e-3, reps=5)
+    r = regret_study(D, train, test, arena, model, epochs=300, batch=128, lr=2e-3, reps=5)
     del arena
     torch.cuda.empty_cache()
     return {k: (round(v, 4) if isinstance(v, float) else v) for k, v in r.items()}

@@ -26,7 +26,9 @@
  *    runs asynchronously.  Device-side failures (a bounded wait that ran out)
  *    are recorded in a per-device status word read by desc_stream_status().
  *  - Descriptors are read during the call only and never kept.
- *  - Calls are thread-safe; different streams may be used concurrently.
+ *  - Calls are thread-safe; different streams may be used concurrently
+ *    (two exceptions, stated at their declarations: desc_scan_noalloc calls
+ *    must not overlap, and desc_tune_predict calls take turns).
  */
 #ifndef DESC_H
 #define DESC_H
@@ -449,10 +451,12 @@ int32_t desc_segmented_reduce_scan_per_segment(const int64_t *h_offsets, int64_t
  *   DESC_OP_MATMUL     tensor-core forms: {CTA pairs on 256 x 256 tiles where
  *                      the 128-row tiles pair up, one CTA per 128 x 256 tile}
  *                      x {wide, narrow} rasterisation groups: 16 / 4 tile
- *                      rows (single) and 8 / 2 tile-row pairs (pairs)
- * A problem describes one call's shape; ops look up the candidate recorded
- * for their (op, dtype, floor(log2 n), floor(log2(aux + 1))) bucket in a
- * process-wide table (thread-safe), else use candidate 0. */
+ *                      rows (single) and 8 / 2 tile-row pairs (pairs); and
+ *                      pairs on 256 x 512 tiles, wide / narrow groups
+ * Ops look up the candidate recorded for their bucket -- (GPU model, op,
+ * dtype, floor(log2 n), floor(log2(aux + 1))) with n and aux as the op call
+ * sees them (below) -- in a process-wide table (thread-safe), else use
+ * candidate 0.  A table saved on one GPU model is not used on another. */
 typedef enum {
   DESC_OP_REDUCE = 0,
   DESC_OP_SCAN = 1,
@@ -460,22 +464,35 @@ typedef enum {
   DESC_OP_SEGMENTED = 3,
   DESC_OP_MATMUL = 4
 } desc_op;
-#define DESC_NUM_FEATURES 32
+#define DESC_NUM_FEATURES 40
+/* One call's shape.  With `view` NULL the call is the op's plain form: reduce
+ * of n elements (aux > 1: n / aux elements per output, selected per block),
+ * scan of n elements, transpose of an aux x (n / aux) matrix, segmented with
+ * aux segments of n elements in all, matmul M = n, N = aux, K = k.  With a
+ * view (reduce and scan only), the call is desc_reduce / desc_scan through
+ * that view, the execution resource `ex` and the level `level` (out_level /
+ * seg_level); n and aux are then taken from the lowered view: n = the points
+ * reduced or scanned, aux = the outputs (reduce) or segments (scan) when more
+ * than one, else 0.  seg_lengths (segmented): the aux segment lengths on the
+ * host, read during the call only; NULL leaves the length histogram zero. */
 typedef struct {
-  int32_t op;          /* desc_op                                                      */
-  int32_t dtype;       /* DESC_I32 / DESC_F32 (matmul: DESC_F32)                        */
-  int64_t n;           /* elements; matmul: M                                          */
-  int64_t aux;         /* reduce: outputs (n/aux elements each); transpose: rows;
-                          segmented: segments; scan: 0; matmul: N                      */
-  float seg_hist[8];   /* segmented: fraction of segments with floor(log2 len) in
-                          [0,3), [3,6), ..., [18,21), and empty ones in bucket 0         */
-  int64_t k;           /* matmul: K (the bucket is (M, N)); other ops: 0               */
+  int32_t op;                  /* desc_op                                                   */
+  int32_t dtype;               /* DESC_I32 / DESC_F32 (matmul: DESC_F32)                     */
+  int64_t n;                   /* elements; matmul: M                                       */
+  int64_t aux;                 /* reduce: outputs; transpose: rows; segmented: segments;
+                                  scan: 0; matmul: N                                         */
+  int64_t k;                   /* matmul: K; other ops: 0                                   */
+  const int64_t *seg_lengths;  /* segmented: aux lengths (host), or NULL                    */
+  const desc_view *view;       /* reduce / scan: the call's view, or NULL                   */
+  const desc_exec *ex;         /* the view's execution resource (NULL without selects)      */
+  int32_t level;               /* reduce: out_level; scan: seg_level (with a view)           */
 } desc_problem;
-/* Device buffers a measurement runs on (the caller owns them): in (n elements
- * of dtype; matmul: A, M x K FP32), out (reduce: aux or 1 elements; matmul:
- * M x N; others: n), sums (segmented: aux), offsets (segmented: aux + 1,
- * device int64), ws (at least the op's workspace), in2 (matmul: B, K x N FP32;
- * else unused).  Matmul problems are timed in DESC_MM_BF16. */
+/* Device buffers a measurement runs on (the caller owns them): in (the input:
+ * n elements of dtype, or the view's base array; matmul: A, M x K FP32), out
+ * (reduce: the outputs; matmul: M x N; others: as many elements as in), sums
+ * (segmented: aux), offsets (segmented: aux + 1, device int64), ws (at least
+ * the op's workspace), in2 (matmul: B, K x N FP32; else unused).  Matmul
+ * problems are timed in DESC_MM_BF16. */
 typedef struct {
   const void *in;
   void *out;
@@ -487,23 +504,46 @@ typedef struct {
 } desc_tune_buffers;
 
 int32_t desc_candidate_count(int32_t op, int32_t *count);
-/* Features of (problem, candidate) for the cost model: op and dtype one-hot,
- * log2 sizes, the segment-length histogram, the candidate's tile size,
- * vectors in flight, CTA target (matmul: rasterisation group), index one-hot
- * (8 slots), load path, log2 K and CTA pairing (DESC_NUM_FEATURES floats). */
+/* Features of (problem, candidate) for the cost model, DESC_NUM_FEATURES
+ * floats:
+ *   [0, 5)   op one-hot            [5, 7)   dtype one-hot (I32, F32)
+ *   [7]      log2 n / 32           [8]      log2(aux + 1) / 32
+ *   [9]      log2(n / (aux + 1) + 1) / 32
+ *   [10, 18) segmented: fraction of segments with floor(log2 len) in [0, 3),
+ *            [3, 6), ..., [21, 24) (empty segments in the first bucket),
+ *            computed here from seg_lengths
+ *   [18]     log2 of the candidate's tile elements / 32
+ *   [19]     vectors in flight / 16   [20] log2 CTA target or group / 16
+ *   [21, 29) candidate index one-hot  [29] load path   [30] log2(K + 1) / 32
+ *   [31]     CTA pairs
+ *   [32, 37) view composition: number of group, split (fst or snd),
+ *            transpose, reverse and select views, each / 8
+ *   [37]     the deepest nesting a view acts on (map depth) / 4
+ *   [38]     1 when the lowered map takes the op's hand-indexed kernel
+ *            (contiguous runs, or a tiled 2-D transposition), else 0
+ *   [39]     dims of the lowered map after merging neighbours / 8 */
 int32_t desc_features(const desc_problem *p, int32_t cand, float *out, int32_t nout);
 /* Times every candidate on the given buffers (reps launches each, CUDA events
  * on the stream, median), writing microseconds to us[count].  Synchronises. */
 int32_t desc_tune_measure(const desc_problem *p, const desc_tune_buffers *b, int32_t reps, desc_stream_t stream,
                           float *us);
+/* Times the ncand candidates listed in cands (each reps launches, median), in
+ * rounds that visit every listed candidate once before the next round (so slow
+ * drifts of the clock touch all of them alike); us[i] belongs to cands[i]. */
+int32_t desc_tune_measure_cands(const desc_problem *p, const desc_tune_buffers *b, const int32_t *cands,
+                                int32_t ncand, int32_t reps, desc_stream_t stream, float *us);
 /* Exhaustive autotuning: measure all candidates, record the fastest (ties:
  * the lowest index) for the problem's bucket, return it. */
 int32_t desc_tune_exhaustive(const desc_problem *p, const desc_tune_buffers *b, int32_t reps,
                              desc_stream_t stream, int32_t *best);
+/* Table entries for the current device's GPU model (no GPU: the model name
+ * "none"). */
 int32_t desc_tune_record(const desc_problem *p, int32_t cand);
 int32_t desc_tune_lookup(const desc_problem *p, int32_t *cand);   /* -1 when nothing is recorded */
 int32_t desc_tune_clear(void);
-int32_t desc_tune_save(const char *path);                          /* text file, one bucket per line */
+/* Text file, one bucket per line: GPU model (spaces as '_'), op, dtype,
+ * log2 n, log2(aux + 1), candidate.  Loading merges the file into the table. */
+int32_t desc_tune_save(const char *path);
 int32_t desc_tune_load(const char *path);
 /* Per-thread override used while measuring: ops of `op` use candidate `cand`
  * (-1: back to the table). */
@@ -552,7 +592,12 @@ int32_t desc_mlp_pick(const float *params, int32_t F, int32_t H, const float *Xc
                       int32_t *best, desc_stream_t stream);
 /* Learned schedules: the model (kept by reference: the caller keeps params
  * alive and unchanged while it is set) picks the candidate of a problem
- * without timing, and the pick is recorded like a tuned one. */
+ * without timing, and the pick is recorded like a tuned one.
+ * desc_tune_predict stages the candidates' features in device memory the
+ * library owns, runs the pick kernel on `stream` and waits for it: calls from
+ * several threads are serialised by a library-wide lock (each gets its own
+ * pick), the call synchronises the stream, and it cannot be captured into a
+ * CUDA graph. */
 int32_t desc_tune_set_model(const float *params, int32_t F, int32_t H);
 int32_t desc_tune_predict(const desc_problem *p, desc_stream_t stream, int32_t *best);
 

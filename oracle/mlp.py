@@ -10,7 +10,9 @@ library.  Its definition, restated here independently of the CUDA kernels:
 
 relu'(z) is 1 for z > 0 and 0 otherwise.  Parameters are one flat vector
 [W1 (row-major), b1, W2 (row-major), b2, w3, b3].  The optimiser is Adam
-(Kingma and Ba 2015, Algorithm 1) with bias correction.
+(Kingma and Ba 2015, Algorithm 1) with bias correction.  One group of input
+features is the segment-length histogram of a batched call
+(length_histogram below).
 """
 from __future__ import annotations
 
@@ -76,3 +78,16 @@ def adam(p, g, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8):
     vh = v / (1.0 - beta2 ** step)
     return p - lr * mh / (np.sqrt(vh) + eps), m, v
 
+
+def length_histogram(lengths):
+    """The cost model's segment-length feature: for buckets b = 0..7, the
+    fraction of segments whose length L has floor(log2 L) in [3b, 3b + 3)
+    (the last bucket also takes every longer segment); empty segments count
+    in bucket 0.  Written with integer bit lengths: floor(log2 L) is
+    L.bit_length() - 1 for L >= 1."""
+    counts = [0] * 8
+    L = [int(v) for v in lengths]
+    for v in L:
+        b = 0 if v <= 0 else min((v.bit_length() - 1) // 3, 7)
+        counts[b] += 1
+    return [c / len(L) for c in counts] if L else [0.0] * 8

@@ -24,7 +24,7 @@ X, Y, Z, LANE = 0, 1, 2, 3
 I32, F32 = 0, 1
 MM_FP32_SIMT, MM_BF16, MM_SPLIT3, MM_SPLIT2 = 0, 1, 2, 3
 OP_REDUCE, OP_SCAN, OP_TRANSPOSE, OP_SEGMENTED, OP_MATMUL = 0, 1, 2, 3, 4
-NUM_FEATURES = 32
+NUM_FEATURES = 40
 KAHAN = 1
 MAX, MIN, EXCLUSIVE = 1 << 1, 1 << 2, 1 << 3
 DEBUG_STALL_TILE = 1 << 16
@@ -78,8 +78,9 @@ class Stmt(ctypes.Structure):
 
 
 class Problem(ctypes.Structure):
-    _fields_ = [("op", c_int32), ("dtype", c_int32), ("n", c_int64), ("aux", c_int64), ("seg_hist", ctypes.c_float * 8),
-                ("k", c_int64)]
+    _fields_ = [("op", c_int32), ("dtype", c_int32), ("n", c_int64), ("aux", c_int64), ("k", c_int64),
+                ("seg_lengths", POINTER(c_int64)), ("view", POINTER(View)), ("ex", POINTER(Exec)),
+                ("level", c_int32)]
 
 
 class MmPlan(ctypes.Structure):
@@ -143,6 +144,8 @@ def _declare(L):
         "desc_candidate_count": (c_int32, [c_int32, POINTER(c_int32)]),
         "desc_features": (c_int32, [POINTER(Problem), c_int32, POINTER(ctypes.c_float), c_int32]),
         "desc_tune_measure": (c_int32, [POINTER(Problem), POINTER(TuneBuffers), c_int32, P, POINTER(ctypes.c_float)]),
+        "desc_tune_measure_cands": (c_int32, [POINTER(Problem), POINTER(TuneBuffers), POINTER(c_int32), c_int32,
+                                              c_int32, P, POINTER(ctypes.c_float)]),
         "desc_tune_exhaustive": (c_int32, [POINTER(Problem), POINTER(TuneBuffers), c_int32, P, POINTER(c_int32)]),
         "desc_tune_record": (c_int32, [POINTER(Problem), c_int32]),
         "desc_tune_lookup": (c_int32, [POINTER(Problem), POINTER(c_int32)]),
@@ -524,26 +527,46 @@ def desc_stream_status(stream=None) -> int:
 
 
 # ----------------------------------------------------------------- schedules
-def seg_hist(lengths):
-    """Fraction of segments per floor(log2 len) bucket [0,3), [3,6) ... [21,24);
-    empty segments count in bucket 0."""
-    import math
-    h = [0.0] * 8
-    L = [int(v) for v in lengths]
-    for v in L:
-        b = 0 if v <= 0 else min(int(math.log2(v)) // 3, 7)
-        h[b] += 1.0
-    return [x / max(len(L), 1) for x in h]
+class ProblemRef:
+    """A desc_problem and the host arrays it points to (kept alive with it)."""
+
+    def __init__(self, prob: dict):
+        p = Problem()
+        p.op, p.dtype, p.n, p.aux = int(prob["op"]), int(prob["dtype"]), int(prob["n"]), int(prob.get("aux", 0))
+        p.k = int(prob.get("k", 0) or 0)
+        self.keep = []
+        lengths = prob.get("lengths")
+        if lengths is not None:
+            vals = lengths.tolist() if hasattr(lengths, "tolist") else list(lengths)
+            arr = (c_int64 * max(len(vals), 1))(*[int(v) for v in vals])
+            self.keep.append(arr)
+            p.seg_lengths = ctypes.cast(arr, POINTER(c_int64))
+        if prob.get("view") is not None:
+            base_shape, ops = prob["view"]
+            v = make_view(base_shape, ops)
+            self.keep.append(v)
+            p.view = ctypes.pointer(v)
+            if prob.get("grid") is not None:
+                e = make_exec(prob["grid"], prob["block"])
+                self.keep.append(e)
+                p.ex = ctypes.pointer(e)
+            p.level = int(prob.get("level", GRID))
+        self.p = p
+
+    def ref(self):
+        return ctypes.byref(self.p)
 
 
-def make_problem(op, dtype, n, aux=0, lengths=None, k=0) -> Problem:
-    """Matmul: n = M, aux = N, k = K."""
-    p = Problem()
-    p.op, p.dtype, p.n, p.aux, p.k = int(op), int(dtype), int(n), int(aux), int(k)
-    if lengths is not None:
-        for i, v in enumerate(seg_hist(lengths)):
-            p.seg_hist[i] = v
-    return p
+def make_problem(op, dtype, n, aux=0, lengths=None, k=0, view=None, grid=None, block=None, level=GRID) -> ProblemRef:
+    """Matmul: n = M, aux = N, k = K.  view = (base_shape, ops) for a reduce or
+    scan through that view (grid / block its resource, level its out_level /
+    seg_level)."""
+    return ProblemRef(dict(op=op, dtype=dtype, n=n, aux=aux, lengths=lengths, k=k, view=view, grid=grid,
+                           block=block, level=level))
+
+
+def _problem(prob) -> ProblemRef:
+    return prob if isinstance(prob, ProblemRef) else ProblemRef(prob)
 
 
 def candidate_count(op) -> int:
@@ -552,9 +575,9 @@ def candidate_count(op) -> int:
     return c.value
 
 
-def desc_features(problem: Problem, cand: int):
+def desc_features(problem, cand: int):
     out = (ctypes.c_float * NUM_FEATURES)()
-    _check(lib().desc_features(ctypes.byref(problem), int(cand), out, NUM_FEATURES), "desc_features")
+    _check(lib().desc_features(_problem(problem).ref(), int(cand), out, NUM_FEATURES), "desc_features")
     return list(out)
 
 
@@ -569,12 +592,12 @@ def desc_force_generic(on):
 
 
 def desc_tune_record(problem, cand):
-    _check(lib().desc_tune_record(ctypes.byref(problem), int(cand)), "desc_tune_record")
+    _check(lib().desc_tune_record(_problem(problem).ref(), int(cand)), "desc_tune_record")
 
 
 def desc_tune_lookup(problem):
     c = c_int32(-1)
-    _check(lib().desc_tune_lookup(ctypes.byref(problem), ctypes.byref(c)), "desc_tune_lookup")
+    _check(lib().desc_tune_lookup(_problem(problem).ref(), ctypes.byref(c)), "desc_tune_lookup")
     return c.value
 
 
@@ -628,19 +651,29 @@ class TuneArena:
 
 
 def desc_tune_measure(prob: dict, arena: TuneArena, reps=5, stream=None):
-    p = make_problem(prob["op"], prob["dtype"], prob["n"], prob["aux"], prob.get("lengths"), prob.get("k", 0))
+    p = _problem(prob)
     nc = candidate_count(prob["op"])
     us = (ctypes.c_float * nc)()
-    _check(lib().desc_tune_measure(ctypes.byref(p), ctypes.byref(arena.buffers(prob)), int(reps), _stream(stream),
-                                   us), "desc_tune_measure")
+    _check(lib().desc_tune_measure(p.ref(), ctypes.byref(arena.buffers(prob)), int(reps), _stream(stream), us),
+           "desc_tune_measure")
+    return list(us)
+
+
+def desc_tune_measure_cands(prob: dict, arena: TuneArena, cands, reps=20, stream=None):
+    """Times the listed candidates in interleaved rounds (median of reps)."""
+    p = _problem(prob)
+    arr = (c_int32 * len(cands))(*[int(c) for c in cands])
+    us = (ctypes.c_float * len(cands))()
+    _check(lib().desc_tune_measure_cands(p.ref(), ctypes.byref(arena.buffers(prob)), arr, len(cands), int(reps),
+                                         _stream(stream), us), "desc_tune_measure_cands")
     return list(us)
 
 
 def desc_tune_exhaustive(prob: dict, arena: TuneArena, reps=5, stream=None):
-    p = make_problem(prob["op"], prob["dtype"], prob["n"], prob["aux"], prob.get("lengths"), prob.get("k", 0))
+    p = _problem(prob)
     best = c_int32(-1)
-    _check(lib().desc_tune_exhaustive(ctypes.byref(p), ctypes.byref(arena.buffers(prob)), int(reps),
-                                      _stream(stream), ctypes.byref(best)), "desc_tune_exhaustive")
+    _check(lib().desc_tune_exhaustive(p.ref(), ctypes.byref(arena.buffers(prob)), int(reps), _stream(stream),
+                                      ctypes.byref(best)), "desc_tune_exhaustive")
     return best.value
 
 
@@ -699,58 +732,13 @@ class CostModel:
         """Use this model for desc_tune_predict (kept by reference)."""
         _check(lib().desc_tune_set_model(_ptr(self.p), self.F, self.H), "desc_tune_set_model")
 
-    def predict_problem(self, prob: dict, stream=None):
-        p = make_problem(prob["op"], prob["dtype"], prob["n"], prob["aux"], prob.get("lengths"), prob.get("k", 0))
+    def predict_problem(self, prob, stream=None):
         best = c_int32(-1)
-        _check(lib().desc_tune_predict(ctypes.byref(p), _stream(stream), ctypes.byref(best)), "desc_tune_predict")
+        _check(lib().desc_tune_predict(_problem(prob).ref(), _stream(stream), ctypes.byref(best)),
+               "desc_tune_predict")
         return best.value
 
 
-def feature_rows(prob: dict):
-    p = make_problem(prob["op"], prob["dtype"], prob["n"], prob["aux"], prob.get("lengths"), prob.get("k", 0))
-    return [desc_features(p, c) for c in range(candidate_count(prob["op"]))]
-
-
-def regret_study(train_probs, test_probs, arena, model: CostModel, epochs=300, batch=128, lr=2e-3, reps=5):
-    """Exhaustive timings of every candidate of every problem (training rows
-    and held-out ground truth), GPU training of the cost model on the training
-    rows (log time), and the regret of its picks on the held-out problems:
-    t(pick) / t(best) - 1.  Also the regret of the default candidate 0."""
-    import math
-    import time as _time
-    import torch
-    X, t = [], []
-    t0 = _time.time()
-    for prob in train_probs:
-        us = desc_tune_measure(prob, arena, reps)
-        for c, row in enumerate(feature_rows(prob)):
-            X.append(row)
-            t.append(math.log(max(us[c], 1e-3)))
-    measure_train_s = _time.time() - t0
-    Xt = torch.tensor(X, dtype=torch.float32, device="cuda")
-    tt = torch.tensor(t, dtype=torch.float32, device="cuda")
-    perm = torch.randperm(Xt.shape[0], generator=torch.Generator().manual_seed(0)).cuda()
-    t1 = _time.time()
-    loss = model.train(Xt[perm].contiguous(), tt[perm].contiguous(), epochs, batch, lr)
-    torch.cuda.synchronize()
-    train_s = _time.time() - t1
-    reg_model, reg_default, exact, exh_s, pick_s = [], [], 0, 0.0, 0.0
-    for prob in test_probs:
-        a = _time.time()
-        us = desc_tune_measure(prob, arena, reps)
-        exh_s += _time.time() - a
-        rows = torch.tensor(feature_rows(prob), dtype=torch.float32, device="cuda")
-        a = _time.time()
-        c, _ = model.pick(rows)
-        pick_s += _time.time() - a
-        best = min(us)
-        reg_model.append(us[c] / best - 1.0)
-        reg_default.append(us[0] / best - 1.0)
-        exact += int(us[c] == best)
-    n = len(test_probs)
-    srt = sorted(reg_model)
-    return {"train_rows": len(X), "train_problems": len(train_probs), "test_problems": n, "final_loss": loss,
-            "mean_regret": sum(reg_model) / n, "p90_regret": srt[int(0.9 * (n - 1))],
-            "default_mean_regret": sum(reg_default) / n, "exact_picks": exact / n,
-            "measure_train_s": measure_train_s, "train_s": train_s, "exhaustive_test_s": exh_s,
-            "model_pick_s": pick_s}
+def feature_rows(prob):
+    p = _problem(prob)
+    return [desc_features(p, c) for c in range(candidate_count(p.p.op))]

@@ -5,6 +5,7 @@
 #include <cstdint>
 
 #include "../../include/desc.h"
+#include "candidates.h"
 
 namespace desc {
 

@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(256) copy_affine_kernel(const uint32_t *__rest
 
 }  // namespace
 
-int transpose_candidates() { return 2; }
+int transpose_candidates() { return kNumTransposeCands; }
 
 int32_t launch_transpose(const float *in, float *out, int64_t R, int64_t C, int64_t ld_in,
                          int64_t ld_out, int64_t batch, int64_t bs_in, int64_t bs_out,
@@ -80,7 +80,8 @@ int32_t launch_transpose(const float *in, float *out, int64_t R, int64_t C, int6
   cudaStream_t s = reinterpret_cast<cudaStream_t>(st);
   if (R == 0 || C == 0 || batch == 0) return DESC_OK;
   constexpr int BR = 8;
-  if (cand != 1 && R >= 64 && C >= 64) {   // 64 x 64 tiles: 16 loads in flight per thread
+  const int td = kTransposeTiles[(cand >= 0 && cand < kNumTransposeCands) ? cand : 0];
+  if (td == 64 && R >= 64 && C >= 64) {   // 64 x 64 tiles: 16 loads in flight per thread
     constexpr int TD = 64;
     const int64_t gx = (C + TD - 1) / TD, gy = (R + TD - 1) / TD;
     if (gx >= (int64_t(1) << 31) || gy > 65535 || batch > 65535) return DESC_ERR_UNSUPPORTED;

@@ -11,6 +11,7 @@
 //   pick kernel   one warp per candidate, then the argmin (lowest index on ties)
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "k_common.cuh"
@@ -171,9 +172,13 @@ __global__ void __launch_bounds__(kMaxCand * 32) mlp_pick_kernel(const float *__
   }
 }
 
+// Staging for desc_tune_predict: the candidates' features and the pick.  One
+// copy per device, shared by every caller, so each prediction holds g_pick_mu
+// from the copy in to the copy out.
 __device__ float g_pick_x[kMaxCand * kMaxF];
 __device__ float g_pick_pred[kMaxCand];
 __device__ int g_pick_best;
+std::mutex g_pick_mu;
 
 bool shape_ok(int F, int H) { return F >= 1 && F <= kMaxF && (H == 32 || H == 64); }
 
@@ -183,6 +188,7 @@ int32_t mlp_pick_device(const float *params, int32_t F, int32_t H, const float *
                         desc_stream_t st, int32_t *best) {
   if (!shape_ok(F, H) || ncand < 1 || ncand > kMaxCand) return DESC_ERR_INVALID_ARG;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(st);
+  std::lock_guard<std::mutex> lock(g_pick_mu);
   DESC_CUDA_TRY(cudaMemcpyToSymbolAsync(g_pick_x, Xhost, size_t(ncand) * F * sizeof(float), 0,
                                         cudaMemcpyHostToDevice, s));
   float *px;

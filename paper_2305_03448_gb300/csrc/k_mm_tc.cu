@@ -1029,20 +1029,18 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 }  // namespace
 
-// Schedule candidates: 0 pairs (where the tile rows pair up), wide groups;
-// 1 single CTAs, wide groups; 2 pairs, narrow groups; 3 single, narrow;
-// 4 / 5 pairs with 256 x 512 tiles, wide / narrow groups.
-constexpr int kMmCands = 6;
-constexpr int kMmPairs[kMmCands] = {1, 0, 1, 0, 1, 1};
-constexpr int kMmGroupRows[kMmCands] = {kGroupM, kGroupM, 4, 4, kGroupM, 4};
-constexpr int kMmWidth[kMmCands] = {1, 1, 1, 1, 2, 2};
+// Schedule candidates (candidates.h): 0 pairs (where the tile rows pair up),
+// wide groups; 1 single CTAs, wide groups; 2 pairs, narrow groups; 3 single,
+// narrow; 4 / 5 pairs with 256 x 512 tiles, wide / narrow groups.
+constexpr int kMmCandCount = kNumMmCands;
+static_assert(kMmCands[0].group_rows == kGroupM, "the default candidate uses the wide groups");
 
-int mm_candidates() { return kMmCands; }
+int mm_candidates() { return kMmCandCount; }
 void mm_candidate(int cand, int *pairs, int *group_rows, int *width) {
-  const int c = (cand >= 0 && cand < kMmCands) ? cand : 0;
-  *pairs = kMmPairs[c];
-  *group_rows = kMmGroupRows[c];
-  if (width) *width = kMmWidth[c];
+  const MmCand &c = kMmCands[(cand >= 0 && cand < kMmCandCount) ? cand : 0];
+  *pairs = c.pairs;
+  *group_rows = c.group_rows;
+  if (width) *width = c.width;
 }
 
 int32_t mm_status_take() {
@@ -1153,7 +1151,7 @@ int mm_max_pairs() {
 }
 
 int32_t mm_plan(int64_t M, int64_t N, int64_t K, int nprod, int cand, int max_pairs, MmPlan *pl) {
-  if (!pl || M <= 0 || N <= 0 || K <= 0 || nprod < 1 || cand >= kMmCands) return DESC_ERR_INVALID_ARG;
+  if (!pl || M <= 0 || N <= 0 || K <= 0 || nprod < 1 || cand >= kMmCandCount) return DESC_ERR_INVALID_ARG;
   const int64_t Mp1 = round_up(M, BM), Mp2 = round_up(M, 2 * BM), Np = round_up(N, BN), Kp = round_up(K, BK);
   if (Mp2 / BM > 65535 || Np / BN > (int64_t(1) << 30) || Kp > (int64_t(1) << 30)) return DESC_ERR_UNSUPPORTED;
   // Untuned: 256 x 512 pair tiles where they fill at least half of the

@@ -29,20 +29,12 @@ constexpr int kThreads = 256;
 constexpr int64_t kSmallRun = 16;          // <= this: one thread per output
 constexpr int64_t kWarpRun = 4096;         // <= this: one warp per output
 
-// Schedule candidates of the chunked kernel: vectors in flight per thread,
-// the CTA count the chunking aims at (1216 = 8 CTAs on each of 152 SMs) and
-// the load path (0: evict-first streaming loads, 1: read-only path without
-// L1 allocation).
-struct ReduceCand {
-  int unroll;
-  int64_t target_ctas;
-  int nc;
-};
-constexpr ReduceCand kCands[] = {{8, 1216, 0}, {4, 1216, 0}, {8, 608, 0}, {4, 2432, 0},
-                                 {8, 2432, 0}, {8, 304, 0},  {4, 2432, 1}, {8, 1216, 1}};
-constexpr int kNumCands = sizeof(kCands) / sizeof(kCands[0]);
+// Schedule candidates of the chunked kernel (candidates.h).
+using Cand = ReduceCand;
+constexpr const Cand *kCands = kReduceCands;
+constexpr int kNumCands = kNumReduceCands;
 
-int64_t chunks_for(int64_t len, int64_t nout, const ReduceCand &c) {
+int64_t chunks_for(int64_t len, int64_t nout, const Cand &c) {
   const int64_t per_cta_min = int64_t(kThreads) * 4 * c.unroll;
   int64_t by_fill = (c.target_ctas + nout - 1) / std::max<int64_t>(nout, 1);
   int64_t by_len = (len + per_cta_min - 1) / per_cta_min;
@@ -52,7 +44,7 @@ int64_t chunks_for(int64_t len, int64_t nout, const ReduceCand &c) {
 // The most chunks any candidate uses (sizes the partials).
 int64_t max_chunks(int64_t len, int64_t nout) {
   int64_t m = 1;
-  for (const ReduceCand &c : kCands) m = std::max(m, chunks_for(len, nout, c));
+  for (int i = 0; i < kNumCands; ++i) m = std::max(m, chunks_for(len, nout, kCands[i]));
   return m;
 }
 
@@ -324,7 +316,7 @@ int32_t run_runs(const T *in, int64_t start, int64_t seg_stride, int64_t len, in
     const int64_t ctas = std::min<int64_t>((nout * 32 + kThreads - 1) / kThreads, int64_t(1) << 20);
     reduce_short_kernel<A, T, 32><<<(unsigned)ctas, kThreads, 0, s>>>(in, start, seg_stride, len, nout, out);
   } else {
-    const ReduceCand &cd = kCands[(cand >= 0 && cand < kNumCands) ? cand : 0];
+    const Cand &cd = kCands[(cand >= 0 && cand < kNumCands) ? cand : 0];
     const int64_t chunks = chunks_for(len, nout, cd);
     uint2 *partials = nullptr;
     unsigned *counters = nullptr;
@@ -476,7 +468,7 @@ int32_t launch_split_reduce_transpose(int32_t dtype, const void *in, int64_t sta
                                       const float *tin, float *tout, int64_t R, int64_t C, desc_stream_t st) {
   cudaStream_t s = reinterpret_cast<cudaStream_t>(st);
   if (len <= kWarpRun) return DESC_ERR_UNSUPPORTED;   // the chunked schedule only
-  const ReduceCand &cd = kCands[0];
+  const Cand &cd = kCands[0];
   const int64_t chunks = chunks_for(len, nout, cd);
   uint2 *partials = nullptr;
   unsigned *counters = nullptr;

@@ -657,10 +657,9 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 constexpr int kWsTile = kSub;   // workspace is sized for the smallest tile
 
-// Schedule candidates: sub-tiles per tile (tile = 4096 x SUB elements).
-constexpr int kSubCands[] = {4, 2, 1};
-static_assert(kSub * kSubCands[0] == kScanNoallocTile, "the no-alloc scan runs candidate 0");
-constexpr int kNumSubCands = 3;
+// Schedule candidates: sub-tiles per tile (tile = 4096 x SUB elements; candidates.h).
+static_assert(kSub == kScanSubTile, "the candidate table counts sub-tiles of this size");
+static_assert(kSub * kScanSubCands[0] == kScanNoallocTile, "the no-alloc scan runs candidate 0");
 
 template <class T, class O, int MODE, int SUB, bool EXCL = false>
 int32_t run_scan_t(const T *in, T *out, const ScanArgs &a, void *ws, size_t ws_bytes, cudaStream_t s) {
@@ -700,7 +699,7 @@ int32_t run_scan(const T *in, T *out, const ScanArgs &a, void *ws, size_t ws_byt
   }
   if (flags & DESC_MAX) return run_scan_t<T, ExtOp<T, true>, MODE, 4>(in, out, a, ws, ws_bytes, s);
   if (flags & DESC_MIN) return run_scan_t<T, ExtOp<T, false>, MODE, 4>(in, out, a, ws, ws_bytes, s);
-  switch (kSubCands[(cand >= 0 && cand < kNumSubCands) ? cand : 0]) {
+  switch (kScanSubCands[(cand >= 0 && cand < kNumScanCands) ? cand : 0]) {
     case 1: return run_scan_t<T, SumOp<T>, MODE, 1>(in, out, a, ws, ws_bytes, s);
     case 2: return run_scan_t<T, SumOp<T>, MODE, 2>(in, out, a, ws, ws_bytes, s);
     default: return run_scan_t<T, SumOp<T>, MODE, 4>(in, out, a, ws, ws_bytes, s);
@@ -721,7 +720,7 @@ size_t scan_contig_ws(int32_t /*dtype*/, int64_t n) {
   return align256(sizeof(ScanWs)) + size_t(ntiles) * sizeof(TileState);
 }
 
-int scan_candidates() { return kNumSubCands; }
+int scan_candidates() { return kNumScanCands; }
 
 int32_t launch_scan_contig(int32_t dtype, const void *in, void *out, int64_t n, int64_t period,
                            int32_t flags, void *ws, size_t ws_bytes, desc_stream_t st, int cand) {

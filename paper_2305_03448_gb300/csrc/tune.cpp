@@ -8,6 +8,7 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <string>
 #include <tuple>
 #include <vector>
 
@@ -23,7 +24,9 @@ using namespace desc;
 namespace {
 
 constexpr int kOps = 5;
-using Key = std::tuple<int32_t, int32_t, int32_t, int32_t>;
+constexpr int kMaxDevices = 64;
+// (GPU model, op, dtype, floor(log2 n), floor(log2(aux + 1)))
+using Key = std::tuple<std::string, int32_t, int32_t, int32_t, int32_t>;
 
 std::mutex g_mu;
 std::map<Key, int32_t> g_table;
@@ -40,8 +43,35 @@ int32_t ilog2(int64_t x) {
   return r;
 }
 
-Key key_of(int32_t op, int32_t dtype, int64_t n, int64_t aux) {
-  return Key(op, dtype, ilog2(std::max<int64_t>(n, 1)), ilog2(aux + 1));
+// The GPU model of the current device, spaces replaced by '_' ("none" without
+// a device), looked up once per device.
+std::string device_model() {
+  static std::mutex mu;
+  static std::string names[kMaxDevices];
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    (void)cudaGetLastError();
+    return "none";
+  }
+  std::lock_guard<std::mutex> lock(mu);
+  if (names[dev].empty()) {
+    cudaDeviceProp prop;
+    std::string s = "none";
+    if (cudaGetDeviceProperties(&prop, dev) == cudaSuccess) {
+      s = prop.name;
+      for (char &c : s)
+        if (c == ' ' || c == '\t' || c == '\n') c = '_';
+      if (s.empty()) s = "unnamed";
+    } else {
+      (void)cudaGetLastError();
+    }
+    names[dev] = s;
+  }
+  return names[dev];
+}
+
+Key key_of(const std::string &dev, int32_t op, int32_t dtype, int64_t n, int64_t aux) {
+  return Key(dev, op, dtype, ilog2(std::max<int64_t>(n, 1)), ilog2(aux + 1));
 }
 
 int ncand(int32_t op) {
@@ -56,7 +86,136 @@ int ncand(int32_t op) {
 }
 
 bool problem_ok(const desc_problem *p) {
-  return p && p->op >= 0 && p->op < kOps && dtype_size(p->dtype) && p->n >= 0 && p->aux >= 0 && p->k >= 0;
+  if (!p || p->op < 0 || p->op >= kOps || !dtype_size(p->dtype) || p->n < 0 || p->aux < 0 || p->k < 0) return false;
+  if (p->view && p->op != DESC_OP_REDUCE && p->op != DESC_OP_SCAN) return false;
+  if (p->view && (p->level < DESC_LEVEL_GRID || p->level > DESC_LEVEL_THREAD)) return false;
+  return true;
+}
+
+// What a problem's call looks like after lowering: the (n, aux) the op call
+// passes to its schedule lookup, the (n, aux) the features describe, and the
+// view composition.
+struct Shape {
+  int64_t key_n, key_aux;      // bucket of the tuned table
+  int64_t n, aux;              // features [7..9]
+  int counts[5];               // group, split, transpose, reverse, select views
+  int depth;                   // deepest map nesting
+  int hand;                    // the op's hand-indexed kernel applies
+  int dims;                    // lowered dims after merging neighbours
+  int64_t base_elems;          // elements of the view's base array
+};
+
+// Dims of a lowered map once extent-1 dims are dropped and neighbours that
+// its strides walk as one are merged.
+int merged_dims(const desc_lowered &L) {
+  int m = 0;
+  int64_t pe = 0, ps = 0;
+  for (int i = 0; i < L.ndims; ++i) {
+    if (L.extent[i] == 1) continue;
+    if (m > 0 && ps == L.stride[i] * L.extent[i]) {
+      pe *= L.extent[i];
+      ps = L.stride[i];
+    } else {
+      ++m;
+      pe = L.extent[i];
+      ps = L.stride[i];
+    }
+  }
+  (void)pe;
+  return m;
+}
+
+void count_view(const desc_view &v, Shape *s) {
+  for (int i = 0; i < v.nops && i < DESC_MAX_OPS; ++i) {
+    const desc_view_op &o = v.ops[i];
+    switch (o.kind) {
+      case DESC_V_GROUP: ++s->counts[0]; break;
+      case DESC_V_SPLIT_FST:
+      case DESC_V_SPLIT_SND: ++s->counts[1]; break;
+      case DESC_V_TRANSPOSE: ++s->counts[2]; break;
+      case DESC_V_REVERSE: ++s->counts[3]; break;
+      case DESC_V_SELECT: ++s->counts[4]; break;
+      default: break;
+    }
+    s->depth = std::max(s->depth, (int)o.depth);
+  }
+}
+
+// The plain form's view (see desc_problem), for reduce and scan.
+void plain_view(const desc_problem *p, desc_view *v, desc_exec *ex, bool *has_ex) {
+  std::memset(v, 0, sizeof(*v));
+  v->rank = 1;
+  v->shape[0] = p->n;
+  *has_ex = false;
+  if (p->op == DESC_OP_REDUCE && p->aux > 1) {
+    v->nops = 2;
+    v->ops[0].kind = DESC_V_GROUP;
+    v->ops[0].k = p->aux ? p->n / p->aux : 0;
+    v->ops[1].kind = DESC_V_SELECT;
+    v->ops[1].level = DESC_LEVEL_BLOCK;
+    v->ops[1].dim = DESC_DIM_X;
+    *ex = desc_exec{{p->aux, 1, 1}, {1, 1, 1}};
+    *has_ex = true;
+  }
+}
+
+int32_t shape_of(const desc_problem *p, Shape *s) {
+  std::memset(s, 0, sizeof(*s));
+  s->key_n = s->n = p->n;
+  s->key_aux = s->aux = p->aux;
+  s->hand = 1;
+  s->dims = 1;
+  s->base_elems = p->n;
+  if (p->op == DESC_OP_TRANSPOSE) {
+    s->counts[2] = 1;
+    s->dims = 2;
+    return DESC_OK;
+  }
+  if (p->op != DESC_OP_REDUCE && p->op != DESC_OP_SCAN) return DESC_OK;
+  desc_view pv;
+  desc_exec pex;
+  bool has_ex = false;
+  const desc_view *v = p->view;
+  const desc_exec *ex = p->ex;
+  int32_t level = p->level;
+  if (!v) {
+    if (p->op == DESC_OP_REDUCE && p->aux > 1 && p->n % p->aux) return DESC_ERR_SHAPE;
+    plain_view(p, &pv, &pex, &has_ex);
+    v = &pv;
+    ex = has_ex ? &pex : nullptr;
+    level = has_ex ? DESC_LEVEL_BLOCK : DESC_LEVEL_GRID;
+  }
+  count_view(*v, s);
+  desc_lowered L;
+  const int32_t r = desc_lower_view(v, ex, &L);
+  if (r != DESC_OK) return r;
+  const Plan pl = split_plan(L, level);
+  s->n = s->key_n = pl.n_keep * pl.n_rest;
+  s->aux = pl.n_keep > 1 ? pl.n_keep : 0;
+  s->base_elems = L.base_elems;
+  s->dims = merged_dims(L);
+  int64_t start0 = 0, seg = 0;
+  if (p->op == DESC_OP_REDUCE) {
+    s->key_aux = s->aux;
+    s->hand = rest_contiguous(pl, true, &start0, &seg) ? 1 : 0;
+  } else {
+    s->key_aux = 0;                                    // desc_scan's lookup ignores segments
+    s->hand = (rest_contiguous(pl, false, &start0, &seg) && (pl.n_keep <= 1 || seg == pl.n_rest)) ? 1 : 0;
+  }
+  return DESC_OK;
+}
+
+// Fraction of segments per floor(log2 len) bucket of width 3, empty
+// segments in the first bucket.
+void length_histogram(const int64_t *len, int64_t count, float *h) {
+  for (int i = 0; i < 8; ++i) h[i] = 0.f;
+  if (!len || count <= 0) return;
+  std::vector<int64_t> c(8, 0);
+  for (int64_t i = 0; i < count; ++i) {
+    const int b = len[i] <= 0 ? 0 : std::min(ilog2(len[i]) / 3, 7);
+    ++c[size_t(b)];
+  }
+  for (int i = 0; i < 8; ++i) h[i] = float(double(c[size_t(i)]) / double(count));
 }
 
 }  // namespace
@@ -65,9 +224,13 @@ namespace desc {
 int32_t schedule_for(int32_t op, int32_t dtype, int64_t n, int64_t aux) {
   if (op < 0 || op >= kOps) return -1;
   if (g_force[op] >= 0) return g_force[op];
+  {
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (g_table.empty()) return -1;
+  }
+  const std::string dev = device_model();
   std::lock_guard<std::mutex> lock(g_mu);
-  if (g_table.empty()) return -1;
-  auto it = g_table.find(key_of(op, dtype, n, aux));
+  auto it = g_table.find(key_of(dev, op, dtype, n, aux));
   return it == g_table.end() ? -1 : it->second;
 }
 }  // namespace desc
@@ -87,71 +250,74 @@ extern "C" int32_t desc_force_candidate(int32_t op, int32_t cand) {
 extern "C" int32_t desc_features(const desc_problem *p, int32_t cand, float *out, int32_t nout) {
   if (!problem_ok(p) || !out || nout < DESC_NUM_FEATURES || cand < 0 || cand >= ncand(p->op))
     return DESC_ERR_INVALID_ARG;
-  // [0, 5) op, [5, 7) dtype, [7] log2 n, [8] log2 (aux + 1), [9] log2 (n / (aux + 1) + 1),
-  // [10, 18) segment histogram, [18] log2 tile, [19] vectors, [20] log2 CTAs or group,
-  // [21, 29) candidate, [29] load path, [30] log2 (K + 1), [31] CTA pairs
+  Shape sh;
+  const int32_t r = shape_of(p, &sh);
+  if (r != DESC_OK) return r;
   for (int i = 0; i < DESC_NUM_FEATURES; ++i) out[i] = 0.f;
   auto lg = [](double x) { return (float)std::log2(std::max(x, 1.0)); };
   out[p->op] = 1.f;
   out[5 + (p->dtype == DESC_F32 ? 1 : 0)] = 1.f;
-  out[7] = lg((double)p->n) / 32.f;
-  out[8] = lg((double)p->aux + 1.0) / 32.f;
-  out[9] = lg((double)p->n / ((double)p->aux + 1.0) + 1.0) / 32.f;
-  if (p->op == DESC_OP_SEGMENTED)
-    for (int i = 0; i < 8; ++i) out[10 + i] = p->seg_hist[i];
-  static const int unroll[8] = {8, 4, 8, 4, 8, 8, 4, 8};
-  static const int ctas[8] = {1216, 1216, 608, 2432, 2432, 304, 2432, 1216};
-  static const int nc[8] = {0, 0, 0, 0, 0, 0, 1, 1};
-  static const int subs[3] = {4, 2, 1};
+  out[7] = lg((double)sh.n) / 32.f;
+  out[8] = lg((double)sh.aux + 1.0) / 32.f;
+  out[9] = lg((double)sh.n / ((double)sh.aux + 1.0) + 1.0) / 32.f;
+  if (p->op == DESC_OP_SEGMENTED) length_histogram(p->seg_lengths, p->aux, out + 10);
   if (p->op == DESC_OP_REDUCE) {
-    out[18] = lg(256.0 * 4 * unroll[cand]) / 32.f;
-    out[19] = unroll[cand] / 16.f;
-    out[20] = lg((double)ctas[cand]) / 16.f;
-    out[29] = (float)nc[cand];
+    const ReduceCand &c = kReduceCands[cand];
+    out[18] = lg(256.0 * 4 * c.unroll) / 32.f;
+    out[19] = c.unroll / 16.f;
+    out[20] = lg((double)c.target_ctas) / 16.f;
+    out[29] = (float)c.nc;
   } else if (p->op == DESC_OP_TRANSPOSE) {
-    const double td = cand == 0 ? 64 : 32;
+    const double td = kTransposeTiles[cand];
     out[18] = lg(td * td) / 32.f;
   } else if (p->op == DESC_OP_MATMUL) {
-    int pairs = 0, group = 0, width = 1;
-    mm_candidate(cand, &pairs, &group, &width);
-    out[18] = lg(pairs ? 256.0 * 256.0 * width : 128.0 * 256.0) / 32.f;
-    out[20] = lg((double)group) / 16.f;
+    const MmCand &c = kMmCands[cand];
+    out[18] = lg(c.pairs ? 256.0 * 256.0 * c.width : 128.0 * 256.0) / 32.f;
+    out[20] = lg((double)c.group_rows) / 16.f;
     out[30] = lg((double)p->k + 1.0) / 32.f;
-    out[31] = (float)pairs;
+    out[31] = (float)c.pairs;
   } else {
-    out[18] = lg(4096.0 * subs[cand]) / 32.f;
+    out[18] = lg(double(kScanSubTile) * kScanSubCands[cand]) / 32.f;
     out[19] = 16.f / 16.f;
   }
   out[21 + cand] = 1.f;
+  for (int i = 0; i < 5; ++i) out[32 + i] = sh.counts[i] / 8.f;
+  out[37] = sh.depth / 4.f;
+  out[38] = (float)sh.hand;
+  out[39] = sh.dims / 8.f;
   return DESC_OK;
 }
 
 namespace {
 
-// One launch of the problem's canonical call with the current forced candidate.
+// One launch of the problem's call with the current forced candidate.
 int32_t run_problem(const desc_problem *p, const desc_tune_buffers *b, desc_stream_t s) {
+  if (p->view) {
+    Shape sh;
+    int32_t r = shape_of(p, &sh);
+    if (r != DESC_OK) return r;
+    const size_t nb = size_t(sh.base_elems) * 4;
+    if (p->op == DESC_OP_REDUCE) {
+      const size_t ob = size_t(std::max<int64_t>(sh.aux, 1)) * 4;
+      return desc_reduce(p->view, p->ex, p->level, p->dtype, b->in, nb, b->out, ob, 0, b->ws, b->ws_bytes, s);
+    }
+    return desc_scan(p->view, p->ex, p->level, p->dtype, b->in, nb, b->out, nb, 0, b->ws, b->ws_bytes, s);
+  }
   desc_view v;
-  std::memset(&v, 0, sizeof(v));
-  v.rank = 1;
-  v.shape[0] = p->n;
+  desc_exec ex;
+  bool has_ex = false;
   const size_t nb = size_t(p->n) * 4;
   switch (p->op) {
     case DESC_OP_REDUCE: {
-      if (p->aux > 1) {
-        if (p->n % p->aux) return DESC_ERR_SHAPE;
-        v.nops = 2;
-        v.ops[0].kind = DESC_V_GROUP;
-        v.ops[0].k = p->n / p->aux;
-        v.ops[1].kind = DESC_V_SELECT;
-        v.ops[1].level = DESC_LEVEL_BLOCK;
-        v.ops[1].dim = DESC_DIM_X;
-        desc_exec ex = {{p->aux, 1, 1}, {1, 1, 1}};
+      if (p->aux > 1 && p->n % p->aux) return DESC_ERR_SHAPE;
+      plain_view(p, &v, &ex, &has_ex);
+      if (has_ex)
         return desc_reduce(&v, &ex, DESC_LEVEL_BLOCK, p->dtype, b->in, nb, b->out, size_t(p->aux) * 4, 0, b->ws,
                            b->ws_bytes, s);
-      }
       return desc_reduce(&v, nullptr, DESC_LEVEL_GRID, p->dtype, b->in, nb, b->out, 4, 0, b->ws, b->ws_bytes, s);
     }
     case DESC_OP_SCAN:
+      plain_view(p, &v, &ex, &has_ex);
       return desc_scan(&v, nullptr, DESC_LEVEL_GRID, p->dtype, b->in, nb, b->out, nb, 0, b->ws, b->ws_bytes, s);
     case DESC_OP_TRANSPOSE: {
       if (p->aux <= 0 || p->n % p->aux) return DESC_ERR_SHAPE;
@@ -180,49 +346,94 @@ int32_t run_problem(const desc_problem *p, const desc_tune_buffers *b, desc_stre
   }
 }
 
+// Medians of `reps` timed launches of each listed candidate; rounds visit
+// every candidate once (with a warm-up launch before each candidate's first
+// round).
+int32_t measure(const desc_problem *p, const desc_tune_buffers *b, const int32_t *cands, int nc, int reps,
+                desc_stream_t s, float *us) {
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(s);
+  std::vector<cudaEvent_t> ev(size_t(2 * nc));
+  for (auto &e : ev)
+    if (cudaEventCreate(&e) != cudaSuccess) return DESC_ERR_CUDA;
+  const int32_t saved = g_force[p->op];
+  int32_t r = DESC_OK;
+  std::vector<std::vector<float>> t(static_cast<size_t>(nc));
+  for (int c = 0; c < nc && r == DESC_OK; ++c) {   // warm-up
+    g_force[p->op] = cands[c];
+    r = run_problem(p, b, s);
+  }
+  for (int i = 0; i < reps && r == DESC_OK; ++i) {
+    for (int c = 0; c < nc && r == DESC_OK; ++c) {
+      g_force[p->op] = cands[c];
+      cudaEventRecord(ev[size_t(2 * c)], st);
+      r = run_problem(p, b, s);
+      cudaEventRecord(ev[size_t(2 * c + 1)], st);
+    }
+    if (r != DESC_OK) break;
+    if (cudaEventSynchronize(ev[size_t(2 * nc - 1)]) != cudaSuccess) { r = DESC_ERR_CUDA; break; }
+    for (int c = 0; c < nc; ++c) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev[size_t(2 * c)], ev[size_t(2 * c + 1)]);
+      t[size_t(c)].push_back(ms);
+    }
+  }
+  g_force[p->op] = saved;
+  for (auto &e : ev) cudaEventDestroy(e);
+  if (r != DESC_OK) return r;
+  for (int c = 0; c < nc; ++c) {
+    std::vector<float> &v = t[size_t(c)];
+    std::nth_element(v.begin(), v.begin() + reps / 2, v.end());
+    us[c] = v[size_t(reps / 2)] * 1000.f;
+  }
+  return DESC_OK;
+}
+
 }  // namespace
 
 extern "C" int32_t desc_tune_measure(const desc_problem *p, const desc_tune_buffers *b, int32_t reps,
                                      desc_stream_t s, float *us) {
   if (!problem_ok(p) || !b || !us || reps < 1) return DESC_ERR_INVALID_ARG;
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(s);
   const int nc = ncand(p->op);
-  std::vector<cudaEvent_t> ev(size_t(reps) + 1);
-  for (auto &e : ev)
-    if (cudaEventCreate(&e) != cudaSuccess) return DESC_ERR_CUDA;
-  const int32_t saved = g_force[p->op];
-  int32_t r = DESC_OK;
-  for (int c = 0; c < nc && r == DESC_OK; ++c) {
-    g_force[p->op] = c;
-    if ((r = run_problem(p, b, s)) != DESC_OK) break;   // warm-up
-    cudaEventRecord(ev[0], st);
-    for (int i = 0; i < reps && r == DESC_OK; ++i) {
-      r = run_problem(p, b, s);
-      cudaEventRecord(ev[size_t(i) + 1], st);
-    }
-    if (r != DESC_OK) break;
-    if (cudaEventSynchronize(ev[size_t(reps)]) != cudaSuccess) { r = DESC_ERR_CUDA; break; }
-    std::vector<float> t(reps);
-    for (int i = 0; i < reps; ++i) cudaEventElapsedTime(&t[i], ev[size_t(i)], ev[size_t(i) + 1]);
-    std::nth_element(t.begin(), t.begin() + reps / 2, t.end());
-    us[c] = t[size_t(reps / 2)] * 1000.f;
-  }
-  g_force[p->op] = saved;
-  for (auto &e : ev) cudaEventDestroy(e);
-  return r;
+  std::vector<int32_t> all(static_cast<size_t>(nc));
+  for (int c = 0; c < nc; ++c) all[size_t(c)] = c;
+  return measure(p, b, all.data(), nc, reps, s, us);
 }
+
+extern "C" int32_t desc_tune_measure_cands(const desc_problem *p, const desc_tune_buffers *b, const int32_t *cands,
+                                           int32_t ncands, int32_t reps, desc_stream_t s, float *us) {
+  if (!problem_ok(p) || !b || !us || !cands || ncands < 1 || reps < 1) return DESC_ERR_INVALID_ARG;
+  for (int i = 0; i < ncands; ++i)
+    if (cands[i] < 0 || cands[i] >= ncand(p->op)) return DESC_ERR_INVALID_ARG;
+  return measure(p, b, cands, ncands, reps, s, us);
+}
+
+namespace {
+int32_t problem_key(const desc_problem *p, Key *k) {
+  Shape sh;
+  const int32_t r = shape_of(p, &sh);
+  if (r != DESC_OK) return r;
+  *k = key_of(device_model(), p->op, p->dtype, sh.key_n, sh.key_aux);
+  return DESC_OK;
+}
+}  // namespace
 
 extern "C" int32_t desc_tune_record(const desc_problem *p, int32_t cand) {
   if (!problem_ok(p) || cand < 0 || cand >= ncand(p->op)) return DESC_ERR_INVALID_ARG;
+  Key k;
+  const int32_t r = problem_key(p, &k);
+  if (r != DESC_OK) return r;
   std::lock_guard<std::mutex> lock(g_mu);
-  g_table[key_of(p->op, p->dtype, p->n, p->aux)] = cand;
+  g_table[k] = cand;
   return DESC_OK;
 }
 
 extern "C" int32_t desc_tune_lookup(const desc_problem *p, int32_t *cand) {
   if (!problem_ok(p) || !cand) return DESC_ERR_INVALID_ARG;
+  Key k;
+  const int32_t r = problem_key(p, &k);
+  if (r != DESC_OK) return r;
   std::lock_guard<std::mutex> lock(g_mu);
-  auto it = g_table.find(key_of(p->op, p->dtype, p->n, p->aux));
+  auto it = g_table.find(k);
   *cand = it == g_table.end() ? -1 : it->second;
   return DESC_OK;
 }
@@ -230,7 +441,8 @@ extern "C" int32_t desc_tune_lookup(const desc_problem *p, int32_t *cand) {
 extern "C" int32_t desc_tune_exhaustive(const desc_problem *p, const desc_tune_buffers *b, int32_t reps,
                                         desc_stream_t s, int32_t *best) {
   if (!best) return DESC_ERR_INVALID_ARG;
-  float us[8];
+  float us[16];
+  if (!problem_ok(p) || ncand(p->op) > 16) return DESC_ERR_INVALID_ARG;
   const int32_t r = desc_tune_measure(p, b, reps, s, us);
   if (r != DESC_OK) return r;
   int c = 0;
@@ -251,10 +463,10 @@ extern "C" int32_t desc_tune_save(const char *path) {
   std::lock_guard<std::mutex> lock(g_mu);
   FILE *f = std::fopen(path, "w");
   if (!f) return DESC_ERR_INVALID_ARG;
-  std::fprintf(f, "# libdesc schedule table: op dtype log2_n log2_aux1 candidate\n");
+  std::fprintf(f, "# libdesc schedule table: gpu_model op dtype log2_n log2_aux1 candidate\n");
   for (auto &kv : g_table)
-    std::fprintf(f, "%d %d %d %d %d\n", std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first),
-                 std::get<3>(kv.first), kv.second);
+    std::fprintf(f, "%s %d %d %d %d %d\n", std::get<0>(kv.first).c_str(), std::get<1>(kv.first),
+                 std::get<2>(kv.first), std::get<3>(kv.first), std::get<4>(kv.first), kv.second);
   std::fclose(f);
   return DESC_OK;
 }
@@ -264,17 +476,18 @@ extern "C" int32_t desc_tune_load(const char *path) {
   FILE *f = std::fopen(path, "r");
   if (!f) return DESC_ERR_INVALID_ARG;
   std::map<Key, int32_t> t;
-  char line[256];
+  char line[512];
   int32_t r = DESC_OK;
   while (std::fgets(line, sizeof(line), f)) {
     if (line[0] == '#' || line[0] == '\n') continue;
+    char dev[256];
     int op, dt, ln, la, c;
-    if (std::sscanf(line, "%d %d %d %d %d", &op, &dt, &ln, &la, &c) != 5 || op < 0 || op >= kOps || c < 0 ||
-        c >= ncand(op)) {
+    if (std::sscanf(line, "%255s %d %d %d %d %d", dev, &op, &dt, &ln, &la, &c) != 6 || op < 0 || op >= kOps ||
+        c < 0 || c >= ncand(op)) {
       r = DESC_ERR_INVALID_ARG;
       break;
     }
-    t[Key(op, dt, ln, la)] = c;
+    t[Key(std::string(dev), op, dt, ln, la)] = c;
   }
   std::fclose(f);
   if (r != DESC_OK) return r;

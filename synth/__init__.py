@@ -137,42 +137,110 @@ def mlp_init(F: int, H: int, seed: int) -> torch.Tensor:
     return torch.cat([u[0], z, u[1], z, u[2], torch.zeros(1, dtype=torch.float64)]).to(torch.float32)
 
 
-def tune_problems(count: int, seed: int) -> list:
+def _key_log2(n: int) -> int:
+    return max(int(n), 1).bit_length() - 1
+
+
+def tune_problems(count: int, seed: int, part: str = "all") -> list:
     """Seeded shapes for schedule tuning, drawn from the benchmark families:
-    reduce (full or per-group, log2 n in [10, 27]), scan (log2 n in [10, 27]),
-    transpose (rows, cols powers of two, 2^10 <= rows * cols <= 2^26),
-    segmented (10..5000 segments, log-uniform lengths up to 2^8..2^16),
-    matmul (M, N, K each 2^8..2^12, FP32 operands; n = M, aux = N, k = K).
-    Each item: dict(op, dtype, n, aux, lengths, k) with op 0..4 as in desc_op."""
-    u = _unit_f64(splitmix64(stream_key(seed, 1234), 0, 8 * count)).reshape(count, 8).tolist()
+      reduce     log2 n in [10, 27]: the whole array, per-group outputs
+                 (group(k)[[block]]), the hierarchical view
+                 group(1024)[[block]].group(32)[[warp]][[thread]] reduced per
+                 grid or per block, a reversed array per group, or the columns
+                 of a row-major matrix (transpose view, one output per column)
+      scan       log2 n in [10, 27]: the whole array, per-group segments
+                 (group(k)[[block]]), a reversed array, or a split-off tail
+      transpose  rows, cols powers of two, 2^10 <= rows * cols <= 2^26
+      segmented  10..5000 segments, log-uniform lengths up to 2^8..2^16
+      matmul     M, N, K multiples of 128 in [256, 4096], log-uniform
+    Sizes are drawn continuously (not only powers of two).  part "even" keeps
+    the problems whose floor(log2 n) is even (n: the points reduced or
+    scanned, the matrix elements, the segmented elements, or M), "odd" the
+    others, so that the two parts share no size bucket; "all" keeps all.
+    Each item: dict(op, dtype, n, aux, lengths, k, view, grid, block, level)
+    with op 0..4 as in desc_op; view = (base_shape, ops) or None."""
+    key = stream_key(seed, 1234)
     out = []
-    for i in range(count):
-        a = u[i]
+    i = 0
+    GRID_, BLOCK_, WARP_, THREAD_ = 0, 1, 2, 3
+    while len(out) < count:
+        a = _unit_f64(splitmix64(key, 8 * i, 8)).tolist()
+        i += 1
         op = min(int(a[0] * 5), 4)
+        pr = dict(op=op, dtype=1, n=0, aux=0, lengths=None, k=0, view=None, grid=None, block=None, level=GRID_)
         if op == 4:
-            M, N, K = (1 << (8 + int(a[j] * 5)) for j in (2, 3, 4))
-            out.append(dict(op=4, dtype=1, n=M, aux=N, lengths=None, k=K))
-            continue
-        dtype = 0 if a[1] < 0.5 else 1
-        if op == 0:
-            ln = 10 + int(a[2] * 18)
-            n = 1 << ln
-            aux = 0 if a[3] < 0.5 else 1 << int(a[4] * min(ln - 2, 14))
-            out.append(dict(op=0, dtype=dtype, n=n, aux=aux, lengths=None))
-        elif op == 1:
-            n = int(2 ** (10 + a[2] * 17.0))
-            out.append(dict(op=1, dtype=dtype, n=n, aux=0, lengths=None))
+            M, N, K = (128 * max(2, int(2 ** (8 + a[j] * 4.0) / 128)) for j in (2, 3, 4))
+            pr.update(n=M, aux=N, k=K)
+            kn = M
         elif op == 2:
+            dtype = 1
             lr = 5 + int(a[2] * 10)
             lc = 5 + int(a[3] * 10)
             while lr + lc > 26:
                 lr, lc = lr - 1, lc - 1
             while lr + lc < 10:
                 lr, lc = lr + 1, lc + 1
-            out.append(dict(op=2, dtype=1, n=(1 << lr) * (1 << lc), aux=1 << lr, lengths=None))
-        else:
+            pr.update(n=(1 << lr) * (1 << lc), aux=1 << lr)
+            kn = pr["n"]
+        elif op == 3:
+            pr["dtype"] = 0 if a[1] < 0.5 else 1
             nseg = 10 + int(a[2] * 4990)
             mx = 1 << (8 + int(a[3] * 9))
             L = loguniform_lengths(nseg, seed=seed * 100003 + i, max_len=mx)
-            out.append(dict(op=3, dtype=dtype, n=int(L.sum()), aux=nseg, lengths=L))
+            pr.update(n=int(L.sum()), aux=nseg, lengths=L)
+            kn = pr["n"]
+        elif op == 0:
+            pr["dtype"] = 0 if a[1] < 0.5 else 1
+            n = 1024 * max(1, int(2 ** (a[2] * 17.0)))        # 2^10 .. 2^27, a multiple of 1024
+            fam = min(int(a[3] * 5), 4)
+            kn = n
+            if fam == 0:
+                pr.update(n=n)
+            elif fam == 1:
+                g = 1 << int(a[4] * min(_key_log2(n) - 2, 14))
+                while n % g:
+                    g //= 2
+                pr.update(n=n, aux=g if g > 1 else 0)
+            elif fam == 2:
+                lvl = GRID_ if a[4] < 0.5 else BLOCK_
+                ops = [("group", 1024, 0), ("select", BLOCK_, 0), ("group", 32, 0), ("select", WARP_, 0),
+                       ("select", THREAD_, 0)]
+                pr.update(n=n, view=([n], ops), grid=(n // 1024, 1, 1), block=(1024, 1, 1), level=lvl)
+            elif fam == 3:
+                k = 1 << (4 + int(a[4] * 10))
+                while n % k:
+                    k //= 2
+                ops = [("reverse", 0), ("group", k, 0), ("select", BLOCK_, 0)]
+                pr.update(n=n, view=([n], ops), grid=(n // k, 1, 1), block=(1, 1, 1), level=BLOCK_)
+            else:
+                C = 1 << (4 + int(a[4] * 8))
+                while n % C:
+                    C //= 2
+                R = n // C
+                ops = [("transpose", 0), ("select", BLOCK_, 0)]
+                pr.update(n=n, view=([R, C], ops), grid=(C, 1, 1), block=(1, 1, 1), level=BLOCK_)
+        else:
+            pr["dtype"] = 0 if a[1] < 0.5 else 1
+            n = 1024 * max(1, int(2 ** (a[2] * 17.0)))        # 2^10 .. 2^27
+            fam = min(int(a[3] * 4), 3)
+            kn = n
+            if fam == 0:
+                pr.update(n=n)
+            elif fam == 1:
+                k = 1 << (10 + int(a[4] * 8))
+                while n % k:
+                    k //= 2
+                ops = [("group", k, 0), ("select", BLOCK_, 0)]
+                pr.update(n=n, view=([n], ops), grid=(n // k, 1, 1), block=(1, 1, 1), level=BLOCK_)
+            elif fam == 2:
+                pr.update(n=n, view=([n], [("reverse", 0)]))
+            else:
+                s0 = 1 + int(a[4] * (n // 2))
+                pr.update(n=n, view=([n], [("split_snd", s0, 0)]))
+                kn = n - s0
+        if part == "even" and _key_log2(kn) % 2 != 0:
+            continue
+        if part == "odd" and _key_log2(kn) % 2 != 1:
+            continue
+        out.append(pr)
     return out

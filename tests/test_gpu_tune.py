@@ -1,7 +1,8 @@
 """GPU checks of the schedule machinery: the cost model's kernels against the
 oracle's FP64 twin (forward, gradient within 1e-4 relative, Adam), every
-schedule candidate against the oracle, the exhaustive tuner, and a small
-regret study of the learned picker against the exhaustive tuner."""
+schedule candidate against the oracle, the exhaustive tuner, predictions from
+two host threads at once, and a small regret study of the learned picker
+against the exhaustive tuner on held-out size buckets."""
 import numpy as np
 import pytest
 import torch
@@ -129,8 +130,7 @@ def test_exhaustive_tuner_records_the_fastest():
         assert len(us) == D.candidate_count(prob["op"]) and min(us) > 0
         best = D.desc_tune_exhaustive(prob, arena, reps=5)
         assert 0 <= best < len(us)
-        assert D.desc_tune_lookup(D.make_problem(prob["op"], prob["dtype"], prob["n"], prob["aux"],
-                                                 k=prob.get("k", 0))) == best
+        assert D.desc_tune_lookup(prob) == best
     D.desc_tune_clear()
 
 
@@ -154,20 +154,69 @@ def test_every_matmul_candidate_is_correct(M, N, K):
 
 
 def test_learned_picker_small_regret_study():
-    """A small version of the regret study the bench runs at full size."""
+    """A small version of the regret study the bench runs at full size: the
+    held-out problems share no tuned-table bucket with the training ones."""
+    import bench
     arena = D.TuneArena(1 << 27, 5000, max_mm=4096)
-    train = synth.tune_problems(160, seed=21)
-    test = synth.tune_problems(60, seed=22)
+    train = synth.tune_problems(160, seed=21, part="even")
+    test = synth.tune_problems(60, seed=22, part="odd")
     model = D.CostModel(synth.mlp_init(F, H, seed=23))
-    r = D.regret_study(train, test, arena, model, epochs=200, batch=64, lr=2e-3, reps=3)
+    r = bench.regret_study(D, train, test, arena, model, epochs=200, batch=64, lr=2e-3, reps=3, retime_reps=7)
     print(r)
+    assert r["overlap"] == {"bucket": 0, "shape": 0}
     assert r["final_loss"] < 0.5
-    assert r["mean_regret"] <= 0.10
+    assert r["mean_regret"] <= 0.15
     # what the trained model gains over the method without it (always the default candidate)
     assert r["mean_regret"] < r["default_mean_regret"]
     # the model predicts for a problem through the library's own picker too
     model.install()
     c = model.predict_problem(test[0])
-    assert D.desc_tune_lookup(D.make_problem(test[0]["op"], test[0]["dtype"], test[0]["n"], test[0]["aux"],
-                                             test[0]["lengths"], test[0].get("k", 0))) == c
+    assert D.desc_tune_lookup(test[0]) == c
     D.lib().desc_tune_set_model(None, 0, 0)
+
+
+def test_predictions_from_two_threads():
+    """desc_tune_predict from two host threads on two streams at once: every
+    pick is the argmin of the oracle twin's predictions for that problem."""
+    import threading
+    p = synth.mlp_init(F, H, seed=31)
+    model = D.CostModel(p)
+    model.install()
+    probs = synth.tune_problems(60, seed=32)
+    want = []
+    for prob in probs:
+        rows = np.array(D.feature_rows(prob), dtype=np.float32).astype(np.float64)
+        y, _ = OMLP.forward(p.double().numpy(), rows, F, H)
+        want.append(int(np.argmin(y)))
+    got = [[None] * len(probs) for _ in range(2)]
+    errors = []
+
+    def worker(t):
+        try:
+            s = torch.cuda.Stream()
+            order = range(len(probs)) if t == 0 else reversed(range(len(probs)))
+            for _ in range(3):
+                for i in order:
+                    c = model.predict_problem(probs[i], stream=s)
+                    if got[t][i] is not None and got[t][i] != c:
+                        errors.append((t, i, "unstable"))
+                    got[t][i] = c
+        except Exception as e:          # noqa: BLE001 -- reported below
+            errors.append((t, repr(e)))
+
+    th = [threading.Thread(target=worker, args=(t,)) for t in range(2)]
+    for x in th:
+        x.start()
+    for x in th:
+        x.join()
+    D.lib().desc_tune_set_model(None, 0, 0)
+    D.desc_tune_clear()
+    assert not errors, errors[:5]
+    # near-ties of the FP32 kernel and the FP64 twin may pick differently; allow
+    # only those
+    for t in range(2):
+        for i, prob in enumerate(probs):
+            if got[t][i] != want[i]:
+                rows = np.array(D.feature_rows(prob), dtype=np.float64)
+                y, _ = OMLP.forward(p.double().numpy(), rows, F, H)
+                assert abs(y[got[t][i]] - y[want[i]]) <= 1e-5 * max(1.0, abs(y[want[i]])), (t, i)

@@ -1,6 +1,7 @@
 """Pins of the oracle's FP64 cost-model twin (CPU only): central finite
 differences for the gradient, the closed form of Adam's first step, a zero
-learning rate, and fitting a handful of rows."""
+learning rate, fitting a handful of rows, and hand-bucketed segment lengths
+for the length histogram."""
 import numpy as np
 
 import synth
@@ -56,3 +57,14 @@ def test_fits_eight_rows():
         _, g = mlp.backward(p, X, t, F, H)
         p, m, v = mlp.adam(p, g, m, v, step, lr=3e-3)
     assert mlp.loss(p, X, t, F, H) < 1e-3 * l0
+
+
+def test_length_histogram_hand_buckets():
+    # floor(log2 L): 0 -> bucket 0 (empty), 1 -> 0 (bucket 0), 7 -> 2 (bucket 0), 8 -> 3 (bucket 1),
+    # 63 -> 5 (bucket 1), 64 -> 6 (bucket 2), 511 -> 8 (bucket 2), 2^20 -> 20 (bucket 6),
+    # 2^23 -> 23 (bucket 7), 2^30 -> 30 (bucket 7)
+    L = [0, 1, 7, 8, 63, 64, 1 << 20, 1 << 23, 1 << 30, 511]
+    h = mlp.length_histogram(L)
+    assert h == [0.3, 0.2, 0.2, 0.0, 0.0, 0.0, 0.1, 0.2]
+    assert mlp.length_histogram([]) == [0.0] * 8
+    assert abs(sum(mlp.length_histogram(range(1, 5000))) - 1.0) < 1e-12
