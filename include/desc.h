@@ -185,6 +185,15 @@ int32_t desc_lower_view(const desc_view *v, const desc_exec *ex, desc_lowered *o
  * 2^24 (element, thread) pairs. */
 int32_t desc_check_disjoint(const desc_access *acc, int32_t n, const desc_exec *ex,
                             int64_t *first_conflict);
+/* The same check; *method (if not NULL) receives which checks decided the
+ * buffers that have a write: DESC_DECIDED_STRUCTURAL when the structural
+ * argument settled at least one of them (every element written by several
+ * threads, or an injective map written by one thread each), and
+ * DESC_DECIDED_ENUMERATION when at least one needed exact enumeration. */
+#define DESC_DECIDED_STRUCTURAL 1
+#define DESC_DECIDED_ENUMERATION 2
+int32_t desc_check_disjoint_ex(const desc_access *acc, int32_t n, const desc_exec *ex,
+                               int64_t *first_conflict, int32_t *method);
 
 /* ---- Programs: accesses, barriers and splits across a kernel body ----
  * Section 3.3 and Section 4 track, per execution resource, which places

@@ -116,6 +116,8 @@ def _declare(L):
         "desc_version": (c_int32, []),
         "desc_lower_view": (c_int32, [POINTER(View), POINTER(Exec), POINTER(Lowered)]),
         "desc_check_disjoint": (c_int32, [POINTER(Access), c_int32, POINTER(Exec), POINTER(c_int64)]),
+        "desc_check_disjoint_ex": (c_int32, [POINTER(Access), c_int32, POINTER(Exec), POINTER(c_int64),
+                                             POINTER(c_int32)]),
         "desc_check_program": (c_int32, [POINTER(Stmt), c_int32, POINTER(Exec), POINTER(c_int32), POINTER(c_int64)]),
         "desc_split_reduce_transpose": (c_int32, [POINTER(View), POINTER(Exec), c_int32, c_int32, c_void_p, c_size_t,
                                                   c_void_p, c_size_t, c_void_p, c_size_t, c_void_p, c_void_p, c_int64,
@@ -252,21 +254,28 @@ def lowered_struct(d: dict) -> Lowered:
     return m
 
 
-def desc_check_disjoint(accesses, grid, block):
+DECIDED_STRUCTURAL, DECIDED_ENUMERATION = 1, 2
+
+
+def desc_check_disjoint(accesses, grid, block, with_method=False):
     """accesses: list of (lowered dict, buffer id, is_write).  Returns None
-    when the accesses are disjoint, else the first conflicting element."""
+    when the accesses are disjoint, else the first conflicting element; with
+    with_method, (that, the DECIDED_* bits of the checks that decided)."""
     n = len(accesses)
     arr = (Access * max(n, 1))()
     for i, (m, buf, w) in enumerate(accesses):
         arr[i].map = lowered_struct(m)
         arr[i].buffer = int(buf)
         arr[i].is_write = 1 if w else 0
-    first = c_int64(-1)
-    st = lib().desc_check_disjoint(arr, n, ctypes.byref(make_exec(grid, block)), ctypes.byref(first))
+    first, how = c_int64(-1), c_int32(0)
+    st = lib().desc_check_disjoint_ex(arr, n, ctypes.byref(make_exec(grid, block)), ctypes.byref(first),
+                                      ctypes.byref(how))
     if st == 3:
-        return first.value
-    _check(st, "desc_check_disjoint")
-    return None
+        res = first.value
+    else:
+        _check(st, "desc_check_disjoint")
+        res = None
+    return (res, how.value) if with_method else res
 
 
 STMT_ACCESS, STMT_SYNC, STMT_SPLIT = 0, 1, 2

@@ -377,8 +377,9 @@ bool enumerate(const desc_lowered &m, const desc_exec &ex, int32_t w, std::vecto
 
 }  // namespace
 
-extern "C" int32_t desc_check_disjoint(const desc_access *acc, int32_t n, const desc_exec *ex,
-                                       int64_t *first_conflict) {
+extern "C" int32_t desc_check_disjoint_ex(const desc_access *acc, int32_t n, const desc_exec *ex,
+                                          int64_t *first_conflict, int32_t *method) {
+  if (method) *method = 0;
   if (n < 0 || (n > 0 && !acc) || !ex) return DESC_ERR_INVALID_ARG;
   if (!exec_ok(*ex)) return DESC_ERR_INVALID_ARG;
   for (int i = 0; i < n; ++i) {
@@ -403,6 +404,7 @@ extern "C" int32_t desc_check_disjoint(const desc_access *acc, int32_t n, const 
 
   bool found = false;
   int64_t worst = 0;
+  int32_t how = 0;
   auto report = [&](int64_t e) {
     if (!found || e < worst) worst = e;
     found = true;
@@ -421,10 +423,15 @@ extern "C" int32_t desc_check_disjoint(const desc_access *acc, int32_t n, const 
       const int64_t rep = replication(m, *ex);
       if (rep > 1) {            // several threads write every element
         report(min_element(m));
+        how |= DESC_DECIDED_STRUCTURAL;
         continue;
       }
-      if (rep == 1 && desc::affine_injective(m.extent, m.stride, m.ndims)) continue;
+      if (rep == 1 && desc::affine_injective(m.extent, m.stride, m.ndims)) {
+        how |= DESC_DECIDED_STRUCTURAL;
+        continue;
+      }
     }
+    how |= DESC_DECIDED_ENUMERATION;
     std::vector<Ent> ents;
     for (auto *a : W)
       if (!enumerate(a->map, *ex, 1, ents)) return DESC_ERR_UNSUPPORTED;
@@ -454,11 +461,17 @@ extern "C" int32_t desc_check_disjoint(const desc_access *acc, int32_t n, const 
       i = j;
     }
   }
+  if (method) *method = how;
   if (found) {
     if (first_conflict) *first_conflict = worst;
     return DESC_ERR_OVERLAP;
   }
   return DESC_OK;
+}
+
+extern "C" int32_t desc_check_disjoint(const desc_access *acc, int32_t n, const desc_exec *ex,
+                                       int64_t *first_conflict) {
+  return desc_check_disjoint_ex(acc, n, ex, first_conflict, nullptr);
 }
 
 namespace desc {

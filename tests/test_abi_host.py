@@ -188,3 +188,234 @@ def test_disjointness_matches_oracle(desc_lib, seed):
     want = V.views_disjoint(accesses, grid, block)
     got = _c_verdict_views(accesses, grid, block)
     assert got == want
+
+
+# ------------------------------------------------ disjointness: the wider sweep
+# Views over 1-, 2- and 3-D base arrays with group, split (fst / snd),
+# transpose and reverse at any nesting depth, selected by blocks (X, Y),
+# warps and lanes or threads (X, Y), with unselected execution dims that
+# replicate the access; several accesses per buffer, some built to overlap
+# (a split half written beside the whole, a read through a reversed view);
+# and raw affine maps whose strides may repeat, vanish or change sign.
+_BASES = [[64], [96], [8, 16], [4, 6, 8], [2, 64], [32, 32], [3, 4, 32], [128, 4], [6, 10], [64, 3], [2, 2, 64],
+          [5, 7], [36]]
+
+
+def _rand_view_op(rng, shape):
+    """One random non-select view op valid for `shape` (or None)."""
+    choices = []
+    for d in range(len(shape)):
+        n = shape[d]
+        divs = [k for k in range(1, n + 1) if n % k == 0]
+        if divs:
+            choices.append(("group", rng.choice(divs), d))
+        choices += [("split_fst", rng.randint(0, n), d), ("split_snd", rng.randint(0, n), d), ("reverse", d)]
+        if d + 1 < len(shape):
+            choices.append(("transpose", d))
+    return rng.choice(choices) if choices else None
+
+
+def _selected_view(rng, base):
+    """A random chain over `base` whose selects narrow block -> warp / lane or
+    thread, with view ops before, between and after them."""
+    ops, shape = [], list(base)
+
+    def some_ops(k):
+        nonlocal shape
+        for _ in range(rng.randint(0, k)):
+            op = _rand_view_op(rng, shape)
+            if op is None or len(shape) > 5:
+                return
+            ops.append(op)
+            shape = V.stages(base, ops)[-1]
+
+    some_ops(3)
+    levels = []
+    if rng.random() < 0.7:
+        levels += rng.sample([(V.BLOCK, V.Y), (V.BLOCK, V.X)], rng.randint(1, 2))
+    r = rng.random()
+    if r < 0.3:
+        levels += [(V.WARP, V.X)] + ([(V.THREAD, V.X)] if rng.random() < 0.7 else [])
+    elif r < 0.8:
+        levels += rng.sample([(V.THREAD, V.Y), (V.THREAD, V.X)], rng.randint(1, 2))
+    warp = False
+    for lvl, dim in levels:
+        some_ops(1)
+        if not shape:
+            break
+        lane = lvl == V.THREAD and warp
+        if lane and shape[0] != 32:
+            if shape[0] > 0 and shape[0] % 32 == 0:     # bring 32 lanes outermost
+                ops.append(("group", shape[0] // 32, 0))
+                ops.append(("transpose", 0))
+                shape = V.stages(base, ops)[-1]
+            else:
+                break
+        if shape[0] > 64 and not lane:
+            continue                                    # keep the resource counts small
+        ops.append(("select", lvl, dim))
+        warp = warp or lvl == V.WARP
+        shape = V.stages(base, ops)[-1]
+    some_ops(2)
+    return ops
+
+
+def _exec_for(rng, base, ops):
+    """The execution resource whose counts match the view's selects; the
+    dims it does not select get small random extents (replication)."""
+    grid, block = [1, 1, 1], [1, 1, 1]
+    sels = V.selects(base, ops)
+    warp_e, lane = None, False
+    for lvl, dim, e in sels:
+        if lvl == V.BLOCK:
+            grid[dim] = e
+        elif lvl == V.WARP:
+            warp_e = e
+        elif warp_e is not None:
+            lane = True
+        else:
+            block[dim] = e
+    bsel = {d for lvl, d, _ in sels if lvl == V.BLOCK}
+    tsel = {d for lvl, d, _ in sels if lvl == V.THREAD}
+    for d in range(2):
+        if d not in bsel and rng.random() < 0.3:
+            grid[d] = rng.choice([2, 3])
+    if warp_e is not None or (lane and warp_e is None):
+        block = [32 * (warp_e if warp_e is not None else rng.choice([1, 2])), 1, 1]
+    else:
+        for d in range(2):
+            if d not in tsel and rng.random() < 0.3:
+                block[d] = rng.choice([2, 4])
+    return tuple(grid), tuple(block)
+
+
+def _wide_case(seed):
+    """(accesses, grid, block) or None when the draw is not a valid program."""
+    rng = random.Random(91000 + seed)
+    base = rng.choice(_BASES)
+    try:
+        ops = _selected_view(rng, base)
+        grid, block = _exec_for(rng, base, ops)
+    except V.ViewError:
+        return None
+    acc = [(0, base, ops, True)]
+    r = rng.random()
+    if r < 0.2:                                         # a split half written beside the whole
+        k = rng.randint(1, base[0])
+        acc.append((0, base, [("split_fst", k, 0)], True))
+    elif r < 0.45:                                      # a read of the same buffer through other views
+        acc.append((0, base, ops[:-1] + [("reverse", 0)] if ops and ops[-1][0] != "select" and
+                    V.stages(base, ops)[-1] else [("reverse", 0)], False))
+    elif r < 0.6:                                       # a second buffer, written through its own view
+        b2 = rng.choice(_BASES)
+        acc.append((1, b2, _selected_view(rng, b2), True))
+    try:
+        for _, b, o, _ in acc:
+            V.check_selects(b, o, grid, block)
+    except V.ViewError:
+        return None
+    if math.prod(grid) * math.prod(block) > 1024 or 0 in grid or 0 in block:
+        return None                                     # an empty resource is not a launch
+    return acc, grid, block
+
+
+def test_disjointness_wide_sweep_matches_oracle(desc_lib):
+    stats = {"accept": 0, "reject": 0, "structural_accept": 0, "structural_reject": 0, "enumerated": 0,
+             "warp": 0, "transpose": 0, "split": 0, "multi_reverse": 0, "replicated": 0, "2d3d": 0}
+    cases, seed = 0, 0
+    while cases < 600:
+        c = _wide_case(seed)
+        seed += 1
+        if c is None:
+            continue
+        acc, grid, block = c
+        want = V.views_disjoint(acc, grid, block)
+        got, how = _c_verdict_views_method(acc, grid, block)
+        assert got == want, (seed - 1, acc, grid, block)
+        cases += 1
+        ops = acc[0][2]
+        stats["accept" if want is None else "reject"] += 1
+        if how == D.DECIDED_STRUCTURAL:
+            stats["structural_accept" if want is None else "structural_reject"] += 1
+        if how & D.DECIDED_ENUMERATION:
+            stats["enumerated"] += 1
+        stats["warp"] += any(o[0] == "select" and o[1] == V.WARP for o in ops)
+        stats["transpose"] += any(o[0] == "transpose" for o in ops)
+        stats["split"] += any(o[0].startswith("split") for o in ops)
+        stats["multi_reverse"] += len({o[1] for o in ops if o[0] == "reverse"}) > 1
+        stats["replicated"] += any(g > 1 for g in grid[:2]) and len(
+            [o for o in ops if o[0] == "select" and o[1] == V.BLOCK]) < sum(g > 1 for g in grid[:2])
+        stats["2d3d"] += len(acc[0][1]) > 1
+    print(stats)
+    assert stats["accept"] >= 100 and stats["reject"] >= 100
+    assert stats["structural_accept"] >= 100 and stats["structural_reject"] >= 20
+    assert stats["enumerated"] >= 50
+    for k in ("warp", "transpose", "split", "multi_reverse", "replicated", "2d3d"):
+        assert stats[k] >= 20, (k, stats)
+
+
+def _c_verdict_views_method(accesses, grid, block):
+    acc = [(D.desc_lower_view(shape, ops, grid, block), buf, w) for buf, shape, ops, w in accesses]
+    return D.desc_check_disjoint(acc, grid, block, with_method=True)
+
+
+_BINDS = [("block", V.X), ("block", V.Y), ("thread", V.X), ("thread", V.Y), ("local",), ("local",)]
+
+
+def _raw_case(rng):
+    """A raw affine write map (and sometimes a read map) with random strides."""
+    grid = (rng.choice([1, 2, 3]), rng.choice([1, 2]), 1)
+    block = (rng.choice([1, 2, 4, 8]), rng.choice([1, 2]), 1)
+    nd = rng.randint(1, 4)
+    binds = rng.sample(_BINDS, nd)
+    ext, stride = [], []
+    for b in binds:
+        if b[0] == "block":
+            ext.append(grid[b[1]] if rng.random() < 0.85 else grid[b[1]] + 1)
+        elif b[0] == "thread":
+            ext.append(block[b[1]] if rng.random() < 0.85 else max(1, block[b[1]] - 1))
+        else:
+            ext.append(rng.randint(1, 5))
+    if rng.random() < 0.5:                              # row-major strides of a permutation: injective
+        order = list(range(nd))
+        rng.shuffle(order)
+        c = 1
+        stride = [0] * nd
+        for i in reversed(order):
+            stride[i] = c * rng.choice([1, -1])
+            c *= ext[i]
+    else:                                               # small strides: repeats, zeros, sign changes
+        stride = [rng.randint(-6, 6) for _ in range(nd)]
+    off = sum(max(0, -s) * (e - 1) for s, e in zip(stride, ext)) + rng.randint(0, 3)
+    return grid, block, binds, ext, stride, off
+
+
+def _lowered_of_raw(binds, ext, stride, off):
+    sel = [i for i, b in enumerate(binds) if b[0] != "local"]
+    loc = [i for i, b in enumerate(binds) if b[0] == "local"]
+    order = sel + loc
+    lvl = {"block": V.BLOCK, "thread": V.THREAD}
+    return {"ndims": len(order), "nsel": len(sel), "extent": [ext[i] for i in order],
+            "stride": [stride[i] for i in order],
+            "level": [lvl[binds[i][0]] if binds[i][0] != "local" else -1 for i in order],
+            "dim": [binds[i][1] if binds[i][0] != "local" else -1 for i in order], "offset": off}
+
+
+@pytest.mark.parametrize("seed", range(400))
+def test_disjointness_raw_maps_match_oracle(desc_lib, seed):
+    rng = random.Random(123000 + seed)
+    grid, block, binds, ext, stride, off = _raw_case(rng)
+    # the oracle's binds: ("block", dim), ("thread", dim), ("local",)
+    t, e = V.affine_access(ext, stride, off, binds, grid, block)
+    acc_o = [(0, t, e, True)]
+    acc_c = [(_lowered_of_raw(binds, ext, stride, off), 0, True)]
+    if rng.random() < 0.4:                              # a read map beside it
+        g2, b2, bi2, ex2, st2, of2 = _raw_case(rng)
+        bi2 = [b if b[0] == "local" or (b[0] == "block" and ex2[i] <= grid[b[1]]) or
+               (b[0] == "thread" and ex2[i] <= block[b[1]]) else ("local",) for i, b in enumerate(bi2)]
+        t2, e2 = V.affine_access(ex2, st2, of2, bi2, grid, block)
+        acc_o.append((0, t2, e2, False))
+        acc_c.append((_lowered_of_raw(bi2, ex2, st2, of2), 0, False))
+    want = V.first_conflict(acc_o)
+    got = D.desc_check_disjoint(acc_c, grid, block)
+    assert got == want, (grid, block, binds, ext, stride, off)
