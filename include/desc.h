@@ -250,18 +250,38 @@ int32_t desc_check_program(const desc_stmt *prog, int32_t n, const desc_exec *ex
  * arithmetic (error within 1e-5 * sum|x|), with compensated (Kahan)
  * accumulation when flags has DESC_KAHAN. */
 #define DESC_KAHAN 1
-/* Operators other than the sum (Section 5 fixes no operator; the generic
- * reduce and scan take any associative one): DESC_MAX / DESC_MIN give the
- * maximum / minimum instead, exact in both dtypes (FP32 follows IEEE maxNum /
- * minNum: a NaN operand is ignored unless every operand is NaN).  The value
- * of an empty reduction or segment is the operator's identity: 0 for the sum,
- * INT32_MIN or -inf for the maximum, INT32_MAX or +inf for the minimum.  At
- * most one of DESC_KAHAN, DESC_MAX, DESC_MIN. */
+/* Operators other than the sum (Section 5 fixes no operator; a generic
+ * reduce or scan takes any associative one).  At most one operator flag:
+ *   DESC_MAX / DESC_MIN      maximum / minimum, exact in both dtypes (FP32
+ *                            follows IEEE maxNum / minNum: a NaN operand is
+ *                            ignored unless every operand is NaN)
+ *   DESC_PROD                product: int32 modulo 2^32 (exact); FP32 in FP32
+ *                            arithmetic, relative error within
+ *                            gamma_(m-1) = (m-1) u / (1 - (m-1) u), u = 2^-24,
+ *                            for m factors when no partial product overflows
+ *                            or falls below the normal range
+ *   DESC_AND / DESC_OR / DESC_XOR  bitwise, int32 only (exact)
+ *   DESC_ARGMAX / DESC_ARGMIN      the index, in the base array, of the
+ *                            element holding the maximum / minimum value
+ *                            (ties: the smallest index; FP32 NaNs lose to
+ *                            every number); the output is int32 whatever the
+ *                            input dtype, and the base array must have fewer
+ *                            than 2^30 elements for scans, 2^31 for reduces
+ * The value of an empty reduction or segment is the operator's identity: 0
+ * for the sum, or and xor, INT32_MIN or -inf for the maximum, INT32_MAX or
+ * +inf for the minimum, 1 for the product, all ones for and, and index -1 for
+ * the arg operators.  DESC_KAHAN counts as the (compensated) sum's flag. */
 #define DESC_MAX (1 << 1)
 #define DESC_MIN (1 << 2)
 /* Scans: out[p] combines the inputs strictly before p in its segment (the
  * identity for a segment's first point) instead of up to and including p. */
 #define DESC_EXCLUSIVE (1 << 3)
+#define DESC_PROD (1 << 4)
+#define DESC_AND (1 << 5)
+#define DESC_OR (1 << 6)
+#define DESC_XOR (1 << 7)
+#define DESC_ARGMAX (1 << 8)
+#define DESC_ARGMIN (1 << 9)
 int32_t desc_reduce_workspace_size(const desc_view *v, const desc_exec *ex, int32_t out_level,
                                    int32_t dtype, size_t *bytes);
 int32_t desc_reduce(const desc_view *v, const desc_exec *ex, int32_t out_level, int32_t dtype,
@@ -277,8 +297,10 @@ int32_t desc_reduce(const desc_view *v, const desc_exec *ex, int32_t out_level, 
  * does not reach are left untouched.  in == out (in place) is allowed.
  * DESC_I32 wraps modulo 2^32 (bit-exact); DESC_F32 has per-element error
  * within 1e-5 * sum_{q<=p} |x_q| (FP32 arithmetic, compensated carries).
- * flags: DESC_MAX or DESC_MIN (the operator; exact, always the default
- * 16384-element tile), DESC_EXCLUSIVE (q < p instead of q <= p). */
+ * flags: one operator flag (see desc_reduce; operators other than the sum
+ * always take the default tile) and DESC_EXCLUSIVE (q < p instead of
+ * q <= p).  With DESC_ARGMAX / DESC_ARGMIN, out[index(p)] is the int32 index
+ * in the base array of the element chosen among the q <= p (or q < p). */
 /* Test hook for the bounded waits: tile 1 never publishes, and the waits
  * give up after tens of milliseconds, so the call records
  * DESC_ERR_DEVICE_TIMEOUT (read by desc_stream_status) instead of hanging.
@@ -298,10 +320,13 @@ int32_t desc_scan(const desc_view *v, const desc_exec *ex, int32_t seg_level, in
  * or a real-time loop that forbids allocation after start-up.  Such callers
  * cannot obtain the workspace desc_scan needs.
  *
- * desc_scan_noalloc computes exactly what desc_scan computes, for views whose
- * scan runs over one contiguous run of the base array (for example the plain
- * array, a split of it, or groups selected at seg_level); other views return
- * DESC_ERR_UNSUPPORTED.  It takes no workspace: its scratch is a fixed
+ * desc_scan_noalloc computes what desc_scan computes (inclusive sums, no
+ * flags), for views whose scan runs over one contiguous run of the base array
+ * (for example the plain array, a split of it, or groups selected at
+ * seg_level); other views return DESC_ERR_UNSUPPORTED.  It always runs the
+ * 16384-element tile, so for int32 its results equal desc_scan's bit for bit,
+ * while for FP32 they may differ from a desc_scan that runs another tile in
+ * the last bits, both within the same 1e-5 * sum_{q<=p} |x_q| bound.  It takes no workspace: its scratch is a fixed
  * static device array inside the library, large enough for
  * DESC_SCAN_NOALLOC_MAX_ELEMS elements (256 bytes plus 128 bytes per 16384
  * elements, about 2 MiB).  Every GPU that loads the library holds that array
@@ -420,7 +445,9 @@ int32_t desc_split_reduce_transpose(const desc_view *rv, const desc_exec *rex, i
  * of the segment).  in == scan_out is allowed.  flags may add DESC_MAX or
  * DESC_MIN (scans and totals under that operator; an empty segment's total is
  * the operator's identity) and DESC_EXCLUSIVE (exclusive scans; the totals are
- * unchanged). */
+ * unchanged); any operator flag of desc_reduce may be given (arg operators:
+ * scan_out and sums_out receive int32 element indices of the array, -1 for
+ * an empty segment's total). */
 #define DESC_CHECK_OFFSETS (1 << 17)
 int32_t desc_segmented_workspace_size(int64_t nseg, int64_t total, size_t *bytes);
 int32_t desc_segmented_reduce_scan(const int64_t *d_offsets, int64_t nseg, int64_t total, int32_t dtype,

@@ -132,30 +132,109 @@ def segmented_reduce_scan(x, offsets):
     return scan_out, sums, pa, sabs
 
 
-# ---- other operators ---------------------------------------------------------
+# ---- other operators ----------------------------------------------------------
 # Section 5 fixes no operator for its reduction and scan; a generic reduce or
-# scan takes any associative operator.  Besides the sum: the maximum and the
-# minimum (exact; on FP32 they follow IEEE maxNum / minNum, so a NaN operand
-# is ignored unless every operand is NaN), and exclusive scans, where a point
-# gets the combination of the points strictly before it in its segment (the
-# operator's identity for the first one).
+# scan takes any associative operator.  Besides the sum:
+#   max / min    exact; on FP32 they follow IEEE maxNum / minNum, so a NaN
+#                operand is ignored unless every operand is NaN
+#   prod         int32: the product modulo 2^32 (exact integers, wrapped);
+#                FP32: the FP64 product of the FP32 inputs (relative error at
+#                most (m - 1) 2^-53 for m factors, far inside the FP32 bound
+#                it is compared with)
+#   and/or/xor   int32 bitwise
+#   argmax/argmin  the index in the base array of the element holding the
+#                largest / smallest value; among equal values the smallest
+#                index; FP32 NaNs lose to every number (all NaN: the smallest
+#                index); -1 for no element
+# and exclusive scans, where a point gets the combination of the points
+# strictly before it in its segment (the operator's identity for the first).
+
+OPS = ("sum", "max", "min", "prod", "and", "or", "xor", "argmax", "argmin")
+
 
 def identity(op, is_int):
-    """0 for the sum, the smallest / largest value for the maximum / minimum."""
-    if op == "sum":
+    """The value of an empty reduction under op."""
+    if op in ("sum", "or", "xor"):
         return 0
     if op == "max":
         return np.iinfo(np.int32).min if is_int else -np.inf
-    return np.iinfo(np.int32).max if is_int else np.inf
+    if op == "min":
+        return np.iinfo(np.int32).max if is_int else np.inf
+    if op == "prod":
+        return 1
+    if op == "and":
+        return -1
+    return -1                                            # argmax / argmin: no element
 
 
-def _combine_rows(vals, op, exclusive):
-    """Prefix combination along each row (inclusive or exclusive), with the
-    sum in int64 (wrapped later) or FP64, max / min exactly."""
+def arg_pick(vals, idx, op):
+    """The arg-maximum / arg-minimum of one set of (value, element index)
+    pairs, from the definition: the best value among the non-NaN ones (all
+    NaN: every element ties), then the smallest index holding it."""
+    vals = np.asarray(vals, dtype=np.float64)
+    idx = np.asarray(idx, dtype=np.int64)
+    if vals.size == 0:
+        return -1
+    num = ~np.isnan(vals)
+    if not num.any():
+        return int(idx.min())
+    best = vals[num].max() if op == "argmax" else vals[num].min()
+    return int(idx[num & (vals == best)].min())
+
+
+def _arg_prefix(vals, idx, op, exclusive):
+    """Running arg operator along one row, point by point in logical order."""
+    out = np.empty(vals.size, dtype=np.int64)
+    bv, bi = None, -1
+    for p in range(vals.size):
+        if exclusive:
+            out[p] = bi
+        v, i = float(vals[p]), int(idx[p])
+        if bi < 0:
+            take = True
+        elif np.isnan(v) != np.isnan(bv):
+            take = not np.isnan(v)
+        elif np.isnan(v):
+            take = i < bi
+        elif v != bv:
+            take = v > bv if op == "argmax" else v < bv
+        else:
+            take = i < bi
+        if take:
+            bv, bi = v, i
+        if not exclusive:
+            out[p] = bi
+    return out
+
+
+def _wrap_prod_prefix(row):
+    """Prefix products of int32 values modulo 2^32 (exact Python integers)."""
+    out, acc = [], 1
+    for v in row.tolist():
+        acc = (acc * int(v)) & 0xFFFFFFFF
+        out.append(acc)
+    return wrap_i32(np.array(out, dtype=np.int64) - ((np.array(out, dtype=np.int64) >> 31) << 32))
+
+
+def _combine_rows(vals, op, exclusive, idx=None):
+    """Prefix combination along each row (inclusive or exclusive): sums in
+    int64 (wrapped later) or FP64, max / min / bitwise exactly, int32
+    products exactly modulo 2^32, FP32 products in FP64, arg operators as
+    element indices (``idx``: the base-array index of every value)."""
     is_int = vals.dtype == np.int32
+    if op in ("argmax", "argmin"):
+        return np.array([_arg_prefix(vals[r], idx[r], op, exclusive) for r in range(vals.shape[0])],
+                        dtype=np.int64).reshape(vals.shape)
     if op == "sum":
         v = vals.astype(np.int64 if is_int else np.float64)
         inc = np.cumsum(v, axis=1)
+    elif op == "prod" and is_int:
+        inc = np.array([_wrap_prod_prefix(r) for r in vals], dtype=np.int64).reshape(vals.shape)
+    elif op == "prod":
+        inc = np.multiply.accumulate(vals.astype(np.float64), axis=1) if vals.shape[1] else vals.astype(np.float64)
+    elif op in ("and", "or", "xor"):
+        f = {"and": np.bitwise_and, "or": np.bitwise_or, "xor": np.bitwise_xor}[op]
+        inc = f.accumulate(vals.astype(np.int64), axis=1) if vals.shape[1] else vals.astype(np.int64)
     else:
         f = np.fmax if op == "max" else np.fmin
         v = vals.astype(np.int64 if is_int else np.float64)
@@ -169,32 +248,61 @@ def _combine_rows(vals, op, exclusive):
     return out
 
 
+def _reduce_row(r, ri, op, is_int):
+    """One output of reduce_op: the plain definition of each operator."""
+    if r.size == 0:
+        return identity(op, is_int)
+    if op == "sum":
+        return int(wrap_i32(r.astype(np.int64).sum())) if is_int else math.fsum(r.astype(np.float64))
+    if op in ("argmax", "argmin"):
+        return arg_pick(r, ri, op)
+    if op == "prod" and is_int:
+        acc = 1
+        for v in r.tolist():
+            acc = (acc * int(v)) & 0xFFFFFFFF
+        return acc - (1 << 32) if acc >= (1 << 31) else acc
+    if op == "prod":
+        return float(np.prod(r.astype(np.float64)))
+    if op in ("and", "or", "xor"):
+        f = {"and": np.bitwise_and, "or": np.bitwise_or, "xor": np.bitwise_xor}[op]
+        return int(f.reduce(r.astype(np.int64)))
+    f = np.fmax if op == "max" else np.fmin
+    return f.reduce(r)
+
+
 def reduce_op(x, base_shape, ops, out_level, op, grid=None, block=None):
-    """Maximum or minimum (op "max" / "min") over the view, one output per
-    resource at ``out_level``; the identity for an empty row."""
+    """The reduction under op (see OPS) over the view, one output per
+    resource at ``out_level``; the identity for an empty row.  int32
+    results (all arg operators, int32 inputs) as int32, FP32 ones in FP64."""
     if grid is not None:
         V.check_selects(base_shape, ops, grid, block)
-    vals, _ = _rows(x, base_shape, ops, out_level)
+    vals, idx = _rows(x, base_shape, ops, out_level)
     is_int = vals.dtype == np.int32
-    f = np.fmax if op == "max" else np.fmin
-    ident = identity(op, is_int)
-    out = np.array([f.reduce(r) if r.size else ident for r in vals], dtype=np.int64 if is_int else np.float64)
-    return out.astype(np.int32) if is_int else out
+    out = [_reduce_row(r, ri, op, is_int) for r, ri in zip(vals, idx)]
+    if is_int or op in ("argmax", "argmin"):
+        return np.array(out, dtype=np.int64).astype(np.int32)
+    return np.array(out, dtype=np.float64)
 
 
 def scan_op(x, out_init, base_shape, ops, seg_level, op="sum", exclusive=False, grid=None, block=None):
-    """Prefix combination over the view, segmented at ``seg_level``, with op
-    "sum" / "max" / "min", inclusive or exclusive.  Returns (out, prefix_abs):
+    """Prefix combination over the view, segmented at ``seg_level``, with an
+    operator of OPS, inclusive or exclusive.  Returns (out, prefix_abs):
     prefix_abs is sum |x| over the combined points (FP sums only, else
-    None), the scale of the sum's tolerance."""
+    None), the scale of the sum's tolerance.  Arg operators write int32
+    element indices (out_init should then be int32)."""
     if grid is not None:
         V.check_selects(base_shape, ops, grid, block)
     vals, idx = _rows(x, base_shape, ops, seg_level)
     is_int = vals.dtype == np.int32
-    res = _combine_rows(vals, op, exclusive)
+    res = _combine_rows(vals, op, exclusive, idx)
     out = np.array(out_init, copy=True).reshape(-1)
+    if op in ("argmax", "argmin"):
+        out = out.astype(np.int32)
+        out[idx.reshape(-1)] = res.astype(np.int32).reshape(-1)
+        return out.reshape(np.shape(out_init)), None
     if is_int:
-        out[idx.reshape(-1)] = wrap_i32(res).reshape(-1) if op == "sum" else res.astype(np.int32).reshape(-1)
+        out[idx.reshape(-1)] = wrap_i32(res).reshape(-1) if op in ("sum", "prod") else \
+            res.astype(np.int32).reshape(-1)
         return out.reshape(np.shape(out_init)), None
     out = out.astype(np.float64)
     out[idx.reshape(-1)] = res.reshape(-1)
@@ -210,30 +318,43 @@ def segmented_op(x, offsets, op="sum", exclusive=False):
     """Per segment [offsets[s], offsets[s+1]): the prefix combination
     (inclusive or exclusive) and the total, under op.  Returns (scan, totals,
     prefix |x| (FP sums), total |x| (FP sums)); empty segments total the
-    identity."""
+    identity.  Arg operators give int32 indices into x."""
     x = np.asarray(x)
     off = np.asarray(offsets, dtype=np.int64)
     S = off.size - 1
     is_int = x.dtype == np.int32
-    scan_out = np.zeros(x.size, dtype=np.int32 if is_int else np.float64)
-    tot = np.zeros(S, dtype=np.int32 if is_int else np.float64)
+    arg = op in ("argmax", "argmin")
+    as_int = is_int or arg
+    scan_out = np.zeros(x.size, dtype=np.int32 if as_int else np.float64)
+    tot = np.zeros(S, dtype=np.int32 if as_int else np.float64)
     fp_sum = (not is_int) and op == "sum"
     pa = np.zeros(x.size) if fp_sum else None
     sabs = np.zeros(S) if fp_sum else None
     for s in range(S):
         a, b = int(off[s]), int(off[s + 1])
         seg = x[a:b].reshape(1, -1)
-        r = _combine_rows(seg, op, exclusive).reshape(-1)
-        full = _combine_rows(seg, op, False).reshape(-1)
-        if is_int:
-            scan_out[a:b] = wrap_i32(r) if op == "sum" else r.astype(np.int32)
-            t = full[-1] if b > a else identity(op, True)
+        sidx = np.arange(a, b, dtype=np.int64).reshape(1, -1)
+        r = _combine_rows(seg, op, exclusive, sidx).reshape(-1)
+        if arg:
+            scan_out[a:b] = r
+            tot[s] = arg_pick(seg.reshape(-1), sidx.reshape(-1), op)
+        elif is_int:
+            scan_out[a:b] = wrap_i32(r) if op in ("sum", "prod") else r.astype(np.int32)
+            t = _reduce_row(seg.reshape(-1), sidx.reshape(-1), op, True)
             tot[s] = wrap_i32(t) if op == "sum" else np.int32(t)
         else:
             scan_out[a:b] = r
-            tot[s] = (math.fsum(seg.reshape(-1).astype(np.float64)) if op == "sum" else full[-1]) if b > a \
-                else identity(op, False)
+            tot[s] = (math.fsum(seg.reshape(-1).astype(np.float64)) if op == "sum" else
+                      _reduce_row(seg.reshape(-1), sidx.reshape(-1), op, False)) if b > a else identity(op, False)
             if fp_sum:
                 pa[a:b] = _combine_rows(np.abs(seg).astype(np.float32), "sum", exclusive).reshape(-1)
                 sabs[s] = math.fsum(np.abs(seg.reshape(-1).astype(np.float64)))
     return scan_out, tot, pa, sabs
+
+
+def prod_tolerance(m):
+    """gamma_(m-1) = (m - 1) u / (1 - (m - 1) u), u = 2^-24: the relative error
+    bound of a product of m FP32 factors computed in FP32 in any order (no
+    overflow or underflow), each multiplication rounding to nearest."""
+    k = max(int(m) - 1, 0) * 2.0 ** -24
+    return k / (1.0 - k)

@@ -27,6 +27,8 @@ OP_REDUCE, OP_SCAN, OP_TRANSPOSE, OP_SEGMENTED, OP_MATMUL = 0, 1, 2, 3, 4
 NUM_FEATURES = 40
 KAHAN = 1
 MAX, MIN, EXCLUSIVE = 1 << 1, 1 << 2, 1 << 3
+PROD, AND, OR, XOR, ARGMAX, ARGMIN = 1 << 4, 1 << 5, 1 << 6, 1 << 7, 1 << 8, 1 << 9
+ARG_FLAGS = ARGMAX | ARGMIN
 DEBUG_STALL_TILE = 1 << 16
 CHECK_OFFSETS = 1 << 17
 
@@ -339,7 +341,8 @@ def _workspace(nbytes, device):
 def desc_reduce(x, base_shape, ops, out_level, grid=None, block=None, kahan=False, out=None,
                 ws=None, stream=None, flags=0):
     """Sum of tensor ``x`` (the base array) through a view; returns ``out``.
-    flags: MAX or MIN for the maximum / minimum instead."""
+    flags: one operator flag (MAX, MIN, PROD, AND, OR, XOR, ARGMAX, ARGMIN)
+    for that operator instead; the arg operators give int32 element indices."""
     import torch
     L = lib()
     v, e = make_view(base_shape, ops), make_exec(grid, block)
@@ -350,7 +353,7 @@ def desc_reduce(x, base_shape, ops, out_level, grid=None, block=None, kahan=Fals
         for i in range(low["nsel"]):
             if low["level"][i] <= out_level:
                 nout *= low["extent"][i]
-        out = torch.empty(nout, dtype=x.dtype, device=x.device)
+        out = torch.empty(nout, dtype=torch.int32 if flags & ARG_FLAGS else x.dtype, device=x.device)
     if ws is None:
         nb = c_size_t(0)
         _check(L.desc_reduce_workspace_size(ctypes.byref(v), _ref(e), out_level, dt, ctypes.byref(nb)),
@@ -364,13 +367,14 @@ def desc_reduce(x, base_shape, ops, out_level, grid=None, block=None, kahan=Fals
 
 def desc_scan(x, base_shape, ops, seg_level, grid=None, block=None, out=None, ws=None, flags=0,
               stream=None):
-    """Inclusive scan of ``x`` through a view into ``out`` (same base array)."""
+    """Inclusive scan of ``x`` through a view into ``out`` (same base array);
+    flags as desc_reduce, plus EXCLUSIVE (arg operators: int32 indices)."""
     import torch
     L = lib()
     v, e = make_view(base_shape, ops), make_exec(grid, block)
     dt = _dtype_code(x)
     if out is None:
-        out = torch.empty_like(x)
+        out = torch.empty_like(x, dtype=torch.int32) if flags & ARG_FLAGS else torch.empty_like(x)
     if ws is None:
         nb = c_size_t(0)
         _check(L.desc_scan_workspace_size(ctypes.byref(v), _ref(e), seg_level, dt, ctypes.byref(nb)),
@@ -463,10 +467,11 @@ def desc_segmented_reduce_scan(x, offsets, out=None, sums=None, ws=None, flags=0
     int64 CSR offsets) in one launch.  Returns (out, sums)."""
     import torch
     nseg = offsets.numel() - 1
+    odt = torch.int32 if flags & ARG_FLAGS else x.dtype
     if out is None:
-        out = torch.empty_like(x)
+        out = torch.empty_like(x, dtype=odt)
     if sums is None:
-        sums = torch.empty(nseg, dtype=x.dtype, device=x.device)
+        sums = torch.empty(nseg, dtype=odt, device=x.device)
     if ws is None:
         ws = desc_segmented_workspace(nseg, x.numel(), x.device)
     _check(lib().desc_segmented_reduce_scan(_ptr(offsets), nseg, x.numel(), _dtype_code(x), _ptr(x), _ptr(out),

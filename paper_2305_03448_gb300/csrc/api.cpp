@@ -87,12 +87,12 @@ extern "C" int32_t desc_reduce(const desc_view *v, const desc_exec *ex, int32_t 
                                desc_stream_t s) {
   if (!dtype_size(dtype)) return DESC_ERR_INVALID_ARG;
   if (out_level < DESC_LEVEL_GRID || out_level > DESC_LEVEL_THREAD) return DESC_ERR_INVALID_ARG;
-  if (flags & ~(DESC_KAHAN | DESC_MAX | DESC_MIN)) return DESC_ERR_INVALID_ARG;
-  if (((flags & DESC_KAHAN) != 0) + ((flags & DESC_MAX) != 0) + ((flags & DESC_MIN) != 0) > 1)
-    return DESC_ERR_INVALID_ARG;
+  if (flags & ~kOperatorFlags) return DESC_ERR_INVALID_ARG;
+  if (check_operator(flags, dtype, false) != DESC_OK) return DESC_ERR_INVALID_ARG;
   desc_lowered L;
   int32_t r = desc_lower_view(v, ex, &L);
   if (r != DESC_OK) return r;
+  if ((flags & kArgFlags) && L.base_elems >= (int64_t(1) << 31)) return DESC_ERR_UNSUPPORTED;   // int32 indices
   const Plan p = split_plan(L, out_level);
   if (in_bytes != size_t(L.base_elems) * 4 || out_bytes != size_t(p.n_keep) * 4)
     return DESC_ERR_SIZE_MISMATCH;
@@ -165,7 +165,7 @@ extern "C" int32_t desc_scan_workspace_size(const desc_view *v, const desc_exec 
   int32_t r = desc_lower_view(v, ex, &L);
   if (r != DESC_OK) return r;
   const ScanPlan sp = plan_scan(L, seg_level);
-  *bytes = (sp.contig ? 0 : align256(size_t(sp.total) * 4)) + scan_contig_ws(dtype, sp.total);
+  *bytes = scan_contig_ws(dtype, sp.total);            // both scans: one tile state per 4096 points
   return DESC_OK;
 }
 
@@ -175,41 +175,28 @@ extern "C" int32_t desc_scan(const desc_view *v, const desc_exec *ex, int32_t se
                              desc_stream_t s) {
   if (!dtype_size(dtype)) return DESC_ERR_INVALID_ARG;
   if (seg_level < DESC_LEVEL_GRID || seg_level > DESC_LEVEL_THREAD) return DESC_ERR_INVALID_ARG;
-  if (flags & ~(DESC_DEBUG_STALL_TILE | DESC_MAX | DESC_MIN | DESC_EXCLUSIVE)) return DESC_ERR_INVALID_ARG;
-  if ((flags & DESC_MAX) && (flags & DESC_MIN)) return DESC_ERR_INVALID_ARG;
+  if (flags & ~(DESC_DEBUG_STALL_TILE | DESC_EXCLUSIVE | kOperatorFlags)) return DESC_ERR_INVALID_ARG;
+  if (check_operator(flags, dtype, true) != DESC_OK) return DESC_ERR_INVALID_ARG;
   desc_lowered L;
   int32_t r = desc_lower_view(v, ex, &L);
   if (r != DESC_OK) return r;
   if (in_bytes != size_t(L.base_elems) * 4 || out_bytes != in_bytes) return DESC_ERR_SIZE_MISMATCH;
+  if ((flags & kArgFlags) && L.base_elems >= (int64_t(1) << 30) - 1) return DESC_ERR_UNSUPPORTED;
   const ScanPlan sp = plan_scan(L, seg_level);
   if (sp.total == 0) return DESC_OK;
   if ((r = check_device_ptr(in, 4)) != DESC_OK) return r;
   if ((r = check_device_ptr(out, 4)) != DESC_OK) return r;
   if (in != out && ranges_overlap(in, in_bytes, out, out_bytes)) return DESC_ERR_OVERLAP;
   if ((r = check_writes(L, ex)) != DESC_OK) return r;
-  const char *ib = static_cast<const char *>(in);
-  char *ob = static_cast<char *>(out);
-  if (sp.contig)
-    return launch_scan_contig(dtype, ib + sp.start * 4, ob + sp.start * 4, sp.total, sp.period,
-                              flags, ws, ws_bytes, s, schedule_for(DESC_OP_SCAN, dtype, sp.total, 0));
-  const size_t gather = align256(size_t(sp.total) * 4);
-  if (!ws || ws_bytes < gather + scan_contig_ws(dtype, sp.total)) return DESC_ERR_WORKSPACE;
-  // general path: gather in logical order, scan in place, scatter back
-  std::vector<int64_t> ext(L.extent, L.extent + L.ndims), st(L.stride, L.stride + L.ndims),
-      cst(L.ndims);
-  int64_t c = 1;
-  for (int i = L.ndims - 1; i >= 0; --i) {
-    cst[i] = c;
-    c *= ext[i];
+  if (sp.contig && !(flags & kMapScanOps)) {
+    const char *ib = static_cast<const char *>(in);
+    char *ob = static_cast<char *>(out);
+    return launch_scan_contig(dtype, ib + sp.start * 4, ob + sp.start * 4, sp.total, sp.period, flags, ws,
+                              ws_bytes, s, schedule_for(DESC_OP_SCAN, dtype, sp.total, 0));
   }
-  void *buf = ws;
-  if ((r = launch_copy_affine(in, L.offset, st.data(), buf, 0, cst.data(), ext.data(), L.ndims, s)))
-    return r;
-  if ((r = launch_scan_contig(dtype, buf, buf, sp.total, sp.period, flags,
-                              static_cast<char *>(ws) + gather, ws_bytes - gather, s,
-                              schedule_for(DESC_OP_SCAN, dtype, sp.total, 0))))
-    return r;
-  return launch_copy_affine(buf, 0, cst.data(), out, L.offset, st.data(), ext.data(), L.ndims, s);
+  // one pass through the lowered map: loads gather, stores scatter
+  return launch_scan_map(dtype, in, out, L.offset, L.extent, L.stride, L.ndims, sp.period, nullptr, 0, nullptr,
+                         flags, ws, ws_bytes, s);
 }
 
 // ---------------------------------------------------------------- scan, no allocation
@@ -450,16 +437,22 @@ extern "C" int32_t desc_segmented_workspace_size(int64_t nseg, int64_t total, si
 extern "C" int32_t desc_segmented_reduce_scan(const int64_t *d_offsets, int64_t nseg, int64_t total,
                                               int32_t dtype, const void *in, void *scan_out, void *sums_out,
                                               int32_t flags, void *ws, size_t ws_bytes, desc_stream_t s) {
-  if (flags & ~(DESC_CHECK_OFFSETS | DESC_DEBUG_STALL_TILE | DESC_MAX | DESC_MIN | DESC_EXCLUSIVE))
+  if (flags & ~(DESC_CHECK_OFFSETS | DESC_DEBUG_STALL_TILE | DESC_EXCLUSIVE | kOperatorFlags))
     return DESC_ERR_INVALID_ARG;
-  if ((flags & DESC_MAX) && (flags & DESC_MIN)) return DESC_ERR_INVALID_ARG;
+  if (check_operator(flags, dtype, true) != DESC_OK) return DESC_ERR_INVALID_ARG;
+  if ((flags & kArgFlags) && total >= (int64_t(1) << 30) - 1) return DESC_ERR_UNSUPPORTED;
   int32_t r = segmented_checks(d_offsets, nseg, total, dtype, in, scan_out, sums_out);
   if (r != DESC_OK) return r;
   if (nseg == 0) return total == 0 ? DESC_OK : DESC_ERR_SHAPE;
   if ((flags & DESC_CHECK_OFFSETS) && (r = check_offsets_device(d_offsets, nseg, total)) != DESC_OK) return r;
   if (total == 0) return fill_identity(sums_out, nseg, dtype, flags, s);   // every segment is empty
-  return launch_scan_csr(dtype, in, scan_out, total, d_offsets, nseg, sums_out,
-                         flags & (DESC_DEBUG_STALL_TILE | DESC_MAX | DESC_MIN | DESC_EXCLUSIVE), ws, ws_bytes, s,
+  const int32_t kf = flags & (DESC_DEBUG_STALL_TILE | DESC_EXCLUSIVE | kOperatorFlags);
+  if (flags & kMapScanOps) {                           // empty segments keep the identity written first
+    if ((r = fill_identity(sums_out, nseg, dtype, flags, s)) != DESC_OK) return r;
+    return launch_scan_map(dtype, in, scan_out, 0, nullptr, nullptr, 0, total, d_offsets, nseg, sums_out, kf, ws,
+                           ws_bytes, s);
+  }
+  return launch_scan_csr(dtype, in, scan_out, total, d_offsets, nseg, sums_out, kf, ws, ws_bytes, s,
                          schedule_for(DESC_OP_SEGMENTED, dtype, total, nseg));
 }
 

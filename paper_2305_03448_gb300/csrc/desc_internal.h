@@ -12,6 +12,22 @@ namespace desc {
 // Element size of a dtype (0 when unknown).
 inline size_t dtype_size(int32_t t) { return (t == DESC_I32 || t == DESC_F32) ? 4 : 0; }
 
+// The operator flags of reduce and scan calls (at most one may be set; none
+// is the sum).
+constexpr int32_t kOperatorFlags = DESC_KAHAN | DESC_MAX | DESC_MIN | DESC_PROD | DESC_AND | DESC_OR | DESC_XOR |
+                                   DESC_ARGMAX | DESC_ARGMIN;
+constexpr int32_t kArgFlags = DESC_ARGMAX | DESC_ARGMIN;
+// DESC_OK when `flags` names at most one operator and that operator applies
+// to `dtype` (bitwise operators: int32 only; the compensated sum: reduces
+// only, and exact anyway for int32), else DESC_ERR_INVALID_ARG.
+inline int32_t check_operator(int32_t flags, int32_t dtype, bool scan) {
+  const int32_t op = flags & kOperatorFlags;
+  if (op & (op - 1)) return DESC_ERR_INVALID_ARG;
+  if ((op & (DESC_AND | DESC_OR | DESC_XOR)) && dtype != DESC_I32) return DESC_ERR_INVALID_ARG;
+  if ((op & DESC_KAHAN) && scan) return DESC_ERR_INVALID_ARG;
+  return DESC_OK;
+}
+
 // A view lowered and split into the dims an op keeps (selected dims at
 // levels <= a cut level, a prefix of the selected dims) and the dims it runs
 // over.  Each dim: extent and stride in elements.
@@ -95,6 +111,18 @@ int32_t launch_scan_csr(int32_t dtype, const void *in, void *out, int64_t n, con
                         int64_t nseg, void *sums, int32_t flags, void *ws, size_t ws_bytes,
                         desc_stream_t s, int cand);
 size_t scan_csr_ws(int64_t n);
+// Operators that only the map scan runs (the look-back scan above takes the
+// sum, the maximum and the minimum).
+constexpr int32_t kMapScanOps = DESC_PROD | DESC_AND | DESC_OR | DESC_XOR | DESC_ARGMAX | DESC_ARGMIN;
+// The single-pass scan through a lowered map: point g (row-major over the
+// nd dims ext / stride, offset off) is in[elem(g)], its result goes to
+// out[elem(g)]; segments of `period` points (nd == 0: the identity map over
+// `period` points); offsets / nseg / sums: CSR segments as launch_scan_csr
+// (the caller fills sums with the identity first).  Any operator flag and
+// DESC_EXCLUSIVE.  Workspace: scan_contig_ws of the point count.
+int32_t launch_scan_map(int32_t dtype, const void *in, void *out, int64_t off, const int64_t *ext,
+                        const int64_t *stride, int nd, int64_t period, const int64_t *offsets, int64_t nseg,
+                        void *sums, int32_t flags, void *ws, size_t ws_bytes, desc_stream_t s);
 
 // Copy over a common logical domain of `nd` dims: out[ostride . p] = in[istride . p].
 int32_t launch_copy_affine(const void *in, int64_t ioff, const int64_t *istride, void *out,

@@ -29,6 +29,7 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
 // Accumulators.  add1/add4 take elements, merge combines two partial
 // accumulators, value() gives the final sum.
 struct AccI32 {   // sum modulo 2^32
+  static constexpr bool kIndexed = false;
   uint32_t s;
   __device__ void init() { s = 0u; }
   __device__ void add1(int32_t x) { s += (uint32_t)x; }
@@ -40,6 +41,7 @@ struct AccI32 {   // sum modulo 2^32
 };
 
 struct AccF32 {   // plain FP32 sum, pairwise inside each vector
+  static constexpr bool kIndexed = false;
   float s;
   __device__ void init() { s = 0.f; }
   __device__ void add1(float x) { s = __fadd_rn(s, x); }
@@ -51,6 +53,7 @@ struct AccF32 {   // plain FP32 sum, pairwise inside each vector
 };
 
 struct AccKahan {  // compensated FP32 sum (Neumaier's variant of Kahan summation)
+  static constexpr bool kIndexed = false;
   float s, c;
   __device__ void init() { s = 0.f; c = 0.f; }
   __device__ void add1(float x) {
@@ -80,6 +83,7 @@ struct AccKahan {  // compensated FP32 sum (Neumaier's variant of Kahan summatio
 // fmaxf / fminf, which ignore a NaN operand.
 template <class T, bool MAX>
 struct AccExt {
+  static constexpr bool kIndexed = false;
   T v;
   __device__ static T ident() {
     if constexpr (std::is_same<T, float>::value) return MAX ? -__int_as_float(0x7f800000) : __int_as_float(0x7f800000);
@@ -98,6 +102,97 @@ struct AccExt {
   __device__ uint2 pack() const { return make_uint2(__builtin_bit_cast(uint32_t, v), 0u); }
   __device__ void unpack(uint2 q) { v = __builtin_bit_cast(T, q.x); }
 };
+
+// Product: int32 modulo 2^32 (exact), FP32 in FP32 arithmetic.
+template <class T>
+struct AccProd {
+  static constexpr bool kIndexed = false;
+  T v;
+  __device__ static T mul(T a, T b) {
+    if constexpr (std::is_same<T, float>::value) return __fmul_rn(a, b);
+    else return (T)((uint32_t)a * (uint32_t)b);
+  }
+  __device__ void init() { v = T(1); }
+  __device__ void add1(T x) { v = mul(v, x); }
+  template <class V4>
+  __device__ void add4(V4 q) { v = mul(v, mul(mul(q.x, q.y), mul(q.z, q.w))); }
+  __device__ void merge(const AccProd &o) { v = mul(v, o.v); }
+  __device__ void shfl_merge(int off) { AccProd o; o.v = __shfl_down_sync(0xffffffffu, v, off); merge(o); }
+  __device__ uint2 pack() const { return make_uint2(__builtin_bit_cast(uint32_t, v), 0u); }
+  __device__ void unpack(uint2 q) { v = __builtin_bit_cast(T, q.x); }
+};
+
+// Bitwise and / or / xor of int32 (OP 0 / 1 / 2).
+template <int OP>
+struct AccBits {
+  static constexpr bool kIndexed = false;
+  uint32_t v;
+  __device__ static uint32_t op(uint32_t a, uint32_t b) { return OP == 0 ? (a & b) : OP == 1 ? (a | b) : (a ^ b); }
+  __device__ void init() { v = OP == 0 ? 0xffffffffu : 0u; }
+  __device__ void add1(int32_t x) { v = op(v, (uint32_t)x); }
+  __device__ void add4(int4 q) { v = op(v, op(op((uint32_t)q.x, (uint32_t)q.y), op((uint32_t)q.z, (uint32_t)q.w))); }
+  __device__ void merge(const AccBits &o) { v = op(v, o.v); }
+  __device__ void shfl_merge(int off) { AccBits o; o.v = __shfl_down_sync(0xffffffffu, v, off); merge(o); }
+  __device__ uint2 pack() const { return make_uint2(v, 0u); }
+  __device__ void unpack(uint2 q) { v = q.x; }
+};
+
+// Arg-maximum / arg-minimum: the element index of the largest / smallest
+// value, the smallest index among equal values; FP32 NaNs lose to every
+// number (all NaN: the smallest index).  Index -1 is "no element" (the
+// identity), which loses to every element.  The winner does not depend on
+// the order of the merges.
+template <class T, bool MAX>
+__device__ __forceinline__ bool arg_better(T av, int32_t ai, T bv, int32_t bi) {
+  if (bi < 0) return ai >= 0;
+  if (ai < 0) return false;
+  if constexpr (std::is_same<T, float>::value) {
+    const bool an = av != av, bn = bv != bv;
+    if (an != bn) return bn;
+    if (an) return ai < bi;
+  }
+  if (av != bv) return MAX ? av > bv : av < bv;
+  return ai < bi;
+}
+template <class T, bool MAX>
+struct AccArg {
+  static constexpr bool kIndexed = true;
+  T v;
+  int32_t i;
+  __device__ void init() { v = T(0); i = -1; }
+  __device__ void take(T x, int32_t j) {
+    if (arg_better<T, MAX>(x, j, v, i)) { v = x; i = j; }
+  }
+  __device__ void add1_at(T x, int64_t j) { take(x, (int32_t)j); }
+  template <class V4>
+  __device__ void add4_at(V4 q, int64_t j) {
+    take(q.x, (int32_t)j);
+    take(q.y, (int32_t)(j + 1));
+    take(q.z, (int32_t)(j + 2));
+    take(q.w, (int32_t)(j + 3));
+  }
+  __device__ void merge(const AccArg &o) { take(o.v, o.i); }
+  __device__ void shfl_merge(int off) {
+    AccArg o;
+    o.v = __shfl_down_sync(0xffffffffu, v, off);
+    o.i = __shfl_down_sync(0xffffffffu, i, off);
+    merge(o);
+  }
+  __device__ uint2 pack() const { return make_uint2(__builtin_bit_cast(uint32_t, v), (uint32_t)i); }
+  __device__ void unpack(uint2 q) { v = __builtin_bit_cast(T, q.x); i = (int32_t)q.y; }
+};
+
+// Elements with their element index (used by the arg accumulators only).
+template <class A, class T>
+__device__ __forceinline__ void acc_add1(A &a, T x, int64_t idx) {
+  if constexpr (A::kIndexed) a.add1_at(x, idx);
+  else a.add1(x);
+}
+template <class A, class V4>
+__device__ __forceinline__ void acc_add4(A &a, V4 q, int64_t idx) {
+  if constexpr (A::kIndexed) a.add4_at(q, idx);
+  else a.add4(q);
+}
 
 template <class A>
 __device__ __forceinline__ void warp_merge(A &a) {

@@ -14,7 +14,10 @@
 //  * affine: any other map; same chunk/partial structure, with every element
 //            index decoded from the remaining dims.
 // int32 sums wrap mod 2^32 (any order gives the same bits); FP32 sums are
-// plain or compensated (Neumaier) FP32.
+// plain or compensated (Neumaier) FP32.  Other operators (maximum, minimum,
+// product, bitwise and / or / xor, arg-maximum / arg-minimum) run through
+// the same kernels with their accumulator; the arg accumulators also take
+// each element's index in the base array and write that index (int32).
 #include <algorithm>
 
 #include <type_traits>
@@ -55,10 +58,25 @@ __device__ __forceinline__ float final_value(const AccF32 &a) { return a.s; }
 template <>
 __device__ __forceinline__ float final_value(const AccKahan &a) { return __fadd_rn(a.s, a.c); }
 
+template <class A>
+struct IsArg : std::false_type {};
+template <class T, bool MAX>
+struct IsArg<AccArg<T, MAX>> : std::true_type {};
+template <class A>
+struct IsPlainValue : std::false_type {};   // accumulators that hold the result in .v
+template <class T, bool MAX>
+struct IsPlainValue<AccExt<T, MAX>> : std::true_type {};
+template <class T>
+struct IsPlainValue<AccProd<T>> : std::true_type {};
+template <int OP>
+struct IsPlainValue<AccBits<OP>> : std::true_type {};
+
 template <class A, class T>
 __device__ __forceinline__ void store_out(T *out, int64_t o, const A &a) {
-  if constexpr (std::is_same<A, AccExt<T, true>>::value || std::is_same<A, AccExt<T, false>>::value)
-    out[o] = a.v;
+  if constexpr (IsArg<A>::value)
+    reinterpret_cast<int32_t *>(out)[o] = a.i;          // the winner's element index
+  else if constexpr (IsPlainValue<A>::value)
+    out[o] = __builtin_bit_cast(T, a.v);
   else
     out[o] = final_value(a);
 }
@@ -135,7 +153,8 @@ __device__ __forceinline__ void reduce_runs_block(const T *__restrict__ in, int6
   using V = typename Vec<T>::type;
   __shared__ A sh[kThreads / 32];
   const int64_t o = blk / chunks, c = blk % chunks;
-  const T *p = in + start + o * seg_stride;
+  const int64_t e0 = start + o * seg_stride;            // element index of the run's first element
+  const T *p = in + e0;
   const int64_t mis = (reinterpret_cast<uintptr_t>(p) & 15) / sizeof(T);
   const int64_t head = std::min<int64_t>(len, mis ? 4 - mis : 0);
   const int64_t nvec = (len - head) / 4;
@@ -143,6 +162,7 @@ __device__ __forceinline__ void reduce_runs_block(const T *__restrict__ in, int6
   A a;
   a.init();
   const V *pv = reinterpret_cast<const V *>(p + head);
+  const int64_t ev = e0 + head;                        // element index of vector 0
   // The run's vectors in stripes of kUnroll x kThreads; CTA c takes stripes
   // c, c + chunks, ... so that the CTAs of a run read neighbouring stripes
   // at the same time (DRAM rows stay open across the GPU) rather than each
@@ -155,12 +175,13 @@ __device__ __forceinline__ void reduce_runs_block(const T *__restrict__ in, int6
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) x[u] = ld_vec<NC>(pv + b + u * kThreads + threadIdx.x);
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) a.add4(x[u]);
+    for (int u = 0; u < kUnroll; ++u) acc_add4(a, x[u], ev + 4 * (b + u * kThreads + threadIdx.x));
   }
   if (b < nvec)                                        // the last, partial stripe
-    for (int64_t i = b + threadIdx.x; i < nvec; i += kThreads) a.add4(ld_vec<NC>(pv + i));
-  if (c == 0 && threadIdx.x < head) a.add1(p[threadIdx.x]);
-  if (c == chunks - 1 && threadIdx.x < tail) a.add1(p[head + 4 * nvec + threadIdx.x]);
+    for (int64_t i = b + threadIdx.x; i < nvec; i += kThreads) acc_add4(a, ld_vec<NC>(pv + i), ev + 4 * i);
+  if (c == 0 && threadIdx.x < head) acc_add1(a, p[threadIdx.x], e0 + threadIdx.x);
+  if (c == chunks - 1 && threadIdx.x < tail)
+    acc_add1(a, p[head + 4 * nvec + threadIdx.x], e0 + head + 4 * nvec + threadIdx.x);
   block_merge<A, kThreads>(a, sh);
   finish_chunk<A, T>(a, sh, o, c, chunks, out, partials, counters);
 }
@@ -206,10 +227,11 @@ __global__ void __launch_bounds__(kThreads) reduce_short_kernel(
   const int64_t ngroups = int64_t(gridDim.x) * (kThreads / GROUP);
   const int lane = threadIdx.x % GROUP;
   for (int64_t o = gid / GROUP; o < nout; o += ngroups) {
-    const T *p = in + start + o * seg_stride;
+    const int64_t e0 = start + o * seg_stride;
+    const T *p = in + e0;
     A a;
     a.init();
-    for (int64_t j = lane; j < len; j += GROUP) a.add1(p[j]);
+    for (int64_t j = lane; j < len; j += GROUP) acc_add1(a, p[j], e0 + j);
     if (GROUP == 32) warp_merge(a);
     if (lane == 0) store_out<A, T>(out, o, a);
   }
@@ -254,9 +276,11 @@ __global__ void __launch_bounds__(kThreads) reduce_affine_kernel(
     for (int64_t s0 = c * kStripe; s0 < qend; s0 += chunks * kStripe) {
       const int64_t q0 = s0 + 4 * threadIdx.x;
       V4 v[U];
+      int64_t ei[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int64_t q = q0 + int64_t(u) * 4 * kThreads;
+        ei[u] = 0;
         if (q < qend) {
           int64_t e = base;
           uint32_t t = (uint32_t)q;
@@ -266,12 +290,13 @@ __global__ void __launch_bounds__(kThreads) reduce_affine_kernel(
             t = qd;
           }
           e += int64_t(t) * args.rest_st[0];
+          ei[u] = e;
           v[u] = __ldcs(reinterpret_cast<const V4 *>(in + e));
         }
       }
 #pragma unroll
       for (int u = 0; u < U; ++u)
-        if (q0 + int64_t(u) * 4 * kThreads < qend) a.add4(v[u]);
+        if (q0 + int64_t(u) * 4 * kThreads < qend) acc_add4(a, v[u], ei[u]);
     }
   } else
   for (int64_t q = c * chunk_len + threadIdx.x; q < q1; q += kThreads) {
@@ -291,7 +316,7 @@ __global__ void __launch_bounds__(kThreads) reduce_affine_kernel(
         t /= args.rest_ext[d];
       }
     }
-    a.add1(in[e]);
+    acc_add1(a, in[e], e);
   }
   block_merge<A, kThreads>(a, sh);
   finish_chunk<A, T>(a, sh, o, c, chunks, out, partials, counters);
@@ -406,31 +431,56 @@ size_t reduce_segments_ws(int32_t /*dtype*/, int64_t len, int64_t nout) { return
 
 int reduce_candidates() { return kNumCands; }
 
+namespace {
+template <class A, class T>
+struct AccTag {
+  using Acc = A;
+  using Elem = T;
+};
+
+// Calls f(AccTag<accumulator, element type>{}) for the operator in `flags`
+// (at most one operator flag; none: the sum, DESC_KAHAN: the compensated sum).
+template <class F>
+int32_t with_accumulator(int32_t dtype, int32_t flags, F &&f) {
+  const int32_t op = flags & kOperatorFlags;
+  if (dtype == DESC_I32) {
+    switch (op) {
+      case DESC_MAX: return f(AccTag<AccExt<int32_t, true>, int32_t>{});
+      case DESC_MIN: return f(AccTag<AccExt<int32_t, false>, int32_t>{});
+      case DESC_PROD: return f(AccTag<AccProd<int32_t>, int32_t>{});
+      case DESC_AND: return f(AccTag<AccBits<0>, int32_t>{});
+      case DESC_OR: return f(AccTag<AccBits<1>, int32_t>{});
+      case DESC_XOR: return f(AccTag<AccBits<2>, int32_t>{});
+      case DESC_ARGMAX: return f(AccTag<AccArg<int32_t, true>, int32_t>{});
+      case DESC_ARGMIN: return f(AccTag<AccArg<int32_t, false>, int32_t>{});
+      case 0:
+      case DESC_KAHAN: return f(AccTag<AccI32, int32_t>{});   // int32 sums are exact
+      default: return DESC_ERR_INVALID_ARG;
+    }
+  }
+  switch (op) {
+    case DESC_MAX: return f(AccTag<AccExt<float, true>, float>{});
+    case DESC_MIN: return f(AccTag<AccExt<float, false>, float>{});
+    case DESC_PROD: return f(AccTag<AccProd<float>, float>{});
+    case DESC_ARGMAX: return f(AccTag<AccArg<float, true>, float>{});
+    case DESC_ARGMIN: return f(AccTag<AccArg<float, false>, float>{});
+    case DESC_KAHAN: return f(AccTag<AccKahan, float>{});
+    case 0: return f(AccTag<AccF32, float>{});
+    default: return DESC_ERR_INVALID_ARG;
+  }
+}
+}  // namespace
+
 int32_t launch_reduce_segments(int32_t dtype, const void *in, int64_t start, int64_t seg_stride,
                                int64_t len, int64_t nout, void *out, int32_t flags, void *ws,
                                size_t ws_bytes, desc_stream_t st, int cand) {
   cudaStream_t s = reinterpret_cast<cudaStream_t>(st);
-  if (flags & (DESC_MAX | DESC_MIN)) {
-    const bool mx = (flags & DESC_MAX) != 0;
-    if (dtype == DESC_I32) {
-      auto i = static_cast<const int32_t *>(in);
-      auto o = static_cast<int32_t *>(out);
-      return mx ? run_runs<AccExt<int32_t, true>, int32_t>(i, start, seg_stride, len, nout, o, ws, ws_bytes, s, cand)
-                : run_runs<AccExt<int32_t, false>, int32_t>(i, start, seg_stride, len, nout, o, ws, ws_bytes, s, cand);
-    }
-    auto i = static_cast<const float *>(in);
-    auto o = static_cast<float *>(out);
-    return mx ? run_runs<AccExt<float, true>, float>(i, start, seg_stride, len, nout, o, ws, ws_bytes, s, cand)
-              : run_runs<AccExt<float, false>, float>(i, start, seg_stride, len, nout, o, ws, ws_bytes, s, cand);
-  }
-  if (dtype == DESC_I32)
-    return run_runs<AccI32, int32_t>(static_cast<const int32_t *>(in), start, seg_stride, len, nout,
-                                     static_cast<int32_t *>(out), ws, ws_bytes, s, cand);
-  if (flags & DESC_KAHAN)
-    return run_runs<AccKahan, float>(static_cast<const float *>(in), start, seg_stride, len, nout,
-                                     static_cast<float *>(out), ws, ws_bytes, s, cand);
-  return run_runs<AccF32, float>(static_cast<const float *>(in), start, seg_stride, len, nout,
-                                 static_cast<float *>(out), ws, ws_bytes, s, cand);
+  return with_accumulator(dtype, flags, [&](auto tag) {
+    using A = typename decltype(tag)::Acc;
+    using T = typename decltype(tag)::Elem;
+    return run_runs<A, T>(static_cast<const T *>(in), start, seg_stride, len, nout, static_cast<T *>(out), ws,
+                          ws_bytes, s, cand);
+  });
 }
 
 size_t reduce_affine_ws(int64_t n_rest, int64_t nout) {
@@ -440,27 +490,11 @@ size_t reduce_affine_ws(int64_t n_rest, int64_t nout) {
 int32_t launch_reduce_affine(int32_t dtype, const void *in, const Plan &p, void *out, int32_t flags,
                              void *ws, size_t ws_bytes, desc_stream_t st) {
   cudaStream_t s = reinterpret_cast<cudaStream_t>(st);
-  if (flags & (DESC_MAX | DESC_MIN)) {
-    const bool mx = (flags & DESC_MAX) != 0;
-    if (dtype == DESC_I32) {
-      auto i = static_cast<const int32_t *>(in);
-      auto o = static_cast<int32_t *>(out);
-      return mx ? run_affine<AccExt<int32_t, true>, int32_t>(i, p, o, ws, ws_bytes, s)
-                : run_affine<AccExt<int32_t, false>, int32_t>(i, p, o, ws, ws_bytes, s);
-    }
-    auto i = static_cast<const float *>(in);
-    auto o = static_cast<float *>(out);
-    return mx ? run_affine<AccExt<float, true>, float>(i, p, o, ws, ws_bytes, s)
-              : run_affine<AccExt<float, false>, float>(i, p, o, ws, ws_bytes, s);
-  }
-  if (dtype == DESC_I32)
-    return run_affine<AccI32, int32_t>(static_cast<const int32_t *>(in), p,
-                                       static_cast<int32_t *>(out), ws, ws_bytes, s);
-  if (flags & DESC_KAHAN)
-    return run_affine<AccKahan, float>(static_cast<const float *>(in), p, static_cast<float *>(out),
-                                       ws, ws_bytes, s);
-  return run_affine<AccF32, float>(static_cast<const float *>(in), p, static_cast<float *>(out), ws,
-                                   ws_bytes, s);
+  return with_accumulator(dtype, flags, [&](auto tag) {
+    using A = typename decltype(tag)::Acc;
+    using T = typename decltype(tag)::Elem;
+    return run_affine<A, T>(static_cast<const T *>(in), p, static_cast<T *>(out), ws, ws_bytes, s);
+  });
 }
 
 int32_t launch_split_reduce_transpose(int32_t dtype, const void *in, int64_t start, int64_t seg_stride,
@@ -507,9 +541,11 @@ __global__ void fill_u32_kernel(uint32_t *out, int64_t n, uint32_t v) {
 int32_t fill_identity(void *out, int64_t count, int32_t dtype, int32_t flags, desc_stream_t st) {
   cudaStream_t s = reinterpret_cast<cudaStream_t>(st);
   if (count <= 0) return DESC_OK;
-  uint32_t v = 0u;
+  uint32_t v = 0u;                                                          // sum, or, xor
   if (flags & DESC_MAX) v = dtype == DESC_I32 ? 0x80000000u : 0xff800000u;   // INT32_MIN, -inf
   if (flags & DESC_MIN) v = dtype == DESC_I32 ? 0x7fffffffu : 0x7f800000u;   // INT32_MAX, +inf
+  if (flags & DESC_PROD) v = dtype == DESC_I32 ? 1u : 0x3f800000u;           // 1, 1.0f
+  if (flags & (DESC_AND | DESC_ARGMAX | DESC_ARGMIN)) v = 0xffffffffu;       // all ones; index -1
   if (v == 0u) return cudaMemsetAsync(out, 0, size_t(count) * 4, s) == cudaSuccess ? DESC_OK : DESC_ERR_CUDA;
   const int64_t blocks = std::min<int64_t>((count + 255) / 256, 4096);
   fill_u32_kernel<<<(unsigned)blocks, 256, 0, s>>>(static_cast<uint32_t *>(out), count, v);

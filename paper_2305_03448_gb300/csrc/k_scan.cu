@@ -24,6 +24,7 @@
 // the device status word, and its CTA leaves without writing.
 #include <algorithm>
 #include <atomic>
+#include <type_traits>
 
 #include "k_common.cuh"
 
@@ -130,15 +131,45 @@ struct SumOp {                          // sum: int32 modulo 2^32, FP32 with com
   __device__ static C unpack(unsigned long long w) { return desc::unpack<T>(w); }
 };
 
-template <class T, bool MAX>
-struct ExtOp {                          // maximum / minimum; FP32 ignores NaN operands (IEEE maxNum / minNum)
-  __device__ static T id();
-  __device__ static T comb(T a, T b);
+// Value operators other than the sum: maximum, minimum (FP32 ignores NaN
+// operands, IEEE maxNum / minNum), product (int32 modulo 2^32, FP32 in FP32),
+// bitwise and / or / xor (int32).  Carries are plain values.
+enum ValKind { kMaxOp = 0, kMinOp = 1, kProdOp = 2, kAndOp = 3, kOrOp = 4, kXorOp = 5 };
+template <class T, int K>
+struct ValOp {
+  __device__ static T id() {
+    if constexpr (std::is_same<T, float>::value) {
+      if (K == kMaxOp) return -__int_as_float(0x7f800000);
+      if (K == kMinOp) return __int_as_float(0x7f800000);
+      return 1.0f;                                      // product
+    } else {
+      if (K == kMaxOp) return INT32_MIN;
+      if (K == kMinOp) return INT32_MAX;
+      if (K == kProdOp) return 1;
+      if (K == kAndOp) return -1;
+      return 0;                                         // or, xor
+    }
+  }
+  __device__ static T comb(T a, T b) {
+    if constexpr (std::is_same<T, float>::value) {
+      if (K == kMaxOp) return fmaxf(a, b);
+      if (K == kMinOp) return fminf(a, b);
+      return __fmul_rn(a, b);
+    } else {
+      const uint32_t x = (uint32_t)a, y = (uint32_t)b;
+      if (K == kMaxOp) return max(a, b);
+      if (K == kMinOp) return min(a, b);
+      if (K == kProdOp) return (int32_t)(x * y);
+      if (K == kAndOp) return (int32_t)(x & y);
+      if (K == kOrOp) return (int32_t)(x | y);
+      return (int32_t)(x ^ y);
+    }
+  }
   struct C {
     T v;
-    __device__ static C zero() { return {ExtOp::id()}; }
+    __device__ static C zero() { return {ValOp::id()}; }
     __device__ static C of(T x) { return {x}; }
-    __device__ C plus(const C &o) const { return {ExtOp::comb(v, o.v)}; }
+    __device__ C plus(const C &o) const { return {ValOp::comb(v, o.v)}; }   // commutative operators
     __device__ C shfl_down(int off) const { return {__shfl_down_sync(0xffffffffu, v, off)}; }
   };
   __device__ static T apply(T x, const C &c) { return comb(c.v, x); }
@@ -147,22 +178,8 @@ struct ExtOp {                          // maximum / minimum; FP32 ignores NaN o
   }
   __device__ static C unpack(unsigned long long w) { return {__builtin_bit_cast(T, (uint32_t)w)}; }
 };
-template <>
-__device__ __forceinline__ int32_t ExtOp<int32_t, true>::id() { return INT32_MIN; }
-template <>
-__device__ __forceinline__ int32_t ExtOp<int32_t, false>::id() { return INT32_MAX; }
-template <>
-__device__ __forceinline__ float ExtOp<float, true>::id() { return -__int_as_float(0x7f800000); }
-template <>
-__device__ __forceinline__ float ExtOp<float, false>::id() { return __int_as_float(0x7f800000); }
-template <>
-__device__ __forceinline__ int32_t ExtOp<int32_t, true>::comb(int32_t a, int32_t b) { return max(a, b); }
-template <>
-__device__ __forceinline__ int32_t ExtOp<int32_t, false>::comb(int32_t a, int32_t b) { return min(a, b); }
-template <>
-__device__ __forceinline__ float ExtOp<float, true>::comb(float a, float b) { return fmaxf(a, b); }
-template <>
-__device__ __forceinline__ float ExtOp<float, false>::comb(float a, float b) { return fminf(a, b); }
+template <class T, bool MAX>
+using ExtOp = ValOp<T, MAX ? kMaxOp : kMinOp>;
 
 template <class O>
 __device__ __forceinline__ void publish(TileState *st, unsigned long long status, const typename O::C &c) {
@@ -653,6 +670,313 @@ __global__ void __launch_bounds__(kThreads + 32) scan_kernel(const T *in, T *out
   }
 }
 
+// ---- the scan through a lowered map, and the arg operators ----------------
+// One CTA per tile of kMapTile logical points (tiles in ticket order).  The
+// CTA loads point g of the tile from in[map(g)] (striped, so a warp reads
+// consecutive points), stages the tile in shared memory, scans it (each
+// thread 16 consecutive points, warp shuffles, warp totals), publishes and
+// looks back as above, and stores point g's result to out[map(g)].  With
+// the identity map this is a plain (or segmented) scan; with any other
+// lowered map it scans a view in one pass, gathering in its loads and
+// scattering in its stores.  Element states are values, or for the arg
+// operators (value, position) pairs whose stored result is the base-array
+// index of the position.
+constexpr int kMapThreads = 256, kMapItems = 16, kMapTile = kMapThreads * kMapItems;
+static_assert(kMapTile == kScanSubTile, "workspace tiles count kScanSubTile elements");
+
+struct MapArgs {
+  int32_t nd;                       // dims of the canonical map; 0: element = off + g
+  int32_t fast;                     // fewer than 2^32 points: 32-bit decoding
+  int64_t off;
+  int64_t ext[DESC_MAX_DIMS];
+  int64_t st[DESC_MAX_DIMS];
+  FastDiv div[DESC_MAX_DIMS];
+};
+
+// Maps of two or more dims: decoded dim by dim (out of line: the kernel
+// inlines only the one-dim case).
+__device__ __noinline__ int64_t map_elem_dims(const MapArgs &m, int64_t g) {
+  int64_t e = m.off;
+  if (m.fast) {
+    uint32_t t = (uint32_t)g;
+    for (int d = m.nd - 1; d > 0; --d) {
+      const uint32_t q = fast_div(t, m.div[d]);
+      e += int64_t(t - q * m.div[d].d) * m.st[d];
+      t = q;
+    }
+    return e + int64_t(t) * m.st[0];
+  }
+  int64_t t = g;
+  for (int d = m.nd - 1; d >= 0; --d) {
+    e += (t % m.ext[d]) * m.st[d];
+    t /= m.ext[d];
+  }
+  return e;
+}
+__device__ __forceinline__ int64_t map_elem(const MapArgs &m, int64_t g) {
+  if (m.nd <= 1) return m.off + (m.nd ? g * m.st[0] : g);
+  return map_elem_dims(m, g);
+}
+
+// Element-state layer of the map kernel for the value operators (the state
+// is the value; make() takes the value and its element index) ...
+template <class T, class O>
+struct ValueStates {
+  using Op = O;
+  using E = T;
+  using C = typename O::C;
+  __device__ static E make(T x, int64_t) { return x; }
+  __device__ static E eid() { return O::id(); }
+  __device__ static E ecomb(E a, E b) { return O::comb(a, b); }   // a before b
+  __device__ static E shfl_up(E e, int off) { return __shfl_up_sync(0xffffffffu, e, off); }
+  __device__ static E shfl(E e, int src) { return __shfl_sync(0xffffffffu, e, src); }
+  __device__ static E apply(E e, const C &c) { return O::apply(e, c); }
+  __device__ static E of_carry(const C &c) { return O::apply(O::id(), c); }
+  __device__ static C carry(E e) { return C::of(e); }
+  __device__ static uint32_t out_bits(E e, const MapArgs &) { return __builtin_bit_cast(uint32_t, e); }
+};
+
+// ... and for the arg operators: (value, element index in the base array),
+// index -1 = none; the better of two states by arg_better (ties: the smaller
+// element index, whatever order the map visits the elements in).
+template <class T, bool MAX>
+struct ArgStates {
+  struct E {
+    T v;
+    int32_t i;                      // element index, -1: none
+  };
+  struct Op;
+  struct C {
+    E e;
+    __device__ static C zero() { return {{T(0), -1}}; }
+    __device__ static C of(E x) { return {x}; }
+    __device__ C plus(const C &o) const;
+    __device__ C shfl_down(int off) const {
+      return {{__shfl_down_sync(0xffffffffu, e.v, off), __shfl_down_sync(0xffffffffu, e.i, off)}};
+    }
+  };
+  struct Op {
+    using C = ArgStates::C;
+    // 30 bits of element index: 0x3FFFFFFF stands for none.
+    __device__ static unsigned long long pack(unsigned long long st, const C &c) {
+      const uint32_t pos = c.e.i < 0 ? 0x3FFFFFFFu : (uint32_t)c.e.i;
+      return (st << 62) | ((unsigned long long)pos << 32) | (unsigned long long)__builtin_bit_cast(uint32_t, c.e.v);
+    }
+    __device__ static C unpack(unsigned long long w) {
+      const uint32_t pos = (uint32_t)(w >> 32) & 0x3FFFFFFFu;
+      return {{__builtin_bit_cast(T, (uint32_t)w), pos == 0x3FFFFFFFu ? -1 : (int32_t)pos}};
+    }
+  };
+  __device__ static E better(E a, E b) { return arg_better<T, MAX>(a.v, a.i, b.v, b.i) ? a : b; }
+  __device__ static E make(T x, int64_t elem) { return {x, (int32_t)elem}; }
+  __device__ static E eid() { return {T(0), -1}; }
+  __device__ static E ecomb(E a, E b) { return better(a, b); }
+  __device__ static E shfl_up(E e, int off) {
+    return {__shfl_up_sync(0xffffffffu, e.v, off), __shfl_up_sync(0xffffffffu, e.i, off)};
+  }
+  __device__ static E shfl(E e, int src) {
+    return {__shfl_sync(0xffffffffu, e.v, src), __shfl_sync(0xffffffffu, e.i, src)};
+  }
+  __device__ static E apply(E e, const C &c) { return better(c.e, e); }
+  __device__ static E of_carry(const C &c) { return c.e; }
+  __device__ static C carry(E e) { return {e}; }
+  __device__ static uint32_t out_bits(E e, const MapArgs &) { return (uint32_t)e.i; }
+};
+template <class T, bool MAX>
+__device__ __forceinline__ typename ArgStates<T, MAX>::C ArgStates<T, MAX>::C::plus(const C &o) const {
+  return {ArgStates<T, MAX>::better(e, o.e)};
+}
+
+// Shared-memory slot of tile point r: one padding slot per 32 (4-byte
+// states) or 16 (8-byte states), so that thread t's 16 consecutive points
+// and a warp's 32 striped points both spread over the banks.
+template <class E>
+__device__ __forceinline__ int map_slot(int r) {
+  return sizeof(E) == 4 ? r + (r >> 5) : r + (r >> 4);
+}
+
+// mode: PLAIN, PERIODIC or CSR; excl: the exclusive form.
+template <class T, class S>
+__global__ void __launch_bounds__(kMapThreads) scan_map_kernel(const T *__restrict__ in, uint32_t *__restrict__ out,
+                                                               const MapArgs m, ScanArgs args, ScanWs *ws,
+                                                               TileState *states, int mode, int excl) {
+  using E = typename S::E;
+  using O = typename S::Op;
+  using CT = typename S::C;
+  constexpr int kSlots = kMapTile + kMapTile / (sizeof(E) == 4 ? 32 : 16);
+  __shared__ E sh[kSlots];
+  __shared__ unsigned sh_heads[kMapTile / 32];
+  __shared__ E sh_wval[kMapThreads / 32];
+  __shared__ int sh_wflag[kMapThreads / 32];
+  __shared__ CT sh_prefix;
+  __shared__ int64_t sh_tile, sh_seg0;
+  __shared__ int sh_ok;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) sh_tile = atomicAdd(&ws->ticket, 1u);
+  if (mode == CSR)
+    for (int i = tid; i < kMapTile / 32; i += kMapThreads) sh_heads[i] = 0u;
+  __syncthreads();
+  const int64_t tile = sh_tile, t0 = tile * kMapTile, n = args.n;
+  const int64_t tend = min(t0 + kMapTile, n);
+  const bool stall = args.debug && tile == 1;
+
+  // ---- striped loads through the map
+#pragma unroll
+  for (int j = 0; j < kMapItems; ++j) {
+    const int r = j * kMapThreads + tid;
+    const int64_t g = t0 + r;
+    E x = S::eid();
+    if (g < n) {
+      const int64_t e = map_elem(m, g);
+      x = S::make(in[e], e);
+    }
+    sh[map_slot<E>(r)] = x;
+  }
+  // ---- segment heads (CSR): boundaries offsets[q] in (t0, tend), and t0
+  if (mode == CSR) {
+    if (warp == 0) {
+      const int64_t s0 = find_segment(args.offsets, args.nseg, t0);
+      if (lane == 0) {
+        sh_seg0 = s0;
+        if (args.offsets[s0] == t0) atomicOr(&sh_heads[0], 1u);
+      }
+    }
+    __syncthreads();
+    for (int64_t q = sh_seg0 + 1 + tid; q <= args.nseg; q += kMapThreads) {
+      const int64_t b = args.offsets[q];
+      if (b >= tend) break;
+      if (b > t0) atomicOr(&sh_heads[(b - t0) >> 5], 1u << ((b - t0) & 31));
+    }
+  }
+  __syncthreads();
+  auto is_head = [&](int r) -> bool {
+    const int64_t g = t0 + r;
+    if (mode == PLAIN) return g == 0;
+    if (mode == PERIODIC) return g % args.period == 0;
+    return (sh_heads[r >> 5] >> (r & 31)) & 1u;
+  };
+
+  // ---- scan of the tile: 16 consecutive points per thread
+  const int r0 = tid * kMapItems;
+  E v[kMapItems];
+  unsigned hm = 0u;
+#pragma unroll
+  for (int i = 0; i < kMapItems; ++i) {
+    v[i] = sh[map_slot<E>(r0 + i)];
+    if (is_head(r0 + i)) hm |= 1u << i;
+  }
+#pragma unroll
+  for (int i = 1; i < kMapItems; ++i)
+    if (!((hm >> i) & 1u)) v[i] = S::ecomb(v[i - 1], v[i]);
+  int f = hm != 0u;
+  E a = v[kMapItems - 1];
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {             // warp scan, segmented operator
+    const E au = S::shfl_up(a, off);
+    const int fu = __shfl_up_sync(0xffffffffu, f, off);
+    if (lane >= off) {
+      if (!f) a = S::ecomb(au, a);
+      f |= fu;
+    }
+  }
+  if (lane == 31) {
+    sh_wval[warp] = a;
+    sh_wflag[warp] = f;
+  }
+  E ex = S::shfl_up(a, 1);
+  int exf = __shfl_up_sync(0xffffffffu, f, 1);
+  if (lane == 0) {
+    ex = S::eid();
+    exf = 0;
+  }
+  __syncthreads();
+  if (warp == 0) {                                     // scan of the warp totals
+    constexpr int kW = kMapThreads / 32;
+    E wa = lane < kW ? sh_wval[lane] : S::eid();
+    int wf = lane < kW ? sh_wflag[lane] : 0;
+#pragma unroll
+    for (int off = 1; off < kW; off <<= 1) {
+      const E au = S::shfl_up(wa, off);
+      const int fu = __shfl_up_sync(0xffffffffu, wf, off);
+      if (lane >= off) {
+        if (!wf) wa = S::ecomb(au, wa);
+        wf |= fu;
+      }
+    }
+    E we = S::shfl_up(wa, 1);
+    int wfe = __shfl_up_sync(0xffffffffu, wf, 1);
+    if (lane == 0) {
+      we = S::eid();
+      wfe = 0;
+    }
+    const E agg = S::shfl(wa, kW - 1);
+    const int aggf = __shfl_sync(0xffffffffu, wf, kW - 1);
+    __syncwarp();
+    if (lane < kW) {
+      sh_wval[lane] = we;
+      sh_wflag[lane] = wfe;
+    }
+    // ---- publish, and look back when a point of the tile needs the prefix
+    const bool first_head = is_head(0);
+    if (lane == 0 && !stall)
+      publish<O>(&states[tile], (tile == 0 || aggf) ? kStatIncl : kStatAgg, S::carry(agg));
+    CT prefix = CT::zero();
+    bool ok = true;
+    if (tile != 0 && !first_head) {
+      ok = look_back<O>(states, tile, ws, args.debug ? kDebugBudgetCycles : kBudgetCycles, prefix);
+      if (ok && lane == 0 && !stall && !aggf) publish<O>(&states[tile], kStatIncl, prefix.plus(S::carry(agg)));
+    }
+    if (lane == 0) {
+      sh_prefix = prefix;
+      sh_ok = ok ? 1 : 0;
+    }
+  }
+  __syncthreads();
+  if (!sh_ok) return;                                  // a wait gave up: write nothing
+  {
+    const E pv = sh_wval[warp];
+    const int pf = sh_wflag[warp];
+    if (!exf) ex = S::ecomb(pv, ex);
+    exf |= pf;                                         // this thread's prefix within the tile
+    const CT pre = sh_prefix;
+#pragma unroll
+    for (int i = 0; i < kMapItems; ++i)
+      if ((hm & ((2u << i) - 1u)) == 0u) {             // no head in this thread up to item i
+        E x = S::ecomb(ex, v[i]);
+        v[i] = exf ? x : S::apply(x, pre);
+      }
+  }
+  __syncthreads();                                     // every thread has read its inputs
+#pragma unroll
+  for (int i = 0; i < kMapItems; ++i) sh[map_slot<E>(r0 + i)] = v[i];
+  __syncthreads();
+
+  // ---- striped stores through the map (the exclusive form shifts by one)
+  const E before = S::of_carry(sh_prefix);             // everything before the tile
+#pragma unroll
+  for (int j = 0; j < kMapItems; ++j) {
+    const int r = j * kMapThreads + tid;
+    const int64_t g = t0 + r;
+    if (g >= n) break;
+    E e;
+    if (excl) e = is_head(r) ? S::eid() : (r == 0 ? before : sh[map_slot<E>(r - 1)]);
+    else e = sh[map_slot<E>(r)];
+    out[map_elem(m, g)] = S::out_bits(e, m);
+  }
+  // ---- CSR: totals of the non-empty segments that end in this tile (the
+  // empty ones hold the identity already)
+  if (mode == CSR && args.sums) {
+    uint32_t *sums = static_cast<uint32_t *>(args.sums);
+    for (int64_t q = sh_seg0 + 1 + tid; q <= args.nseg; q += kMapThreads) {
+      const int64_t b = args.offsets[q];
+      if (b > tend) break;
+      if (b <= t0 || args.offsets[q - 1] == b) continue;
+      sums[q - 1] = S::out_bits(sh[map_slot<E>((int)(b - 1 - t0))], m);
+    }
+  }
+}
+
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 constexpr int kWsTile = kSub;   // workspace is sized for the smallest tile
@@ -741,6 +1065,101 @@ int32_t launch_scan_contig(int32_t dtype, const void *in, void *out, int64_t n, 
   auto o = static_cast<float *>(out);
   return periodic ? run_scan<float, PERIODIC>(i, o, a, ws, ws_bytes, s, cand, flags)
                   : run_scan<float, PLAIN>(i, o, a, ws, ws_bytes, s, cand, flags);
+}
+
+namespace {
+
+template <class T, class S>
+struct StateTag {
+  using Elem = T;
+  using States = S;
+};
+
+// Calls f(StateTag<element type, state layer>{}) for the operator in flags.
+template <class F>
+int32_t with_states(int32_t dtype, int32_t flags, F &&f) {
+  const int32_t op = flags & kOperatorFlags;
+  if (dtype == DESC_I32) {
+    using T = int32_t;
+    switch (op) {
+      case 0: return f(StateTag<T, ValueStates<T, SumOp<T>>>{});
+      case DESC_MAX: return f(StateTag<T, ValueStates<T, ValOp<T, kMaxOp>>>{});
+      case DESC_MIN: return f(StateTag<T, ValueStates<T, ValOp<T, kMinOp>>>{});
+      case DESC_PROD: return f(StateTag<T, ValueStates<T, ValOp<T, kProdOp>>>{});
+      case DESC_AND: return f(StateTag<T, ValueStates<T, ValOp<T, kAndOp>>>{});
+      case DESC_OR: return f(StateTag<T, ValueStates<T, ValOp<T, kOrOp>>>{});
+      case DESC_XOR: return f(StateTag<T, ValueStates<T, ValOp<T, kXorOp>>>{});
+      case DESC_ARGMAX: return f(StateTag<T, ArgStates<T, true>>{});
+      case DESC_ARGMIN: return f(StateTag<T, ArgStates<T, false>>{});
+      default: return DESC_ERR_INVALID_ARG;
+    }
+  }
+  using T = float;
+  switch (op) {
+    case 0: return f(StateTag<T, ValueStates<T, SumOp<T>>>{});
+    case DESC_MAX: return f(StateTag<T, ValueStates<T, ValOp<T, kMaxOp>>>{});
+    case DESC_MIN: return f(StateTag<T, ValueStates<T, ValOp<T, kMinOp>>>{});
+    case DESC_PROD: return f(StateTag<T, ValueStates<T, ValOp<T, kProdOp>>>{});
+    case DESC_ARGMAX: return f(StateTag<T, ArgStates<T, true>>{});
+    case DESC_ARGMIN: return f(StateTag<T, ArgStates<T, false>>{});
+    default: return DESC_ERR_INVALID_ARG;
+  }
+}
+
+}  // namespace
+
+int32_t launch_scan_map(int32_t dtype, const void *in, void *out, int64_t off, const int64_t *ext,
+                        const int64_t *stride, int nd, int64_t period, const int64_t *offsets, int64_t nseg,
+                        void *sums, int32_t flags, void *ws, size_t ws_bytes, desc_stream_t st) {
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(st);
+  MapArgs m{};
+  int64_t n = 1;
+  for (int i = 0; i < nd; ++i) {
+    m.ext[i] = ext[i];
+    m.st[i] = stride[i];
+    n *= ext[i];
+  }
+  if (nd == 0) n = period;                             // the identity map over `period` points
+  if (n == 0) return DESC_OK;
+  m.off = off;
+  int64_t *sets[1] = {m.st};
+  m.nd = nd ? canon_dims(nd, m.ext, sets, 1) : 0;
+  if (nd && m.nd == 0) {                               // a single point
+    m.nd = 1;
+    m.ext[0] = 1;
+    m.st[0] = 0;
+  }
+  bool fast = n < (int64_t(1) << 32);
+  for (int i = 0; i < m.nd; ++i) {
+    fast = fast && m.ext[i] <= (int64_t(1) << 31);
+    if (fast) m.div[i] = make_fastdiv((uint32_t)m.ext[i]);
+  }
+  m.fast = fast ? 1 : 0;
+  const int64_t ntiles = (n + kMapTile - 1) / kMapTile;
+  const size_t need = align256(sizeof(ScanWs)) + size_t(ntiles) * sizeof(TileState);
+  if (!ws || ws_bytes < need) return DESC_ERR_WORKSPACE;
+  if (ntiles >= (int64_t(1) << 31)) return DESC_ERR_UNSUPPORTED;
+  ScanArgs a{};
+  a.n = n;
+  a.period = period > 0 ? period : n;
+  a.offsets = offsets;
+  a.nseg = nseg;
+  a.sums = sums;
+  a.debug = (flags & DESC_DEBUG_STALL_TILE) ? 1 : 0;
+  const int mode = offsets ? CSR : (a.period < n ? PERIODIC : PLAIN);
+  const int excl = (flags & DESC_EXCLUSIVE) ? 1 : 0;
+  DESC_CUDA_TRY(cudaMemsetAsync(ws, 0, need, s));
+  ScanWs *w = static_cast<ScanWs *>(ws);
+  TileState *ts = reinterpret_cast<TileState *>(static_cast<char *>(ws) + align256(sizeof(ScanWs)));
+  return with_states(dtype, flags, [&](auto tag) {
+    using T = typename decltype(tag)::Elem;
+    using S = typename decltype(tag)::States;
+    scan_map_kernel<T, S><<<(unsigned)ntiles, kMapThreads, 0, s>>>(static_cast<const T *>(in),
+                                                                    static_cast<uint32_t *>(out), m, a, w, ts,
+                                                                    mode, excl);
+    DESC_CUDA_TRY(cudaGetLastError());
+    return DESC_OK;
+  });
 }
 
 size_t scan_csr_ws(int64_t n) { return scan_contig_ws(DESC_F32, n); }

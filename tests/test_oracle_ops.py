@@ -216,3 +216,112 @@ def test_segmented_operators_match_per_segment_definition():
                 assert np.array_equal(sc[a:b], want)
                 if b > a and not excl:
                     assert tot[s] == sc[b - 1]          # total = last inclusive value
+
+
+# ---- pins of the caller-chosen operators (product, bitwise, arg-max / arg-min)
+def test_int_product_closed_forms():
+    # powers of two: 2^(sum k) modulo 2^32
+    ks = [3, 5, 7, 11, 2, 1]
+    x = np.array([1 << k for k in ks], np.int32)
+    got = O.reduce_op(x, [6], [], V.GRID, "prod")[0]
+    assert int(got) == (1 << 29)
+    assert int(O.reduce_op(np.array([65536, 65536], np.int32), [2], [], V.GRID, "prod")[0]) == 0
+    assert int(O.reduce_op(np.full(7, -1, np.int32), [7], [], V.GRID, "prod")[0]) == -1
+    # 3^20 modulo 2^32 through Python's modular pow, as a signed int32
+    p = pow(3, 20, 1 << 32)
+    assert int(O.reduce_op(np.full(20, 3, np.int32), [20], [], V.GRID, "prod")[0]) == (p - (1 << 32) if p >= 1 << 31 else p)
+    # the scan's prefixes are the powers
+    sc, _ = O.scan_op(np.full(20, 3, np.int32), np.zeros(20, np.int32), [20], [], V.GRID, "prod")
+    want = [pow(3, i + 1, 1 << 32) for i in range(20)]
+    assert [int(v) & 0xFFFFFFFF for v in sc] == want
+
+
+def test_float_product_against_exact_fractions():
+    from fractions import Fraction
+    rng = np.random.default_rng(5)
+    x = (1.0 + rng.uniform(-1, 1, 300) * 2.0 ** -6).astype(np.float32)
+    exact = Fraction(1)
+    for v in x.tolist():
+        exact *= Fraction(v)
+    got = O.reduce_op(x, [300], [], V.GRID, "prod")[0]
+    assert abs(Fraction(float(got)) - exact) <= Fraction(299, 1 << 53) * abs(exact) * 2
+    assert O.reduce_op(np.array([2, 0.5, 4, 0.25], np.float32), [4], [], V.GRID, "prod")[0] == 1.0
+    u = 2.0 ** -24
+    assert O.prod_tolerance(1) == 0.0 and abs(O.prod_tolerance(3) - 2 * u) <= 8 * u * u
+
+
+def test_bitwise_closed_forms_and_brute_force():
+    import functools
+    import operator
+    xs = np.arange(64, dtype=np.int32)                   # xor of 0 .. 4k - 1 is 0
+    assert int(O.reduce_op(xs, [64], [], V.GRID, "xor")[0]) == 0
+    pw = np.array([1 << k for k in (0, 3, 9, 30)], np.int32)
+    assert int(O.reduce_op(pw, [4], [], V.GRID, "or")[0]) == int(pw.astype(np.int64).sum())
+    assert int(O.reduce_op(np.array([0x5A5A5A5A, ~0x5A5A5A5A], np.int32), [2], [], V.GRID, "and")[0]) == 0
+    rng = np.random.default_rng(7)
+    x = rng.integers(-2 ** 31, 2 ** 31, 50).astype(np.int32)
+    for op, f in (("and", operator.and_), ("or", operator.or_), ("xor", operator.xor)):
+        sc, _ = O.scan_op(x, np.zeros(50, np.int32), [50], [], V.GRID, op)
+        for p in range(50):
+            assert int(sc[p]) == functools.reduce(f, [int(v) for v in x[:p + 1]])
+        ex, _ = O.scan_op(x, np.zeros(50, np.int32), [50], [], V.GRID, op, True)
+        assert int(ex[0]) == O.identity(op, True) and np.array_equal(ex[1:], sc[:-1])
+
+
+def _brute_arg(vals, idx, op):
+    """Brute force: among the non-NaN values the best, then the smallest
+    index (all NaN: the smallest index)."""
+    pairs = [(float(v), int(i)) for v, i in zip(vals, idx)]
+    if not pairs:
+        return -1
+    num = [p for p in pairs if not math.isnan(p[0])] or [(0.0, p[1]) for p in pairs]
+    if op == "argmax":
+        return max(num, key=lambda p: (p[0], -p[1]))[1]
+    return min(num, key=lambda p: (p[0], p[1]))[1]
+
+
+def test_arg_operators_brute_force():
+    rng = np.random.default_rng(9)
+    for trial in range(40):
+        n = int(rng.integers(1, 40))
+        x = rng.integers(-3, 4, n).astype(np.float32)    # many ties
+        if trial % 3 == 0:
+            x[rng.integers(0, n, 3)] = np.nan
+        if trial % 5 == 0:
+            x[:] = np.nan
+        for op in ("argmax", "argmin"):
+            assert int(O.reduce_op(x, [n], [], V.GRID, op)[0]) == _brute_arg(x, range(n), op)
+            # through a reversed view the indices stay base-array indices
+            assert int(O.reduce_op(x, [n], [("reverse", 0)], V.GRID, op)[0]) == _brute_arg(x, range(n), op)
+            sc, _ = O.scan_op(x, np.zeros(n, np.int32), [n], [], V.GRID, op)
+            rv, _ = O.scan_op(x, np.zeros(n, np.int32), [n], [("reverse", 0)], V.GRID, op)
+            for p in range(n):
+                assert int(sc[p]) == _brute_arg(x[:p + 1], range(p + 1), op)
+                # reversed: point p of the view is element n-1-p; its prefix is elements n-1-p .. n-1
+                assert int(rv[n - 1 - p]) == _brute_arg(x[n - 1 - p:], range(n - 1 - p, n), op)
+            ex, _ = O.scan_op(x, np.zeros(n, np.int32), [n], [], V.GRID, op, True)
+            assert int(ex[0]) == -1 and np.array_equal(ex[1:], sc[:-1])
+    xi = np.array([4, 9, 9, -2, 9], np.int32)
+    assert int(O.reduce_op(xi, [5], [], V.GRID, "argmax")[0]) == 1
+    assert int(O.reduce_op(xi, [5], [], V.GRID, "argmin")[0]) == 3
+    assert int(O.reduce_op(np.array([0.0, -0.0], np.float32), [2], [], V.GRID, "argmin")[0]) == 0
+
+
+def test_new_operators_segmented_match_scans():
+    rng = np.random.default_rng(13)
+    L = rng.integers(0, 9, size=25)
+    off = np.concatenate([[0], np.cumsum(L)])
+    x = rng.integers(-4, 5, size=int(off[-1])).astype(np.int32)
+    for op in ("prod", "and", "or", "xor", "argmax", "argmin"):
+        for excl in (False, True):
+            sc, tot, _, _ = O.segmented_op(x, off, op, excl)
+            for s in range(25):
+                a, b = int(off[s]), int(off[s + 1])
+                if b == a:
+                    assert int(tot[s]) == O.identity(op, True)
+                    continue
+                want, _ = O.scan_op(x[a:b], np.zeros(b - a, np.int32), [b - a], [], V.GRID, op, excl)
+                if op.startswith("arg"):
+                    want = np.where(want >= 0, want + a, want)   # indices into the whole array
+                    assert int(tot[s]) == _brute_arg(x[a:b], range(a, b), op)
+                assert np.array_equal(sc[a:b], want)

@@ -6,14 +6,16 @@ array instead of a caller-provided workspace.
 
 Checked here through the C ABI: on two calls in a row its output matches
 desc_scan's (bit for bit for int32, within 1e-5 * sum_{q<=p} |x_q| for
-FP32), and a scan longer than the static scratch allows is refused without
-touching the output.  This file is collected last on purpose."""
+FP32) and the CPU oracle's; a view whose scan is not one contiguous run is
+refused, and so is a scan longer than the static scratch allows, both
+without touching the output.  This file is collected last on purpose."""
 import numpy as np
 import pytest
 import torch
 
 import paper_2305_03448_gb300 as D
 import synth
+from oracle import ops as O
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-5
@@ -44,6 +46,13 @@ def test_noalloc_matches_desc_scan_twice(dt):
         D.desc_scan_noalloc(x, [n], [], D.GRID, out=got)
         assert D.desc_stream_status() == 0
         _compare(x, got, want)
+        # and against the oracle: int32 bit for bit, FP32 within 1e-5 * sum |x| of each prefix
+        xo = x.cpu().numpy()
+        ref, pa = O.scan(xo, np.zeros(n, xo.dtype), [n], [], D.GRID)
+        if dt == "i32":
+            assert np.array_equal(got.cpu().numpy(), ref)
+        else:
+            assert np.all(np.abs(got.cpu().numpy().astype(np.float64) - ref) <= TOL * pa + 1e-30)
 
 
 def test_noalloc_segments_and_split_views():
@@ -62,6 +71,18 @@ def test_noalloc_segments_and_split_views():
     want = D.desc_scan(xi, [n], ops, D.GRID, out=torch.zeros_like(xi))
     got = D.desc_scan_noalloc(xi, [n], ops, D.GRID, out=torch.zeros_like(xi))
     assert torch.equal(got.cpu(), want.cpu())
+
+
+def test_noalloc_refuses_views_that_are_not_one_run():
+    n = 5000
+    x = synth.ints_pm1000(n, seed=9).cuda()
+    for ops in ([("reverse", 0)], [("group", 50, 0), ("transpose", 0)]):
+        out = torch.full((n,), 5, dtype=torch.int32, device="cuda")
+        with pytest.raises(D.DescError) as e:
+            D.desc_scan_noalloc(x, [n], ops, D.GRID, out=out)
+        assert e.value.status == 7                       # DESC_ERR_UNSUPPORTED
+        torch.cuda.synchronize()
+        assert torch.equal(out.cpu(), torch.full((n,), 5, dtype=torch.int32))
 
 
 def test_noalloc_refuses_more_than_its_scratch():
