@@ -195,6 +195,9 @@ extern "C" int32_t desc_scan(const desc_view *v, const desc_exec *ex, int32_t se
                               ws_bytes, s, schedule_for(DESC_OP_SCAN, dtype, sp.total, 0));
   }
   // one pass through the lowered map: loads gather, stores scatter
+  if (!(flags & kMapScanOps))
+    return launch_scan_mapped(dtype, in, out, L.offset, L.extent, L.stride, L.ndims, sp.period, flags, ws, ws_bytes,
+                              s);
   return launch_scan_map(dtype, in, out, L.offset, L.extent, L.stride, L.ndims, sp.period, nullptr, 0, nullptr,
                          flags, ws, ws_bytes, s);
 }

@@ -123,6 +123,12 @@ constexpr int32_t kMapScanOps = DESC_PROD | DESC_AND | DESC_OR | DESC_XOR | DESC
 int32_t launch_scan_map(int32_t dtype, const void *in, void *out, int64_t off, const int64_t *ext,
                         const int64_t *stride, int nd, int64_t period, const int64_t *offsets, int64_t nseg,
                         void *sums, int32_t flags, void *ws, size_t ws_bytes, desc_stream_t s);
+// The look-back scan with 4 x 4096-point tiles through a lowered map (as
+// launch_scan_map, no CSR): sums, maxima and minima, inclusive or exclusive;
+// maps of more than two canonical dims go to launch_scan_map.
+int32_t launch_scan_mapped(int32_t dtype, const void *in, void *out, int64_t off, const int64_t *ext,
+                           const int64_t *stride, int nd, int64_t period, int32_t flags, void *ws, size_t ws_bytes,
+                           desc_stream_t s);
 
 // Copy over a common logical domain of `nd` dims: out[ostride . p] = in[istride . p].
 int32_t launch_copy_affine(const void *in, int64_t ioff, const int64_t *istride, void *out,

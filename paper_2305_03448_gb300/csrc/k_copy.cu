@@ -7,8 +7,12 @@
 // coalesced 128-byte lines.  The padding of one word per row makes the
 // column-wise shared-memory reads conflict-free.
 //
-// Affine copy: any pair of affine maps over a common domain; one element per
-// thread and iteration, indices decoded from the domain extents.
+// Affine copy: any pair of affine maps over a common domain.  Where the
+// input map has a unit-stride dim and the output map another one, the copy
+// is tiled over those two dims through shared memory (reads and writes both
+// coalesced; the other dims are decoded once per CTA); otherwise one element
+// per thread and iteration, indices decoded from the domain extents, with a
+// unit-stride dim (if any) innermost so that at least one side coalesces.
 #include <algorithm>
 
 #include "k_bodies.cuh"
@@ -70,6 +74,31 @@ __global__ void __launch_bounds__(256) copy_affine_kernel(const uint32_t *__rest
   }
 }
 
+// The tiled general copy: point (batch, r, c) of the domain reads
+// in[ioff(batch) + r * ld_in + c] (c: the input's unit-stride dim) and writes
+// out[ooff(batch) + c * ld_out + r] (r: the output's unit-stride dim).  Batch
+// index z + blockIdx.z decoded over nb dims (extents / strides).
+struct TiledCopyArgs {
+  int32_t nb;
+  int64_t R, C, ld_in, ld_out, batch;
+  int64_t ext[DESC_MAX_DIMS], ist[DESC_MAX_DIMS], ost[DESC_MAX_DIMS];
+  int64_t ioff, ooff;
+};
+// (8 CTAs of 256 threads per SM, as the hand-indexed transpose: 32 registers.)
+__global__ void __launch_bounds__(256, 8) copy_tiled_kernel(const float *__restrict__ in, float *__restrict__ out,
+                                                            const TiledCopyArgs a, int64_t z) {
+  __shared__ float tile[64][65];
+  int64_t io = a.ioff, oo = a.ooff, t = z + blockIdx.z;
+  for (int d = a.nb - 1; d >= 0; --d) {
+    const int64_t c = t % a.ext[d];
+    t /= a.ext[d];
+    io += c * a.ist[d];
+    oo += c * a.ost[d];
+  }
+  transpose_tile<64, 8>(in + io, out + oo, a.R, a.C, a.ld_in, a.ld_out, 0, 0, blockIdx.x, blockIdx.y, 0,
+                        threadIdx.x, threadIdx.y, tile);
+}
+
 }  // namespace
 
 int transpose_candidates() { return kNumTransposeCands; }
@@ -119,6 +148,47 @@ int32_t launch_copy_affine(const void *in, int64_t ioff, const int64_t *istride,
     a.nd = 1;
     a.extent[0] = 1;
     a.istride[0] = a.ostride[0] = 0;
+  }
+  // unit-stride dims of the two maps (the longest, if several)
+  int ua = -1, ub = -1;
+  for (int i = 0; i < a.nd; ++i) {
+    if (a.istride[i] == 1 && (ua < 0 || a.extent[i] > a.extent[ua])) ua = i;
+    if (a.ostride[i] == 1 && (ub < 0 || a.extent[i] > a.extent[ub])) ub = i;
+  }
+  if (ua >= 0 && ub >= 0 && ua != ub && a.extent[ua] >= 16 && a.extent[ub] >= 16) {
+    TiledCopyArgs t{};
+    t.C = a.extent[ua];
+    t.R = a.extent[ub];
+    t.ld_in = a.istride[ub];
+    t.ld_out = a.ostride[ua];
+    t.batch = 1;
+    for (int i = 0; i < a.nd; ++i) {
+      if (i == ua || i == ub) continue;
+      t.ext[t.nb] = a.extent[i];
+      t.ist[t.nb] = a.istride[i];
+      t.ost[t.nb] = a.ostride[i];
+      t.batch *= a.extent[i];
+      ++t.nb;
+    }
+    t.ioff = a.ioff;
+    t.ooff = a.ooff;
+    const int64_t gx = (t.C + 63) / 64, gy = (t.R + 63) / 64;
+    if (gx < (int64_t(1) << 31) && gy <= 65535) {
+      for (int64_t z = 0; z < t.batch; z += 65535) {   // launches of at most 65535 batch entries
+        const unsigned gz = (unsigned)std::min<int64_t>(t.batch - z, 65535);
+        copy_tiled_kernel<<<dim3((unsigned)gx, (unsigned)gy, gz), dim3(32, 8), 0, s>>>(
+            static_cast<const float *>(in), static_cast<float *>(out), t, z);
+      }
+      DESC_CUDA_TRY(cudaGetLastError());
+      return DESC_OK;
+    }
+  }
+  // element-wise: a unit-stride dim innermost (the output's, else the input's)
+  const int u = ub >= 0 ? ub : ua;
+  if (u >= 0 && u != a.nd - 1) {
+    std::swap(a.extent[u], a.extent[a.nd - 1]);
+    std::swap(a.istride[u], a.istride[a.nd - 1]);
+    std::swap(a.ostride[u], a.ostride[a.nd - 1]);
   }
   bool fast = a.total < (int64_t(1) << 32);
   for (int i = 0; i < a.nd; ++i) {

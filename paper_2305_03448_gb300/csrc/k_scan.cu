@@ -186,6 +186,59 @@ __device__ __forceinline__ void publish(TileState *st, unsigned long long status
   st_relaxed(&st->w, O::pack(status, c));
 }
 
+// A lowered map for the scans that read and write through it: point g
+// (row-major over the canonical dims) is element map_elem(m, g).
+struct MapArgs {
+  int32_t nd;                       // dims of the canonical map; 0: element = off + g
+  int32_t fast;                     // fewer than 2^32 points: 32-bit decoding
+  int64_t off;
+  int64_t ext[DESC_MAX_DIMS];
+  int64_t st[DESC_MAX_DIMS];
+  FastDiv div[DESC_MAX_DIMS];
+};
+
+// Maps of two or more dims: decoded dim by dim (out of line: the kernel
+// inlines only the one-dim case).
+__device__ __noinline__ int64_t map_elem_dims(const MapArgs &m, int64_t g) {
+  int64_t e = m.off;
+  if (m.fast) {
+    uint32_t t = (uint32_t)g;
+    for (int d = m.nd - 1; d > 0; --d) {
+      const uint32_t q = fast_div(t, m.div[d]);
+      e += int64_t(t - q * m.div[d].d) * m.st[d];
+      t = q;
+    }
+    return e + int64_t(t) * m.st[0];
+  }
+  int64_t t = g;
+  for (int d = m.nd - 1; d >= 0; --d) {
+    e += (t % m.ext[d]) * m.st[d];
+    t /= m.ext[d];
+  }
+  return e;
+}
+__device__ __forceinline__ int64_t map_elem(const MapArgs &m, int64_t g) {
+  if (m.nd <= 1) return m.off + (m.nd ? g * m.st[0] : g);
+  return map_elem_dims(m, g);
+}
+
+// Global addressing of the look-back scan: the identity (contiguous runs)
+// or a lowered map.
+struct RunAddr {
+  const MapArgs &m;                                     // not used
+  __device__ int64_t operator()(int64_t g) const { return g; }
+};
+// The look-back scan takes maps of at most two dims with 32-bit decoding
+// (launch_scan_mapped checks), decoded inline.
+struct MapAddr {
+  const MapArgs &m;
+  __device__ int64_t operator()(int64_t g) const {
+    if (m.nd < 2) return m.off + (m.nd ? g * m.st[0] : g);
+    const uint32_t t = (uint32_t)g, q = fast_div(t, m.div[1]);
+    return m.off + int64_t(q) * m.st[0] + int64_t(t - q * m.div[1].d) * m.st[1];
+  }
+};
+
 struct ScanArgs {
   int64_t n;
   int64_t period;          // PERIODIC: segment length
@@ -302,10 +355,11 @@ __device__ __forceinline__ void compute_bar() { asm volatile("bar.sync 1, %0;" :
 // CSR: the compute warps and the look-back warp, once the tile's segment heads are marked.
 __device__ __forceinline__ void heads_bar() { asm volatile("bar.sync 2, %0;" ::"n"(kThreads + 32) : "memory"); }
 
-// Start copying kSub elements from g_start (elements past n read as zero).
-template <class T>
+// Start copying kSub elements from g_start (elements past n read as zero);
+// point g is in[addr(g)].
+template <class T, class A>
 __device__ __forceinline__ void load_sub(unsigned char *stage, const T *in, int64_t g_start,
-                                         int64_t n, bool vec) {
+                                         int64_t n, bool vec, const A &addr) {
 #pragma unroll
   for (int q = 0; q < kSubChunks / kThreads; ++q) {
     const int j = q * kThreads + threadIdx.x;
@@ -314,11 +368,11 @@ __device__ __forceinline__ void load_sub(unsigned char *stage, const T *in, int6
     if (vec) {
       const int64_t rem = n - g;
       const int bytes = rem >= 4 ? 16 : (rem > 0 ? int(rem) * 4 : 0);
-      cp_async16(dst, bytes ? static_cast<const void *>(in + g) : static_cast<const void *>(in), bytes);
+      cp_async16(dst, bytes ? static_cast<const void *>(in + addr(g)) : static_cast<const void *>(in), bytes);
     } else {
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
-        if (g + c < n) cp_async4(dst + 4 * c, in + g + c);
+        if (g + c < n) cp_async4(dst + 4 * c, in + addr(g + c));
         else *reinterpret_cast<T *>(dst + 4 * c) = T(0);
       }
     }
@@ -358,9 +412,13 @@ __device__ __forceinline__ int64_t find_segment(const int64_t *offsets, int64_t 
 // of a tile does not depend on its data) and publishes the inclusive prefix
 // once it has both.  The carry is added during the coalesced store pass, to
 // the elements that have no segment start before them in the tile.
-template <class T, class O, int MODE, int SUB, bool EXCL>
-__global__ void __launch_bounds__(kThreads + 32) scan_kernel(const T *in, T *out, ScanArgs args,
-                                                             ScanWs *ws, TileState *states) {
+// MAPPED: points are addressed through the lowered map m (in and out are
+// then the base arrays; vec means four consecutive points from a multiple of
+// 4 are four consecutive elements on a 16-byte boundary).
+template <class T, class O, int MODE, int SUB, bool EXCL, bool MAPPED = false>
+__global__ void __launch_bounds__(kThreads + 32, 3) scan_kernel(const T *in, T *out, ScanArgs args,
+                                                             ScanWs *ws, TileState *states,
+                                                             const __grid_constant__ MapArgs m) {
   using CT = typename O::C;
   constexpr int kTile = kSub * SUB;
   extern __shared__ __align__(128) unsigned char ring[];   // SUB stages
@@ -381,6 +439,8 @@ __global__ void __launch_bounds__(kThreads + 32) scan_kernel(const T *in, T *out
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t n = args.n;
   const bool vec = args.vec != 0;
+  using Addr = typename std::conditional<MAPPED, MapAddr, RunAddr>::type;
+  const Addr addr{m};
   if (tid == 0) {
     sh_tile = atomicAdd(&ws->ticket, 1u);
     sh_go = 0;
@@ -454,7 +514,7 @@ __global__ void __launch_bounds__(kThreads + 32) scan_kernel(const T *in, T *out
   // ---- compute warps
 #pragma unroll
   for (int s = 0; s < SUB; ++s) {
-    load_sub<T>(ring + s * kStageBytes, in, t0 + int64_t(s) * kSub, n, vec);
+    load_sub<T>(ring + s * kStageBytes, in, t0 + int64_t(s) * kSub, n, vec, addr);
     cp_async_commit();
   }
   if (tid == 0) {
@@ -644,11 +704,11 @@ __global__ void __launch_bounds__(kThreads + 32) scan_kernel(const T *in, T *out
         x.y = __builtin_bit_cast(int, y[1]);
         x.z = __builtin_bit_cast(int, y[2]);
         x.w = __builtin_bit_cast(int, y[3]);
-        __stcs(reinterpret_cast<int4 *>(out + g), x);
+        __stcs(reinterpret_cast<int4 *>(out + addr(g)), x);
       } else {
 #pragma unroll
         for (int c = 0; c < 4; ++c)
-          if (g + c < n) out[g + c] = y[c];
+          if (g + c < n) out[addr(g + c)] = y[c];
       }
     }
   }
@@ -683,40 +743,6 @@ __global__ void __launch_bounds__(kThreads + 32) scan_kernel(const T *in, T *out
 // index of the position.
 constexpr int kMapThreads = 256, kMapItems = 16, kMapTile = kMapThreads * kMapItems;
 static_assert(kMapTile == kScanSubTile, "workspace tiles count kScanSubTile elements");
-
-struct MapArgs {
-  int32_t nd;                       // dims of the canonical map; 0: element = off + g
-  int32_t fast;                     // fewer than 2^32 points: 32-bit decoding
-  int64_t off;
-  int64_t ext[DESC_MAX_DIMS];
-  int64_t st[DESC_MAX_DIMS];
-  FastDiv div[DESC_MAX_DIMS];
-};
-
-// Maps of two or more dims: decoded dim by dim (out of line: the kernel
-// inlines only the one-dim case).
-__device__ __noinline__ int64_t map_elem_dims(const MapArgs &m, int64_t g) {
-  int64_t e = m.off;
-  if (m.fast) {
-    uint32_t t = (uint32_t)g;
-    for (int d = m.nd - 1; d > 0; --d) {
-      const uint32_t q = fast_div(t, m.div[d]);
-      e += int64_t(t - q * m.div[d].d) * m.st[d];
-      t = q;
-    }
-    return e + int64_t(t) * m.st[0];
-  }
-  int64_t t = g;
-  for (int d = m.nd - 1; d >= 0; --d) {
-    e += (t % m.ext[d]) * m.st[d];
-    t /= m.ext[d];
-  }
-  return e;
-}
-__device__ __forceinline__ int64_t map_elem(const MapArgs &m, int64_t g) {
-  if (m.nd <= 1) return m.off + (m.nd ? g * m.st[0] : g);
-  return map_elem_dims(m, g);
-}
 
 // Element-state layer of the map kernel for the value operators (the state
 // is the value; make() takes the value and its element index) ...
@@ -787,51 +813,119 @@ __device__ __forceinline__ typename ArgStates<T, MAX>::C ArgStates<T, MAX>::C::p
   return {ArgStates<T, MAX>::better(e, o.e)};
 }
 
-// Shared-memory slot of tile point r: one padding slot per 32 (4-byte
-// states) or 16 (8-byte states), so that thread t's 16 consecutive points
-// and a warp's 32 striped points both spread over the banks.
+// The tile in shared memory.  4-byte states use the look-back scan's
+// layout: 16-byte chunks in XOR-swizzled slots (chunk_off), conflict-free
+// for a warp's striped chunks, a warp's 32 consecutive points and each
+// thread's 4 consecutive chunks.  8-byte states (the arg operators) take one
+// padding slot per 16.
 template <class E>
-__device__ __forceinline__ int map_slot(int r) {
-  return sizeof(E) == 4 ? r + (r >> 5) : r + (r >> 4);
-}
+struct MapTileSmem {
+  static constexpr int kBytes = sizeof(E) == 4 ? kMapTile * 4 : (kMapTile + kMapTile / 16) * 8;
+  __device__ static E *at(unsigned char *t, int r) {
+    if constexpr (sizeof(E) == 4) return reinterpret_cast<E *>(t + chunk_off(r >> 2) + 4 * (r & 3));
+    else return reinterpret_cast<E *>(t) + (r + (r >> 4));
+  }
+};
 
-// mode: PLAIN, PERIODIC or CSR; excl: the exclusive form.
+// Compute warps only (the look-back warp has left).
+__device__ __forceinline__ void map_compute_bar() { asm volatile("bar.sync 1, %0;" ::"n"(kMapThreads) : "memory"); }
+
+// Warps 0..7 load the tile through the map (128-bit chunks where the map's
+// inner dim is unit-stride: vec), stage it, scan it and store it; warp 8
+// looks back from the start, while the loads are in flight.  mode: PLAIN,
+// PERIODIC or CSR; excl: the exclusive form.
 template <class T, class S>
-__global__ void __launch_bounds__(kMapThreads) scan_map_kernel(const T *__restrict__ in, uint32_t *__restrict__ out,
-                                                               const MapArgs m, ScanArgs args, ScanWs *ws,
-                                                               TileState *states, int mode, int excl) {
+__global__ void __launch_bounds__(kMapThreads + 32) scan_map_kernel(const T *__restrict__ in, uint32_t *__restrict__ out,
+                                                                    const MapArgs m, ScanArgs args, ScanWs *ws,
+                                                                    TileState *states, int mode, int excl) {
   using E = typename S::E;
   using O = typename S::Op;
   using CT = typename S::C;
-  constexpr int kSlots = kMapTile + kMapTile / (sizeof(E) == 4 ? 32 : 16);
-  __shared__ E sh[kSlots];
+  using SM = MapTileSmem<E>;
+  constexpr bool kVec4 = sizeof(E) == 4;
+  __shared__ __align__(128) unsigned char tile_smem[SM::kBytes];
   __shared__ unsigned sh_heads[kMapTile / 32];
   __shared__ E sh_wval[kMapThreads / 32];
   __shared__ int sh_wflag[kMapThreads / 32];
+  __shared__ E sh_agg;
+  __shared__ int sh_aggf;
   __shared__ CT sh_prefix;
   __shared__ int64_t sh_tile, sh_seg0;
   __shared__ int sh_ok;
+  __shared__ volatile int sh_go;                       // the tile's inputs have landed: start polling
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (tid == 0) sh_tile = atomicAdd(&ws->ticket, 1u);
+  if (tid == 0) {
+    sh_tile = atomicAdd(&ws->ticket, 1u);
+    sh_go = 0;
+  }
   if (mode == CSR)
-    for (int i = tid; i < kMapTile / 32; i += kMapThreads) sh_heads[i] = 0u;
+    for (int i = tid; i < kMapTile / 32; i += kMapThreads + 32) sh_heads[i] = 0u;
   __syncthreads();
   const int64_t tile = sh_tile, t0 = tile * kMapTile, n = args.n;
   const int64_t tend = min(t0 + kMapTile, n);
   const bool stall = args.debug && tile == 1;
 
-  // ---- striped loads through the map
-#pragma unroll
-  for (int j = 0; j < kMapItems; ++j) {
-    const int r = j * kMapThreads + tid;
-    const int64_t g = t0 + r;
-    E x = S::eid();
-    if (g < n) {
-      const int64_t e = map_elem(m, g);
-      x = S::make(in[e], e);
+  if (warp == kMapThreads / 32) {
+    // ---- look-back warp: the prefix of everything before t0
+    bool first_head = tile == 0;
+    if (mode == PERIODIC) first_head = first_head || t0 % args.period == 0;
+    if (mode == CSR) first_head = first_head || args.offsets[find_segment(args.offsets, args.nseg, t0)] == t0;
+    CT prefix = CT::zero();
+    bool ok = true;
+    if (!first_head) {
+      // Predecessors publish about when this tile's own loads land; polls
+      // before that only load the tile states (bounded wait).
+      for (unsigned i = 0; i < kGoSpins && !sh_go; ++i) __nanosleep(64);
+      ok = look_back<O>(states, tile, ws, args.debug ? kDebugBudgetCycles : kBudgetCycles, prefix);
     }
-    sh[map_slot<E>(r)] = x;
+    if (lane == 0) {
+      sh_prefix = prefix;
+      sh_ok = ok ? 1 : 0;
+    }
+    __syncthreads();                                   // (S) the tile's aggregate is known
+    if (ok && lane == 0 && !stall && tile != 0 && !sh_aggf)
+      publish<O>(&states[tile], kStatIncl, prefix.plus(S::carry(sh_agg)));
+    return;
+  }
+
+  unsigned char *tsm = tile_smem;
+  const bool vec = args.vec != 0;
+  // ---- loads through the map
+  bool done = false;
+  if constexpr (kVec4) {
+    if (vec) {                                         // chunk c = points 4c .. 4c + 3
+      done = true;
+#pragma unroll
+    for (int q = 0; q < kMapTile / 4 / kMapThreads; ++q) {
+      const int c = q * kMapThreads + tid;
+      const int64_t g = t0 + 4 * int64_t(c);
+      int4 x;
+      if (g + 4 <= n) {
+        x = __ldcs(reinterpret_cast<const int4 *>(in + map_elem(m, g)));
+      } else {
+        E e[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) e[k] = g + k < n ? S::make(in[map_elem(m, g + k)], 0) : S::eid();
+        x = make_int4(__builtin_bit_cast(int, e[0]), __builtin_bit_cast(int, e[1]), __builtin_bit_cast(int, e[2]),
+                      __builtin_bit_cast(int, e[3]));
+      }
+      *reinterpret_cast<int4 *>(tsm + chunk_off(c)) = x;
+    }
+    }
+  }
+  if (!done) {
+#pragma unroll
+    for (int j = 0; j < kMapItems; ++j) {
+      const int r = j * kMapThreads + tid;
+      const int64_t g = t0 + r;
+      E x = S::eid();
+      if (g < n) {
+        const int64_t e = map_elem(m, g);
+        x = S::make(in[e], e);
+      }
+      *SM::at(tsm, r) = x;
+    }
   }
   // ---- segment heads (CSR): boundaries offsets[q] in (t0, tend), and t0
   if (mode == CSR) {
@@ -842,14 +936,15 @@ __global__ void __launch_bounds__(kMapThreads) scan_map_kernel(const T *__restri
         if (args.offsets[s0] == t0) atomicOr(&sh_heads[0], 1u);
       }
     }
-    __syncthreads();
+    map_compute_bar();
     for (int64_t q = sh_seg0 + 1 + tid; q <= args.nseg; q += kMapThreads) {
       const int64_t b = args.offsets[q];
       if (b >= tend) break;
       if (b > t0) atomicOr(&sh_heads[(b - t0) >> 5], 1u << ((b - t0) & 31));
     }
   }
-  __syncthreads();
+  map_compute_bar();
+  if (tid == 0) sh_go = 1;
   auto is_head = [&](int r) -> bool {
     const int64_t g = t0 + r;
     if (mode == PLAIN) return g == 0;
@@ -860,11 +955,26 @@ __global__ void __launch_bounds__(kMapThreads) scan_map_kernel(const T *__restri
   // ---- scan of the tile: 16 consecutive points per thread
   const int r0 = tid * kMapItems;
   E v[kMapItems];
-  unsigned hm = 0u;
+  if constexpr (kVec4) {
 #pragma unroll
-  for (int i = 0; i < kMapItems; ++i) {
-    v[i] = sh[map_slot<E>(r0 + i)];
-    if (is_head(r0 + i)) hm |= 1u << i;
+    for (int q = 0; q < kMapItems / 4; ++q) {
+      const int4 x = *reinterpret_cast<const int4 *>(tsm + chunk_off((kMapItems / 4) * tid + q));
+      v[4 * q] = __builtin_bit_cast(E, x.x);
+      v[4 * q + 1] = __builtin_bit_cast(E, x.y);
+      v[4 * q + 2] = __builtin_bit_cast(E, x.z);
+      v[4 * q + 3] = __builtin_bit_cast(E, x.w);
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < kMapItems; ++i) v[i] = *SM::at(tsm, r0 + i);
+  }
+  unsigned hm = 0u;
+  if (mode == CSR) {
+    hm = (sh_heads[r0 >> 5] >> (r0 & 31)) & 0xffffu;
+  } else {
+#pragma unroll
+    for (int i = 0; i < kMapItems; ++i)
+      if (is_head(r0 + i)) hm |= 1u << i;
   }
 #pragma unroll
   for (int i = 1; i < kMapItems; ++i)
@@ -890,8 +1000,8 @@ __global__ void __launch_bounds__(kMapThreads) scan_map_kernel(const T *__restri
     ex = S::eid();
     exf = 0;
   }
-  __syncthreads();
-  if (warp == 0) {                                     // scan of the warp totals
+  map_compute_bar();
+  if (warp == 0) {                                     // scan of the warp totals; publish
     constexpr int kW = kMapThreads / 32;
     E wa = lane < kW ? sh_wval[lane] : S::eid();
     int wf = lane < kW ? sh_wflag[lane] : 0;
@@ -917,22 +1027,15 @@ __global__ void __launch_bounds__(kMapThreads) scan_map_kernel(const T *__restri
       sh_wval[lane] = we;
       sh_wflag[lane] = wfe;
     }
-    // ---- publish, and look back when a point of the tile needs the prefix
-    const bool first_head = is_head(0);
-    if (lane == 0 && !stall)
-      publish<O>(&states[tile], (tile == 0 || aggf) ? kStatIncl : kStatAgg, S::carry(agg));
-    CT prefix = CT::zero();
-    bool ok = true;
-    if (tile != 0 && !first_head) {
-      ok = look_back<O>(states, tile, ws, args.debug ? kDebugBudgetCycles : kBudgetCycles, prefix);
-      if (ok && lane == 0 && !stall && !aggf) publish<O>(&states[tile], kStatIncl, prefix.plus(S::carry(agg)));
-    }
     if (lane == 0) {
-      sh_prefix = prefix;
-      sh_ok = ok ? 1 : 0;
+      sh_agg = agg;
+      sh_aggf = aggf;
+      // at once: the inclusive value when nothing before can change it
+      // (tile 0, or a tile holding a segment head), else the tile total
+      if (!stall) publish<O>(&states[tile], (tile == 0 || aggf) ? kStatIncl : kStatAgg, S::carry(agg));
     }
   }
-  __syncthreads();
+  __syncthreads();                                     // (S) with the look-back warp
   if (!sh_ok) return;                                  // a wait gave up: write nothing
   {
     const E pv = sh_wval[warp];
@@ -947,22 +1050,57 @@ __global__ void __launch_bounds__(kMapThreads) scan_map_kernel(const T *__restri
         v[i] = exf ? x : S::apply(x, pre);
       }
   }
-  __syncthreads();                                     // every thread has read its inputs
+  if constexpr (kVec4) {                               // each thread rewrites only its own chunks
 #pragma unroll
-  for (int i = 0; i < kMapItems; ++i) sh[map_slot<E>(r0 + i)] = v[i];
-  __syncthreads();
+    for (int q = 0; q < kMapItems / 4; ++q)
+      *reinterpret_cast<int4 *>(tsm + chunk_off((kMapItems / 4) * tid + q)) =
+          make_int4(__builtin_bit_cast(int, v[4 * q]), __builtin_bit_cast(int, v[4 * q + 1]),
+                    __builtin_bit_cast(int, v[4 * q + 2]), __builtin_bit_cast(int, v[4 * q + 3]));
+  } else {
+#pragma unroll
+    for (int i = 0; i < kMapItems; ++i) *SM::at(tsm, r0 + i) = v[i];
+  }
+  map_compute_bar();
 
-  // ---- striped stores through the map (the exclusive form shifts by one)
+  // ---- stores through the map (the exclusive form shifts by one)
   const E before = S::of_carry(sh_prefix);             // everything before the tile
+  auto result = [&](int r) -> E {
+    if (!excl) return *SM::at(tsm, r);
+    return is_head(r) ? S::eid() : (r == 0 ? before : *SM::at(tsm, r - 1));
+  };
+  bool stored = false;
+  if constexpr (kVec4) {
+    if (vec) {
+      stored = true;
 #pragma unroll
-  for (int j = 0; j < kMapItems; ++j) {
-    const int r = j * kMapThreads + tid;
-    const int64_t g = t0 + r;
-    if (g >= n) break;
-    E e;
-    if (excl) e = is_head(r) ? S::eid() : (r == 0 ? before : sh[map_slot<E>(r - 1)]);
-    else e = sh[map_slot<E>(r)];
-    out[map_elem(m, g)] = S::out_bits(e, m);
+    for (int q = 0; q < kMapTile / 4 / kMapThreads; ++q) {
+      const int c = q * kMapThreads + tid;
+      const int64_t g = t0 + 4 * int64_t(c);
+      if (g >= n) break;
+      uint32_t w[4];
+      if (!excl) {
+        const int4 x = *reinterpret_cast<const int4 *>(tsm + chunk_off(c));
+        w[0] = (uint32_t)x.x; w[1] = (uint32_t)x.y; w[2] = (uint32_t)x.z; w[3] = (uint32_t)x.w;
+      } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) w[k] = S::out_bits(result(4 * c + k), m);
+      }
+      if (g + 4 <= n) {
+        __stcs(reinterpret_cast<int4 *>(out + map_elem(m, g)), make_int4((int)w[0], (int)w[1], (int)w[2], (int)w[3]));
+      } else {
+        for (int k = 0; k < 4 && g + k < n; ++k) out[map_elem(m, g + k)] = w[k];
+      }
+    }
+    }
+  }
+  if (!stored) {
+#pragma unroll
+    for (int j = 0; j < kMapItems; ++j) {
+      const int r = j * kMapThreads + tid;
+      const int64_t g = t0 + r;
+      if (g >= n) break;
+      out[map_elem(m, g)] = S::out_bits(result(r), m);
+    }
   }
   // ---- CSR: totals of the non-empty segments that end in this tile (the
   // empty ones hold the identity already)
@@ -972,7 +1110,7 @@ __global__ void __launch_bounds__(kMapThreads) scan_map_kernel(const T *__restri
       const int64_t b = args.offsets[q];
       if (b > tend) break;
       if (b <= t0 || args.offsets[q - 1] == b) continue;
-      sums[q - 1] = S::out_bits(sh[map_slot<E>((int)(b - 1 - t0))], m);
+      sums[q - 1] = S::out_bits(*SM::at(tsm, (int)(b - 1 - t0)), m);
     }
   }
 }
@@ -985,8 +1123,9 @@ constexpr int kWsTile = kSub;   // workspace is sized for the smallest tile
 static_assert(kSub == kScanSubTile, "the candidate table counts sub-tiles of this size");
 static_assert(kSub * kScanSubCands[0] == kScanNoallocTile, "the no-alloc scan runs candidate 0");
 
-template <class T, class O, int MODE, int SUB, bool EXCL = false>
-int32_t run_scan_t(const T *in, T *out, const ScanArgs &a, void *ws, size_t ws_bytes, cudaStream_t s) {
+template <class T, class O, int MODE, int SUB, bool EXCL = false, bool MAPPED = false>
+int32_t run_scan_t(const T *in, T *out, const ScanArgs &a, void *ws, size_t ws_bytes, cudaStream_t s,
+                   const MapArgs &m) {
   constexpr int kTile = kSub * SUB;
   const int64_t ntiles = (a.n + kTile - 1) / kTile;
   if (ntiles == 0) return DESC_OK;
@@ -999,34 +1138,38 @@ int32_t run_scan_t(const T *in, T *out, const ScanArgs &a, void *ws, size_t ws_b
   DESC_CUDA_TRY(cudaGetDevice(&dev));
   const unsigned long long bit = dev >= 0 && dev < 64 ? 1ull << dev : 0ull;
   if (!(attr_devs.load(std::memory_order_acquire) & bit) || !bit) {
-    DESC_CUDA_TRY(
-        cudaFuncSetAttribute(scan_kernel<T, O, MODE, SUB, EXCL>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    DESC_CUDA_TRY(cudaFuncSetAttribute(scan_kernel<T, O, MODE, SUB, EXCL, MAPPED>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     attr_devs.fetch_or(bit, std::memory_order_release);
   }
   DESC_CUDA_TRY(cudaMemsetAsync(ws, 0, need, s));
   ScanWs *w = static_cast<ScanWs *>(ws);
   TileState *st = reinterpret_cast<TileState *>(static_cast<char *>(ws) + align256(sizeof(ScanWs)));
-  scan_kernel<T, O, MODE, SUB, EXCL><<<(unsigned)ntiles, kThreads + 32, smem, s>>>(in, out, a, w, st);
+  scan_kernel<T, O, MODE, SUB, EXCL, MAPPED><<<(unsigned)ntiles, kThreads + 32, smem, s>>>(in, out, a, w, st, m);
   DESC_CUDA_TRY(cudaGetLastError());
   return DESC_OK;
 }
 
 // Inclusive sums take every schedule candidate; maximum, minimum and the
-// exclusive forms the default tile.
-template <class T, int MODE>
+// exclusive forms the default tile; through a map, the default tile.
+template <class T, int MODE, bool MAPPED = false>
 int32_t run_scan(const T *in, T *out, const ScanArgs &a, void *ws, size_t ws_bytes, cudaStream_t s, int cand,
-                 int32_t flags) {
+                 int32_t flags, const MapArgs &m) {
   if (flags & DESC_EXCLUSIVE) {
-    if (flags & DESC_MAX) return run_scan_t<T, ExtOp<T, true>, MODE, 4, true>(in, out, a, ws, ws_bytes, s);
-    if (flags & DESC_MIN) return run_scan_t<T, ExtOp<T, false>, MODE, 4, true>(in, out, a, ws, ws_bytes, s);
-    return run_scan_t<T, SumOp<T>, MODE, 4, true>(in, out, a, ws, ws_bytes, s);
+    if (flags & DESC_MAX) return run_scan_t<T, ExtOp<T, true>, MODE, 4, true, MAPPED>(in, out, a, ws, ws_bytes, s, m);
+    if (flags & DESC_MIN) return run_scan_t<T, ExtOp<T, false>, MODE, 4, true, MAPPED>(in, out, a, ws, ws_bytes, s, m);
+    return run_scan_t<T, SumOp<T>, MODE, 4, true, MAPPED>(in, out, a, ws, ws_bytes, s, m);
   }
-  if (flags & DESC_MAX) return run_scan_t<T, ExtOp<T, true>, MODE, 4>(in, out, a, ws, ws_bytes, s);
-  if (flags & DESC_MIN) return run_scan_t<T, ExtOp<T, false>, MODE, 4>(in, out, a, ws, ws_bytes, s);
-  switch (kScanSubCands[(cand >= 0 && cand < kNumScanCands) ? cand : 0]) {
-    case 1: return run_scan_t<T, SumOp<T>, MODE, 1>(in, out, a, ws, ws_bytes, s);
-    case 2: return run_scan_t<T, SumOp<T>, MODE, 2>(in, out, a, ws, ws_bytes, s);
-    default: return run_scan_t<T, SumOp<T>, MODE, 4>(in, out, a, ws, ws_bytes, s);
+  if (flags & DESC_MAX) return run_scan_t<T, ExtOp<T, true>, MODE, 4, false, MAPPED>(in, out, a, ws, ws_bytes, s, m);
+  if (flags & DESC_MIN) return run_scan_t<T, ExtOp<T, false>, MODE, 4, false, MAPPED>(in, out, a, ws, ws_bytes, s, m);
+  if constexpr (MAPPED) {
+    return run_scan_t<T, SumOp<T>, MODE, 4, false, true>(in, out, a, ws, ws_bytes, s, m);
+  } else {
+    switch (kScanSubCands[(cand >= 0 && cand < kNumScanCands) ? cand : 0]) {
+      case 1: return run_scan_t<T, SumOp<T>, MODE, 1>(in, out, a, ws, ws_bytes, s, m);
+      case 2: return run_scan_t<T, SumOp<T>, MODE, 2>(in, out, a, ws, ws_bytes, s, m);
+      default: return run_scan_t<T, SumOp<T>, MODE, 4>(in, out, a, ws, ws_bytes, s, m);
+    }
   }
 }
 
@@ -1055,16 +1198,17 @@ int32_t launch_scan_contig(int32_t dtype, const void *in, void *out, int64_t n, 
   a.debug = (flags & DESC_DEBUG_STALL_TILE) ? 1 : 0;
   a.vec = ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15) == 0;
   const bool periodic = period > 0 && period < n;
+  const MapArgs none{};
   if (dtype == DESC_I32) {
     auto i = static_cast<const int32_t *>(in);
     auto o = static_cast<int32_t *>(out);
-    return periodic ? run_scan<int32_t, PERIODIC>(i, o, a, ws, ws_bytes, s, cand, flags)
-                    : run_scan<int32_t, PLAIN>(i, o, a, ws, ws_bytes, s, cand, flags);
+    return periodic ? run_scan<int32_t, PERIODIC>(i, o, a, ws, ws_bytes, s, cand, flags, none)
+                    : run_scan<int32_t, PLAIN>(i, o, a, ws, ws_bytes, s, cand, flags, none);
   }
   auto i = static_cast<const float *>(in);
   auto o = static_cast<float *>(out);
-  return periodic ? run_scan<float, PERIODIC>(i, o, a, ws, ws_bytes, s, cand, flags)
-                  : run_scan<float, PLAIN>(i, o, a, ws, ws_bytes, s, cand, flags);
+  return periodic ? run_scan<float, PERIODIC>(i, o, a, ws, ws_bytes, s, cand, flags, none)
+                  : run_scan<float, PLAIN>(i, o, a, ws, ws_bytes, s, cand, flags, none);
 }
 
 namespace {
@@ -1108,33 +1252,57 @@ int32_t with_states(int32_t dtype, int32_t flags, F &&f) {
 
 }  // namespace
 
+namespace {
+
+// The canonical map of nd dims (extent-1 dims dropped, neighbours merged)
+// and its point count; nd == 0: the identity over `count` points.
+int64_t build_map(int64_t off, const int64_t *ext, const int64_t *stride, int nd, int64_t count, MapArgs *m) {
+  *m = MapArgs{};
+  int64_t n = 1;
+  for (int i = 0; i < nd; ++i) {
+    m->ext[i] = ext[i];
+    m->st[i] = stride[i];
+    n *= ext[i];
+  }
+  if (nd == 0) n = count;
+  m->off = off;
+  int64_t *sets[1] = {m->st};
+  m->nd = nd ? canon_dims(nd, m->ext, sets, 1) : 0;
+  if (nd && m->nd == 0) {                              // a single point
+    m->nd = 1;
+    m->ext[0] = 1;
+    m->st[0] = 0;
+  }
+  bool fast = n < (int64_t(1) << 32);
+  for (int i = 0; i < m->nd; ++i) {
+    fast = fast && m->ext[i] <= (int64_t(1) << 31);
+    if (fast) m->div[i] = make_fastdiv((uint32_t)m->ext[i]);
+  }
+  m->fast = fast ? 1 : 0;
+  return n;
+}
+
+// 128-bit accesses through the map: four consecutive points (from a multiple
+// of 4) are four consecutive elements starting on a 16-byte boundary of in
+// and out.
+bool map_vec(const MapArgs &m, const void *in, const void *out) {
+  bool vec = ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15) == 0 && m.off % 4 == 0;
+  if (m.nd >= 1) {
+    vec = vec && m.st[m.nd - 1] == 1 && m.ext[m.nd - 1] % 4 == 0;
+    for (int i = 0; i + 1 < m.nd; ++i) vec = vec && m.st[i] % 4 == 0;
+  }
+  return vec;
+}
+
+}  // namespace
+
 int32_t launch_scan_map(int32_t dtype, const void *in, void *out, int64_t off, const int64_t *ext,
                         const int64_t *stride, int nd, int64_t period, const int64_t *offsets, int64_t nseg,
                         void *sums, int32_t flags, void *ws, size_t ws_bytes, desc_stream_t st) {
   cudaStream_t s = reinterpret_cast<cudaStream_t>(st);
-  MapArgs m{};
-  int64_t n = 1;
-  for (int i = 0; i < nd; ++i) {
-    m.ext[i] = ext[i];
-    m.st[i] = stride[i];
-    n *= ext[i];
-  }
-  if (nd == 0) n = period;                             // the identity map over `period` points
+  MapArgs m;
+  const int64_t n = build_map(off, ext, stride, nd, period, &m);
   if (n == 0) return DESC_OK;
-  m.off = off;
-  int64_t *sets[1] = {m.st};
-  m.nd = nd ? canon_dims(nd, m.ext, sets, 1) : 0;
-  if (nd && m.nd == 0) {                               // a single point
-    m.nd = 1;
-    m.ext[0] = 1;
-    m.st[0] = 0;
-  }
-  bool fast = n < (int64_t(1) << 32);
-  for (int i = 0; i < m.nd; ++i) {
-    fast = fast && m.ext[i] <= (int64_t(1) << 31);
-    if (fast) m.div[i] = make_fastdiv((uint32_t)m.ext[i]);
-  }
-  m.fast = fast ? 1 : 0;
   const int64_t ntiles = (n + kMapTile - 1) / kMapTile;
   const size_t need = align256(sizeof(ScanWs)) + size_t(ntiles) * sizeof(TileState);
   if (!ws || ws_bytes < need) return DESC_ERR_WORKSPACE;
@@ -1146,6 +1314,7 @@ int32_t launch_scan_map(int32_t dtype, const void *in, void *out, int64_t off, c
   a.nseg = nseg;
   a.sums = sums;
   a.debug = (flags & DESC_DEBUG_STALL_TILE) ? 1 : 0;
+  a.vec = map_vec(m, in, out) ? 1 : 0;
   const int mode = offsets ? CSR : (a.period < n ? PERIODIC : PLAIN);
   const int excl = (flags & DESC_EXCLUSIVE) ? 1 : 0;
   DESC_CUDA_TRY(cudaMemsetAsync(ws, 0, need, s));
@@ -1154,12 +1323,41 @@ int32_t launch_scan_map(int32_t dtype, const void *in, void *out, int64_t off, c
   return with_states(dtype, flags, [&](auto tag) {
     using T = typename decltype(tag)::Elem;
     using S = typename decltype(tag)::States;
-    scan_map_kernel<T, S><<<(unsigned)ntiles, kMapThreads, 0, s>>>(static_cast<const T *>(in),
-                                                                    static_cast<uint32_t *>(out), m, a, w, ts,
-                                                                    mode, excl);
+    scan_map_kernel<T, S><<<(unsigned)ntiles, kMapThreads + 32, 0, s>>>(static_cast<const T *>(in),
+                                                                         static_cast<uint32_t *>(out), m, a, w, ts,
+                                                                         mode, excl);
     DESC_CUDA_TRY(cudaGetLastError());
     return DESC_OK;
   });
+}
+
+int32_t launch_scan_mapped(int32_t dtype, const void *in, void *out, int64_t off, const int64_t *ext,
+                           const int64_t *stride, int nd, int64_t period, int32_t flags, void *ws, size_t ws_bytes,
+                           desc_stream_t st) {
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(st);
+  if (flags & kMapScanOps) return DESC_ERR_INVALID_ARG;
+  MapArgs m;
+  const int64_t n = build_map(off, ext, stride, nd, period, &m);
+  if (n == 0) return DESC_OK;
+  if (m.nd > 2 || !m.fast)                             // the one-tile map scan decodes any map
+    return launch_scan_map(dtype, in, out, off, ext, stride, nd, period, nullptr, 0, nullptr, flags, ws, ws_bytes,
+                           st);
+  ScanArgs a{};
+  a.n = n;
+  a.period = period > 0 ? period : n;
+  a.debug = (flags & DESC_DEBUG_STALL_TILE) ? 1 : 0;
+  a.vec = map_vec(m, in, out) ? 1 : 0;
+  const bool periodic = a.period < n;
+  if (dtype == DESC_I32) {
+    auto i = static_cast<const int32_t *>(in);
+    auto o = static_cast<int32_t *>(out);
+    return periodic ? run_scan<int32_t, PERIODIC, true>(i, o, a, ws, ws_bytes, s, -1, flags, m)
+                    : run_scan<int32_t, PLAIN, true>(i, o, a, ws, ws_bytes, s, -1, flags, m);
+  }
+  auto i = static_cast<const float *>(in);
+  auto o = static_cast<float *>(out);
+  return periodic ? run_scan<float, PERIODIC, true>(i, o, a, ws, ws_bytes, s, -1, flags, m)
+                  : run_scan<float, PLAIN, true>(i, o, a, ws, ws_bytes, s, -1, flags, m);
 }
 
 size_t scan_csr_ws(int64_t n) { return scan_contig_ws(DESC_F32, n); }
@@ -1175,11 +1373,12 @@ int32_t launch_scan_csr(int32_t dtype, const void *in, void *out, int64_t n, con
   a.sums = sums;
   a.debug = (flags & DESC_DEBUG_STALL_TILE) ? 1 : 0;
   a.vec = ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15) == 0;
+  const MapArgs none{};
   if (dtype == DESC_I32)
     return run_scan<int32_t, CSR>(static_cast<const int32_t *>(in), static_cast<int32_t *>(out), a,
-                                  ws, ws_bytes, s, cand, flags);
+                                  ws, ws_bytes, s, cand, flags, none);
   return run_scan<float, CSR>(static_cast<const float *>(in), static_cast<float *>(out), a, ws,
-                              ws_bytes, s, cand, flags);
+                              ws_bytes, s, cand, flags, none);
 }
 
 }  // namespace desc

@@ -160,7 +160,8 @@ def test_scan_general_views_one_pass(op):
              ([("group", 257, 0), ("transpose", 0)], V.GRID, None, None),                # columns of [192][257]
              ([("group", 257, 0), ("transpose", 0), ("select", V.BLOCK, V.X)], V.BLOCK, (257, 1, 1), (1, 1, 1)),
              ([("group", 64, 0), ("reverse", 1)], V.GRID, None, None),                    # map(reverse)
-             ([("split_snd", 1001, 0), ("reverse", 0)], V.GRID, None, None)]
+             ([("split_snd", 1001, 0), ("reverse", 0)], V.GRID, None, None),
+             ([("group", 257, 0), ("group", 8, 0), ("transpose", 0)], V.GRID, None, None)]   # three map dims
     for ops, lvl, g, b in cases:
         for excl in (False, True):
             check_scan(x, op, excl, ops, lvl, g, b)

@@ -104,3 +104,24 @@ def test_reduce_generic_odd_groups_reversed(m, g):
     got = D.desc_reduce(x.cuda(), [n], ops, V.BLOCK, (g, 1, 1), (1, 1, 1)).cpu().numpy()
     want, _ = O.reduce(x.numpy(), [n], ops, V.BLOCK, (g, 1, 1), (1, 1, 1))
     assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("shape,in_ops,perm", [
+    ((6, 40, 5, 48), [("transpose", 0), ("transpose", 2)], (1, 0, 3, 2)),    # two batch dims, tiled
+    ((70000, 16, 16), [("transpose", 1)], (0, 2, 1)),                       # batch above the grid's z limit
+    ((17, 33, 70), [("transpose", 0), ("transpose", 1)], (1, 2, 0)),        # a rotation of the dims
+    ((64, 96), [("reverse", 1), ("transpose", 0)], None),                    # reversed rows: element path
+])
+def test_copy_generic_tiled_and_batched(shape, in_ops, perm):
+    """General copies through the tiled path (the input's and the output's
+    unit-stride dims tiled through shared memory, the other dims decoded per
+    CTA) and through the element path, bit-exact against the oracle."""
+    n = int(np.prod(shape))
+    x = synth.normal_f32(n, seed=n % 1000).reshape(shape)
+    dom = V.domain_shape(list(shape), in_ops)
+    out = torch.zeros(*dom, device="cuda")
+    D.desc_transpose(x.cuda(), list(shape), in_ops, out, dom, [])
+    want = O.view_copy(x.numpy(), np.zeros(dom, np.float32), list(shape), in_ops, dom, [])
+    assert np.array_equal(out.cpu().numpy().view(np.int32), want.astype(np.float32).view(np.int32))
+    if perm is not None:
+        assert np.array_equal(out.cpu().numpy(), np.ascontiguousarray(x.numpy().transpose(perm)))
