@@ -42,6 +42,13 @@ def op_bytes(sz):
     return {"reduce": 4 * sz["reduce_n"], "scan": 8 * sz["scan_n"], "transpose": 8 * sz["T"] * sz["T"]}
 
 
+# Nominal GB300 figures (the data sheet's, not measured here): HBM3e 7.9 TB/s,
+# dense BF16 tensor 2.25 PFLOP/s at the 2070 MHz maximum SM clock.
+NOMINAL_HBM_GBS = 7900.0
+NOMINAL_BF16_TFLOPS = 2250.0
+NOMINAL_SM_MHZ = 2070.0
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -242,10 +249,12 @@ def run_ours(args, rank, world, local_rank):
     pk = peaks()
     for name in per_op:
         per_op[name]["frac"] = round(per_op[name]["GB/s"] / pk["hbm_gbs"], 4)
+        per_op[name]["frac_of_nominal"] = round(per_op[name]["GB/s"] / NOMINAL_HBM_GBS, 4)
     dom = max(per_op, key=lambda n: per_op[n]["ms"])
     roofline = {"bound": "hbm", "kernel": dom, "achieved": per_op[dom]["GB/s"], "peak": pk["hbm_gbs"],
                 "unit": "GB/s", "frac": per_op[dom]["frac"],
                 "peak_source": f"{pk['source']} hbm_gbs (of {pk['source']})",
+                "frac_of_nominal": per_op[dom]["frac_of_nominal"], "nominal_peak": NOMINAL_HBM_GBS,
                 "traffic": traffic_for(dom)}
 
     # the same step with the scan on a second stream (the three ops are
@@ -506,9 +515,13 @@ def run_matmul(torch, D, dev, stream, pk, n=8192, forms=("split3", "bf16", "fp32
                               "frac_of_bf16_sustained_peak": round(nprod * eff_long / pk["bf16_tflops_sustained"], 4)}
             if clk:
                 r["sustained"]["clocks"] = {k: clk[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")}
+                # the nominal dense peak at the SM clock the loop ran at
+                nom = NOMINAL_BF16_TFLOPS * clk["sm_mhz"] / NOMINAL_SM_MHZ
+                r["sustained"]["frac_of_nominal_at_sampled_clock"] = round(nprod * eff_long / nom, 4)
         if p != D.MM_FP32_SIMT:
             r["tensor_tflops"] = round(nprod * eff, 1)
             r["frac_of_bf16_peak"] = round(nprod * eff / pk["bf16_tflops"], 4)
+            r["frac_of_nominal_bf16"] = round(nprod * eff / NOMINAL_BF16_TFLOPS, 4)
         out[name] = r
         del ws
     if D.desc_stream_status(stream) != 0:
@@ -678,6 +691,7 @@ def run_segmented(torch, D, synth, dev, stream, nseg=20000):
         raise RuntimeError("device status after segmented")
     return {"segments": nseg, "elements": total, "graph_ms": round(t_graph, 4), "direct_ms": round(t_direct, 4),
             "per_segment_ms": round(t_per, 3), "graph_GB/s": round(nbytes / (t_graph * 1e-3) / 1e9, 1),
+            "frac_of_nominal": round(nbytes / (t_graph * 1e-3) / 1e9 / NOMINAL_HBM_GBS, 4),
             "speedup_vs_per_segment": round(t_per / t_graph, 1)}
 
 
@@ -777,35 +791,50 @@ def run_e2e(args, torch, dev, stream, ops, nb, Rn, Sn, T, op_reduce, op_scan, op
 
 
 # --------------------------------------------------------------------- oracle
-def oracle_rate(sz, only, scale):
-    """GB/s of the CPU oracle on samples of the workload, weighted by the
-    full step's bytes.  scale picks the sample size (1.0 ~ 10 s of work)."""
-    import numpy as np
+ORACLE_SCALE = 1.0          # the oracle's sample: reduce 2^26, scan 2^24, transpose 4096^2 (both CPU legs)
+
+
+def oracle_samples(sz, only, scale=ORACLE_SCALE):
+    """Seeded inputs of the CPU oracle's bounded sample of the workload."""
     import synth
-    from oracle import ops as O
-    full = op_bytes(sz)
     nr = max(1 << 12, int((1 << 26) * scale))
     ns = max(1 << 12, int((1 << 24) * scale))
     tt = max(64, int(4096 * scale ** 0.5))
-    samples = {}
-    t_est = 0.0
+    out = {}
     if not only or "reduce" in only:
-        x = synth.ints_pm1000(nr, seed=11).numpy()
-        t = time.perf_counter(); O.reduce(x, [nr], [], 0); dt_ = time.perf_counter() - t
-        t_est += dt_ * full["reduce"] / (4 * nr)
-        samples["reduce"] = nr
+        out["reduce"] = synth.ints_pm1000(nr, seed=11).numpy()
     if not only or "scan" in only:
-        x = synth.uniform_grid(ns, seed=12).numpy()
-        t = time.perf_counter(); O.scan(x, np.zeros(ns, np.float32), [ns], [], 0); dt_ = time.perf_counter() - t
-        t_est += dt_ * full["scan"] / (8 * ns)
-        samples["scan"] = ns
+        out["scan"] = synth.uniform_grid(ns, seed=12).numpy()
     if not only or "transpose" in only:
-        x = synth.normal_f32(tt * tt, seed=13).numpy().reshape(tt, tt)
-        t = time.perf_counter(); O.transpose2d(x); dt_ = time.perf_counter() - t
-        t_est += dt_ * full["transpose"] / (8 * tt * tt)
-        samples["transpose"] = [tt, tt]
-    step_bytes = sum(full[k] for k in (only or full))
-    return step_bytes / t_est / 1e9, samples
+        out["transpose"] = synth.normal_f32(tt * tt, seed=13).numpy().reshape(tt, tt)
+    return out
+
+
+def sample_desc(samples):
+    d = {k: (list(v.shape) if k == "transpose" else v.size) for k, v in samples.items()}
+    return f"reduce {d.get('reduce')} int32, scan {d.get('scan')} FP32, transpose {d.get('transpose')} FP32"
+
+
+def oracle_rate(sz, samples):
+    """GB/s of the CPU oracle on the samples, weighted by the full step's
+    bytes: each op's sample time is scaled to its full size."""
+    import numpy as np
+    from oracle import ops as O
+    full = op_bytes(sz)
+    t_est = 0.0
+    for op, x in samples.items():
+        t = time.perf_counter()
+        if op == "reduce":
+            O.reduce(x, [x.size], [], 0)
+            t_est += (time.perf_counter() - t) * full["reduce"] / (4 * x.size)
+        elif op == "scan":
+            O.scan(x, np.zeros(x.size, np.float32), [x.size], [], 0)
+            t_est += (time.perf_counter() - t) * full["scan"] / (8 * x.size)
+        else:
+            O.transpose2d(x)
+            t_est += (time.perf_counter() - t) * full["transpose"] / (8 * x.size)
+    step_bytes = sum(full[k] for k in samples)
+    return step_bytes / t_est / 1e9
 
 
 def _oracle_task(task):
@@ -824,62 +853,56 @@ def _oracle_task(task):
     return time.perf_counter() - t
 
 
-def oracle_rate_all_cores(sz, only, cores):
+def oracle_rate_all_cores(sz, samples, cores):
     """The oracle as it stands on every host core at once: each worker runs
-    its own copy of the samples (independent problems, weak scaling); GB/s =
-    cores x the step-weighted bytes / the slowest worker's time per op."""
+    its own copy of the same samples (independent problems, weak scaling);
+    GB/s = cores x the step-weighted bytes / the slowest worker's time per op."""
     import multiprocessing as mp
     from concurrent.futures import ProcessPoolExecutor
-    import synth
     full = op_bytes(sz)
-    nr, ns, tt = 1 << 24, 1 << 22, 2048
-    tasks = []
-    if not only or "reduce" in only:
-        tasks.append(("reduce", synth.ints_pm1000(nr, seed=11).numpy(), full["reduce"] / (4 * nr)))
-    if not only or "scan" in only:
-        tasks.append(("scan", synth.uniform_grid(ns, seed=12).numpy(), full["scan"] / (8 * ns)))
-    if not only or "transpose" in only:
-        tasks.append(("transpose", synth.normal_f32(tt * tt, seed=13).numpy().reshape(tt, tt),
-                      full["transpose"] / (8 * tt * tt)))
+    scale = {"reduce": lambda x: full["reduce"] / (4 * x.size), "scan": lambda x: full["scan"] / (8 * x.size),
+             "transpose": lambda x: full["transpose"] / (8 * x.size)}
     t_est = 0.0
     # a pool that fails to start raises (BrokenProcessPool) instead of retrying for ever
     with ProcessPoolExecutor(max_workers=cores, mp_context=mp.get_context("spawn")) as pool:
-        list(pool.map(_oracle_task, [("reduce", tasks[0][1][:4096])] * cores, timeout=120))   # workers up
-        for op, x, scale in tasks:
-            t_est += max(pool.map(_oracle_task, [(op, x)] * cores, timeout=300)) * scale
-    step_bytes = sum(full[k] for k in (only or full))
-    return cores * step_bytes / t_est / 1e9, {"reduce": nr, "scan": ns, "transpose": [tt, tt]}
+        first = next(iter(samples.items()))
+        list(pool.map(_oracle_task, [(first[0], first[1][:64])] * cores, timeout=120))   # workers up
+        for op, x in samples.items():
+            t_est += max(pool.map(_oracle_task, [(op, x)] * cores, timeout=600)) * scale[op](x)
+    step_bytes = sum(full[k] for k in samples)
+    return cores * step_bytes / t_est / 1e9
 
 
 def cpu_baseline(sz, only):
-    v, s = oracle_rate(sz, only, 1.0)
+    samples = oracle_samples(sz, only)
+    v = oracle_rate(sz, samples)
     out = {"value": round(v, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
-           "sample": f"reduce {s.get('reduce')} int32, scan {s.get('scan')} FP32, transpose {s.get('transpose')} "
-                     "FP32 (NumPy, single-threaded); rates weighted by the full step's bytes"}
+           "sample": sample_desc(samples) + " (NumPy, single-threaded; the reference arm's sample); rates "
+                     "weighted by the full step's bytes"}
     cores = os.cpu_count() or 1
     if cores > 1:
         try:
-            va, sa = oracle_rate_all_cores(sz, only, cores)
+            va = oracle_rate_all_cores(sz, samples, cores)
             out["all_cores"] = {"value": round(va, 3), "unit": "GB/s", "cores": cores,
-                                "sample": f"one copy per core of reduce {sa['reduce']} int32, scan {sa['scan']} "
-                                          f"FP32, transpose {sa['transpose']} FP32 (spawned workers)"}
+                                "sample": "one copy per core of the same sample (spawned workers)"}
         except Exception as e:                           # no process pool here: the single-core figure stands
             out["all_cores"] = {"unavailable": str(e)[:200]}
     return out
 
 
 def run_reference(args, rank, world):
+    """The CPU oracle as it stands, timed on the same bounded sample as the
+    default line's cpu_baseline: inputs drawn once, then W untimed and K timed
+    passes over the sample, each pass's rate weighted by the full step's bytes."""
     if rank != 0:
         return None
     sz = sizes(args.small)
     only = set(args.ops.split(",")) if args.ops else None
+    samples = oracle_samples(sz, only)
     for _ in range(args.warmup):
-        oracle_rate(sz, only, 1 / 64)
+        oracle_rate(sz, samples)
     t0 = time.perf_counter()
-    rates = []
-    for _ in range(args.steps):
-        r, samples = oracle_rate(sz, only, 1 / 64)
-        rates.append(r)
+    rates = [oracle_rate(sz, samples) for _ in range(args.steps)]
     el = time.perf_counter() - t0
     value = len(rates) / sum(1.0 / r for r in rates)     # bytes-weighted mean rate
     return {"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": world,
@@ -889,8 +912,8 @@ def run_reference(args, rank, world):
             "config": {"workload": WORKLOAD + (" (small)" if args.small else ""), "reduce_n": sz["reduce_n"],
                        "scan_n": sz["scan_n"], "transpose": [sz["T"], sz["T"]]},
             "cpu_baseline": {"value": round(value, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
-                             "sample": f"per step: reduce {samples.get('reduce')}, scan {samples.get('scan')}, "
-                                       f"transpose {samples.get('transpose')}; rates weighted by the full step's bytes"},
+                             "sample": "per step: " + sample_desc(samples) + "; rates weighted by the full step's "
+                                       "bytes"},
             "e2e": {"value": round(value, 3), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "gpu_launches": 0}
 
