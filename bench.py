@@ -146,6 +146,8 @@ def run_ours(args, rank, world, local_rank):
 
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
+    if args.generic:
+        D.desc_force_generic(True)
     sz = sizes(args.small)
     nb = op_bytes(sz)
     Rn, Sn, T = sz["reduce_n"], sz["scan_n"], sz["T"]
@@ -278,7 +280,7 @@ def run_ours(args, rank, world, local_rank):
                        "reduce_n": Rn, "scan_n": Sn, "transpose": [T, T],
                        "reduce_view": "group(1024)[[block]].group(32)[[warp]][[thread]]",
                        "l2": "inputs larger than L2 (129 MB); no flush", "parallelism": f"replicas x{world}",
-                       "schedules": schedules},
+                       "schedules": schedules, "general_kernels": bool(args.generic)},
             "ops": per_op, "roofline": roofline, "gpu_launches": K * len(ops), "e2e": e2e}
     if concurrent:
         line["step_concurrent"] = concurrent
@@ -666,11 +668,30 @@ def run_split_launch(torch, D, synth, dev, iters=20, replays=10):
     return res
 
 
+def segment_schedules(D, stream, x, off, out, sums, ws, reps=5):
+    """Every schedule of the batched call timed on these buffers (CUDA-event
+    medians, desc_tune_measure): microseconds per candidate."""
+    import ctypes
+    nseg = off.numel() - 1
+    p = D.make_problem(D.OP_SEGMENTED, D.F32, x.numel(), nseg, off[1:].cpu() - off[:-1].cpu())
+    b = D.TuneBuffers()
+    b.inp, b.out, b.sums, b.offsets = x.data_ptr(), out.data_ptr(), sums.data_ptr(), off.data_ptr()
+    b.ws, b.ws_bytes = ws.data_ptr(), ws.numel()
+    nc = D.candidate_count(D.OP_SEGMENTED)
+    us = (ctypes.c_float * nc)()
+    D._check(D.lib().desc_tune_measure(p.ref(), ctypes.byref(b), reps, D._stream(stream), us), "desc_tune_measure")
+    names = ["tiles 16384", "tiles 8192", "tiles 4096", "warp per segment", "CTA per segment"]
+    return {names[c]: round(us[c], 1) for c in range(nc)}
+
+
 def run_segmented(torch, D, synth, dev, stream, nseg=20000):
     """20,000 FP32 segments, lengths log-uniform in [1, 2^20]: every segment
     reduced and inclusive-scanned.  One graph-captured persistent launch vs.
     the same call launched directly vs. one scan + one reduce launch per
-    segment.  GB/s counts 8 B per element + 8 B of offsets + 4 B per sum."""
+    segment.  GB/s counts 8 B per element + 8 B of offsets + 4 B per sum.
+    Also every schedule of the call (tiles of three sizes, a warp or a CTA
+    per segment) on this workload and on 2,000,000 segments of at most 256
+    points, where a group of threads per segment pays."""
     L = synth.loguniform_lengths(nseg, seed=7, device=dev)
     off = synth.offsets_from_lengths(L)
     total = int(off[-1])
@@ -686,13 +707,30 @@ def run_segmented(torch, D, synth, dev, stream, nseg=20000):
     t_per = _time(torch, stream, lambda: D.desc_segmented_reduce_scan_per_segment(x, h, out=out, sums=sums, ws=ws,
                                                                                  stream=stream), 1)
     g.close()
+    sched = segment_schedules(D, stream, x, off, out, sums, ws)
+    del x, out, sums, ws, g
     nbytes = 8 * total + 8 * (nseg + 1) + 4 * nseg
+    # many short segments
+    ns2 = 2_000_000
+    L2 = synth.loguniform_lengths(ns2, seed=9, max_len=256, device=dev)
+    off2 = synth.offsets_from_lengths(L2)
+    tot2 = int(off2[-1])
+    x2 = synth.uniform_grid(tot2, seed=10, device=dev)
+    o2 = torch.empty_like(x2)
+    s2 = torch.empty(ns2, device=dev)
+    ws2 = D.desc_segmented_workspace(ns2, tot2, dev)
+    sched_short = segment_schedules(D, stream, x2, off2, o2, s2, ws2)
+    b2 = 8 * tot2 + 8 * (ns2 + 1) + 4 * ns2
+    best2 = min(sched_short.values())
+    del x2, o2, s2, ws2
     if D.desc_stream_status(stream) != 0:
         raise RuntimeError("device status after segmented")
     return {"segments": nseg, "elements": total, "graph_ms": round(t_graph, 4), "direct_ms": round(t_direct, 4),
             "per_segment_ms": round(t_per, 3), "graph_GB/s": round(nbytes / (t_graph * 1e-3) / 1e9, 1),
             "frac_of_nominal": round(nbytes / (t_graph * 1e-3) / 1e9 / NOMINAL_HBM_GBS, 4),
-            "speedup_vs_per_segment": round(t_per / t_graph, 1)}
+            "speedup_vs_per_segment": round(t_per / t_graph, 1), "schedules_us": sched,
+            "short_segments": {"segments": ns2, "elements": tot2, "max_len": 256, "schedules_us": sched_short,
+                               "best_GB/s": round(b2 / (best2 * 1e-6) / 1e9, 1)}}
 
 
 def run_e2e(args, torch, dev, stream, ops, nb, Rn, Sn, T, op_reduce, op_scan, op_transpose, world):
@@ -932,6 +970,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the matmul and segmented measurements")
     ap.add_argument("--no-model", action="store_true", help="skip the learned-schedule regret study")
     ap.add_argument("--no-tune", action="store_true", help="time the default schedules, without autotuning")
+    ap.add_argument("--generic", action="store_true",
+                    help="run the step's views through the general kernels (desc_force_generic), for profiles")
     ap.add_argument("--save-tune", default="", help="save the tuned schedule table to this file")
     ap.add_argument("--load-tune", default="", help="use a saved schedule table instead of tuning")
     ap.add_argument("--case", choices=["step", "matmul", "segmented", "overhead", "split"], default="step",

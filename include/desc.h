@@ -483,7 +483,9 @@ int32_t desc_segmented_reduce_scan_per_segment(const int64_t *h_offsets, int64_t
  *                      loads, r = read-only path without L1 allocation
  *   DESC_OP_SCAN       look-back scan: tile of 4096 x {4, 2, 1} elements
  *   DESC_OP_TRANSPOSE  tiles of {64, 32} squared
- *   DESC_OP_SEGMENTED  CSR look-back scan: tile of 4096 x {4, 2, 1} elements
+ *   DESC_OP_SEGMENTED  CSR look-back scan: tile of 4096 x {4, 2, 1} elements;
+ *                      or one warp (3), or one CTA of 256 threads (4), per
+ *                      segment, walking it in steps of 4 points per thread
  *   DESC_OP_MATMUL     tensor-core forms: {CTA pairs on 256 x 256 tiles where
  *                      the 128-row tiles pair up, one CTA per 128 x 256 tile}
  *                      x {wide, narrow} rasterisation groups: 16 / 4 tile

@@ -26,6 +26,16 @@ constexpr int kScanSubTile = 4096;
 constexpr int kScanSubCands[] = {4, 2, 1};
 constexpr int kNumScanCands = sizeof(kScanSubCands) / sizeof(kScanSubCands[0]);
 
+// Segmented (CSR) scans: the look-back scan over tiles of 4096 x sub points
+// (threads = 0: every segment shares the tiles), or one group of `threads`
+// threads per segment, walking it in steps of threads x 4 points.
+struct SegCand {
+  int sub;
+  int threads;
+};
+constexpr SegCand kSegCands[] = {{4, 0}, {2, 0}, {1, 0}, {0, 32}, {0, 256}};
+constexpr int kNumSegCands = sizeof(kSegCands) / sizeof(kSegCands[0]);
+
 // Tiled transpose: square tiles of this many rows and columns.
 constexpr int kTransposeTiles[] = {64, 32};
 constexpr int kNumTransposeCands = sizeof(kTransposeTiles) / sizeof(kTransposeTiles[0]);

@@ -1211,6 +1211,92 @@ int32_t launch_scan_contig(int32_t dtype, const void *in, void *out, int64_t n, 
                   : run_scan<float, PLAIN>(i, o, a, ws, ws_bytes, s, cand, flags, none);
 }
 
+// ---- segments by groups of threads -----------------------------------------
+// One group of G threads (a warp, or the whole CTA) per CSR segment, the
+// groups striding over the segments.  The group walks its segment in steps of
+// G x 4 points: each thread loads 4 consecutive points, scans them, the group
+// scans the thread totals (shuffles; for a CTA also the warp totals in shared
+// memory), applies the carry of the earlier steps and writes; the carry then
+// takes in the step's total (compensated for FP32 sums).  No look-back and no
+// workspace: suited to many short segments, where the tiles would hold many
+// segment heads.
+constexpr int kSegGroupThreads = 256, kSegItems = 4;
+
+template <class T, class O, bool EXCL, int G>
+__global__ void __launch_bounds__(kSegGroupThreads) seg_group_kernel(const T *__restrict__ in, T *__restrict__ out,
+                                                                     const int64_t *__restrict__ offsets, int64_t nseg,
+                                                                     T *__restrict__ sums) {
+  using CT = typename O::C;
+  constexpr int kGroups = kSegGroupThreads / G;
+  constexpr int kStep = G * kSegItems;
+  __shared__ T sh_w[kSegGroupThreads / 32];
+  const int gl = threadIdx.x % G, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int64_t sg = int64_t(blockIdx.x) * kGroups; sg < nseg; sg += int64_t(gridDim.x) * kGroups) {
+    const int64_t s = sg + threadIdx.x / G;
+    const bool live = s < nseg;                         // every thread takes part in the barriers
+    const int64_t a = live ? offsets[s] : 0, b = live ? offsets[s + 1] : 0;
+    CT carry = CT::zero();
+    // with G = the CTA, every thread has the same segment and step count, so
+    // the barriers inside the step are reached by all of them
+    const int64_t nsteps = b > a ? (b - a + kStep - 1) / kStep : 0;
+    for (int64_t k = 0; k < nsteps; ++k) {
+      const int64_t p0 = a + k * kStep + int64_t(gl) * kSegItems;
+      T v[kSegItems];
+#pragma unroll
+      for (int i = 0; i < kSegItems; ++i) v[i] = p0 + i < b ? in[p0 + i] : O::id();
+#pragma unroll
+      for (int i = 1; i < kSegItems; ++i) v[i] = O::comb(v[i - 1], v[i]);
+      T t = v[kSegItems - 1];                           // inclusive scan of the thread totals
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const T u = __shfl_up_sync(0xffffffffu, t, off);
+        if (lane >= off) t = O::comb(u, t);
+      }
+      T ex = __shfl_up_sync(0xffffffffu, t, 1);
+      if (lane == 0) ex = O::id();
+      T total = __shfl_sync(0xffffffffu, t, 31);
+      if (G == kSegGroupThreads) {                      // across the warps of the CTA
+        if (lane == 31) sh_w[warp] = t;
+        __syncthreads();
+        T wp = O::id();
+        total = O::id();
+#pragma unroll
+        for (int w = 0; w < kSegGroupThreads / 32; ++w) {
+          const T x = sh_w[w];
+          if (w < warp) wp = O::comb(wp, x);
+          total = O::comb(total, x);
+        }
+        ex = O::comb(wp, ex);
+        __syncthreads();                                // sh_w is reused by the next step
+      }
+      // results: carry, then the thread's prefix within the step, then the item
+      T prev = O::apply(ex, carry);                     // everything before this thread's first item
+#pragma unroll
+      for (int i = 0; i < kSegItems; ++i) {
+        const T inc = O::apply(O::comb(ex, v[i]), carry);
+        if (p0 + i < b) out[p0 + i] = EXCL ? prev : inc;
+        prev = inc;
+      }
+      carry = carry.plus(CT::of(total));
+    }
+    if (live && gl == 0 && sums) sums[s] = O::apply(O::id(), carry);
+  }
+}
+
+template <class T, class O, bool EXCL>
+int32_t run_seg_group(const T *in, T *out, const int64_t *offsets, int64_t nseg, T *sums, int threads,
+                      cudaStream_t s) {
+  const int groups = kSegGroupThreads / threads;
+  const int64_t ctas = std::max<int64_t>(1, std::min<int64_t>((nseg + groups - 1) / groups, 152 * 16));
+  if (threads == 32)
+    seg_group_kernel<T, O, EXCL, 32><<<(unsigned)ctas, kSegGroupThreads, 0, s>>>(in, out, offsets, nseg, sums);
+  else
+    seg_group_kernel<T, O, EXCL, kSegGroupThreads><<<(unsigned)ctas, kSegGroupThreads, 0, s>>>(in, out, offsets,
+                                                                                                 nseg, sums);
+  DESC_CUDA_TRY(cudaGetLastError());
+  return DESC_OK;
+}
+
 namespace {
 
 template <class T, class S>
@@ -1366,6 +1452,26 @@ int32_t launch_scan_csr(int32_t dtype, const void *in, void *out, int64_t n, con
                         int64_t nseg, void *sums, int32_t flags, void *ws, size_t ws_bytes,
                         desc_stream_t st, int cand) {
   cudaStream_t s = reinterpret_cast<cudaStream_t>(st);
+  const SegCand sc = kSegCands[(cand >= 0 && cand < kNumSegCands) ? cand : 0];
+  if (sc.threads > 0 && !(flags & DESC_DEBUG_STALL_TILE)) {   // a group of threads per segment
+    const bool ex = (flags & DESC_EXCLUSIVE) != 0;
+    auto go = [&](auto tag) -> int32_t {
+      using T = decltype(tag);
+      const T *i = static_cast<const T *>(in);
+      T *o = static_cast<T *>(out);
+      T *sm = static_cast<T *>(sums);
+      if (flags & DESC_MAX)
+        return ex ? run_seg_group<T, ExtOp<T, true>, true>(i, o, offsets, nseg, sm, sc.threads, s)
+                  : run_seg_group<T, ExtOp<T, true>, false>(i, o, offsets, nseg, sm, sc.threads, s);
+      if (flags & DESC_MIN)
+        return ex ? run_seg_group<T, ExtOp<T, false>, true>(i, o, offsets, nseg, sm, sc.threads, s)
+                  : run_seg_group<T, ExtOp<T, false>, false>(i, o, offsets, nseg, sm, sc.threads, s);
+      return ex ? run_seg_group<T, SumOp<T>, true>(i, o, offsets, nseg, sm, sc.threads, s)
+                : run_seg_group<T, SumOp<T>, false>(i, o, offsets, nseg, sm, sc.threads, s);
+    };
+    return dtype == DESC_I32 ? go(int32_t(0)) : go(0.f);
+  }
+  if (sc.threads == 0) cand = cand >= 0 && cand < kNumScanCands ? cand : 0;   // tiles of 4096 x sub
   ScanArgs a{};
   a.n = n;
   a.offsets = offsets;

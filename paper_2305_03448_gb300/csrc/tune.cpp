@@ -79,7 +79,7 @@ int ncand(int32_t op) {
     case DESC_OP_REDUCE: return reduce_candidates();
     case DESC_OP_SCAN: return scan_candidates();
     case DESC_OP_TRANSPOSE: return transpose_candidates();
-    case DESC_OP_SEGMENTED: return scan_candidates();
+    case DESC_OP_SEGMENTED: return kNumSegCands;
     case DESC_OP_MATMUL: return mm_candidates();
     default: return 0;
   }
@@ -276,6 +276,11 @@ extern "C" int32_t desc_features(const desc_problem *p, int32_t cand, float *out
     out[20] = lg((double)c.group_rows) / 16.f;
     out[30] = lg((double)p->k + 1.0) / 32.f;
     out[31] = (float)c.pairs;
+  } else if (p->op == DESC_OP_SEGMENTED) {
+    const SegCand &c = kSegCands[cand];
+    out[18] = lg(c.threads ? double(c.threads) * 4 : double(kScanSubTile) * c.sub) / 32.f;   // points per step
+    out[19] = (c.threads ? 4.f : 16.f) / 16.f;                                            // items per thread
+    out[20] = c.threads ? lg((double)c.threads) / 16.f : 0.f;                              // threads per segment
   } else {
     out[18] = lg(double(kScanSubTile) * kScanSubCands[cand]) / 32.f;
     out[19] = 16.f / 16.f;

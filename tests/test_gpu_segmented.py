@@ -92,3 +92,32 @@ def test_bad_offsets_are_rejected_when_checked():
     assert e.value.status == 2
     with pytest.raises(D.DescError):
         D.SegmentedGraph(x, off, torch.empty_like(x), torch.empty(3, device="cuda"))
+
+
+@pytest.mark.parametrize("cand", range(5))
+@pytest.mark.parametrize("lens", ["short", "mixed", "long"])
+def test_every_segment_schedule(cand, lens):
+    """Each schedule of the batched call, forced -- the look-back scan over
+    tiles of 16384 / 8192 / 4096 points, one warp per segment, one CTA per
+    segment -- with sums, maxima, minima and exclusive scans, empty and
+    one-point segments, against the oracle."""
+    spec = {"short": (3000, 40, 4), "mixed": (600, 20000, 7), "long": (6, 300000, 0)}[lens]
+    off = segments(spec[0], spec[1], seed=cand + spec[0], zero_every=spec[2])
+    n = int(off[-1])
+    D.desc_force_candidate(D.OP_SEGMENTED, cand)
+    try:
+        for dt in ("i32", "f32"):
+            x = synth.ints_pm1000(n, seed=cand + 1) if dt == "i32" else synth.uniform_grid(n, seed=cand + 2)
+            scan, sums = D.desc_segmented_reduce_scan(x.cuda(), off.cuda())
+            check(x, off, scan, sums)
+            for op, flag in (("max", D.MAX), ("min", D.MIN), ("sum", D.EXCLUSIVE), ("max", D.MAX | D.EXCLUSIVE)):
+                sc, tot = D.desc_segmented_reduce_scan(x.cuda(), off.cuda(), flags=flag)
+                want, wtot, pa, sa = O.segmented_op(x.numpy(), off.numpy(), op, bool(flag & D.EXCLUSIVE))
+                if dt == "i32" or op != "sum":
+                    assert np.array_equal(sc.cpu().numpy().astype(np.float64), want.astype(np.float64))
+                    assert np.array_equal(tot.cpu().numpy().astype(np.float64), wtot.astype(np.float64))
+                else:
+                    assert np.all(np.abs(sc.cpu().numpy().astype(np.float64) - want) <= TOL * pa + 1e-30)
+                    assert np.all(np.abs(tot.cpu().numpy().astype(np.float64) - wtot) <= TOL * sa + 1e-30)
+    finally:
+        D.desc_force_candidate(D.OP_SEGMENTED, -1)

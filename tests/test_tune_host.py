@@ -14,7 +14,7 @@ V = D
 
 
 def test_candidate_counts(desc_lib):
-    assert [D.candidate_count(o) for o in range(5)] == [8, 3, 2, 3, 6]
+    assert [D.candidate_count(o) for o in range(5)] == [8, 3, 2, 5, 6]
     with pytest.raises(D.DescError):
         D.candidate_count(7)
 
