@@ -445,6 +445,19 @@ __global__ void __launch_bounds__(kThreads + 32, 3) scan_kernel(const T *in, T *
     sh_tile = atomicAdd(&ws->ticket, 1u);
     sh_go = 0;
   }
+  if (warp < kWarps) {
+    // While the ticket travels: pull into L2 the tile this CTA's index
+    // suggests (CTAs take tickets in about the order they start, so a wrong
+    // guess is a tile a neighbour loads soon; nothing reads it from here).
+    // One prefetch per 32 points: a 128-byte line where the points are
+    // contiguous.
+    const int64_t guess = int64_t(blockIdx.x) * kTile;
+#pragma unroll
+    for (int k = 0; k < kTile / 32 / kThreads; ++k) {
+      const int64_t g = guess + 32 * int64_t(k * kThreads + tid);
+      if (g < n) asm volatile("prefetch.global.L2 [%0];" ::"l"(in + addr(g)));
+    }
+  }
   __syncthreads();
   const int64_t tile = sh_tile;
   const int64_t t0 = tile * kTile;
@@ -861,6 +874,10 @@ __global__ void __launch_bounds__(kMapThreads + 32) scan_map_kernel(const T *__r
   }
   if (mode == CSR)
     for (int i = tid; i < kMapTile / 32; i += kMapThreads + 32) sh_heads[i] = 0u;
+  if (warp < kMapThreads / 32) {                       // the guessed tile into L2 (as scan_kernel)
+    const int64_t g = int64_t(blockIdx.x) * kMapTile + 16 * int64_t(tid);
+    if (g < args.n) asm volatile("prefetch.global.L2 [%0];" ::"l"(in + map_elem(m, g)));
+  }
   __syncthreads();
   const int64_t tile = sh_tile, t0 = tile * kMapTile, n = args.n;
   const int64_t tend = min(t0 + kMapTile, n);
