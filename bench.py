@@ -611,6 +611,49 @@ def run_view_overhead(torch, D, synth, dev, stream, reps=100, mbs=(256, 512, 102
     return out
 
 
+def run_sanitize_case(torch, D, synth, dev):
+    """One small call of every memory-bound kernel (for a race checker):
+    reduce through the hierarchical view and a general map, the look-back
+    scan (plain, per-block segments, mapped, CSR), the map scan (arg
+    operator), the per-segment group schedules, the tiled transpose, the
+    tiled general copy and the element-wise copy.  Returns the call names."""
+    V = D
+    n = 1 << 16
+    x = synth.ints_pm1000(n, seed=1, device=dev)
+    xf = synth.uniform_grid(n, seed=2, device=dev)
+    hier = [("group", 1024, 0), ("select", V.BLOCK, V.X), ("group", 32, 0), ("select", V.WARP, V.X),
+            ("select", V.THREAD, V.X)]
+    calls = []
+    D.desc_reduce(x, [n], hier, V.BLOCK, (n // 1024, 1, 1), (1024, 1, 1)); calls.append("reduce runs")
+    D.desc_reduce(x, [256, 256], [("transpose", 0), ("select", V.BLOCK, V.X)], V.BLOCK, (256, 1, 1), (1, 1, 1))
+    calls.append("reduce affine")
+    D.desc_scan(xf, [n], [], V.GRID); calls.append("scan")
+    D.desc_scan(x, [n], [("group", 4096, 0), ("select", V.BLOCK, V.X)], V.BLOCK, (16, 1, 1), (1, 1, 1))
+    calls.append("scan per block")
+    D.desc_scan(xf, [n], [("reverse", 0)], V.GRID); calls.append("scan mapped")
+    D.desc_scan(x, [n], [], V.GRID, flags=D.ARGMAX); calls.append("map scan (argmax)")
+    L = synth.loguniform_lengths(100, seed=3, max_len=2000, device=dev)
+    off = synth.offsets_from_lengths(L)
+    xs = synth.uniform_grid(int(off[-1]), seed=4, device=dev)
+    D.desc_segmented_reduce_scan(xs, off); calls.append("segmented tiles")
+    for c in (3, 4):
+        D.desc_force_candidate(D.OP_SEGMENTED, c)
+        D.desc_segmented_reduce_scan(xs, off); calls.append(f"segmented group {c}")
+    D.desc_force_candidate(D.OP_SEGMENTED, -1)
+    t = synth.normal_f32(300 * 500, seed=5, device=dev).reshape(300, 500)
+    D.desc_transpose(t, [300, 500], [("transpose", 0)], torch.empty(500, 300, device=dev), [500, 300], [])
+    calls.append("transpose")
+    c3 = synth.normal_f32(6 * 40 * 48, seed=6, device=dev).reshape(6, 40, 48)
+    D.desc_transpose(c3, [6, 40, 48], [("transpose", 0), ("transpose", 1)], torch.empty(40, 48, 6, device=dev),
+                     [40, 48, 6], []); calls.append("general copy (tiled)")
+    D.desc_transpose(t, [300, 500], [("reverse", 1), ("transpose", 0)], torch.empty(500, 300, device=dev),
+                     [500, 300], []); calls.append("general copy")
+    torch.cuda.synchronize()
+    if D.desc_stream_status() != 0:
+        raise RuntimeError("device status after the sanitizer case")
+    return calls
+
+
 def run_split_launch(torch, D, synth, dev, iters=20, replays=10):
     """One launch whose first blocks reduce and whose other blocks transpose
     (desc_split_reduce_transpose) against the two separate launches, both
@@ -974,7 +1017,7 @@ def main():
                     help="run the step's views through the general kernels (desc_force_generic), for profiles")
     ap.add_argument("--save-tune", default="", help="save the tuned schedule table to this file")
     ap.add_argument("--load-tune", default="", help="use a saved schedule table instead of tuning")
-    ap.add_argument("--case", choices=["step", "matmul", "segmented", "overhead", "split"], default="step",
+    ap.add_argument("--case", choices=["step", "matmul", "segmented", "overhead", "split", "sanitize"], default="step",
                     help="matmul / segmented: run only that measurement (for profiler captures)")
     ap.add_argument("--mm-n", type=int, default=8192, help="matmul size for --case matmul")
     ap.add_argument("--mm-prec", default="split3,bf16,fp32_simt",
@@ -1011,6 +1054,8 @@ def main():
             line = {"case": "split", "split_launch": run_split_launch(torch, D, synth, dev)}
         elif args.case == "overhead":
             line = {"case": "overhead", "view_overhead": run_view_overhead(torch, D, synth, dev, stream)}
+        elif args.case == "sanitize":
+            line = {"case": "sanitize", "calls": run_sanitize_case(torch, D, synth, dev)}
         else:
             line = {"case": "segmented", "segmented": run_segmented(torch, D, synth, dev, stream, nseg=args.seg_count)}
     else:
