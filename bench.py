@@ -291,6 +291,7 @@ def run_ours(args, rank, world, local_rank):
         line["segmented"] = run_segmented(torch, D, synth, dev, stream)
         line["view_overhead"] = run_view_overhead(torch, D, synth, dev, stream)
         line["split_launch"] = run_split_launch(torch, D, synth, dev)
+        line["operators"] = run_operators(torch, D, dev, stream, xr, xs, pk)
         if not args.no_model:
             line["schedule_model"] = run_schedule_model(torch, D, synth)
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -608,6 +609,46 @@ def run_view_overhead(torch, D, synth, dev, stream, reps=100, mbs=(256, 512, 102
                               "overhead_pct": round(100 * (v[True] / v[False] - 1), 1)} for k, v in row.items()}
     if D.desc_stream_status(stream) != 0:
         raise RuntimeError("device status after the view-overhead runs")
+    return out
+
+
+def run_operators(torch, D, dev, stream, xr, xs, pk, reps=10):
+    """The operators beyond the sum at full size: int32 reduce of 2^30
+    values and FP32 / int32 scans of 2^28 values with each operator family
+    (maximum, product, xor, arg-maximum), CUDA-event means of `reps` calls,
+    GB/s of algorithmic bytes (reduce 4 B, scan 8 B per element) and the
+    fraction of the measured copy peak."""
+    V = D
+    Rn, Sn = xr.numel(), xs.numel()
+    out = {}
+    r_out = torch.empty(1, dtype=torch.int32, device=dev)
+    s_out = torch.empty(Sn, dtype=torch.int32, device=dev)
+    xsi = xs.view(torch.int32)                         # the same bytes as int32 for the bitwise scans
+    import ctypes
+    def ws_reduce(n, dt):
+        b = ctypes.c_size_t(0)
+        D.lib().desc_reduce_workspace_size(ctypes.byref(D.make_view([n], [])), None, V.GRID, dt, ctypes.byref(b))
+        return torch.empty(max(b.value, 1), dtype=torch.uint8, device=dev)
+    def ws_scan(n, dt):
+        b = ctypes.c_size_t(0)
+        D.lib().desc_scan_workspace_size(ctypes.byref(D.make_view([n], [])), None, V.GRID, dt, ctypes.byref(b))
+        return torch.empty(max(b.value, 1), dtype=torch.uint8, device=dev)
+    wr, ws_ = ws_reduce(Rn, V.I32), ws_scan(Sn, V.F32)
+    for name, flag in (("max", D.MAX), ("prod", D.PROD), ("xor", D.XOR), ("argmax", D.ARGMAX)):
+        ms = _time(torch, stream, lambda: D.desc_reduce(xr, [Rn], [], V.GRID, out=r_out, ws=wr, flags=flag,
+                                                         stream=stream), reps)
+        gbs = 4 * Rn / (ms * 1e-3) / 1e9
+        out[f"reduce_i32_{name}"] = {"ms": round(ms, 4), "GB/s": round(gbs, 1), "frac": round(gbs / pk["hbm_gbs"], 4)}
+    for name, x, flag in (("f32_max", xs, D.MAX), ("f32_prod", xs, D.PROD), ("i32_xor", xsi, D.XOR),
+                          ("f32_argmax", xs, D.ARGMAX)):
+        o = s_out if flag in (D.XOR, D.ARGMAX) else s_out.view(torch.float32)
+        ms = _time(torch, stream, lambda: D.desc_scan(x, [Sn], [], V.GRID, out=o, ws=ws_, flags=flag,
+                                                       stream=stream), reps)
+        gbs = 8 * Sn / (ms * 1e-3) / 1e9
+        out[f"scan_{name}"] = {"ms": round(ms, 4), "GB/s": round(gbs, 1), "frac": round(gbs / pk["hbm_gbs"], 4)}
+    if D.desc_stream_status(stream) != 0:
+        raise RuntimeError("device status after the operators")
+    del s_out, wr, ws_
     return out
 
 

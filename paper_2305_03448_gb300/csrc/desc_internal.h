@@ -65,9 +65,13 @@ bool same_map_quick(const desc_lowered &a, const desc_lowered &b);
 // Pointer checks: device (or managed) memory and element alignment.
 int32_t check_device_ptr(const void *p, size_t align);
 
-// Device status words of the translation units that hold bounded waits.
-int32_t scan_status_take();   // k_scan.cu
-int32_t mm_status_take();     // k_mm_tc.cu
+// Device status words of the translation units that hold bounded waits
+// (scan_status_take reads the four scan units' words).
+int32_t scan_status_take();          // k_scan.cu
+int32_t scan_status_take_ops();      // k_scan_ops.cu
+int32_t scan_status_take_mapped();   // k_scan_mapped.cu
+int32_t scan_status_take_map();      // k_scan_map.cu
+int32_t mm_status_take();            // k_mm_tc.cu
 
 // ----- launchers (k_*.cu) -------------------------------------------------
 // Reduce: contiguous segments [start + o*seg_stride, +len), o < nout.
@@ -105,6 +109,16 @@ constexpr int64_t kScanNoallocTile = 16384;
 // The same scan with the library's static scratch array (noalloc.cu).
 int32_t launch_scan_contig_noalloc(int32_t dtype, const void *in, void *out, int64_t n,
                                    int64_t period, desc_stream_t s);
+// The product and bitwise scans (k_scan_ops.cu): as launch_scan_contig /
+// launch_scan_csr, default tile.
+int32_t launch_scan_contig_ops(int32_t dtype, const void *in, void *out, int64_t n, int64_t period, int32_t flags,
+                               void *ws, size_t ws_bytes, desc_stream_t s);
+int32_t launch_scan_csr_ops(int32_t dtype, const void *in, void *out, int64_t n, const int64_t *offsets,
+                            int64_t nseg, void *sums, int32_t flags, void *ws, size_t ws_bytes, desc_stream_t s);
+// One group of `threads` threads (32 or 256) per CSR segment (k_scan_map.cu):
+// sums, maxima, minima, inclusive or exclusive; no workspace.
+int32_t launch_seg_group(int32_t dtype, const void *in, void *out, const int64_t *offsets, int64_t nseg, void *sums,
+                         int32_t flags, int threads, desc_stream_t s);
 // Scan segmented by CSR offsets (nseg + 1 entries, device); sums (nullable)
 // receives the total of every segment (0 for empty ones).
 int32_t launch_scan_csr(int32_t dtype, const void *in, void *out, int64_t n, const int64_t *offsets,
@@ -112,8 +126,8 @@ int32_t launch_scan_csr(int32_t dtype, const void *in, void *out, int64_t n, con
                         desc_stream_t s, int cand);
 size_t scan_csr_ws(int64_t n);
 // Operators that only the map scan runs (the look-back scan above takes the
-// sum, the maximum and the minimum).
-constexpr int32_t kMapScanOps = DESC_PROD | DESC_AND | DESC_OR | DESC_XOR | DESC_ARGMAX | DESC_ARGMIN;
+// value operators: sum, maximum, minimum, product, and, or, xor).
+constexpr int32_t kMapScanOps = DESC_ARGMAX | DESC_ARGMIN;
 // The single-pass scan through a lowered map: point g (row-major over the
 // nd dims ext / stride, offset off) is in[elem(g)], its result goes to
 // out[elem(g)]; segments of `period` points (nd == 0: the identity map over
@@ -124,7 +138,7 @@ int32_t launch_scan_map(int32_t dtype, const void *in, void *out, int64_t off, c
                         const int64_t *stride, int nd, int64_t period, const int64_t *offsets, int64_t nseg,
                         void *sums, int32_t flags, void *ws, size_t ws_bytes, desc_stream_t s);
 // The look-back scan with 4 x 4096-point tiles through a lowered map (as
-// launch_scan_map, no CSR): sums, maxima and minima, inclusive or exclusive;
+// launch_scan_map, no CSR): every value operator, inclusive or exclusive;
 // maps of more than two canonical dims go to launch_scan_map.
 int32_t launch_scan_mapped(int32_t dtype, const void *in, void *out, int64_t off, const int64_t *ext,
                            const int64_t *stride, int nd, int64_t period, int32_t flags, void *ws, size_t ws_bytes,

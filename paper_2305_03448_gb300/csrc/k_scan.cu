@@ -1,1202 +1,22 @@
-// Inclusive scan kernels: single pass, decoupled look-back.
-//
-// Each CTA takes the next tile (TILE = THREADS * ITEMS elements) from an
-// atomic ticket, so every tile's predecessors are already running or done.
-// In the tile: 128-bit loads, a sequential segmented scan of each thread's
-// ITEMS, a warp scan with shuffles and a scan of the warp totals in shared
-// memory.  The tile then publishes its total and looks back over earlier
-// tiles (one warp, 32 tiles per step) until it meets a tile that has
-// published its inclusive prefix; it adds what it saw, publishes its own
-// inclusive prefix, and applies the carry.
-//
-// Segments: head flags mark segment starts (none for one segment; every
-// `period` elements; or CSR offsets).  A tile that contains a head publishes
-// its inclusive value at once (nothing before the head can change it).
-//
-// Published words (64 bit, single-copy atomic, so one load reads a whole
-// state): status in bits 63..62 (1 = tile total, 2 = inclusive prefix) and
-// the value.  FP32 carries travel as an unevaluated (hi, lo) pair and are
-// accumulated with error-free transformations, so the per-element error
-// stays within (ITEMS + log2 THREADS + 2) ulp-sized terms of sum |x|.
-//
-// Every wait is bounded: a waiting warp gives up after a clock64 budget (or
-// as soon as another tile has given up), records DESC_ERR_DEVICE_TIMEOUT in
-// the device status word, and its CTA leaves without writing.
-#include <algorithm>
-#include <atomic>
-#include <type_traits>
-
-#include "k_common.cuh"
+// Inclusive (and exclusive) scans: sums, maxima and minima over contiguous
+// runs, per-level segments and CSR segments -- the single-pass look-back scan
+// of k_scan_core.cuh -- and the entry points that route the other operators
+// and the other schedules to the units that compile them.
+#include "k_scan_core.cuh"
 
 namespace desc {
 
-__device__ int g_scan_status;
-
 namespace {
-
-constexpr unsigned long long kStatAgg = 1ull, kStatIncl = 2ull;
-constexpr long long kBudgetCycles = 1ll << 31;      // about one second
-constexpr long long kDebugBudgetCycles = 1ll << 26; // tens of milliseconds
-constexpr unsigned kGoSpins = 1u << 16;                // x 64 ns: the look-back start wait
-
-enum Mode { PLAIN = 0, PERIODIC = 1, CSR = 2 };
-
-struct alignas(kScanTileStateBytes) TileState {
-  unsigned long long w;
-};
-
-struct ScanWs {
-  unsigned ticket;
-  unsigned abort;
-};
-
-__device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long *p) {
-  unsigned long long v;
-  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_relaxed(unsigned long long *p, unsigned long long v) {
-  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-
-// Carry value: int32 modulo 2^32, or an FP32 (hi, lo) pair.
-template <class T> struct Carry;
-template <> struct Carry<int32_t> {
-  uint32_t v;
-  __device__ static Carry zero() { return {0u}; }
-  __device__ static Carry of(int32_t x) { return {(uint32_t)x}; }
-  __device__ Carry plus(const Carry &o) const { return {v + o.v}; }
-  __device__ Carry shfl_down(int off) const { return {__shfl_down_sync(0xffffffffu, v, off)}; }
-};
-template <> struct Carry<float> {
-  float hi, lo;
-  __device__ static Carry zero() { return {0.f, 0.f}; }
-  __device__ static Carry of(float x) { return {x, 0.f}; }
-  __device__ Carry plus(const Carry &o) const {
-    float s, e;
-    two_sum(hi, o.hi, s, e);
-    e = __fadd_rn(e, __fadd_rn(lo, o.lo));
-    const float h = __fadd_rn(s, e);
-    return {h, __fsub_rn(e, __fsub_rn(h, s))};
-  }
-  __device__ Carry shfl_down(int off) const {
-    return {__shfl_down_sync(0xffffffffu, hi, off), __shfl_down_sync(0xffffffffu, lo, off)};
-  }
-};
-
-template <class T>
-__device__ __forceinline__ T add_t(T a, T b);
-template <>
-__device__ __forceinline__ int32_t add_t(int32_t a, int32_t b) { return (int32_t)((uint32_t)a + (uint32_t)b); }
-template <>
-__device__ __forceinline__ float add_t(float a, float b) { return __fadd_rn(a, b); }
-
-// x + carry, the carry added last so its low part is not lost.
-__device__ __forceinline__ int32_t apply_carry(int32_t x, const Carry<int32_t> &c) {
-  return (int32_t)((uint32_t)x + c.v);
-}
-__device__ __forceinline__ float apply_carry(float x, const Carry<float> &c) {
-  return __fadd_rn(c.hi, __fadd_rn(c.lo, x));
-}
-
-// One 64-bit word per tile: status in bits 63..62, value below.  int32:
-// the value in bits 31..0.  FP32: hi in bits 31..0 and lo, with its two
-// lowest mantissa bits dropped (a relative change below 2^-21 of a term that
-// is itself below half an ulp of hi), in bits 61..32.
-__device__ __forceinline__ unsigned long long pack(unsigned long long status, const Carry<int32_t> &c) {
-  return (status << 62) | c.v;
-}
-__device__ __forceinline__ unsigned long long pack(unsigned long long status, const Carry<float> &c) {
-  return (status << 62) | ((unsigned long long)(__float_as_uint(c.lo) >> 2) << 32) | __float_as_uint(c.hi);
-}
-template <class T>
-__device__ __forceinline__ Carry<T> unpack(unsigned long long w);
-template <>
-__device__ __forceinline__ Carry<int32_t> unpack(unsigned long long w) { return {(uint32_t)w}; }
-template <>
-__device__ __forceinline__ Carry<float> unpack(unsigned long long w) {
-  return {__uint_as_float((uint32_t)w), __uint_as_float((uint32_t)((w >> 32) & 0x3FFFFFFFull) << 2)};
-}
-
-// Scan operators.  O::C is the carry type a look-back folds; apply(x, c)
-// combines a carry with an element's in-tile prefix; pack/unpack place a
-// carry in the 62 value bits of a tile state.
-template <class T>
-struct SumOp {                          // sum: int32 modulo 2^32, FP32 with compensated carries
-  using C = Carry<T>;
-  __device__ static T id() { return T(0); }
-  __device__ static T comb(T a, T b) { return add_t(a, b); }
-  __device__ static T apply(T x, const C &c) { return apply_carry(x, c); }
-  __device__ static unsigned long long pack(unsigned long long st, const C &c) { return desc::pack(st, c); }
-  __device__ static C unpack(unsigned long long w) { return desc::unpack<T>(w); }
-};
-
-// Value operators other than the sum: maximum, minimum (FP32 ignores NaN
-// operands, IEEE maxNum / minNum), product (int32 modulo 2^32, FP32 in FP32),
-// bitwise and / or / xor (int32).  Carries are plain values.
-enum ValKind { kMaxOp = 0, kMinOp = 1, kProdOp = 2, kAndOp = 3, kOrOp = 4, kXorOp = 5 };
-template <class T, int K>
-struct ValOp {
-  __device__ static T id() {
-    if constexpr (std::is_same<T, float>::value) {
-      if (K == kMaxOp) return -__int_as_float(0x7f800000);
-      if (K == kMinOp) return __int_as_float(0x7f800000);
-      return 1.0f;                                      // product
-    } else {
-      if (K == kMaxOp) return INT32_MIN;
-      if (K == kMinOp) return INT32_MAX;
-      if (K == kProdOp) return 1;
-      if (K == kAndOp) return -1;
-      return 0;                                         // or, xor
-    }
-  }
-  __device__ static T comb(T a, T b) {
-    if constexpr (std::is_same<T, float>::value) {
-      if (K == kMaxOp) return fmaxf(a, b);
-      if (K == kMinOp) return fminf(a, b);
-      return __fmul_rn(a, b);
-    } else {
-      const uint32_t x = (uint32_t)a, y = (uint32_t)b;
-      if (K == kMaxOp) return max(a, b);
-      if (K == kMinOp) return min(a, b);
-      if (K == kProdOp) return (int32_t)(x * y);
-      if (K == kAndOp) return (int32_t)(x & y);
-      if (K == kOrOp) return (int32_t)(x | y);
-      return (int32_t)(x ^ y);
-    }
-  }
-  struct C {
-    T v;
-    __device__ static C zero() { return {ValOp::id()}; }
-    __device__ static C of(T x) { return {x}; }
-    __device__ C plus(const C &o) const { return {ValOp::comb(v, o.v)}; }   // commutative operators
-    __device__ C shfl_down(int off) const { return {__shfl_down_sync(0xffffffffu, v, off)}; }
-  };
-  __device__ static T apply(T x, const C &c) { return comb(c.v, x); }
-  __device__ static unsigned long long pack(unsigned long long st, const C &c) {
-    return (st << 62) | (unsigned long long)__builtin_bit_cast(uint32_t, c.v);
-  }
-  __device__ static C unpack(unsigned long long w) { return {__builtin_bit_cast(T, (uint32_t)w)}; }
-};
-template <class T, bool MAX>
-using ExtOp = ValOp<T, MAX ? kMaxOp : kMinOp>;
-
-template <class O>
-__device__ __forceinline__ void publish(TileState *st, unsigned long long status, const typename O::C &c) {
-  st_relaxed(&st->w, O::pack(status, c));
-}
-
-// A lowered map for the scans that read and write through it: point g
-// (row-major over the canonical dims) is element map_elem(m, g).
-struct MapArgs {
-  int32_t nd;                       // dims of the canonical map; 0: element = off + g
-  int32_t fast;                     // fewer than 2^32 points: 32-bit decoding
-  int64_t off;
-  int64_t ext[DESC_MAX_DIMS];
-  int64_t st[DESC_MAX_DIMS];
-  FastDiv div[DESC_MAX_DIMS];
-};
-
-// Maps of two or more dims: decoded dim by dim (out of line: the kernel
-// inlines only the one-dim case).
-__device__ __noinline__ int64_t map_elem_dims(const MapArgs &m, int64_t g) {
-  int64_t e = m.off;
-  if (m.fast) {
-    uint32_t t = (uint32_t)g;
-    for (int d = m.nd - 1; d > 0; --d) {
-      const uint32_t q = fast_div(t, m.div[d]);
-      e += int64_t(t - q * m.div[d].d) * m.st[d];
-      t = q;
-    }
-    return e + int64_t(t) * m.st[0];
-  }
-  int64_t t = g;
-  for (int d = m.nd - 1; d >= 0; --d) {
-    e += (t % m.ext[d]) * m.st[d];
-    t /= m.ext[d];
-  }
-  return e;
-}
-__device__ __forceinline__ int64_t map_elem(const MapArgs &m, int64_t g) {
-  if (m.nd <= 1) return m.off + (m.nd ? g * m.st[0] : g);
-  return map_elem_dims(m, g);
-}
-
-// Global addressing of the look-back scan: the identity (contiguous runs)
-// or a lowered map.
-struct RunAddr {
-  const MapArgs &m;                                     // not used
-  __device__ int64_t operator()(int64_t g) const { return g; }
-};
-// The look-back scan takes maps of at most two dims with 32-bit decoding
-// (launch_scan_mapped checks), decoded inline.
-struct MapAddr {
-  const MapArgs &m;
-  __device__ int64_t operator()(int64_t g) const {
-    if (m.nd < 2) return m.off + (m.nd ? g * m.st[0] : g);
-    const uint32_t t = (uint32_t)g, q = fast_div(t, m.div[1]);
-    return m.off + int64_t(q) * m.st[0] + int64_t(t - q * m.div[1].d) * m.st[1];
-  }
-};
-
-struct ScanArgs {
-  int64_t n;
-  int64_t period;          // PERIODIC: segment length
-  const int64_t *offsets;  // CSR: nseg + 1 offsets
-  int64_t nseg;
-  void *sums;              // CSR: per-segment totals (may be null)
-  int32_t debug;           // 1: tile 1 never publishes (tests the timeout path)
-  int32_t vec;             // in and out are 16-byte aligned: 128-bit accesses
-};
-
-// Looks back from tile `tile` (one warp).  Each poll reads a window of
-// 32 x kSlots tile states (lane l takes kSlots consecutive ones); everything
-// up to the nearest inclusive prefix in the window must have published
-// before the window is folded in.  Failed polls back off exponentially, which
-// keeps the hot tile states from being flooded.  Returns false on timeout.
-constexpr int kSlots = 1;
-
-template <class O>
-__device__ bool look_back(TileState *states, int64_t tile, ScanWs *ws, long long budget,
-                          typename O::C &prefix) {
-  using CT = typename O::C;
-  const int lane = threadIdx.x & 31;
-  CT acc = CT::zero();
-  int64_t j = tile - 1;   // nearest predecessor not yet folded in
-  const long long t0 = clock64();
-  unsigned polls = 0;
-  while (true) {
-    unsigned long long w[kSlots];
-    int stop;
-    unsigned incl_lanes;
-    while (true) {
-#pragma unroll
-      for (int k = 0; k < kSlots; ++k) {
-        const int64_t me = j - (lane * kSlots + k);
-        w[k] = me >= 0 ? ld_relaxed(&states[me].w) : (kStatIncl << 62);   // before tile 0: empty
-      }
-      int kin = kSlots;                                 // nearest inclusive slot of this lane
-#pragma unroll
-      for (int k = kSlots - 1; k >= 0; --k)
-        if ((w[k] >> 62) == kStatIncl) kin = k;
-      incl_lanes = __ballot_sync(0xffffffffu, kin < kSlots);
-      const int first = incl_lanes ? __ffs(incl_lanes) - 1 : 31;
-      const int kfirst = __shfl_sync(0xffffffffu, kin, first);
-      stop = incl_lanes ? first * kSlots + kfirst : 32 * kSlots - 1;
-      bool ready = true;
-#pragma unroll
-      for (int k = 0; k < kSlots; ++k)
-        if (lane * kSlots + k <= stop && (w[k] >> 62) == 0) ready = false;
-      if (__all_sync(0xffffffffu, ready)) break;
-      int give_up = 0;
-      ++polls;
-      if (lane == 0 && (polls & 31) == 0)      // the abort flag is one more L2 round trip
-        give_up = (*(volatile unsigned *)&ws->abort != 0u) || (clock64() - t0 > budget);
-      give_up = __shfl_sync(0xffffffffu, give_up, 0);
-      if (give_up) {
-        if (lane == 0) {
-          atomicExch(&ws->abort, 1u);
-          atomicCAS(&g_scan_status, 0, (int)DESC_ERR_DEVICE_TIMEOUT);
-        }
-        return false;
-      }
-      __nanosleep(min(32u << min(polls, 5u), 1024u));   // exponential back-off
-    }
-    CT mine = CT::zero();
-#pragma unroll
-    for (int k = 0; k < kSlots; ++k)
-      if (lane * kSlots + k <= stop) mine = mine.plus(O::unpack(w[k]));
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) mine = mine.plus(mine.shfl_down(off));
-    acc = acc.plus(mine);
-    if (incl_lanes) break;
-    j -= 32 * kSlots;
-  }
-  prefix = acc;
-  return true;
-}
-
-// ---- asynchronous tile copies (cp.async) into swizzled shared memory ----
-// A sub-tile is 1024 chunks of 16 bytes.  Chunk j sits in slot
-// j ^ ((j >> 3) & 3): within each 128-byte row the slots are permuted so
-// that both the striped accesses (lane l on chunk base + l, used to move
-// data to and from global memory with full 128-byte lines) and the blocked
-// accesses (thread t on chunks 4t..4t+3, used by the scan) hit 8 distinct
-// 16-byte bank groups in every phase of 8 lanes, without padding.
-__device__ __forceinline__ int chunk_off(int j) { return 16 * (j ^ ((j >> 3) & 3)); }
-
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, int src_bytes) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(s), "l"(gmem), "r"(src_bytes)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-
-// A CTA scans one tile of kSub * SUB elements: SUB sub-tiles of kSub
-// elements (kThreads threads x kItems items), each staged in shared memory.
-// Large tiles matter: decoupled look-back serves at most about one window of
-// tiles per L2 round trip, so the bytes per tile set the attainable rate.
-constexpr int kThreads = 256;                       // scanning threads
-constexpr int kItems = 16;                          // elements per thread and sub-tile
-constexpr int kWarps = kThreads / 32;
-constexpr int kSub = kThreads * kItems;             // elements per sub-tile
-constexpr int kSubChunks = kSub / 4;                // 16-byte chunks per sub-tile
-constexpr int kStageBytes = 16 * kSubChunks;
-
-__device__ __forceinline__ void compute_bar() { asm volatile("bar.sync 1, %0;" ::"n"(kThreads) : "memory"); }
-// CSR: the compute warps and the look-back warp, once the tile's segment heads are marked.
-__device__ __forceinline__ void heads_bar() { asm volatile("bar.sync 2, %0;" ::"n"(kThreads + 32) : "memory"); }
-
-// Start copying kSub elements from g_start (elements past n read as zero);
-// point g is in[addr(g)].
-template <class T, class A>
-__device__ __forceinline__ void load_sub(unsigned char *stage, const T *in, int64_t g_start,
-                                         int64_t n, bool vec, const A &addr) {
-#pragma unroll
-  for (int q = 0; q < kSubChunks / kThreads; ++q) {
-    const int j = q * kThreads + threadIdx.x;
-    const int64_t g = g_start + 4 * int64_t(j);
-    unsigned char *dst = stage + chunk_off(j);
-    if (vec) {
-      const int64_t rem = n - g;
-      const int bytes = rem >= 4 ? 16 : (rem > 0 ? int(rem) * 4 : 0);
-      cp_async16(dst, bytes ? static_cast<const void *>(in + addr(g)) : static_cast<const void *>(in), bytes);
-    } else {
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        if (g + c < n) cp_async4(dst + 4 * c, in + addr(g + c));
-        else *reinterpret_cast<T *>(dst + 4 * c) = T(0);
-      }
-    }
-  }
-}
-
-__device__ __forceinline__ void cp_async_wait_dyn(int pending) {
-  switch (pending) {
-    case 0: cp_async_wait<0>(); break;
-    case 1: cp_async_wait<1>(); break;
-    case 2: cp_async_wait<2>(); break;
-    default: cp_async_wait<3>(); break;
-  }
-}
-
-// The segment containing element t0: the largest s with offsets[s] <= t0
-// (one warp, 32-way search).
-__device__ __forceinline__ int64_t find_segment(const int64_t *offsets, int64_t nseg, int64_t t0) {
-  const int lane = threadIdx.x & 31;
-  int64_t lo = 0, hi = nseg;
-  while (hi - lo > 1) {
-    const int64_t step = (hi - lo + 31) / 32;
-    const int64_t probe = lo + int64_t(lane) * step;
-    const bool le = probe < hi && offsets[probe] <= t0;
-    const unsigned m = __ballot_sync(0xffffffffu, le);
-    const int last = 31 - __clz(m);   // lane 0 always qualifies
-    lo = lo + int64_t(last) * step;
-    hi = std::min<int64_t>(hi, lo + step);
-  }
-  return lo;
-}
-
-// One CTA per tile, tiles in ticket order.  Warps 0..7 load the tile (one
-// cp.async group per sub-tile into padded shared memory, full 128-byte
-// lines), scan the sub-tiles in order with an in-tile carry, and publish the
-// tile total as soon as it is known.  Warp 8 looks back meanwhile (the prefix
-// of a tile does not depend on its data) and publishes the inclusive prefix
-// once it has both.  The carry is added during the coalesced store pass, to
-// the elements that have no segment start before them in the tile.
-// MAPPED: points are addressed through the lowered map m (in and out are
-// then the base arrays; vec means four consecutive points from a multiple of
-// 4 are four consecutive elements on a 16-byte boundary).
-template <class T, class O, int MODE, int SUB, bool EXCL, bool MAPPED = false>
-__global__ void __launch_bounds__(kThreads + 32, 3) scan_kernel(const T *in, T *out, ScanArgs args,
-                                                             ScanWs *ws, TileState *states,
-                                                             const __grid_constant__ MapArgs m) {
-  using CT = typename O::C;
-  constexpr int kTile = kSub * SUB;
-  extern __shared__ __align__(128) unsigned char ring[];   // SUB stages
-  __shared__ int64_t sh_tile;
-  __shared__ T sh_wval[kWarps];
-  __shared__ int sh_wflag[kWarps];
-  __shared__ T sh_carry;                // in-tile carry after the sub-tiles done so far
-  __shared__ int sh_carry_flag;
-  __shared__ CT sh_prefix;
-  __shared__ int sh_ok;
-  __shared__ unsigned sh_heads[MODE == CSR ? kTile / 32 : 1];
-  __shared__ unsigned short sh_need[MODE == PLAIN ? 1 : SUB * kThreads];  // carry-needed bits
-  __shared__ int64_t sh_seg0;
-  __shared__ int sh_any_end;            // CSR: a non-empty segment ends in this tile
-  __shared__ int sh_dense;              // CSR: more boundaries than one warp-wide read covers
-  __shared__ volatile int sh_go;        // look-back may start polling
-
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int64_t n = args.n;
-  const bool vec = args.vec != 0;
-  using Addr = typename std::conditional<MAPPED, MapAddr, RunAddr>::type;
-  const Addr addr{m};
-  if (tid == 0) {
-    sh_tile = atomicAdd(&ws->ticket, 1u);
-    sh_go = 0;
-  }
-  if (warp < kWarps) {
-    // While the ticket travels: pull into L2 the tile this CTA's index
-    // suggests (CTAs take tickets in about the order they start, so a wrong
-    // guess is a tile a neighbour loads soon; nothing reads it from here).
-    // One prefetch per 32 points: a 128-byte line where the points are
-    // contiguous.
-    const int64_t guess = int64_t(blockIdx.x) * kTile;
-#pragma unroll
-    for (int k = 0; k < kTile / 32 / kThreads; ++k) {
-      const int64_t g = guess + 32 * int64_t(k * kThreads + tid);
-      if (g < n) asm volatile("prefetch.global.L2 [%0];" ::"l"(in + addr(g)));
-    }
-  }
-  __syncthreads();
-  const int64_t tile = sh_tile;
-  const int64_t t0 = tile * kTile;
-  const bool stall = args.debug && tile == 1;
-
-  if (warp == kWarps) {
-    // ---- look-back warp: prefix of everything before t0
-    bool first_is_head = tile == 0;
-    if (MODE == PERIODIC) first_is_head = first_is_head || (t0 % args.period == 0);
-    if (MODE == CSR) {
-      // The tile's segment heads, found while the compute warps' loads are in
-      // flight: zero the bitmap, find the segment holding t0, and mark the
-      // boundaries b = offsets[s] in (t0, tend] -- a segment starts at b
-      // (b < tend) and segment s - 1 ends at b - 1 -- from one warp-wide read
-      // of the next 32 offsets.  Where all 32 lie in the tile there may be
-      // more: the compute warps then mark them together (sh_dense).
-      for (int i = lane; i < kTile / 32; i += 32) sh_heads[i] = 0u;
-      const int64_t tend = std::min<int64_t>(t0 + kTile, n);
-      T *sums = static_cast<T *>(args.sums);
-      const int64_t s0 = find_segment(args.offsets, args.nseg, t0);
-      const int64_t sl = s0 + 1 + lane;
-      const int64_t b = sl <= args.nseg ? args.offsets[sl] : INT64_MAX;
-      const int64_t bprev = sl <= args.nseg ? args.offsets[sl - 1] : 0;   // lane 0: offsets[s0]
-      const bool h0 = __shfl_sync(0xffffffffu, bprev, 0) == t0;           // a segment starts at t0
-      const bool dense = __all_sync(0xffffffffu, b <= tend);
-      __syncwarp();                                     // bitmap zeroed before marking
-      int ends = 0;
-      if (!dense && b > t0 && b <= tend) {
-        const int64_t rel = b - t0;
-        if (b < tend) atomicOr(&sh_heads[rel >> 5], 1u << (rel & 31));
-        if (sums) {                                     // empty segments get their total here
-          if (bprev == b) sums[sl - 1] = O::id();
-          else ends = 1;
-        }
-      }
-      ends = __any_sync(0xffffffffu, ends);
-      if (sums && tile == 0)                            // empty segments before the first element
-        for (int64_t q = lane; q < s0; q += 32) sums[q] = O::id();
-      if (lane == 0) {
-        if (h0) atomicOr(&sh_heads[0], 1u);
-        sh_seg0 = s0;
-        sh_dense = dense ? 1 : 0;
-        sh_any_end = ends;
-      }
-      first_is_head = first_is_head || h0;
-      heads_bar();
-    }
-    CT prefix = CT::zero();
-    bool ok = true;
-    if (!first_is_head) {
-      // Polls made before the predecessors, which started just before this
-      // tile, can have published only fail and load the tile states; start
-      // once part of this tile's own input has landed (bounded wait).
-      for (unsigned i = 0; i < kGoSpins && !sh_go; ++i) __nanosleep(64);
-      ok = look_back<O>(states, tile, ws, args.debug ? kDebugBudgetCycles : kBudgetCycles, prefix);
-    }
-    if (lane == 0) {
-      sh_prefix = prefix;
-      sh_ok = ok ? 1 : 0;
-    }
-    __syncthreads();                                    // (S) tile total known
-    if (ok && lane == 0 && !stall && tile != 0 && !sh_carry_flag)
-      publish<O>(&states[tile], kStatIncl, prefix.plus(CT::of(sh_carry)));
-    return;
-  }
-
-  // ---- compute warps
-#pragma unroll
-  for (int s = 0; s < SUB; ++s) {
-    load_sub<T>(ring + s * kStageBytes, in, t0 + int64_t(s) * kSub, n, vec, addr);
-    cp_async_commit();
-  }
-  if (tid == 0) {
-    sh_carry = O::id();
-    sh_carry_flag = 0;
-  }
-
-#pragma unroll 1
-  for (int s = 0; s < SUB; ++s) {
-    unsigned char *st = ring + s * kStageBytes;
-    cp_async_wait_dyn(SUB - 1 - s);                     // sub-tile s has landed (this thread)
-    if (MODE == CSR && s == 0) {                        // ... for every thread, and the heads are marked
-      heads_bar();
-      if (sh_dense) {                                   // many boundaries: all compute threads mark them
-        const int64_t tend = std::min<int64_t>(t0 + kTile, n);
-        T *sums = static_cast<T *>(args.sums);
-        for (int64_t q = sh_seg0 + 1 + tid; q <= args.nseg; q += kThreads) {
-          const int64_t b = args.offsets[q];
-          if (b > tend) break;
-          if (b <= t0) continue;                        // only if the offsets were not sorted
-          const int64_t rel = b - t0;
-          if (b < tend) atomicOr(&sh_heads[rel >> 5], 1u << (rel & 31));
-          if (sums) {
-            if (args.offsets[q - 1] == b) sums[q - 1] = O::id();
-            else sh_any_end = 1;
-          }
-        }
-        compute_bar();
-      }
-    } else {
-      compute_bar();                                    // ... for every thread; carry visible
-    }
-    if (s == SUB / 2 && tid == 0) sh_go = 1;
-    const T cv = sh_carry;
-    const int cf = sh_carry_flag;
-    const int64_t g0 = t0 + int64_t(s) * kSub + int64_t(tid) * kItems;
-    unsigned hmask = 0u;
-    if (MODE == PERIODIC) {
-      int64_t r = g0 % args.period;
-#pragma unroll
-      for (int i = 0; i < kItems; ++i) {
-        if (r == 0) hmask |= 1u << i;
-        if (++r == args.period) r = 0;
-      }
-    } else if (MODE == CSR) {
-      const int rel0 = s * kSub + tid * kItems;
-      hmask = (sh_heads[rel0 >> 5] >> (rel0 & 31)) & 0xffffu;
-    }
-    T v[kItems];
-#pragma unroll
-    for (int q = 0; q < kItems / 4; ++q) {
-      const int4 x = *reinterpret_cast<const int4 *>(st + chunk_off((kItems / 4) * tid + q));
-      v[4 * q] = __builtin_bit_cast(T, x.x);
-      v[4 * q + 1] = __builtin_bit_cast(T, x.y);
-      v[4 * q + 2] = __builtin_bit_cast(T, x.z);
-      v[4 * q + 3] = __builtin_bit_cast(T, x.w);
-    }
-#pragma unroll
-    for (int i = 1; i < kItems; ++i)
-      if (!((hmask >> i) & 1u)) v[i] = O::comb(v[i - 1], v[i]);
-    int f = hmask != 0u;
-    T a = v[kItems - 1];
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {           // warp scan, segmented operator
-      const T au = __shfl_up_sync(0xffffffffu, a, off);
-      const int fu = __shfl_up_sync(0xffffffffu, f, off);
-      if (lane >= off) {
-        if (!f) a = O::comb(au, a);
-        f |= fu;
-      }
-    }
-    if (lane == 31) {
-      sh_wval[warp] = a;
-      sh_wflag[warp] = f;
-    }
-    T ex = __shfl_up_sync(0xffffffffu, a, 1);
-    int exf = __shfl_up_sync(0xffffffffu, f, 1);
-    if (lane == 0) { ex = O::id(); exf = 0; }
-    compute_bar();
-    if (warp == 0) {                                    // scan of the warp totals
-      T wa = lane < kWarps ? sh_wval[lane] : O::id();
-      int wf = lane < kWarps ? sh_wflag[lane] : 0;
-#pragma unroll
-      for (int off = 1; off < kWarps; off <<= 1) {
-        const T au = __shfl_up_sync(0xffffffffu, wa, off);
-        const int fu = __shfl_up_sync(0xffffffffu, wf, off);
-        if (lane >= off) {
-          if (!wf) wa = O::comb(au, wa);
-          wf |= fu;
-        }
-      }
-      T we = __shfl_up_sync(0xffffffffu, wa, 1);
-      int wfe = __shfl_up_sync(0xffffffffu, wf, 1);
-      if (lane == 0) { we = O::id(); wfe = 0; }
-      const T sub_val = __shfl_sync(0xffffffffu, wa, kWarps - 1);
-      const int sub_flag = __shfl_sync(0xffffffffu, wf, kWarps - 1);
-      __syncwarp();
-      if (lane < kWarps) {
-        sh_wval[lane] = we;
-        sh_wflag[lane] = wfe;
-      }
-      if (lane == 0) {                                  // carry after this sub-tile
-        sh_carry = sub_flag ? sub_val : O::comb(cv, sub_val);
-        sh_carry_flag = cf | sub_flag;
-      }
-    }
-    compute_bar();
-    // prefix of this thread within the tile: carry, then warp, then thread
-    T pv = sh_wval[warp];
-    int pf = sh_wflag[warp];
-    if (!exf) ex = O::comb(pv, ex);
-    exf |= pf;                                          // (pf, pv) (+) (exf, ex)
-    const T in_tile = exf ? ex : O::comb(cv, ex);
-    const int in_flag = exf | cf;
-    unsigned need = 0u;                                 // elements with no head before them
-#pragma unroll
-    for (int i = 0; i < kItems; ++i) {
-      if ((hmask & ((2u << i) - 1u)) == 0u) {           // before this thread's first head
-        v[i] = O::comb(in_tile, v[i]);
-        if (!in_flag) need |= 1u << i;
-      }
-    }
-    if (MODE != PLAIN) sh_need[s * kThreads + tid] = (unsigned short)need;
-#pragma unroll
-    for (int q = 0; q < kItems / 4; ++q) {
-      int4 x;
-      x.x = __builtin_bit_cast(int, v[4 * q]);
-      x.y = __builtin_bit_cast(int, v[4 * q + 1]);
-      x.z = __builtin_bit_cast(int, v[4 * q + 2]);
-      x.w = __builtin_bit_cast(int, v[4 * q + 3]);
-      *reinterpret_cast<int4 *>(st + chunk_off((kItems / 4) * tid + q)) = x;
-    }
-  }
-  compute_bar();
-  if (tid == 0 && !stall) {
-    // publish at once: the inclusive value when nothing before can change it
-    // (tile 0, or a tile holding a segment start), else the tile total
-    publish<O>(&states[tile], (tile == 0 || sh_carry_flag) ? kStatIncl : kStatAgg, CT::of(sh_carry));
-  }
-  __syncthreads();                                      // (S) with the look-back warp
-  if (!sh_ok) return;                                   // a wait gave up: write nothing
-
-  // ---- coalesced stores, adding the tile carry where needed (the exclusive
-  // form, chosen once per launch, shifts each segment by one)
-  const CT pre = sh_prefix;
-#pragma unroll 1
-  for (int s = 0; s < SUB; ++s) {
-    const unsigned char *st = ring + s * kStageBytes;
-#pragma unroll
-    for (int q = 0; q < kSubChunks / kThreads; ++q) {
-      const int j = q * kThreads + tid;
-      const int64_t g = t0 + int64_t(s) * kSub + 4 * int64_t(j);
-      int4 x = *reinterpret_cast<const int4 *>(st + chunk_off(j));
-      const unsigned nb = MODE == PLAIN ? 0xfu : (unsigned(sh_need[s * kThreads + (j >> 2)]) >> ((j & 3) * 4)) & 0xfu;
-      T y[4] = {__builtin_bit_cast(T, x.x), __builtin_bit_cast(T, x.y), __builtin_bit_cast(T, x.z),
-                __builtin_bit_cast(T, x.w)};
-#pragma unroll
-      for (int c = 0; c < 4; ++c)
-        if ((nb >> c) & 1u) y[c] = O::apply(y[c], pre);
-      if (EXCL) {                                       // shift by one within each segment
-        const int rel0 = s * kSub + 4 * j;
-        T prev = __shfl_up_sync(0xffffffffu, y[3], 1);  // lane - 1 holds chunk j - 1
-        if (lane == 0) {
-          if (rel0 == 0) {
-            prev = O::apply(O::id(), pre);              // everything before the tile
-          } else {                                      // from the staged tile
-            const int r = rel0 - 1, sb = r / kSub, r2 = r % kSub;
-            const T v = reinterpret_cast<const T *>(ring + sb * kStageBytes + chunk_off(r2 / 4))[r2 % 4];
-            const bool nd = MODE == PLAIN || ((sh_need[sb * kThreads + r2 / kItems] >> (r2 % kItems)) & 1u);
-            prev = nd ? O::apply(v, pre) : v;
-          }
-        }
-        T e[4];
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          bool head;
-          if (MODE == PLAIN) head = g + c == 0;
-          else if (MODE == PERIODIC) head = (g + c) % args.period == 0;
-          else head = (sh_heads[(rel0 + c) >> 5] >> ((rel0 + c) & 31)) & 1u;
-          e[c] = head ? O::id() : (c == 0 ? prev : y[c - 1]);
-        }
-#pragma unroll
-        for (int c = 0; c < 4; ++c) y[c] = e[c];
-      }
-      if (vec && g + 4 <= n) {
-        x.x = __builtin_bit_cast(int, y[0]);
-        x.y = __builtin_bit_cast(int, y[1]);
-        x.z = __builtin_bit_cast(int, y[2]);
-        x.w = __builtin_bit_cast(int, y[3]);
-        __stcs(reinterpret_cast<int4 *>(out + addr(g)), x);
-      } else {
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-          if (g + c < n) out[addr(g + c)] = y[c];
-      }
-    }
-  }
-  if (MODE == CSR && args.sums && sh_any_end) {         // totals of non-empty segments ending here
-    // the value at the segment's last element, from the staged tile
-    T *sums = static_cast<T *>(args.sums);
-    const int64_t tend = std::min<int64_t>(t0 + kTile, n);
-    for (int64_t s = sh_seg0 + 1 + tid; s <= args.nseg; s += kThreads) {
-      const int64_t b = args.offsets[s];
-      if (b > tend) break;
-      if (b <= t0 || args.offsets[s - 1] == b) continue;
-      const int rel = (int)(b - 1 - t0);
-      const int sub = rel / kSub, r2 = rel % kSub;
-      const T *v = reinterpret_cast<const T *>(ring + sub * kStageBytes + chunk_off(r2 / 4));
-      T y = v[r2 % 4];
-      if ((sh_need[sub * kThreads + r2 / kItems] >> (r2 % kItems)) & 1u) y = O::apply(y, pre);
-      sums[s - 1] = y;
-    }
-  }
-}
-
-// ---- the scan through a lowered map, and the arg operators ----------------
-// One CTA per tile of kMapTile logical points (tiles in ticket order).  The
-// CTA loads point g of the tile from in[map(g)] (striped, so a warp reads
-// consecutive points), stages the tile in shared memory, scans it (each
-// thread 16 consecutive points, warp shuffles, warp totals), publishes and
-// looks back as above, and stores point g's result to out[map(g)].  With
-// the identity map this is a plain (or segmented) scan; with any other
-// lowered map it scans a view in one pass, gathering in its loads and
-// scattering in its stores.  Element states are values, or for the arg
-// operators (value, position) pairs whose stored result is the base-array
-// index of the position.
-constexpr int kMapThreads = 256, kMapItems = 16, kMapTile = kMapThreads * kMapItems;
-static_assert(kMapTile == kScanSubTile, "workspace tiles count kScanSubTile elements");
-
-// Element-state layer of the map kernel for the value operators (the state
-// is the value; make() takes the value and its element index) ...
-template <class T, class O>
-struct ValueStates {
-  using Op = O;
-  using E = T;
-  using C = typename O::C;
-  __device__ static E make(T x, int64_t) { return x; }
-  __device__ static E eid() { return O::id(); }
-  __device__ static E ecomb(E a, E b) { return O::comb(a, b); }   // a before b
-  __device__ static E shfl_up(E e, int off) { return __shfl_up_sync(0xffffffffu, e, off); }
-  __device__ static E shfl(E e, int src) { return __shfl_sync(0xffffffffu, e, src); }
-  __device__ static E apply(E e, const C &c) { return O::apply(e, c); }
-  __device__ static E of_carry(const C &c) { return O::apply(O::id(), c); }
-  __device__ static C carry(E e) { return C::of(e); }
-  __device__ static uint32_t out_bits(E e, const MapArgs &) { return __builtin_bit_cast(uint32_t, e); }
-};
-
-// ... and for the arg operators: (value, element index in the base array),
-// index -1 = none; the better of two states by arg_better (ties: the smaller
-// element index, whatever order the map visits the elements in).
-template <class T, bool MAX>
-struct ArgStates {
-  struct E {
-    T v;
-    int32_t i;                      // element index, -1: none
-  };
-  struct Op;
-  struct C {
-    E e;
-    __device__ static C zero() { return {{T(0), -1}}; }
-    __device__ static C of(E x) { return {x}; }
-    __device__ C plus(const C &o) const;
-    __device__ C shfl_down(int off) const {
-      return {{__shfl_down_sync(0xffffffffu, e.v, off), __shfl_down_sync(0xffffffffu, e.i, off)}};
-    }
-  };
-  struct Op {
-    using C = ArgStates::C;
-    // 30 bits of element index: 0x3FFFFFFF stands for none.
-    __device__ static unsigned long long pack(unsigned long long st, const C &c) {
-      const uint32_t pos = c.e.i < 0 ? 0x3FFFFFFFu : (uint32_t)c.e.i;
-      return (st << 62) | ((unsigned long long)pos << 32) | (unsigned long long)__builtin_bit_cast(uint32_t, c.e.v);
-    }
-    __device__ static C unpack(unsigned long long w) {
-      const uint32_t pos = (uint32_t)(w >> 32) & 0x3FFFFFFFu;
-      return {{__builtin_bit_cast(T, (uint32_t)w), pos == 0x3FFFFFFFu ? -1 : (int32_t)pos}};
-    }
-  };
-  __device__ static E better(E a, E b) { return arg_better<T, MAX>(a.v, a.i, b.v, b.i) ? a : b; }
-  __device__ static E make(T x, int64_t elem) { return {x, (int32_t)elem}; }
-  __device__ static E eid() { return {T(0), -1}; }
-  __device__ static E ecomb(E a, E b) { return better(a, b); }
-  __device__ static E shfl_up(E e, int off) {
-    return {__shfl_up_sync(0xffffffffu, e.v, off), __shfl_up_sync(0xffffffffu, e.i, off)};
-  }
-  __device__ static E shfl(E e, int src) {
-    return {__shfl_sync(0xffffffffu, e.v, src), __shfl_sync(0xffffffffu, e.i, src)};
-  }
-  __device__ static E apply(E e, const C &c) { return better(c.e, e); }
-  __device__ static E of_carry(const C &c) { return c.e; }
-  __device__ static C carry(E e) { return {e}; }
-  __device__ static uint32_t out_bits(E e, const MapArgs &) { return (uint32_t)e.i; }
-};
-template <class T, bool MAX>
-__device__ __forceinline__ typename ArgStates<T, MAX>::C ArgStates<T, MAX>::C::plus(const C &o) const {
-  return {ArgStates<T, MAX>::better(e, o.e)};
-}
-
-// The tile in shared memory.  4-byte states use the look-back scan's
-// layout: 16-byte chunks in XOR-swizzled slots (chunk_off), conflict-free
-// for a warp's striped chunks, a warp's 32 consecutive points and each
-// thread's 4 consecutive chunks.  8-byte states (the arg operators) take one
-// padding slot per 16.
-template <class E>
-struct MapTileSmem {
-  static constexpr int kBytes = sizeof(E) == 4 ? kMapTile * 4 : (kMapTile + kMapTile / 16) * 8;
-  __device__ static E *at(unsigned char *t, int r) {
-    if constexpr (sizeof(E) == 4) return reinterpret_cast<E *>(t + chunk_off(r >> 2) + 4 * (r & 3));
-    else return reinterpret_cast<E *>(t) + (r + (r >> 4));
-  }
-};
-
-// Compute warps only (the look-back warp has left).
-__device__ __forceinline__ void map_compute_bar() { asm volatile("bar.sync 1, %0;" ::"n"(kMapThreads) : "memory"); }
-
-// Warps 0..7 load the tile through the map (128-bit chunks where the map's
-// inner dim is unit-stride: vec), stage it, scan it and store it; warp 8
-// looks back from the start, while the loads are in flight.  mode: PLAIN,
-// PERIODIC or CSR; excl: the exclusive form.
-template <class T, class S>
-__global__ void __launch_bounds__(kMapThreads + 32) scan_map_kernel(const T *__restrict__ in, uint32_t *__restrict__ out,
-                                                                    const MapArgs m, ScanArgs args, ScanWs *ws,
-                                                                    TileState *states, int mode, int excl) {
-  using E = typename S::E;
-  using O = typename S::Op;
-  using CT = typename S::C;
-  using SM = MapTileSmem<E>;
-  constexpr bool kVec4 = sizeof(E) == 4;
-  __shared__ __align__(128) unsigned char tile_smem[SM::kBytes];
-  __shared__ unsigned sh_heads[kMapTile / 32];
-  __shared__ E sh_wval[kMapThreads / 32];
-  __shared__ int sh_wflag[kMapThreads / 32];
-  __shared__ E sh_agg;
-  __shared__ int sh_aggf;
-  __shared__ CT sh_prefix;
-  __shared__ int64_t sh_tile, sh_seg0;
-  __shared__ int sh_ok;
-  __shared__ volatile int sh_go;                       // the tile's inputs have landed: start polling
-
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (tid == 0) {
-    sh_tile = atomicAdd(&ws->ticket, 1u);
-    sh_go = 0;
-  }
-  if (mode == CSR)
-    for (int i = tid; i < kMapTile / 32; i += kMapThreads + 32) sh_heads[i] = 0u;
-  if (warp < kMapThreads / 32) {                       // the guessed tile into L2 (as scan_kernel)
-    const int64_t g = int64_t(blockIdx.x) * kMapTile + 16 * int64_t(tid);
-    if (g < args.n) asm volatile("prefetch.global.L2 [%0];" ::"l"(in + map_elem(m, g)));
-  }
-  __syncthreads();
-  const int64_t tile = sh_tile, t0 = tile * kMapTile, n = args.n;
-  const int64_t tend = min(t0 + kMapTile, n);
-  const bool stall = args.debug && tile == 1;
-
-  if (warp == kMapThreads / 32) {
-    // ---- look-back warp: the prefix of everything before t0
-    bool first_head = tile == 0;
-    if (mode == PERIODIC) first_head = first_head || t0 % args.period == 0;
-    if (mode == CSR) first_head = first_head || args.offsets[find_segment(args.offsets, args.nseg, t0)] == t0;
-    CT prefix = CT::zero();
-    bool ok = true;
-    if (!first_head) {
-      // Predecessors publish about when this tile's own loads land; polls
-      // before that only load the tile states (bounded wait).
-      for (unsigned i = 0; i < kGoSpins && !sh_go; ++i) __nanosleep(64);
-      ok = look_back<O>(states, tile, ws, args.debug ? kDebugBudgetCycles : kBudgetCycles, prefix);
-    }
-    if (lane == 0) {
-      sh_prefix = prefix;
-      sh_ok = ok ? 1 : 0;
-    }
-    __syncthreads();                                   // (S) the tile's aggregate is known
-    if (ok && lane == 0 && !stall && tile != 0 && !sh_aggf)
-      publish<O>(&states[tile], kStatIncl, prefix.plus(S::carry(sh_agg)));
-    return;
-  }
-
-  unsigned char *tsm = tile_smem;
-  const bool vec = args.vec != 0;
-  // ---- loads through the map
-  bool done = false;
-  if constexpr (kVec4) {
-    if (vec) {                                         // chunk c = points 4c .. 4c + 3
-      done = true;
-#pragma unroll
-    for (int q = 0; q < kMapTile / 4 / kMapThreads; ++q) {
-      const int c = q * kMapThreads + tid;
-      const int64_t g = t0 + 4 * int64_t(c);
-      int4 x;
-      if (g + 4 <= n) {
-        x = __ldcs(reinterpret_cast<const int4 *>(in + map_elem(m, g)));
-      } else {
-        E e[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) e[k] = g + k < n ? S::make(in[map_elem(m, g + k)], 0) : S::eid();
-        x = make_int4(__builtin_bit_cast(int, e[0]), __builtin_bit_cast(int, e[1]), __builtin_bit_cast(int, e[2]),
-                      __builtin_bit_cast(int, e[3]));
-      }
-      *reinterpret_cast<int4 *>(tsm + chunk_off(c)) = x;
-    }
-    }
-  }
-  if (!done) {
-#pragma unroll
-    for (int j = 0; j < kMapItems; ++j) {
-      const int r = j * kMapThreads + tid;
-      const int64_t g = t0 + r;
-      E x = S::eid();
-      if (g < n) {
-        const int64_t e = map_elem(m, g);
-        x = S::make(in[e], e);
-      }
-      *SM::at(tsm, r) = x;
-    }
-  }
-  // ---- segment heads (CSR): boundaries offsets[q] in (t0, tend), and t0
-  if (mode == CSR) {
-    if (warp == 0) {
-      const int64_t s0 = find_segment(args.offsets, args.nseg, t0);
-      if (lane == 0) {
-        sh_seg0 = s0;
-        if (args.offsets[s0] == t0) atomicOr(&sh_heads[0], 1u);
-      }
-    }
-    map_compute_bar();
-    for (int64_t q = sh_seg0 + 1 + tid; q <= args.nseg; q += kMapThreads) {
-      const int64_t b = args.offsets[q];
-      if (b >= tend) break;
-      if (b > t0) atomicOr(&sh_heads[(b - t0) >> 5], 1u << ((b - t0) & 31));
-    }
-  }
-  map_compute_bar();
-  if (tid == 0) sh_go = 1;
-  auto is_head = [&](int r) -> bool {
-    const int64_t g = t0 + r;
-    if (mode == PLAIN) return g == 0;
-    if (mode == PERIODIC) return g % args.period == 0;
-    return (sh_heads[r >> 5] >> (r & 31)) & 1u;
-  };
-
-  // ---- scan of the tile: 16 consecutive points per thread
-  const int r0 = tid * kMapItems;
-  E v[kMapItems];
-  if constexpr (kVec4) {
-#pragma unroll
-    for (int q = 0; q < kMapItems / 4; ++q) {
-      const int4 x = *reinterpret_cast<const int4 *>(tsm + chunk_off((kMapItems / 4) * tid + q));
-      v[4 * q] = __builtin_bit_cast(E, x.x);
-      v[4 * q + 1] = __builtin_bit_cast(E, x.y);
-      v[4 * q + 2] = __builtin_bit_cast(E, x.z);
-      v[4 * q + 3] = __builtin_bit_cast(E, x.w);
-    }
-  } else {
-#pragma unroll
-    for (int i = 0; i < kMapItems; ++i) v[i] = *SM::at(tsm, r0 + i);
-  }
-  unsigned hm = 0u;
-  if (mode == CSR) {
-    hm = (sh_heads[r0 >> 5] >> (r0 & 31)) & 0xffffu;
-  } else {
-#pragma unroll
-    for (int i = 0; i < kMapItems; ++i)
-      if (is_head(r0 + i)) hm |= 1u << i;
-  }
-#pragma unroll
-  for (int i = 1; i < kMapItems; ++i)
-    if (!((hm >> i) & 1u)) v[i] = S::ecomb(v[i - 1], v[i]);
-  int f = hm != 0u;
-  E a = v[kMapItems - 1];
-#pragma unroll
-  for (int off = 1; off < 32; off <<= 1) {             // warp scan, segmented operator
-    const E au = S::shfl_up(a, off);
-    const int fu = __shfl_up_sync(0xffffffffu, f, off);
-    if (lane >= off) {
-      if (!f) a = S::ecomb(au, a);
-      f |= fu;
-    }
-  }
-  if (lane == 31) {
-    sh_wval[warp] = a;
-    sh_wflag[warp] = f;
-  }
-  E ex = S::shfl_up(a, 1);
-  int exf = __shfl_up_sync(0xffffffffu, f, 1);
-  if (lane == 0) {
-    ex = S::eid();
-    exf = 0;
-  }
-  map_compute_bar();
-  if (warp == 0) {                                     // scan of the warp totals; publish
-    constexpr int kW = kMapThreads / 32;
-    E wa = lane < kW ? sh_wval[lane] : S::eid();
-    int wf = lane < kW ? sh_wflag[lane] : 0;
-#pragma unroll
-    for (int off = 1; off < kW; off <<= 1) {
-      const E au = S::shfl_up(wa, off);
-      const int fu = __shfl_up_sync(0xffffffffu, wf, off);
-      if (lane >= off) {
-        if (!wf) wa = S::ecomb(au, wa);
-        wf |= fu;
-      }
-    }
-    E we = S::shfl_up(wa, 1);
-    int wfe = __shfl_up_sync(0xffffffffu, wf, 1);
-    if (lane == 0) {
-      we = S::eid();
-      wfe = 0;
-    }
-    const E agg = S::shfl(wa, kW - 1);
-    const int aggf = __shfl_sync(0xffffffffu, wf, kW - 1);
-    __syncwarp();
-    if (lane < kW) {
-      sh_wval[lane] = we;
-      sh_wflag[lane] = wfe;
-    }
-    if (lane == 0) {
-      sh_agg = agg;
-      sh_aggf = aggf;
-      // at once: the inclusive value when nothing before can change it
-      // (tile 0, or a tile holding a segment head), else the tile total
-      if (!stall) publish<O>(&states[tile], (tile == 0 || aggf) ? kStatIncl : kStatAgg, S::carry(agg));
-    }
-  }
-  __syncthreads();                                     // (S) with the look-back warp
-  if (!sh_ok) return;                                  // a wait gave up: write nothing
-  {
-    const E pv = sh_wval[warp];
-    const int pf = sh_wflag[warp];
-    if (!exf) ex = S::ecomb(pv, ex);
-    exf |= pf;                                         // this thread's prefix within the tile
-    const CT pre = sh_prefix;
-#pragma unroll
-    for (int i = 0; i < kMapItems; ++i)
-      if ((hm & ((2u << i) - 1u)) == 0u) {             // no head in this thread up to item i
-        E x = S::ecomb(ex, v[i]);
-        v[i] = exf ? x : S::apply(x, pre);
-      }
-  }
-  if constexpr (kVec4) {                               // each thread rewrites only its own chunks
-#pragma unroll
-    for (int q = 0; q < kMapItems / 4; ++q)
-      *reinterpret_cast<int4 *>(tsm + chunk_off((kMapItems / 4) * tid + q)) =
-          make_int4(__builtin_bit_cast(int, v[4 * q]), __builtin_bit_cast(int, v[4 * q + 1]),
-                    __builtin_bit_cast(int, v[4 * q + 2]), __builtin_bit_cast(int, v[4 * q + 3]));
-  } else {
-#pragma unroll
-    for (int i = 0; i < kMapItems; ++i) *SM::at(tsm, r0 + i) = v[i];
-  }
-  map_compute_bar();
-
-  // ---- stores through the map (the exclusive form shifts by one)
-  const E before = S::of_carry(sh_prefix);             // everything before the tile
-  auto result = [&](int r) -> E {
-    if (!excl) return *SM::at(tsm, r);
-    return is_head(r) ? S::eid() : (r == 0 ? before : *SM::at(tsm, r - 1));
-  };
-  bool stored = false;
-  if constexpr (kVec4) {
-    if (vec) {
-      stored = true;
-#pragma unroll
-    for (int q = 0; q < kMapTile / 4 / kMapThreads; ++q) {
-      const int c = q * kMapThreads + tid;
-      const int64_t g = t0 + 4 * int64_t(c);
-      if (g >= n) break;
-      uint32_t w[4];
-      if (!excl) {
-        const int4 x = *reinterpret_cast<const int4 *>(tsm + chunk_off(c));
-        w[0] = (uint32_t)x.x; w[1] = (uint32_t)x.y; w[2] = (uint32_t)x.z; w[3] = (uint32_t)x.w;
-      } else {
-#pragma unroll
-        for (int k = 0; k < 4; ++k) w[k] = S::out_bits(result(4 * c + k), m);
-      }
-      if (g + 4 <= n) {
-        __stcs(reinterpret_cast<int4 *>(out + map_elem(m, g)), make_int4((int)w[0], (int)w[1], (int)w[2], (int)w[3]));
-      } else {
-        for (int k = 0; k < 4 && g + k < n; ++k) out[map_elem(m, g + k)] = w[k];
-      }
-    }
-    }
-  }
-  if (!stored) {
-#pragma unroll
-    for (int j = 0; j < kMapItems; ++j) {
-      const int r = j * kMapThreads + tid;
-      const int64_t g = t0 + r;
-      if (g >= n) break;
-      out[map_elem(m, g)] = S::out_bits(result(r), m);
-    }
-  }
-  // ---- CSR: totals of the non-empty segments that end in this tile (the
-  // empty ones hold the identity already)
-  if (mode == CSR && args.sums) {
-    uint32_t *sums = static_cast<uint32_t *>(args.sums);
-    for (int64_t q = sh_seg0 + 1 + tid; q <= args.nseg; q += kMapThreads) {
-      const int64_t b = args.offsets[q];
-      if (b > tend) break;
-      if (b <= t0 || args.offsets[q - 1] == b) continue;
-      sums[q - 1] = S::out_bits(*SM::at(tsm, (int)(b - 1 - t0)), m);
-    }
-  }
-}
-
-size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
-
-constexpr int kWsTile = kSub;   // workspace is sized for the smallest tile
-
-// Schedule candidates: sub-tiles per tile (tile = 4096 x SUB elements; candidates.h).
-static_assert(kSub == kScanSubTile, "the candidate table counts sub-tiles of this size");
-static_assert(kSub * kScanSubCands[0] == kScanNoallocTile, "the no-alloc scan runs candidate 0");
-
-template <class T, class O, int MODE, int SUB, bool EXCL = false, bool MAPPED = false>
-int32_t run_scan_t(const T *in, T *out, const ScanArgs &a, void *ws, size_t ws_bytes, cudaStream_t s,
-                   const MapArgs &m) {
-  constexpr int kTile = kSub * SUB;
-  const int64_t ntiles = (a.n + kTile - 1) / kTile;
-  if (ntiles == 0) return DESC_OK;
-  const size_t need = align256(sizeof(ScanWs)) + size_t(ntiles) * sizeof(TileState);
-  if (!ws || ws_bytes < need) return DESC_ERR_WORKSPACE;
-  if (ntiles >= (int64_t(1) << 31)) return DESC_ERR_UNSUPPORTED;
-  const int smem = SUB * kStageBytes;
-  static std::atomic<unsigned long long> attr_devs{0};   // devices this kernel's attribute is set on
-  int dev = 0;
-  DESC_CUDA_TRY(cudaGetDevice(&dev));
-  const unsigned long long bit = dev >= 0 && dev < 64 ? 1ull << dev : 0ull;
-  if (!(attr_devs.load(std::memory_order_acquire) & bit) || !bit) {
-    DESC_CUDA_TRY(cudaFuncSetAttribute(scan_kernel<T, O, MODE, SUB, EXCL, MAPPED>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    attr_devs.fetch_or(bit, std::memory_order_release);
-  }
-  DESC_CUDA_TRY(cudaMemsetAsync(ws, 0, need, s));
-  ScanWs *w = static_cast<ScanWs *>(ws);
-  TileState *st = reinterpret_cast<TileState *>(static_cast<char *>(ws) + align256(sizeof(ScanWs)));
-  scan_kernel<T, O, MODE, SUB, EXCL, MAPPED><<<(unsigned)ntiles, kThreads + 32, smem, s>>>(in, out, a, w, st, m);
-  DESC_CUDA_TRY(cudaGetLastError());
-  return DESC_OK;
-}
-
-// Inclusive sums take every schedule candidate; maximum, minimum and the
-// exclusive forms the default tile; through a map, the default tile.
-template <class T, int MODE, bool MAPPED = false>
-int32_t run_scan(const T *in, T *out, const ScanArgs &a, void *ws, size_t ws_bytes, cudaStream_t s, int cand,
-                 int32_t flags, const MapArgs &m) {
-  if (flags & DESC_EXCLUSIVE) {
-    if (flags & DESC_MAX) return run_scan_t<T, ExtOp<T, true>, MODE, 4, true, MAPPED>(in, out, a, ws, ws_bytes, s, m);
-    if (flags & DESC_MIN) return run_scan_t<T, ExtOp<T, false>, MODE, 4, true, MAPPED>(in, out, a, ws, ws_bytes, s, m);
-    return run_scan_t<T, SumOp<T>, MODE, 4, true, MAPPED>(in, out, a, ws, ws_bytes, s, m);
-  }
-  if (flags & DESC_MAX) return run_scan_t<T, ExtOp<T, true>, MODE, 4, false, MAPPED>(in, out, a, ws, ws_bytes, s, m);
-  if (flags & DESC_MIN) return run_scan_t<T, ExtOp<T, false>, MODE, 4, false, MAPPED>(in, out, a, ws, ws_bytes, s, m);
-  if constexpr (MAPPED) {
-    return run_scan_t<T, SumOp<T>, MODE, 4, false, true>(in, out, a, ws, ws_bytes, s, m);
-  } else {
-    switch (kScanSubCands[(cand >= 0 && cand < kNumScanCands) ? cand : 0]) {
-      case 1: return run_scan_t<T, SumOp<T>, MODE, 1>(in, out, a, ws, ws_bytes, s, m);
-      case 2: return run_scan_t<T, SumOp<T>, MODE, 2>(in, out, a, ws, ws_bytes, s, m);
-      default: return run_scan_t<T, SumOp<T>, MODE, 4>(in, out, a, ws, ws_bytes, s, m);
-    }
-  }
-}
-
+constexpr int32_t kOtherValueOps = DESC_PROD | DESC_AND | DESC_OR | DESC_XOR;
 }  // namespace
 
 int32_t scan_status_take() {
-  int v = 0, z = 0;
-  if (cudaMemcpyFromSymbol(&v, g_scan_status, sizeof(int)) != cudaSuccess) return DESC_ERR_CUDA;
-  if (v != 0 && cudaMemcpyToSymbol(g_scan_status, &z, sizeof(int)) != cudaSuccess) return DESC_ERR_CUDA;
-  return v;
+  // every unit's word is read (and cleared); the first error is reported
+  const int32_t w[4] = {take_status_word(), scan_status_take_ops(), scan_status_take_mapped(),
+                        scan_status_take_map()};
+  for (int32_t v : w)
+    if (v != DESC_OK) return v;
+  return DESC_OK;
 }
 
 size_t scan_contig_ws(int32_t /*dtype*/, int64_t n) {
@@ -1205,6 +25,8 @@ size_t scan_contig_ws(int32_t /*dtype*/, int64_t n) {
 }
 
 int scan_candidates() { return kNumScanCands; }
+
+size_t scan_csr_ws(int64_t n) { return scan_contig_ws(DESC_F32, n); }
 
 int32_t launch_scan_contig(int32_t dtype, const void *in, void *out, int64_t n, int64_t period,
                            int32_t flags, void *ws, size_t ws_bytes, desc_stream_t st, int cand) {
@@ -1216,278 +38,27 @@ int32_t launch_scan_contig(int32_t dtype, const void *in, void *out, int64_t n, 
   a.vec = ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15) == 0;
   const bool periodic = period > 0 && period < n;
   const MapArgs none{};
+  if (flags & kOtherValueOps) return launch_scan_contig_ops(dtype, in, out, n, period, flags, ws, ws_bytes, st);
   if (dtype == DESC_I32) {
     auto i = static_cast<const int32_t *>(in);
     auto o = static_cast<int32_t *>(out);
-    return periodic ? run_scan<int32_t, PERIODIC>(i, o, a, ws, ws_bytes, s, cand, flags, none)
-                    : run_scan<int32_t, PLAIN>(i, o, a, ws, ws_bytes, s, cand, flags, none);
+    return periodic ? run_scan_basic<int32_t, PERIODIC, false>(i, o, a, ws, ws_bytes, s, cand, flags, none)
+                    : run_scan_basic<int32_t, PLAIN, false>(i, o, a, ws, ws_bytes, s, cand, flags, none);
   }
   auto i = static_cast<const float *>(in);
   auto o = static_cast<float *>(out);
-  return periodic ? run_scan<float, PERIODIC>(i, o, a, ws, ws_bytes, s, cand, flags, none)
-                  : run_scan<float, PLAIN>(i, o, a, ws, ws_bytes, s, cand, flags, none);
+  return periodic ? run_scan_basic<float, PERIODIC, false>(i, o, a, ws, ws_bytes, s, cand, flags, none)
+                  : run_scan_basic<float, PLAIN, false>(i, o, a, ws, ws_bytes, s, cand, flags, none);
 }
-
-// ---- segments by groups of threads -----------------------------------------
-// One group of G threads (a warp, or the whole CTA) per CSR segment, the
-// groups striding over the segments.  The group walks its segment in steps of
-// G x 4 points: each thread loads 4 consecutive points, scans them, the group
-// scans the thread totals (shuffles; for a CTA also the warp totals in shared
-// memory), applies the carry of the earlier steps and writes; the carry then
-// takes in the step's total (compensated for FP32 sums).  No look-back and no
-// workspace: suited to many short segments, where the tiles would hold many
-// segment heads.
-constexpr int kSegGroupThreads = 256, kSegItems = 4;
-
-template <class T, class O, bool EXCL, int G>
-__global__ void __launch_bounds__(kSegGroupThreads) seg_group_kernel(const T *__restrict__ in, T *__restrict__ out,
-                                                                     const int64_t *__restrict__ offsets, int64_t nseg,
-                                                                     T *__restrict__ sums) {
-  using CT = typename O::C;
-  constexpr int kGroups = kSegGroupThreads / G;
-  constexpr int kStep = G * kSegItems;
-  __shared__ T sh_w[kSegGroupThreads / 32];
-  const int gl = threadIdx.x % G, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int64_t sg = int64_t(blockIdx.x) * kGroups; sg < nseg; sg += int64_t(gridDim.x) * kGroups) {
-    const int64_t s = sg + threadIdx.x / G;
-    const bool live = s < nseg;                         // every thread takes part in the barriers
-    const int64_t a = live ? offsets[s] : 0, b = live ? offsets[s + 1] : 0;
-    CT carry = CT::zero();
-    // with G = the CTA, every thread has the same segment and step count, so
-    // the barriers inside the step are reached by all of them
-    const int64_t nsteps = b > a ? (b - a + kStep - 1) / kStep : 0;
-    for (int64_t k = 0; k < nsteps; ++k) {
-      const int64_t p0 = a + k * kStep + int64_t(gl) * kSegItems;
-      T v[kSegItems];
-#pragma unroll
-      for (int i = 0; i < kSegItems; ++i) v[i] = p0 + i < b ? in[p0 + i] : O::id();
-#pragma unroll
-      for (int i = 1; i < kSegItems; ++i) v[i] = O::comb(v[i - 1], v[i]);
-      T t = v[kSegItems - 1];                           // inclusive scan of the thread totals
-#pragma unroll
-      for (int off = 1; off < 32; off <<= 1) {
-        const T u = __shfl_up_sync(0xffffffffu, t, off);
-        if (lane >= off) t = O::comb(u, t);
-      }
-      T ex = __shfl_up_sync(0xffffffffu, t, 1);
-      if (lane == 0) ex = O::id();
-      T total = __shfl_sync(0xffffffffu, t, 31);
-      if (G == kSegGroupThreads) {                      // across the warps of the CTA
-        if (lane == 31) sh_w[warp] = t;
-        __syncthreads();
-        T wp = O::id();
-        total = O::id();
-#pragma unroll
-        for (int w = 0; w < kSegGroupThreads / 32; ++w) {
-          const T x = sh_w[w];
-          if (w < warp) wp = O::comb(wp, x);
-          total = O::comb(total, x);
-        }
-        ex = O::comb(wp, ex);
-        __syncthreads();                                // sh_w is reused by the next step
-      }
-      // results: carry, then the thread's prefix within the step, then the item
-      T prev = O::apply(ex, carry);                     // everything before this thread's first item
-#pragma unroll
-      for (int i = 0; i < kSegItems; ++i) {
-        const T inc = O::apply(O::comb(ex, v[i]), carry);
-        if (p0 + i < b) out[p0 + i] = EXCL ? prev : inc;
-        prev = inc;
-      }
-      carry = carry.plus(CT::of(total));
-    }
-    if (live && gl == 0 && sums) sums[s] = O::apply(O::id(), carry);
-  }
-}
-
-template <class T, class O, bool EXCL>
-int32_t run_seg_group(const T *in, T *out, const int64_t *offsets, int64_t nseg, T *sums, int threads,
-                      cudaStream_t s) {
-  const int groups = kSegGroupThreads / threads;
-  const int64_t ctas = std::max<int64_t>(1, std::min<int64_t>((nseg + groups - 1) / groups, 152 * 16));
-  if (threads == 32)
-    seg_group_kernel<T, O, EXCL, 32><<<(unsigned)ctas, kSegGroupThreads, 0, s>>>(in, out, offsets, nseg, sums);
-  else
-    seg_group_kernel<T, O, EXCL, kSegGroupThreads><<<(unsigned)ctas, kSegGroupThreads, 0, s>>>(in, out, offsets,
-                                                                                                 nseg, sums);
-  DESC_CUDA_TRY(cudaGetLastError());
-  return DESC_OK;
-}
-
-namespace {
-
-template <class T, class S>
-struct StateTag {
-  using Elem = T;
-  using States = S;
-};
-
-// Calls f(StateTag<element type, state layer>{}) for the operator in flags.
-template <class F>
-int32_t with_states(int32_t dtype, int32_t flags, F &&f) {
-  const int32_t op = flags & kOperatorFlags;
-  if (dtype == DESC_I32) {
-    using T = int32_t;
-    switch (op) {
-      case 0: return f(StateTag<T, ValueStates<T, SumOp<T>>>{});
-      case DESC_MAX: return f(StateTag<T, ValueStates<T, ValOp<T, kMaxOp>>>{});
-      case DESC_MIN: return f(StateTag<T, ValueStates<T, ValOp<T, kMinOp>>>{});
-      case DESC_PROD: return f(StateTag<T, ValueStates<T, ValOp<T, kProdOp>>>{});
-      case DESC_AND: return f(StateTag<T, ValueStates<T, ValOp<T, kAndOp>>>{});
-      case DESC_OR: return f(StateTag<T, ValueStates<T, ValOp<T, kOrOp>>>{});
-      case DESC_XOR: return f(StateTag<T, ValueStates<T, ValOp<T, kXorOp>>>{});
-      case DESC_ARGMAX: return f(StateTag<T, ArgStates<T, true>>{});
-      case DESC_ARGMIN: return f(StateTag<T, ArgStates<T, false>>{});
-      default: return DESC_ERR_INVALID_ARG;
-    }
-  }
-  using T = float;
-  switch (op) {
-    case 0: return f(StateTag<T, ValueStates<T, SumOp<T>>>{});
-    case DESC_MAX: return f(StateTag<T, ValueStates<T, ValOp<T, kMaxOp>>>{});
-    case DESC_MIN: return f(StateTag<T, ValueStates<T, ValOp<T, kMinOp>>>{});
-    case DESC_PROD: return f(StateTag<T, ValueStates<T, ValOp<T, kProdOp>>>{});
-    case DESC_ARGMAX: return f(StateTag<T, ArgStates<T, true>>{});
-    case DESC_ARGMIN: return f(StateTag<T, ArgStates<T, false>>{});
-    default: return DESC_ERR_INVALID_ARG;
-  }
-}
-
-}  // namespace
-
-namespace {
-
-// The canonical map of nd dims (extent-1 dims dropped, neighbours merged)
-// and its point count; nd == 0: the identity over `count` points.
-int64_t build_map(int64_t off, const int64_t *ext, const int64_t *stride, int nd, int64_t count, MapArgs *m) {
-  *m = MapArgs{};
-  int64_t n = 1;
-  for (int i = 0; i < nd; ++i) {
-    m->ext[i] = ext[i];
-    m->st[i] = stride[i];
-    n *= ext[i];
-  }
-  if (nd == 0) n = count;
-  m->off = off;
-  int64_t *sets[1] = {m->st};
-  m->nd = nd ? canon_dims(nd, m->ext, sets, 1) : 0;
-  if (nd && m->nd == 0) {                              // a single point
-    m->nd = 1;
-    m->ext[0] = 1;
-    m->st[0] = 0;
-  }
-  bool fast = n < (int64_t(1) << 32);
-  for (int i = 0; i < m->nd; ++i) {
-    fast = fast && m->ext[i] <= (int64_t(1) << 31);
-    if (fast) m->div[i] = make_fastdiv((uint32_t)m->ext[i]);
-  }
-  m->fast = fast ? 1 : 0;
-  return n;
-}
-
-// 128-bit accesses through the map: four consecutive points (from a multiple
-// of 4) are four consecutive elements starting on a 16-byte boundary of in
-// and out.
-bool map_vec(const MapArgs &m, const void *in, const void *out) {
-  bool vec = ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15) == 0 && m.off % 4 == 0;
-  if (m.nd >= 1) {
-    vec = vec && m.st[m.nd - 1] == 1 && m.ext[m.nd - 1] % 4 == 0;
-    for (int i = 0; i + 1 < m.nd; ++i) vec = vec && m.st[i] % 4 == 0;
-  }
-  return vec;
-}
-
-}  // namespace
-
-int32_t launch_scan_map(int32_t dtype, const void *in, void *out, int64_t off, const int64_t *ext,
-                        const int64_t *stride, int nd, int64_t period, const int64_t *offsets, int64_t nseg,
-                        void *sums, int32_t flags, void *ws, size_t ws_bytes, desc_stream_t st) {
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(st);
-  MapArgs m;
-  const int64_t n = build_map(off, ext, stride, nd, period, &m);
-  if (n == 0) return DESC_OK;
-  const int64_t ntiles = (n + kMapTile - 1) / kMapTile;
-  const size_t need = align256(sizeof(ScanWs)) + size_t(ntiles) * sizeof(TileState);
-  if (!ws || ws_bytes < need) return DESC_ERR_WORKSPACE;
-  if (ntiles >= (int64_t(1) << 31)) return DESC_ERR_UNSUPPORTED;
-  ScanArgs a{};
-  a.n = n;
-  a.period = period > 0 ? period : n;
-  a.offsets = offsets;
-  a.nseg = nseg;
-  a.sums = sums;
-  a.debug = (flags & DESC_DEBUG_STALL_TILE) ? 1 : 0;
-  a.vec = map_vec(m, in, out) ? 1 : 0;
-  const int mode = offsets ? CSR : (a.period < n ? PERIODIC : PLAIN);
-  const int excl = (flags & DESC_EXCLUSIVE) ? 1 : 0;
-  DESC_CUDA_TRY(cudaMemsetAsync(ws, 0, need, s));
-  ScanWs *w = static_cast<ScanWs *>(ws);
-  TileState *ts = reinterpret_cast<TileState *>(static_cast<char *>(ws) + align256(sizeof(ScanWs)));
-  return with_states(dtype, flags, [&](auto tag) {
-    using T = typename decltype(tag)::Elem;
-    using S = typename decltype(tag)::States;
-    scan_map_kernel<T, S><<<(unsigned)ntiles, kMapThreads + 32, 0, s>>>(static_cast<const T *>(in),
-                                                                         static_cast<uint32_t *>(out), m, a, w, ts,
-                                                                         mode, excl);
-    DESC_CUDA_TRY(cudaGetLastError());
-    return DESC_OK;
-  });
-}
-
-int32_t launch_scan_mapped(int32_t dtype, const void *in, void *out, int64_t off, const int64_t *ext,
-                           const int64_t *stride, int nd, int64_t period, int32_t flags, void *ws, size_t ws_bytes,
-                           desc_stream_t st) {
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(st);
-  if (flags & kMapScanOps) return DESC_ERR_INVALID_ARG;
-  MapArgs m;
-  const int64_t n = build_map(off, ext, stride, nd, period, &m);
-  if (n == 0) return DESC_OK;
-  if (m.nd > 2 || !m.fast)                             // the one-tile map scan decodes any map
-    return launch_scan_map(dtype, in, out, off, ext, stride, nd, period, nullptr, 0, nullptr, flags, ws, ws_bytes,
-                           st);
-  ScanArgs a{};
-  a.n = n;
-  a.period = period > 0 ? period : n;
-  a.debug = (flags & DESC_DEBUG_STALL_TILE) ? 1 : 0;
-  a.vec = map_vec(m, in, out) ? 1 : 0;
-  const bool periodic = a.period < n;
-  if (dtype == DESC_I32) {
-    auto i = static_cast<const int32_t *>(in);
-    auto o = static_cast<int32_t *>(out);
-    return periodic ? run_scan<int32_t, PERIODIC, true>(i, o, a, ws, ws_bytes, s, -1, flags, m)
-                    : run_scan<int32_t, PLAIN, true>(i, o, a, ws, ws_bytes, s, -1, flags, m);
-  }
-  auto i = static_cast<const float *>(in);
-  auto o = static_cast<float *>(out);
-  return periodic ? run_scan<float, PERIODIC, true>(i, o, a, ws, ws_bytes, s, -1, flags, m)
-                  : run_scan<float, PLAIN, true>(i, o, a, ws, ws_bytes, s, -1, flags, m);
-}
-
-size_t scan_csr_ws(int64_t n) { return scan_contig_ws(DESC_F32, n); }
 
 int32_t launch_scan_csr(int32_t dtype, const void *in, void *out, int64_t n, const int64_t *offsets,
                         int64_t nseg, void *sums, int32_t flags, void *ws, size_t ws_bytes,
                         desc_stream_t st, int cand) {
   cudaStream_t s = reinterpret_cast<cudaStream_t>(st);
   const SegCand sc = kSegCands[(cand >= 0 && cand < kNumSegCands) ? cand : 0];
-  if (sc.threads > 0 && !(flags & DESC_DEBUG_STALL_TILE)) {   // a group of threads per segment
-    const bool ex = (flags & DESC_EXCLUSIVE) != 0;
-    auto go = [&](auto tag) -> int32_t {
-      using T = decltype(tag);
-      const T *i = static_cast<const T *>(in);
-      T *o = static_cast<T *>(out);
-      T *sm = static_cast<T *>(sums);
-      if (flags & DESC_MAX)
-        return ex ? run_seg_group<T, ExtOp<T, true>, true>(i, o, offsets, nseg, sm, sc.threads, s)
-                  : run_seg_group<T, ExtOp<T, true>, false>(i, o, offsets, nseg, sm, sc.threads, s);
-      if (flags & DESC_MIN)
-        return ex ? run_seg_group<T, ExtOp<T, false>, true>(i, o, offsets, nseg, sm, sc.threads, s)
-                  : run_seg_group<T, ExtOp<T, false>, false>(i, o, offsets, nseg, sm, sc.threads, s);
-      return ex ? run_seg_group<T, SumOp<T>, true>(i, o, offsets, nseg, sm, sc.threads, s)
-                : run_seg_group<T, SumOp<T>, false>(i, o, offsets, nseg, sm, sc.threads, s);
-    };
-    return dtype == DESC_I32 ? go(int32_t(0)) : go(0.f);
-  }
+  if (sc.threads > 0 && !(flags & DESC_DEBUG_STALL_TILE) && !(flags & kOtherValueOps))   // a group per segment
+    return launch_seg_group(dtype, in, out, offsets, nseg, sums, flags, sc.threads, st);
+  if (flags & kOtherValueOps) return launch_scan_csr_ops(dtype, in, out, n, offsets, nseg, sums, flags, ws, ws_bytes, st);
   if (sc.threads == 0) cand = cand >= 0 && cand < kNumScanCands ? cand : 0;   // tiles of 4096 x sub
   ScanArgs a{};
   a.n = n;
@@ -1498,9 +69,9 @@ int32_t launch_scan_csr(int32_t dtype, const void *in, void *out, int64_t n, con
   a.vec = ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15) == 0;
   const MapArgs none{};
   if (dtype == DESC_I32)
-    return run_scan<int32_t, CSR>(static_cast<const int32_t *>(in), static_cast<int32_t *>(out), a,
+    return run_scan_basic<int32_t, CSR, false>(static_cast<const int32_t *>(in), static_cast<int32_t *>(out), a,
                                   ws, ws_bytes, s, cand, flags, none);
-  return run_scan<float, CSR>(static_cast<const float *>(in), static_cast<float *>(out), a, ws,
+  return run_scan_basic<float, CSR, false>(static_cast<const float *>(in), static_cast<float *>(out), a, ws,
                               ws_bytes, s, cand, flags, none);
 }
 
