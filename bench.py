@@ -1058,7 +1058,8 @@ def main():
                     help="run the step's views through the general kernels (desc_force_generic), for profiles")
     ap.add_argument("--save-tune", default="", help="save the tuned schedule table to this file")
     ap.add_argument("--load-tune", default="", help="use a saved schedule table instead of tuning")
-    ap.add_argument("--case", choices=["step", "matmul", "segmented", "overhead", "split", "sanitize"], default="step",
+    ap.add_argument("--case", choices=["step", "matmul", "segmented", "overhead", "split", "sanitize", "operators"],
+                    default="step",
                     help="matmul / segmented: run only that measurement (for profiler captures)")
     ap.add_argument("--mm-n", type=int, default=8192, help="matmul size for --case matmul")
     ap.add_argument("--mm-prec", default="split3,bf16,fp32_simt",
@@ -1097,6 +1098,11 @@ def main():
             line = {"case": "overhead", "view_overhead": run_view_overhead(torch, D, synth, dev, stream)}
         elif args.case == "sanitize":
             line = {"case": "sanitize", "calls": run_sanitize_case(torch, D, synth, dev)}
+        elif args.case == "operators":
+            sz = sizes(args.small)
+            xr = synth.ints_pm1000(sz["reduce_n"], seed=1, device=dev)
+            xs = synth.uniform_grid(sz["scan_n"], seed=2, device=dev)
+            line = {"case": "operators", "operators": run_operators(torch, D, dev, stream, xr, xs, peaks())}
         else:
             line = {"case": "segmented", "segmented": run_segmented(torch, D, synth, dev, stream, nseg=args.seg_count)}
     else:

@@ -188,9 +188,12 @@ extern "C" int32_t desc_scan(const desc_view *v, const desc_exec *ex, int32_t se
   if ((r = check_device_ptr(out, 4)) != DESC_OK) return r;
   if (in != out && ranges_overlap(in, in_bytes, out, out_bytes)) return DESC_ERR_OVERLAP;
   if ((r = check_writes(L, ex)) != DESC_OK) return r;
-  if (sp.contig && !(flags & kMapScanOps)) {
+  if (sp.contig) {
     const char *ib = static_cast<const char *>(in);
     char *ob = static_cast<char *>(out);
+    if (flags & kArgFlags)                             // arg operators: element indices from sp.start
+      return launch_scan_arg(dtype, ib + sp.start * 4, ob + sp.start * 4, sp.total, sp.period, nullptr, 0, nullptr,
+                             sp.start, flags, ws, ws_bytes, s);
     return launch_scan_contig(dtype, ib + sp.start * 4, ob + sp.start * 4, sp.total, sp.period, flags, ws,
                               ws_bytes, s, schedule_for(DESC_OP_SCAN, dtype, sp.total, 0));
   }
@@ -450,10 +453,9 @@ extern "C" int32_t desc_segmented_reduce_scan(const int64_t *d_offsets, int64_t 
   if ((flags & DESC_CHECK_OFFSETS) && (r = check_offsets_device(d_offsets, nseg, total)) != DESC_OK) return r;
   if (total == 0) return fill_identity(sums_out, nseg, dtype, flags, s);   // every segment is empty
   const int32_t kf = flags & (DESC_DEBUG_STALL_TILE | DESC_EXCLUSIVE | kOperatorFlags);
-  if (flags & kMapScanOps) {                           // empty segments keep the identity written first
+  if (flags & kArgFlags) {                             // empty segments keep the identity written first
     if ((r = fill_identity(sums_out, nseg, dtype, flags, s)) != DESC_OK) return r;
-    return launch_scan_map(dtype, in, scan_out, 0, nullptr, nullptr, 0, total, d_offsets, nseg, sums_out, kf, ws,
-                           ws_bytes, s);
+    return launch_scan_arg(dtype, in, scan_out, total, 0, d_offsets, nseg, sums_out, 0, kf, ws, ws_bytes, s);
   }
   return launch_scan_csr(dtype, in, scan_out, total, d_offsets, nseg, sums_out, kf, ws, ws_bytes, s,
                          schedule_for(DESC_OP_SEGMENTED, dtype, total, nseg));

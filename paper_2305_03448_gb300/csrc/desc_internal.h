@@ -115,6 +115,13 @@ int32_t launch_scan_contig_ops(int32_t dtype, const void *in, void *out, int64_t
                                void *ws, size_t ws_bytes, desc_stream_t s);
 int32_t launch_scan_csr_ops(int32_t dtype, const void *in, void *out, int64_t n, const int64_t *offsets,
                             int64_t nseg, void *sums, int32_t flags, void *ws, size_t ws_bytes, desc_stream_t s);
+// The arg-maximum / arg-minimum scan over one contiguous run of n points
+// (segments of `period` points, or CSR offsets / nseg / sums as
+// launch_scan_csr, the caller filling sums with -1 first); point g is element
+// idx_base + g, whose index is written (int32).  Workspace: scan_contig_ws.
+int32_t launch_scan_arg(int32_t dtype, const void *in, void *out, int64_t n, int64_t period, const int64_t *offsets,
+                        int64_t nseg, void *sums, int64_t idx_base, int32_t flags, void *ws, size_t ws_bytes,
+                        desc_stream_t s);
 // One group of `threads` threads (32 or 256) per CSR segment (k_scan_map.cu):
 // sums, maxima, minima, inclusive or exclusive; no workspace.
 int32_t launch_seg_group(int32_t dtype, const void *in, void *out, const int64_t *offsets, int64_t nseg, void *sums,

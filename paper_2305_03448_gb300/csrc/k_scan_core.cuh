@@ -1142,6 +1142,384 @@ __global__ void __launch_bounds__(kMapThreads + 32) scan_map_kernel(const T *__r
   }
 }
 
+// ---- the arg operators over contiguous runs ---------------------------------
+// An element (x, index) as one 64-bit key whose unsigned maximum is the
+// arg-maximum (arg-minimum): the high word is an order-preserving code of x
+// (for the minimum, of -x in effect), with every NaN at 0 and -0 read as +0;
+// the low word is ~index, so that among equal codes the smaller index wins.
+// Key 0 is "no element".  A real key is never 0: ~index has its two top bits
+// set for every index below 2^30.
+template <class T, bool MAX>
+__device__ __forceinline__ uint32_t order_code(T x) {
+  uint32_t u;
+  if constexpr (std::is_same<T, float>::value) {
+    if (x != x) return 0u;                              // NaN: below every number
+    u = x == 0.f ? 0u : __float_as_uint(x);             // -0 and +0 are one value
+    u = (u & 0x80000000u) ? ~u : (u | 0x80000000u);     // monotone in x
+  } else {
+    u = (uint32_t)x ^ 0x80000000u;                      // monotone in x
+  }
+  return MAX ? u : ~u;
+}
+
+template <class T, bool MAX>
+struct ArgKeys {
+  using E = unsigned long long;
+  struct C {
+    E k;
+    __device__ static C zero() { return {0ull}; }
+    __device__ static C of(E x) { return {x}; }
+    __device__ C plus(const C &o) const { return {k > o.k ? k : o.k}; }
+    __device__ C shfl_down(int off) const {
+      return {(E)__shfl_down_sync(0xffffffffu, (long long)k, off)};
+    }
+  };
+  // In a 62-bit tile state: the code and the low 30 bits of ~index (the top
+  // two are 1 for every real key); all 62 bits 0 is "no element".
+  struct Op {
+    using C = ArgKeys::C;
+    __device__ static unsigned long long pack(unsigned long long st, const C &c) {
+      return (st << 62) | ((c.k >> 32) << 30) | (c.k & 0x3FFFFFFFull);
+    }
+    __device__ static C unpack(unsigned long long w) {
+      const unsigned long long code = (w >> 30) & 0xFFFFFFFFull, low = w & 0x3FFFFFFFull;
+      if (code == 0 && low == 0) return {0ull};
+      return {(code << 32) | 0xC0000000ull | low};
+    }
+  };
+  __device__ static E eid() { return 0ull; }
+  __device__ static E ecomb(E a, E b) { return a > b ? a : b; }
+  __device__ static E shfl_up(E e, int off) { return (E)__shfl_up_sync(0xffffffffu, (long long)e, off); }
+  __device__ static E shfl(E e, int src) { return (E)__shfl_sync(0xffffffffu, (long long)e, src); }
+  __device__ static C carry(E e) { return {e}; }
+};
+
+// The look-back scan's pipeline (ticket with the guessed tile prefetched,
+// cp.async into the swizzled stages, a look-back warp) over tiles of two
+// 4096-point sub-tiles, for the arg-maximum / arg-minimum: point g is element
+// idx_base + g.  Two passes over the staged tile.  The first turns every
+// element into its 32-bit order code, in place, and scans the threads'
+// (code, first position of the best) aggregates into each thread's
+// in-tile start state; once the look-back prefix is known, the second walks
+// each thread's points again from its start state, one 32-bit comparison a
+// point, and leaves the inclusive indices in place for a coalesced store
+// (the exclusive form shifts them by one).  The tile state carries ArgKeys.
+constexpr int kArgSub = 2;
+constexpr int kArgTile = kSub * kArgSub;
+constexpr int kArgSmem = kArgSub * kStageBytes;
+static_assert(kItems == 16, "a thread's points are one 16-bit head mask");
+
+template <class T, bool MAX, int MODE, bool EXCL>
+__global__ void __launch_bounds__(kThreads + 32, 3) scan_arg_kernel(const T *in, int32_t *out, ScanArgs args,
+                                                                    int64_t idx_base, ScanWs *ws,
+                                                                    TileState *states) {
+  using S = ArgKeys<T, MAX>;
+  using E = typename S::E;
+  using O = typename S::Op;
+  using CT = typename S::C;
+  constexpr int kTile = kArgTile;
+  extern __shared__ __align__(128) unsigned char ring[];   // kArgSub stages
+  __shared__ int64_t sh_tile, sh_seg0;
+  __shared__ E sh_wval[kWarps];
+  __shared__ int sh_wflag[kWarps];
+  __shared__ E sh_carry;                // in-tile state after the sub-tiles done so far
+  __shared__ int sh_carry_flag;
+  __shared__ CT sh_prefix;
+  __shared__ int sh_ok;
+  __shared__ unsigned sh_heads[kTile / 32];              // one bit a point: a segment starts there
+  __shared__ volatile int sh_go;
+  unsigned short *heads16 = reinterpret_cast<unsigned short *>(sh_heads);
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t n = args.n;
+  const MapArgs none{};
+  const RunAddr addr{none};
+  if (tid == 0) {
+    sh_tile = atomicAdd(&ws->ticket, 1u);
+    sh_go = 0;
+  }
+  if (MODE == CSR)
+    for (int i = tid; i < kTile / 32; i += kThreads + 32) sh_heads[i] = 0u;
+  if (warp < kWarps) {                                 // the guessed tile into L2 (as scan_kernel)
+    const int64_t guess = int64_t(blockIdx.x) * kTile;
+#pragma unroll
+    for (int k = 0; k < kTile / 32 / kThreads; ++k) {
+      const int64_t g = guess + 32 * int64_t(k * kThreads + tid);
+      if (g < n) asm volatile("prefetch.global.L2 [%0];" ::"l"(in + g));
+    }
+  }
+  __syncthreads();
+  const int64_t tile = sh_tile;
+  const int64_t t0 = tile * kTile;
+  const int64_t tend = std::min<int64_t>(t0 + kTile, n);
+  const bool stall = args.debug && tile == 1;
+
+  if (warp == kWarps) {
+    // ---- look-back warp: the prefix of everything before t0
+    bool first_is_head = tile == 0;
+    if (MODE == PERIODIC) first_is_head = first_is_head || (t0 % args.period == 0);
+    if (MODE == CSR) first_is_head = first_is_head || args.offsets[find_segment(args.offsets, args.nseg, t0)] == t0;
+    CT prefix = CT::zero();
+    bool ok = true;
+    if (!first_is_head) {
+      for (unsigned i = 0; i < kGoSpins && !sh_go; ++i) __nanosleep(64);
+      ok = look_back<O>(states, tile, ws, args.debug ? kDebugBudgetCycles : kBudgetCycles, prefix);
+    }
+    if (lane == 0) {
+      sh_prefix = prefix;
+      sh_ok = ok ? 1 : 0;
+    }
+    __syncthreads();                                    // (S) the tile's state is known
+    if (ok && lane == 0 && !stall && tile != 0 && !sh_carry_flag)
+      publish<O>(&states[tile], kStatIncl, prefix.plus(S::carry(sh_carry)));
+    return;
+  }
+
+  // ---- compute warps
+#pragma unroll
+  for (int s = 0; s < kArgSub; ++s) {
+    load_sub<T>(ring + s * kStageBytes, in, t0 + int64_t(s) * kSub, n, args.vec != 0, addr);
+    cp_async_commit();
+  }
+  if (MODE == CSR) {                                   // segment heads: offsets[q] in (t0, tend), and t0
+    if (warp == 0) {
+      const int64_t s0 = find_segment(args.offsets, args.nseg, t0);
+      if (lane == 0) {
+        sh_seg0 = s0;
+        if (args.offsets[s0] == t0 || t0 == 0) atomicOr(&sh_heads[0], 1u);
+      }
+    }
+    compute_bar();
+    for (int64_t q = sh_seg0 + 1 + tid; q <= args.nseg; q += kThreads) {
+      const int64_t b = args.offsets[q];
+      if (b >= tend) break;
+      if (b > t0) atomicOr(&sh_heads[(b - t0) >> 5], 1u << ((b - t0) & 31));
+    }
+  }
+  if (tid == 0) {
+    sh_carry = S::eid();
+    sh_carry_flag = 0;
+  }
+  // this thread's absolute index of its first point in sub-tile 0 (below 2^30)
+  const int32_t ibase = int32_t(idx_base + t0) + tid * kItems;
+  // per sub-tile: the in-tile state before the thread's points, whether a
+  // head precedes them in the tile, and the heads among them (named, not
+  // arrays, so that they stay in registers across the rolled loop)
+  static_assert(kArgSub == 2, "two sub-tiles a tile");
+  E start0 = 0, start1 = 0;
+  int sflag0 = 0, sflag1 = 0;
+  unsigned hm0 = 0u, hm1 = 0u;
+
+  // ---- pass 1: order codes in place; thread aggregates scanned over the tile
+#pragma unroll 1
+  for (int s = 0; s < kArgSub; ++s) {
+    unsigned char *st = ring + s * kStageBytes;
+    cp_async_wait_dyn(kArgSub - 1 - s);
+    compute_bar();                                      // sub-tile s, the heads and the carry are visible
+    if (s == 0 && tid == 0) sh_go = 1;
+    const E cv = sh_carry;
+    const int cf = sh_carry_flag;
+    const int rel0 = s * kSub + tid * kItems;
+    const int64_t g0 = t0 + rel0;
+    const int64_t lim64 = n - g0;
+    const int lim = lim64 >= kItems ? kItems : (lim64 > 0 ? int(lim64) : 0);
+    unsigned hm = 0u;
+    if (MODE == PLAIN) {
+      hm = g0 == 0 ? 1u : 0u;
+    } else if (MODE == PERIODIC) {
+      int64_t r = g0 % args.period;
+#pragma unroll
+      for (int i = 0; i < kItems; ++i) {
+        if (r == 0) hm |= 1u << i;
+        if (++r == args.period) r = 0;
+      }
+      heads16[rel0 >> 4] = (unsigned short)hm;
+    } else {
+      hm = heads16[rel0 >> 4];
+    }
+    if (s == 0) hm0 = hm;
+    else hm1 = hm;
+    uint32_t c[kItems];
+#pragma unroll
+    for (int q = 0; q < kItems / 4; ++q) {
+      int4 *p = reinterpret_cast<int4 *>(st + chunk_off((kItems / 4) * tid + q));
+      const int4 x = *p;
+      c[4 * q + 0] = order_code<T, MAX>(__builtin_bit_cast(T, x.x));
+      c[4 * q + 1] = order_code<T, MAX>(__builtin_bit_cast(T, x.y));
+      c[4 * q + 2] = order_code<T, MAX>(__builtin_bit_cast(T, x.z));
+      c[4 * q + 3] = order_code<T, MAX>(__builtin_bit_cast(T, x.w));
+      *p = make_int4(int(c[4 * q]), int(c[4 * q + 1]), int(c[4 * q + 2]), int(c[4 * q + 3]));
+    }
+    // the thread's aggregate: the best code after its last head, first position on ties
+    uint32_t best = 0u;
+    int pos = -1;
+    if (hm == 0u && lim == kItems) {
+      best = c[0];
+      pos = 0;
+#pragma unroll
+      for (int i = 1; i < kItems; ++i)
+        if (c[i] > best) {
+          best = c[i];
+          pos = i;
+        }
+    } else {
+#pragma unroll
+      for (int i = 0; i < kItems; ++i)
+        if (i < lim && (((hm >> i) & 1u) || pos < 0 || c[i] > best)) {
+          best = c[i];
+          pos = i;
+        }
+    }
+    E a = pos < 0 ? S::eid() : ((E)best << 32) | (uint32_t)~(uint32_t)(ibase + s * kSub + pos);
+    int f = hm != 0u;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {           // warp scan, segmented operator
+      const E au = S::shfl_up(a, off);
+      const int fu = __shfl_up_sync(0xffffffffu, f, off);
+      if (lane >= off) {
+        if (!f) a = S::ecomb(au, a);
+        f |= fu;
+      }
+    }
+    if (lane == 31) {
+      sh_wval[warp] = a;
+      sh_wflag[warp] = f;
+    }
+    E ex = S::shfl_up(a, 1);
+    int exf = __shfl_up_sync(0xffffffffu, f, 1);
+    if (lane == 0) {
+      ex = S::eid();
+      exf = 0;
+    }
+    compute_bar();
+    if (warp == 0) {                                    // scan of the warp totals
+      E wa = lane < kWarps ? sh_wval[lane] : S::eid();
+      int wf = lane < kWarps ? sh_wflag[lane] : 0;
+#pragma unroll
+      for (int off = 1; off < kWarps; off <<= 1) {
+        const E au = S::shfl_up(wa, off);
+        const int fu = __shfl_up_sync(0xffffffffu, wf, off);
+        if (lane >= off) {
+          if (!wf) wa = S::ecomb(au, wa);
+          wf |= fu;
+        }
+      }
+      E we = S::shfl_up(wa, 1);
+      int wfe = __shfl_up_sync(0xffffffffu, wf, 1);
+      if (lane == 0) {
+        we = S::eid();
+        wfe = 0;
+      }
+      const E sub_val = S::shfl(wa, kWarps - 1);
+      const int sub_flag = __shfl_sync(0xffffffffu, wf, kWarps - 1);
+      __syncwarp();
+      if (lane < kWarps) {
+        sh_wval[lane] = we;
+        sh_wflag[lane] = wfe;
+      }
+      if (lane == 0) {                                  // the state after this sub-tile
+        sh_carry = sub_flag ? sub_val : S::ecomb(cv, sub_val);
+        sh_carry_flag = cf | sub_flag;
+      }
+    }
+    compute_bar();
+    const E pv = sh_wval[warp];
+    const int pf = sh_wflag[warp];
+    if (!exf) ex = S::ecomb(pv, ex);
+    exf |= pf;                                          // (pf, pv) then (exf, ex)
+    const E st_in = exf ? ex : S::ecomb(cv, ex);
+    if (s == 0) {
+      start0 = st_in;
+      sflag0 = exf | cf;
+    } else {
+      start1 = st_in;
+      sflag1 = exf | cf;
+    }
+  }
+  compute_bar();
+  if (tid == 0 && !stall)
+    publish<O>(&states[tile], (tile == 0 || sh_carry_flag) ? kStatIncl : kStatAgg, S::carry(sh_carry));
+  __syncthreads();                                      // (S) with the look-back warp
+  if (!sh_ok) return;
+  const E pre = sh_prefix.k;
+
+  // ---- pass 2: each thread's points from its start state; inclusive indices in place
+#pragma unroll
+  for (int s = 0; s < kArgSub; ++s) {
+    unsigned char *st = ring + s * kStageBytes;
+    const E e0 = (s == 0 ? sflag0 : sflag1) ? (s == 0 ? start0 : start1) : S::ecomb(pre, s == 0 ? start0 : start1);
+    uint32_t best = uint32_t(e0 >> 32);
+    int32_t idx = int32_t(~uint32_t(e0));               // "no element": code 0, index -1
+    const int32_t ib = ibase + s * kSub;
+    const unsigned hm = s == 0 ? hm0 : hm1;
+    const int64_t lim64 = n - (t0 + s * kSub + tid * kItems);
+    const bool full = hm == 0u && lim64 >= kItems;
+#pragma unroll
+    for (int q = 0; q < kItems / 4; ++q) {
+      int4 *p = reinterpret_cast<int4 *>(st + chunk_off((kItems / 4) * tid + q));
+      const int4 x = *p;
+      const uint32_t cs[4] = {uint32_t(x.x), uint32_t(x.y), uint32_t(x.z), uint32_t(x.w)};
+      int32_t r[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int i = 4 * q + c;
+        if (full) {
+          if (cs[c] > best) {
+            best = cs[c];
+            idx = ib + i;
+          }
+        } else if (i < lim64 && (((hm >> i) & 1u) || idx < 0 || cs[c] > best)) {
+          best = cs[c];
+          idx = ib + i;
+        }
+        r[c] = idx;
+      }
+      *p = make_int4(r[0], r[1], r[2], r[3]);
+    }
+  }
+  compute_bar();                                        // every point's inclusive index is in place
+
+  auto incl_at = [&](int r) -> int32_t {
+    return reinterpret_cast<const int32_t *>(ring + (r / kSub) * kStageBytes + chunk_off((r % kSub) / 4))[r % 4];
+  };
+  auto head_at = [&](int r) -> bool {
+    if (MODE == PLAIN) return t0 + r == 0;
+    return (sh_heads[r >> 5] >> (r & 31)) & 1u;
+  };
+  const int32_t pre_idx = pre ? int32_t(~uint32_t(pre)) : -1;
+#pragma unroll 1
+  for (int j = tid; j < kTile / 4; j += kThreads) {
+    const int64_t g = t0 + 4 * int64_t(j);
+    if (g >= n) break;
+    const int4 x = *reinterpret_cast<const int4 *>(ring + (j / (kSub / 4)) * kStageBytes + chunk_off(j % (kSub / 4)));
+    int32_t w[4] = {x.x, x.y, x.z, x.w};
+    if (EXCL) {
+      const int r = 4 * j;
+      const int32_t before = r == 0 ? pre_idx : incl_at(r - 1);
+      w[3] = head_at(r + 3) ? -1 : w[2];
+      w[2] = head_at(r + 2) ? -1 : w[1];
+      w[1] = head_at(r + 1) ? -1 : w[0];
+      w[0] = head_at(r) ? -1 : before;
+    }
+    if (args.vec && g + 4 <= n) {
+      __stcs(reinterpret_cast<int4 *>(out + g), make_int4(w[0], w[1], w[2], w[3]));
+    } else {
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        if (g + c < n) out[g + c] = w[c];
+    }
+  }
+  if (MODE == CSR && args.sums) {                       // totals of the non-empty segments ending here
+    int32_t *sums = static_cast<int32_t *>(args.sums);
+    for (int64_t q = sh_seg0 + 1 + tid; q <= args.nseg; q += kThreads) {
+      const int64_t b = args.offsets[q];
+      if (b > tend) break;
+      if (b <= t0 || args.offsets[q - 1] == b) continue;
+      sums[q - 1] = incl_at(int(b - 1 - t0));
+    }
+  }
+}
+
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 constexpr int kWsTile = kSub;   // workspace is sized for the smallest tile
