@@ -1151,15 +1151,14 @@ __global__ void __launch_bounds__(kMapThreads + 32) scan_map_kernel(const T *__r
 // set for every index below 2^30.
 template <class T, bool MAX>
 __device__ __forceinline__ uint32_t order_code(T x) {
-  uint32_t u;
   if constexpr (std::is_same<T, float>::value) {
-    if (x != x) return 0u;                              // NaN: below every number
-    u = x == 0.f ? 0u : __float_as_uint(x);             // -0 and +0 are one value
-    u = (u & 0x80000000u) ? ~u : (u | 0x80000000u);     // monotone in x
+    const uint32_t u = __float_as_uint(__fadd_rn(x, 0.0f));   // -0 + 0 = +0; every other x kept
+    const uint32_t k = u ^ (uint32_t(int32_t(u) >> 31) | 0x80000000u);   // monotone in x
+    return x != x ? 0u : (MAX ? k : ~k);                // NaN: below every number
   } else {
-    u = (uint32_t)x ^ 0x80000000u;                      // monotone in x
+    const uint32_t k = uint32_t(x) ^ 0x80000000u;       // monotone in x
+    return MAX ? k : ~k;
   }
-  return MAX ? u : ~u;
 }
 
 template <class T, bool MAX>
@@ -1198,37 +1197,49 @@ struct ArgKeys {
 // cp.async into the swizzled stages, a look-back warp) over tiles of two
 // 4096-point sub-tiles, for the arg-maximum / arg-minimum: point g is element
 // idx_base + g.  Two passes over the staged tile.  The first turns every
-// element into its 32-bit order code, in place, and scans the threads'
-// (code, first position of the best) aggregates into each thread's
-// in-tile start state; once the look-back prefix is known, the second walks
-// each thread's points again from its start state, one 32-bit comparison a
-// point, and leaves the inclusive indices in place for a coalesced store
-// (the exclusive form shifts them by one).  The tile state carries ArgKeys.
+// element into its 32-bit order code, in place, and reduces each thread's 16
+// points of each sub-tile to (code, first position of the best) after the
+// last segment head among them; the threads' aggregates, as 64-bit keys, are
+// scanned over the whole tile at once (warp shuffles, then every warp scans
+// the 16 warp totals itself: two barriers a tile).  Once the look-back prefix
+// is known the second pass walks each thread's points from its start state,
+// one 32-bit comparison a point, and stores the 16 indices (inclusive or
+// exclusive) straight from registers.  The tile state carries ArgKeys.
+// SUBS sub-tiles a tile; PIPE: pass 1 takes each sub-tile as it lands (one
+// barrier each, the look-back released at the first) instead of all at once;
+// MINB CTAs a SM (registers capped to fit; three for PERIODIC, whose head
+// masks would spill at four).  Measured on 2^28 FP32: two
+// pipelined sub-tiles at four CTAs a SM 0.43-0.45 ms; three CTAs 0.48,
+// five the same as four (with spills), six 0.52; four sub-tiles 0.54.
 constexpr int kArgSub = 2;
+constexpr bool kArgPipe = true;
+constexpr int kArgBlocksPerSM = 4;
 constexpr int kArgTile = kSub * kArgSub;
 constexpr int kArgSmem = kArgSub * kStageBytes;
 static_assert(kItems == 16, "a thread's points are one 16-bit head mask");
 
-template <class T, bool MAX, int MODE, bool EXCL>
-__global__ void __launch_bounds__(kThreads + 32, 3) scan_arg_kernel(const T *in, int32_t *out, ScanArgs args,
+template <class T, bool MAX, int MODE, bool EXCL, int SUBS = kArgSub, bool PIPE = kArgPipe,
+          int MINB = (MODE == PERIODIC ? 3 : kArgBlocksPerSM)>
+__global__ void __launch_bounds__(kThreads + 32, MINB) scan_arg_kernel(const T *in, int32_t *out, ScanArgs args,
                                                                     int64_t idx_base, ScanWs *ws,
                                                                     TileState *states) {
   using S = ArgKeys<T, MAX>;
   using E = typename S::E;
   using O = typename S::Op;
   using CT = typename S::C;
-  constexpr int kTile = kArgTile;
-  extern __shared__ __align__(128) unsigned char ring[];   // kArgSub stages
+  static_assert(SUBS * kWarps <= 32 && SUBS <= 4, "one lane a warp total");
+  constexpr int kTile = kSub * SUBS;
+  constexpr int kTotals = SUBS * kWarps;           // warp totals in tile order
+  extern __shared__ __align__(128) unsigned char ring[];   // SUBS stages
   __shared__ int64_t sh_tile, sh_seg0;
-  __shared__ E sh_wval[kWarps];
-  __shared__ int sh_wflag[kWarps];
-  __shared__ E sh_carry;                // in-tile state after the sub-tiles done so far
-  __shared__ int sh_carry_flag;
+  __shared__ E sh_wval[kTotals];
+  __shared__ int sh_wflag[kTotals];
+  __shared__ E sh_carry;                // the tile's aggregate
+  __shared__ int sh_carry_flag;         // a segment starts in the tile
   __shared__ CT sh_prefix;
   __shared__ int sh_ok;
-  __shared__ unsigned sh_heads[kTile / 32];              // one bit a point: a segment starts there
+  __shared__ unsigned sh_heads[MODE == CSR ? kTile / 32 : 1];   // one bit a point: a segment starts there
   __shared__ volatile int sh_go;
-  unsigned short *heads16 = reinterpret_cast<unsigned short *>(sh_heads);
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t n = args.n;
@@ -1277,7 +1288,7 @@ __global__ void __launch_bounds__(kThreads + 32, 3) scan_arg_kernel(const T *in,
 
   // ---- compute warps
 #pragma unroll
-  for (int s = 0; s < kArgSub; ++s) {
+  for (int s = 0; s < SUBS; ++s) {
     load_sub<T>(ring + s * kStageBytes, in, t0 + int64_t(s) * kSub, n, args.vec != 0, addr);
     cp_async_commit();
   }
@@ -1296,29 +1307,28 @@ __global__ void __launch_bounds__(kThreads + 32, 3) scan_arg_kernel(const T *in,
       if (b > t0) atomicOr(&sh_heads[(b - t0) >> 5], 1u << ((b - t0) & 31));
     }
   }
-  if (tid == 0) {
-    sh_carry = S::eid();
-    sh_carry_flag = 0;
-  }
   // this thread's absolute index of its first point in sub-tile 0 (below 2^30)
   const int32_t ibase = int32_t(idx_base + t0) + tid * kItems;
-  // per sub-tile: the in-tile state before the thread's points, whether a
-  // head precedes them in the tile, and the heads among them (named, not
-  // arrays, so that they stay in registers across the rolled loop)
-  static_assert(kArgSub == 2, "two sub-tiles a tile");
-  E start0 = 0, start1 = 0;
-  int sflag0 = 0, sflag1 = 0;
-  unsigned hm0 = 0u, hm1 = 0u;
+  if (!PIPE) {
+    cp_async_wait<0>();
+    compute_bar();                                      // the tile and its heads are visible
+    if (tid == 0) sh_go = 1;
+  }
 
-  // ---- pass 1: order codes in place; thread aggregates scanned over the tile
-#pragma unroll 1
-  for (int s = 0; s < kArgSub; ++s) {
+  // ---- pass 1: order codes in place; per sub-tile the thread's aggregate
+  // and its warp-exclusive prefix
+  E ex[SUBS];
+  int exf[SUBS];
+  unsigned hmq[SUBS];
+  uint32_t tmax[SUBS];                                  // the best code after the thread's last head
+#pragma unroll
+  for (int s = 0; s < SUBS; ++s) {
     unsigned char *st = ring + s * kStageBytes;
-    cp_async_wait_dyn(kArgSub - 1 - s);
-    compute_bar();                                      // sub-tile s, the heads and the carry are visible
-    if (s == 0 && tid == 0) sh_go = 1;
-    const E cv = sh_carry;
-    const int cf = sh_carry_flag;
+    if (PIPE) {
+      cp_async_wait_dyn(SUBS - 1 - s);
+      compute_bar();                                    // sub-tile s (and the heads) visible
+      if (s == 0 && tid == 0) sh_go = 1;
+    }
     const int rel0 = s * kSub + tid * kItems;
     const int64_t g0 = t0 + rel0;
     const int64_t lim64 = n - g0;
@@ -1333,12 +1343,10 @@ __global__ void __launch_bounds__(kThreads + 32, 3) scan_arg_kernel(const T *in,
         if (r == 0) hm |= 1u << i;
         if (++r == args.period) r = 0;
       }
-      heads16[rel0 >> 4] = (unsigned short)hm;
     } else {
-      hm = heads16[rel0 >> 4];
+      hm = (sh_heads[rel0 >> 5] >> (rel0 & 31)) & 0xffffu;
     }
-    if (s == 0) hm0 = hm;
-    else hm1 = hm;
+    hmq[s] = hm;
     uint32_t c[kItems];
 #pragma unroll
     for (int q = 0; q < kItems / 4; ++q) {
@@ -1350,18 +1358,16 @@ __global__ void __launch_bounds__(kThreads + 32, 3) scan_arg_kernel(const T *in,
       c[4 * q + 3] = order_code<T, MAX>(__builtin_bit_cast(T, x.w));
       *p = make_int4(int(c[4 * q]), int(c[4 * q + 1]), int(c[4 * q + 2]), int(c[4 * q + 3]));
     }
-    // the thread's aggregate: the best code after its last head, first position on ties
+    // the best code after the thread's last head, its first position on ties
     uint32_t best = 0u;
     int pos = -1;
-    if (hm == 0u && lim == kItems) {
+    if (hm == 0u && lim == kItems) {                    // the maximum, then its first position
       best = c[0];
-      pos = 0;
 #pragma unroll
-      for (int i = 1; i < kItems; ++i)
-        if (c[i] > best) {
-          best = c[i];
-          pos = i;
-        }
+      for (int i = 1; i < kItems; ++i) best = max(best, c[i]);
+      pos = kItems - 1;
+#pragma unroll
+      for (int i = kItems - 2; i >= 0; --i) pos = c[i] == best ? i : pos;
     } else {
 #pragma unroll
       for (int i = 0; i < kItems; ++i)
@@ -1370,6 +1376,7 @@ __global__ void __launch_bounds__(kThreads + 32, 3) scan_arg_kernel(const T *in,
           pos = i;
         }
     }
+    tmax[s] = best;
     E a = pos < 0 ? S::eid() : ((E)best << 32) | (uint32_t)~(uint32_t)(ibase + s * kSub + pos);
     int f = hm != 0u;
 #pragma unroll
@@ -1382,140 +1389,160 @@ __global__ void __launch_bounds__(kThreads + 32, 3) scan_arg_kernel(const T *in,
       }
     }
     if (lane == 31) {
-      sh_wval[warp] = a;
-      sh_wflag[warp] = f;
+      sh_wval[s * kWarps + warp] = a;
+      sh_wflag[s * kWarps + warp] = f;
     }
-    E ex = S::shfl_up(a, 1);
-    int exf = __shfl_up_sync(0xffffffffu, f, 1);
+    ex[s] = S::shfl_up(a, 1);
+    exf[s] = __shfl_up_sync(0xffffffffu, f, 1);
     if (lane == 0) {
-      ex = S::eid();
-      exf = 0;
-    }
-    compute_bar();
-    if (warp == 0) {                                    // scan of the warp totals
-      E wa = lane < kWarps ? sh_wval[lane] : S::eid();
-      int wf = lane < kWarps ? sh_wflag[lane] : 0;
-#pragma unroll
-      for (int off = 1; off < kWarps; off <<= 1) {
-        const E au = S::shfl_up(wa, off);
-        const int fu = __shfl_up_sync(0xffffffffu, wf, off);
-        if (lane >= off) {
-          if (!wf) wa = S::ecomb(au, wa);
-          wf |= fu;
-        }
-      }
-      E we = S::shfl_up(wa, 1);
-      int wfe = __shfl_up_sync(0xffffffffu, wf, 1);
-      if (lane == 0) {
-        we = S::eid();
-        wfe = 0;
-      }
-      const E sub_val = S::shfl(wa, kWarps - 1);
-      const int sub_flag = __shfl_sync(0xffffffffu, wf, kWarps - 1);
-      __syncwarp();
-      if (lane < kWarps) {
-        sh_wval[lane] = we;
-        sh_wflag[lane] = wfe;
-      }
-      if (lane == 0) {                                  // the state after this sub-tile
-        sh_carry = sub_flag ? sub_val : S::ecomb(cv, sub_val);
-        sh_carry_flag = cf | sub_flag;
-      }
-    }
-    compute_bar();
-    const E pv = sh_wval[warp];
-    const int pf = sh_wflag[warp];
-    if (!exf) ex = S::ecomb(pv, ex);
-    exf |= pf;                                          // (pf, pv) then (exf, ex)
-    const E st_in = exf ? ex : S::ecomb(cv, ex);
-    if (s == 0) {
-      start0 = st_in;
-      sflag0 = exf | cf;
-    } else {
-      start1 = st_in;
-      sflag1 = exf | cf;
+      ex[s] = S::eid();
+      exf[s] = 0;
     }
   }
   compute_bar();
-  if (tid == 0 && !stall)
-    publish<O>(&states[tile], (tile == 0 || sh_carry_flag) ? kStatIncl : kStatAgg, S::carry(sh_carry));
+  // every warp scans the warp totals of the whole tile (sub-tile 0's warps, then sub-tile 1's)
+  E wa = lane < kTotals ? sh_wval[lane] : S::eid();
+  int wf = lane < kTotals ? sh_wflag[lane] : 0;
+#pragma unroll
+  for (int off = 1; off < kTotals; off <<= 1) {
+    const E au = S::shfl_up(wa, off);
+    const int fu = __shfl_up_sync(0xffffffffu, wf, off);
+    if (lane >= off) {
+      if (!wf) wa = S::ecomb(au, wa);
+      wf |= fu;
+    }
+  }
+  const E tot = S::shfl(wa, kTotals - 1);
+  const int totf = __shfl_sync(0xffffffffu, wf, kTotals - 1);
+  E we = S::shfl_up(wa, 1);
+  int wfe = __shfl_up_sync(0xffffffffu, wf, 1);
+  if (lane == 0) {
+    we = S::eid();
+    wfe = 0;
+  }
+  E start[SUBS];                                     // in-tile state before the thread's points
+  int sflag[SUBS];                                   // a head precedes them in the tile
+#pragma unroll
+  for (int s = 0; s < SUBS; ++s) {
+    const E pv = S::shfl(we, s * kWarps + warp);
+    const int pf = __shfl_sync(0xffffffffu, wfe, s * kWarps + warp);
+    start[s] = exf[s] ? ex[s] : S::ecomb(pv, ex[s]);    // (pf, pv) then (exf, ex)
+    sflag[s] = exf[s] | pf;
+  }
+  if (tid == 0) {
+    if (!stall) publish<O>(&states[tile], (tile == 0 || totf) ? kStatIncl : kStatAgg, S::carry(tot));
+    sh_carry = tot;
+    sh_carry_flag = totf;
+  }
   __syncthreads();                                      // (S) with the look-back warp
   if (!sh_ok) return;
   const E pre = sh_prefix.k;
 
-  // ---- pass 2: each thread's points from its start state; inclusive indices in place
+  // ---- pass 2: each thread's points from its start state.  Where a CSR
+  // call wants its segment totals, the inclusive indices stay in the stage
+  // and each thread stores its 16 results itself; otherwise the results take
+  // the place of the thread's codes and each warp stores its 512 points as
+  // whole rows.
+  const bool keep_incl = MODE == CSR && args.sums != nullptr;
 #pragma unroll
-  for (int s = 0; s < kArgSub; ++s) {
+  for (int s = 0; s < SUBS; ++s) {
     unsigned char *st = ring + s * kStageBytes;
-    const E e0 = (s == 0 ? sflag0 : sflag1) ? (s == 0 ? start0 : start1) : S::ecomb(pre, s == 0 ? start0 : start1);
+    const E e0 = sflag[s] ? start[s] : S::ecomb(pre, start[s]);
     uint32_t best = uint32_t(e0 >> 32);
     int32_t idx = int32_t(~uint32_t(e0));               // "no element": code 0, index -1
     const int32_t ib = ibase + s * kSub;
-    const unsigned hm = s == 0 ? hm0 : hm1;
-    const int64_t lim64 = n - (t0 + s * kSub + tid * kItems);
-    const bool full = hm == 0u && lim64 >= kItems;
+    const unsigned hm = hmq[s];
+    const int64_t g0 = t0 + s * kSub + tid * kItems;
+    const int64_t lim64 = n - g0;
+    const bool full = lim64 >= kItems;
+    int32_t r[kItems];
+    auto chunk = [&](int q) { return reinterpret_cast<int4 *>(st + chunk_off((kItems / 4) * tid + q)); };
+    if (hm == 0u && full && idx >= 0 && best >= tmax[s]) {
+      // the start state beats every point (on a tie it comes first)
 #pragma unroll
-    for (int q = 0; q < kItems / 4; ++q) {
-      int4 *p = reinterpret_cast<int4 *>(st + chunk_off((kItems / 4) * tid + q));
-      const int4 x = *p;
-      const uint32_t cs[4] = {uint32_t(x.x), uint32_t(x.y), uint32_t(x.z), uint32_t(x.w)};
-      int32_t r[4];
+      for (int i = 0; i < kItems; ++i) r[i] = idx;
+      if (keep_incl)
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const int i = 4 * q + c;
-        if (full) {
-          if (cs[c] > best) {
+        for (int q = 0; q < kItems / 4; ++q) *chunk(q) = make_int4(idx, idx, idx, idx);
+    } else if (hm == 0u && full) {
+#pragma unroll
+      for (int q = 0; q < kItems / 4; ++q) {
+        const int4 x = *chunk(q);
+        const uint32_t cs[4] = {uint32_t(x.x), uint32_t(x.y), uint32_t(x.z), uint32_t(x.w)};
+        int32_t in4[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const int i = 4 * q + c;
+          if (EXCL) r[i] = idx;
+          const bool gt = cs[c] > best;
+          best = gt ? cs[c] : best;
+          idx = gt ? ib + i : idx;
+          if (!EXCL) r[i] = idx;
+          in4[c] = idx;
+        }
+        if (keep_incl) *chunk(q) = make_int4(in4[0], in4[1], in4[2], in4[3]);
+      }
+    } else {                                            // heads among the points, or the array's end
+#pragma unroll
+      for (int q = 0; q < kItems / 4; ++q) {
+        int4 *p = chunk(q);
+        const int4 x = *p;
+        const uint32_t cs[4] = {uint32_t(x.x), uint32_t(x.y), uint32_t(x.z), uint32_t(x.w)};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const int i = 4 * q + c;
+          const bool head = (hm >> i) & 1u;
+          if (EXCL) r[i] = head ? -1 : idx;
+          if (i < lim64 && (head || idx < 0 || cs[c] > best)) {
             best = cs[c];
             idx = ib + i;
           }
-        } else if (i < lim64 && (((hm >> i) & 1u) || idx < 0 || cs[c] > best)) {
-          best = cs[c];
-          idx = ib + i;
+          if (!EXCL) r[i] = idx;
+          if (keep_incl) reinterpret_cast<int32_t *>(p)[c] = idx;   // inclusive, for the totals
         }
-        r[c] = idx;
       }
-      *p = make_int4(r[0], r[1], r[2], r[3]);
     }
-  }
-  compute_bar();                                        // every point's inclusive index is in place
-
-  auto incl_at = [&](int r) -> int32_t {
-    return reinterpret_cast<const int32_t *>(ring + (r / kSub) * kStageBytes + chunk_off((r % kSub) / 4))[r % 4];
-  };
-  auto head_at = [&](int r) -> bool {
-    if (MODE == PLAIN) return t0 + r == 0;
-    return (sh_heads[r >> 5] >> (r & 31)) & 1u;
-  };
-  const int32_t pre_idx = pre ? int32_t(~uint32_t(pre)) : -1;
-#pragma unroll 1
-  for (int j = tid; j < kTile / 4; j += kThreads) {
-    const int64_t g = t0 + 4 * int64_t(j);
-    if (g >= n) break;
-    const int4 x = *reinterpret_cast<const int4 *>(ring + (j / (kSub / 4)) * kStageBytes + chunk_off(j % (kSub / 4)));
-    int32_t w[4] = {x.x, x.y, x.z, x.w};
-    if (EXCL) {
-      const int r = 4 * j;
-      const int32_t before = r == 0 ? pre_idx : incl_at(r - 1);
-      w[3] = head_at(r + 3) ? -1 : w[2];
-      w[2] = head_at(r + 2) ? -1 : w[1];
-      w[1] = head_at(r + 1) ? -1 : w[0];
-      w[0] = head_at(r) ? -1 : before;
-    }
-    if (args.vec && g + 4 <= n) {
-      __stcs(reinterpret_cast<int4 *>(out + g), make_int4(w[0], w[1], w[2], w[3]));
+    if (keep_incl) {
+      int32_t *o = out + g0;
+      if (args.vec && full) {
+#pragma unroll
+        for (int q = 0; q < kItems / 4; ++q)
+          __stcs(reinterpret_cast<int4 *>(o) + q, make_int4(r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]));
+      } else {
+#pragma unroll
+        for (int i = 0; i < kItems; ++i)
+          if (i < lim64) o[i] = r[i];
+      }
     } else {
 #pragma unroll
-      for (int c = 0; c < 4; ++c)
-        if (g + c < n) out[g + c] = w[c];
+      for (int q = 0; q < kItems / 4; ++q) *chunk(q) = make_int4(r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
+      __syncwarp();                                     // the warp's 512 results are in its own slots
+#pragma unroll
+      for (int q = 0; q < kItems / 4; ++q) {
+        const int j = (kItems / 4) * 32 * warp + 32 * q + lane;   // chunk of the sub-tile
+        const int4 v = *reinterpret_cast<const int4 *>(st + chunk_off(j));
+        const int64_t g = t0 + s * kSub + 4 * int64_t(j);
+        if (args.vec && g + 4 <= n) {
+          __stcs(reinterpret_cast<int4 *>(out + g), v);
+        } else {
+          const int32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+          for (int c = 0; c < 4; ++c)
+            if (g + c < n) out[g + c] = w[c];
+        }
+      }
     }
   }
   if (MODE == CSR && args.sums) {                       // totals of the non-empty segments ending here
+    compute_bar();
     int32_t *sums = static_cast<int32_t *>(args.sums);
     for (int64_t q = sh_seg0 + 1 + tid; q <= args.nseg; q += kThreads) {
       const int64_t b = args.offsets[q];
       if (b > tend) break;
       if (b <= t0 || args.offsets[q - 1] == b) continue;
-      sums[q - 1] = incl_at(int(b - 1 - t0));
+      const int rr = int(b - 1 - t0);
+      sums[q - 1] = reinterpret_cast<const int32_t *>(ring + (rr / kSub) * kStageBytes +
+                                                      chunk_off((rr % kSub) / 4))[rr % 4];
     }
   }
 }
