@@ -66,10 +66,11 @@ bool same_map_quick(const desc_lowered &a, const desc_lowered &b);
 int32_t check_device_ptr(const void *p, size_t align);
 
 // Device status words of the translation units that hold bounded waits
-// (scan_status_take reads the four scan units' words).
+// (scan_status_take reads the five scan units' words).
 int32_t scan_status_take();          // k_scan.cu
 int32_t scan_status_take_ops();      // k_scan_ops.cu
 int32_t scan_status_take_mapped();   // k_scan_mapped.cu
+int32_t scan_status_take_mapped2();  // k_scan_mapped2.cu
 int32_t scan_status_take_map();      // k_scan_map.cu
 int32_t mm_status_take();            // k_mm_tc.cu
 
@@ -146,10 +147,14 @@ int32_t launch_scan_map(int32_t dtype, const void *in, void *out, int64_t off, c
                         void *sums, int32_t flags, void *ws, size_t ws_bytes, desc_stream_t s);
 // The look-back scan with 4 x 4096-point tiles through a lowered map (as
 // launch_scan_map, no CSR): every value operator, inclusive or exclusive;
-// maps of more than two canonical dims go to launch_scan_map.
+// maps of more than two canonical dims go to launch_scan_map.  Maps of two
+// dims are launched by launch_scan_mapped_2d (its own translation unit).
 int32_t launch_scan_mapped(int32_t dtype, const void *in, void *out, int64_t off, const int64_t *ext,
                            const int64_t *stride, int nd, int64_t period, int32_t flags, void *ws, size_t ws_bytes,
                            desc_stream_t s);
+int32_t launch_scan_mapped_2d(int32_t dtype, const void *in, void *out, int64_t off, const int64_t *ext,
+                              const int64_t *stride, int nd, int64_t period, int32_t flags, void *ws,
+                              size_t ws_bytes, desc_stream_t s);
 
 // Copy over a common logical domain of `nd` dims: out[ostride . p] = in[istride . p].
 int32_t launch_copy_affine(const void *in, int64_t ioff, const int64_t *istride, void *out,

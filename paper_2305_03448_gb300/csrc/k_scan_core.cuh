@@ -238,14 +238,23 @@ struct RunAddr {
   const MapArgs &m;                                     // not used
   __device__ int64_t operator()(int64_t g) const { return g; }
 };
-// The look-back scan takes maps of at most two dims with 32-bit decoding
-// (launch_scan_mapped checks), decoded inline.
+// The look-back scan takes maps of one or two dims, the count fixed at
+// compile time (a run-time test of it cost 7 % of the scan), decoded inline
+// (launch_scan_mapped checks the ranges):
+//   ND = 1: off + g * st[0], as one 32 x 32 -> 64-bit product (g < 2^31,
+//           |st[0]| < 2^31);
+//   ND = 2: g split by the inner extent with a 32-bit multiply-high division
+//           (fewer than 2^32 points).
+template <int ND>
 struct MapAddr {
   const MapArgs &m;
   __device__ int64_t operator()(int64_t g) const {
-    if (m.nd < 2) return m.off + (m.nd ? g * m.st[0] : g);
-    const uint32_t t = (uint32_t)g, q = fast_div(t, m.div[1]);
-    return m.off + int64_t(q) * m.st[0] + int64_t(t - q * m.div[1].d) * m.st[1];
+    if constexpr (ND == 1) {
+      return m.off + int64_t(int32_t(g)) * int64_t(int32_t(m.st[0]));
+    } else {
+      const uint32_t t = (uint32_t)g, q = fast_div(t, m.div[1]);
+      return m.off + int64_t(q) * m.st[0] + int64_t(t - q * m.div[1].d) * m.st[1];
+    }
   }
 };
 
@@ -422,10 +431,11 @@ __device__ __forceinline__ int64_t find_segment(const int64_t *offsets, int64_t 
 // of a tile does not depend on its data) and publishes the inclusive prefix
 // once it has both.  The carry is added during the coalesced store pass, to
 // the elements that have no segment start before them in the tile.
-// MAPPED: points are addressed through the lowered map m (in and out are
-// then the base arrays; vec means four consecutive points from a multiple of
-// 4 are four consecutive elements on a 16-byte boundary).
-template <class T, class O, int MODE, int SUB, bool EXCL, bool MAPPED>
+// MAPPED (the map's dims, 1 or 2; 0: a contiguous run): points are addressed
+// through the lowered map m (in and out are then the base arrays; vec means
+// four consecutive points from a multiple of 4 are four consecutive elements
+// on a 16-byte boundary).
+template <class T, class O, int MODE, int SUB, bool EXCL, int MAPPED>
 __global__ void __launch_bounds__(kThreads + 32, 3) scan_kernel(const T *in, T *out, ScanArgs args,
                                                              ScanWs *ws, TileState *states,
                                                              const __grid_constant__ MapArgs m) {
@@ -449,7 +459,7 @@ __global__ void __launch_bounds__(kThreads + 32, 3) scan_kernel(const T *in, T *
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t n = args.n;
   const bool vec = args.vec != 0;
-  using Addr = typename std::conditional<MAPPED, MapAddr, RunAddr>::type;
+  using Addr = typename std::conditional<MAPPED == 0, RunAddr, MapAddr<MAPPED == 2 ? 2 : 1>>::type;
   const Addr addr{m};
   if (tid == 0) {
     sh_tile = atomicAdd(&ws->ticket, 1u);
@@ -1555,7 +1565,7 @@ constexpr int kWsTile = kSub;   // workspace is sized for the smallest tile
 static_assert(kSub == kScanSubTile, "the candidate table counts sub-tiles of this size");
 static_assert(kSub * kScanSubCands[0] == kScanNoallocTile, "the no-alloc scan runs candidate 0");
 
-template <class T, class O, int MODE, int SUB, bool EXCL, bool MAPPED>
+template <class T, class O, int MODE, int SUB, bool EXCL, int MAPPED>
 int32_t run_scan_t(const T *in, T *out, const ScanArgs &a, void *ws, size_t ws_bytes, cudaStream_t s,
                    const MapArgs &m) {
   constexpr int kTile = kSub * SUB;
@@ -1584,7 +1594,7 @@ int32_t run_scan_t(const T *in, T *out, const ScanArgs &a, void *ws, size_t ws_b
 
 // The sum (every schedule candidate when inclusive and read directly, the
 // default tile otherwise), the maximum and the minimum.
-template <class T, int MODE, bool MAPPED>
+template <class T, int MODE, int MAPPED>
 int32_t run_scan_basic(const T *in, T *out, const ScanArgs &a, void *ws, size_t ws_bytes, cudaStream_t s, int cand,
                        int32_t flags, const MapArgs &m) {
   const bool ex = (flags & DESC_EXCLUSIVE) != 0;
@@ -1612,7 +1622,7 @@ int32_t run_scan_basic(const T *in, T *out, const ScanArgs &a, void *ws, size_t 
 }
 
 // The product (int32 and FP32) and the bitwise operators (int32), default tile.
-template <class T, int MODE, bool MAPPED>
+template <class T, int MODE, int MAPPED>
 int32_t run_scan_ops(const T *in, T *out, const ScanArgs &a, void *ws, size_t ws_bytes, cudaStream_t s,
                      int32_t flags, const MapArgs &m) {
   const bool ex = (flags & DESC_EXCLUSIVE) != 0;
@@ -1796,6 +1806,31 @@ bool map_vec(const MapArgs &m, const void *in, const void *out) {
   return vec;
 }
 
+
+// The look-back scan through a map of ND (1 or 2) canonical dims: every
+// value operator, plain or per-level segments.
+template <int ND>
+int32_t run_scan_mapped_nd(int32_t dtype, const void *in, void *out, const MapArgs &m, int64_t n, int64_t period,
+                           int32_t flags, void *ws, size_t ws_bytes, cudaStream_t s) {
+  ScanArgs a{};
+  a.n = n;
+  a.period = period > 0 ? period : n;
+  a.debug = (flags & DESC_DEBUG_STALL_TILE) ? 1 : 0;
+  a.vec = map_vec(m, in, out) ? 1 : 0;
+  const bool periodic = a.period < n;
+  const bool basic = !(flags & (DESC_PROD | DESC_AND | DESC_OR | DESC_XOR));
+  auto go = [&](auto tag) -> int32_t {
+    using T = decltype(tag);
+    auto i = static_cast<const T *>(in);
+    auto o = static_cast<T *>(out);
+    if (basic)
+      return periodic ? run_scan_basic<T, PERIODIC, ND>(i, o, a, ws, ws_bytes, s, -1, flags, m)
+                      : run_scan_basic<T, PLAIN, ND>(i, o, a, ws, ws_bytes, s, -1, flags, m);
+    return periodic ? run_scan_ops<T, PERIODIC, ND>(i, o, a, ws, ws_bytes, s, flags, m)
+                    : run_scan_ops<T, PLAIN, ND>(i, o, a, ws, ws_bytes, s, flags, m);
+  };
+  return dtype == DESC_I32 ? go(int32_t(0)) : go(0.f);
+}
 
 // Reads and clears this translation unit's device status word.
 int32_t take_status_word() {

@@ -1,6 +1,7 @@
 // Scans of views whose lowered map is not one contiguous run, through the
-// look-back scan of k_scan_core.cuh with every address taken from the map
-// (maps of up to two canonical dims; others go to the one-tile map scan).
+// look-back scan of k_scan_core.cuh with every address taken from the map:
+// maps of one canonical dim here, two in k_scan_mapped2.cu, others in the
+// one-tile map scan.
 #include "k_scan_core.cuh"
 
 namespace desc {
@@ -15,27 +16,18 @@ int32_t launch_scan_mapped(int32_t dtype, const void *in, void *out, int64_t off
   MapArgs m;
   const int64_t n = build_map(off, ext, stride, nd, period, &m);
   if (n == 0) return DESC_OK;
-  if (m.nd > 2 || !m.fast)                             // the one-tile map scan decodes any map
+  if (m.nd == 2 && m.fast)
+    return launch_scan_mapped_2d(dtype, in, out, off, ext, stride, nd, period, flags, ws, ws_bytes, st);
+  if (m.nd == 0) {                                     // off + g
+    m.nd = 1;
+    m.ext[0] = n;
+    m.st[0] = 1;
+  }
+  const int64_t lim = int64_t(1) << 31;
+  if (m.nd != 1 || n >= lim || m.st[0] >= lim || m.st[0] <= -lim)   // the one-tile map scan decodes any map
     return launch_scan_map(dtype, in, out, off, ext, stride, nd, period, nullptr, 0, nullptr, flags, ws, ws_bytes,
                            st);
-  ScanArgs a{};
-  a.n = n;
-  a.period = period > 0 ? period : n;
-  a.debug = (flags & DESC_DEBUG_STALL_TILE) ? 1 : 0;
-  a.vec = map_vec(m, in, out) ? 1 : 0;
-  const bool periodic = a.period < n;
-  const bool basic = !(flags & (DESC_PROD | DESC_AND | DESC_OR | DESC_XOR));
-  auto go = [&](auto tag) -> int32_t {
-    using T = decltype(tag);
-    auto i = static_cast<const T *>(in);
-    auto o = static_cast<T *>(out);
-    if (basic)
-      return periodic ? run_scan_basic<T, PERIODIC, true>(i, o, a, ws, ws_bytes, s, -1, flags, m)
-                      : run_scan_basic<T, PLAIN, true>(i, o, a, ws, ws_bytes, s, -1, flags, m);
-    return periodic ? run_scan_ops<T, PERIODIC, true>(i, o, a, ws, ws_bytes, s, flags, m)
-                    : run_scan_ops<T, PLAIN, true>(i, o, a, ws, ws_bytes, s, flags, m);
-  };
-  return dtype == DESC_I32 ? go(int32_t(0)) : go(0.f);
+  return run_scan_mapped_nd<1>(dtype, in, out, m, n, period, flags, ws, ws_bytes, s);
 }
 
 }  // namespace desc
