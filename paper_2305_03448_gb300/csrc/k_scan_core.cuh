@@ -605,9 +605,14 @@ __global__ void __launch_bounds__(kThreads + 32, 3) scan_kernel(const T *in, T *
       v[4 * q + 2] = __builtin_bit_cast(T, x.z);
       v[4 * q + 3] = __builtin_bit_cast(T, x.w);
     }
+    if (MODE == PLAIN || hmask == 0u) {                 // no head among the thread's points
 #pragma unroll
-    for (int i = 1; i < kItems; ++i)
-      if (!((hmask >> i) & 1u)) v[i] = O::comb(v[i - 1], v[i]);
+      for (int i = 1; i < kItems; ++i) v[i] = O::comb(v[i - 1], v[i]);
+    } else {
+#pragma unroll
+      for (int i = 1; i < kItems; ++i)
+        if (!((hmask >> i) & 1u)) v[i] = O::comb(v[i - 1], v[i]);
+    }
     int f = hmask != 0u;
     T a = v[kItems - 1];
 #pragma unroll
@@ -663,11 +668,17 @@ __global__ void __launch_bounds__(kThreads + 32, 3) scan_kernel(const T *in, T *
     const T in_tile = exf ? ex : O::comb(cv, ex);
     const int in_flag = exf | cf;
     unsigned need = 0u;                                 // elements with no head before them
+    if (MODE == PLAIN || hmask == 0u) {
 #pragma unroll
-    for (int i = 0; i < kItems; ++i) {
-      if ((hmask & ((2u << i) - 1u)) == 0u) {           // before this thread's first head
-        v[i] = O::comb(in_tile, v[i]);
-        if (!in_flag) need |= 1u << i;
+      for (int i = 0; i < kItems; ++i) v[i] = O::comb(in_tile, v[i]);
+      need = in_flag ? 0u : 0xffffu;
+    } else {
+#pragma unroll
+      for (int i = 0; i < kItems; ++i) {
+        if ((hmask & ((2u << i) - 1u)) == 0u) {         // before this thread's first head
+          v[i] = O::comb(in_tile, v[i]);
+          if (!in_flag) need |= 1u << i;
+        }
       }
     }
     if (MODE != PLAIN) sh_need[s * kThreads + tid] = (unsigned short)need;
@@ -691,8 +702,10 @@ __global__ void __launch_bounds__(kThreads + 32, 3) scan_kernel(const T *in, T *
   if (!sh_ok) return;                                   // a wait gave up: write nothing
 
   // ---- coalesced stores, adding the tile carry where needed (the exclusive
-  // form, chosen once per launch, shifts each segment by one)
+  // form, chosen once per launch, shifts each segment by one); a tile with
+  // no segment head takes the carry on every element
   const CT pre = sh_prefix;
+  const bool no_heads = MODE == PLAIN || !sh_carry_flag;
 #pragma unroll 1
   for (int s = 0; s < SUB; ++s) {
     const unsigned char *st = ring + s * kStageBytes;
@@ -701,7 +714,7 @@ __global__ void __launch_bounds__(kThreads + 32, 3) scan_kernel(const T *in, T *
       const int j = q * kThreads + tid;
       const int64_t g = t0 + int64_t(s) * kSub + 4 * int64_t(j);
       int4 x = *reinterpret_cast<const int4 *>(st + chunk_off(j));
-      const unsigned nb = MODE == PLAIN ? 0xfu : (unsigned(sh_need[s * kThreads + (j >> 2)]) >> ((j & 3) * 4)) & 0xfu;
+      const unsigned nb = no_heads ? 0xfu : (unsigned(sh_need[s * kThreads + (j >> 2)]) >> ((j & 3) * 4)) & 0xfu;
       T y[4] = {__builtin_bit_cast(T, x.x), __builtin_bit_cast(T, x.y), __builtin_bit_cast(T, x.z),
                 __builtin_bit_cast(T, x.w)};
 #pragma unroll
@@ -716,7 +729,7 @@ __global__ void __launch_bounds__(kThreads + 32, 3) scan_kernel(const T *in, T *
           } else {                                      // from the staged tile
             const int r = rel0 - 1, sb = r / kSub, r2 = r % kSub;
             const T v = reinterpret_cast<const T *>(ring + sb * kStageBytes + chunk_off(r2 / 4))[r2 % 4];
-            const bool nd = MODE == PLAIN || ((sh_need[sb * kThreads + r2 / kItems] >> (r2 % kItems)) & 1u);
+            const bool nd = no_heads || ((sh_need[sb * kThreads + r2 / kItems] >> (r2 % kItems)) & 1u);
             prev = nd ? O::apply(v, pre) : v;
           }
         }
