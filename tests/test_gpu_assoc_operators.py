@@ -237,3 +237,43 @@ def test_large_sampled():
     for v, c in zip(vals.tolist(), cnt.tolist()):
         acc = (acc * pow(int(v) & 0xFFFFFFFF, int(c), 1 << 32)) & 0xFFFFFFFF
     assert (int(got) & 0xFFFFFFFF) == acc
+
+
+@pytest.mark.parametrize("n", [5, 8191, 3 * 8192 + 5, 200_003])
+def test_arg_scan_closed_forms(n):
+    """Monotone inputs, where every point beats (or never beats) its prefix:
+    the running arg-maximum of an increasing array is p and its arg-minimum 0;
+    of a decreasing array the reverse.  Arrays of INT_MIN or INT_MAX (order
+    code 0 under arg-maximum or arg-minimum) keep element 0 throughout; the
+    exclusive form is -1 at 0 and the inclusive value shifted by one."""
+    p = np.arange(n, dtype=np.int64)
+    up = torch.arange(n, dtype=torch.int32)
+    down = torch.flip(up, [0]).contiguous()
+    upf = up.to(torch.float32) - n / 2.0                     # exact in FP32 for these n
+    cases = [(up, D.ARGMAX, p), (up, D.ARGMIN, 0 * p), (down, D.ARGMAX, 0 * p), (down, D.ARGMIN, p),
+             (upf, D.ARGMAX, p), (-upf, D.ARGMIN, p)]
+    for v in (-2 ** 31, 2 ** 31 - 1):
+        c = torch.full((n,), v, dtype=torch.int32)
+        cases += [(c, D.ARGMAX, 0 * p), (c, D.ARGMIN, 0 * p)]
+    for x, flags, want in cases:
+        got = D.desc_scan(x.cuda(), [n], [], V.GRID, flags=flags).cpu().numpy()
+        assert np.array_equal(got.astype(np.int64), want), (x[:3], flags)
+        ex = D.desc_scan(x.cuda(), [n], [], V.GRID, flags=flags | D.EXCLUSIVE).cpu().numpy()
+        assert ex[0] == -1 and np.array_equal(ex[1:].astype(np.int64), want[:-1])
+
+
+@pytest.mark.parametrize("op", ["argmax", "argmin"])
+def test_arg_scan_unaligned_buffers(op):
+    """Input and output that start 4 bytes past a 16-byte boundary take the
+    scan's single-element loads and stores; the result is the oracle's."""
+    n = 3 * 8192 + 7
+    for dtype in ("i32", "f32"):
+        x = data(op, dtype, n + 1, 31)
+        xd = x.cuda()[1:]
+        out = torch.zeros(n + 1, dtype=torch.int32, device="cuda")[1:]
+        assert xd.data_ptr() % 16 and out.data_ptr() % 16
+        for excl in (False, True):
+            flags = FLAG[op] | (D.EXCLUSIVE if excl else 0)
+            got = D.desc_scan(xd, [n], [], V.GRID, out=out, flags=flags).cpu().numpy()
+            want, _ = O.scan_op(x[1:].numpy(), np.zeros(n, np.int32), [n], [], V.GRID, op, excl)
+            assert np.array_equal(got.astype(np.int64), np.asarray(want).astype(np.int64))
