@@ -266,7 +266,37 @@ struct ScanArgs {
   void *sums;              // CSR: per-segment totals (may be null)
   int32_t debug;           // 1: tile 1 never publishes (tests the timeout path)
   int32_t vec;             // in and out are 16-byte aligned: 128-bit accesses
+  FastDiv pdiv;            // PERIODIC: the period, where it is below 2^30 (set by with_period)
 };
+
+// The launch arguments with the period's divisor filled in.
+inline ScanArgs with_period(ScanArgs a) {
+  if (a.period > 0 && a.period < (int64_t(1) << 30)) a.pdiv = make_fastdiv(uint32_t(a.period));
+  return a;
+}
+
+// PERIODIC: the position in its segment of the point `off` (0 <= off < TILE)
+// past a tile start whose own position is r0 (0 <= r0 < period): one
+// conditional subtraction where segments are at least a tile long, else a
+// 32-bit multiply-high division (the operand is below period + TILE).
+template <int TILE>
+__device__ __forceinline__ int64_t seg_pos(int64_t r0, int off, const ScanArgs &a) {
+  if (a.period >= TILE) {
+    const int64_t x = r0 + off;
+    return x >= a.period ? x - a.period : x;
+  }
+  const uint32_t x = uint32_t(r0) + uint32_t(off);
+  return int64_t(x - fast_div(x, a.pdiv) * a.pdiv.d);
+}
+
+// Bit i (i < COUNT) set where point i of a run starting at position pos
+// (0 <= pos < period) of its segment is a segment head.
+template <int COUNT>
+__device__ __forceinline__ unsigned seg_heads(int64_t pos, int64_t period) {
+  unsigned hm = 0u;
+  for (int64_t i = pos == 0 ? 0 : period - pos; i < COUNT; i += period) hm |= 1u << i;
+  return hm;
+}
 
 // Looks back from tile `tile` (one warp).  Each poll reads a window of
 // 32 x kSlots tile states (lane l takes kSlots consecutive ones); everything
@@ -452,6 +482,7 @@ __global__ void __launch_bounds__(kThreads + 32, 3) scan_kernel(const T *in, T *
   __shared__ unsigned sh_heads[MODE == CSR ? kTile / 32 : 1];
   __shared__ unsigned short sh_need[MODE == PLAIN ? 1 : SUB * kThreads];  // carry-needed bits
   __shared__ int64_t sh_seg0;
+  __shared__ int64_t sh_r0;             // PERIODIC: t0's position in its segment
   __shared__ int sh_any_end;            // CSR: a non-empty segment ends in this tile
   __shared__ int sh_dense;              // CSR: more boundaries than one warp-wide read covers
   __shared__ volatile int sh_go;        // look-back may start polling
@@ -553,6 +584,7 @@ __global__ void __launch_bounds__(kThreads + 32, 3) scan_kernel(const T *in, T *
   if (tid == 0) {
     sh_carry = O::id();
     sh_carry_flag = 0;
+    if (MODE == PERIODIC) sh_r0 = t0 % args.period;   // one 64-bit division a tile
   }
 
 #pragma unroll 1
@@ -586,12 +618,7 @@ __global__ void __launch_bounds__(kThreads + 32, 3) scan_kernel(const T *in, T *
     const int64_t g0 = t0 + int64_t(s) * kSub + int64_t(tid) * kItems;
     unsigned hmask = 0u;
     if (MODE == PERIODIC) {
-      int64_t r = g0 % args.period;
-#pragma unroll
-      for (int i = 0; i < kItems; ++i) {
-        if (r == 0) hmask |= 1u << i;
-        if (++r == args.period) r = 0;
-      }
+      hmask = seg_heads<kItems>(seg_pos<kTile>(sh_r0, s * kSub + tid * kItems, args), args.period);
     } else if (MODE == CSR) {
       const int rel0 = s * kSub + tid * kItems;
       hmask = (sh_heads[rel0 >> 5] >> (rel0 & 31)) & 0xffffu;
@@ -734,11 +761,12 @@ __global__ void __launch_bounds__(kThreads + 32, 3) scan_kernel(const T *in, T *
           }
         }
         T e[4];
+        const unsigned ph = MODE == PERIODIC ? seg_heads<4>(seg_pos<kTile>(sh_r0, rel0, args), args.period) : 0u;
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
           bool head;
           if (MODE == PLAIN) head = g + c == 0;
-          else if (MODE == PERIODIC) head = (g + c) % args.period == 0;
+          else if (MODE == PERIODIC) head = (ph >> c) & 1u;
           else head = (sh_heads[(rel0 + c) >> 5] >> ((rel0 + c) & 31)) & 1u;
           e[c] = head ? O::id() : (c == 0 ? prev : y[c - 1]);
         }
@@ -1263,6 +1291,7 @@ __global__ void __launch_bounds__(kThreads + 32, MINB) scan_arg_kernel(const T *
   __shared__ int sh_ok;
   __shared__ unsigned sh_heads[MODE == CSR ? kTile / 32 : 1];   // one bit a point: a segment starts there
   __shared__ volatile int sh_go;
+  __shared__ int64_t sh_r0;             // PERIODIC: t0's position in its segment
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t n = args.n;
@@ -1332,6 +1361,7 @@ __global__ void __launch_bounds__(kThreads + 32, MINB) scan_arg_kernel(const T *
   }
   // this thread's absolute index of its first point in sub-tile 0 (below 2^30)
   const int32_t ibase = int32_t(idx_base + t0) + tid * kItems;
+  if (MODE == PERIODIC && tid == 0) sh_r0 = t0 % args.period;   // one 64-bit division a tile
   if (!PIPE) {
     cp_async_wait<0>();
     compute_bar();                                      // the tile and its heads are visible
@@ -1360,12 +1390,7 @@ __global__ void __launch_bounds__(kThreads + 32, MINB) scan_arg_kernel(const T *
     if (MODE == PLAIN) {
       hm = g0 == 0 ? 1u : 0u;
     } else if (MODE == PERIODIC) {
-      int64_t r = g0 % args.period;
-#pragma unroll
-      for (int i = 0; i < kItems; ++i) {
-        if (r == 0) hm |= 1u << i;
-        if (++r == args.period) r = 0;
-      }
+      hm = seg_heads<kItems>(seg_pos<kTile>(sh_r0, rel0, args), args.period);
     } else {
       hm = (sh_heads[rel0 >> 5] >> (rel0 & 31)) & 0xffffu;
     }
@@ -1600,7 +1625,8 @@ int32_t run_scan_t(const T *in, T *out, const ScanArgs &a, void *ws, size_t ws_b
   DESC_CUDA_TRY(cudaMemsetAsync(ws, 0, need, s));
   ScanWs *w = static_cast<ScanWs *>(ws);
   TileState *st = reinterpret_cast<TileState *>(static_cast<char *>(ws) + align256(sizeof(ScanWs)));
-  scan_kernel<T, O, MODE, SUB, EXCL, MAPPED><<<(unsigned)ntiles, kThreads + 32, smem, s>>>(in, out, a, w, st, m);
+  scan_kernel<T, O, MODE, SUB, EXCL, MAPPED><<<(unsigned)ntiles, kThreads + 32, smem, s>>>(in, out, with_period(a), w,
+                                                                                          st, m);
   DESC_CUDA_TRY(cudaGetLastError());
   return DESC_OK;
 }
