@@ -615,7 +615,8 @@ def run_view_overhead(torch, D, synth, dev, stream, reps=100, mbs=(256, 512, 102
 def run_operators(torch, D, dev, stream, xr, xs, pk, reps=10):
     """The operators beyond the sum at full size: int32 reduce of 2^30
     values and FP32 / int32 scans of 2^28 values with each operator family
-    (maximum, product, xor, arg-maximum), CUDA-event means of `reps` calls,
+    (maximum, product, xor, arg-maximum), and FP32 sum scans segmented per
+    block of the view group(m)[[block]] (m = 1024, 2^20), CUDA-event means of `reps` calls,
     GB/s of algorithmic bytes (reduce 4 B, scan 8 B per element) and the
     fraction of the measured copy peak."""
     V = D
@@ -646,6 +647,15 @@ def run_operators(torch, D, dev, stream, xr, xs, pk, reps=10):
                                                        stream=stream), reps)
         gbs = 8 * Sn / (ms * 1e-3) / 1e9
         out[f"scan_{name}"] = {"ms": round(ms, 4), "GB/s": round(gbs, 1), "frac": round(gbs / pk["hbm_gbs"], 4)}
+    # segmented per level: group(m)[[block]], one segment per block of the view
+    so = s_out.view(torch.float32)
+    for m in (1024, 1 << 20):
+        ops = [("group", m, 0), ("select", V.BLOCK, V.X)]
+        ms = _time(torch, stream, lambda: D.desc_scan(xs, [Sn], ops, V.BLOCK, (Sn // m, 1, 1), (1, 1, 1), out=so,
+                                                       ws=ws_, stream=stream), reps)
+        gbs = 8 * Sn / (ms * 1e-3) / 1e9
+        out[f"scan_f32_sum_per_block_{m}"] = {"ms": round(ms, 4), "GB/s": round(gbs, 1),
+                                              "frac": round(gbs / pk["hbm_gbs"], 4)}
     if D.desc_stream_status(stream) != 0:
         raise RuntimeError("device status after the operators")
     del s_out, wr, ws_
