@@ -19,8 +19,10 @@
 // the same kernels with their accumulator; the arg accumulators also take
 // each element's index in the base array and write that index (int32).
 #include <algorithm>
-
+#include <map>
+#include <mutex>
 #include <type_traits>
+#include <utility>
 
 #include "k_bodies.cuh"
 #include "k_common.cuh"
@@ -37,9 +39,18 @@ using Cand = ReduceCand;
 constexpr const Cand *kCands = kReduceCands;
 constexpr int kNumCands = kNumReduceCands;
 
-int64_t chunks_for(int64_t len, int64_t nout, const Cand &c) {
+// The candidates' CTA targets assume kNominalResident CTAs of the kernel on
+// each SM (1216 = 8 x 152: one wave).  A kernel that holds fewer (the arg
+// accumulators at 8 vectors in flight take 40 registers: 6 a SM) scales its
+// target down by its own count, so that the grid stays whole waves; never up,
+// so no candidate makes more chunks than max_chunks sized the workspace for.
+constexpr int kNominalResident = 8;
+
+int64_t chunks_for(int64_t len, int64_t nout, const Cand &c, int resident = kNominalResident) {
   const int64_t per_cta_min = int64_t(kThreads) * 4 * c.unroll;
-  int64_t by_fill = (c.target_ctas + nout - 1) / std::max<int64_t>(nout, 1);
+  const int r = std::max(1, std::min(resident, kNominalResident));
+  const int64_t target = std::max<int64_t>(1, c.target_ctas * r / kNominalResident);
+  int64_t by_fill = (target + nout - 1) / std::max<int64_t>(nout, 1);
   int64_t by_len = (len + per_cta_min - 1) / per_cta_min;
   return std::max<int64_t>(1, std::min(by_fill, by_len));
 }
@@ -324,6 +335,28 @@ __global__ void __launch_bounds__(kThreads) reduce_affine_kernel(
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
+// CTAs of `kernel` (kThreads threads, no dynamic shared memory) that one SM
+// of the current device holds, asked once per kernel and device.
+cudaError_t resident_ctas(const void *kernel, int *out) {
+  static std::mutex mu;
+  static std::map<std::pair<const void *, int>, int> known;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = known.find({kernel, dev});
+  if (it != known.end()) {
+    *out = it->second;
+    return cudaSuccess;
+  }
+  int r = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, kernel, kThreads, 0);
+  if (e != cudaSuccess) return e;
+  known[{kernel, dev}] = r;
+  *out = r;
+  return cudaSuccess;
+}
+
 size_t ws_for(int64_t len, int64_t nout) {
   if (len <= kWarpRun) return 0;
   const int64_t ch = max_chunks(len, nout);
@@ -342,7 +375,11 @@ int32_t run_runs(const T *in, int64_t start, int64_t seg_stride, int64_t len, in
     reduce_short_kernel<A, T, 32><<<(unsigned)ctas, kThreads, 0, s>>>(in, start, seg_stride, len, nout, out);
   } else {
     const Cand &cd = kCands[(cand >= 0 && cand < kNumCands) ? cand : 0];
-    const int64_t chunks = chunks_for(len, nout, cd);
+    auto kern = cd.unroll == 4 ? (cd.nc ? reduce_runs_kernel<A, T, 4, 1> : reduce_runs_kernel<A, T, 4, 0>)
+                               : (cd.nc ? reduce_runs_kernel<A, T, 8, 1> : reduce_runs_kernel<A, T, 8, 0>);
+    int resident = kNominalResident;
+    DESC_CUDA_TRY(resident_ctas(reinterpret_cast<const void *>(kern), &resident));
+    const int64_t chunks = chunks_for(len, nout, cd, resident);
     uint2 *partials = nullptr;
     unsigned *counters = nullptr;
     if (chunks > 1) {
@@ -356,18 +393,7 @@ int32_t run_runs(const T *in, int64_t start, int64_t seg_stride, int64_t len, in
     const int64_t chunk_vec = (nvec + chunks - 1) / chunks;
     if (nout * chunks >= (int64_t(1) << 31)) return DESC_ERR_UNSUPPORTED;
     const unsigned grid = (unsigned)(nout * chunks);
-    if (cd.unroll == 4 && !cd.nc)
-      reduce_runs_kernel<A, T, 4, 0><<<grid, kThreads, 0, s>>>(in, start, seg_stride, len, chunks, chunk_vec, out,
-                                                               partials, counters);
-    else if (cd.unroll == 4)
-      reduce_runs_kernel<A, T, 4, 1><<<grid, kThreads, 0, s>>>(in, start, seg_stride, len, chunks, chunk_vec, out,
-                                                               partials, counters);
-    else if (!cd.nc)
-      reduce_runs_kernel<A, T, 8, 0><<<grid, kThreads, 0, s>>>(in, start, seg_stride, len, chunks, chunk_vec, out,
-                                                               partials, counters);
-    else
-      reduce_runs_kernel<A, T, 8, 1><<<grid, kThreads, 0, s>>>(in, start, seg_stride, len, chunks, chunk_vec, out,
-                                                               partials, counters);
+    kern<<<grid, kThreads, 0, s>>>(in, start, seg_stride, len, chunks, chunk_vec, out, partials, counters);
   }
   DESC_CUDA_TRY(cudaGetLastError());
   return DESC_OK;
