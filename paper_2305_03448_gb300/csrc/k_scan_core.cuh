@@ -483,6 +483,7 @@ __global__ void __launch_bounds__(kThreads + 32, 3) scan_kernel(const T *in, T *
   __shared__ unsigned short sh_need[MODE == PLAIN ? 1 : SUB * kThreads];  // carry-needed bits
   __shared__ int64_t sh_seg0;
   __shared__ int64_t sh_r0;             // PERIODIC: t0's position in its segment
+  __shared__ int sh_tile_heads;         // PERIODIC / CSR: a segment may start in this tile
   __shared__ int sh_any_end;            // CSR: a non-empty segment ends in this tile
   __shared__ int sh_dense;              // CSR: more boundaries than one warp-wide read covers
   __shared__ volatile int sh_go;        // look-back may start polling
@@ -545,6 +546,7 @@ __global__ void __launch_bounds__(kThreads + 32, 3) scan_kernel(const T *in, T *
         }
       }
       ends = __any_sync(0xffffffffu, ends);
+      const bool any_head = __any_sync(0xffffffffu, b > t0 && b < tend);
       if (sums && tile == 0)                            // empty segments before the first element
         for (int64_t q = lane; q < s0; q += 32) sums[q] = O::id();
       if (lane == 0) {
@@ -552,6 +554,7 @@ __global__ void __launch_bounds__(kThreads + 32, 3) scan_kernel(const T *in, T *
         sh_seg0 = s0;
         sh_dense = dense ? 1 : 0;
         sh_any_end = ends;
+        sh_tile_heads = (h0 || dense || any_head) ? 1 : 0;
       }
       first_is_head = first_is_head || h0;
       heads_bar();
@@ -584,9 +587,13 @@ __global__ void __launch_bounds__(kThreads + 32, 3) scan_kernel(const T *in, T *
   if (tid == 0) {
     sh_carry = O::id();
     sh_carry_flag = 0;
-    if (MODE == PERIODIC) sh_r0 = t0 % args.period;   // one 64-bit division a tile
+    if (MODE == PERIODIC) {
+      sh_r0 = t0 % args.period;                       // one 64-bit division a tile
+      sh_tile_heads = sh_r0 == 0 || args.period - sh_r0 < kTile;
+    }
   }
 
+  bool tile_heads = false;
 #pragma unroll 1
   for (int s = 0; s < SUB; ++s) {
     unsigned char *st = ring + s * kStageBytes;
@@ -613,15 +620,21 @@ __global__ void __launch_bounds__(kThreads + 32, 3) scan_kernel(const T *in, T *
       compute_bar();                                    // ... for every thread; carry visible
     }
     if (s == SUB / 2 && tid == 0) sh_go = 1;
+    if (s == 0) tile_heads = MODE != PLAIN && sh_tile_heads;
+    // HEADS: the tile may hold segment heads; without them the sub-tile is
+    // scanned as a plain run (no flags in the warp and block scans)
+    auto sub_tile = [&](auto heads) {
+    constexpr bool HEADS = decltype(heads)::value;
     const T cv = sh_carry;
     const int cf = sh_carry_flag;
-    const int64_t g0 = t0 + int64_t(s) * kSub + int64_t(tid) * kItems;
     unsigned hmask = 0u;
-    if (MODE == PERIODIC) {
-      hmask = seg_heads<kItems>(seg_pos<kTile>(sh_r0, s * kSub + tid * kItems, args), args.period);
-    } else if (MODE == CSR) {
-      const int rel0 = s * kSub + tid * kItems;
-      hmask = (sh_heads[rel0 >> 5] >> (rel0 & 31)) & 0xffffu;
+    if constexpr (HEADS) {
+      if (MODE == PERIODIC) {
+        hmask = seg_heads<kItems>(seg_pos<kTile>(sh_r0, s * kSub + tid * kItems, args), args.period);
+      } else if (MODE == CSR) {
+        const int rel0 = s * kSub + tid * kItems;
+        hmask = (sh_heads[rel0 >> 5] >> (rel0 & 31)) & 0xffffu;
+      }
     }
     T v[kItems];
 #pragma unroll
@@ -718,6 +731,9 @@ __global__ void __launch_bounds__(kThreads + 32, 3) scan_kernel(const T *in, T *
       x.w = __builtin_bit_cast(int, v[4 * q + 3]);
       *reinterpret_cast<int4 *>(st + chunk_off((kItems / 4) * tid + q)) = x;
     }
+    };
+    if (tile_heads) sub_tile(std::true_type{});
+    else sub_tile(std::false_type{});
   }
   compute_bar();
   if (tid == 0 && !stall) {
