@@ -39,17 +39,17 @@ using Cand = ReduceCand;
 constexpr const Cand *kCands = kReduceCands;
 constexpr int kNumCands = kNumReduceCands;
 
-// The candidates' CTA targets assume kNominalResident CTAs of the kernel on
-// each SM (1216 = 8 x 152: one wave).  A kernel that holds fewer (the arg
-// accumulators at 8 vectors in flight take 40 registers: 6 a SM) scales its
-// target down by its own count, so that the grid stays whole waves; never up,
-// so no candidate makes more chunks than max_chunks sized the workspace for.
-constexpr int kNominalResident = 8;
-
-int64_t chunks_for(int64_t len, int64_t nout, const Cand &c, int resident = kNominalResident) {
+// A candidate's CTA target counts whole waves where the kernel holds 8 CTAs
+// on each SM (1216 = 8 x 152).  A kernel that holds fewer (the arg
+// accumulators at 8 vectors in flight take 40 registers: 6 a SM) would leave
+// a ragged last wave, so a target above one wave of the kernel's own
+// (per_wave = CTAs a SM x SMs) is cut to whole waves; a target within one
+// wave is kept.  Targets only shrink, so no candidate makes more chunks than
+// max_chunks sized the workspace for.
+int64_t chunks_for(int64_t len, int64_t nout, const Cand &c, int64_t per_wave = 0) {
   const int64_t per_cta_min = int64_t(kThreads) * 4 * c.unroll;
-  const int r = std::max(1, std::min(resident, kNominalResident));
-  const int64_t target = std::max<int64_t>(1, c.target_ctas * r / kNominalResident);
+  const int64_t target = per_wave > 0 && c.target_ctas > per_wave ? (c.target_ctas / per_wave) * per_wave
+                                                                    : c.target_ctas;
   int64_t by_fill = (target + nout - 1) / std::max<int64_t>(nout, 1);
   int64_t by_len = (len + per_cta_min - 1) / per_cta_min;
   return std::max<int64_t>(1, std::min(by_fill, by_len));
@@ -335,11 +335,11 @@ __global__ void __launch_bounds__(kThreads) reduce_affine_kernel(
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-// CTAs of `kernel` (kThreads threads, no dynamic shared memory) that one SM
-// of the current device holds, asked once per kernel and device.
-cudaError_t resident_ctas(const void *kernel, int *out) {
+// CTAs of `kernel` (kThreads threads, no dynamic shared memory) that all
+// SMs of the current device hold at once, asked once per kernel and device.
+cudaError_t wave_ctas(const void *kernel, int64_t *out) {
   static std::mutex mu;
-  static std::map<std::pair<const void *, int>, int> known;
+  static std::map<std::pair<const void *, int>, int64_t> known;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
@@ -349,11 +349,12 @@ cudaError_t resident_ctas(const void *kernel, int *out) {
     *out = it->second;
     return cudaSuccess;
   }
-  int r = 0;
+  int r = 0, sms = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, kernel, kThreads, 0);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
-  known[{kernel, dev}] = r;
-  *out = r;
+  known[{kernel, dev}] = int64_t(r) * sms;
+  *out = int64_t(r) * sms;
   return cudaSuccess;
 }
 
@@ -377,9 +378,9 @@ int32_t run_runs(const T *in, int64_t start, int64_t seg_stride, int64_t len, in
     const Cand &cd = kCands[(cand >= 0 && cand < kNumCands) ? cand : 0];
     auto kern = cd.unroll == 4 ? (cd.nc ? reduce_runs_kernel<A, T, 4, 1> : reduce_runs_kernel<A, T, 4, 0>)
                                : (cd.nc ? reduce_runs_kernel<A, T, 8, 1> : reduce_runs_kernel<A, T, 8, 0>);
-    int resident = kNominalResident;
-    DESC_CUDA_TRY(resident_ctas(reinterpret_cast<const void *>(kern), &resident));
-    const int64_t chunks = chunks_for(len, nout, cd, resident);
+    int64_t per_wave = 0;
+    DESC_CUDA_TRY(wave_ctas(reinterpret_cast<const void *>(kern), &per_wave));
+    const int64_t chunks = chunks_for(len, nout, cd, per_wave);
     uint2 *partials = nullptr;
     unsigned *counters = nullptr;
     if (chunks > 1) {
