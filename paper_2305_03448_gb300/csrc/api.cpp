@@ -201,8 +201,8 @@ extern "C" int32_t desc_scan(const desc_view *v, const desc_exec *ex, int32_t se
   if (!(flags & kMapScanOps))
     return launch_scan_mapped(dtype, in, out, L.offset, L.extent, L.stride, L.ndims, sp.period, flags, ws, ws_bytes,
                               s);
-  return launch_scan_map(dtype, in, out, L.offset, L.extent, L.stride, L.ndims, sp.period, nullptr, 0, nullptr,
-                         flags, ws, ws_bytes, s);
+  return launch_scan_arg_mapped(dtype, in, out, L.offset, L.extent, L.stride, L.ndims, sp.period, flags, ws, ws_bytes,
+                                s);
 }
 
 // ---------------------------------------------------------------- scan, no allocation

@@ -66,11 +66,12 @@ bool same_map_quick(const desc_lowered &a, const desc_lowered &b);
 int32_t check_device_ptr(const void *p, size_t align);
 
 // Device status words of the translation units that hold bounded waits
-// (scan_status_take reads the five scan units' words).
+// (scan_status_take reads the six scan units' words).
 int32_t scan_status_take();          // k_scan.cu
 int32_t scan_status_take_ops();      // k_scan_ops.cu
 int32_t scan_status_take_mapped();   // k_scan_mapped.cu
 int32_t scan_status_take_mapped2();  // k_scan_mapped2.cu
+int32_t scan_status_take_argmap();   // k_scan_arg_mapped.cu
 int32_t scan_status_take_map();      // k_scan_map.cu
 int32_t mm_status_take();            // k_mm_tc.cu
 
@@ -152,6 +153,12 @@ int32_t launch_scan_map(int32_t dtype, const void *in, void *out, int64_t off, c
 int32_t launch_scan_mapped(int32_t dtype, const void *in, void *out, int64_t off, const int64_t *ext,
                            const int64_t *stride, int nd, int64_t period, int32_t flags, void *ws, size_t ws_bytes,
                            desc_stream_t s);
+// Arg-maximum / arg-minimum scans through a lowered map (plain or per-level
+// segments): the arg look-back scan for maps of one or two canonical dims,
+// launch_scan_map for others.
+int32_t launch_scan_arg_mapped(int32_t dtype, const void *in, void *out, int64_t off, const int64_t *ext,
+                               const int64_t *stride, int nd, int64_t period, int32_t flags, void *ws,
+                               size_t ws_bytes, desc_stream_t s);
 int32_t launch_scan_mapped_2d(int32_t dtype, const void *in, void *out, int64_t off, const int64_t *ext,
                               const int64_t *stride, int nd, int64_t period, int32_t flags, void *ws,
                               size_t ws_bytes, desc_stream_t s);

@@ -12,8 +12,8 @@ constexpr int32_t kOtherValueOps = DESC_PROD | DESC_AND | DESC_OR | DESC_XOR;
 
 int32_t scan_status_take() {
   // every unit's word is read (and cleared); the first error is reported
-  const int32_t w[5] = {take_status_word(), scan_status_take_ops(), scan_status_take_mapped(),
-                        scan_status_take_mapped2(), scan_status_take_map()};
+  const int32_t w[6] = {take_status_word(), scan_status_take_ops(), scan_status_take_mapped(),
+                        scan_status_take_mapped2(), scan_status_take_argmap(), scan_status_take_map()};
   for (int32_t v : w)
     if (v != DESC_OK) return v;
   return DESC_OK;

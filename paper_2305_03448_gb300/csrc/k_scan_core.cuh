@@ -1285,16 +1285,22 @@ constexpr int kArgTile = kSub * kArgSub;
 constexpr int kArgSmem = kArgSub * kStageBytes;
 static_assert(kItems == 16, "a thread's points are one 16-bit head mask");
 
+// MAPPED (the map's dims, 1 or 2; 0: a contiguous run): points are read and
+// written through the lowered map m, and point g is element m(g) of the base
+// array; there the element indices need not grow with g, so the scan keeps
+// every point's full key (code, ~index) instead of its position.
 template <class T, bool MAX, int MODE, bool EXCL, int SUBS = kArgSub, bool PIPE = kArgPipe,
-          int MINB = (MODE == PERIODIC ? 3 : kArgBlocksPerSM)>
+          int MINB = (MODE == PERIODIC ? 3 : kArgBlocksPerSM), int MAPPED = 0>
 __global__ void __launch_bounds__(kThreads + 32, MINB) scan_arg_kernel(const T *in, int32_t *out, ScanArgs args,
                                                                     int64_t idx_base, ScanWs *ws,
-                                                                    TileState *states) {
+                                                                    TileState *states,
+                                                                    const __grid_constant__ MapArgs m) {
   using S = ArgKeys<T, MAX>;
   using E = typename S::E;
   using O = typename S::Op;
   using CT = typename S::C;
   static_assert(SUBS * kWarps <= 32 && SUBS <= 4, "one lane a warp total");
+  static_assert(MAPPED == 0 || MODE != CSR, "the CSR call scans contiguous runs");
   constexpr int kTile = kSub * SUBS;
   constexpr int kTotals = SUBS * kWarps;           // warp totals in tile order
   extern __shared__ __align__(128) unsigned char ring[];   // SUBS stages
@@ -1311,8 +1317,10 @@ __global__ void __launch_bounds__(kThreads + 32, MINB) scan_arg_kernel(const T *
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t n = args.n;
-  const MapArgs none{};
-  const RunAddr addr{none};
+  using Addr = typename std::conditional<MAPPED == 0, RunAddr, MapAddr<MAPPED == 2 ? 2 : 1>>::type;
+  const Addr addr{m};
+  // the key of a point of code c at g: (c, ~ element index)
+  auto key_at = [&](uint32_t c, int64_t g) -> E { return ((E)c << 32) | (uint32_t)~(uint32_t)addr(g); };
   if (tid == 0) {
     sh_tile = atomicAdd(&ws->ticket, 1u);
     sh_go = 0;
@@ -1324,7 +1332,7 @@ __global__ void __launch_bounds__(kThreads + 32, MINB) scan_arg_kernel(const T *
 #pragma unroll
     for (int k = 0; k < kTile / 32 / kThreads; ++k) {
       const int64_t g = guess + 32 * int64_t(k * kThreads + tid);
-      if (g < n) asm volatile("prefetch.global.L2 [%0];" ::"l"(in + g));
+      if (g < n) asm volatile("prefetch.global.L2 [%0];" ::"l"(in + addr(g)));
     }
   }
   __syncthreads();
@@ -1390,6 +1398,7 @@ __global__ void __launch_bounds__(kThreads + 32, MINB) scan_arg_kernel(const T *
   int exf[SUBS];
   unsigned hmq[SUBS];
   uint32_t tmax[SUBS];                                  // the best code after the thread's last head
+  E tkey[SUBS];                                         // MAPPED: the best key after it
 #pragma unroll
   for (int s = 0; s < SUBS; ++s) {
     unsigned char *st = ring + s * kStageBytes;
@@ -1422,26 +1431,45 @@ __global__ void __launch_bounds__(kThreads + 32, MINB) scan_arg_kernel(const T *
       c[4 * q + 3] = order_code<T, MAX>(__builtin_bit_cast(T, x.w));
       *p = make_int4(int(c[4 * q]), int(c[4 * q + 1]), int(c[4 * q + 2]), int(c[4 * q + 3]));
     }
-    // the best code after the thread's last head, its first position on ties
-    uint32_t best = 0u;
-    int pos = -1;
-    if (hm == 0u && lim == kItems) {                    // the maximum, then its first position
-      best = c[0];
+    E a;
+    if constexpr (MAPPED == 0) {
+      // the best code after the thread's last head, its first position on ties
+      uint32_t best = 0u;
+      int pos = -1;
+      if (hm == 0u && lim == kItems) {                  // the maximum, then its first position
+        best = c[0];
 #pragma unroll
-      for (int i = 1; i < kItems; ++i) best = max(best, c[i]);
-      pos = kItems - 1;
+        for (int i = 1; i < kItems; ++i) best = max(best, c[i]);
+        pos = kItems - 1;
 #pragma unroll
-      for (int i = kItems - 2; i >= 0; --i) pos = c[i] == best ? i : pos;
+        for (int i = kItems - 2; i >= 0; --i) pos = c[i] == best ? i : pos;
+      } else {
+#pragma unroll
+        for (int i = 0; i < kItems; ++i)
+          if (i < lim && (((hm >> i) & 1u) || pos < 0 || c[i] > best)) {
+            best = c[i];
+            pos = i;
+          }
+      }
+      tmax[s] = best;
+      a = pos < 0 ? S::eid() : ((E)best << 32) | (uint32_t)~(uint32_t)(ibase + s * kSub + pos);
     } else {
+      // the largest key after the thread's last head
+      E kb = S::eid();
+      if (hm == 0u && lim == kItems) {
 #pragma unroll
-      for (int i = 0; i < kItems; ++i)
-        if (i < lim && (((hm >> i) & 1u) || pos < 0 || c[i] > best)) {
-          best = c[i];
-          pos = i;
-        }
+        for (int i = 0; i < kItems; ++i) kb = S::ecomb(kb, key_at(c[i], g0 + i));
+      } else {
+#pragma unroll
+        for (int i = 0; i < kItems; ++i)
+          if (i < lim) {
+            const E ki = key_at(c[i], g0 + i);
+            kb = ((hm >> i) & 1u) ? ki : S::ecomb(kb, ki);
+          }
+      }
+      tkey[s] = kb;
+      a = kb;
     }
-    tmax[s] = best;
-    E a = pos < 0 ? S::eid() : ((E)best << 32) | (uint32_t)~(uint32_t)(ibase + s * kSub + pos);
     int f = hm != 0u;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {           // warp scan, segmented operator
@@ -1521,7 +1549,31 @@ __global__ void __launch_bounds__(kThreads + 32, MINB) scan_arg_kernel(const T *
     const bool full = lim64 >= kItems;
     int32_t r[kItems];
     auto chunk = [&](int q) { return reinterpret_cast<int4 *>(st + chunk_off((kItems / 4) * tid + q)); };
-    if (hm == 0u && full && idx >= 0 && best >= tmax[s]) {
+    if constexpr (MAPPED != 0) {
+      // the running key; a start key at least the thread's largest beats every point
+      E cur = e0;
+      if (hm == 0u && full && cur >= tkey[s]) {
+#pragma unroll
+        for (int i = 0; i < kItems; ++i) r[i] = int32_t(~uint32_t(cur));
+      } else {
+#pragma unroll
+        for (int q = 0; q < kItems / 4; ++q) {
+          const int4 x = *chunk(q);
+          const uint32_t cs[4] = {uint32_t(x.x), uint32_t(x.y), uint32_t(x.z), uint32_t(x.w)};
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const int i = 4 * q + c;
+            const bool head = (hm >> i) & 1u;
+            if (EXCL) r[i] = head ? -1 : int32_t(~uint32_t(cur));   // key 0: index -1
+            if (i < lim64) {
+              const E ki = key_at(cs[c], g0 + i);
+              cur = head ? ki : S::ecomb(cur, ki);
+            }
+            if (!EXCL) r[i] = int32_t(~uint32_t(cur));
+          }
+        }
+      }
+    } else if (hm == 0u && full && idx >= 0 && best >= tmax[s]) {
       // the start state beats every point (on a tie it comes first)
 #pragma unroll
       for (int i = 0; i < kItems; ++i) r[i] = idx;
@@ -1587,12 +1639,12 @@ __global__ void __launch_bounds__(kThreads + 32, MINB) scan_arg_kernel(const T *
         const int4 v = *reinterpret_cast<const int4 *>(st + chunk_off(j));
         const int64_t g = t0 + s * kSub + 4 * int64_t(j);
         if (args.vec && g + 4 <= n) {
-          __stcs(reinterpret_cast<int4 *>(out + g), v);
+          __stcs(reinterpret_cast<int4 *>(out + addr(g)), v);
         } else {
           const int32_t w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
           for (int c = 0; c < 4; ++c)
-            if (g + c < n) out[g + c] = w[c];
+            if (g + c < n) out[addr(g + c)] = w[c];
         }
       }
     }

@@ -88,8 +88,7 @@ int32_t launch_scan_arg(int32_t dtype, const void *in, void *out, int64_t n, int
   auto launch = [&](auto kernel, auto typed_in) -> int32_t {
     DESC_CUDA_TRY(allow_arg_smem(reinterpret_cast<const void *>(kernel)));
     kernel<<<(unsigned)ntiles, kThreads + 32, kArgSmem, s>>>(typed_in, static_cast<int32_t *>(out), with_period(a),
-                                                              idx_base, w,
-                                                              ts);
+                                                              idx_base, w, ts, MapArgs{});
     DESC_CUDA_TRY(cudaGetLastError());
     return DESC_OK;
   };

@@ -277,3 +277,23 @@ def test_arg_scan_unaligned_buffers(op):
             got = D.desc_scan(xd, [n], [], V.GRID, out=out, flags=flags).cpu().numpy()
             want, _ = O.scan_op(x[1:].numpy(), np.zeros(n, np.int32), [n], [], V.GRID, op, excl)
             assert np.array_equal(got.astype(np.int64), np.asarray(want).astype(np.int64))
+
+
+@pytest.mark.parametrize("op", ["argmax", "argmin"])
+def test_arg_scan_mapped_many_tiles(op):
+    """Arg scans through maps of one and two dims over many 8192-point tiles,
+    with many ties (ties go to the smallest base index, which a reversed or
+    column view visits last): a reversed array, the columns of a matrix as
+    one scan and as one segment per column, every view inclusive and
+    exclusive, int32 and FP32, against the oracle."""
+    R, C = 301, 997
+    n = R * C
+    cases = [([("reverse", 0)], V.GRID, None, None),
+             ([("group", C, 0), ("transpose", 0)], V.GRID, None, None),
+             ([("group", C, 0), ("transpose", 0), ("select", V.BLOCK, V.X)], V.BLOCK, (C, 1, 1), (1, 1, 1)),
+             ([("group", C, 0), ("reverse", 1), ("select", V.BLOCK, V.X)], V.BLOCK, (R, 1, 1), (1, 1, 1))]
+    for dtype in ("i32", "f32"):
+        x = data(op, dtype, n, 53)
+        for ops, lvl, g, b in cases:
+            for excl in (False, True):
+                check_scan(x, op, excl, ops, lvl, g, b)
