@@ -615,7 +615,7 @@ def run_view_overhead(torch, D, synth, dev, stream, reps=100, mbs=(256, 512, 102
 def run_operators(torch, D, dev, stream, xr, xs, pk, reps=10):
     """The operators beyond the sum at full size: int32 reduce of 2^30
     values and FP32 / int32 scans of 2^28 values with each operator family
-    (maximum, product, xor, arg-maximum; the arg-maximum also through a reversed view), and FP32 sum scans segmented per
+    (maximum, product, xor, arg-maximum; the arg-maximum and the sum also through a reversed view), and FP32 sum scans segmented per
     block of the view group(m)[[block]] (m = 1024, 2^20), CUDA-event means of `reps` calls,
     GB/s of algorithmic bytes (reduce 4 B, scan 8 B per element) and the
     fraction of the measured copy peak."""
@@ -652,6 +652,10 @@ def run_operators(torch, D, dev, stream, xr, xs, pk, reps=10):
                                                    stream=stream), reps)
     gbs = 8 * Sn / (ms * 1e-3) / 1e9
     out["scan_f32_argmax_reversed"] = {"ms": round(ms, 4), "GB/s": round(gbs, 1), "frac": round(gbs / pk["hbm_gbs"], 4)}
+    ms = _time(torch, stream, lambda: D.desc_scan(xs, [Sn], [("reverse", 0)], V.GRID, out=s_out.view(torch.float32),
+                                                   ws=ws_, stream=stream), reps)
+    gbs = 8 * Sn / (ms * 1e-3) / 1e9
+    out["scan_f32_sum_reversed"] = {"ms": round(ms, 4), "GB/s": round(gbs, 1), "frac": round(gbs / pk["hbm_gbs"], 4)}
     # segmented per level: group(m)[[block]], one segment per block of the view
     so = s_out.view(torch.float32)
     for m in (1024, 1 << 20):

@@ -23,7 +23,7 @@ int32_t run_arg_mapped(int32_t dtype, const void *in, void *out, const MapArgs &
   a.n = n;
   a.period = period > 0 ? period : n;
   a.debug = (flags & DESC_DEBUG_STALL_TILE) ? 1 : 0;
-  a.vec = map_vec(m, in, out) ? 1 : 0;
+  a.vec = map_load_mode(m, in, out);
   const bool periodic = a.period < n;
   const bool mx = (flags & DESC_ARGMAX) != 0, ex = (flags & DESC_EXCLUSIVE) != 0;
   DESC_CUDA_TRY(cudaMemsetAsync(ws, 0, need, s));

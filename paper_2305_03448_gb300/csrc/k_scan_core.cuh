@@ -265,7 +265,7 @@ struct ScanArgs {
   int64_t nseg;
   void *sums;              // CSR: per-segment totals (may be null)
   int32_t debug;           // 1: tile 1 never publishes (tests the timeout path)
-  int32_t vec;             // in and out are 16-byte aligned: 128-bit accesses
+  int32_t vec;             // 128-bit accesses: 1 ascending, 2 descending chunks (load_sub); 0 none
   FastDiv pdiv;            // PERIODIC: the period, where it is below 2^30 (set by with_period)
 };
 
@@ -405,27 +405,39 @@ __device__ __forceinline__ void compute_bar() { asm volatile("bar.sync 1, %0;" :
 __device__ __forceinline__ void heads_bar() { asm volatile("bar.sync 2, %0;" ::"n"(kThreads + 32) : "memory"); }
 
 // Start copying kSub elements from g_start (elements past n read as zero);
-// point g is in[addr(g)].
+// point g is in[addr(g)].  vec: 0, one element a copy; 1, four consecutive
+// points are four ascending elements on a 16-byte boundary; 2, four
+// descending ones (a reversed run), copied whole and so stored in the chunk
+// last point first -- every chunk of such a stage is in that order, the
+// partial one at the end too, and readers swap it.
 template <class T, class A>
 __device__ __forceinline__ void load_sub(unsigned char *stage, const T *in, int64_t g_start,
-                                         int64_t n, bool vec, const A &addr) {
+                                         int64_t n, int vec, const A &addr) {
 #pragma unroll
   for (int q = 0; q < kSubChunks / kThreads; ++q) {
     const int j = q * kThreads + threadIdx.x;
     const int64_t g = g_start + 4 * int64_t(j);
     unsigned char *dst = stage + chunk_off(j);
-    if (vec) {
+    if (vec == 1) {
       const int64_t rem = n - g;
       const int bytes = rem >= 4 ? 16 : (rem > 0 ? int(rem) * 4 : 0);
       cp_async16(dst, bytes ? static_cast<const void *>(in + addr(g)) : static_cast<const void *>(in), bytes);
+    } else if (vec == 2 && g + 4 <= n) {
+      cp_async16(dst, in + addr(g + 3), 16);
     } else {
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
-        if (g + c < n) cp_async4(dst + 4 * c, in + addr(g + c));
-        else *reinterpret_cast<T *>(dst + 4 * c) = T(0);
+        unsigned char *slot = dst + 4 * (vec == 2 ? 3 - c : c);
+        if (g + c < n) cp_async4(slot, in + addr(g + c));
+        else *reinterpret_cast<T *>(slot) = T(0);
       }
     }
   }
+}
+
+// A chunk of a stage in point order (see load_sub).
+__device__ __forceinline__ int4 chunk_in_order(int4 x, int vec) {
+  return vec == 2 ? make_int4(x.w, x.z, x.y, x.x) : x;
 }
 
 __device__ __forceinline__ void cp_async_wait_dyn(int pending) {
@@ -490,7 +502,7 @@ __global__ void __launch_bounds__(kThreads + 32, 3) scan_kernel(const T *in, T *
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t n = args.n;
-  const bool vec = args.vec != 0;
+  const int vec = MAPPED == 1 ? args.vec : (args.vec != 0 ? 1 : 0);   // 2 only through one-dim maps
   using Addr = typename std::conditional<MAPPED == 0, RunAddr, MapAddr<MAPPED == 2 ? 2 : 1>>::type;
   const Addr addr{m};
   if (tid == 0) {
@@ -639,7 +651,7 @@ __global__ void __launch_bounds__(kThreads + 32, 3) scan_kernel(const T *in, T *
     T v[kItems];
 #pragma unroll
     for (int q = 0; q < kItems / 4; ++q) {
-      const int4 x = *reinterpret_cast<const int4 *>(st + chunk_off((kItems / 4) * tid + q));
+      const int4 x = chunk_in_order(*reinterpret_cast<const int4 *>(st + chunk_off((kItems / 4) * tid + q)), vec);
       v[4 * q] = __builtin_bit_cast(T, x.x);
       v[4 * q + 1] = __builtin_bit_cast(T, x.y);
       v[4 * q + 2] = __builtin_bit_cast(T, x.z);
@@ -789,12 +801,18 @@ __global__ void __launch_bounds__(kThreads + 32, 3) scan_kernel(const T *in, T *
 #pragma unroll
         for (int c = 0; c < 4; ++c) y[c] = e[c];
       }
-      if (vec && g + 4 <= n) {
+      if (vec == 1 && g + 4 <= n) {
         x.x = __builtin_bit_cast(int, y[0]);
         x.y = __builtin_bit_cast(int, y[1]);
         x.z = __builtin_bit_cast(int, y[2]);
         x.w = __builtin_bit_cast(int, y[3]);
         __stcs(reinterpret_cast<int4 *>(out + addr(g)), x);
+      } else if (vec == 2 && g + 4 <= n) {              // descending: the last point's element first
+        x.x = __builtin_bit_cast(int, y[3]);
+        x.y = __builtin_bit_cast(int, y[2]);
+        x.z = __builtin_bit_cast(int, y[1]);
+        x.w = __builtin_bit_cast(int, y[0]);
+        __stcs(reinterpret_cast<int4 *>(out + addr(g + 3)), x);
       } else {
 #pragma unroll
         for (int c = 0; c < 4; ++c)
@@ -1318,6 +1336,7 @@ __global__ void __launch_bounds__(kThreads + 32, MINB) scan_arg_kernel(const T *
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t n = args.n;
   using Addr = typename std::conditional<MAPPED == 0, RunAddr, MapAddr<MAPPED == 2 ? 2 : 1>>::type;
+  const int vec = MAPPED == 1 ? args.vec : (args.vec != 0 ? 1 : 0);   // 2 only through one-dim maps
   const Addr addr{m};
   // the key of a point of code c at g: (c, ~ element index)
   auto key_at = [&](uint32_t c, int64_t g) -> E { return ((E)c << 32) | (uint32_t)~(uint32_t)addr(g); };
@@ -1365,7 +1384,7 @@ __global__ void __launch_bounds__(kThreads + 32, MINB) scan_arg_kernel(const T *
   // ---- compute warps
 #pragma unroll
   for (int s = 0; s < SUBS; ++s) {
-    load_sub<T>(ring + s * kStageBytes, in, t0 + int64_t(s) * kSub, n, args.vec != 0, addr);
+    load_sub<T>(ring + s * kStageBytes, in, t0 + int64_t(s) * kSub, n, vec, addr);
     cp_async_commit();
   }
   if (MODE == CSR) {                                   // segment heads: offsets[q] in (t0, tend), and t0
@@ -1424,7 +1443,7 @@ __global__ void __launch_bounds__(kThreads + 32, MINB) scan_arg_kernel(const T *
 #pragma unroll
     for (int q = 0; q < kItems / 4; ++q) {
       int4 *p = reinterpret_cast<int4 *>(st + chunk_off((kItems / 4) * tid + q));
-      const int4 x = *p;
+      const int4 x = chunk_in_order(*p, vec);
       c[4 * q + 0] = order_code<T, MAX>(__builtin_bit_cast(T, x.x));
       c[4 * q + 1] = order_code<T, MAX>(__builtin_bit_cast(T, x.y));
       c[4 * q + 2] = order_code<T, MAX>(__builtin_bit_cast(T, x.z));
@@ -1620,7 +1639,7 @@ __global__ void __launch_bounds__(kThreads + 32, MINB) scan_arg_kernel(const T *
     }
     if (keep_incl) {
       int32_t *o = out + g0;
-      if (args.vec && full) {
+      if (vec == 1 && full) {
 #pragma unroll
         for (int q = 0; q < kItems / 4; ++q)
           __stcs(reinterpret_cast<int4 *>(o) + q, make_int4(r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]));
@@ -1638,8 +1657,10 @@ __global__ void __launch_bounds__(kThreads + 32, MINB) scan_arg_kernel(const T *
         const int j = (kItems / 4) * 32 * warp + 32 * q + lane;   // chunk of the sub-tile
         const int4 v = *reinterpret_cast<const int4 *>(st + chunk_off(j));
         const int64_t g = t0 + s * kSub + 4 * int64_t(j);
-        if (args.vec && g + 4 <= n) {
+        if (vec == 1 && g + 4 <= n) {
           __stcs(reinterpret_cast<int4 *>(out + addr(g)), v);
+        } else if (vec == 2 && g + 4 <= n) {            // descending: the last point's element first
+          __stcs(reinterpret_cast<int4 *>(out + addr(g + 3)), make_int4(v.w, v.z, v.y, v.x));
         } else {
           const int32_t w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
@@ -1914,6 +1935,18 @@ bool map_vec(const MapArgs &m, const void *in, const void *out) {
 }
 
 
+// 128-bit accesses to a reversed run: a one-dim map of stride -1 whose
+// chunks of four points (from a multiple of 4) end on a 16-byte boundary.
+bool map_descending(const MapArgs &m, const void *in, const void *out) {
+  return ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15) == 0 && m.nd == 1 &&
+         m.st[0] == -1 && (m.off + 1) % 4 == 0;
+}
+
+// The load mode of the look-back scans through a map (see load_sub).
+int map_load_mode(const MapArgs &m, const void *in, const void *out) {
+  return map_vec(m, in, out) ? 1 : (map_descending(m, in, out) ? 2 : 0);
+}
+
 // The look-back scan through a map of ND (1 or 2) canonical dims: every
 // value operator, plain or per-level segments.
 template <int ND>
@@ -1923,7 +1956,7 @@ int32_t run_scan_mapped_nd(int32_t dtype, const void *in, void *out, const MapAr
   a.n = n;
   a.period = period > 0 ? period : n;
   a.debug = (flags & DESC_DEBUG_STALL_TILE) ? 1 : 0;
-  a.vec = map_vec(m, in, out) ? 1 : 0;
+  a.vec = map_load_mode(m, in, out);
   const bool periodic = a.period < n;
   const bool basic = !(flags & (DESC_PROD | DESC_AND | DESC_OR | DESC_XOR));
   auto go = [&](auto tag) -> int32_t {

@@ -297,3 +297,9 @@ def test_arg_scan_mapped_many_tiles(op):
         for ops, lvl, g, b in cases:
             for excl in (False, True):
                 check_scan(x, op, excl, ops, lvl, g, b)
+        # a reversed run whose chunks of four end on 16-byte boundaries (whole 128-bit
+        # copies, read last point first), whole and with a ragged end
+        x4 = data(op, dtype, 300_004, 54)
+        for ops in ([("reverse", 0)], [("split_snd", 777, 0), ("reverse", 0)]):
+            for excl in (False, True):
+                check_scan(x4, op, excl, ops)
