@@ -303,3 +303,21 @@ def test_arg_scan_mapped_many_tiles(op):
         for ops in ([("reverse", 0)], [("split_snd", 777, 0), ("reverse", 0)]):
             for excl in (False, True):
                 check_scan(x4, op, excl, ops)
+
+
+@pytest.mark.parametrize("op", ["argmax", "argmin"])
+def test_arg_scan_general_path(op):
+    """desc_force_generic: contiguous arg scans through the map form of the
+    arg look-back scan (a one-dim map of stride 1, 128-bit copies), plain and
+    one segment per block, against the oracle."""
+    n = 5 * 8192 + 12
+    D.desc_force_generic(True)
+    try:
+        for dtype in ("i32", "f32"):
+            x = data(op, dtype, n, 61)
+            for excl in (False, True):
+                check_scan(x, op, excl)
+                check_scan(x, op, excl, [("group", 4, 0), ("select", V.BLOCK, V.X)], V.BLOCK, (n // 4, 1, 1),
+                           (1, 1, 1), seg_len=4)
+    finally:
+        D.desc_force_generic(False)
