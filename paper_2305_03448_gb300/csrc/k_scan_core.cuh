@@ -409,8 +409,8 @@ __device__ __forceinline__ void heads_bar() { asm volatile("bar.sync 2, %0;" ::"
 // points are four ascending elements on a 16-byte boundary; 2, four
 // descending ones (a reversed run), copied whole and so stored in the chunk
 // last point first -- every chunk of such a stage is in that order, the
-// partial one at the end too, and readers swap it.
-template <class T, class A>
+// partial one at the end too, and readers swap it (DESC: the caller may pass 2).
+template <class T, bool DESC = false, class A>
 __device__ __forceinline__ void load_sub(unsigned char *stage, const T *in, int64_t g_start,
                                          int64_t n, int vec, const A &addr) {
 #pragma unroll
@@ -422,12 +422,12 @@ __device__ __forceinline__ void load_sub(unsigned char *stage, const T *in, int6
       const int64_t rem = n - g;
       const int bytes = rem >= 4 ? 16 : (rem > 0 ? int(rem) * 4 : 0);
       cp_async16(dst, bytes ? static_cast<const void *>(in + addr(g)) : static_cast<const void *>(in), bytes);
-    } else if (vec == 2 && g + 4 <= n) {
+    } else if (DESC && vec == 2 && g + 4 <= n) {
       cp_async16(dst, in + addr(g + 3), 16);
     } else {
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
-        unsigned char *slot = dst + 4 * (vec == 2 ? 3 - c : c);
+        unsigned char *slot = dst + 4 * (DESC && vec == 2 ? 3 - c : c);
         if (g + c < n) cp_async4(slot, in + addr(g + c));
         else *reinterpret_cast<T *>(slot) = T(0);
       }
@@ -435,9 +435,12 @@ __device__ __forceinline__ void load_sub(unsigned char *stage, const T *in, int6
   }
 }
 
-// A chunk of a stage in point order (see load_sub).
+// A chunk of a stage in point order (see load_sub); only a scan through a
+// one-dim map (DESC = true) can have descending chunks.
+template <bool DESC>
 __device__ __forceinline__ int4 chunk_in_order(int4 x, int vec) {
-  return vec == 2 ? make_int4(x.w, x.z, x.y, x.x) : x;
+  if constexpr (DESC) return vec == 2 ? make_int4(x.w, x.z, x.y, x.x) : x;
+  return x;
 }
 
 __device__ __forceinline__ void cp_async_wait_dyn(int pending) {
@@ -593,7 +596,7 @@ __global__ void __launch_bounds__(kThreads + 32, 3) scan_kernel(const T *in, T *
   // ---- compute warps
 #pragma unroll
   for (int s = 0; s < SUB; ++s) {
-    load_sub<T>(ring + s * kStageBytes, in, t0 + int64_t(s) * kSub, n, vec, addr);
+    load_sub<T, MAPPED == 1>(ring + s * kStageBytes, in, t0 + int64_t(s) * kSub, n, vec, addr);
     cp_async_commit();
   }
   if (tid == 0) {
@@ -651,7 +654,7 @@ __global__ void __launch_bounds__(kThreads + 32, 3) scan_kernel(const T *in, T *
     T v[kItems];
 #pragma unroll
     for (int q = 0; q < kItems / 4; ++q) {
-      const int4 x = chunk_in_order(*reinterpret_cast<const int4 *>(st + chunk_off((kItems / 4) * tid + q)), vec);
+      const int4 x = chunk_in_order<MAPPED == 1>(*reinterpret_cast<const int4 *>(st + chunk_off((kItems / 4) * tid + q)), vec);
       v[4 * q] = __builtin_bit_cast(T, x.x);
       v[4 * q + 1] = __builtin_bit_cast(T, x.y);
       v[4 * q + 2] = __builtin_bit_cast(T, x.z);
@@ -807,7 +810,7 @@ __global__ void __launch_bounds__(kThreads + 32, 3) scan_kernel(const T *in, T *
         x.z = __builtin_bit_cast(int, y[2]);
         x.w = __builtin_bit_cast(int, y[3]);
         __stcs(reinterpret_cast<int4 *>(out + addr(g)), x);
-      } else if (vec == 2 && g + 4 <= n) {              // descending: the last point's element first
+      } else if (MAPPED == 1 && vec == 2 && g + 4 <= n) {   // descending: the last point's element first
         x.x = __builtin_bit_cast(int, y[3]);
         x.y = __builtin_bit_cast(int, y[2]);
         x.z = __builtin_bit_cast(int, y[1]);
@@ -1384,7 +1387,7 @@ __global__ void __launch_bounds__(kThreads + 32, MINB) scan_arg_kernel(const T *
   // ---- compute warps
 #pragma unroll
   for (int s = 0; s < SUBS; ++s) {
-    load_sub<T>(ring + s * kStageBytes, in, t0 + int64_t(s) * kSub, n, vec, addr);
+    load_sub<T, MAPPED == 1>(ring + s * kStageBytes, in, t0 + int64_t(s) * kSub, n, vec, addr);
     cp_async_commit();
   }
   if (MODE == CSR) {                                   // segment heads: offsets[q] in (t0, tend), and t0
@@ -1443,7 +1446,7 @@ __global__ void __launch_bounds__(kThreads + 32, MINB) scan_arg_kernel(const T *
 #pragma unroll
     for (int q = 0; q < kItems / 4; ++q) {
       int4 *p = reinterpret_cast<int4 *>(st + chunk_off((kItems / 4) * tid + q));
-      const int4 x = chunk_in_order(*p, vec);
+      const int4 x = chunk_in_order<MAPPED == 1>(*p, vec);
       c[4 * q + 0] = order_code<T, MAX>(__builtin_bit_cast(T, x.x));
       c[4 * q + 1] = order_code<T, MAX>(__builtin_bit_cast(T, x.y));
       c[4 * q + 2] = order_code<T, MAX>(__builtin_bit_cast(T, x.z));
@@ -1659,7 +1662,7 @@ __global__ void __launch_bounds__(kThreads + 32, MINB) scan_arg_kernel(const T *
         const int64_t g = t0 + s * kSub + 4 * int64_t(j);
         if (vec == 1 && g + 4 <= n) {
           __stcs(reinterpret_cast<int4 *>(out + addr(g)), v);
-        } else if (vec == 2 && g + 4 <= n) {            // descending: the last point's element first
+        } else if (MAPPED == 1 && vec == 2 && g + 4 <= n) {   // descending: the last point's element first
           __stcs(reinterpret_cast<int4 *>(out + addr(g + 3)), make_int4(v.w, v.z, v.y, v.x));
         } else {
           const int32_t w[4] = {v.x, v.y, v.z, v.w};
