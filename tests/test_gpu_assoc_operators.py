@@ -321,3 +321,25 @@ def test_arg_scan_general_path(op):
                            (1, 1, 1), seg_len=4)
     finally:
         D.desc_force_generic(False)
+
+
+@pytest.mark.parametrize("op", ["argmax", "argmin", "sum", "max", "xor"])
+def test_scan_reversed_runs_per_block(op):
+    """A reversed array grouped per block lowers to one dim of stride -1 with
+    a period: per-level segments through the descending 128-bit copies, the
+    segment length a multiple of 4 and not, against the oracle."""
+    n = 12 * 4100                                        # six 8192-point tiles and a ragged seventh
+    for m in (8, 1025, 4100, 4920):
+        ops = [("reverse", 0), ("group", m, 0), ("select", V.BLOCK, V.X)]
+        for dtype in (("i32", "f32") if op in ("argmax", "argmin", "sum", "max") else ("i32",)):
+            x = data(op, dtype, n, 71) if op in INT_OPS else (
+                synth.ints_pm1000(n, seed=71) if dtype == "i32" else synth.uniform_grid(n, seed=71))
+            for excl in (False, True):
+                if op == "sum" and dtype == "f32":
+                    got = D.desc_scan(x.cuda(), [n], ops, V.BLOCK, (n // m, 1, 1), (1, 1, 1),
+                                      flags=D.EXCLUSIVE if excl else 0).cpu().numpy()
+                    want, pa = O.scan_op(x.numpy(), np.zeros(n, np.float32), [n], ops, V.BLOCK, "sum", excl,
+                                         (n // m, 1, 1), (1, 1, 1))
+                    assert np.all(np.abs(got - want) <= 1e-5 * pa + 1e-30)
+                else:
+                    check_scan(x, op, excl, ops, V.BLOCK, (n // m, 1, 1), (1, 1, 1), seg_len=m)
