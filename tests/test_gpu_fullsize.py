@@ -8,6 +8,8 @@ bench.py times (every schedule candidate the autotuner may pick):
   matmul    8192^3 (SPLIT3 and BF16) -- 64 sampled rows against the FP64 product
   segmented 20,000 log-uniform segments (about 1.5e9 elements) -- 64 sampled
             segments in full, and the sums of all segments against their scans
+  arg scan  2^28 FP32 arg-maximum, plain and through a reversed view -- sampled
+            prefixes against the oracle's selection
 """
 import numpy as np
 import pytest
@@ -108,3 +110,28 @@ def test_segmented_20000_sampled_segments():
     nz = offh[1:] > offh[:-1]
     last = torch.from_numpy(offh[1:][nz] - 1).cuda()
     assert torch.equal(sums[torch.from_numpy(nz).cuda()], out[last])
+
+
+def test_arg_scan_2_28_sampled():
+    """The arg-maximum scan of 2^28 FP32 (the operators benchmark), plain and
+    through a reversed view: sampled outputs against the oracle's selection
+    over each prefix (ties to the smallest element index), and the last
+    output against the arg-maximum reduce of the whole array."""
+    n = 1 << 28
+    x = synth.uniform_grid(n, seed=81, device="cuda")
+    xn = x.cpu().numpy()
+    rng = np.random.default_rng(3)
+    # mostly short prefixes (the oracle converts each prefix to FP64), three long ones
+    picks = [0, 1, 8191, 8192, 1 << 20, n - 1, int(rng.integers(0, n)), int(rng.integers(0, n))] + \
+        [int(p) for p in rng.integers(0, 1 << 22, 4)]
+    got = D.desc_scan(x, [n], [], V.GRID, flags=D.ARGMAX).cpu().numpy()
+    for p in picks:
+        assert int(got[p]) == O.arg_pick(xn[:p + 1], np.arange(p + 1), "argmax"), p
+    assert int(got[n - 1]) == D.desc_reduce(x, [n], [], V.GRID, flags=D.ARGMAX).item()
+    # reversed: point p is element n-1-p, its prefix the elements n-1-p .. n-1, written at n-1-p
+    got = D.desc_scan(x, [n], [("reverse", 0)], V.GRID, flags=D.ARGMAX).cpu().numpy()
+    for p in picks:
+        e = n - 1 - p
+        assert int(got[e]) == O.arg_pick(xn[e:], np.arange(e, n), "argmax"), p
+    del x
+    torch.cuda.empty_cache()
