@@ -490,7 +490,7 @@ __global__ void __launch_bounds__(kThreads + 32, 3) scan_kernel(const T *in, T *
   __shared__ int64_t sh_tile;
   __shared__ T sh_wval[kWarps];
   __shared__ int sh_wflag[kWarps];
-  __shared__ T sh_carry;                // in-tile carry after the sub-tiles done so far
+  __shared__ T sh_carry;                // the tile aggregate, once its sub-tiles are scanned
   __shared__ int sh_carry_flag;
   __shared__ CT sh_prefix;
   __shared__ int sh_ok;
@@ -609,6 +609,8 @@ __global__ void __launch_bounds__(kThreads + 32, 3) scan_kernel(const T *in, T *
   }
 
   bool tile_heads = false;
+  T run_cv = O::id();                                   // the in-tile carry, the same in every thread
+  int run_cf = 0;
 #pragma unroll 1
   for (int s = 0; s < SUB; ++s) {
     unsigned char *st = ring + s * kStageBytes;
@@ -640,8 +642,8 @@ __global__ void __launch_bounds__(kThreads + 32, 3) scan_kernel(const T *in, T *
     // scanned as a plain run (no flags in the warp and block scans)
     auto sub_tile = [&](auto heads) {
     constexpr bool HEADS = decltype(heads)::value;
-    const T cv = sh_carry;
-    const int cf = sh_carry_flag;
+    const T cv = run_cv;                                // the in-tile carry before this sub-tile
+    const int cf = run_cf;
     unsigned hmask = 0u;
     if constexpr (HEADS) {
       if (MODE == PERIODIC) {
@@ -681,43 +683,35 @@ __global__ void __launch_bounds__(kThreads + 32, 3) scan_kernel(const T *in, T *
     }
     if (lane == 31) {
       sh_wval[warp] = a;
-      sh_wflag[warp] = f;
+      if (HEADS) sh_wflag[warp] = f;
     }
     T ex = __shfl_up_sync(0xffffffffu, a, 1);
     int exf = __shfl_up_sync(0xffffffffu, f, 1);
     if (lane == 0) { ex = O::id(); exf = 0; }
-    compute_bar();
-    if (warp == 0) {                                    // scan of the warp totals
-      T wa = lane < kWarps ? sh_wval[lane] : O::id();
-      int wf = lane < kWarps ? sh_wflag[lane] : 0;
+    compute_bar();                                      // the sub-tile's warp totals are visible
+    // every warp scans the warp totals itself (no warp waits for another, no
+    // second barrier); the carry for the next sub-tile stays in registers
+    T wa = lane < kWarps ? sh_wval[lane] : O::id();
+    int wf = HEADS && lane < kWarps ? sh_wflag[lane] : 0;
 #pragma unroll
-      for (int off = 1; off < kWarps; off <<= 1) {
-        const T au = __shfl_up_sync(0xffffffffu, wa, off);
-        const int fu = __shfl_up_sync(0xffffffffu, wf, off);
-        if (lane >= off) {
-          if (!wf) wa = O::comb(au, wa);
-          wf |= fu;
-        }
-      }
-      T we = __shfl_up_sync(0xffffffffu, wa, 1);
-      int wfe = __shfl_up_sync(0xffffffffu, wf, 1);
-      if (lane == 0) { we = O::id(); wfe = 0; }
-      const T sub_val = __shfl_sync(0xffffffffu, wa, kWarps - 1);
-      const int sub_flag = __shfl_sync(0xffffffffu, wf, kWarps - 1);
-      __syncwarp();
-      if (lane < kWarps) {
-        sh_wval[lane] = we;
-        sh_wflag[lane] = wfe;
-      }
-      if (lane == 0) {                                  // carry after this sub-tile
-        sh_carry = sub_flag ? sub_val : O::comb(cv, sub_val);
-        sh_carry_flag = cf | sub_flag;
+    for (int off = 1; off < kWarps; off <<= 1) {
+      const T au = __shfl_up_sync(0xffffffffu, wa, off);
+      const int fu = __shfl_up_sync(0xffffffffu, wf, off);
+      if (lane >= off) {
+        if (!wf) wa = O::comb(au, wa);
+        wf |= fu;
       }
     }
-    compute_bar();
+    T we = __shfl_up_sync(0xffffffffu, wa, 1);
+    int wfe = __shfl_up_sync(0xffffffffu, wf, 1);
+    if (lane == 0) { we = O::id(); wfe = 0; }
+    const T sub_val = __shfl_sync(0xffffffffu, wa, kWarps - 1);
+    const int sub_flag = __shfl_sync(0xffffffffu, wf, kWarps - 1);
+    run_cv = sub_flag ? sub_val : O::comb(cv, sub_val);
+    run_cf = cf | sub_flag;
     // prefix of this thread within the tile: carry, then warp, then thread
-    T pv = sh_wval[warp];
-    int pf = sh_wflag[warp];
+    const T pv = __shfl_sync(0xffffffffu, we, warp);
+    const int pf = __shfl_sync(0xffffffffu, wfe, warp);
     if (!exf) ex = O::comb(pv, ex);
     exf |= pf;                                          // (pf, pv) (+) (exf, ex)
     const T in_tile = exf ? ex : O::comb(cv, ex);
@@ -749,6 +743,10 @@ __global__ void __launch_bounds__(kThreads + 32, 3) scan_kernel(const T *in, T *
     };
     if (tile_heads) sub_tile(std::true_type{});
     else sub_tile(std::false_type{});
+  }
+  if (tid == 0) {                                       // the tile's aggregate, for the publish and the look-back warp
+    sh_carry = run_cv;
+    sh_carry_flag = run_cf;
   }
   compute_bar();
   if (tid == 0 && !stall) {
