@@ -10,6 +10,7 @@ bench.py times (every schedule candidate the autotuner may pick):
             segments in full, and the sums of all segments against their scans
   arg scan  2^28 FP32 arg-maximum, plain and through a reversed view -- sampled
             prefixes against the oracle's selection
+  per-block 2^28 FP32 sums in segments of 1024 and 2^20 -- sampled segments in full
 """
 import numpy as np
 import pytest
@@ -133,5 +134,26 @@ def test_arg_scan_2_28_sampled():
     for p in picks:
         e = n - 1 - p
         assert int(got[e]) == O.arg_pick(xn[e:], np.arange(e, n), "argmax"), p
+    del x
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("m", [1024, 1 << 20])
+def test_scan_per_block_2_28_sampled(m):
+    """FP32 sum scans of 2^28 segmented per block of group(m)[[block]] (the
+    operators benchmark): 24 sampled segments, each against the oracle's scan
+    of that segment, every element within 1e-5 * sum_{q<=p}|x_q|."""
+    n = 1 << 28
+    x = synth.uniform_grid(n, seed=91, device="cuda")
+    ops = [("group", m, 0), ("select", V.BLOCK, V.X)]
+    got = D.desc_scan(x, [n], ops, V.BLOCK, (n // m, 1, 1), (1, 1, 1)).cpu().numpy()
+    xn = x.cpu().numpy()
+    rng = np.random.default_rng(5)
+    segs = sorted({0, n // m - 1} | {int(s) for s in rng.integers(0, n // m, 22)})
+    for sgi in segs:
+        a, b = sgi * m, (sgi + 1) * m
+        want, pa = O.scan(xn[a:b], np.zeros(m, np.float32), [m], [], V.GRID)
+        err = np.abs(got[a:b].astype(np.float64) - want)
+        assert np.all(err <= 1e-5 * pa + 1e-30), (sgi, float(err.max()))
     del x
     torch.cuda.empty_cache()
