@@ -236,7 +236,9 @@ __device__ __forceinline__ int64_t map_elem(const MapArgs &m, int64_t g) {
 // or a lowered map.
 struct RunAddr {
   const MapArgs &m;                                     // not used
+  static constexpr bool kAffine = true;                 // addr(g + k) = addr(g) + step(k)
   __device__ int64_t operator()(int64_t g) const { return g; }
+  __device__ int64_t step(int64_t k) const { return k; }
 };
 // The look-back scan takes maps of one or two dims, the count fixed at
 // compile time (a run-time test of it cost 7 % of the scan), decoded inline
@@ -248,6 +250,8 @@ struct RunAddr {
 template <int ND>
 struct MapAddr {
   const MapArgs &m;
+  static constexpr bool kAffine = ND == 1;              // addr(g + k) = addr(g) + step(k)
+  __device__ int64_t step(int64_t k) const { return k * m.st[0]; }
   __device__ int64_t operator()(int64_t g) const {
     if constexpr (ND == 1) {
       return m.off + int64_t(int32_t(g)) * int64_t(int32_t(m.st[0]));
@@ -413,22 +417,26 @@ __device__ __forceinline__ void heads_bar() { asm volatile("bar.sync 2, %0;" ::"
 template <class T, bool DESC = false, class A>
 __device__ __forceinline__ void load_sub(unsigned char *stage, const T *in, int64_t g_start,
                                          int64_t n, int vec, const A &addr) {
+  // an affine map: chunk q's element from the first chunk's by q steps
+  const int64_t e0 = A::kAffine ? addr(g_start + 4 * int64_t(threadIdx.x)) : 0;
+  const int64_t de = A::kAffine ? addr.step(4 * kThreads) : 0;
 #pragma unroll
   for (int q = 0; q < kSubChunks / kThreads; ++q) {
     const int j = q * kThreads + threadIdx.x;
     const int64_t g = g_start + 4 * int64_t(j);
+    const int64_t eg = A::kAffine ? e0 + q * de : addr(g);   // the element of point g
     unsigned char *dst = stage + chunk_off(j);
     if (vec == 1) {
       const int64_t rem = n - g;
       const int bytes = rem >= 4 ? 16 : (rem > 0 ? int(rem) * 4 : 0);
-      cp_async16(dst, bytes ? static_cast<const void *>(in + addr(g)) : static_cast<const void *>(in), bytes);
+      cp_async16(dst, bytes ? static_cast<const void *>(in + eg) : static_cast<const void *>(in), bytes);
     } else if (DESC && vec == 2 && g + 4 <= n) {
-      cp_async16(dst, in + addr(g + 3), 16);
+      cp_async16(dst, in + (A::kAffine ? eg + addr.step(3) : addr(g + 3)), 16);
     } else {
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         unsigned char *slot = dst + 4 * (DESC && vec == 2 ? 3 - c : c);
-        if (g + c < n) cp_async4(slot, in + addr(g + c));
+        if (g + c < n) cp_async4(slot, in + (A::kAffine ? eg + addr.step(c) : addr(g + c)));
         else *reinterpret_cast<T *>(slot) = T(0);
       }
     }
@@ -762,13 +770,16 @@ __global__ void __launch_bounds__(kThreads + 32, 3) scan_kernel(const T *in, T *
   // no segment head takes the carry on every element
   const CT pre = sh_prefix;
   const bool no_heads = MODE == PLAIN || !sh_carry_flag;
+  const int64_t de = Addr::kAffine ? addr.step(4 * kThreads) : 0;   // elements from chunk j to j + kThreads
 #pragma unroll 1
   for (int s = 0; s < SUB; ++s) {
     const unsigned char *st = ring + s * kStageBytes;
+    const int64_t e0 = Addr::kAffine ? addr(t0 + int64_t(s) * kSub + 4 * int64_t(tid)) : 0;
 #pragma unroll
     for (int q = 0; q < kSubChunks / kThreads; ++q) {
       const int j = q * kThreads + tid;
       const int64_t g = t0 + int64_t(s) * kSub + 4 * int64_t(j);
+      const int64_t eg = Addr::kAffine ? e0 + q * de : addr(g);   // the element of point g
       int4 x = *reinterpret_cast<const int4 *>(st + chunk_off(j));
       const unsigned nb = no_heads ? 0xfu : (unsigned(sh_need[s * kThreads + (j >> 2)]) >> ((j & 3) * 4)) & 0xfu;
       T y[4] = {__builtin_bit_cast(T, x.x), __builtin_bit_cast(T, x.y), __builtin_bit_cast(T, x.z),
@@ -807,17 +818,17 @@ __global__ void __launch_bounds__(kThreads + 32, 3) scan_kernel(const T *in, T *
         x.y = __builtin_bit_cast(int, y[1]);
         x.z = __builtin_bit_cast(int, y[2]);
         x.w = __builtin_bit_cast(int, y[3]);
-        __stcs(reinterpret_cast<int4 *>(out + addr(g)), x);
+        __stcs(reinterpret_cast<int4 *>(out + eg), x);
       } else if (MAPPED == 1 && vec == 2 && g + 4 <= n) {   // descending: the last point's element first
         x.x = __builtin_bit_cast(int, y[3]);
         x.y = __builtin_bit_cast(int, y[2]);
         x.z = __builtin_bit_cast(int, y[1]);
         x.w = __builtin_bit_cast(int, y[0]);
-        __stcs(reinterpret_cast<int4 *>(out + addr(g + 3)), x);
+        __stcs(reinterpret_cast<int4 *>(out + eg + addr.step(3)), x);
       } else {
 #pragma unroll
         for (int c = 0; c < 4; ++c)
-          if (g + c < n) out[addr(g + c)] = y[c];
+          if (g + c < n) out[Addr::kAffine ? eg + addr.step(c) : addr(g + c)] = y[c];
       }
     }
   }
@@ -1653,20 +1664,23 @@ __global__ void __launch_bounds__(kThreads + 32, MINB) scan_arg_kernel(const T *
 #pragma unroll
       for (int q = 0; q < kItems / 4; ++q) *chunk(q) = make_int4(r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
       __syncwarp();                                     // the warp's 512 results are in its own slots
+      const int64_t gw = t0 + s * kSub + 4 * int64_t((kItems / 4) * 32 * warp + lane);   // chunk q = 0
+      const int64_t e0 = Addr::kAffine ? addr(gw) : 0, de = Addr::kAffine ? addr.step(4 * 32) : 0;
 #pragma unroll
       for (int q = 0; q < kItems / 4; ++q) {
         const int j = (kItems / 4) * 32 * warp + 32 * q + lane;   // chunk of the sub-tile
         const int4 v = *reinterpret_cast<const int4 *>(st + chunk_off(j));
         const int64_t g = t0 + s * kSub + 4 * int64_t(j);
+        const int64_t eg = Addr::kAffine ? e0 + q * de : addr(g);   // the element of point g
         if (vec == 1 && g + 4 <= n) {
-          __stcs(reinterpret_cast<int4 *>(out + addr(g)), v);
+          __stcs(reinterpret_cast<int4 *>(out + eg), v);
         } else if (MAPPED == 1 && vec == 2 && g + 4 <= n) {   // descending: the last point's element first
-          __stcs(reinterpret_cast<int4 *>(out + addr(g + 3)), make_int4(v.w, v.z, v.y, v.x));
+          __stcs(reinterpret_cast<int4 *>(out + eg + addr.step(3)), make_int4(v.w, v.z, v.y, v.x));
         } else {
           const int32_t w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
           for (int c = 0; c < 4; ++c)
-            if (g + c < n) out[addr(g + c)] = w[c];
+            if (g + c < n) out[Addr::kAffine ? eg + addr.step(c) : addr(g + c)] = w[c];
         }
       }
     }
