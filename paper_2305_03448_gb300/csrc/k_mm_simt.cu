@@ -1,11 +1,12 @@
 // FP32 matrix multiplication on the CUDA cores (the non-tensor baseline).
 //
 // Classic register-tiled SGEMM: a CTA of 256 threads computes a 128 x 128
-// or 128 x 256 tile of C; K advances in steps of 8 through double-buffered
+// (or 128 x 256) tile of C; K advances in steps of 8 through double-buffered
 // shared memory (A stored transposed so both operands are read as float4
-// rows).  Each thread accumulates an 8 x 8 or 8 x 16 block held as 4 x 4
+// rows).  Each thread accumulates an 8 x 8 (or 8 x 16) block held as 4 x 4
 // quadrants 64 rows / columns apart, so the float4 shared-memory reads of a
-// warp are bank-conflict-free.
+// warp are bank-conflict-free, and multiplies with the paired FP32 FMA
+// (fma.rn.f32x2) on column pairs.
 // Global loads are register-prefetched one K step ahead.  Edges are guarded
 // (zero fill on load, bounds on store).
 #include "k_common.cuh"
@@ -57,11 +58,13 @@ __global__ void __launch_bounds__(256) sgemm_kernel(const float *__restrict__ A,
     }
   };
 
-  float acc[8][4 * NQ];
+  // accumulators as column pairs (2p, 2p + 1): one fma.rn.f32x2 does the two
+  // FMAs of a pair (per lane exactly fmaf), half the FMA instructions to issue
+  unsigned long long acc2[8][2 * NQ];
 #pragma unroll
   for (int i = 0; i < 8; ++i)
 #pragma unroll
-    for (int j = 0; j < 4 * NQ; ++j) acc[i][j] = 0.f;
+    for (int p = 0; p < 2 * NQ; ++p) acc2[i][p] = 0ull;
 
   float ra[4], rb[VB];
   auto store_b = [&](int nb) {
@@ -89,16 +92,21 @@ __global__ void __launch_bounds__(256) sgemm_kernel(const float *__restrict__ A,
       const float4 a0 = *reinterpret_cast<const float4 *>(&As[buf][k][ty * 4]);
       const float4 a1 = *reinterpret_cast<const float4 *>(&As[buf][k][64 + ty * 4]);
       const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-      float b[4 * NQ];
+      unsigned long long b2[2 * NQ];
 #pragma unroll
       for (int q = 0; q < NQ; ++q) {
         const float4 bq = *reinterpret_cast<const float4 *>(&Bs[buf][k][q * 64 + tx * 4]);
-        b[4 * q] = bq.x; b[4 * q + 1] = bq.y; b[4 * q + 2] = bq.z; b[4 * q + 3] = bq.w;
+        asm("mov.b64 %0, {%1, %2};" : "=l"(b2[2 * q]) : "f"(bq.x), "f"(bq.y));
+        asm("mov.b64 %0, {%1, %2};" : "=l"(b2[2 * q + 1]) : "f"(bq.z), "f"(bq.w));
       }
 #pragma unroll
-      for (int i = 0; i < 8; ++i)
+      for (int i = 0; i < 8; ++i) {
+        unsigned long long a2;                          // a[i] in both halves
+        asm("mov.b64 %0, {%1, %1};" : "=l"(a2) : "f"(a[i]));
 #pragma unroll
-        for (int j = 0; j < 4 * NQ; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        for (int p = 0; p < 2 * NQ; ++p)
+          asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc2[i][p]) : "l"(a2), "l"(b2[p]));
+      }
     }
     if (more) {
       const int nb = buf ^ 1;
@@ -110,6 +118,12 @@ __global__ void __launch_bounds__(256) sgemm_kernel(const float *__restrict__ A,
     }
   }
   const bool c_vec = (ldc % 4 == 0) && ((reinterpret_cast<uintptr_t>(C) & 15) == 0);
+  float acc[8][4 * NQ];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int p = 0; p < 2 * NQ; ++p)
+      asm("mov.b64 {%0, %1}, %2;" : "=f"(acc[i][2 * p]), "=f"(acc[i][2 * p + 1]) : "l"(acc2[i][p]));
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
     const int64_t r = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + i - 4);
@@ -143,19 +157,14 @@ int32_t launch_nq(const float *A, const float *B, float *C, int64_t M, int64_t N
 }
 }  // namespace
 
-// 128 x 256 tiles (8 x 16 outputs per thread: 6 float4 shared loads per 128
-// FMAs instead of 4 per 64) where they make at least eight waves of CTAs,
-// else 128 x 128 (measured on GB300: 8192^3 22.8 -> 21.7 ms, but 4096^3,
-// 3.4 waves, 2.86 -> 3.11 ms).  Both give the same bits.
+// 128 x 128 tiles (8 x 8 outputs per thread, 128 registers: two CTAs per
+// SM).  With the paired FMAs it beats the 128 x 256 tile at every size
+// measured on GB300 (8192^3: 19.6 against 20.8 ms; 4096^3: 2.59 against
+// 3.02 ms); with single FMAs the wide tile had won at 8192^3 (22.7 against
+// 23.6 ms).  All give the same bits.
 int32_t launch_sgemm(const float *A, const float *B, float *C, int64_t M, int64_t N, int64_t K, int64_t lda,
                      int64_t ldb, int64_t ldc, desc_stream_t st) {
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(st);
-  int dev = 0, nsm = 0;
-  DESC_CUDA_TRY(cudaGetDevice(&dev));
-  DESC_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  const int64_t wide_ctas = ((M + SBM - 1) / SBM) * ((N + 255) / 256);
-  if (wide_ctas >= 8 * int64_t(nsm)) return launch_nq<4>(A, B, C, M, N, K, lda, ldb, ldc, s);
-  return launch_nq<2>(A, B, C, M, N, K, lda, ldb, ldc, s);
+  return launch_nq<2>(A, B, C, M, N, K, lda, ldb, ldc, reinterpret_cast<cudaStream_t>(st));
 }
 
 }  // namespace desc
