@@ -1258,6 +1258,27 @@ __device__ __forceinline__ uint32_t order_code(T x) {
   }
 }
 
+// The value a (non-zero) order code stands for: order_code inverted, -0
+// coming back as +0.
+template <class T, bool MAX>
+__device__ __forceinline__ T code_value(uint32_t code) {
+  const uint32_t k = MAX ? code : ~code;
+  if constexpr (std::is_same<T, float>::value) {
+    return __uint_as_float((k & 0x80000000u) ? (k ^ 0x80000000u) : ~k);
+  } else {
+    return T(k ^ 0x80000000u);
+  }
+}
+
+// The better of two values under the arg operator's order, NaN losing to
+// every number (fmaxf / fminf return the other operand); which of two equal
+// values (+0, -0) comes back does not matter to the callers.
+template <class T, bool MAX>
+__device__ __forceinline__ T value_better(T a, T b) {
+  if constexpr (std::is_same<T, float>::value) return MAX ? fmaxf(a, b) : fminf(a, b);
+  else return MAX ? max(a, b) : min(a, b);
+}
+
 template <class T, bool MAX>
 struct ArgKeys {
   using E = unsigned long long;
@@ -1451,35 +1472,48 @@ __global__ void __launch_bounds__(kThreads + 32, MINB) scan_arg_kernel(const T *
       hm = (sh_heads[rel0 >> 5] >> (rel0 & 31)) & 0xffffu;
     }
     hmq[s] = hm;
+    // a contiguous scan leaves the values in the stage (pass 2 compares values);
+    // a scan through a map replaces them by their order codes
+    T xv[kItems];
     uint32_t c[kItems];
 #pragma unroll
     for (int q = 0; q < kItems / 4; ++q) {
       int4 *p = reinterpret_cast<int4 *>(st + chunk_off((kItems / 4) * tid + q));
       const int4 x = chunk_in_order<MAPPED == 1>(*p, vec);
-      c[4 * q + 0] = order_code<T, MAX>(__builtin_bit_cast(T, x.x));
-      c[4 * q + 1] = order_code<T, MAX>(__builtin_bit_cast(T, x.y));
-      c[4 * q + 2] = order_code<T, MAX>(__builtin_bit_cast(T, x.z));
-      c[4 * q + 3] = order_code<T, MAX>(__builtin_bit_cast(T, x.w));
-      *p = make_int4(int(c[4 * q]), int(c[4 * q + 1]), int(c[4 * q + 2]), int(c[4 * q + 3]));
+      xv[4 * q + 0] = __builtin_bit_cast(T, x.x);
+      xv[4 * q + 1] = __builtin_bit_cast(T, x.y);
+      xv[4 * q + 2] = __builtin_bit_cast(T, x.z);
+      xv[4 * q + 3] = __builtin_bit_cast(T, x.w);
+      if constexpr (MAPPED != 0) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) c[4 * q + e] = order_code<T, MAX>(xv[4 * q + e]);
+        *p = make_int4(int(c[4 * q]), int(c[4 * q + 1]), int(c[4 * q + 2]), int(c[4 * q + 3]));
+      }
     }
     E a;
     if constexpr (MAPPED == 0) {
       // the best code after the thread's last head, its first position on ties
       uint32_t best = 0u;
       int pos = -1;
-      if (hm == 0u && lim == kItems) {                  // the maximum, then its first position
-        best = c[0];
+      if (hm == 0u && lim == kItems) {                  // the extreme value, then its first position
+        T mv = xv[0];
 #pragma unroll
-        for (int i = 1; i < kItems; ++i) best = max(best, c[i]);
+        for (int i = 1; i < kItems; ++i) mv = value_better<T, MAX>(mv, xv[i]);   // NaN loses
         pos = kItems - 1;
 #pragma unroll
-        for (int i = kItems - 2; i >= 0; --i) pos = c[i] == best ? i : pos;
+        for (int i = kItems - 2; i >= 0; --i) pos = xv[i] == mv ? i : pos;      // -0 == +0
+        if constexpr (std::is_same<T, float>::value)
+          if (mv != mv) pos = 0;                        // all NaN: the first
+        best = order_code<T, MAX>(mv);
       } else {
 #pragma unroll
         for (int i = 0; i < kItems; ++i)
-          if (i < lim && (((hm >> i) & 1u) || pos < 0 || c[i] > best)) {
-            best = c[i];
-            pos = i;
+          if (i < lim) {
+            const uint32_t ci = order_code<T, MAX>(xv[i]);
+            if (((hm >> i) & 1u) || pos < 0 || ci > best) {
+              best = ci;
+              pos = i;
+            }
           }
       }
       tmax[s] = best;
@@ -1611,18 +1645,22 @@ __global__ void __launch_bounds__(kThreads + 32, MINB) scan_arg_kernel(const T *
       if (keep_incl)
 #pragma unroll
         for (int q = 0; q < kItems / 4; ++q) *chunk(q) = make_int4(idx, idx, idx, idx);
-    } else if (hm == 0u && full) {
+    } else if (hm == 0u && full && (best != 0u || !std::is_same<T, float>::value)) {
+      // compare values: the start state's value (a FP32 code 0 is a NaN, which
+      // every number beats: the per-point codes below take that case)
+      T bv = code_value<T, MAX>(best);
 #pragma unroll
       for (int q = 0; q < kItems / 4; ++q) {
         const int4 x = *chunk(q);
-        const uint32_t cs[4] = {uint32_t(x.x), uint32_t(x.y), uint32_t(x.z), uint32_t(x.w)};
+        const T xs[4] = {__builtin_bit_cast(T, x.x), __builtin_bit_cast(T, x.y), __builtin_bit_cast(T, x.z),
+                         __builtin_bit_cast(T, x.w)};
         int32_t in4[4];
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
           const int i = 4 * q + c;
           if (EXCL) r[i] = idx;
-          const bool gt = cs[c] > best;
-          best = gt ? cs[c] : best;
+          const bool gt = MAX ? xs[c] > bv : xs[c] < bv;   // NaN and equal values lose
+          bv = gt ? xs[c] : bv;
           idx = gt ? ib + i : idx;
           if (!EXCL) r[i] = idx;
           in4[c] = idx;
@@ -1634,7 +1672,10 @@ __global__ void __launch_bounds__(kThreads + 32, MINB) scan_arg_kernel(const T *
       for (int q = 0; q < kItems / 4; ++q) {
         int4 *p = chunk(q);
         const int4 x = *p;
-        const uint32_t cs[4] = {uint32_t(x.x), uint32_t(x.y), uint32_t(x.z), uint32_t(x.w)};
+        const uint32_t cs[4] = {order_code<T, MAX>(__builtin_bit_cast(T, x.x)),
+                                order_code<T, MAX>(__builtin_bit_cast(T, x.y)),
+                                order_code<T, MAX>(__builtin_bit_cast(T, x.z)),
+                                order_code<T, MAX>(__builtin_bit_cast(T, x.w))};
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
           const int i = 4 * q + c;
