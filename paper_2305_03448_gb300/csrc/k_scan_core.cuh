@@ -1314,15 +1314,17 @@ struct ArgKeys {
 // The look-back scan's pipeline (ticket with the guessed tile prefetched,
 // cp.async into the swizzled stages, a look-back warp) over tiles of two
 // 4096-point sub-tiles, for the arg-maximum / arg-minimum: point g is element
-// idx_base + g.  Two passes over the staged tile.  The first turns every
-// element into its 32-bit order code, in place, and reduces each thread's 16
-// points of each sub-tile to (code, first position of the best) after the
-// last segment head among them; the threads' aggregates, as 64-bit keys, are
-// scanned over the whole tile at once (warp shuffles, then every warp scans
-// the 16 warp totals itself: two barriers a tile).  Once the look-back prefix
-// is known the second pass walks each thread's points from its start state,
-// one 32-bit comparison a point, and stores the 16 indices (inclusive or
-// exclusive) straight from registers.  The tile state carries ArgKeys.
+// idx_base + g.  Two passes over the staged tile.  The first reduces each
+// thread's 16 points of each sub-tile to its best after the last segment head
+// among them -- on the values (a NaN-losing max / min, then the first
+// position holding it) with one 32-bit order code for the result -- and
+// scans the threads' results, as 64-bit keys, over the whole tile at once
+// (warp shuffles, then every warp scans the 16 warp totals itself).  Once the
+// look-back prefix is known the second pass walks each thread's points from
+// its start state, one value comparison a point (a thread whose start beats
+// all its points writes the start's index 16 times), and each warp stores its
+// 512 indices (inclusive or exclusive) as whole rows through its own slots
+// of the stage.  The tile state carries ArgKeys.
 // SUBS sub-tiles a tile; PIPE: pass 1 takes each sub-tile as it lands (one
 // barrier each, the look-back released at the first) instead of all at once;
 // MINB CTAs a SM (registers capped to fit; three for PERIODIC, whose head
